@@ -1,0 +1,2 @@
+"""Seeded synthetic inputs shared by the oracle and the CUDA path (no method arithmetic)."""
+from .workloads import *  # noqa: F401,F403
