@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Throughput of the per-step metadynamics bias path on one GB300.
+
+Metric: atom-steps/s of one whole step (cell-list neighbour build, per-atom
+coordination number and locally averaged Q6, their FP64 means, the
+well-tempered Gaussian-hill bias from a 200 x 200 FP64 grid plus 20,000 live
+hills, the adjoint and the bias forces; a hill deposited every 500 frames) on
+the 1,000,000-atom half-wurtzite / half-liquid workload, frames resident in
+HBM.  One JSON line on stdout.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl metad|reference]
+
+--impl reference times the FP64 CPU oracle (the slow, plain restatement the
+tests compare against) on the host cores instead.  Under torchrun each rank
+runs an independent replica (weak scaling; the path has no exchange step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "atom-steps/s CV+bias+force at 1M atoms (%HBM roofline); served p50/p99 vs plain"
+UNIT = "atom-steps/s"
+WORKLOAD = ("1M-atom half-wurtzite/half-RSA-liquid periodic box (228.6 A), 2 CVs (unlike-pair coordination "
+            "number + locally averaged Q6, rc 3.5 A), FP64 bias = 200x200 bicubic-Hermite grid (20,000 folded "
+            "hills) + 20,000 live well-tempered hills, one deposit per 500 frames")
+
+# FP32 peak of the dominant (ALU-bound) kernel: 152 SMs x 128 FP32 lanes x 2
+# flop per FMA x 2.07 GHz maximum SM clock.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# Algorithmic work per unordered neighbour pair (one evaluation; the kernels
+# evaluate each pair from both ends, which is not counted).
+FLOP_PER_PAIR = {"force": 340.0, "cv_fwd": 130.0, "cv_avg": 45.0, "adjoint": 45.0, "neighbors": 0.0}
+# Algorithmic bytes per atom of each stage (compulsory traffic, FP32 state).
+BYTES_PER_ATOM = {"bin": 16 + 16 + 4 * 6, "neighbors": 16 + 4 + 4 * 15.45, "cv_fwd": 16 + 4 + 4 * 15.45 + 60,
+                  "cv_avg": 16 + 4 + 4 * 15.45 + 56 + 60, "adjoint": 16 + 4 + 4 * 15.45 + 56 + 56,
+                  "force": 16 + 4 + 4 * 15.45 + 160 + 12 + 4}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="metad", choices=["metad", "reference"])
+    ap.add_argument("--frames", type=int, default=16, help="distinct resident frames, cycled")
+    ap.add_argument("--e2e-steps", type=int, default=40)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--atoms", type=int, default=1_000_000, help="workload size (1M is the reported config)")
+    ap.add_argument("--hills", type=int, default=None, help="live hills (default: the workload's 20,000)")
+    ap.add_argument("--hills-folded", type=int, default=None, help="hills folded into the grid (default 20,000)")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- helpers
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def kbdt(mp):
+    return mp.kB * mp.temperature * (mp.biasfactor - 1.0)
+
+
+def make_system(n):
+    if n == 1_000_000:
+        return synth.config3_system()
+    return synth.wurtzite_system(n, cfg=3)
+
+
+# ---------------------------------------------------------------- CPU legs
+def oracle_sample(n_atoms, frames, nthreads=0):
+    """The FP64 oracle on `frames` frames of the workload (hills and grid set up
+    by the oracle itself, not timed).  Returns (atom-steps/s, cores, seconds)."""
+    import oracle
+    system = make_system(n_atoms)
+    mp = synth.method_params(3)
+    cfgp = synth.CONFIG_PARAMS[3]
+    p = oracle.params_from(mp, system.box)
+    s_ref, _, _ = oracle.cv(system.base, p, nthreads)
+    K1, K2 = cfgp["hills_folded"], cfgp["hills"]
+    cen = synth.hill_centres(3, system.sys, s_ref, mp.sigma, K1 + K2)
+    sig = np.asarray(mp.sigma)
+    w1 = oracle.deposit_sequence(cen[:K1], mp.sigma, mp.w0, kbdt(mp))
+    G = oracle.HillGrid(cfgp["grid_n"], s_ref - 16 * sig, s_ref + 16 * sig)
+    G.fold(cen[:K1], w1, mp.sigma, nthreads)
+    w2 = oracle.deposit_sequence(cen[K1:], mp.sigma, mp.w0, kbdt(mp), grid=G)
+    fr = [synth.perturbed_frame(system, f) for f in range(frames)]
+    t0 = time.perf_counter()
+    for f in fr:
+        oracle.step(f, p, cen[K1:], w2, mp.sigma, grid=G, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    cores = nthreads if nthreads > 0 else oracle.max_threads()
+    return system.n * frames / dt, cores, dt
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    # each step: the oracle on one frame of a 100,000-atom sample built the
+    # same way (atom-steps/s of the oracle is flat in N), so K + W steps end
+    # within a few minutes on the host cores
+    n_sample = 100_000 if (args.steps + args.warmup) <= 300 else 20_000
+    system = make_system(n_sample)
+    mp = synth.method_params(3)
+    cfgp = synth.CONFIG_PARAMS[3]
+    p = oracle.params_from(mp, system.box)
+    s_ref, _, _ = oracle.cv(system.base, p)
+    K1, K2 = cfgp["hills_folded"], cfgp["hills"]
+    cen = synth.hill_centres(3, system.sys, s_ref, mp.sigma, K1 + K2)
+    sig = np.asarray(mp.sigma)
+    w1 = oracle.deposit_sequence(cen[:K1], mp.sigma, mp.w0, kbdt(mp))
+    G = oracle.HillGrid(cfgp["grid_n"], s_ref - 16 * sig, s_ref + 16 * sig)
+    G.fold(cen[:K1], w1, mp.sigma)
+    w2 = oracle.deposit_sequence(cen[K1:], mp.sigma, mp.w0, kbdt(mp), grid=G)
+    nfr = 4
+    frames = [synth.perturbed_frame(system, f) for f in range(nfr)]
+    for k in range(args.warmup):
+        oracle.step(frames[k % nfr], p, cen[K1:], w2, mp.sigma, grid=G)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        oracle.step(frames[k % nfr], p, cen[K1:], w2, mp.sigma, grid=G)
+    dt = time.perf_counter() - t0
+    value = system.n * args.steps / dt
+    cores = oracle.max_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_atoms_sampled": system.n, "parallelism": "host cores (OpenMP)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"one frame of a {system.n}-atom system built like the 1M workload per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU leg
+def run_metad(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    # a non-default stream shared by torch's copies and the library's kernels
+    torch.cuda.set_stream(torch.cuda.Stream(dev))
+    from paper_2510_06873_gb300 import build, metad
+    if rank == 0 or not os.path.exists(metad.LIB_PATH):
+        build.build()
+    if ws > 1:
+        dist.barrier()
+    stream = torch.cuda.current_stream(dev)
+    system = make_system(args.atoms)
+    mp = synth.method_params(3)
+    cfgp = synth.CONFIG_PARAMS[3]
+    n = system.n
+    # ---- context, hills and grid, all made by the CUDA path
+    base = torch.from_numpy(system.base).to(dev)
+    probe = metad.Metad(metad.params_for(n, system.box, n_cv=2, sigma=mp.sigma, stream=stream.cuda_stream))
+    probe.build_neighbors(base)
+    s_ref = probe.cv_forward()
+    probe_launches = probe.launch_count
+    probe.close()
+    sig = np.asarray(mp.sigma)
+    lo, hi = s_ref - 16 * sig, s_ref + 16 * sig
+    params = metad.params_for(n, system.box, n_cv=2, sigma=mp.sigma, grid=(cfgp["grid_n"], lo, hi),
+                              hill_capacity=cfgp["hills"] + 1024, stream=stream.cuda_stream)
+    ctx = metad.Metad(params)
+    K1 = cfgp["hills_folded"] if args.hills_folded is None else args.hills_folded
+    K2 = cfgp["hills"] if args.hills is None else args.hills
+    cen = synth.hill_centres(3, system.sys, s_ref, mp.sigma, K1 + K2)
+    ctx.deposit_hills(cen[:K1], want_heights=False)
+    ctx.fold_hills()
+    ctx.deposit_hills(cen[K1:], want_heights=False)
+    ctx.sync()
+    # ---- resident frames (16 x 16 MB; each step reads a frame not in L2)
+    nfr = max(1, args.frames)
+    frames_h = [synth.perturbed_frame(system, f) for f in range(nfr)]
+    frames = torch.from_numpy(np.stack(frames_h)).to(dev)
+    F = torch.zeros((n, 3), dtype=torch.float32, device=dev)
+    every = cfgp["deposit_every"]
+    frame_no = 0
+
+    def one_step():
+        nonlocal frame_no
+        ctx.step(frames[frame_no % nfr], F, deposit=((frame_no + 1) % every == 0))
+        frame_no += 1
+
+    for _ in range(max(3, args.warmup)):
+        one_step()
+    ctx.sync()
+    entries, max_nn = ctx.neighbor_stats()
+    pairs = entries / 2
+    # kernels of this library launched before the timed region (for ncu -s)
+    print(f"setup_launches={probe_launches + ctx.launch_count}", file=sys.stderr, flush=True)
+    # ---- timed region: CUDA events on the context stream, profile per stage
+    clocks = ClockSampler(local)
+    launches0 = ctx.launch_count
+    ctx.profile_begin(16 * args.steps + 64)
+    clocks.start()
+    time.sleep(0.3)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        one_step()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1)
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    stages = ctx.profile_end()
+    launches = ctx.launch_count - launches0
+    if ws > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * n * args.steps / (ms / 1e3)
+    # ---- dominant kernel roofline from the live per-stage events
+    dom = max((k for k in stages if stages[k][1] > 0 and k != "other"), key=lambda k: stages[k][0])
+    dom_ms, dom_cnt = stages[dom]
+    avg_s = dom_ms / dom_cnt / 1e3
+    if FLOP_PER_PAIR.get(dom, 0) > 0:
+        achieved = FLOP_PER_PAIR[dom] * pairs / avg_s / 1e12
+        roof = {"kernel": f"k_{dom}", "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 flop x 2.07 GHz",
+                "algorithmic": f"{FLOP_PER_PAIR[dom]:.0f} flop per unordered pair x {pairs:.0f} pairs"}
+    else:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
+        achieved = BYTES_PER_ATOM[dom] * n / avg_s / 1e9
+        roof = {"kernel": f"k_{dom}", "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None}
+    step_bytes = sum(BYTES_PER_ATOM.values()) * n
+    peaks_hbm = 6787.2
+    try:
+        peaks_hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except (OSError, KeyError, ValueError):
+        pass
+    step_ms = ms / args.steps
+    stage_line = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1], "share": v[0] / max(ms, 1e-9)}
+                  for k, v in stages.items() if v[1] > 0}
+    # ---- end to end through the host-buffer entry point (pinned memory)
+    e2e = None
+    if args.e2e_steps > 0:
+        pin_pos = [torch.from_numpy(f).pin_memory().numpy() for f in frames_h[: min(nfr, 4)]]
+        pin_F = torch.zeros((n, 3), dtype=torch.float32).pin_memory().numpy()
+        ctx.step_host(pin_pos[0], pin_F)
+        if ws > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for k in range(args.e2e_steps):
+            ctx.step_host(pin_pos[k % len(pin_pos)], pin_F, deposit=((frame_no + 1) % every == 0))
+            frame_no += 1
+        dt = time.perf_counter() - t0
+        if ws > 1:
+            t = torch.tensor([dt], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": ws * n * args.e2e_steps / dt, "unit": UNIT, "h2d_bytes_per_step": 16 * n,
+               "d2h_bytes_per_step": 12 * n + 24, "steps": args.e2e_steps,
+               "call": "metad_step_host (pinned host positions in, host forces + CVs + bias out)"}
+    ctx.sync()
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, cores, dt = oracle_sample(n, 2)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"2 frames of the same {n}-atom workload (oracle hills/grid set up untimed), {dt:.1f} s"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n_atoms": n, "unordered_pairs": int(pairs),
+                           "max_neighbors_per_atom": max_nn, "live_hills_end": ctx.hill_count,
+                           "precision": "FP32 pair arithmetic, FP64 CV reductions, hills and grid",
+                           "frames_resident": nfr, "parallelism": f"replica x{ws}" if ws > 1 else "single GPU",
+                           "l2": f"inputs larger than L2: {nfr} resident frames cycled, per-step working set "
+                                 f"~{step_bytes / 1e6:.0f} MB > 129 MB"},
+                "roofline": roof, "step_hbm": {"algorithmic_bytes": step_bytes,
+                                               "achieved_gbs": step_bytes / (step_ms / 1e3) / 1e9,
+                                               "peak_gbs": peaks_hbm,
+                                               "frac": step_bytes / (step_ms / 1e3) / 1e9 / peaks_hbm},
+                "stages": stage_line, "gpu_launches": launches, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_metad(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,221 @@
+/*
+ * metad.h -- C ABI of the GB300 (sm_103a) metadynamics bias path.
+ *
+ * One context holds one periodic system: its neighbour list, collective
+ * variables (CVs), deposited hills and bias grid, all resident on one GPU.
+ * Each MD step the caller hands over positions and receives bias forces to
+ * add to its own forces, following the paper's biased potential
+ *     U_b = U_0 + V_b                                      (Methods, Eq. 1)
+ *     V_b(s) = sum_tau w_tau exp(-(s - s_tau)^2 / 2 sigma^2)  (Eqs. 2-3)
+ * and its interface, which extracts the MD data every step and returns the
+ * bias-driven forces (Section "Frameworks of GPU-MetaD", Fig. 1).
+ *
+ * Conventions (all entry points):
+ *   * Units: Angstrom, kJ/mol, kJ/mol/Angstrom.
+ *   * Positions: device float32 [N][4] = x, y, z, species id as a float
+ *     (0.0 or 1.0), in the caller's atom order, inside the orthorhombic box
+ *     [0, L) per axis (coordinates outside are wrapped: x - L floor(x/L) in
+ *     FP64, rounded to float32, a result equal to L becomes 0).
+ *   * Forces: device float32 [N][3] in the caller's atom order.
+ *   * Ownership: the caller owns every pointer it passes and keeps device
+ *     buffers alive until the context's stream has passed the call; the
+ *     library owns all internal state and copies nothing out except through
+ *     the explicit host outputs below.
+ *   * Streams: work is enqueued on params.stream (a cudaStream_t; NULL makes
+ *     the context create its own).  Calls with host outputs synchronise that
+ *     stream; calls without them are asynchronous.
+ *   * Errors: every call returns a metad_status and never throws.  Device-side
+ *     errors (neighbour-list overflow, non-finite positions) are recorded in a
+ *     device word and reported by the next synchronising call; after any error
+ *     the context returns METAD_ERR_STATE until it is destroyed.
+ *   * Call order per frame: build_neighbors -> cv_forward -> bias_eval ->
+ *     bias_forces (-> deposit_hill).  A call out of order returns
+ *     METAD_ERR_STATE without touching the context.
+ */
+#ifndef METAD_H
+#define METAD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct metad_ctx metad_ctx;
+
+typedef enum {
+    METAD_OK = 0,
+    METAD_ERR_INVALID = 1,  /* bad argument, size or parameter */
+    METAD_ERR_OOM = 2,      /* device or host allocation failed */
+    METAD_ERR_CUDA = 3,     /* a CUDA runtime call failed */
+    METAD_ERR_CAPACITY = 4, /* neighbour list or hill list capacity exceeded */
+    METAD_ERR_TIMEOUT = 5,  /* a bounded device wait gave up */
+    METAD_ERR_STATE = 6     /* call out of order, or context already failed */
+} metad_status;
+
+/* Parameters of one context.  Fill with metad_params_default, then edit. */
+typedef struct {
+    int32_t n_atoms;        /* N >= 1 */
+    int32_t n_cv;           /* 1: coordination number; 2: CN and averaged Q6 */
+    double box[3];          /* orthorhombic box lengths, each >= 2 rc */
+    double rc;              /* neighbour cutoff (3.5) */
+    double r0;              /* switch length (2.5) */
+    int32_t sw_n, sw_m;     /* rational switch exponents (6, 12) */
+    int32_t stretch;        /* 1: switch shifted and scaled to vanish at rc */
+    int32_t cn_pairs;       /* 1: CN counts unlike-species pairs only; 0: all */
+    double sigma[2];        /* hill widths per CV */
+    double w0;              /* initial hill height, kJ/mol */
+    double biasfactor;      /* well-tempered gamma > 1 */
+    double temperature;     /* K */
+    double kB;              /* kJ/mol/K (0.0083144626) */
+    int32_t grid_on;        /* 1: bicubic Hermite bias grid (n_cv == 2 only) */
+    int32_t grid_n[2];      /* nodes per axis, both ends included (>= 2) */
+    int32_t hill_capacity;  /* maximum live hills */
+    double grid_lo[2];
+    double grid_hi[2];
+    int32_t precision;      /* 0: FP32 pair arithmetic, FP64 reductions and
+                               hills; 1: FP64 throughout */
+    int32_t max_neighbors;  /* per-atom capacity of the neighbour list (0: 64) */
+    int32_t device;         /* CUDA device ordinal */
+    int32_t reserved;
+    void *stream;           /* cudaStream_t, or NULL */
+    double skin;            /* Verlet skin in Angstrom (1.0): the cell order and
+                               the rc + skin candidate list are rebuilt only
+                               when an atom has moved more than skin/2 since
+                               the last rebuild; 0 rebuilds every step.  The
+                               exact rc list is recomputed every step. */
+} metad_params;
+
+/* Defaults of the paper's GaN-style workloads: rc 3.5, r0 2.5, n 6, m 12,
+ * stretched switch, unlike-pair CN, two CVs, sigma (0.05, 0.02), w0 1,
+ * gamma 10, T 300 K, no grid, 65,536 hills, FP32 pairs, skin 1 A. */
+void metad_params_default(metad_params *p);
+
+/* Create a context for one system.  Validates p (METAD_ERR_INVALID), allocates
+ * all device state up front (METAD_ERR_OOM).  *out is NULL on failure. */
+metad_status metad_create(const metad_params *p, metad_ctx **out);
+
+/* Release everything the context owns.  Safe on NULL. */
+metad_status metad_destroy(metad_ctx *ctx);
+
+/* Step a1-a3: wrap, Morton-order cell binning and the full neighbour list
+ * {j : r_ij^2 < rc^2}, minimum image, strict inequality, decided exactly as
+ * the FP64 definition.  pos_dev: device float32 [N][4] (see conventions). */
+metad_status metad_build_neighbors(metad_ctx *ctx, const float *pos_dev);
+
+/* Steps a4-a5: per-atom CVs and their FP64 means.
+ *   s1 = (1/N) sum_i CN_i,  CN_i = sum_j s(r_ij)   (unlike pairs by default)
+ *   s2 = (1/N) sum_i qbar6_i (locally averaged Steinhardt Q6, n_cv == 2)
+ * cv_host (NULL or double[n_cv]) receives s and synchronises.
+ * per_atom_dev (NULL or device double [n_cv][N], caller order) receives CN_i
+ * and qbar6_i. */
+metad_status metad_cv_forward(metad_ctx *ctx, double *cv_host, double *per_atom_dev);
+
+/* Step a6: V(s) = grid(s) + sum_k w_k exp(-sum_d (s_d - c_kd)^2 / 2 sigma_d^2)
+ * and dV/ds in FP64 (Eqs. 2-3, a per-dimension sigma).  s_host NULL uses the
+ * CVs of the last cv_forward (on the device, no synchronisation); otherwise
+ * double[n_cv].  V_host / dVds_host (NULL or double / double[n_cv]) receive
+ * the result and synchronise. */
+metad_status metad_bias_eval(metad_ctx *ctx, const double *s_host, double *V_host, double *dVds_host);
+
+/* Steps a7-a8: bias forces F = -sum_d (dV/ds_d) ds_d/dr, chain rule through
+ * the CVs (the paper obtains them by automatic differentiation), written in
+ * the caller's atom order, times `scale` (1.0 for plain forces).
+ * accumulate 0: forces_dev = F; 1: forces_dev += F.  Deterministic: no
+ * floating-point atomics. */
+metad_status metad_bias_forces(metad_ctx *ctx, float *forces_dev, int32_t accumulate, double scale);
+
+/* Step a9: deposit one hill at c (center_host double[n_cv], or NULL for the
+ * last CVs) with the well-tempered height
+ *   w = w0 exp(-V(c) / (kB T (gamma - 1)))
+ * (the rule the paper names for its rutile runs; V includes the grid and
+ * every earlier hill).  height_host (NULL or double) synchronises.
+ * METAD_ERR_CAPACITY when the live list is full. */
+metad_status metad_deposit_hill(metad_ctx *ctx, const double *center_host, double *height_host);
+
+/* Deposit K hills one after another at centers_host (double[K][n_cv]), each
+ * with its well-tempered height from the bias of all earlier ones; heights
+ * (NULL or double[K]) receives them and synchronises. */
+metad_status metad_deposit_hills(metad_ctx *ctx, const double *centers_host, int32_t K, double *heights_host);
+
+/* Replace the live hills by K given hills (centers double[K][n_cv], heights
+ * double[K], host memory). */
+metad_status metad_load_hills(metad_ctx *ctx, const double *centers_host, const double *heights_host, int32_t K);
+
+/* Copy the live hills out: *K receives the count; centers/heights (NULL or
+ * room for cap hills) receive up to cap of them.  Synchronises. */
+metad_status metad_get_hills(metad_ctx *ctx, double *centers_host, double *heights_host, int32_t cap, int32_t *K);
+
+/* Fold every live hill into the bias grid (node values V, dV/ds1, dV/ds2,
+ * d2V/ds1ds2 as exact FP64 sums) and empty the live list.  Needs grid_on. */
+metad_status metad_fold_hills(metad_ctx *ctx);
+
+/* Copy the grid nodes out: double [grid_n0][grid_n1][4].  Synchronises. */
+metad_status metad_get_grid(metad_ctx *ctx, double *grid_host);
+
+/* The last neighbour list as unordered pairs (i < j, caller indices,
+ * ascending): *P receives the count, pairs_host (NULL or int64[cap][2])
+ * up to cap pairs.  Synchronises. */
+metad_status metad_export_neighbors(metad_ctx *ctx, int64_t *pairs_host, int64_t cap, int64_t *P);
+
+/* One whole step a1-a8 (+ a9 when deposit != 0) without any host
+ * synchronisation: build_neighbors, cv_forward, bias_eval, bias_forces. */
+metad_status metad_step(metad_ctx *ctx, const float *pos_dev, float *forces_dev, int32_t accumulate,
+                        int32_t deposit);
+
+/* One whole step from HOST buffers, for callers whose positions live in host
+ * memory: copies pos_host (float32 [N][4]) to a context-owned device buffer,
+ * runs metad_step, copies the forces back to forces_host (float32 [N][3];
+ * with accumulate 1 its incoming values are uploaded and added to) and the
+ * CVs / bias to cv_host / V_host (NULL to skip).  Synchronises.  Page-locked
+ * host memory makes the copies asynchronous DMA.  The device staging buffers
+ * are allocated on the first call. */
+metad_status metad_step_host(metad_ctx *ctx, const float *pos_host, float *forces_host, int32_t accumulate,
+                             int32_t deposit, double *cv_host, double *V_host);
+
+/* Stage profiling.  Between begin and end, every kernel stage this context
+ * launches is bracketed by CUDA events on its stream (at most max_records
+ * stages are recorded).  end synchronises and writes, per stage index
+ * 0..METAD_NUM_STAGES-1 (names from metad_stage_name), the summed device
+ * milliseconds and the number of records (either pointer may be NULL). */
+#define METAD_NUM_STAGES 9
+metad_status metad_profile_begin(metad_ctx *ctx, int32_t max_records);
+metad_status metad_profile_end(metad_ctx *ctx, double *ms_per_stage, int32_t *records_per_stage);
+const char *metad_stage_name(int32_t stage);
+
+/* Statistics of the last neighbour list: total entries of the full list
+ * (twice the unordered pair count) and the largest per-atom count.
+ * Synchronises. */
+metad_status metad_neighbor_stats(metad_ctx *ctx, int64_t *entries, int32_t *max_per_atom);
+
+/* Number of cell-order / Verlet-list rebuilds since creation (the first
+ * build_neighbors always rebuilds).  Synchronises. */
+metad_status metad_rebuild_count(metad_ctx *ctx, int64_t *count);
+
+/* Number of kernels this context has launched since creation. */
+int64_t metad_launch_count(const metad_ctx *ctx);
+
+/* Copy the last CVs, bias and bias gradient to the host (any may be NULL).
+ * Synchronises and reports any pending device error. */
+metad_status metad_read_results(metad_ctx *ctx, double *cv_host, double *V_host, double *dVds_host);
+
+/* Wait for the context's stream and report any pending device error. */
+metad_status metad_sync(metad_ctx *ctx);
+
+/* The stream the context enqueues on (cudaStream_t). */
+void *metad_stream(metad_ctx *ctx);
+
+/* Live hill count as tracked on the host (no synchronisation). */
+int32_t metad_hill_count(const metad_ctx *ctx);
+
+/* Static text for a status code. */
+const char *metad_status_string(metad_status s);
+
+/* Text of the last error recorded on this context (never NULL). */
+const char *metad_last_error(const metad_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* METAD_H */

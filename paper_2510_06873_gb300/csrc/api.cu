@@ -1,0 +1,863 @@
+// C ABI of the metadynamics bias path (declared in include/metad.h).
+//
+// A context owns every device buffer of one system, allocated once at
+// creation; the per-step calls only enqueue kernels on the context stream.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "metad.h"
+#include "metad_impl.cuh"
+
+using metad::Sys;
+
+struct metad_ctx {
+    metad_params p{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    Sys sys{};
+    int fp64 = 0;
+    int K = 0;
+    bool have_nbr = false, have_cv = false, have_bias = false;
+    bool filter_pending = false;  // exact rows not yet compacted from the Verlet rows
+    bool failed = false;
+    std::string last_error;
+    std::vector<void *> allocs;
+    double *stage = nullptr;      // hill centres staged for deposit_hills
+    long long *pairs = nullptr;   // export buffer (allocated on first export)
+    int *pair_count = nullptr;
+    int64_t pairs_cap = 0;
+    double *host_pinned = nullptr;
+    int *err_pinned = nullptr;
+    // host-buffer step staging (allocated on first metad_step_host)
+    float *pos_stage = nullptr;
+    float *force_stage = nullptr;
+    // stage profiling with CUDA events on the context stream
+    bool prof_on = false;
+    int prof_cap = 0, prof_used = 0;
+    std::vector<cudaEvent_t> prof_ev;
+    std::vector<int> prof_stage;
+    int64_t launches = 0;
+};
+
+namespace {
+
+metad_status fail(metad_ctx *c, metad_status s, const std::string &msg)
+{
+    if (c) {
+        c->last_error = msg;
+        if (s == METAD_ERR_CUDA || s == METAD_ERR_CAPACITY || s == METAD_ERR_TIMEOUT) c->failed = true;
+    }
+    return s;
+}
+
+metad_status cuda_check(metad_ctx *c, cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return METAD_OK;
+    return fail(c, METAD_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+metad_status launched(metad_ctx *c, const char *what) { return cuda_check(c, cudaGetLastError(), what); }
+
+enum Stage { ST_BIN, ST_NBR, ST_CV_FWD, ST_CV_AVG, ST_BIAS, ST_ADJ, ST_FORCE, ST_DEPOSIT, ST_OTHER, ST_COUNT };
+// "gather": positions into cell order + rebuild test; "neighbors": the
+// conditional rebuild chain (and a stand-alone exact filter); "cv_fwd" holds
+// the fused exact filter.
+const char *kStageNames[ST_COUNT] = {"gather",  "neighbors", "cv_fwd",  "cv_avg", "bias",
+                                     "adjoint", "force",     "deposit", "other"};
+
+// Brackets the kernels of one stage with CUDA events while profiling is on,
+// and counts the kernels launched.
+struct StageScope {
+    metad_ctx *c;
+    int idx = -1;
+    StageScope(metad_ctx *ctx, int stage, int kernels) : c(ctx)
+    {
+        c->launches += kernels;
+        if (c->prof_on && c->prof_used < c->prof_cap) {
+            idx = c->prof_used++;
+            c->prof_stage[idx] = stage;
+            cudaEventRecord(c->prof_ev[2 * idx], c->stream);
+        }
+    }
+    ~StageScope()
+    {
+        if (idx >= 0) cudaEventRecord(c->prof_ev[2 * idx + 1], c->stream);
+    }
+};
+
+template <typename T>
+metad_status dalloc(metad_ctx *c, T **ptr, size_t count)
+{
+    void *p = nullptr;
+    size_t bytes = sizeof(T) * (count > 0 ? count : 1);
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, METAD_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    c->allocs.push_back(p);
+    *ptr = static_cast<T *>(p);
+    return METAD_OK;
+}
+
+double switch_raw_host(double x, int n, int m)
+{
+    if (m == 2 * n) return 1.0 / (1.0 + std::pow(x, n));
+    if (std::fabs(x - 1.0) < 1e-6) return ((double)n / m) * (1.0 + 0.5 * (n - m) * (x - 1.0));
+    return (1.0 - std::pow(x, n)) / (1.0 - std::pow(x, m));
+}
+
+void split(double v, float &hi, float &lo)
+{
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
+
+uint32_t spread3(uint32_t v)
+{
+    uint32_t r = 0;
+    for (int b = 0; b < 10; ++b) r |= ((v >> b) & 1u) << (3 * b);
+    return r;
+}
+
+metad_status check_usable(metad_ctx *c)
+{
+    if (!c) return METAD_ERR_INVALID;
+    if (c->failed) return METAD_ERR_STATE;
+    cudaError_t e = cudaSetDevice(c->p.device);
+    if (e != cudaSuccess) return cuda_check(c, e, "cudaSetDevice");
+    return METAD_OK;
+}
+
+// Wait for the stream and turn a recorded device error into a status.
+metad_status sync_and_check(metad_ctx *c)
+{
+    metad_status s = cuda_check(c, cudaMemcpyAsync(c->err_pinned, c->sys.err, sizeof(int), cudaMemcpyDeviceToHost,
+                                                   c->stream), "error word copy");
+    if (s != METAD_OK) return s;
+    s = cuda_check(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    if (s != METAD_OK) return s;
+    int e = *c->err_pinned;
+    if (e) c->failed = true;
+    if (e & metad::kErrNonFinite) return fail(c, METAD_ERR_INVALID, "non-finite position");
+    if (e & metad::kErrCapacity)
+        return fail(c, METAD_ERR_CAPACITY, "an atom has more neighbours than max_neighbors");
+    if (e & metad::kErrHills) return fail(c, METAD_ERR_CAPACITY, "hill list full");
+    if (e) return fail(c, METAD_ERR_CUDA, "internal launch-shape check failed (error word " + std::to_string(e) + ")");
+    return METAD_OK;
+}
+
+metad_status validate(const metad_params *p, std::string &why)
+{
+    if (!p) { why = "params is NULL"; return METAD_ERR_INVALID; }
+    if (p->n_atoms < 1) { why = "n_atoms < 1"; return METAD_ERR_INVALID; }
+    if (p->n_cv != 1 && p->n_cv != 2) { why = "n_cv must be 1 or 2"; return METAD_ERR_INVALID; }
+    if (!(p->rc > 0) || !(p->r0 > 0)) { why = "rc and r0 must be positive"; return METAD_ERR_INVALID; }
+    for (int a = 0; a < 3; ++a)
+        if (!(p->box[a] >= 2.0 * p->rc) || !std::isfinite(p->box[a])) {
+            why = "every box length must be >= 2 rc";
+            return METAD_ERR_INVALID;
+        }
+    if (p->sw_n < 1 || p->sw_m < 1 || p->sw_n == p->sw_m) { why = "switch exponents"; return METAD_ERR_INVALID; }
+    for (int d = 0; d < p->n_cv; ++d)
+        if (!(p->sigma[d] > 0)) { why = "sigma must be positive"; return METAD_ERR_INVALID; }
+    if (!(p->biasfactor > 1.0) || !(p->temperature > 0) || !(p->kB > 0)) {
+        why = "well-tempered parameters";
+        return METAD_ERR_INVALID;
+    }
+    if (p->hill_capacity < 1) { why = "hill_capacity < 1"; return METAD_ERR_INVALID; }
+    if (p->grid_on) {
+        if (p->n_cv != 2) { why = "the grid needs n_cv == 2"; return METAD_ERR_INVALID; }
+        for (int a = 0; a < 2; ++a)
+            if (p->grid_n[a] < 2 || !(p->grid_hi[a] > p->grid_lo[a])) {
+                why = "grid shape";
+                return METAD_ERR_INVALID;
+            }
+    }
+    if (p->precision != 0 && p->precision != 1) { why = "precision must be 0 or 1"; return METAD_ERR_INVALID; }
+    if (p->max_neighbors < 0) { why = "max_neighbors < 0"; return METAD_ERR_INVALID; }
+    if (!(p->skin >= 0.0) || !std::isfinite(p->skin)) { why = "skin must be >= 0"; return METAD_ERR_INVALID; }
+    return METAD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void metad_params_default(metad_params *p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->n_atoms = 1;
+    p->n_cv = 2;
+    p->box[0] = p->box[1] = p->box[2] = 10.0;
+    p->rc = 3.5;
+    p->r0 = 2.5;
+    p->sw_n = 6;
+    p->sw_m = 12;
+    p->stretch = 1;
+    p->cn_pairs = 1;
+    p->sigma[0] = 0.05;
+    p->sigma[1] = 0.02;
+    p->w0 = 1.0;
+    p->biasfactor = 10.0;
+    p->temperature = 300.0;
+    p->kB = 0.0083144626;
+    p->grid_on = 0;
+    p->grid_n[0] = p->grid_n[1] = 200;
+    p->hill_capacity = 65536;
+    p->precision = 0;
+    p->max_neighbors = 64;
+    p->device = 0;
+    p->stream = nullptr;
+    p->skin = 1.0;
+}
+
+const char *metad_status_string(metad_status s)
+{
+    switch (s) {
+    case METAD_OK: return "ok";
+    case METAD_ERR_INVALID: return "invalid argument";
+    case METAD_ERR_OOM: return "out of memory";
+    case METAD_ERR_CUDA: return "CUDA error";
+    case METAD_ERR_CAPACITY: return "capacity exceeded";
+    case METAD_ERR_TIMEOUT: return "device wait timed out";
+    case METAD_ERR_STATE: return "call out of order or context failed";
+    }
+    return "unknown status";
+}
+
+const char *metad_last_error(const metad_ctx *c) { return c ? c->last_error.c_str() : "null context"; }
+
+int32_t metad_hill_count(const metad_ctx *c) { return c ? c->K : 0; }
+
+void *metad_stream(metad_ctx *c) { return c ? (void *)c->stream : nullptr; }
+
+metad_status metad_destroy(metad_ctx *c)
+{
+    if (!c) return METAD_OK;
+    cudaSetDevice(c->p.device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+    for (void *ptr : c->allocs) cudaFree(ptr);
+    if (c->host_pinned) cudaFreeHost(c->host_pinned);
+    if (c->err_pinned) cudaFreeHost(c->err_pinned);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    cudaGetLastError();
+    delete c;
+    return METAD_OK;
+}
+
+metad_status metad_create(const metad_params *p, metad_ctx **out)
+{
+    if (!out) return METAD_ERR_INVALID;
+    *out = nullptr;
+    std::string why;
+    metad_status v = validate(p, why);
+    if (v != METAD_OK) return v;
+    metad_ctx *c = new (std::nothrow) metad_ctx();
+    if (!c) return METAD_ERR_OOM;
+    c->p = *p;
+    if (c->p.max_neighbors == 0) c->p.max_neighbors = 64;
+    c->fp64 = c->p.precision == 1;
+    metad_status s = cuda_check(c, cudaSetDevice(c->p.device), "cudaSetDevice");
+    if (s != METAD_OK) { metad_destroy(c); return s; }
+    if (c->p.stream) {
+        c->stream = (cudaStream_t)c->p.stream;
+    } else {
+        s = cuda_check(c, cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking), "cudaStreamCreate");
+        if (s != METAD_OK) { metad_destroy(c); return s; }
+        c->own_stream = true;
+    }
+    Sys &y = c->sys;
+    const int n = c->p.n_atoms;
+    y.n = n;
+    y.ncv = c->p.n_cv;
+    y.cn_unlike = c->p.cn_pairs ? 1 : 0;
+    y.max_nb = c->p.max_neighbors;
+    for (int a = 0; a < 3; ++a) {
+        const double L = c->p.box[a];
+        y.L[a] = L;
+        split(L, y.Lhi[a], y.Llo[a]);
+        y.halfL[a] = (float)(0.5 * L);
+        // cell edge >= (rc + skin)(1 + 1e-4): float32 cell assignment can
+        // never split a Verlet pair across non-adjacent cells
+        int nc = (int)std::floor(L / ((c->p.rc + c->p.skin) * (1.0 + 1e-4)));
+        if (nc < 1) nc = 1;
+        if (nc > 1023) { metad_destroy(c); return METAD_ERR_INVALID; }
+        y.nc[a] = nc;
+        y.inv_h[a] = (float)(nc / L);
+    }
+    y.ncell = y.nc[0] * y.nc[1] * y.nc[2];
+    y.rc = c->p.rc;
+    y.rc2 = c->p.rc * c->p.rc;
+    y.rc2_lo = (float)(y.rc2 * (1.0 - 3e-5));
+    y.rc2_hi = (float)(y.rc2 * (1.0 + 3e-5));
+    {
+        const double rv = c->p.rc + c->p.skin;
+        y.rv2 = (float)(rv * rv * (1.0 + 1e-4));
+        const double half = 0.5 * c->p.skin * (1.0 - 1e-3);
+        y.disp_thr2 = (float)(half * half);
+        y.always_rebuild = c->p.skin > 0.0 ? 0 : 1;
+        const double grow = std::pow(rv / c->p.rc, 3.0);
+        y.max_vnb = ((int)std::ceil(y.max_nb * grow) + 7) / 8 * 8;
+    }
+    y.sw_n = c->p.sw_n;
+    y.sw_m = c->p.sw_m;
+    y.stretch = c->p.stretch;
+    y.r0 = c->p.r0;
+    y.inv_r0_d = 1.0 / c->p.r0;
+    split(y.inv_r0_d, y.inv_r0_hi, y.inv_r0_lo);
+    const double sc = c->p.stretch ? switch_raw_host(c->p.rc / c->p.r0, c->p.sw_n, c->p.sw_m) : 0.0;
+    y.a_d = 1.0 / (1.0 - sc);
+    y.k_d = sc * y.a_d;
+    split(y.a_d, y.a_hi, y.a_lo);
+    split(y.k_d, y.k_hi, y.k_lo);
+    y.hill_cap = c->p.hill_capacity;
+    y.sigma[0] = c->p.sigma[0];
+    y.sigma[1] = c->p.n_cv == 2 ? c->p.sigma[1] : 1.0;
+    y.w0 = c->p.w0;
+    y.kbdt = c->p.kB * c->p.temperature * (c->p.biasfactor - 1.0);
+    y.grid_on = c->p.grid_on;
+    for (int a = 0; a < 2; ++a) {
+        y.gn[a] = c->p.grid_on ? c->p.grid_n[a] : 2;
+        y.glo[a] = c->p.grid_lo[a];
+        y.ghi[a] = c->p.grid_hi[a];
+        y.gh[a] = c->p.grid_on ? (y.ghi[a] - y.glo[a]) / (y.gn[a] - 1) : 1.0;
+    }
+    const size_t rs = c->fp64 ? sizeof(double) : sizeof(float);
+    // one FP64 partial per block of the per-atom kernels (slot 0: CN, 1: Q6),
+    // three per block of the hill kernel (slot 2), the neighbour statistics
+    // (slot 3)
+    y.part_stride = std::max(metad::group_grid(n), metad::kMaxBiasBlocks * 3);
+    const size_t nq = c->p.n_cv == 2 ? (size_t)16 * n : 16;
+    int *rank_xyz = nullptr, *xyz_rank = nullptr;
+    char *rb = nullptr, *wlb = nullptr, *pfb = nullptr;
+    if ((s = dalloc(c, &y.pos_s, n)) || (s = dalloc(c, &y.perm, n)) || (s = dalloc(c, &y.scell, n)) ||
+        (s = dalloc(c, &y.ucell, n)) || (s = dalloc(c, &y.uslot, n)) || (s = dalloc(c, &y.cell_count, y.ncell)) ||
+        (s = dalloc(c, &y.cell_start, (size_t)y.ncell + 1)) || (s = dalloc(c, &y.scan_part, y.ncell / 4096 + 2)) ||
+        (s = dalloc(c, &rank_xyz, y.ncell)) || (s = dalloc(c, &xyz_rank, y.ncell)) ||
+        (s = dalloc(c, &y.nbr, (size_t)y.max_nb * n)) || (s = dalloc(c, &y.nn, n)) || (s = dalloc(c, &y.nh, n)) ||
+        (s = dalloc(c, &y.vnh, n)) || (s = dalloc(c, &wlb, rs * (size_t)y.max_nb * n)) ||
+        (s = dalloc(c, &pfb, rs * 4 * (size_t)y.max_nb * n)) ||
+        (s = dalloc(c, &y.pos_ref, n)) || (s = dalloc(c, &y.vnbr, (size_t)y.max_vnb * n)) ||
+        (s = dalloc(c, &y.vnn, n)) || (s = dalloc(c, &y.flag, 1)) || (s = dalloc(c, &y.rebuilds, 1)) ||
+        (s = dalloc(c, &rb, rs * (nq * 3 + (size_t)n * 4 + 64))) || (s = dalloc(c, &y.part, (size_t)y.part_stride * 4)) ||
+        (s = dalloc(c, &y.ticket, 8)) || (s = dalloc(c, &y.scal, metad::kNumScal)) || (s = dalloc(c, &y.err, 1)) ||
+        (s = dalloc(c, &y.hc, 2 * (size_t)y.hill_cap + 2)) || (s = dalloc(c, &y.hw, (size_t)y.hill_cap + 1)) ||
+        (s = dalloc(c, &c->stage, 2 * (size_t)y.hill_cap + 2)) ||
+        (s = dalloc(c, &y.grid, (size_t)y.gn[0] * y.gn[1] * 4))) {
+        metad_destroy(c);
+        return s;
+    }
+    // records first (16-element rows stay 64 / 128 B aligned), scalars after
+    y.q = rb;
+    y.b = rb + rs * nq;
+    y.h = rb + rs * 2 * nq;
+    y.cn = rb + rs * 3 * nq;
+    y.W = rb + rs * (3 * nq + n);
+    y.qb6 = rb + rs * (3 * nq + 2 * (size_t)n);
+    y.wl = wlb;
+    y.pairF = pfb;
+    y.rank_of_xyz = rank_xyz;
+    y.xyz_of_rank = xyz_rank;
+    // Morton ranks of the cells: sort cell coordinates by interleaved bits
+    {
+        std::vector<std::pair<uint32_t, int>> key(y.ncell);
+        for (int z = 0; z < y.nc[2]; ++z)
+            for (int yy = 0; yy < y.nc[1]; ++yy)
+                for (int x = 0; x < y.nc[0]; ++x) {
+                    int id = (z * y.nc[1] + yy) * y.nc[0] + x;
+                    key[id] = {spread3(x) | (spread3(yy) << 1) | (spread3(z) << 2), id};
+                }
+        std::sort(key.begin(), key.end());
+        std::vector<int> r(y.ncell), xr(y.ncell);
+        for (int k = 0; k < y.ncell; ++k) {
+            int id = key[k].second;
+            int x = id % y.nc[0], yy = (id / y.nc[0]) % y.nc[1], z = id / (y.nc[0] * y.nc[1]);
+            r[id] = k;
+            xr[k] = x | (yy << 10) | (z << 20);
+        }
+        if ((s = cuda_check(c, cudaMemcpy(rank_xyz, r.data(), sizeof(int) * y.ncell, cudaMemcpyHostToDevice),
+                            "rank upload")) ||
+            (s = cuda_check(c, cudaMemcpy(xyz_rank, xr.data(), sizeof(int) * y.ncell, cudaMemcpyHostToDevice),
+                            "rank upload"))) {
+            metad_destroy(c);
+            return s;
+        }
+    }
+    if (cudaMallocHost(&c->host_pinned, 64 * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&c->err_pinned, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        metad_destroy(c);
+        return METAD_ERR_OOM;
+    }
+    cudaMemsetAsync(y.ticket, 0, 8 * sizeof(unsigned), c->stream);
+    cudaMemsetAsync(y.scal, 0, metad::kNumScal * sizeof(double), c->stream);
+    cudaMemsetAsync(y.err, 0, sizeof(int), c->stream);
+    cudaMemsetAsync(y.grid, 0, sizeof(double) * (size_t)y.gn[0] * y.gn[1] * 4, c->stream);
+    cudaMemsetAsync(y.nn, 0, sizeof(int) * (size_t)n, c->stream);
+    cudaMemsetAsync(y.nh, 0, sizeof(int) * (size_t)n, c->stream);
+    cudaMemsetAsync(y.vnh, 0, sizeof(int) * (size_t)n, c->stream);
+    cudaMemsetAsync(y.vnn, 0, sizeof(int) * (size_t)n, c->stream);
+    cudaMemsetAsync(y.rebuilds, 0, sizeof(unsigned long long), c->stream);
+    cudaMemsetAsync(y.pos_ref, 0, sizeof(float4) * (size_t)n, c->stream);
+    {
+        // identity order until the first rebuild, which the set flag forces
+        std::vector<int> iota(n);
+        for (int k = 0; k < n; ++k) iota[k] = k;
+        const int one = 1;
+        if ((s = cuda_check(c, cudaMemcpy(y.perm, iota.data(), sizeof(int) * n, cudaMemcpyHostToDevice), "perm")) ||
+            (s = cuda_check(c, cudaMemcpy(y.flag, &one, sizeof(int), cudaMemcpyHostToDevice), "flag"))) {
+            metad_destroy(c);
+            return s;
+        }
+    }
+    metad::set_ylm_constants(c->stream);
+    s = cuda_check(c, cudaStreamSynchronize(c->stream), "create");
+    if (s != METAD_OK) { metad_destroy(c); return s; }
+    *out = c;
+    return METAD_OK;
+}
+
+metad_status metad_build_neighbors(metad_ctx *c, const float *pos_dev)
+{
+    metad_status s = check_usable(c);
+    if (s) return s;
+    if (!pos_dev) return fail(c, METAD_ERR_INVALID, "pos_dev is NULL");
+    c->sys.pos_in = reinterpret_cast<const float4 *>(pos_dev);
+    {
+        StageScope t(c, ST_BIN, 1);
+        metad::launch_gather_check(c->sys, c->stream);
+    }
+    {
+        StageScope t(c, ST_NBR, 8);
+        metad::launch_rebuild(c->sys, c->stream);
+    }
+    s = launched(c, "build_neighbors");
+    if (s) return s;
+    c->have_nbr = true;
+    c->filter_pending = true;
+    c->have_cv = c->have_bias = false;
+    return METAD_OK;
+}
+
+metad_status metad_cv_forward(metad_ctx *c, double *cv_host, double *per_atom_dev)
+{
+    metad_status s = check_usable(c);
+    if (s) return s;
+    if (!c->have_nbr) return fail(c, METAD_ERR_STATE, "cv_forward before build_neighbors");
+    {
+        StageScope t(c, ST_CV_FWD, 1);
+        metad::launch_cv_fwd(c->sys, c->fp64, c->filter_pending ? 1 : 0, c->stream);
+        c->filter_pending = false;
+    }
+    if (c->p.n_cv == 2) {
+        StageScope t(c, ST_CV_AVG, 1);
+        metad::launch_cv_avg(c->sys, c->fp64, c->stream);
+    }
+    if (per_atom_dev) {
+        StageScope t(c, ST_OTHER, 1);
+        metad::launch_per_atom_out(c->sys, c->fp64, per_atom_dev, c->stream);
+    }
+    s = launched(c, "cv_forward");
+    if (s) return s;
+    c->have_cv = true;
+    c->have_bias = false;
+    if (cv_host) {
+        s = cuda_check(c, cudaMemcpyAsync(c->host_pinned, c->sys.scal + metad::kS0, 2 * sizeof(double),
+                                          cudaMemcpyDeviceToHost, c->stream), "cv copy");
+        if (s) return s;
+        if ((s = sync_and_check(c))) return s;
+        for (int d = 0; d < c->p.n_cv; ++d) cv_host[d] = c->host_pinned[d];
+    }
+    return METAD_OK;
+}
+
+metad_status metad_bias_eval(metad_ctx *c, const double *s_host, double *V_host, double *dVds_host)
+{
+    metad_status s = check_usable(c);
+    if (s) return s;
+    const double *x = c->sys.scal + metad::kS0;
+    if (s_host) {
+        double tmp[2] = {s_host[0], c->p.n_cv == 2 ? s_host[1] : 0.0};
+        // a user-given CV point: evaluate into the deposit slots so the step's
+        // own CVs stay untouched
+        s = cuda_check(c, cudaMemcpyAsync(c->sys.scal + metad::kDepC0, tmp, sizeof(tmp), cudaMemcpyHostToDevice,
+                                          c->stream), "s upload");
+        if (s) return s;
+        x = c->sys.scal + metad::kDepC0;
+    } else if (!c->have_cv) {
+        return fail(c, METAD_ERR_STATE, "bias_eval(NULL) before cv_forward");
+    }
+    {
+        StageScope t(c, ST_BIAS, 1);
+        metad::launch_bias(c->sys, c->K, x, c->sys.scal + metad::kV, 0, c->stream);
+    }
+    s = launched(c, "bias_eval");
+    if (s) return s;
+    c->have_bias = !s_host ? true : false;
+    if (V_host || dVds_host) {
+        s = cuda_check(c, cudaMemcpyAsync(c->host_pinned, c->sys.scal + metad::kV, 3 * sizeof(double),
+                                          cudaMemcpyDeviceToHost, c->stream), "bias copy");
+        if (s) return s;
+        if ((s = sync_and_check(c))) return s;
+        if (V_host) *V_host = c->host_pinned[0];
+        if (dVds_host)
+            for (int d = 0; d < c->p.n_cv; ++d) dVds_host[d] = c->host_pinned[1 + d];
+    }
+    return METAD_OK;
+}
+
+metad_status metad_bias_forces(metad_ctx *c, float *forces_dev, int32_t accumulate, double scale)
+{
+    metad_status s = check_usable(c);
+    if (s) return s;
+    if (!forces_dev) return fail(c, METAD_ERR_INVALID, "forces_dev is NULL");
+    if (!c->have_bias || !c->have_cv) return fail(c, METAD_ERR_STATE, "bias_forces before bias_eval");
+    if (c->p.n_cv == 2) {
+        StageScope t(c, ST_ADJ, 1);
+        metad::launch_adjoint(c->sys, c->fp64, c->stream);
+    }
+    {
+        StageScope t(c, ST_FORCE, metad::force_kernels(c->sys));
+        metad::launch_force(c->sys, c->fp64, forces_dev, accumulate ? 1 : 0, scale, c->stream);
+    }
+    return launched(c, "bias_forces");
+}
+
+metad_status metad_deposit_hill(metad_ctx *c, const double *center_host, double *height_host)
+{
+    metad_status s = check_usable(c);
+    if (s) return s;
+    if (c->K >= c->p.hill_capacity) return fail(c, METAD_ERR_CAPACITY, "hill list full");
+    const double *x = c->sys.scal + metad::kS0;
+    if (center_host) {
+        double tmp[2] = {center_host[0], c->p.n_cv == 2 ? center_host[1] : 0.0};
+        s = cuda_check(c, cudaMemcpyAsync(c->sys.scal + metad::kDepC0, tmp, sizeof(tmp), cudaMemcpyHostToDevice,
+                                          c->stream), "centre upload");
+        if (s) return s;
+        x = c->sys.scal + metad::kDepC0;
+    } else if (!c->have_cv) {
+        return fail(c, METAD_ERR_STATE, "deposit_hill(NULL) before cv_forward");
+    }
+    {
+        StageScope t(c, ST_DEPOSIT, 1);
+        metad::launch_bias(c->sys, c->K, x, c->sys.scal + metad::kDepV, 1, c->stream);
+    }
+    s = launched(c, "deposit_hill");
+    if (s) return s;
+    c->K += 1;
+    if (height_host) {
+        s = cuda_check(c, cudaMemcpyAsync(c->host_pinned, c->sys.scal + metad::kDepW, sizeof(double),
+                                          cudaMemcpyDeviceToHost, c->stream), "height copy");
+        if (s) return s;
+        if ((s = sync_and_check(c))) return s;
+        *height_host = c->host_pinned[0];
+    }
+    return METAD_OK;
+}
+
+metad_status metad_deposit_hills(metad_ctx *c, const double *centers_host, int32_t K, double *heights_host)
+{
+    metad_status s = check_usable(c);
+    if (s) return s;
+    if (K < 0 || (K > 0 && !centers_host)) return fail(c, METAD_ERR_INVALID, "bad hill arguments");
+    if ((int64_t)c->K + K > c->p.hill_capacity) return fail(c, METAD_ERR_CAPACITY, "hill list full");
+    if (K == 0) return METAD_OK;
+    std::vector<double> tmp(2 * (size_t)K);
+    for (int k = 0; k < K; ++k) {
+        tmp[2 * k] = centers_host[(size_t)c->p.n_cv * k];
+        tmp[2 * k + 1] = c->p.n_cv == 2 ? centers_host[(size_t)c->p.n_cv * k + 1] : 0.0;
+    }
+    s = cuda_check(c, cudaMemcpyAsync(c->stage, tmp.data(), sizeof(double) * tmp.size(), cudaMemcpyHostToDevice,
+                                      c->stream), "centre upload");
+    if (s) return s;
+    const int k0 = c->K;
+    for (int k = 0; k < K; ++k) {
+        StageScope t(c, ST_DEPOSIT, 1);
+        metad::launch_bias(c->sys, c->K, c->stage + 2 * (size_t)k, c->sys.scal + metad::kDepV, 1, c->stream);
+        c->K += 1;
+    }
+    s = launched(c, "deposit_hills");
+    if (s) return s;
+    if (heights_host) {
+        s = cuda_check(c, cudaMemcpyAsync(heights_host, c->sys.hw + k0, sizeof(double) * K, cudaMemcpyDeviceToHost,
+                                          c->stream), "heights copy");
+        if (s) return s;
+        return sync_and_check(c);
+    }
+    return METAD_OK;
+}
+
+metad_status metad_load_hills(metad_ctx *c, const double *centers_host, const double *heights_host, int32_t K)
+{
+    metad_status s = check_usable(c);
+    if (s) return s;
+    if (K < 0 || (K > 0 && (!centers_host || !heights_host))) return fail(c, METAD_ERR_INVALID, "bad hills");
+    if (K > c->p.hill_capacity) return fail(c, METAD_ERR_CAPACITY, "hill list full");
+    std::vector<double> tmp(2 * (size_t)K + 2);
+    for (int k = 0; k < K; ++k) {
+        tmp[2 * k] = centers_host[(size_t)c->p.n_cv * k];
+        tmp[2 * k + 1] = c->p.n_cv == 2 ? centers_host[(size_t)c->p.n_cv * k + 1] : 0.0;
+    }
+    if (K > 0) {
+        if ((s = cuda_check(c, cudaMemcpyAsync(c->sys.hc, tmp.data(), sizeof(double) * 2 * K, cudaMemcpyHostToDevice,
+                                               c->stream), "hill upload")))
+            return s;
+        if ((s = cuda_check(c, cudaMemcpyAsync(c->sys.hw, heights_host, sizeof(double) * K, cudaMemcpyHostToDevice,
+                                               c->stream), "hill upload")))
+            return s;
+    }
+    c->K = K;
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "load_hills");
+}
+
+metad_status metad_get_hills(metad_ctx *c, double *centers_host, double *heights_host, int32_t cap, int32_t *K)
+{
+    metad_status s = check_usable(c);
+    if (s) return s;
+    if (K) *K = c->K;
+    const int m = std::min(cap, c->K);
+    if (m <= 0) return sync_and_check(c);
+    std::vector<double> tmp(2 * (size_t)m);
+    if (centers_host &&
+        (s = cuda_check(c, cudaMemcpyAsync(tmp.data(), c->sys.hc, sizeof(double) * 2 * m, cudaMemcpyDeviceToHost,
+                                           c->stream), "hill copy")))
+        return s;
+    if (heights_host &&
+        (s = cuda_check(c, cudaMemcpyAsync(heights_host, c->sys.hw, sizeof(double) * m, cudaMemcpyDeviceToHost,
+                                           c->stream), "hill copy")))
+        return s;
+    if ((s = sync_and_check(c))) return s;
+    if (centers_host)
+        for (int k = 0; k < m; ++k) {
+            centers_host[(size_t)c->p.n_cv * k] = tmp[2 * k];
+            if (c->p.n_cv == 2) centers_host[(size_t)c->p.n_cv * k + 1] = tmp[2 * k + 1];
+        }
+    return METAD_OK;
+}
+
+metad_status metad_fold_hills(metad_ctx *c)
+{
+    metad_status s = check_usable(c);
+    if (s) return s;
+    if (!c->p.grid_on) return fail(c, METAD_ERR_INVALID, "fold_hills needs grid_on");
+    if (c->K > 0) {
+        StageScope t(c, ST_OTHER, 1);
+        metad::launch_grid_fold(c->sys, c->K, c->stream);
+    }
+    s = launched(c, "fold_hills");
+    if (s) return s;
+    c->K = 0;
+    c->have_bias = false;
+    return METAD_OK;
+}
+
+metad_status metad_get_grid(metad_ctx *c, double *grid_host)
+{
+    metad_status s = check_usable(c);
+    if (s) return s;
+    if (!c->p.grid_on || !grid_host) return fail(c, METAD_ERR_INVALID, "no grid");
+    s = cuda_check(c, cudaMemcpyAsync(grid_host, c->sys.grid, sizeof(double) * c->sys.gn[0] * c->sys.gn[1] * 4,
+                                      cudaMemcpyDeviceToHost, c->stream), "grid copy");
+    if (s) return s;
+    return sync_and_check(c);
+}
+
+metad_status metad_export_neighbors(metad_ctx *c, int64_t *pairs_host, int64_t cap, int64_t *P)
+{
+    metad_status s = check_usable(c);
+    if (s) return s;
+    if (!c->have_nbr) return fail(c, METAD_ERR_STATE, "export before build_neighbors");
+    const int64_t need = (int64_t)c->sys.n * c->sys.max_nb / 2 + 1;
+    if (c->pairs_cap < need) {
+        if ((s = dalloc(c, &c->pairs, 2 * (size_t)need)) || (s = dalloc(c, &c->pair_count, 1))) return s;
+        c->pairs_cap = need;
+    }
+    if (c->filter_pending) {
+        StageScope t(c, ST_NBR, 1);
+        metad::launch_filter(c->sys, c->stream);
+        c->filter_pending = false;
+    }
+    {
+        StageScope t(c, ST_OTHER, 1);
+        metad::launch_export_pairs(c->sys, c->pairs, c->pair_count, c->stream);
+    }
+    if ((s = launched(c, "export"))) return s;
+    int cnt = 0;
+    if ((s = cuda_check(c, cudaMemcpyAsync(&cnt, c->pair_count, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+                        "count copy")))
+        return s;
+    if ((s = sync_and_check(c))) return s;
+    if (P) *P = cnt;
+    if (!pairs_host || cap <= 0) return METAD_OK;
+    std::vector<long long> tmp(2 * (size_t)cnt);
+    if (cnt > 0 &&
+        (s = cuda_check(c, cudaMemcpy(tmp.data(), c->pairs, sizeof(long long) * 2 * cnt, cudaMemcpyDeviceToHost),
+                        "pair copy")))
+        return s;
+    std::vector<std::pair<long long, long long>> v(cnt);
+    for (int k = 0; k < cnt; ++k) v[k] = {tmp[2 * k], tmp[2 * k + 1]};
+    std::sort(v.begin(), v.end());
+    const int64_t m = std::min<int64_t>(cap, cnt);
+    for (int64_t k = 0; k < m; ++k) {
+        pairs_host[2 * k] = v[k].first;
+        pairs_host[2 * k + 1] = v[k].second;
+    }
+    return METAD_OK;
+}
+
+metad_status metad_step(metad_ctx *c, const float *pos_dev, float *forces_dev, int32_t accumulate, int32_t deposit)
+{
+    metad_status s;
+    if ((s = metad_build_neighbors(c, pos_dev))) return s;
+    if ((s = metad_cv_forward(c, nullptr, nullptr))) return s;
+    if ((s = metad_bias_eval(c, nullptr, nullptr, nullptr))) return s;
+    if ((s = metad_bias_forces(c, forces_dev, accumulate, 1.0))) return s;
+    if (deposit && (s = metad_deposit_hill(c, nullptr, nullptr))) return s;
+    return METAD_OK;
+}
+
+metad_status metad_step_host(metad_ctx *c, const float *pos_host, float *forces_host, int32_t accumulate,
+                             int32_t deposit, double *cv_host, double *V_host)
+{
+    metad_status s = check_usable(c);
+    if (s) return s;
+    if (!pos_host || !forces_host) return fail(c, METAD_ERR_INVALID, "NULL host buffer");
+    const size_t n = (size_t)c->p.n_atoms;
+    if (!c->pos_stage) {
+        if ((s = dalloc(c, &c->pos_stage, 4 * n)) || (s = dalloc(c, &c->force_stage, 3 * n))) return s;
+    }
+    if ((s = cuda_check(c, cudaMemcpyAsync(c->pos_stage, pos_host, sizeof(float) * 4 * n, cudaMemcpyHostToDevice,
+                                           c->stream), "position upload")))
+        return s;
+    if (accumulate &&
+        (s = cuda_check(c, cudaMemcpyAsync(c->force_stage, forces_host, sizeof(float) * 3 * n,
+                                           cudaMemcpyHostToDevice, c->stream), "force upload")))
+        return s;
+    if ((s = metad_step(c, c->pos_stage, c->force_stage, accumulate, deposit))) return s;
+    if ((s = cuda_check(c, cudaMemcpyAsync(forces_host, c->force_stage, sizeof(float) * 3 * n,
+                                           cudaMemcpyDeviceToHost, c->stream), "force download")))
+        return s;
+    if ((s = cuda_check(c, cudaMemcpyAsync(c->host_pinned, c->sys.scal, 5 * sizeof(double), cudaMemcpyDeviceToHost,
+                                           c->stream), "result copy")))
+        return s;
+    if ((s = sync_and_check(c))) return s;
+    if (cv_host)
+        for (int d = 0; d < c->p.n_cv; ++d) cv_host[d] = c->host_pinned[metad::kS0 + d];
+    if (V_host) *V_host = c->host_pinned[metad::kV];
+    return METAD_OK;
+}
+
+metad_status metad_profile_begin(metad_ctx *c, int32_t max_records)
+{
+    metad_status s = check_usable(c);
+    if (s) return s;
+    if (max_records < 1) return fail(c, METAD_ERR_INVALID, "max_records < 1");
+    for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+    c->prof_ev.assign(2 * (size_t)max_records, nullptr);
+    c->prof_stage.assign(max_records, 0);
+    for (auto &e : c->prof_ev)
+        if ((s = cuda_check(c, cudaEventCreate(&e), "cudaEventCreate"))) return s;
+    c->prof_cap = max_records;
+    c->prof_used = 0;
+    c->prof_on = true;
+    return METAD_OK;
+}
+
+metad_status metad_profile_end(metad_ctx *c, double *ms_per_stage, int32_t *records_per_stage)
+{
+    metad_status s = check_usable(c);
+    if (s) return s;
+    if (!c->prof_on) return fail(c, METAD_ERR_STATE, "profiling was not started");
+    c->prof_on = false;
+    if ((s = sync_and_check(c))) return s;
+    for (int k = 0; k < ST_COUNT; ++k) {
+        if (ms_per_stage) ms_per_stage[k] = 0.0;
+        if (records_per_stage) records_per_stage[k] = 0;
+    }
+    for (int r = 0; r < c->prof_used; ++r) {
+        float ms = 0.0f;
+        if ((s = cuda_check(c, cudaEventElapsedTime(&ms, c->prof_ev[2 * r], c->prof_ev[2 * r + 1]), "elapsed")))
+            return s;
+        if (ms_per_stage) ms_per_stage[c->prof_stage[r]] += ms;
+        if (records_per_stage) records_per_stage[c->prof_stage[r]] += 1;
+    }
+    c->prof_used = 0;
+    return METAD_OK;
+}
+
+const char *metad_stage_name(int32_t stage) { return (stage >= 0 && stage < ST_COUNT) ? kStageNames[stage] : "?"; }
+
+int64_t metad_launch_count(const metad_ctx *c) { return c ? c->launches : 0; }
+
+metad_status metad_rebuild_count(metad_ctx *c, int64_t *count)
+{
+    metad_status s = check_usable(c);
+    if (s) return s;
+    unsigned long long v = 0;
+    if ((s = cuda_check(c, cudaMemcpyAsync(&v, c->sys.rebuilds, sizeof(v), cudaMemcpyDeviceToHost, c->stream),
+                        "rebuild count")))
+        return s;
+    if ((s = sync_and_check(c))) return s;
+    if (count) *count = (int64_t)v;
+    return METAD_OK;
+}
+
+metad_status metad_neighbor_stats(metad_ctx *c, int64_t *entries, int32_t *max_per_atom)
+{
+    metad_status s = check_usable(c);
+    if (s) return s;
+    if (!c->have_nbr) return fail(c, METAD_ERR_STATE, "neighbor_stats before build_neighbors");
+    unsigned long long *sum = reinterpret_cast<unsigned long long *>(c->sys.part + 3 * (size_t)c->sys.part_stride);
+    int *mx = reinterpret_cast<int *>(sum + 1);
+    if (c->filter_pending) {
+        StageScope t(c, ST_NBR, 1);
+        metad::launch_filter(c->sys, c->stream);
+        c->filter_pending = false;
+    }
+    {
+        StageScope t(c, ST_OTHER, 1);
+        metad::launch_nn_stats(c->sys, sum, mx, c->stream);
+    }
+    if ((s = launched(c, "neighbor_stats"))) return s;
+    unsigned long long hs[2] = {0, 0};
+    if ((s = cuda_check(c, cudaMemcpyAsync(hs, sum, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                           c->stream), "stats copy")))
+        return s;
+    if ((s = sync_and_check(c))) return s;
+    if (entries) *entries = (int64_t)hs[0];
+    if (max_per_atom) *max_per_atom = (int32_t)(hs[1] & 0xffffffffu);
+    return METAD_OK;
+}
+
+metad_status metad_read_results(metad_ctx *c, double *cv_host, double *V_host, double *dVds_host)
+{
+    metad_status s = check_usable(c);
+    if (s) return s;
+    s = cuda_check(c, cudaMemcpyAsync(c->host_pinned, c->sys.scal, 5 * sizeof(double), cudaMemcpyDeviceToHost,
+                                      c->stream), "result copy");
+    if (s) return s;
+    if ((s = sync_and_check(c))) return s;
+    for (int d = 0; d < c->p.n_cv; ++d) {
+        if (cv_host) cv_host[d] = c->host_pinned[metad::kS0 + d];
+        if (dVds_host) dVds_host[d] = c->host_pinned[metad::kDV0 + d];
+    }
+    if (V_host) *V_host = c->host_pinned[metad::kV];
+    return METAD_OK;
+}
+
+metad_status metad_sync(metad_ctx *c)
+{
+    metad_status s = check_usable(c);
+    if (s) return s;
+    return sync_and_check(c);
+}
+
+}  // extern "C"

@@ -1,0 +1,176 @@
+// Steps a6 and a9: the Gaussian-hill bias (Methods, Eqs. 2-3, a per-dimension
+// sigma), its gradient, well-tempered deposition and the bias grid, all FP64.
+//
+//   V(s) = grid(s) + sum_k w_k exp(-sum_d (s_d - c_kd)^2 / (2 sigma_d^2))
+//   w_new = w0 exp(-V(c_new) / (kB T (gamma - 1)))
+//
+// The hill sum is spread over many blocks (FP64 throughput per SM is low on
+// this part) and finished by the last block to arrive, which adds the
+// partials in block order, so the result is independent of scheduling.
+#include "metad_impl.cuh"
+
+namespace metad {
+
+namespace {
+
+__device__ __forceinline__ void hermite(double t, double A[2], double B[2], double dA[2], double dB[2])
+{
+    const double t2 = t * t, t3 = t2 * t;
+    A[0] = 2.0 * t3 - 3.0 * t2 + 1.0;
+    A[1] = 3.0 * t2 - 2.0 * t3;
+    B[0] = t3 - 2.0 * t2 + t;
+    B[1] = t3 - t2;
+    dA[0] = 6.0 * (t2 - t);
+    dA[1] = 6.0 * (t - t2);
+    dB[0] = 3.0 * t2 - 4.0 * t + 1.0;
+    dB[1] = 3.0 * t2 - 2.0 * t;
+}
+
+// Bicubic Hermite patch of the node grid; zero outside [lo, hi].
+__device__ void grid_value(const Sys &s, double x0, double x1, double &V, double &g0, double &g1)
+{
+    V = g0 = g1 = 0.0;
+    if (!s.grid_on) return;
+    const double x[2] = {x0, x1};
+    int c[2];
+    double t[2];
+    for (int a = 0; a < 2; ++a) {
+        if (!(x[a] >= s.glo[a] && x[a] <= s.ghi[a])) return;
+        int k = (int)floor((x[a] - s.glo[a]) / s.gh[a]);
+        k = k < 0 ? 0 : (k > s.gn[a] - 2 ? s.gn[a] - 2 : k);
+        c[a] = k;
+        t[a] = (x[a] - (s.glo[a] + k * s.gh[a])) / s.gh[a];
+    }
+    double A0[2], B0[2], dA0[2], dB0[2], A1[2], B1[2], dA1[2], dB1[2];
+    hermite(t[0], A0, B0, dA0, dB0);
+    hermite(t[1], A1, B1, dA1, dB1);
+    const double h0 = s.gh[0], h1 = s.gh[1];
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+            const double *nd = s.grid + ((size_t)(c[0] + a) * s.gn[1] + (c[1] + b)) * 4;
+            const double f = nd[0], fx = h0 * nd[1], fy = h1 * nd[2], fxy = h0 * h1 * nd[3];
+            V += A0[a] * A1[b] * f + B0[a] * A1[b] * fx + A0[a] * B1[b] * fy + B0[a] * B1[b] * fxy;
+            g0 += dA0[a] * A1[b] * f + dB0[a] * A1[b] * fx + dA0[a] * B1[b] * fy + dB0[a] * B1[b] * fxy;
+            g1 += A0[a] * dA1[b] * f + B0[a] * dA1[b] * fx + A0[a] * dB1[b] * fy + B0[a] * dB1[b] * fxy;
+        }
+    g0 /= h0;
+    g1 /= h1;
+}
+
+__global__ void __launch_bounds__(kBlockBias) k_bias(Sys s, int K, const double *x_dev, double *out, int deposit)
+{
+    const double x0 = x_dev[0];
+    const double x1 = s.ncv == 2 ? x_dev[1] : 0.0;
+    const double inv2v0 = 0.5 / (s.sigma[0] * s.sigma[0]), inv2v1 = 0.5 / (s.sigma[1] * s.sigma[1]);
+    double V = 0.0, g0 = 0.0, g1 = 0.0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
+        const double d0 = x0 - s.hc[2 * (size_t)k];
+        double e = d0 * d0 * inv2v0;
+        double d1 = 0.0;
+        if (s.ncv == 2) {
+            d1 = x1 - s.hc[2 * (size_t)k + 1];
+            e += d1 * d1 * inv2v1;
+        }
+        const double gk = s.hw[k] * exp(-e);
+        V += gk;
+        g0 -= gk * d0 * (2.0 * inv2v0);
+        g1 -= gk * d1 * (2.0 * inv2v1);
+    }
+    // block sums in a fixed order
+    __shared__ double sh[3][kBlockBias / 32];
+    __shared__ bool am_last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        V += __shfl_down_sync(0xffffffffu, V, o);
+        g0 += __shfl_down_sync(0xffffffffu, g0, o);
+        g1 += __shfl_down_sync(0xffffffffu, g1, o);
+    }
+    if (lane == 0) { sh[0][wid] = V; sh[1][wid] = g0; sh[2][wid] = g1; }
+    __syncthreads();
+    double *part = s.part + 2 * (size_t)s.part_stride;
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0, c = 0.0;
+        for (int w = 0; w < kBlockBias / 32; ++w) { a += sh[0][w]; b += sh[1][w]; c += sh[2][w]; }
+        part[3 * blockIdx.x + 0] = a;
+        part[3 * blockIdx.x + 1] = b;
+        part[3 * blockIdx.x + 2] = c;
+        __threadfence();
+        unsigned prev = atomicAdd(&s.ticket[2], 1u);
+        am_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!am_last || threadIdx.x != 0) return;
+    __threadfence();
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int q = 0; q < (int)gridDim.x; ++q) {
+        a += __ldcg(part + 3 * q);
+        b += __ldcg(part + 3 * q + 1);
+        c += __ldcg(part + 3 * q + 2);
+    }
+    if (s.ncv == 2) {
+        double gv, gg0, gg1;
+        grid_value(s, x0, x1, gv, gg0, gg1);
+        a += gv;
+        b += gg0;
+        c += gg1;
+    }
+    out[0] = a;
+    out[1] = b;
+    out[2] = c;
+    s.ticket[2] = 0u;
+    if (deposit) {
+        const double w = s.w0 * exp(-a / s.kbdt);
+        s.hc[2 * (size_t)K] = x0;
+        s.hc[2 * (size_t)K + 1] = x1;
+        s.hw[K] = w;
+        s.scal[kDepW] = w;
+    }
+}
+
+// One thread per grid node: exact sums over hills [0, K).
+__global__ void k_grid_fold(Sys s, int K)
+{
+    const int node = blockIdx.x * blockDim.x + threadIdx.x;
+    if (node >= s.gn[0] * s.gn[1]) return;
+    const int a = node / s.gn[1], b = node % s.gn[1];
+    const double x = s.glo[0] + a * s.gh[0], y = s.glo[1] + b * s.gh[1];
+    const double v0 = s.sigma[0] * s.sigma[0], v1 = s.sigma[1] * s.sigma[1];
+    double f = 0.0, fx = 0.0, fy = 0.0, fxy = 0.0;
+    for (int k = 0; k < K; ++k) {
+        const double dx = x - s.hc[2 * (size_t)k], dy = y - s.hc[2 * (size_t)k + 1];
+        const double g = s.hw[k] * exp(-(dx * dx / (2.0 * v0) + dy * dy / (2.0 * v1)));
+        f += g;
+        fx -= g * dx / v0;
+        fy -= g * dy / v1;
+        fxy += g * dx * dy / (v0 * v1);
+    }
+    double *nd = s.grid + (size_t)node * 4;
+    nd[0] += f;
+    nd[1] += fx;
+    nd[2] += fy;
+    nd[3] += fxy;
+}
+
+}  // namespace
+
+int bias_blocks(int K)
+{
+    int b = (K + kBlockBias - 1) / kBlockBias;
+    if (b < 1) b = 1;
+    if (b > kMaxBiasBlocks) b = kMaxBiasBlocks;
+    return b;
+}
+
+void launch_bias(const Sys &s, int K, const double *x_dev, double *out_dev, int deposit, cudaStream_t st)
+{
+    k_bias<<<bias_blocks(K), kBlockBias, 0, st>>>(s, K, x_dev, out_dev, deposit);
+}
+
+void launch_grid_fold(const Sys &s, int K, cudaStream_t st)
+{
+    const int nodes = s.gn[0] * s.gn[1];
+    k_grid_fold<<<(nodes + 127) / 128, 128, 0, st>>>(s, K);
+}
+
+}  // namespace metad

@@ -1,0 +1,760 @@
+// Steps a4-a5 (CV forward) and a7-a8 (adjoint and bias forces).
+//
+// Per-atom definitions (sorted order i; N(i) the full neighbour list):
+//   w_ij = s(r_ij)                 rational switch, stretched to vanish at rc
+//   CN_i = sum_j w_ij [unlike]     s1 = (1/N) sum_i CN_i
+//   W_i  = sum_j w_ij              q_m(i) = sum_j w_ij Y_m(rhat_ij) / W_i
+//   qb_m(i) = (q_m(i) + sum_j w_ij q_m(j)) / (1 + W_i)
+//   qb6(i)  = sqrt(4 pi / 13 sum_m qb_m(i)^2)     s2 = (1/N) sum_i qb6(i)
+// (computed with unnormalised harmonics and weights K_m, see below)
+// Adjoint (reverse mode, the paper's autograd written by hand):
+//   b_m(i) = K_m qb_m(i) / (N qb6(i) (1 + W_i))                ds2/dA_m(i)
+//   g_m(k) = b_m(k) + sum_i w_ik b_m(i)                        ds2/dq_m(k)
+//   h_m(k) = g_m(k) / W_k                                      ds2/dQ_m(k)
+//   -ds2/dW_k = h(k).q(k) + b(k).qb(k), folded into the pair term:
+//   per pair (i, j), d = r_j - r_i:
+//     ds2/dw = h(i).(Y - q(i)) + h(j).(Y - q(j)) + b(i).(q(j) - qb(i)) + b(j).(q(i) - qb(j))
+//     ds2/dd = ds2/dw w'(r) d/r + w sum_m (h_m(i)+h_m(j)) dY_m/dd
+//     ds1/dd = (2/N) w'(r) d/r [unlike]
+//   F_i = sum_{j in N(i)} (V1 ds1/dd + V2 ds2/dd)
+// The CV passes walk full rows (each atom gathers its own sums); the force
+// evaluates each unordered pair once and gathers per atom in a fixed order:
+// no floating-point atomics, bit-reproducible.
+#include "metad_impl.cuh"
+
+namespace metad {
+
+// Real Y_6^m on the unit sphere, unnormalised: the pole-free associated-
+// Legendre parts P_m(z) = d^m P_6 / dz^m (dyadic coefficients from the
+// recurrence, exact in float32) times C_m, S_m, the real and imaginary parts
+// of (x + i y)^m.  The normalisation enters only through the weights
+//   K_0 = 1,  K_m = 2 (6-m)!/(6+m)!   (m > 0),
+// with qbar6^2 = sum_m K_m (unnormalised qbar_m)^2 (the 4 pi / 13 of the
+// Steinhardt definition cancels against the Y_6^m norms).  K_m is carried as
+// a float pair so no rounded constant biases the CV.
+// Layout: Y[0] m = 0; Y[2m-1] = P_m C_m; Y[2m] = P_m S_m, m = 1..6.
+struct YlmConst {
+    float pf[7][4];   // P_m(z) coefficients over z^2 powers (highest first)
+    float dpf[7][4];  // dP_m/dz likewise
+    double pd[7][4];
+    double dpd[7][4];
+    float kf_hi[kNY], kf_lo[kNY];  // K per Y slot
+    double kd[kNY];
+};
+__constant__ YlmConst c_ylm;
+
+template <typename real>
+__device__ __forceinline__ real ylm_c(int m, int k);
+template <>
+__device__ __forceinline__ float ylm_c<float>(int m, int k) { return c_ylm.pf[m][k]; }
+template <>
+__device__ __forceinline__ double ylm_c<double>(int m, int k) { return c_ylm.pd[m][k]; }
+template <typename real>
+__device__ __forceinline__ real ylm_dc(int m, int k);
+template <>
+__device__ __forceinline__ float ylm_dc<float>(int m, int k) { return c_ylm.dpf[m][k]; }
+template <>
+__device__ __forceinline__ double ylm_dc<double>(int m, int k) { return c_ylm.dpd[m][k]; }
+
+// P_m(z): degree 6 - m with the parity of 6 - m.
+template <typename real>
+__device__ __forceinline__ void legendre_parts(real z, real P[7])
+{
+#define C_(m, k) ylm_c<real>(m, k)
+    real z2 = z * z;
+    P[0] = ((C_(0, 0) * z2 + C_(0, 1)) * z2 + C_(0, 2)) * z2 + C_(0, 3);
+    P[1] = z * ((C_(1, 0) * z2 + C_(1, 1)) * z2 + C_(1, 2));
+    P[2] = (C_(2, 0) * z2 + C_(2, 1)) * z2 + C_(2, 2);
+    P[3] = z * (C_(3, 0) * z2 + C_(3, 1));
+    P[4] = C_(4, 0) * z2 + C_(4, 1);
+    P[5] = z * C_(5, 0);
+    P[6] = C_(6, 0);
+#undef C_
+}
+
+template <typename real>
+__device__ __forceinline__ void legendre_dparts(real z, real D[7])
+{
+#define C_(m, k) ylm_dc<real>(m, k)
+    real z2 = z * z;
+    D[0] = z * ((C_(0, 0) * z2 + C_(0, 1)) * z2 + C_(0, 2));
+    D[1] = (C_(1, 0) * z2 + C_(1, 1)) * z2 + C_(1, 2);
+    D[2] = z * (C_(2, 0) * z2 + C_(2, 1));
+    D[3] = C_(3, 0) * z2 + C_(3, 1);
+    D[4] = z * C_(4, 0);
+    D[5] = C_(5, 0);
+    D[6] = real(0);
+#undef C_
+}
+
+template <typename real>
+__device__ __forceinline__ void cs_powers(real x, real y, real C[7], real S[7])
+{
+    C[0] = real(1);
+    S[0] = real(0);
+#pragma unroll
+    for (int m = 1; m <= 6; ++m) {
+        C[m] = x * C[m - 1] - y * S[m - 1];
+        S[m] = x * S[m - 1] + y * C[m - 1];
+    }
+}
+
+template <typename real>
+__device__ __forceinline__ void ylm13(real x, real y, real z, real Y[kNY])
+{
+    real P[7], C[7], S[7];
+    legendre_parts<real>(z, P);
+    cs_powers<real>(x, y, C, S);
+    Y[0] = P[0];
+#pragma unroll
+    for (int m = 1; m <= 6; ++m) {
+        Y[2 * m - 1] = P[m] * C[m];
+        Y[2 * m] = P[m] * S[m];
+    }
+}
+
+// Y_k(u) and g = (I - u u^T) grad(sum_k c_k Y_k) / r.
+template <typename real>
+__device__ __forceinline__ void ylm13_grad(real x, real y, real z, real inv_r, const real c[kNY], real Y[kNY],
+                                           real g[3])
+{
+    real P[7], D[7], C[7], S[7];
+    legendre_parts<real>(z, P);
+    legendre_dparts<real>(z, D);
+    cs_powers<real>(x, y, C, S);
+    Y[0] = P[0];
+    real gx = real(0), gy = real(0), gz = c[0] * D[0];
+#pragma unroll
+    for (int m = 1; m <= 6; ++m) {
+        real cc = c[2 * m - 1], cs = c[2 * m];
+        Y[2 * m - 1] = P[m] * C[m];
+        Y[2 * m] = P[m] * S[m];
+        real pm = P[m] * real(m);
+        gx += pm * (cc * C[m - 1] + cs * S[m - 1]);
+        gy += pm * (cs * C[m - 1] - cc * S[m - 1]);
+        gz += D[m] * (cc * C[m] + cs * S[m]);
+    }
+    real ug = x * gx + y * gy + z * gz;
+    g[0] = (gx - ug * x) * inv_r;
+    g[1] = (gy - ug * y) * inv_r;
+    g[2] = (gz - ug * z) * inv_r;
+}
+
+// sum_k K_k a_k^2 with K as a float pair (FP32) or exact (FP64).
+template <typename real>
+__device__ __forceinline__ real weighted_sq(const real a[kNY]);
+template <>
+__device__ __forceinline__ float weighted_sq<float>(const float a[kNY])
+{
+    float hi = 0.0f, lo = 0.0f;
+#pragma unroll
+    for (int m = 0; m < kNY; ++m) {
+        float a2 = a[m] * a[m];
+        hi = fmaf(c_ylm.kf_hi[m], a2, hi);
+        lo = fmaf(c_ylm.kf_lo[m], a2, lo);
+    }
+    return hi + lo;
+}
+template <>
+__device__ __forceinline__ double weighted_sq<double>(const double a[kNY])
+{
+    double s = 0.0;
+#pragma unroll
+    for (int m = 0; m < kNY; ++m) s += c_ylm.kd[m] * a[m] * a[m];
+    return s;
+}
+template <typename real>
+__device__ __forceinline__ real weighted_term(int m, real a);
+template <>
+__device__ __forceinline__ float weighted_term<float>(int m, float a)
+{
+    const float a2 = a * a;
+    return fmaf(c_ylm.kf_lo[m], a2, c_ylm.kf_hi[m] * a2);
+}
+template <>
+__device__ __forceinline__ double weighted_term<double>(int m, double a) { return c_ylm.kd[m] * a * a; }
+
+template <typename real>
+__device__ __forceinline__ real kweight(int m);
+template <>
+__device__ __forceinline__ float kweight<float>(int m) { return c_ylm.kf_hi[m]; }
+template <>
+__device__ __forceinline__ double kweight<double>(int m) { return c_ylm.kd[m]; }
+
+// 16-wide per-atom records (13 used): one 64 B (FP32) or 128 B (FP64) row
+// per atom, so a neighbour's record is two sectors, not thirteen.
+constexpr int kRec = 16;
+
+template <typename real>
+__device__ __forceinline__ void load_rec(const real *base, int i, real v[kRec]);
+template <>
+__device__ __forceinline__ void load_rec<float>(const float *base, int i, float v[kRec])
+{
+    const float4 *p = reinterpret_cast<const float4 *>(base + (size_t)i * kRec);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float4 t = p[k];
+        v[4 * k] = t.x;
+        v[4 * k + 1] = t.y;
+        v[4 * k + 2] = t.z;
+        v[4 * k + 3] = t.w;
+    }
+}
+template <>
+__device__ __forceinline__ void load_rec<double>(const double *base, int i, double v[kRec])
+{
+    const double2 *p = reinterpret_cast<const double2 *>(base + (size_t)i * kRec);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        double2 t = p[k];
+        v[2 * k] = t.x;
+        v[2 * k + 1] = t.y;
+    }
+}
+template <typename real>
+__device__ __forceinline__ void store_rec(real *base, int i, const real v[kRec]);
+template <>
+__device__ __forceinline__ void store_rec<float>(float *base, int i, const float v[kRec])
+{
+    float4 *p = reinterpret_cast<float4 *>(base + (size_t)i * kRec);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) p[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+}
+template <>
+__device__ __forceinline__ void store_rec<double>(double *base, int i, const double v[kRec])
+{
+    double2 *p = reinterpret_cast<double2 *>(base + (size_t)i * kRec);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) p[k] = make_double2(v[2 * k], v[2 * k + 1]);
+}
+
+namespace {
+
+template <typename real>
+__device__ __forceinline__ real *R(void *p) { return reinterpret_cast<real *>(p); }
+
+// Fixed-order FP64 block sum (result valid in thread 0).
+__device__ __forceinline__ double block_sum(double v, double *sh)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    __syncthreads();
+    return t;
+}
+
+// Block partial -> part[slot * part_stride + block]; the last block to finish
+// sums all partials in block order (fixed, independent of completion order)
+// and stores total * scale in *dst.
+__device__ void last_block_reduce(const Sys &s, double v, int slot, double *dst, double scale)
+{
+    __shared__ double sh[32];
+    __shared__ bool am_last;
+    if (gridDim.x > (unsigned)s.part_stride) {  // never with group_grid(); refuse rather than overrun
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_err(s, kErrInternal);
+        return;
+    }
+    double t = block_sum(v, sh);
+    double *part = s.part + (size_t)slot * s.part_stride;
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = t;
+        __threadfence();
+        unsigned prev = atomicAdd(&s.ticket[slot], 1u);
+        am_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    double acc = 0.0;
+    // each thread sums a contiguous chunk in order; chunks are then added in
+    // thread order: a fixed association for a given grid size
+    const int nb = gridDim.x, per = (nb + blockDim.x - 1) / blockDim.x;
+    for (int b = threadIdx.x * per; b < min(nb, (int)(threadIdx.x + 1) * per); ++b) acc += __ldcg(part + b);
+    __shared__ double all[kBlockAtoms];
+    all[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int k = 0; k < (int)blockDim.x; ++k) tot += all[k];
+        *dst = tot * scale;
+        s.ticket[slot] = 0u;
+    }
+}
+
+template <typename real>
+__device__ __forceinline__ void pair_geometry(const Sys &s, float4 pi, float4 pj, Vec3<real> &d, real &inv_r,
+                                              real &w, real &dw)
+{
+    d = displacement<real>(s, pi, pj);
+    real r2 = d.x * d.x + d.y * d.y + d.z * d.z;
+    inv_r = rsqrt_r<real>(r2);
+    switch_eval<real>(s, r2 * inv_r, w, dw);
+}
+
+// Butterfly reduce-scatter of 16 values over the kG lanes of a group:
+// afterwards lane l holds the group sums of values 2l and 2l + 1 in v[0], v[1].
+template <typename real>
+__device__ __forceinline__ void reduce_scatter16(real v[kRec], int l)
+{
+    int len = kRec;
+#pragma unroll
+    for (int o = kG / 2; o >= 1; o >>= 1) {
+        len >>= 1;
+        const bool upper = (l & o) != 0;
+#pragma unroll
+        for (int t = 0; t < kRec / 2; ++t) {
+            if (t < len) {
+                real a = v[t], b = v[t + len];
+                real send = upper ? a : b;
+                real keep = upper ? b : a;
+                v[t] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
+        }
+    }
+}
+
+// Sum over the kG lanes of a group, result in every lane.
+template <typename real>
+__device__ __forceinline__ real group_sum(real v)
+{
+#pragma unroll
+    for (int o = kG / 2; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename real>
+__device__ __forceinline__ real group_get(real v, int src_lane)
+{
+    const int base = (threadIdx.x & 31) & ~(kG - 1);
+    return __shfl_sync(0xffffffffu, v, base + src_lane);
+}
+
+template <typename real>
+__device__ __forceinline__ void store_pair(real *base, int i, int l, real a, real b);
+template <>
+__device__ __forceinline__ void store_pair<float>(float *base, int i, int l, float a, float b)
+{
+    reinterpret_cast<float2 *>(base + (size_t)i * kRec)[l] = make_float2(a, b);
+}
+template <>
+__device__ __forceinline__ void store_pair<double>(double *base, int i, int l, double a, double b)
+{
+    reinterpret_cast<double2 *>(base + (size_t)i * kRec)[l] = make_double2(a, b);
+}
+
+__device__ __forceinline__ const int *nbr_row(const Sys &s, int i) { return s.nbr + (size_t)i * s.max_nb; }
+
+// a4: CN_i, W_i and q_m(i) = sum_j w_ij Y_m(rhat_ij) / W_i.
+// With kFilter the exact row is first compacted from the Verlet row.
+template <typename real, bool kFilter>
+__global__ void __launch_bounds__(kBlockAtoms) k_cv_fwd(Sys s)
+{
+    const AtomLane a = atom_lane(s);
+    int nn_f = 0;
+    if (kFilter) nn_f = filter_row(s, a);
+    real v[kRec];  // 0..12: sum w Y_m ; 13: W ; 14: CN
+#pragma unroll
+    for (int m = 0; m < kRec; ++m) v[m] = real(0);
+    if (a.ok) {
+        const float4 pi = s.pos_s[a.i];
+        const int nn = kFilter ? nn_f : s.nn[a.i];
+        const int *row = nbr_row(s, a.i);
+        real *wrow = R<real>(s.wl) + (size_t)a.i * s.max_nb;
+        for (int k = a.l; k < nn; k += kG) {
+            const float4 pj = s.pos_s[row[k]];
+            Vec3<real> d;
+            real inv_r, w, dw;
+            pair_geometry<real>(s, pi, pj, d, inv_r, w, dw);
+            wrow[k] = w;
+            if (!s.cn_unlike || pj.w != pi.w) v[14] += w;
+            v[13] += w;
+            if (s.ncv == 2) {
+                real Y[kNY];
+                ylm13<real>(d.x * inv_r, d.y * inv_r, d.z * inv_r, Y);
+#pragma unroll
+                for (int m = 0; m < kNY; ++m) v[m] += w * Y[m];
+            }
+        }
+    }
+    reduce_scatter16<real>(v, a.l);
+    // lane 6 holds (13: W, ...) in v[1]; lane 7 holds (14: CN, 15) in v[0]
+    const real W = group_get<real>(v[1], 6);
+    double cn_out = 0.0;
+    if (a.ok) {
+        if (a.l == 7) {
+            R<real>(s.cn)[a.i] = v[0];
+            cn_out = (double)v[0];
+        }
+        if (a.l == 6) R<real>(s.W)[a.i] = W;
+        if (s.ncv == 2) {
+            const real inv_W = W > real(0) ? real(1) / W : real(0);
+            real q0 = v[0] * inv_W, q1 = v[1] * inv_W;
+            if (a.l == 6) q1 = real(0);
+            if (a.l == 7) q0 = q1 = real(0);
+            store_pair<real>(R<real>(s.q), a.i, a.l, q0, q1);
+        }
+    }
+    last_block_reduce(s, cn_out, 0, s.scal + kS0, 1.0 / s.n);
+}
+
+// a5: qbar_m(i), qbar6(i), s2.  Record qb: qbar_m (0..12) and
+// c_i = 1 / (N qbar6 (1 + W_i)) (13), so b_m(i) = c_i K_m qbar_m(i).
+template <typename real>
+__global__ void __launch_bounds__(kBlockAtoms) k_cv_avg(Sys s)
+{
+    const AtomLane a = atom_lane(s);
+    const real *q = R<real>(s.q);
+    real v[kRec];
+#pragma unroll
+    for (int m = 0; m < kRec; ++m) v[m] = real(0);
+    if (a.ok) {
+        const int nn = s.nn[a.i];
+        const int *row = nbr_row(s, a.i);
+        const real *wrow = R<real>(s.wl) + (size_t)a.i * s.max_nb;
+        for (int k = a.l; k < nn; k += kG) {
+            const int j = row[k];
+            const real w = wrow[k];
+            real qj[kRec];
+            load_rec<real>(q, j, qj);
+#pragma unroll
+            for (int m = 0; m < kNY; ++m) v[m] += w * qj[m];
+        }
+    }
+    reduce_scatter16<real>(v, a.l);
+    real qb0 = real(0), qb1 = real(0), sq = real(0);
+    real inv_D = real(0);
+    if (a.ok) {
+        inv_D = real(1) / (real(1) + R<real>(s.W)[a.i]);
+        const int m0 = 2 * a.l, m1 = 2 * a.l + 1;
+        if (m0 < kNY) qb0 = (q[(size_t)a.i * kRec + m0] + v[0]) * inv_D;
+        if (m1 < kNY) qb1 = (q[(size_t)a.i * kRec + m1] + v[1]) * inv_D;
+        if (m0 < kNY) sq += weighted_term<real>(m0, qb0);
+        if (m1 < kNY) sq += weighted_term<real>(m1, qb1);
+    }
+    sq = group_sum<real>(sq);
+    const real qb6 = sqrt(sq);
+    double q6_out = 0.0;
+    if (a.ok) {
+        const real ci = qb6 > real(0) ? inv_D / (real(s.n) * qb6) : real(0);
+        if (a.l == 6) qb1 = ci;  // slot 13
+        store_pair<real>(R<real>(s.b), a.i, a.l, qb0, qb1);
+        if (a.l == 0) {
+            R<real>(s.qb6)[a.i] = qb6;
+            q6_out = (double)qb6;
+        }
+    }
+    last_block_reduce(s, q6_out, 1, s.scal + kS1, 1.0 / s.n);
+}
+
+// a7: g_m(k) = K_m (c_k qbar_m(k) + sum_i w_ik c_i qbar_m(i)) ; h = g / W.
+template <typename real>
+__global__ void __launch_bounds__(kBlockAtoms) k_adjoint(Sys s)
+{
+    const AtomLane a = atom_lane(s);
+    const real *qb = R<real>(s.b);
+    real v[kRec];
+#pragma unroll
+    for (int m = 0; m < kRec; ++m) v[m] = real(0);
+    if (a.ok) {
+        const int nn = s.nn[a.i];
+        const int *row = nbr_row(s, a.i);
+        const real *wrow = R<real>(s.wl) + (size_t)a.i * s.max_nb;
+        for (int k = a.l; k < nn; k += kG) {
+            const int j = row[k];
+            const real w = wrow[k];
+            real bj[kRec];
+            load_rec<real>(qb, j, bj);
+            const real wc = w * bj[13];
+#pragma unroll
+            for (int m = 0; m < kNY; ++m) v[m] += wc * bj[m];
+        }
+    }
+    reduce_scatter16<real>(v, a.l);
+    if (a.ok) {
+        const real W = R<real>(s.W)[a.i];
+        const real inv_W = W > real(0) ? real(1) / W : real(0);
+        const real *own = qb + (size_t)a.i * kRec;
+        const real ci = own[13];
+        const int m0 = 2 * a.l, m1 = 2 * a.l + 1;
+        real h0 = real(0), h1 = real(0);
+        if (m0 < kNY) h0 = kweight<real>(m0) * (ci * own[m0] + v[0]) * inv_W;
+        if (m1 < kNY) h1 = kweight<real>(m1) * (ci * own[m1] + v[1]) * inv_W;
+        store_pair<real>(R<real>(s.h), a.i, a.l, h0, h1);
+    }
+}
+
+// a8, pass 1: for every unordered pair, from the row of its lower index i
+// (entries k < nh_i, j > i), G_ij = V1 ds1/dd + V2 ds2/dd at d = r_j - r_i,
+// stored in the pair's slot.  Each pair is evaluated once.
+//   ds2/dw = h_i.(Y - q_i) + h_j.(Y - q_j) + b_i.(q_j - qb_i) + b_j.(q_i - qb_j)
+// (differences formed before the products), ds2/dd = ds2/dw w' d/r
+// + w sum_m (h_i + h_j)_m dY_m/dd, ds1/dd = (2/N) w' d/r [unlike].
+template <typename real>
+__device__ __forceinline__ void store_pair_force(real *slot, real fx, real fy, real fz);
+template <>
+__device__ __forceinline__ void store_pair_force<float>(float *slot, float fx, float fy, float fz)
+{
+    *reinterpret_cast<float4 *>(slot) = make_float4(fx, fy, fz, 0.0f);
+}
+template <>
+__device__ __forceinline__ void store_pair_force<double>(double *slot, double fx, double fy, double fz)
+{
+    reinterpret_cast<double2 *>(slot)[0] = make_double2(fx, fy);
+    reinterpret_cast<double2 *>(slot)[1] = make_double2(fz, 0.0);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kBlockAtoms) k_force_pairs(Sys s, double scale)
+{
+    const AtomLane a = atom_lane(s);
+    if (!a.ok) return;
+    const int nh = s.nh[a.i];
+    if (a.l >= nh) return;
+    const real cn_fac = (real)(s.scal[kDV0] * scale * 2.0 / s.n);
+    const bool q6 = s.ncv == 2;
+    const real V2 = q6 ? (real)(s.scal[kDV1] * scale) : real(0);
+    const real *hh = R<real>(s.h), *qq = R<real>(s.q), *qbb = R<real>(s.b);
+    const float4 pi = s.pos_s[a.i];
+    real hi[kRec], qi[kRec], qbi[kRec];
+    if (q6) {
+        load_rec<real>(hh, a.i, hi);
+        load_rec<real>(qq, a.i, qi);
+        load_rec<real>(qbb, a.i, qbi);
+    }
+    const int *row = nbr_row(s, a.i);
+    real *slots = R<real>(s.pairF) + (size_t)a.i * s.max_nb * 4;
+    for (int k = a.l; k < nh; k += kG) {
+        const int j = row[k];
+        const float4 pj = s.pos_s[j];
+        Vec3<real> d;
+        real inv_r, w, dw;
+        pair_geometry<real>(s, pi, pj, d, inv_r, w, dw);
+        const real ux = d.x * inv_r, uy = d.y * inv_r, uz = d.z * inv_r;
+        real radial = (!s.cn_unlike || pj.w != pi.w) ? cn_fac * dw : real(0);
+        real fx = real(0), fy = real(0), fz = real(0);
+        if (q6) {
+            real hj[kRec], qj[kRec], qbj[kRec];
+            load_rec<real>(hh, j, hj);
+            load_rec<real>(qq, j, qj);
+            load_rec<real>(qbb, j, qbj);
+            real cvec[kNY];
+#pragma unroll
+            for (int m = 0; m < kNY; ++m) cvec[m] = w * (hi[m] + hj[m]);
+            real Y[kNY], gY[3];
+            ylm13_grad<real>(ux, uy, uz, inv_r, cvec, Y, gY);
+            const real ci = qbi[13], cj = qbj[13];
+            real t_h = real(0), t_b = real(0);
+#pragma unroll
+            for (int m = 0; m < kNY; ++m) {
+                t_h += hi[m] * (Y[m] - qi[m]) + hj[m] * (Y[m] - qj[m]);
+                t_b += kweight<real>(m) * (ci * qbi[m] * (qj[m] - qbi[m]) + cj * qbj[m] * (qi[m] - qbj[m]));
+            }
+            radial += V2 * (t_h + t_b) * dw;
+            fx = V2 * gY[0];
+            fy = V2 * gY[1];
+            fz = V2 * gY[2];
+        }
+        fx += radial * ux;
+        fy += radial * uy;
+        fz += radial * uz;
+        store_pair_force<real>(slots + 4 * (size_t)k, fx, fy, fz);
+    }
+}
+
+template <typename real>
+__device__ __forceinline__ void load_pair_force(const real *slot, real &fx, real &fy, real &fz);
+template <>
+__device__ __forceinline__ void load_pair_force<float>(const float *slot, float &fx, float &fy, float &fz)
+{
+    const float4 t = *reinterpret_cast<const float4 *>(slot);
+    fx = t.x;
+    fy = t.y;
+    fz = t.z;
+}
+template <>
+__device__ __forceinline__ void load_pair_force<double>(const double *slot, double &fx, double &fy, double &fz)
+{
+    const double2 a = reinterpret_cast<const double2 *>(slot)[0];
+    const double2 b = reinterpret_cast<const double2 *>(slot)[1];
+    fx = a.x;
+    fy = a.y;
+    fz = b.x;
+}
+
+// a8, pass 2: F_i = sum_{j > i} G_ij - sum_{j < i} G_ji over i's row, in row
+// order per lane and a fixed shuffle tree across lanes: deterministic, no
+// atomics.  G_ji sits in j's slot of i, found in the j > i part of j's row.
+template <typename real>
+__global__ void __launch_bounds__(kBlockAtoms) k_force_gather(Sys s, float *F, int accumulate)
+{
+    const AtomLane a = atom_lane(s);
+    real fx = real(0), fy = real(0), fz = real(0);
+    if (a.ok) {
+        const int nn = s.nn[a.i], nh = s.nh[a.i];
+        const int *row = nbr_row(s, a.i);
+        const real *pf = R<real>(s.pairF);
+        for (int k = a.l; k < nn; k += kG) {
+            real gx, gy, gz;
+            if (k < nh) {
+                load_pair_force<real>(pf + ((size_t)a.i * s.max_nb + k) * 4, gx, gy, gz);
+                fx += gx;
+                fy += gy;
+                fz += gz;
+            } else {
+                const int j = row[k];
+                const int *rj = nbr_row(s, j);
+                const int nhj = s.nh[j];
+                int kk = 0;
+                while (kk < nhj && rj[kk] != a.i) ++kk;
+                if (kk == nhj) {
+                    set_err(s, kErrInternal);  // rows not symmetric: never expected
+                    continue;
+                }
+                load_pair_force<real>(pf + ((size_t)j * s.max_nb + kk) * 4, gx, gy, gz);
+                fx -= gx;
+                fy -= gy;
+                fz -= gz;
+            }
+        }
+    }
+    fx = group_sum<real>(fx);
+    fy = group_sum<real>(fy);
+    fz = group_sum<real>(fz);
+    if (a.ok && a.l == 0) {
+        float *o = F + 3 * (size_t)s.perm[a.i];
+        if (accumulate) {
+            o[0] += (float)fx;
+            o[1] += (float)fy;
+            o[2] += (float)fz;
+        } else {
+            o[0] = (float)fx;
+            o[1] = (float)fy;
+            o[2] = (float)fz;
+        }
+    }
+}
+
+template <typename real>
+__global__ void k_per_atom_out(Sys s, double *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s.n) return;
+    const int u = s.perm[i];
+    out[u] = (double)R<real>(s.cn)[i];
+    if (s.ncv == 2) out[(size_t)s.n + u] = (double)R<real>(s.qb6)[i];
+}
+
+inline int atom_blocks(int n) { return group_grid(n); }
+
+}  // namespace
+
+void launch_cv_fwd(const Sys &s, int fp64, int fused_filter, cudaStream_t st)
+{
+    const int nb = atom_blocks(s.n);
+    if (fp64) {
+        if (fused_filter)
+            k_cv_fwd<double, true><<<nb, kBlockAtoms, 0, st>>>(s);
+        else
+            k_cv_fwd<double, false><<<nb, kBlockAtoms, 0, st>>>(s);
+    } else {
+        if (fused_filter)
+            k_cv_fwd<float, true><<<nb, kBlockAtoms, 0, st>>>(s);
+        else
+            k_cv_fwd<float, false><<<nb, kBlockAtoms, 0, st>>>(s);
+    }
+}
+
+void launch_cv_avg(const Sys &s, int fp64, cudaStream_t st)
+{
+    if (fp64)
+        k_cv_avg<double><<<atom_blocks(s.n), kBlockAtoms, 0, st>>>(s);
+    else
+        k_cv_avg<float><<<atom_blocks(s.n), kBlockAtoms, 0, st>>>(s);
+}
+
+void launch_adjoint(const Sys &s, int fp64, cudaStream_t st)
+{
+    if (fp64)
+        k_adjoint<double><<<atom_blocks(s.n), kBlockAtoms, 0, st>>>(s);
+    else
+        k_adjoint<float><<<atom_blocks(s.n), kBlockAtoms, 0, st>>>(s);
+}
+
+void launch_force(const Sys &s, int fp64, float *F, int accumulate, double scale, cudaStream_t st)
+{
+    const int nb = atom_blocks(s.n);
+    if (fp64) {
+        k_force_pairs<double><<<nb, kBlockAtoms, 0, st>>>(s, scale);
+        k_force_gather<double><<<nb, kBlockAtoms, 0, st>>>(s, F, accumulate);
+    } else {
+        k_force_pairs<float><<<nb, kBlockAtoms, 0, st>>>(s, scale);
+        k_force_gather<float><<<nb, kBlockAtoms, 0, st>>>(s, F, accumulate);
+    }
+}
+
+int force_kernels(const Sys &) { return 2; }
+
+void launch_per_atom_out(const Sys &s, int fp64, double *out, cudaStream_t st)
+{
+    if (fp64)
+        k_per_atom_out<double><<<(s.n + 255) / 256, 256, 0, st>>>(s, out);
+    else
+        k_per_atom_out<float><<<(s.n + 255) / 256, 256, 0, st>>>(s, out);
+}
+
+// Polynomial parts from the associated-Legendre recurrence on coefficient
+// arrays (pole-free, unnormalised):
+//   P_m^m = (2m-1)!!,  P_{m+1}^m = (2m+1) z P_m^m,
+//   P_l^m = ((2l-1) z P_{l-1}^m - (l+m-1) P_{l-2}^m) / (l-m);
+// every coefficient is a dyadic rational, exact in float32.  Weights
+// K_0 = 1, K_m = 2 (6-m)!/(6+m)!.
+void set_ylm_constants(cudaStream_t st)
+{
+    YlmConst h{};
+    const int l = 6;
+    for (int m = 0; m <= l; ++m) {
+        double prev2[8] = {0}, prev1[8] = {0}, cur[8] = {0};
+        double dfact = 1.0;
+        for (int k = 1; k <= 2 * m - 1; k += 2) dfact *= k;
+        prev1[0] = dfact;
+        if (m == l) {
+            for (int p = 0; p < 8; ++p) cur[p] = prev1[p];
+        } else {
+            for (int p = 0; p < 7; ++p) cur[p + 1] = (2 * m + 1) * prev1[p];
+            for (int ll = m + 2; ll <= l; ++ll) {
+                for (int p = 0; p < 8; ++p) { prev2[p] = prev1[p]; prev1[p] = cur[p]; cur[p] = 0.0; }
+                for (int p = 0; p < 7; ++p) cur[p + 1] += (2 * ll - 1) * prev1[p];
+                for (int p = 0; p < 8; ++p) cur[p] -= (ll + m - 1) * prev2[p];
+                for (int p = 0; p < 8; ++p) cur[p] /= (ll - m);
+            }
+        }
+        const int deg = l - m;
+        int t = 0;
+        for (int p = deg; p >= 0; p -= 2, ++t) {
+            h.pd[m][t] = cur[p];
+            h.pf[m][t] = (float)cur[p];
+        }
+        t = 0;
+        for (int p = deg; p >= 1; p -= 2, ++t) {
+            h.dpd[m][t] = cur[p] * p;
+            h.dpf[m][t] = (float)(cur[p] * p);
+        }
+        double fr = 1.0;  // (l-m)!/(l+m)!
+        for (int k = l - m + 1; k <= l + m; ++k) fr /= k;
+        const double K = m > 0 ? 2.0 * fr : 1.0;
+        const int slots[2] = {m == 0 ? 0 : 2 * m - 1, m == 0 ? 0 : 2 * m};
+        for (int q = 0; q < (m == 0 ? 1 : 2); ++q) {
+            h.kd[slots[q]] = K;
+            h.kf_hi[slots[q]] = (float)K;
+            h.kf_lo[slots[q]] = (float)(K - (double)(float)K);
+        }
+    }
+    cudaMemcpyToSymbolAsync(c_ylm, &h, sizeof(h), 0, cudaMemcpyHostToDevice, st);
+}
+
+}  // namespace metad

@@ -1,0 +1,377 @@
+// Steps a1-a3: ingest, Morton-ranked cell order, Verlet list and the exact
+// neighbour list.
+//
+// Each step:
+//   k_gather_check  positions in cell order (wrapped), and a flag when any
+//                   atom moved more than skin/2 since the last rebuild
+//   rebuild chain   (early exit unless flagged) counting sort of the atoms
+//                   into Morton-ranked cells of edge >= rc + skin, stable by
+//                   caller index, and the Verlet list r < rc + skin
+//   filter          exact rows {j : r_ij^2 < rc^2} from the Verlet rows
+//                   (fused into the CV kernel, or k_filter on its own)
+// The exact rows are the FP64 definition bit for bit: while no atom has moved
+// more than skin/2, every pair now inside rc was inside rc + skin at the
+// rebuild, and the float32 estimate only decides outside a guard band.
+#include "metad_impl.cuh"
+
+namespace metad {
+
+namespace {
+
+__device__ __forceinline__ float wrap_coord(float x, double L)
+{
+    double xd = (double)x;
+    if (xd >= 0.0 && xd < L) return x;
+    double w = xd - L * floor(xd / L);
+    float f = (float)w;
+    if ((double)f >= L) f = 0.0f;
+    return f;
+}
+
+__device__ __forceinline__ float4 load_wrapped(const Sys &s, int u, bool &bad)
+{
+    float4 p = s.pos_in[u];
+    bad = !(isfinite(p.x) && isfinite(p.y) && isfinite(p.z));
+    if (bad) {
+        p.x = p.y = p.z = 0.0f;
+        return p;
+    }
+    p.x = wrap_coord(p.x, s.L[0]);
+    p.y = wrap_coord(p.y, s.L[1]);
+    p.z = wrap_coord(p.z, s.L[2]);
+    return p;
+}
+
+__device__ __forceinline__ int cell_axis(float x, float inv_h, int nc)
+{
+    int c = (int)floorf(x * inv_h);
+    return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
+}
+
+// Current positions in the cell order of the last rebuild, and the rebuild
+// test.  Before the first rebuild the flag is already set.
+__global__ void k_gather_check(Sys s)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    bool move = false;
+    if (t < s.n) {
+        bool bad;
+        float4 p = load_wrapped(s, s.perm[t], bad);
+        if (bad) set_err(s, kErrNonFinite);
+        s.pos_s[t] = p;
+        const float4 r = s.pos_ref[t];
+        float dx = mi_f(p.x - r.x, s.halfL[0], s.Lhi[0], s.Llo[0]);
+        float dy = mi_f(p.y - r.y, s.halfL[1], s.Lhi[1], s.Llo[1]);
+        float dz = mi_f(p.z - r.z, s.halfL[2], s.Lhi[2], s.Llo[2]);
+        move = !(dx * dx + dy * dy + dz * dz <= s.disp_thr2) || p.w != r.w;
+    }
+    if (__any_sync(0xffffffffu, move) && (threadIdx.x & 31) == 0) atomicOr(s.flag, 1);
+}
+
+__global__ void k_rebuild_zero(Sys s)
+{
+    if (!*s.flag) return;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < s.ncell; c += gridDim.x * blockDim.x)
+        s.cell_count[c] = 0;
+}
+
+__device__ __forceinline__ void bin_one(const Sys &s, int u)
+{
+    bool bad;
+    float4 p = load_wrapped(s, u, bad);
+    int cx = cell_axis(p.x, s.inv_h[0], s.nc[0]);
+    int cy = cell_axis(p.y, s.inv_h[1], s.nc[1]);
+    int cz = cell_axis(p.z, s.inv_h[2], s.nc[2]);
+    int c = s.rank_of_xyz[(cz * s.nc[1] + cy) * s.nc[0] + cx];
+    s.ucell[u] = c;
+    s.uslot[u] = atomicAdd(&s.cell_count[c], 1);
+}
+
+__global__ void k_bin_count(Sys s)
+{
+    if (!*s.flag) return;
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < s.n; u += gridDim.x * blockDim.x)
+        bin_one(s, u);
+}
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int *warp_sums, int &total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int w = warp_sums[lane];
+        int t = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        warp_sums[lane] = t - w;
+        if (lane == 31) warp_sums[32] = t;
+    }
+    __syncthreads();
+    total = warp_sums[32];
+    int r = warp_sums[wid] + x - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(Sys s)
+{
+    if (!*s.flag) return;
+    __shared__ int ws[33];
+    int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    int v = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+        if (base + k < s.ncell) v += s.cell_count[base + k];
+    int total;
+    block_exclusive_scan(v, ws, total);
+    if (threadIdx.x == 0) s.scan_part[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(Sys s)
+{
+    if (!*s.flag) return;
+    __shared__ int ws[33];
+    __shared__ int prefix;
+    if (threadIdx.x < 32) {
+        int acc = 0;
+        for (int b = threadIdx.x; b < (int)blockIdx.x; b += 32) acc += s.scan_part[b];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (threadIdx.x == 0) prefix = acc;
+    }
+    __syncthreads();
+    int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    int c[kScanItems];
+    int v = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        c[k] = (base + k < s.ncell) ? s.cell_count[base + k] : 0;
+        v += c[k];
+    }
+    int total;
+    int ex = block_exclusive_scan(v, ws, total) + prefix;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < s.ncell) s.cell_start[base + k] = ex;
+        ex += c[k];
+    }
+    if (base <= s.ncell - 1 && s.ncell - 1 < base + kScanItems) s.cell_start[s.ncell] = s.n;
+}
+
+__global__ void k_bin_scatter(Sys s)
+{
+    if (!*s.flag) return;
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < s.n; u += gridDim.x * blockDim.x)
+        s.perm[s.cell_start[s.ucell[u]] + s.uslot[u]] = u;
+}
+
+// One thread per cell: order the cell's atoms by caller index (the atomic
+// slots above are not deterministic), gather their wrapped positions and
+// keep them as the reference of the new Verlet list.
+__device__ __forceinline__ void sort_gather_cell(const Sys &s, int c)
+{
+    int a = s.cell_start[c], e = s.cell_start[c + 1];
+    for (int t = a + 1; t < e; ++t) {
+        int v = s.perm[t];
+        int k = t - 1;
+        while (k >= a && s.perm[k] > v) {
+            s.perm[k + 1] = s.perm[k];
+            --k;
+        }
+        s.perm[k + 1] = v;
+    }
+    for (int t = a; t < e; ++t) {
+        bool bad;
+        float4 p = load_wrapped(s, s.perm[t], bad);
+        s.pos_s[t] = p;
+        s.pos_ref[t] = p;
+        s.scell[t] = c;
+    }
+}
+
+__global__ void k_cell_sort_gather(Sys s)
+{
+    if (!*s.flag) return;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < s.ncell; c += gridDim.x * blockDim.x)
+        sort_gather_cell(s, c);
+}
+
+__device__ __forceinline__ int axis_offsets(int nc, int *off)
+{
+    if (nc >= 3) { off[0] = -1; off[1] = 0; off[2] = 1; return 3; }
+    if (nc == 2) { off[0] = 0; off[1] = 1; return 2; }
+    off[0] = 0;
+    return 1;
+}
+
+__device__ __forceinline__ int wrap_cell(int c, int nc)
+{
+    c += (c < 0) ? nc : 0;
+    c -= (c >= nc) ? nc : 0;
+    return c;
+}
+
+// Verlet rows {j : r_ij^2 < (rc + skin)^2 (1 + 1e-4)} over the 27 surrounding
+// cells (each distinct cell once): entries with j > i first, then j < i.  A
+// group of kG lanes per atom, lanes over the atoms of each cell,
+// ballot-compacted in cell order; grid-stride over atom groups so an idle
+// launch (no rebuild) retires at once.
+__global__ void __launch_bounds__(kBlockAtoms) k_verlet(Sys s)
+{
+    if (!*s.flag) return;
+    int ox[3], oy[3], oz[3];
+    const int sx = axis_offsets(s.nc[0], ox), sy = axis_offsets(s.nc[1], oy), sz = axis_offsets(s.nc[2], oz);
+    const int nblk = group_grid(s.n);
+    for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+        const AtomLane a = atom_lane_at(s, blk);
+        const int i = a.ok ? a.i : 0;
+        const float4 pi = s.pos_s[i];
+        const int xyz = s.xyz_of_rank[s.scell[i]];
+        const int cx = xyz & 1023, cy = (xyz >> 10) & 1023, cz = xyz >> 20;
+        int *vrow = s.vnbr + (size_t)i * s.max_vnb;
+        int cnt = 0, nup = 0;
+#pragma unroll 1
+        for (int part = 0; part < 2; ++part) {
+            for (int q = 0; q < sx * sy * sz; ++q) {
+                const int e = q % sx, b = (q / sx) % sy, c3 = q / (sx * sy);
+                const int c = s.rank_of_xyz[(wrap_cell(cz + oz[c3], s.nc[2]) * s.nc[1] +
+                                             wrap_cell(cy + oy[b], s.nc[1])) * s.nc[0] +
+                                            wrap_cell(cx + ox[e], s.nc[0])];
+                const int j0 = s.cell_start[c], j1 = s.cell_start[c + 1];
+                const int span = a.ok ? j1 - j0 : 0;
+                const int smax = __reduce_max_sync(0xffffffffu, span);
+                for (int base = 0; base < smax; base += kG) {
+                    const int j = j0 + base + a.l;
+                    bool in = false;
+                    if (base + a.l < span && (part == 0 ? j > i : j < i)) {
+                        const float4 pj = s.pos_s[j];
+                        Vec3<float> d = displacement<float>(s, pi, pj);
+                        in = fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z)) < s.rv2;
+                    }
+                    const unsigned gm = group_mask_bits(__ballot_sync(0xffffffffu, in));
+                    const int at = cnt + __popc(gm & ((1u << a.l) - 1u));
+                    if (in && at < s.max_vnb) vrow[at] = j;
+                    cnt += __popc(gm);
+                }
+            }
+            if (part == 0) nup = cnt;
+        }
+        if (a.ok && a.l == 0) {
+            if (cnt > s.max_vnb) set_err(s, kErrCapacity);
+            s.vnn[i] = min(cnt, s.max_vnb);
+            s.vnh[i] = min(nup, s.max_vnb);
+        }
+    }
+}
+
+// Exact rows from the Verlet rows, when the CV kernel does not fuse it.
+__global__ void __launch_bounds__(kBlockAtoms) k_filter(Sys s)
+{
+    const AtomLane a = atom_lane(s);
+    filter_row(s, a);
+}
+
+// End of a rebuild: the flag is cleared for the next step (kept set when the
+// skin is zero, so every step rebuilds).
+__global__ void k_clear_flag(Sys s)
+{
+    if (*s.flag) *s.rebuilds += 1ull;
+    *s.flag = s.always_rebuild ? 1 : 0;
+}
+
+// Pairs (i < j) in caller indices, for export: one thread per sorted atom,
+// entries with caller(i) < caller(j) appended through one counter.
+__global__ void k_export_pairs(Sys s, long long *pairs, int *count)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s.n) return;
+    int ui = s.perm[i];
+    for (int k = 0; k < s.nn[i]; ++k) {
+        int uj = s.perm[s.nbr[(size_t)i * s.max_nb + k]];
+        if (ui < uj) {
+            int slot = atomicAdd(count, 1);
+            pairs[2 * (size_t)slot] = ui;
+            pairs[2 * (size_t)slot + 1] = uj;
+        }
+    }
+}
+
+// Sum and maximum of the per-atom neighbour counts.
+__global__ void k_nn_stats(Sys s, unsigned long long *sum, int *mx)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int v = i < s.n ? s.nn[i] : 0;
+    int m = v;
+    unsigned long long t = (unsigned long long)v;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        t += __shfl_xor_sync(0xffffffffu, t, o);
+        m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(sum, t);
+        atomicMax(mx, m);
+    }
+}
+
+inline int group_blocks(int n) { return group_grid(n); }
+
+}  // namespace
+
+void launch_gather_check(const Sys &s, cudaStream_t st)
+{
+    k_gather_check<<<(s.n + 255) / 256, 256, 0, st>>>(s);
+}
+
+// Grids of the rebuild chain are capped (grid-stride loops inside) so that
+// the common no-rebuild step pays a few microseconds of launches.
+constexpr int kRebuildGrid = 152 * 8;
+
+inline int capped(int blocks) { return blocks < kRebuildGrid ? (blocks < 1 ? 1 : blocks) : kRebuildGrid; }
+
+void launch_rebuild(const Sys &s, cudaStream_t st)
+{
+    const int tiles = (s.ncell + kScanTile - 1) / kScanTile;
+    k_rebuild_zero<<<capped((s.ncell + 1023) / 1024), 1024, 0, st>>>(s);
+    k_bin_count<<<capped((s.n + 255) / 256), 256, 0, st>>>(s);
+    k_scan_reduce<<<tiles, kScanThreads, 0, st>>>(s);
+    k_scan_down<<<tiles, kScanThreads, 0, st>>>(s);
+    k_bin_scatter<<<capped((s.n + 255) / 256), 256, 0, st>>>(s);
+    k_cell_sort_gather<<<capped((s.ncell + 127) / 128), 128, 0, st>>>(s);
+    k_verlet<<<capped(group_blocks(s.n)), kBlockAtoms, 0, st>>>(s);
+    k_clear_flag<<<1, 1, 0, st>>>(s);
+}
+
+void launch_filter(const Sys &s, cudaStream_t st)
+{
+    k_filter<<<group_blocks(s.n), kBlockAtoms, 0, st>>>(s);
+}
+
+void launch_nn_stats(const Sys &s, unsigned long long *sum, int *mx, cudaStream_t st)
+{
+    cudaMemsetAsync(sum, 0, sizeof(unsigned long long), st);
+    cudaMemsetAsync(mx, 0, sizeof(int), st);
+    k_nn_stats<<<(s.n + 255) / 256, 256, 0, st>>>(s, sum, mx);
+}
+
+void launch_export_pairs(const Sys &s, long long *pairs, int *count, cudaStream_t st)
+{
+    cudaMemsetAsync(count, 0, sizeof(int), st);
+    k_export_pairs<<<(s.n + 255) / 256, 256, 0, st>>>(s, pairs, count);
+}
+
+}  // namespace metad

@@ -1,0 +1,362 @@
+// Internal declarations of the sm_103a metadynamics bias path.
+//
+// One `Sys` value describes one system: geometry, switch constants and the
+// device pointers of all its per-atom state.  Kernels take it by value; the
+// batched kernels take a device array of them.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace metad {
+
+constexpr int kNY = 13;          // real Y_6^m, m = -6..6
+constexpr int kMaxBatch = 256;   // systems per batched launch
+constexpr int kBlockAtoms = 128; // threads per block of the per-atom kernels
+constexpr int kBlockBias = 256;  // threads per block of the hill kernels
+constexpr int kMaxBiasBlocks = 304;  // two per SM
+
+enum ErrBits : int {
+    kErrCapacity = 1,   // an atom had more neighbours than max_nb
+    kErrNonFinite = 2,  // a position was NaN or infinite
+    kErrHills = 4,      // live hill list overflow
+    kErrInternal = 8,   // a launch shape the buffers were not sized for
+};
+
+// Slots of the per-system FP64 scalar block `scal`.
+enum Scal : int {
+    kS0 = 0, kS1 = 1,            // CVs s1, s2
+    kV = 2, kDV0 = 3, kDV1 = 4,  // bias and its gradient at (s1, s2)
+    kDepV = 5, kDepDV0 = 6, kDepDV1 = 7,  // bias and gradient at the last deposit centre
+    kDepW = 8,                   // height of the last deposited hill
+    kDepC0 = 9, kDepC1 = 10,     // the last deposit centre (or a caller's CV point)
+    kNumScal = 16
+};
+
+struct Sys {
+    int n;          // atoms
+    int ncv;        // 1 or 2
+    int cn_unlike;  // CN mask
+    int max_nb;     // ELL capacity per atom
+    // box
+    double L[3];
+    float Lhi[3], Llo[3], halfL[3];
+    // cells (edge >= rc, Morton-ranked)
+    int nc[3];
+    int ncell;
+    float inv_h[3];
+    // neighbour predicate: r^2 < rc^2 decided in FP64 inside the guard band
+    double rc2;
+    float rc2_lo, rc2_hi;
+    // switch
+    int sw_n, sw_m, stretch;
+    double r0, rc;
+    float inv_r0_hi, inv_r0_lo;  // 1/r0 as a float pair
+    float a_hi, a_lo;            // 1/(1 - s_raw(rc)) (1 when not stretched)
+    float k_hi, k_lo;            // s_raw(rc)/(1 - s_raw(rc)) (0 when not stretched)
+    double a_d, k_d, inv_r0_d;
+    // per-atom state, sorted (Morton) order unless noted
+    const float4 *pos_in;  // caller order
+    float4 *pos_s;
+    int *perm;             // sorted -> caller
+    int *scell;            // cell of each sorted atom
+    int *ucell, *uslot;    // caller order: cell and slot within it
+    int *cell_count;       // [ncell]
+    int *cell_start;       // [ncell + 1]
+    int *scan_part;        // block partial sums of the cell scan
+    const int *rank_of_xyz;  // cell (x, y, z) -> Morton rank
+    const int *xyz_of_rank;  // Morton rank -> packed x | y << 10 | z << 20
+    int *nbr;              // [n][max_nb] sorted indices, row per atom: r < rc exactly;
+                           // entries j > i first (nh of them), then j < i
+    int *nn;               // [n]
+    int *nh;               // [n] entries with j > i
+    void *wl;              // real [n][max_nb]: switch weight w_ij of each entry
+    void *pairF;           // real [n][max_nb][4]: force of pair (i, j > i), slot of i's entry
+    // Verlet list (cutoff rc + skin, built at the reference positions)
+    float4 *pos_ref;       // sorted positions at the last rebuild
+    int *vnbr;             // [n][max_vnb]
+    int *vnn;              // [n]
+    int *vnh;              // [n] Verlet entries with j > i (stored first)
+    int max_vnb;
+    int *flag;             // 1: rebuild the cell order and Verlet list this step
+    float disp_thr2;       // (skin / 2)^2 with margin: rebuild above it
+    float rv2;             // (rc + skin)^2 with margin: Verlet cutoff
+    int always_rebuild;    // skin == 0
+    unsigned long long *rebuilds;  // number of rebuilds done
+    void *cn, *W, *qb6;    // real-typed per-atom scalars
+    void *q, *b, *h;       // real-typed per-atom records [n][16]: q_m; qbar_m and c; h_m
+    double *part;          // per-block FP64 partial sums, slots of part_stride
+    int part_stride;
+    unsigned *ticket;      // completion counters of the last-block reductions
+    double *scal;          // kNumScal doubles
+    int *err;
+    // hills and grid
+    double *hc;            // [cap][2]
+    double *hw;            // [cap]
+    int hill_cap;
+    double sigma[2];
+    double w0, kbdt;
+    int grid_on;
+    int gn[2];
+    double glo[2], ghi[2], gh[2];
+    double *grid;          // [gn0][gn1][4]
+};
+
+// Launch entry points (stream-ordered, no host synchronisation).
+void launch_gather_check(const Sys &s, cudaStream_t st);
+void launch_rebuild(const Sys &s, cudaStream_t st);  // kernels early-exit unless *flag
+void launch_filter(const Sys &s, cudaStream_t st);
+void launch_cv_fwd(const Sys &s, int fp64, int fused_filter, cudaStream_t st);
+void launch_cv_avg(const Sys &s, int fp64, cudaStream_t st);
+void launch_bias(const Sys &s, int K, const double *s_dev, double *out_dev, int deposit, cudaStream_t st);
+void launch_adjoint(const Sys &s, int fp64, cudaStream_t st);
+void launch_force(const Sys &s, int fp64, float *F, int accumulate, double scale, cudaStream_t st);
+int force_kernels(const Sys &s);
+void launch_grid_fold(const Sys &s, int K, cudaStream_t st);
+void launch_nn_stats(const Sys &s, unsigned long long *sum, int *mx, cudaStream_t st);
+void launch_export_pairs(const Sys &s, long long *pairs, int *count, cudaStream_t st);
+void launch_per_atom_out(const Sys &s, int fp64, double *out, cudaStream_t st);
+void set_ylm_constants(cudaStream_t st);
+
+int bias_blocks(int K);
+
+// ----------------------------------------------------------------- device math
+__device__ __forceinline__ float mi_f(float d, float halfL, float Lhi, float Llo)
+{
+    // one periodic shift, L carried as a float pair so the shift adds no
+    // systematic error
+    if (d > halfL) d = (d - Lhi) - Llo;
+    else if (d < -halfL) d = (d + Lhi) + Llo;
+    return d;
+}
+
+__device__ __forceinline__ double mi_d(double d, double L)
+{
+    if (d > 0.5 * L) d -= L;
+    else if (d < -0.5 * L) d += L;
+    return d;
+}
+
+template <typename real>
+struct Vec3 {
+    real x, y, z;
+};
+
+// Displacement r_j - r_i, minimum image, in the pair precision.
+template <typename real>
+__device__ __forceinline__ Vec3<real> displacement(const Sys &s, float4 pi, float4 pj);
+
+template <>
+__device__ __forceinline__ Vec3<float> displacement<float>(const Sys &s, float4 pi, float4 pj)
+{
+    Vec3<float> d;
+    d.x = mi_f(pj.x - pi.x, s.halfL[0], s.Lhi[0], s.Llo[0]);
+    d.y = mi_f(pj.y - pi.y, s.halfL[1], s.Lhi[1], s.Llo[1]);
+    d.z = mi_f(pj.z - pi.z, s.halfL[2], s.Lhi[2], s.Llo[2]);
+    return d;
+}
+
+template <>
+__device__ __forceinline__ Vec3<double> displacement<double>(const Sys &s, float4 pi, float4 pj)
+{
+    Vec3<double> d;
+    d.x = mi_d((double)pj.x - (double)pi.x, s.L[0]);
+    d.y = mi_d((double)pj.y - (double)pi.y, s.L[1]);
+    d.z = mi_d((double)pj.z - (double)pi.z, s.L[2]);
+    return d;
+}
+
+// 1/sqrt(v) and 1/v.  FP32: the SFU estimate refined by one Newton step
+// (a few FMAs instead of an IEEE square root and division); the residual is
+// at the level of the final rounding, with no systematic sign.  FP64: IEEE.
+template <typename real>
+__device__ __forceinline__ real rsqrt_r(real v);
+template <>
+__device__ __forceinline__ float rsqrt_r<float>(float v)
+{
+    float y = rsqrtf(v);
+    const float hv = 0.5f * v;
+    return y * fmaf(-hv * y, y, 1.5f);
+}
+template <>
+__device__ __forceinline__ double rsqrt_r<double>(double v) { return 1.0 / sqrt(v); }
+
+template <typename real>
+__device__ __forceinline__ real recip_r(real v);
+template <>
+__device__ __forceinline__ float recip_r<float>(float v)
+{
+    float y = __fdividef(1.0f, v);
+    return fmaf(y, fmaf(-v, y, 1.0f), y);
+}
+template <>
+__device__ __forceinline__ double recip_r<double>(double v) { return 1.0 / v; }
+
+// Rational switch.  For m == 2n, (1 - x^n)/(1 - x^m) = 1/(1 + x^n) has no
+// removable singularity; other (n, m) use the plain ratio with its first-order
+// expansion within 1e-6 of x = 1.  Returns w and dw/dr (stretched: shifted and
+// scaled to vanish at rc).
+template <typename real>
+__device__ __forceinline__ void switch_eval(const Sys &s, real r, real &w, real &dw);
+
+template <typename real>
+__device__ __forceinline__ real ipow(real x, int n)
+{
+    real v = real(1);
+    real b = x;
+    while (n > 0) {
+        if (n & 1) v *= b;
+        b *= b;
+        n >>= 1;
+    }
+    return v;
+}
+
+template <typename real>
+__device__ __forceinline__ void switch_raw(const Sys &s, real x, real &f, real &dfdx)
+{
+    const int n = s.sw_n, m = s.sw_m;
+    if (m == 2 * n) {
+        real xn1 = ipow<real>(x, n - 1);
+        real xn = xn1 * x;
+        real inv = recip_r<real>(real(1) + xn);
+        f = inv;
+        dfdx = -real(n) * xn1 * inv * inv;
+        return;
+    }
+    real e = x - real(1);
+    if (fabs((double)e) < 1e-6) {
+        f = (real(n) / real(m)) * (real(1) + real(0.5) * real(n - m) * e);
+        dfdx = real(n) * real(n - m) / (real(2) * real(m));
+        return;
+    }
+    real xn1 = ipow<real>(x, n - 1), xm1 = ipow<real>(x, m - 1);
+    real num = real(1) - xn1 * x, den = real(1) - xm1 * x;
+    real inv = real(1) / den;
+    f = num * inv;
+    dfdx = (-real(n) * xn1 * den + real(m) * xm1 * num) * inv * inv;
+}
+
+template <>
+__device__ __forceinline__ void switch_eval<float>(const Sys &s, float r, float &w, float &dw)
+{
+    float x = fmaf(r, s.inv_r0_hi, r * s.inv_r0_lo);
+    float f, dfdx;
+    switch_raw<float>(s, x, f, dfdx);
+    // (f - s_c) / (1 - s_c) = f*a - k with a, k carried as float pairs
+    w = (fmaf(f, s.a_hi, f * s.a_lo) - s.k_hi) - s.k_lo;
+    dw = dfdx * s.a_hi * s.inv_r0_hi;
+}
+
+template <>
+__device__ __forceinline__ void switch_eval<double>(const Sys &s, double r, double &w, double &dw)
+{
+    double x = r * s.inv_r0_d;
+    double f, dfdx;
+    switch_raw<double>(s, x, f, dfdx);
+    w = f * s.a_d - s.k_d;
+    dw = dfdx * s.a_d * s.inv_r0_d;
+}
+
+
+
+__device__ __forceinline__ void set_err(const Sys &s, int bits) { atomicOr(s.err, bits); }
+
+// ------------------------------------------------------------ lane groups
+// Per-atom kernels give one atom a group of kG lanes; lane l handles the
+// atom's neighbours l, l + kG, ... so all its neighbour loads are in flight
+// together.
+constexpr int kG = 8;
+constexpr int kAtomsPerBlock = kBlockAtoms / kG;
+
+// Grid of every lane-group kernel; the FP64 partial-sum slots are sized from
+// it, so launches and allocations can never disagree.
+__host__ __device__ inline int group_grid(int n) { return (n + kAtomsPerBlock - 1) / kAtomsPerBlock; }
+
+struct AtomLane {
+    int i;    // atom (sorted index), may be >= n for idle groups
+    int l;    // lane within the group
+    bool ok;  // i < n
+};
+
+__device__ __forceinline__ AtomLane atom_lane_at(const Sys &s, int blk)
+{
+    AtomLane a;
+    a.i = blk * kAtomsPerBlock + (threadIdx.x / kG);
+    a.l = threadIdx.x & (kG - 1);
+    a.ok = a.i < s.n;
+    return a;
+}
+
+__device__ __forceinline__ AtomLane atom_lane(const Sys &s) { return atom_lane_at(s, blockIdx.x); }
+
+__device__ __forceinline__ unsigned group_mask_bits(unsigned ballot)
+{
+    const int base = (threadIdx.x & 31) & ~(kG - 1);
+    return (ballot >> base) & ((1u << kG) - 1u);
+}
+
+// Exact FP64 pair test: r^2 = (dx*dx + dy*dy) + dz*dz < rc^2 on the
+// minimum-image displacement, no contraction.
+__device__ __forceinline__ bool pair_exact(const Sys &s, float4 pi, float4 pj)
+{
+    double dx = mi_d(__dadd_rn((double)pj.x, -(double)pi.x), s.L[0]);
+    double dy = mi_d(__dadd_rn((double)pj.y, -(double)pi.y), s.L[1]);
+    double dz = mi_d(__dadd_rn((double)pj.z, -(double)pi.z), s.L[2]);
+    double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+    r2 = __dadd_rn(r2, __dmul_rn(dz, dz));
+    return r2 < s.rc2;
+}
+
+// The float32 estimate decides every candidate outside a relative guard band
+// of 3e-5 around rc^2; inside it the FP64 definition decides.
+__device__ __forceinline__ bool pair_in(const Sys &s, float4 pi, float4 pj)
+{
+    Vec3<float> d = displacement<float>(s, pi, pj);
+    float r2 = fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z));
+    if (r2 < s.rc2_lo) return true;
+    if (r2 > s.rc2_hi) return false;
+    return pair_exact(s, pi, pj);
+}
+
+// Compact atom a.i's Verlet row into its exact row, the j > i part first (the
+// Verlet row is ordered the same way), order kept within each part.  Every
+// lane of the warp must call this (loop counts are made warp-uniform).
+__device__ __forceinline__ int filter_row(const Sys &s, const AtomLane &a)
+{
+    const int vn = a.ok ? s.vnn[a.i] : 0;
+    const int vh = a.ok ? s.vnh[a.i] : 0;
+    const float4 pi = a.ok ? s.pos_s[a.i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int *vrow = s.vnbr + (size_t)(a.ok ? a.i : 0) * s.max_vnb;
+    int *row = s.nbr + (size_t)(a.ok ? a.i : 0) * s.max_nb;
+    int cnt = 0, nh = 0;
+#pragma unroll 1
+    for (int part = 0; part < 2; ++part) {
+        const int k0 = part == 0 ? 0 : vh, k1 = part == 0 ? vh : vn;
+        const int span = k1 - k0;
+        const int smax = __reduce_max_sync(0xffffffffu, span);
+        for (int base = 0; base < smax; base += kG) {
+            const int k = k0 + base + a.l;
+            bool in = false;
+            int j = 0;
+            if (base + a.l < span) {
+                j = vrow[k];
+                in = pair_in(s, pi, s.pos_s[j]);
+            }
+            const unsigned gm = group_mask_bits(__ballot_sync(0xffffffffu, in));
+            const int at = cnt + __popc(gm & ((1u << a.l) - 1u));
+            if (in && at < s.max_nb) row[at] = j;
+            cnt += __popc(gm);
+        }
+        if (part == 0) nh = cnt;
+    }
+    if (a.ok && a.l == 0) {
+        if (cnt > s.max_nb) set_err(s, kErrCapacity);
+        s.nn[a.i] = min(cnt, s.max_nb);
+        s.nh[a.i] = min(nh, s.max_nb);
+    }
+    __syncwarp();
+    return min(cnt, s.max_nb);
+}
+
+}  // namespace metad

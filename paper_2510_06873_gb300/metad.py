@@ -1,0 +1,411 @@
+"""Thin Python binding of the C ABI in include/metad.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of its own; all work runs in the CUDA kernels of libmetad.so.
+Device buffers are torch tensors (``tensor.data_ptr()``); host outputs are
+numpy arrays.  If the library has not been built, importing this module
+raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libmetad.so")
+
+METAD_OK, METAD_ERR_INVALID, METAD_ERR_OOM, METAD_ERR_CUDA, METAD_ERR_CAPACITY, METAD_ERR_TIMEOUT, \
+    METAD_ERR_STATE = range(7)
+
+
+class metad_params(ctypes.Structure):
+    _fields_ = [
+        ("n_atoms", ctypes.c_int32), ("n_cv", ctypes.c_int32), ("box", ctypes.c_double * 3),
+        ("rc", ctypes.c_double), ("r0", ctypes.c_double), ("sw_n", ctypes.c_int32), ("sw_m", ctypes.c_int32),
+        ("stretch", ctypes.c_int32), ("cn_pairs", ctypes.c_int32), ("sigma", ctypes.c_double * 2),
+        ("w0", ctypes.c_double), ("biasfactor", ctypes.c_double), ("temperature", ctypes.c_double),
+        ("kB", ctypes.c_double), ("grid_on", ctypes.c_int32), ("grid_n", ctypes.c_int32 * 2),
+        ("hill_capacity", ctypes.c_int32), ("grid_lo", ctypes.c_double * 2), ("grid_hi", ctypes.c_double * 2),
+        ("precision", ctypes.c_int32), ("max_neighbors", ctypes.c_int32), ("device", ctypes.c_int32),
+        ("reserved", ctypes.c_int32), ("stream", ctypes.c_void_p), ("skin", ctypes.c_double),
+    ]
+
+
+class MetadError(RuntimeError):
+    def __init__(self, status, where, detail=""):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} ({status}) {detail}".rstrip())
+
+
+_lib = None
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "metad_params_default": (None, [ctypes.POINTER(metad_params)]),
+    "metad_create": (ctypes.c_int, [ctypes.POINTER(metad_params), ctypes.POINTER(ctypes.c_void_p)]),
+    "metad_destroy": (ctypes.c_int, [_P]),
+    "metad_build_neighbors": (ctypes.c_int, [_P, _P]),
+    "metad_cv_forward": (ctypes.c_int, [_P, _P, _P]),
+    "metad_bias_eval": (ctypes.c_int, [_P, _P, _P, _P]),
+    "metad_bias_forces": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_double]),
+    "metad_deposit_hill": (ctypes.c_int, [_P, _P, _P]),
+    "metad_deposit_hills": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P]),
+    "metad_load_hills": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32]),
+    "metad_get_hills": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
+    "metad_fold_hills": (ctypes.c_int, [_P]),
+    "metad_get_grid": (ctypes.c_int, [_P, _P]),
+    "metad_export_neighbors": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
+    "metad_step": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32]),
+    "metad_read_results": (ctypes.c_int, [_P, _P, _P, _P]),
+    "metad_sync": (ctypes.c_int, [_P]),
+    "metad_stream": (ctypes.c_void_p, [_P]),
+    "metad_hill_count": (ctypes.c_int32, [_P]),
+    "metad_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "metad_last_error": (ctypes.c_char_p, [_P]),
+    "metad_step_host": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P]),
+    "metad_profile_begin": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "metad_profile_end": (ctypes.c_int, [_P, _P, _P]),
+    "metad_stage_name": (ctypes.c_char_p, [ctypes.c_int32]),
+    "metad_launch_count": (ctypes.c_int64, [_P]),
+    "metad_neighbor_stats": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]),
+    "metad_rebuild_count": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
+}
+METAD_NUM_STAGES = 9
+OPTIONAL = {}
+
+
+def lib():
+    """Load libmetad.so (built in-tree by build.py); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run paper_2510_06873_gb300.build.build() first "
+                              "(the library has no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in {**_SIGS, **OPTIONAL}.items():
+            if not hasattr(L, name):
+                if name in OPTIONAL:
+                    continue
+                raise ImportError(f"{LIB_PATH} does not export {name}")
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return sorted(_SIGS)
+
+
+def status_string(s: int) -> str:
+    try:
+        return lib().metad_status_string(int(s)).decode()
+    except ImportError:
+        return str(s)
+
+
+def _check(ctx, s, where):
+    if s != METAD_OK:
+        detail = ""
+        if ctx:
+            detail = lib().metad_last_error(ctx).decode()
+        raise MetadError(s, where, detail)
+
+
+def _dptr(t):
+    """Device pointer of a torch tensor (or an int address, or None)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _hptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def metad_params_default() -> metad_params:
+    p = metad_params()
+    lib().metad_params_default(ctypes.byref(p))
+    return p
+
+
+def metad_create(p: metad_params):
+    ctx = ctypes.c_void_p()
+    s = lib().metad_create(ctypes.byref(p), ctypes.byref(ctx))
+    _check(None, s, "metad_create")
+    return ctx.value
+
+
+def metad_destroy(ctx):
+    lib().metad_destroy(ctx)
+
+
+def metad_build_neighbors(ctx, pos):
+    _check(ctx, lib().metad_build_neighbors(ctx, _dptr(pos)), "metad_build_neighbors")
+
+
+def metad_cv_forward(ctx, n_cv=None, per_atom=None, want_host=True):
+    out = np.zeros(2) if want_host else None
+    _check(ctx, lib().metad_cv_forward(ctx, _hptr(out), _dptr(per_atom)), "metad_cv_forward")
+    return None if out is None else out[: (n_cv or 2)]
+
+
+def metad_bias_eval(ctx, s=None, want_host=True):
+    sh = None if s is None else np.ascontiguousarray(np.atleast_1d(s), dtype=np.float64)
+    V = ctypes.c_double(0.0)
+    dV = np.zeros(2)
+    if want_host:
+        _check(ctx, lib().metad_bias_eval(ctx, _hptr(sh), ctypes.byref(V), _hptr(dV)), "metad_bias_eval")
+        return V.value, dV
+    _check(ctx, lib().metad_bias_eval(ctx, _hptr(sh), None, None), "metad_bias_eval")
+    return None
+
+
+def metad_bias_forces(ctx, forces, accumulate=False, scale=1.0):
+    _check(ctx, lib().metad_bias_forces(ctx, _dptr(forces), int(bool(accumulate)), float(scale)),
+           "metad_bias_forces")
+
+
+def metad_deposit_hill(ctx, center=None, want_height=True):
+    c = None if center is None else np.ascontiguousarray(np.atleast_1d(center), dtype=np.float64)
+    h = ctypes.c_double(0.0)
+    _check(ctx, lib().metad_deposit_hill(ctx, _hptr(c), ctypes.byref(h) if want_height else None),
+           "metad_deposit_hill")
+    return h.value if want_height else None
+
+
+def metad_deposit_hills(ctx, centers, want_heights=True):
+    c = np.ascontiguousarray(centers, dtype=np.float64)
+    K = c.shape[0]
+    w = np.zeros(K) if want_heights else None
+    _check(ctx, lib().metad_deposit_hills(ctx, _hptr(c), K, _hptr(w)), "metad_deposit_hills")
+    return w
+
+
+def metad_load_hills(ctx, centers, heights):
+    c = np.ascontiguousarray(centers, dtype=np.float64)
+    w = np.ascontiguousarray(heights, dtype=np.float64)
+    _check(ctx, lib().metad_load_hills(ctx, _hptr(c), _hptr(w), int(w.size)), "metad_load_hills")
+
+
+def metad_get_hills(ctx, n_cv):
+    K = ctypes.c_int32(0)
+    _check(ctx, lib().metad_get_hills(ctx, None, None, 0, ctypes.byref(K)), "metad_get_hills")
+    c = np.zeros((K.value, n_cv))
+    w = np.zeros(K.value)
+    _check(ctx, lib().metad_get_hills(ctx, _hptr(c), _hptr(w), K.value, ctypes.byref(K)), "metad_get_hills")
+    return c, w
+
+
+def metad_fold_hills(ctx):
+    _check(ctx, lib().metad_fold_hills(ctx), "metad_fold_hills")
+
+
+def metad_get_grid(ctx, shape):
+    g = np.zeros((shape[0], shape[1], 4))
+    _check(ctx, lib().metad_get_grid(ctx, _hptr(g)), "metad_get_grid")
+    return g
+
+
+def metad_export_neighbors(ctx):
+    P = ctypes.c_int64(0)
+    _check(ctx, lib().metad_export_neighbors(ctx, None, 0, ctypes.byref(P)), "metad_export_neighbors")
+    out = np.zeros((P.value, 2), dtype=np.int64)
+    _check(ctx, lib().metad_export_neighbors(ctx, _hptr(out), P.value, ctypes.byref(P)), "metad_export_neighbors")
+    return out
+
+
+def metad_step(ctx, pos, forces, accumulate=False, deposit=False):
+    _check(ctx, lib().metad_step(ctx, _dptr(pos), _dptr(forces), int(bool(accumulate)), int(bool(deposit))),
+           "metad_step")
+
+
+def metad_step_host(ctx, pos_host, forces_host, accumulate=False, deposit=False):
+    """pos_host float32 [N,4], forces_host float32 [N,3] (numpy, ideally pinned)."""
+    cv = np.zeros(2)
+    V = ctypes.c_double(0.0)
+    _check(ctx, lib().metad_step_host(ctx, _hptr(pos_host), _hptr(forces_host), int(bool(accumulate)),
+                                      int(bool(deposit)), _hptr(cv), ctypes.byref(V)), "metad_step_host")
+    return cv, V.value
+
+
+def metad_profile_begin(ctx, max_records):
+    _check(ctx, lib().metad_profile_begin(ctx, int(max_records)), "metad_profile_begin")
+
+
+def metad_profile_end(ctx):
+    ms = np.zeros(METAD_NUM_STAGES)
+    cnt = np.zeros(METAD_NUM_STAGES, dtype=np.int32)
+    _check(ctx, lib().metad_profile_end(ctx, _hptr(ms), _hptr(cnt)), "metad_profile_end")
+    return {metad_stage_name(k): (float(ms[k]), int(cnt[k])) for k in range(METAD_NUM_STAGES)}
+
+
+def metad_stage_name(k) -> str:
+    return lib().metad_stage_name(int(k)).decode()
+
+
+def metad_neighbor_stats(ctx):
+    e, mx = ctypes.c_int64(0), ctypes.c_int32(0)
+    _check(ctx, lib().metad_neighbor_stats(ctx, ctypes.byref(e), ctypes.byref(mx)), "metad_neighbor_stats")
+    return int(e.value), int(mx.value)
+
+
+def metad_rebuild_count(ctx) -> int:
+    v = ctypes.c_int64(0)
+    _check(ctx, lib().metad_rebuild_count(ctx, ctypes.byref(v)), "metad_rebuild_count")
+    return int(v.value)
+
+
+def metad_launch_count(ctx) -> int:
+    return int(lib().metad_launch_count(ctx))
+
+
+def metad_read_results(ctx):
+    cv, dV = np.zeros(2), np.zeros(2)
+    V = ctypes.c_double(0.0)
+    _check(ctx, lib().metad_read_results(ctx, _hptr(cv), ctypes.byref(V), _hptr(dV)), "metad_read_results")
+    return cv, V.value, dV
+
+
+def metad_sync(ctx):
+    _check(ctx, lib().metad_sync(ctx), "metad_sync")
+
+
+def metad_stream(ctx) -> int:
+    return int(lib().metad_stream(ctx) or 0)
+
+
+def metad_hill_count(ctx) -> int:
+    return int(lib().metad_hill_count(ctx))
+
+
+# --------------------------------------------------------------------- helper
+def params_for(n_atoms, box, n_cv=2, sigma=(0.05, 0.02), rc=3.5, r0=2.5, sw_n=6, sw_m=12, cn_unlike=True,
+               w0=1.0, biasfactor=10.0, temperature=300.0, kB=0.0083144626, grid=None, hill_capacity=65536,
+               fp64=False, max_neighbors=64, device=0, stream=None, skin=1.0) -> metad_params:
+    """metad_params from keyword values; grid = (n, lo, hi) or None."""
+    p = metad_params_default()
+    p.n_atoms = int(n_atoms)
+    p.n_cv = int(n_cv)
+    for a in range(3):
+        p.box[a] = float(box[a])
+    p.rc, p.r0, p.sw_n, p.sw_m = float(rc), float(r0), int(sw_n), int(sw_m)
+    p.cn_pairs = 1 if cn_unlike else 0
+    sig = list(sigma) + [1.0] * (2 - len(sigma))
+    p.sigma[0], p.sigma[1] = float(sig[0]), float(sig[1])
+    p.w0, p.biasfactor, p.temperature, p.kB = float(w0), float(biasfactor), float(temperature), float(kB)
+    if grid is not None:
+        gn, lo, hi = grid
+        p.grid_on = 1
+        p.grid_n[0], p.grid_n[1] = int(gn[0]), int(gn[1])
+        p.grid_lo[0], p.grid_lo[1] = float(lo[0]), float(lo[1])
+        p.grid_hi[0], p.grid_hi[1] = float(hi[0]), float(hi[1])
+    p.hill_capacity = int(hill_capacity)
+    p.precision = 1 if fp64 else 0
+    p.max_neighbors = int(max_neighbors)
+    p.device = int(device)
+    p.stream = stream
+    p.skin = float(skin)
+    return p
+
+
+class Metad:
+    """One context: owns the C handle, forwards to the metad_* calls."""
+
+    def __init__(self, params: metad_params):
+        self.params = params
+        self.n = params.n_atoms
+        self.n_cv = params.n_cv
+        self.ctx = metad_create(params)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            metad_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def build_neighbors(self, pos):
+        metad_build_neighbors(self.ctx, pos)
+
+    def cv_forward(self, per_atom=None, want_host=True):
+        out = metad_cv_forward(self.ctx, self.n_cv, per_atom, want_host)
+        return out
+
+    def bias_eval(self, s=None, want_host=True):
+        r = metad_bias_eval(self.ctx, s, want_host)
+        if r is None:
+            return None
+        return r[0], r[1][: self.n_cv]
+
+    def bias_forces(self, forces, accumulate=False, scale=1.0):
+        metad_bias_forces(self.ctx, forces, accumulate, scale)
+
+    def deposit_hill(self, center=None, want_height=True):
+        return metad_deposit_hill(self.ctx, center, want_height)
+
+    def deposit_hills(self, centers, want_heights=True):
+        return metad_deposit_hills(self.ctx, centers, want_heights)
+
+    def load_hills(self, centers, heights):
+        metad_load_hills(self.ctx, centers, heights)
+
+    def get_hills(self):
+        return metad_get_hills(self.ctx, self.n_cv)
+
+    def fold_hills(self):
+        metad_fold_hills(self.ctx)
+
+    def get_grid(self):
+        return metad_get_grid(self.ctx, (self.params.grid_n[0], self.params.grid_n[1]))
+
+    def export_neighbors(self):
+        return metad_export_neighbors(self.ctx)
+
+    def step(self, pos, forces, accumulate=False, deposit=False):
+        metad_step(self.ctx, pos, forces, accumulate, deposit)
+
+    def read_results(self):
+        cv, V, dV = metad_read_results(self.ctx)
+        return cv[: self.n_cv], V, dV[: self.n_cv]
+
+    def sync(self):
+        metad_sync(self.ctx)
+
+    def step_host(self, pos_host, forces_host, accumulate=False, deposit=False):
+        cv, V = metad_step_host(self.ctx, pos_host, forces_host, accumulate, deposit)
+        return cv[: self.n_cv], V
+
+    def profile_begin(self, max_records):
+        metad_profile_begin(self.ctx, max_records)
+
+    def profile_end(self):
+        return metad_profile_end(self.ctx)
+
+    def neighbor_stats(self):
+        return metad_neighbor_stats(self.ctx)
+
+    @property
+    def rebuild_count(self) -> int:
+        return metad_rebuild_count(self.ctx)
+
+    @property
+    def launch_count(self) -> int:
+        return metad_launch_count(self.ctx)
+
+    @property
+    def stream(self) -> int:
+        return metad_stream(self.ctx)
+
+    @property
+    def hill_count(self) -> int:
+        return metad_hill_count(self.ctx)

@@ -172,9 +172,10 @@ def wurtzite_cell(a: float, c: float, u: float):
 def wurtzite_liquid_system(n: int, cfg: int, sys: int, density_scale: float = 1.0,
                            lattice_noise: float = 0.1, liquid_dmin: float = 2.0,
                            liquid_density: float = LIQUID_DENSITY) -> System:
-    """Half wurtzite-like lattice with N(0, noise) displacements (x < Lx/2),
-    half RSA liquid (x >= Lx/2, min distance dmin to every atom); exactly n
-    atoms.  A density_scale j rescales every length by j**(-1/3)."""
+    """Wurtzite-like lattice slab with N(0, noise) displacements (about half
+    the box, x < half*a) and an RSA liquid slab at liquid_density beside it
+    (min distance dmin to every atom, lattice included); exactly n atoms.  A
+    density_scale j rescales every length by j**(-1/3)."""
     lf = density_scale ** (-1.0 / 3.0)
     a, c = WURTZITE_A * lf, WURTZITE_C * lf
     noise = lattice_noise * lf
@@ -183,11 +184,17 @@ def wurtzite_liquid_system(n: int, cfg: int, sys: int, density_scale: float = 1.
     frac, spec, dims = wurtzite_cell(a, c, WURTZITE_U)
     rho_lat = 8.0 / float(np.prod(dims))
     L = (n / (0.5 * (rho_lat + rho_liq))) ** (1.0 / 3.0)
-    nx = max(2, 2 * int(round(L / (2 * dims[0]))))
+    half = max(1, int(round(L / (2 * dims[0]))))
     ny = max(1, int(round(L / dims[1])))
     nz = max(1, int(round(L / dims[2])))
-    box = np.array([nx * dims[0], ny * dims[1], nz * dims[2]], dtype=np.float64)
-    half = nx // 2
+    while half > 1 and 8 * half * ny * nz >= n:
+        half -= 1
+    n_lat0 = 8 * half * ny * nz
+    if n_lat0 >= n:
+        raise ValueError(f"{n} atoms is too few for a lattice slab")
+    # the liquid slab is as wide as its atom count needs at density rho_liq
+    lx_liq = (n - n_lat0) / (rho_liq * ny * dims[1] * nz * dims[2])
+    box = np.array([half * dims[0] + lx_liq, ny * dims[1], nz * dims[2]], dtype=np.float64)
     ix, iy, iz = np.meshgrid(np.arange(half), np.arange(ny), np.arange(nz), indexing="ij")
     cells = np.stack([ix.ravel(), iy.ravel(), iz.ravel()], axis=1).astype(np.float64)
     lat = ((cells[:, None, :] + frac[None, :, :]) * dims[None, None, :]).reshape(-1, 3)
@@ -200,7 +207,7 @@ def wurtzite_liquid_system(n: int, cfg: int, sys: int, density_scale: float = 1.
     g_noise = np.random.Generator(np.random.PCG64(ss[0]))
     lat = wrap_to_box(lat + g_noise.normal(0.0, noise, size=lat.shape), box)
     seed = int(ss[1].generate_state(1, dtype=np.uint64)[0])
-    liq = rsa_fill(lat, n_liq, box, 0.5 * box[0], box[0], dmin, seed)
+    liq = rsa_fill(lat, n_liq, box, half * dims[0], box[0], dmin, seed)
     liq_spec = np.zeros(n_liq, dtype=np.float32)
     liq_spec[n_liq // 2:] = 1.0
     liq_spec = np.random.Generator(np.random.PCG64(ss[2])).permutation(liq_spec)
@@ -210,8 +217,8 @@ def wurtzite_liquid_system(n: int, cfg: int, sys: int, density_scale: float = 1.
     base = np.concatenate([xyz[order], species[order, None]], axis=1).astype(np.float32)
     return System(base=np.ascontiguousarray(base), box=box, cfg=cfg, sys=sys,
                   info={"kind": "wurtzite_liquid", "n_lattice": int(n_lat), "n_liquid": int(n_liq),
-                        "liquid_density": n_liq / (0.5 * float(np.prod(box))),
-                        "density_scale": density_scale, "cells": [nx, ny, nz]})
+                        "liquid_density": n_liq / ((box[0] - half * dims[0]) * box[1] * box[2]),
+                        "density_scale": density_scale, "cells": [half, ny, nz]})
 
 
 def perturbed_frame(system: System, frame: int, sigma: float = 0.05) -> np.ndarray:
@@ -263,7 +270,7 @@ def config1_system() -> System:
 
 
 def wurtzite_system(n: int, cfg: int, sys: int = 0, density_scale: float = 1.0) -> System:
-    return _cached(f"wl-v1-{n}-{cfg}-{sys}-{density_scale!r}",
+    return _cached(f"wl-v2-{n}-{cfg}-{sys}-{density_scale!r}",
                    lambda: wurtzite_liquid_system(n, cfg, sys, density_scale=density_scale))
 
 

@@ -1,0 +1,89 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+include/metad.h declares.  No compute call is made: these run without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def metad():
+    from paper_2510_06873_gb300 import build
+    build.build()
+    from paper_2510_06873_gb300 import metad as m
+    m.lib()
+    return m
+
+
+def declared_functions():
+    names = set()
+    for hdr in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not hdr.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", hdr)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(metad_\w+)\s*\(", text))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(metad):
+    names = declared_functions()
+    assert len(names) >= 20
+    lib = metad.lib()
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    unbound = [n for n in names if n not in metad._SIGS]
+    assert not unbound, unbound
+
+
+def test_params_struct_round_trips(metad):
+    p = metad.metad_params_default()
+    assert ctypes.sizeof(metad.metad_params) == 192
+    assert (p.n_atoms, p.n_cv, p.sw_n, p.sw_m, p.stretch, p.cn_pairs) == (1, 2, 6, 12, 1, 1)
+    assert (p.rc, p.r0, p.w0, p.biasfactor, p.temperature) == (3.5, 2.5, 1.0, 10.0, 300.0)
+    assert list(p.sigma) == [0.05, 0.02] and p.kB == 0.0083144626
+    assert p.hill_capacity == 65536 and p.max_neighbors == 64 and list(p.grid_n) == [200, 200]
+    assert p.skin == 1.0
+
+
+@pytest.mark.parametrize("field,value", [("n_atoms", 0), ("n_cv", 3), ("box", 6.9), ("sigma", 0.0),
+                                         ("biasfactor", 1.0), ("precision", 2), ("sw_m", 6),
+                                         ("hill_capacity", 0), ("max_neighbors", -1),
+                                         ("skin", -0.5)])
+def test_invalid_params_rejected_before_any_device_call(metad, field, value):
+    p = metad.metad_params_default()
+    p.n_atoms = 100
+    if field == "box":
+        p.box[0] = value
+    elif field == "sigma":
+        p.sigma[0] = value
+    else:
+        setattr(p, field, value)
+    with pytest.raises(metad.MetadError) as e:
+        metad.metad_create(p)
+    assert e.value.status == metad.METAD_ERR_INVALID
+
+
+def test_grid_needs_two_cvs(metad):
+    p = metad.params_for(10, [10, 10, 10], n_cv=1, sigma=(0.05,), grid=((200, 200), (0, 0), (1, 1)))
+    with pytest.raises(metad.MetadError) as e:
+        metad.metad_create(p)
+    assert e.value.status == metad.METAD_ERR_INVALID
+
+
+def test_status_strings_and_stage_names(metad):
+    assert metad.status_string(0) == "ok"
+    assert metad.status_string(4) == "capacity exceeded"
+    assert [metad.metad_stage_name(k) for k in range(metad.METAD_NUM_STAGES)][6] == "force"
+    assert metad.lib().metad_destroy(None) == 0
+
+
+def test_package_import_does_not_load_oracle():
+    import subprocess
+    import sys
+    code = ("import sys; import paper_2510_06873_gb300.metad as m; m.lib(); "
+            "assert 'oracle' not in sys.modules, 'oracle imported by the library path'")
+    subprocess.check_call([sys.executable, "-c", code], cwd=ROOT)

@@ -1,0 +1,382 @@
+"""CUDA path against the FP64 oracle, through the C ABI (libmetad.so).
+
+Neighbour sets must match bit for bit (as sorted pair lists); CVs, bias,
+bias gradient and forces within the tolerances of parity_util.  Sizes span
+several thread blocks with ragged tails; the 1M-atom case runs the launch
+configuration the benchmark times.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from parity_util import check_bias, check_cv, check_forces, force_errors, kbdt, setup_hills
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RC = 3.5
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_06873_gb300 import build
+    build.build()
+    d = torch.device("cuda:0")
+    # a non-default stream shared by torch's copies and the library's kernels
+    torch.cuda.set_stream(torch.cuda.Stream(d))
+    return d
+
+
+def _metad():
+    from paper_2510_06873_gb300 import metad
+    return metad
+
+
+def make_ctx(dev, system, mp, fp64=False, grid=None, hill_capacity=65536, max_nb=64, cn_unlike=True,
+             sw=(6, 12), skin=1.0):
+    metad = _metad()
+    params = metad.params_for(system.n if hasattr(system, "n") else system[0], system.box, n_cv=mp.n_cv,
+                              sigma=mp.sigma, fp64=fp64, grid=grid, hill_capacity=hill_capacity,
+                              max_neighbors=max_nb, cn_unlike=cn_unlike, sw_n=sw[0], sw_m=sw[1],
+                              stream=torch.cuda.current_stream(dev).cuda_stream, skin=skin)
+    return metad.Metad(params)
+
+
+def gpu_step(ctx, dev, frame, per_atom=False):
+    pos = torch.from_numpy(np.ascontiguousarray(frame)).to(dev)
+    F = torch.zeros((frame.shape[0], 3), dtype=torch.float32, device=dev)
+    ctx.build_neighbors(pos)
+    pa = torch.zeros((2, frame.shape[0]), dtype=torch.float64, device=dev) if per_atom else None
+    s = ctx.cv_forward(per_atom=pa)
+    V, dV = ctx.bias_eval()
+    ctx.bias_forces(F)
+    ctx.sync()
+    out = {"s": s, "V": V, "dV": dV, "F": F.cpu().numpy().astype(np.float64)}
+    if per_atom:
+        out["per_atom"] = pa.cpu().numpy()
+    return out
+
+
+class _Sys:
+    def __init__(self, pos, box):
+        self.base = pos
+        self.box = np.asarray(box, dtype=np.float64)
+        self.n = pos.shape[0]
+        self.sys = 0
+
+
+# ------------------------------------------------------------------ neighbours
+@pytest.mark.parametrize("lfac", [2.0, 2.2, 2.5, 3.0, 3.2, 4.0, 6.1])
+def test_neighbours_bit_exact_small_boxes(dev, lfac):
+    g = np.random.default_rng(int(lfac * 100))
+    box = np.array([lfac * RC, (lfac + 0.37) * RC, (lfac + 0.71) * RC])
+    n = 200 + int(lfac * 37)
+    xyz = g.uniform(0.0, 1.0, (n, 3)) * box
+    pos = np.zeros((n, 4), np.float32)
+    pos[:, :3] = synth.wrap_to_box(xyz, box)
+    pos[:, 3] = (np.arange(n) % 2).astype(np.float32)
+    s = _Sys(pos, box)
+    mp = synth.MethodParams(n_cv=1, sigma=(0.05,))
+    ctx = make_ctx(dev, s, mp, max_nb=128)
+    ctx.build_neighbors(torch.from_numpy(pos).to(dev))
+    got = ctx.export_neighbors()
+    ref = oracle.pairs_brute(pos, box, RC)
+    assert np.array_equal(got, ref)
+
+
+def test_neighbours_guard_band_exact(dev):
+    """Pairs placed within a few ulps of rc: the float32 estimate alone
+    would misclassify some; the FP64 decision must match the definition."""
+    g = np.random.default_rng(7)
+    box = np.array([30.0, 30.0, 30.0])
+    n = 400
+    a = g.uniform(1.0, 28.0, (n // 2, 3))
+    u = g.normal(size=(n // 2, 3))
+    u /= np.linalg.norm(u, axis=1)[:, None]
+    b = a + u * RC * (1.0 + g.uniform(-3e-7, 3e-7, (n // 2, 1)))
+    xyz = np.concatenate([a, b])
+    pos = np.zeros((n, 4), np.float32)
+    pos[:, :3] = synth.wrap_to_box(xyz, box)
+    s = _Sys(pos, box)
+    ctx = make_ctx(dev, s, synth.MethodParams(n_cv=1, sigma=(0.05,)), max_nb=128)
+    ctx.build_neighbors(torch.from_numpy(pos).to(dev))
+    ref = oracle.pairs_brute(pos, box, RC)
+    assert np.array_equal(ctx.export_neighbors(), ref)
+
+
+@pytest.mark.parametrize("which", ["cfg1", "cfg2"])
+def test_neighbours_bit_exact_configs(dev, which):
+    system = synth.config1_system() if which == "cfg1" else synth.config2_system()
+    frame = synth.perturbed_frame(system, 3)
+    ctx = make_ctx(dev, system, synth.MethodParams(n_cv=1, sigma=(0.05,)))
+    ctx.build_neighbors(torch.from_numpy(frame).to(dev))
+    assert np.array_equal(ctx.export_neighbors(), oracle.pairs_cells(frame, system.box, RC))
+
+
+@pytest.mark.parametrize("skin", [0.0, 1.0])
+def test_verlet_reuse_and_rebuild_stay_exact(dev, skin):
+    """Frames within skin/2 of the last rebuild reuse the cell order and the
+    Verlet rows; a larger move forces a rebuild; every exact row set equals
+    the definition's."""
+    system = synth.wurtzite_system(20000, cfg=95)
+    ctx = make_ctx(dev, system, synth.MethodParams(n_cv=1, sigma=(0.05,)), skin=skin)
+    frames = [synth.perturbed_frame(system, f) for f in range(3)]
+    moved = frames[2].copy()
+    moved[123, 0] = np.float32((float(moved[123, 0]) + 0.8) % system.box[0])  # > skin/2 from frame 0
+    far = synth.perturbed_frame(system, 7, sigma=0.4)
+    expect_rebuilds = [1, 1, 1, 2, 3] if skin > 0 else [1, 2, 3, 4, 5]
+    for k, fr in enumerate(frames + [moved, far]):
+        ctx.build_neighbors(torch.from_numpy(fr).to(dev))
+        assert np.array_equal(ctx.export_neighbors(), oracle.pairs_cells(fr, system.box, RC)), k
+        assert ctx.rebuild_count == expect_rebuilds[k], (k, ctx.rebuild_count)
+
+
+# ------------------------------------------------------------------ config 1 (FP64)
+def test_config1_fp64_frames(dev):
+    system = synth.config1_system()
+    mp = synth.method_params(1)
+    c, s_ref = setup_hills(system, mp, 200, cfg=1)
+    ctx = make_ctx(dev, system, mp, fp64=True)
+    w_gpu = ctx.deposit_hills(c)
+    w_ref = oracle.deposit_sequence(c, mp.sigma, mp.w0, kbdt(mp))
+    assert np.allclose(w_gpu, w_ref, rtol=1e-13, atol=0)
+    p = oracle.params_from(mp, system.box)
+    for f in (0, 1, 57, 99):
+        frame = synth.perturbed_frame(system, f)
+        got = gpu_step(ctx, dev, frame, per_atom=True)
+        ref = oracle.step(frame, p, c, w_ref, mp.sigma)
+        check_cv(got["s"], ref["s"], tol=1e-12)
+        check_bias(got["V"], got["dV"], ref["V"], ref["dV"], mp, tol=1e-12)
+        # FP64 pairs, float32 force output: float32 rounding only
+        check_forces(got["F"], ref["F"], tol=2e-7)
+        _, cn, _ = oracle.cv(frame, p)
+        assert np.allclose(got["per_atom"][0], cn, rtol=1e-12, atol=1e-14)
+
+
+# ------------------------------------------------------------------ config 2 (FP32 pairs)
+def test_config2_frames(dev):
+    system = synth.config2_system()
+    mp = synth.method_params(2)
+    c, s_ref = setup_hills(system, mp, 5000, cfg=2)
+    ctx = make_ctx(dev, system, mp)
+    w_gpu = ctx.deposit_hills(c)
+    w_ref = oracle.deposit_sequence(c, mp.sigma, mp.w0, kbdt(mp))
+    assert np.allclose(w_gpu, w_ref, rtol=1e-12, atol=0)
+    p = oracle.params_from(mp, system.box)
+    for f in (0, 41, 99):
+        frame = synth.perturbed_frame(system, f)
+        got = gpu_step(ctx, dev, frame, per_atom=True)
+        ref = oracle.step(frame, p, c, w_ref, mp.sigma)
+        check_cv(got["s"], ref["s"])
+        check_bias(got["V"], got["dV"], ref["V"], ref["dV"], mp)
+        check_forces(got["F"], ref["F"])
+        _, cn, q6 = oracle.cv(frame, p)
+        assert np.max(np.abs(got["per_atom"][0] - cn)) <= 1e-5 * np.max(cn)
+        assert np.max(np.abs(got["per_atom"][1] - q6)) <= 1e-5 * np.max(q6)
+
+
+# ------------------------------------------------------------------ config 3 (1M, grid)
+@pytest.mark.slow
+def test_config3_grid_deposit_and_frames(dev):
+    system = synth.config3_system()
+    mp = synth.method_params(3)
+    cfgp = synth.CONFIG_PARAMS[3]
+    K1, K2 = cfgp["hills_folded"], cfgp["hills"]
+    cen, s_ref = setup_hills(system, mp, K1 + K2, cfg=3)
+    sig = np.asarray(mp.sigma)
+    lo, hi = s_ref - 16 * sig, s_ref + 16 * sig
+    # oracle: deposit, fold, deposit again
+    w1 = oracle.deposit_sequence(cen[:K1], mp.sigma, mp.w0, kbdt(mp))
+    G = oracle.HillGrid(cfgp["grid_n"], lo, hi)
+    G.fold(cen[:K1], w1, mp.sigma)
+    w2 = oracle.deposit_sequence(cen[K1:], mp.sigma, mp.w0, kbdt(mp), grid=G)
+    # GPU
+    ctx = make_ctx(dev, system, mp, grid=(cfgp["grid_n"], lo, hi))
+    g1 = ctx.deposit_hills(cen[:K1])
+    assert np.allclose(g1, w1, rtol=1e-12, atol=0)
+    ctx.fold_hills()
+    grid = ctx.get_grid()
+    assert np.allclose(grid, G.data, rtol=1e-11, atol=1e-12 * np.max(np.abs(G.data)))
+    g2 = ctx.deposit_hills(cen[K1:])
+    assert np.allclose(g2, w2, rtol=1e-11, atol=0)
+    p = oracle.params_from(mp, system.box)
+    live_c, live_w = cen[K1:].copy(), w2.copy()
+    for f in (0, 499):
+        frame = synth.perturbed_frame(system, f)
+        got = gpu_step(ctx, dev, frame)
+        ref = oracle.step(frame, p, live_c, live_w, mp.sigma, grid=G)
+        # error budget: CV rounding (through dV/ds) versus pair arithmetic (the
+        # oracle's forces at the GPU's dV/ds)
+        F_at_gpu_dv, _ = oracle.forces(frame, p, got["dV"])
+        print(f"frame {f}: ds/s {(got['s'] - ref['s']) / ref['s']}, V {got['V']} vs {ref['V']}, "
+              f"dV {got['dV']} vs {ref['dV']}, F err {force_errors(got['F'], ref['F'])}, "
+              f"F err at GPU dV {force_errors(got['F'], F_at_gpu_dv)}")
+        check_forces(got["F"], F_at_gpu_dv)
+        check_cv(got["s"], ref["s"])
+        check_bias(got["V"], got["dV"], ref["V"], ref["dV"], mp)
+        check_forces(got["F"], ref["F"])
+        if (f + 1) % cfgp["deposit_every"] == 0:
+            h = ctx.deposit_hill()
+            href = oracle.deposit_sequence(np.vstack([live_c, got["s"][None, :]]), mp.sigma, mp.w0, kbdt(mp),
+                                           grid=G, heights_prefix=live_w)[-1]
+            assert h == pytest.approx(href, rel=1e-11)
+            live_c = np.vstack([live_c, got["s"][None, :]])
+            live_w = np.append(live_w, h)
+    assert ctx.hill_count == K2 + 1
+
+
+# ------------------------------------------------------------------ variants and edges
+@pytest.mark.parametrize("n", [1, 2, 129, 1023, 4097])
+def test_ragged_and_tiny_systems(dev, n):
+    box = np.array([9.0, 9.5, 10.0]) * max(1.0, (n / 60.0) ** (1 / 3))
+    if n <= 2:
+        box = np.array([12.0, 12.0, 12.0])
+        xyz = np.array([[1.0, 2.0, 3.0], [3.25, 2.5, 3.75]])[:n]
+    else:
+        g = np.random.default_rng(n)
+        xyz = synth.rsa_fill(np.zeros((0, 3), np.float32), n, box, 0.0, box[0], 1.7, int(g.integers(1 << 62)))
+    pos = np.zeros((n, 4), np.float32)
+    pos[:, :3] = xyz
+    pos[:, 3] = (np.arange(n) % 2).astype(np.float32)
+    s = _Sys(pos, box)
+    mp = synth.MethodParams(n_cv=2)
+    p = oracle.params_from(mp, box)
+    s0, _, _ = oracle.cv(pos, p)
+    c = s0[None, :] + np.random.default_rng(1).normal(size=(20, 2)) * np.asarray(mp.sigma)
+    ctx = make_ctx(dev, s, mp)
+    w = ctx.deposit_hills(c)
+    ref = oracle.step(pos, p, c, w, mp.sigma)
+    got = gpu_step(ctx, dev, pos)
+    if n == 1:
+        assert np.all(got["s"] == 0.0) and np.all(got["F"] == 0.0)
+        return
+    check_cv(got["s"], ref["s"])
+    check_bias(got["V"], got["dV"], ref["V"], ref["dV"], mp)
+    check_forces(got["F"], ref["F"])
+
+
+def test_isolated_atoms_have_zero_cv_and_force(dev):
+    box = np.array([40.0, 40.0, 40.0])
+    xyz = np.array([[5, 5, 5], [20, 20, 20], [33, 5, 20], [34.0, 6.0, 21.0], [10, 30, 30]], np.float64)
+    pos = np.zeros((5, 4), np.float32)
+    pos[:, :3] = xyz
+    pos[:, 3] = [0, 1, 0, 1, 1]
+    mp = synth.MethodParams(n_cv=2)
+    p = oracle.params_from(mp, box)
+    ctx = make_ctx(dev, _Sys(pos, box), mp)
+    c = np.array([[0.2, 0.1], [0.25, 0.12]])
+    w = ctx.deposit_hills(c)
+    got = gpu_step(ctx, dev, pos, per_atom=True)
+    ref = oracle.step(pos, p, c, w, mp.sigma)
+    check_cv(got["s"], ref["s"])
+    check_forces(got["F"], ref["F"])
+    for k in (0, 1, 4):
+        assert got["per_atom"][0][k] == 0.0 and got["per_atom"][1][k] == 0.0
+        assert np.all(got["F"][k] == 0.0)
+
+
+@pytest.mark.parametrize("variant", ["all_pairs", "switch_6_10", "unstretched_n1"])
+def test_switch_and_mask_variants(dev, variant):
+    system = synth.wurtzite_system(6000, cfg=91)
+    frame = synth.perturbed_frame(system, 0)
+    unlike, sw, ncv = True, (6, 12), 2
+    if variant == "all_pairs":
+        unlike = False
+    elif variant == "switch_6_10":
+        sw = (6, 10)
+    else:
+        ncv = 1
+    mp = synth.MethodParams(n_cv=ncv, sigma=(0.05, 0.02)[:ncv], cn_unlike_only=unlike, sw_n=sw[0], sw_m=sw[1])
+    p = oracle.make_params(system.box, mp.rc, mp.r0, sw[0], sw[1], True, unlike, ncv)
+    s0, _, _ = oracle.cv(system.base, p)
+    c = synth.hill_centres(91, 0, s0, mp.sigma, 300)
+    ctx = make_ctx(dev, system, mp, cn_unlike=unlike, sw=sw)
+    w = ctx.deposit_hills(c)
+    got = gpu_step(ctx, dev, frame)
+    ref = oracle.step(frame, p, c, w, mp.sigma)
+    check_cv(got["s"], ref["s"])
+    check_bias(got["V"], got["dV"], ref["V"], ref["dV"], mp)
+    check_forces(got["F"], ref["F"])
+
+
+def test_accumulate_scale_and_determinism(dev):
+    system = synth.wurtzite_system(5000, cfg=92)
+    frame = synth.perturbed_frame(system, 2)
+    mp = synth.MethodParams(n_cv=2)
+    p = oracle.params_from(mp, system.box)
+    s0, _, _ = oracle.cv(system.base, p)
+    c = synth.hill_centres(92, 0, s0, mp.sigma, 200)
+    ctx = make_ctx(dev, system, mp)
+    ctx.deposit_hills(c)
+    pos = torch.from_numpy(frame).to(dev)
+    F1 = torch.zeros((system.n, 3), dtype=torch.float32, device=dev)
+    F2 = torch.zeros_like(F1)
+    ctx.step(pos, F1)
+    ctx.step(pos, F2)
+    ctx.sync()
+    assert torch.equal(F1, F2)
+    base = torch.full_like(F1, 0.25)
+    ctx.build_neighbors(pos)
+    ctx.cv_forward(want_host=False)
+    ctx.bias_eval(want_host=False)
+    ctx.bias_forces(base, accumulate=True, scale=-2.0)
+    ctx.sync()
+    assert torch.allclose(base, 0.25 - 2.0 * F1, rtol=1e-6, atol=1e-9)
+
+
+def test_call_order_and_capacity_errors(dev):
+    metad = _metad()
+    system = synth.wurtzite_system(3000, cfg=93)
+    frame = synth.perturbed_frame(system, 0)
+    mp = synth.MethodParams(n_cv=2)
+    ctx = make_ctx(dev, system, mp)
+    F = torch.zeros((system.n, 3), dtype=torch.float32, device=dev)
+    with pytest.raises(metad.MetadError) as e:
+        ctx.cv_forward()
+    assert e.value.status == metad.METAD_ERR_STATE
+    with pytest.raises(metad.MetadError) as e:
+        ctx.bias_forces(F)
+    assert e.value.status == metad.METAD_ERR_STATE
+    small = make_ctx(dev, system, mp, max_nb=4)
+    small.build_neighbors(torch.from_numpy(frame).to(dev))
+    with pytest.raises(metad.MetadError) as e:
+        small.sync()
+    assert e.value.status == metad.METAD_ERR_CAPACITY
+    with pytest.raises(metad.MetadError) as e:
+        small.build_neighbors(torch.from_numpy(frame).to(dev))
+    assert e.value.status == metad.METAD_ERR_STATE
+    full = make_ctx(dev, system, mp, hill_capacity=3)
+    full.deposit_hills(np.zeros((3, 2)))
+    with pytest.raises(metad.MetadError) as e:
+        full.deposit_hill(np.zeros(2))
+    assert e.value.status == metad.METAD_ERR_CAPACITY
+
+
+def test_non_finite_position_reported(dev):
+    metad = _metad()
+    system = synth.wurtzite_system(3000, cfg=93)
+    frame = synth.perturbed_frame(system, 0)
+    frame[17, 1] = np.nan
+    ctx = make_ctx(dev, system, synth.MethodParams(n_cv=2))
+    ctx.build_neighbors(torch.from_numpy(frame).to(dev))
+    with pytest.raises(metad.MetadError) as e:
+        ctx.sync()
+    assert e.value.status == metad.METAD_ERR_INVALID
+
+
+def test_unwrapped_positions_are_wrapped(dev):
+    system = synth.wurtzite_system(4000, cfg=94)
+    frame = synth.perturbed_frame(system, 0)
+    shifted = frame.copy()
+    k = np.arange(system.n) % 3 == 0
+    # whole-box shifts are exact in float32 for these magnitudes only when the
+    # FP64 wrap reproduces the original coordinate; compare neighbour sets
+    shifted[k, 0] = (frame[k, 0].astype(np.float64) + system.box[0]).astype(np.float32)
+    wrapped = frame.copy()
+    wrapped[:, :3] = synth.wrap_to_box(shifted[:, :3].astype(np.float64), system.box)
+    ctx = make_ctx(dev, system, synth.MethodParams(n_cv=1, sigma=(0.05,)))
+    ctx.build_neighbors(torch.from_numpy(shifted).to(dev))
+    assert np.array_equal(ctx.export_neighbors(), oracle.pairs_cells(wrapped, system.box, RC))
