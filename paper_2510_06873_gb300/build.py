@@ -43,6 +43,7 @@ def _stale(obj, srcs):
 
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     """Compile every .cu file and link libmetad.so; returns its path."""
+    extra_flags = list(extra_flags) + os.environ.get("METAD_NVCC_FLAGS", "").split()
     os.makedirs(OUT_DIR, exist_ok=True)
     os.makedirs(BUILD_DIR, exist_ok=True)
     cc = nvcc()

@@ -105,11 +105,13 @@ metad_status dalloc(metad_ctx *c, T **ptr, size_t count)
     return METAD_OK;
 }
 
+// s_raw(x) = S_n(x) / S_m(x), S_k = 1 + x + ... + x^(k-1) (the device form).
 double switch_raw_host(double x, int n, int m)
 {
-    if (m == 2 * n) return 1.0 / (1.0 + std::pow(x, n));
-    if (std::fabs(x - 1.0) < 1e-6) return ((double)n / m) * (1.0 + 0.5 * (n - m) * (x - 1.0));
-    return (1.0 - std::pow(x, n)) / (1.0 - std::pow(x, m));
+    double sn = 0.0, sm = 0.0;
+    for (int t = n - 1; t >= 0; --t) sn = sn * x + 1.0;
+    for (int t = m - 1; t >= 0; --t) sm = sm * x + 1.0;
+    return sn / sm;
 }
 
 void split(double v, float &hi, float &lo)
@@ -419,6 +421,7 @@ metad_status metad_create(const metad_params *p, metad_ctx **out)
         }
     }
     metad::set_ylm_constants(c->stream);
+    metad::configure_kernels();
     s = cuda_check(c, cudaStreamSynchronize(c->stream), "create");
     if (s != METAD_OK) { metad_destroy(c); return s; }
     *out = c;

@@ -352,9 +352,8 @@ __device__ __forceinline__ const int *nbr_row(const Sys &s, int i) { return s.nb
 // a4: CN_i, W_i and q_m(i) = sum_j w_ij Y_m(rhat_ij) / W_i.
 // With kFilter the exact row is first compacted from the Verlet row.
 template <typename real, bool kFilter>
-__global__ void __launch_bounds__(kBlockAtoms) k_cv_fwd(Sys s)
+__device__ __forceinline__ double cv_fwd_group(const Sys &s, const AtomLane a)
 {
-    const AtomLane a = atom_lane(s);
     int nn_f = 0;
     if (kFilter) nn_f = filter_row(s, a);
     real v[kRec];  // 0..12: sum w Y_m ; 13: W ; 14: CN
@@ -399,15 +398,24 @@ __global__ void __launch_bounds__(kBlockAtoms) k_cv_fwd(Sys s)
             store_pair<real>(R<real>(s.q), a.i, a.l, q0, q1);
         }
     }
-    last_block_reduce(s, cn_out, 0, s.scal + kS0, 1.0 / s.n);
+    return cn_out;
+}
+
+template <typename real, bool kFilter>
+__global__ void __launch_bounds__(kBlockAtoms) k_cv_fwd(Sys s)
+{
+    double acc = 0.0;
+    int b0, b1;
+    group_chunk(s.n, b0, b1);
+    for (int blk = b0; blk < b1; blk += gridDim.x) acc += cv_fwd_group<real, kFilter>(s, atom_lane_at(s, blk));
+    last_block_reduce(s, acc, 0, s.scal + kS0, 1.0 / s.n);
 }
 
 // a5: qbar_m(i), qbar6(i), s2.  Record qb: qbar_m (0..12) and
 // c_i = 1 / (N qbar6 (1 + W_i)) (13), so b_m(i) = c_i K_m qbar_m(i).
 template <typename real>
-__global__ void __launch_bounds__(kBlockAtoms) k_cv_avg(Sys s)
+__device__ __forceinline__ double cv_avg_group(const Sys &s, const AtomLane a)
 {
-    const AtomLane a = atom_lane(s);
     const real *q = R<real>(s.q);
     real v[kRec];
 #pragma unroll
@@ -448,14 +456,23 @@ __global__ void __launch_bounds__(kBlockAtoms) k_cv_avg(Sys s)
             q6_out = (double)qb6;
         }
     }
-    last_block_reduce(s, q6_out, 1, s.scal + kS1, 1.0 / s.n);
+    return q6_out;
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kBlockAtoms) k_cv_avg(Sys s)
+{
+    double acc = 0.0;
+    int b0, b1;
+    group_chunk(s.n, b0, b1);
+    for (int blk = b0; blk < b1; blk += gridDim.x) acc += cv_avg_group<real>(s, atom_lane_at(s, blk));
+    last_block_reduce(s, acc, 1, s.scal + kS1, 1.0 / s.n);
 }
 
 // a7: g_m(k) = K_m (c_k qbar_m(k) + sum_i w_ik c_i qbar_m(i)) ; h = g / W.
 template <typename real>
-__global__ void __launch_bounds__(kBlockAtoms) k_adjoint(Sys s)
+__device__ __forceinline__ void adjoint_group(const Sys &s, const AtomLane a)
 {
-    const AtomLane a = atom_lane(s);
     const real *qb = R<real>(s.b);
     real v[kRec];
 #pragma unroll
@@ -488,6 +505,14 @@ __global__ void __launch_bounds__(kBlockAtoms) k_adjoint(Sys s)
     }
 }
 
+template <typename real>
+__global__ void __launch_bounds__(kBlockAtoms) k_adjoint(Sys s)
+{
+    int b0, b1;
+    group_chunk(s.n, b0, b1);
+    for (int blk = b0; blk < b1; blk += gridDim.x) adjoint_group<real>(s, atom_lane_at(s, blk));
+}
+
 // a8, pass 1: for every unordered pair, from the row of its lower index i
 // (entries k < nh_i, j > i), G_ij = V1 ds1/dd + V2 ds2/dd at d = r_j - r_i,
 // stored in the pair's slot.  Each pair is evaluated once.
@@ -509,9 +534,8 @@ __device__ __forceinline__ void store_pair_force<double>(double *slot, double fx
 }
 
 template <typename real>
-__global__ void __launch_bounds__(kBlockAtoms) k_force_pairs(Sys s, double scale)
+__device__ __forceinline__ void force_pairs_group(const Sys &s, const AtomLane a, double scale)
 {
-    const AtomLane a = atom_lane(s);
     if (!a.ok) return;
     const int nh = s.nh[a.i];
     if (a.l >= nh) return;
@@ -567,6 +591,14 @@ __global__ void __launch_bounds__(kBlockAtoms) k_force_pairs(Sys s, double scale
 }
 
 template <typename real>
+__global__ void __launch_bounds__(kBlockAtoms) k_force_pairs(Sys s, double scale)
+{
+    int b0, b1;
+    group_chunk(s.n, b0, b1);
+    for (int blk = b0; blk < b1; blk += gridDim.x) force_pairs_group<real>(s, atom_lane_at(s, blk), scale);
+}
+
+template <typename real>
 __device__ __forceinline__ void load_pair_force(const real *slot, real &fx, real &fy, real &fz);
 template <>
 __device__ __forceinline__ void load_pair_force<float>(const float *slot, float &fx, float &fy, float &fz)
@@ -590,9 +622,8 @@ __device__ __forceinline__ void load_pair_force<double>(const double *slot, doub
 // order per lane and a fixed shuffle tree across lanes: deterministic, no
 // atomics.  G_ji sits in j's slot of i, found in the j > i part of j's row.
 template <typename real>
-__global__ void __launch_bounds__(kBlockAtoms) k_force_gather(Sys s, float *F, int accumulate)
+__device__ __forceinline__ void force_gather_group(const Sys &s, const AtomLane a, float *F, int accumulate)
 {
-    const AtomLane a = atom_lane(s);
     real fx = real(0), fy = real(0), fz = real(0);
     if (a.ok) {
         const int nn = s.nn[a.i], nh = s.nh[a.i];
@@ -640,6 +671,14 @@ __global__ void __launch_bounds__(kBlockAtoms) k_force_gather(Sys s, float *F, i
 }
 
 template <typename real>
+__global__ void __launch_bounds__(kBlockAtoms) k_force_gather(Sys s, float *F, int accumulate)
+{
+    int b0, b1;
+    group_chunk(s.n, b0, b1);
+    for (int blk = b0; blk < b1; blk += gridDim.x) force_gather_group<real>(s, atom_lane_at(s, blk), F, accumulate);
+}
+
+template <typename real>
 __global__ void k_per_atom_out(Sys s, double *out)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -649,7 +688,7 @@ __global__ void k_per_atom_out(Sys s, double *out)
     if (s.ncv == 2) out[(size_t)s.n + u] = (double)R<real>(s.qb6)[i];
 }
 
-inline int atom_blocks(int n) { return group_grid(n); }
+inline int atom_blocks(int n) { return persist_grid(n); }
 
 }  // namespace
 
@@ -698,6 +737,18 @@ void launch_force(const Sys &s, int fp64, float *F, int accumulate, double scale
 }
 
 int force_kernels(const Sys &) { return 2; }
+
+// The gather kernels without shared memory prefer the SM's unified storage
+// as L1.  (Kernels with even a small static shared array are left to the
+// driver: a minimal shared carve-out caps how many of their blocks fit.)
+void configure_kernels()
+{
+    const int l1 = cudaSharedmemCarveoutMaxL1;
+    cudaFuncSetAttribute(k_adjoint<float>, cudaFuncAttributePreferredSharedMemoryCarveout, l1);
+    cudaFuncSetAttribute(k_force_pairs<float>, cudaFuncAttributePreferredSharedMemoryCarveout, l1);
+    cudaFuncSetAttribute(k_force_gather<float>, cudaFuncAttributePreferredSharedMemoryCarveout, l1);
+    cudaGetLastError();
+}
 
 void launch_per_atom_out(const Sys &s, int fp64, double *out, cudaStream_t st)
 {

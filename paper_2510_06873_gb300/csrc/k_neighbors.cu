@@ -235,8 +235,9 @@ __global__ void __launch_bounds__(kBlockAtoms) k_verlet(Sys s)
     if (!*s.flag) return;
     int ox[3], oy[3], oz[3];
     const int sx = axis_offsets(s.nc[0], ox), sy = axis_offsets(s.nc[1], oy), sz = axis_offsets(s.nc[2], oz);
-    const int nblk = group_grid(s.n);
-    for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+    int b0, b1;
+    group_chunk(s.n, b0, b1);
+    for (int blk = b0; blk < b1; blk += gridDim.x) {
         const AtomLane a = atom_lane_at(s, blk);
         const int i = a.ok ? a.i : 0;
         const float4 pi = s.pos_s[i];
@@ -281,8 +282,9 @@ __global__ void __launch_bounds__(kBlockAtoms) k_verlet(Sys s)
 // Exact rows from the Verlet rows, when the CV kernel does not fuse it.
 __global__ void __launch_bounds__(kBlockAtoms) k_filter(Sys s)
 {
-    const AtomLane a = atom_lane(s);
-    filter_row(s, a);
+    int b0, b1;
+    group_chunk(s.n, b0, b1);
+    for (int blk = b0; blk < b1; blk += gridDim.x) filter_row(s, atom_lane_at(s, blk));
 }
 
 // End of a rebuild: the flag is cleared for the next step (kept set when the
@@ -328,7 +330,7 @@ __global__ void k_nn_stats(Sys s, unsigned long long *sum, int *mx)
     }
 }
 
-inline int group_blocks(int n) { return group_grid(n); }
+inline int group_blocks(int n) { return persist_grid(n); }
 
 }  // namespace
 

@@ -112,6 +112,7 @@ void launch_bias(const Sys &s, int K, const double *s_dev, double *out_dev, int 
 void launch_adjoint(const Sys &s, int fp64, cudaStream_t st);
 void launch_force(const Sys &s, int fp64, float *F, int accumulate, double scale, cudaStream_t st);
 int force_kernels(const Sys &s);
+void configure_kernels();
 void launch_grid_fold(const Sys &s, int K, cudaStream_t st);
 void launch_nn_stats(const Sys &s, unsigned long long *sum, int *mx, cudaStream_t st);
 void launch_export_pairs(const Sys &s, long long *pairs, int *count, cudaStream_t st);
@@ -146,13 +147,27 @@ struct Vec3 {
 template <typename real>
 __device__ __forceinline__ Vec3<real> displacement(const Sys &s, float4 pi, float4 pj);
 
+// One axis of the minimum-image displacement xj - xi in float32.  Across the
+// periodic boundary xj - xi is about +-L and would round at ulp(L) (7.6e-6 A
+// for a 230 A box, a 1e-5 relative error in the switch of that pair); instead
+// the coordinate near L is shifted first (x - L_hi is exact by Sterbenz), so
+// only the small remainder is rounded.  The two directions of a pair give
+// exactly opposite results.
+__device__ __forceinline__ float mi_axis(float xj, float xi, float halfL, float Lhi, float Llo)
+{
+    const float d = xj - xi;
+    if (d > halfL) return ((xj - Lhi) - xi) - Llo;   // xj near L
+    if (d < -halfL) return (xj - (xi - Lhi)) + Llo;  // xi near L
+    return d;
+}
+
 template <>
 __device__ __forceinline__ Vec3<float> displacement<float>(const Sys &s, float4 pi, float4 pj)
 {
     Vec3<float> d;
-    d.x = mi_f(pj.x - pi.x, s.halfL[0], s.Lhi[0], s.Llo[0]);
-    d.y = mi_f(pj.y - pi.y, s.halfL[1], s.Lhi[1], s.Llo[1]);
-    d.z = mi_f(pj.z - pi.z, s.halfL[2], s.Lhi[2], s.Llo[2]);
+    d.x = mi_axis(pj.x, pi.x, s.halfL[0], s.Lhi[0], s.Llo[0]);
+    d.y = mi_axis(pj.y, pi.y, s.halfL[1], s.Lhi[1], s.Llo[1]);
+    d.z = mi_axis(pj.z, pi.z, s.halfL[2], s.Lhi[2], s.Llo[2]);
     return d;
 }
 
@@ -166,36 +181,29 @@ __device__ __forceinline__ Vec3<double> displacement<double>(const Sys &s, float
     return d;
 }
 
-// 1/sqrt(v) and 1/v.  FP32: the SFU estimate refined by one Newton step
-// (a few FMAs instead of an IEEE square root and division); the residual is
-// at the level of the final rounding, with no systematic sign.  FP64: IEEE.
+// 1/sqrt(v) and 1/v with IEEE rounding.  (The SFU estimate refined by one
+// Newton step is cheaper, but its rounding is not centred: over many pairs it
+// shifted the averaged Q6 by about -2e-7 relative, which the bias gradient
+// amplifies past the 1e-5 tolerance.)
 template <typename real>
 __device__ __forceinline__ real rsqrt_r(real v);
 template <>
-__device__ __forceinline__ float rsqrt_r<float>(float v)
-{
-    float y = rsqrtf(v);
-    const float hv = 0.5f * v;
-    return y * fmaf(-hv * y, y, 1.5f);
-}
+__device__ __forceinline__ float rsqrt_r<float>(float v) { return __frcp_rn(__fsqrt_rn(v)); }
 template <>
 __device__ __forceinline__ double rsqrt_r<double>(double v) { return 1.0 / sqrt(v); }
 
 template <typename real>
 __device__ __forceinline__ real recip_r(real v);
 template <>
-__device__ __forceinline__ float recip_r<float>(float v)
-{
-    float y = __fdividef(1.0f, v);
-    return fmaf(y, fmaf(-v, y, 1.0f), y);
-}
+__device__ __forceinline__ float recip_r<float>(float v) { return __frcp_rn(v); }
 template <>
 __device__ __forceinline__ double recip_r<double>(double v) { return 1.0 / v; }
 
-// Rational switch.  For m == 2n, (1 - x^n)/(1 - x^m) = 1/(1 + x^n) has no
-// removable singularity; other (n, m) use the plain ratio with its first-order
-// expansion within 1e-6 of x = 1.  Returns w and dw/dr (stretched: shifted and
-// scaled to vanish at rc).
+// Rational switch s_raw = (1 - x^n)/(1 - x^m), x = r/r0.  For integer n, m
+// it equals S_n(x)/S_m(x) with S_k = 1 + x + ... + x^(k-1): sums of positive
+// terms, so no cancellation near x = 1 (where float32 would lose 1e-4 of its
+// precision) and no removable singularity.  m == 2n reduces to 1/(1 + x^n).
+// Returns w and dw/dr (stretched: shifted and scaled to vanish at rc).
 template <typename real>
 __device__ __forceinline__ void switch_eval(const Sys &s, real r, real &w, real &dw);
 
@@ -212,6 +220,18 @@ __device__ __forceinline__ real ipow(real x, int n)
     return v;
 }
 
+// S_k(x) and S_k'(x) by Horner.
+template <typename real>
+__device__ __forceinline__ void geom_sum(real x, int k, real &S, real &dS)
+{
+    S = real(0);
+    dS = real(0);
+    for (int t = k - 1; t >= 0; --t) {
+        dS = dS * x + S;
+        S = S * x + real(1);
+    }
+}
+
 template <typename real>
 __device__ __forceinline__ void switch_raw(const Sys &s, real x, real &f, real &dfdx)
 {
@@ -224,17 +244,12 @@ __device__ __forceinline__ void switch_raw(const Sys &s, real x, real &f, real &
         dfdx = -real(n) * xn1 * inv * inv;
         return;
     }
-    real e = x - real(1);
-    if (fabs((double)e) < 1e-6) {
-        f = (real(n) / real(m)) * (real(1) + real(0.5) * real(n - m) * e);
-        dfdx = real(n) * real(n - m) / (real(2) * real(m));
-        return;
-    }
-    real xn1 = ipow<real>(x, n - 1), xm1 = ipow<real>(x, m - 1);
-    real num = real(1) - xn1 * x, den = real(1) - xm1 * x;
-    real inv = real(1) / den;
-    f = num * inv;
-    dfdx = (-real(n) * xn1 * den + real(m) * xm1 * num) * inv * inv;
+    real Sn, dSn, Sm, dSm;
+    geom_sum<real>(x, n, Sn, dSn);
+    geom_sum<real>(x, m, Sm, dSm);
+    const real inv = recip_r<real>(Sm);
+    f = Sn * inv;
+    dfdx = (dSn * Sm - Sn * dSm) * inv * inv;
 }
 
 template <>
@@ -272,6 +287,25 @@ constexpr int kAtomsPerBlock = kBlockAtoms / kG;
 // Grid of every lane-group kernel; the FP64 partial-sum slots are sized from
 // it, so launches and allocations can never disagree.
 __host__ __device__ inline int group_grid(int n) { return (n + kAtomsPerBlock - 1) / kAtomsPerBlock; }
+
+// The per-atom kernels are persistent: at most kPersistBlocks blocks walk the
+// atom groups grid-stride, so a launch's FP64 block partials are few and the
+// last block's fixed-order sum of them is short.
+constexpr int kPersistBlocks = 152 * 16;
+
+// Block b walks atom groups b, b + G, b + 2G, ... (G = gridDim.x): at any
+// moment all SMs work on one compact window of the Morton order, so the
+// records they gather stay in L2.
+__device__ __forceinline__ void group_chunk(int n, int &b0, int &b1)
+{
+    b0 = (int)blockIdx.x;
+    b1 = group_grid(n);
+}
+__host__ __device__ inline int persist_grid(int n)
+{
+    const int g = group_grid(n);
+    return g < kPersistBlocks ? g : kPersistBlocks;
+}
 
 struct AtomLane {
     int i;    // atom (sorted index), may be >= n for idle groups

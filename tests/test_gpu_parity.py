@@ -229,8 +229,12 @@ def test_config3_grid_deposit_and_frames(dev):
 
 
 # ------------------------------------------------------------------ variants and edges
-@pytest.mark.parametrize("n", [1, 2, 129, 1023, 4097])
-def test_ragged_and_tiny_systems(dev, n):
+@pytest.mark.parametrize("n,fp64", [(1, False), (1, True), (2, True), (129, False), (129, True), (1023, False),
+                                    (1023, True), (4097, False), (4097, True)])
+def test_ragged_and_tiny_systems(dev, n, fp64):
+    """Ragged sizes around the block shape.  Two atoms run in FP64 only: with a
+    single bond the float32 CV is one rounding sample (~1e-7), which hills
+    within a few sigma amplify past the bias-gradient floor."""
     box = np.array([9.0, 9.5, 10.0]) * max(1.0, (n / 60.0) ** (1 / 3))
     if n <= 2:
         box = np.array([12.0, 12.0, 12.0])
@@ -245,17 +249,18 @@ def test_ragged_and_tiny_systems(dev, n):
     mp = synth.MethodParams(n_cv=2)
     p = oracle.params_from(mp, box)
     s0, _, _ = oracle.cv(pos, p)
-    c = s0[None, :] + np.random.default_rng(1).normal(size=(20, 2)) * np.asarray(mp.sigma)
-    ctx = make_ctx(dev, s, mp)
+    c = synth.hill_centres(96, n, s0, mp.sigma, 200)
+    ctx = make_ctx(dev, s, mp, fp64=fp64)
     w = ctx.deposit_hills(c)
     ref = oracle.step(pos, p, c, w, mp.sigma)
     got = gpu_step(ctx, dev, pos)
     if n == 1:
         assert np.all(got["s"] == 0.0) and np.all(got["F"] == 0.0)
         return
-    check_cv(got["s"], ref["s"])
-    check_bias(got["V"], got["dV"], ref["V"], ref["dV"], mp)
-    check_forces(got["F"], ref["F"])
+    tol = 1e-10 if fp64 else 1e-5
+    check_cv(got["s"], ref["s"], tol=tol)
+    check_bias(got["V"], got["dV"], ref["V"], ref["dV"], mp, tol=tol)
+    check_forces(got["F"], ref["F"], tol=2e-7 if fp64 else 1e-5)
 
 
 def test_isolated_atoms_have_zero_cv_and_force(dev):
@@ -267,7 +272,8 @@ def test_isolated_atoms_have_zero_cv_and_force(dev):
     mp = synth.MethodParams(n_cv=2)
     p = oracle.params_from(mp, box)
     ctx = make_ctx(dev, _Sys(pos, box), mp)
-    c = np.array([[0.2, 0.1], [0.25, 0.12]])
+    s0, _, _ = oracle.cv(pos, p)
+    c = np.array([s0 + np.array([0.01, 0.01]), s0 - np.array([0.02, 0.005])])
     w = ctx.deposit_hills(c)
     got = gpu_step(ctx, dev, pos, per_atom=True)
     ref = oracle.step(pos, p, c, w, mp.sigma)
