@@ -195,6 +195,36 @@ metad_status metad_rebuild_count(metad_ctx *ctx, int64_t *count);
 /* Number of kernels this context has launched since creation. */
 int64_t metad_launch_count(const metad_ctx *ctx);
 
+/* Bias V(s) and dV/ds from caller-held hills, allocating nothing.
+ *
+ * (No counterpart in the paper: this serves callers that cannot allocate
+ * device memory where they need the bias -- an MD engine whose step runs on
+ * its own stream while other work is in flight, where cudaMalloc/cudaFree
+ * could synchronise the device and stall it; code bound to a fixed memory
+ * budget or pool; code that must not create a metad_ctx, which allocates.)
+ *
+ * Computes the same hill sum as metad_bias_eval without a grid:
+ *   out_dev[0] = sum_k w_k exp(-sum_d (s_d - c_kd)^2 / 2 sigma_d^2)
+ *   out_dev[1 + d] = dV/ds_d
+ * s_dev: device double[n_cv]; centers_dev: device double[K][n_cv];
+ * heights_dev: device double[K]; sigma_host: host double[n_cv];
+ * out_dev: device double[3] (out_dev[2] = 0 when n_cv == 1).  Work is
+ * enqueued on `stream` of `device` and the call returns without waiting;
+ * the caller's current device is restored before returning.
+ *
+ * Scratch: a fixed array inside the library (about 12 KB on every GPU that
+ * loads it, held until the process exits) that holds one partial sum per
+ * block of 256 hills, so K may be at most 131,072: larger K returns
+ * METAD_ERR_CAPACITY.  The first call on a device looks up that array's
+ * device address; make the first call before any stream capture.  Each call
+ * clears the completion counter it needs; calls that overlap on the GPU
+ * (concurrent streams) share the array and race, so order them.
+ * Errors: METAD_ERR_INVALID (NULL pointers, n_cv not 1 or 2, K < 0,
+ * sigma <= 0), METAD_ERR_CUDA (a runtime call failed). */
+metad_status metad_bias_eval_noalloc(const double *s_dev, int32_t n_cv, const double *centers_dev,
+                                     const double *heights_dev, int32_t K, const double *sigma_host,
+                                     double *out_dev, int32_t device, void *stream);
+
 /* Copy the last CVs, bias and bias gradient to the host (any may be NULL).
  * Synchronises and reports any pending device error. */
 metad_status metad_read_results(metad_ctx *ctx, double *cv_host, double *V_host, double *dVds_host);

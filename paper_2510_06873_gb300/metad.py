@@ -71,6 +71,8 @@ _SIGS = {
     "metad_launch_count": (ctypes.c_int64, [_P]),
     "metad_neighbor_stats": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]),
     "metad_rebuild_count": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
+    "metad_bias_eval_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.c_int32, _P, _P, ctypes.c_int32,
+                                               _P]),
 }
 METAD_NUM_STAGES = 9
 OPTIONAL = {}
@@ -263,6 +265,16 @@ def metad_rebuild_count(ctx) -> int:
 
 def metad_launch_count(ctx) -> int:
     return int(lib().metad_launch_count(ctx))
+
+
+def metad_bias_eval_noalloc(s, centers, heights, sigma, out, device=0, stream=None):
+    """s, centers [K, n_cv], heights [K], out [3]: device tensors (float64);
+    sigma: host sequence.  Asynchronous on `stream`; allocates nothing."""
+    sg = np.ascontiguousarray(np.atleast_1d(sigma), dtype=np.float64)
+    K = int(heights.shape[0]) if heights is not None else 0
+    n_cv = int(sg.size)
+    _check(None, lib().metad_bias_eval_noalloc(_dptr(s), n_cv, _dptr(centers), _dptr(heights), K, _hptr(sg),
+                                               _dptr(out), int(device), stream), "metad_bias_eval_noalloc")
 
 
 def metad_read_results(ctx):
