@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--atoms", type=int, default=1_000_000, help="workload size (1M is the reported config)")
     ap.add_argument("--hills", type=int, default=None, help="live hills (default: the workload's 20,000)")
     ap.add_argument("--hills-folded", type=int, default=None, help="hills folded into the grid (default 20,000)")
+    ap.add_argument("--max-neighbors", type=int, default=64, help="per-atom neighbour-row capacity")
     return ap.parse_args()
 
 
@@ -239,7 +240,8 @@ def run_metad(args):
     sig = np.asarray(mp.sigma)
     lo, hi = s_ref - 16 * sig, s_ref + 16 * sig
     params = metad.params_for(n, system.box, n_cv=2, sigma=mp.sigma, grid=(cfgp["grid_n"], lo, hi),
-                              hill_capacity=cfgp["hills"] + 1024, stream=stream.cuda_stream)
+                              hill_capacity=cfgp["hills"] + 1024, stream=stream.cuda_stream,
+                              max_neighbors=args.max_neighbors)
     ctx = metad.Metad(params)
     K1 = cfgp["hills_folded"] if args.hills_folded is None else args.hills_folded
     K2 = cfgp["hills"] if args.hills is None else args.hills

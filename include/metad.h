@@ -75,7 +75,8 @@ typedef struct {
     double grid_hi[2];
     int32_t precision;      /* 0: FP32 pair arithmetic, FP64 reductions and
                                hills; 1: FP64 throughout */
-    int32_t max_neighbors;  /* per-atom capacity of the neighbour list (0: 64) */
+    int32_t max_neighbors;  /* per-atom capacity of the neighbour list (0: 64;
+                               rounded up to a multiple of 4) */
     int32_t device;         /* CUDA device ordinal */
     int32_t reserved;
     void *stream;           /* cudaStream_t, or NULL */

@@ -266,6 +266,8 @@ metad_status metad_create(const metad_params *p, metad_ctx **out)
     if (!c) return METAD_ERR_OOM;
     c->p = *p;
     if (c->p.max_neighbors == 0) c->p.max_neighbors = 64;
+    // rows are read four entries at a time: keep their length a multiple of 4
+    c->p.max_neighbors = (c->p.max_neighbors + 3) / 4 * 4;
     c->fp64 = c->p.precision == 1;
     metad_status s = cuda_check(c, cudaSetDevice(c->p.device), "cudaSetDevice");
     if (s != METAD_OK) { metad_destroy(c); return s; }

@@ -11,9 +11,9 @@
 //   b_m(i) = K_m qb_m(i) / (N qb6(i) (1 + W_i))                ds2/dA_m(i)
 //   g_m(k) = b_m(k) + sum_i w_ik b_m(i)                        ds2/dq_m(k)
 //   h_m(k) = g_m(k) / W_k                                      ds2/dQ_m(k)
-//   -ds2/dW_k = h(k).q(k) + b(k).qb(k), folded into the pair term:
+//   gam_k  = h(k).q(k) + b(k).qb(k)                            -ds2/dW_k
 //   per pair (i, j), d = r_j - r_i:
-//     ds2/dw = h(i).(Y - q(i)) + h(j).(Y - q(j)) + b(i).(q(j) - qb(i)) + b(j).(q(i) - qb(j))
+//     ds2/dw = (h_i + h_j).Y - gam_i - gam_j + b(i).q(j) + b(j).q(i)
 //     ds2/dd = ds2/dw w'(r) d/r + w sum_m (h_m(i)+h_m(j)) dY_m/dd
 //     ds1/dd = (2/N) w'(r) d/r [unlike]
 //   F_i = sum_{j in N(i)} (V1 ds1/dd + V2 ds2/dd)
@@ -347,6 +347,44 @@ __device__ __forceinline__ void store_pair<double>(double *base, int i, int l, d
     reinterpret_cast<double2 *>(base + (size_t)i * kRec)[l] = make_double2(a, b);
 }
 
+// Components (2l, 2l + 1) of record i: the kG lanes of a group together read
+// the whole 64 B (FP32) row with one coalesced access.
+template <typename real>
+__device__ __forceinline__ void load_pair(const real *base, int i, int l, real &a, real &b);
+template <>
+__device__ __forceinline__ void load_pair<float>(const float *base, int i, int l, float &a, float &b)
+{
+    const float2 t = reinterpret_cast<const float2 *>(base + (size_t)i * kRec)[l];
+    a = t.x;
+    b = t.y;
+}
+template <>
+__device__ __forceinline__ void load_pair<double>(const double *base, int i, int l, double &a, double &b)
+{
+    const double2 t = reinterpret_cast<const double2 *>(base + (size_t)i * kRec)[l];
+    a = t.x;
+    b = t.y;
+}
+
+// A group's row entries k0 .. k0+15, staged with two coalesced loads: lane l
+// holds entries k0 + l and k0 + l + kG; entry t is then shuffled out of lane
+// t % kG, so the dependent record loads of all 16 entries can be issued back
+// to back.
+__device__ __forceinline__ unsigned group_lane_mask()
+{
+    return 0xFFu << ((threadIdx.x & 31) & ~(kG - 1));
+}
+
+template <typename real>
+__device__ __forceinline__ void stage_row(const int *row, const real *wrow, int k0, int nn, int l, int &j0, int &j1,
+                                          real &w0, real &w1)
+{
+    j0 = k0 + l < nn ? row[k0 + l] : 0;
+    j1 = k0 + l + kG < nn ? row[k0 + l + kG] : 0;
+    w0 = k0 + l < nn ? wrow[k0 + l] : real(0);
+    w1 = k0 + l + kG < nn ? wrow[k0 + l + kG] : real(0);
+}
+
 __device__ __forceinline__ const int *nbr_row(const Sys &s, int i) { return s.nbr + (size_t)i * s.max_nb; }
 
 // a4: CN_i, W_i and q_m(i) = sum_j w_ij Y_m(rhat_ij) / W_i.
@@ -411,46 +449,50 @@ __global__ void __launch_bounds__(kBlockAtoms) k_cv_fwd(Sys s)
     last_block_reduce(s, acc, 0, s.scal + kS0, 1.0 / s.n);
 }
 
-// a5: qbar_m(i), qbar6(i), s2.  Record qb: qbar_m (0..12) and
-// c_i = 1 / (N qbar6 (1 + W_i)) (13), so b_m(i) = c_i K_m qbar_m(i).
+// a5: qbar_m(i), qbar6(i), s2.  Record b: b_m(i) = K_m qbar_m(i) / (N qbar6
+// (1 + W_i)) (slots 0..12) and beta_i = b(i).qbar(i) (slot 13).
 template <typename real>
 __device__ __forceinline__ double cv_avg_group(const Sys &s, const AtomLane a)
 {
+    // lane l owns components 2l, 2l + 1 and walks every neighbour of the atom
     const real *q = R<real>(s.q);
-    real v[kRec];
-#pragma unroll
-    for (int m = 0; m < kRec; ++m) v[m] = real(0);
+    real a0 = real(0), a1 = real(0);
+    double q6_out = 0.0;
     if (a.ok) {
         const int nn = s.nn[a.i];
         const int *row = nbr_row(s, a.i);
         const real *wrow = R<real>(s.wl) + (size_t)a.i * s.max_nb;
-        for (int k = a.l; k < nn; k += kG) {
+#pragma unroll 4
+        for (int k = 0; k < nn; ++k) {
             const int j = row[k];
             const real w = wrow[k];
-            real qj[kRec];
-            load_rec<real>(q, j, qj);
-#pragma unroll
-            for (int m = 0; m < kNY; ++m) v[m] += w * qj[m];
+            real x0, x1;
+            load_pair<real>(q, j, a.l, x0, x1);
+            a0 += w * x0;
+            a1 += w * x1;
         }
     }
-    reduce_scatter16<real>(v, a.l);
-    real qb0 = real(0), qb1 = real(0), sq = real(0);
-    real inv_D = real(0);
+    real qb0 = real(0), qb1 = real(0), sq = real(0), inv_D = real(0);
     if (a.ok) {
         inv_D = real(1) / (real(1) + R<real>(s.W)[a.i]);
+        real o0, o1;
+        load_pair<real>(q, a.i, a.l, o0, o1);
         const int m0 = 2 * a.l, m1 = 2 * a.l + 1;
-        if (m0 < kNY) qb0 = (q[(size_t)a.i * kRec + m0] + v[0]) * inv_D;
-        if (m1 < kNY) qb1 = (q[(size_t)a.i * kRec + m1] + v[1]) * inv_D;
+        if (m0 < kNY) qb0 = (o0 + a0) * inv_D;
+        if (m1 < kNY) qb1 = (o1 + a1) * inv_D;
         if (m0 < kNY) sq += weighted_term<real>(m0, qb0);
         if (m1 < kNY) sq += weighted_term<real>(m1, qb1);
     }
     sq = group_sum<real>(sq);
     const real qb6 = sqrt(sq);
-    double q6_out = 0.0;
+    const real ci = qb6 > real(0) ? inv_D / (real(s.n) * qb6) : real(0);
+    const int m0 = 2 * a.l, m1 = 2 * a.l + 1;
+    real b0 = m0 < kNY ? ci * kweight<real>(m0) * qb0 : real(0);
+    real b1 = m1 < kNY ? ci * kweight<real>(m1) * qb1 : real(0);
+    const real beta = group_sum<real>(b0 * qb0 + b1 * qb1);
     if (a.ok) {
-        const real ci = qb6 > real(0) ? inv_D / (real(s.n) * qb6) : real(0);
-        if (a.l == 6) qb1 = ci;  // slot 13
-        store_pair<real>(R<real>(s.b), a.i, a.l, qb0, qb1);
+        if (a.l == 6) b1 = beta;  // slot 13
+        store_pair<real>(R<real>(s.b), a.i, a.l, b0, b1);
         if (a.l == 0) {
             R<real>(s.qb6)[a.i] = qb6;
             q6_out = (double)qb6;
@@ -469,38 +511,55 @@ __global__ void __launch_bounds__(kBlockAtoms) k_cv_avg(Sys s)
     last_block_reduce(s, acc, 1, s.scal + kS1, 1.0 / s.n);
 }
 
-// a7: g_m(k) = K_m (c_k qbar_m(k) + sum_i w_ik c_i qbar_m(i)) ; h = g / W.
+// a7: g_m(k) = b_m(k) + sum_i w_ik b_m(i) ; h = g / W ; record h holds h_m
+// (0..12) and gamma_k = h(k).q(k) + beta_k (slot 13).
 template <typename real>
 __device__ __forceinline__ void adjoint_group(const Sys &s, const AtomLane a)
 {
-    const real *qb = R<real>(s.b);
-    real v[kRec];
-#pragma unroll
-    for (int m = 0; m < kRec; ++m) v[m] = real(0);
+    // lane l owns components 2l, 2l + 1; record b holds b_m (0..12), beta (13)
+    const real *bb = R<real>(s.b);
+    real g0 = real(0), g1 = real(0);
     if (a.ok) {
         const int nn = s.nn[a.i];
         const int *row = nbr_row(s, a.i);
         const real *wrow = R<real>(s.wl) + (size_t)a.i * s.max_nb;
-        for (int k = a.l; k < nn; k += kG) {
-            const int j = row[k];
-            const real w = wrow[k];
-            real bj[kRec];
-            load_rec<real>(qb, j, bj);
-            const real wc = w * bj[13];
+        const unsigned gm = group_lane_mask();
+        for (int k0 = 0; k0 < nn; k0 += 2 * kG) {
+            int j0, j1;
+            real w0, w1;
+            stage_row<real>(row, wrow, k0, nn, a.l, j0, j1, w0, w1);
+            real x0[2 * kG], x1[2 * kG], wt[2 * kG];
 #pragma unroll
-            for (int m = 0; m < kNY; ++m) v[m] += wc * bj[m];
+            for (int t = 0; t < 2 * kG; ++t) {
+                const int jt = __shfl_sync(gm, t < kG ? j0 : j1, t & (kG - 1), kG);
+                wt[t] = __shfl_sync(gm, t < kG ? w0 : w1, t & (kG - 1), kG);
+                x0[t] = x1[t] = real(0);
+                if (k0 + t < nn) load_pair<real>(bb, jt, a.l, x0[t], x1[t]);
+            }
+#pragma unroll
+            for (int t = 0; t < 2 * kG; ++t) {
+                g0 += wt[t] * x0[t];
+                g1 += wt[t] * x1[t];
+            }
         }
     }
-    reduce_scatter16<real>(v, a.l);
+    real h0 = real(0), h1 = real(0), alpha = real(0), beta = real(0);
     if (a.ok) {
         const real W = R<real>(s.W)[a.i];
         const real inv_W = W > real(0) ? real(1) / W : real(0);
-        const real *own = qb + (size_t)a.i * kRec;
-        const real ci = own[13];
+        real o0, o1, q0, q1;
+        load_pair<real>(bb, a.i, a.l, o0, o1);
+        load_pair<real>(R<real>(s.q), a.i, a.l, q0, q1);
         const int m0 = 2 * a.l, m1 = 2 * a.l + 1;
-        real h0 = real(0), h1 = real(0);
-        if (m0 < kNY) h0 = kweight<real>(m0) * (ci * own[m0] + v[0]) * inv_W;
-        if (m1 < kNY) h1 = kweight<real>(m1) * (ci * own[m1] + v[1]) * inv_W;
+        if (m0 < kNY) h0 = (o0 + g0) * inv_W;
+        if (m1 < kNY) h1 = (o1 + g1) * inv_W;
+        alpha = h0 * q0 + (m1 < kNY ? h1 * q1 : real(0));
+        if (m1 == 13) beta = o1;
+    }
+    alpha = group_sum<real>(alpha);
+    beta = group_sum<real>(beta);
+    if (a.ok) {
+        if (a.l == 6) h1 = alpha + beta;  // slot 13: gamma = h.q + b.qbar
         store_pair<real>(R<real>(s.h), a.i, a.l, h0, h1);
     }
 }
@@ -516,9 +575,9 @@ __global__ void __launch_bounds__(kBlockAtoms) k_adjoint(Sys s)
 // a8, pass 1: for every unordered pair, from the row of its lower index i
 // (entries k < nh_i, j > i), G_ij = V1 ds1/dd + V2 ds2/dd at d = r_j - r_i,
 // stored in the pair's slot.  Each pair is evaluated once.
-//   ds2/dw = h_i.(Y - q_i) + h_j.(Y - q_j) + b_i.(q_j - qb_i) + b_j.(q_i - qb_j)
-// (differences formed before the products), ds2/dd = ds2/dw w' d/r
-// + w sum_m (h_i + h_j)_m dY_m/dd, ds1/dd = (2/N) w' d/r [unlike].
+//   ds2/dw = (h_i + h_j).Y - gamma_i - gamma_j + b_i.q_j + b_j.q_i
+//   ds2/dd = ds2/dw w' d/r + w sum_m (h_i + h_j)_m dY_m/dd
+//   ds1/dd = (2/N) w' d/r [unlike]
 template <typename real>
 __device__ __forceinline__ void store_pair_force(real *slot, real fx, real fy, real fz);
 template <>
@@ -566,19 +625,18 @@ __device__ __forceinline__ void force_pairs_group(const Sys &s, const AtomLane a
             load_rec<real>(hh, j, hj);
             load_rec<real>(qq, j, qj);
             load_rec<real>(qbb, j, qbj);
-            real cvec[kNY];
-#pragma unroll
-            for (int m = 0; m < kNY; ++m) cvec[m] = w * (hi[m] + hj[m]);
-            real Y[kNY], gY[3];
-            ylm13_grad<real>(ux, uy, uz, inv_r, cvec, Y, gY);
-            const real ci = qbi[13], cj = qbj[13];
-            real t_h = real(0), t_b = real(0);
+            real hs[kNY], cvec[kNY];
 #pragma unroll
             for (int m = 0; m < kNY; ++m) {
-                t_h += hi[m] * (Y[m] - qi[m]) + hj[m] * (Y[m] - qj[m]);
-                t_b += kweight<real>(m) * (ci * qbi[m] * (qj[m] - qbi[m]) + cj * qbj[m] * (qi[m] - qbj[m]));
+                hs[m] = hi[m] + hj[m];
+                cvec[m] = w * hs[m];
             }
-            radial += V2 * (t_h + t_b) * dw;
+            real Y[kNY], gY[3];
+            ylm13_grad<real>(ux, uy, uz, inv_r, cvec, Y, gY);
+            real t = -(hi[13] + hj[13]);
+#pragma unroll
+            for (int m = 0; m < kNY; ++m) t += hs[m] * Y[m] + qbi[m] * qj[m] + qbj[m] * qi[m];
+            radial += V2 * t * dw;
             fx = V2 * gY[0];
             fy = V2 * gY[1];
             fz = V2 * gY[2];
@@ -640,9 +698,16 @@ __device__ __forceinline__ void force_gather_group(const Sys &s, const AtomLane 
                 const int j = row[k];
                 const int *rj = nbr_row(s, j);
                 const int nhj = s.nh[j];
-                int kk = 0;
-                while (kk < nhj && rj[kk] != a.i) ++kk;
-                if (kk == nhj) {
+                // position of i in the j > i part of j's row, four entries per load
+                int kk = -1;
+                for (int b = 0; b < nhj && kk < 0; b += 4) {
+                    const int4 v = *reinterpret_cast<const int4 *>(rj + b);
+                    if (v.x == a.i && b < nhj) kk = b;
+                    else if (v.y == a.i && b + 1 < nhj) kk = b + 1;
+                    else if (v.z == a.i && b + 2 < nhj) kk = b + 2;
+                    else if (v.w == a.i && b + 3 < nhj) kk = b + 3;
+                }
+                if (kk < 0) {
                     set_err(s, kErrInternal);  // rows not symmetric: never expected
                     continue;
                 }

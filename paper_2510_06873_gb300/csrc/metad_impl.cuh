@@ -84,7 +84,7 @@ struct Sys {
     int always_rebuild;    // skin == 0
     unsigned long long *rebuilds;  // number of rebuilds done
     void *cn, *W, *qb6;    // real-typed per-atom scalars
-    void *q, *b, *h;       // real-typed per-atom records [n][16]: q_m; qbar_m and c; h_m
+    void *q, *b, *h;       // real-typed per-atom records [n][16]: q_m; b_m, beta; h_m, gamma
     double *part;          // per-block FP64 partial sums, slots of part_stride
     int part_stride;
     unsigned *ticket;      // completion counters of the last-block reductions
@@ -364,25 +364,24 @@ __device__ __forceinline__ int filter_row(const Sys &s, const AtomLane &a)
     const int *vrow = s.vnbr + (size_t)(a.ok ? a.i : 0) * s.max_vnb;
     int *row = s.nbr + (size_t)(a.ok ? a.i : 0) * s.max_nb;
     int cnt = 0, nh = 0;
-#pragma unroll 1
-    for (int part = 0; part < 2; ++part) {
-        const int k0 = part == 0 ? 0 : vh, k1 = part == 0 ? vh : vn;
-        const int span = k1 - k0;
-        const int smax = __reduce_max_sync(0xffffffffu, span);
-        for (int base = 0; base < smax; base += kG) {
-            const int k = k0 + base + a.l;
-            bool in = false;
-            int j = 0;
-            if (base + a.l < span) {
-                j = vrow[k];
-                in = pair_in(s, pi, s.pos_s[j]);
-            }
-            const unsigned gm = group_mask_bits(__ballot_sync(0xffffffffu, in));
-            const int at = cnt + __popc(gm & ((1u << a.l) - 1u));
-            if (in && at < s.max_nb) row[at] = j;
-            cnt += __popc(gm);
+    // one pass: the Verlet row already has its j > i part first, so accepted
+    // entries come out in the same order; nh counts those from that part
+    const int vmax = __reduce_max_sync(0xffffffffu, vn);
+    for (int base = 0; base < vmax; base += kG) {
+        const int k = base + a.l;
+        bool in = false;
+        int j = 0;
+        if (k < vn) {
+            j = vrow[k];
+            in = pair_in(s, pi, s.pos_s[j]);
         }
-        if (part == 0) nh = cnt;
+        const unsigned ball = __ballot_sync(0xffffffffu, in);
+        const unsigned gm = group_mask_bits(ball);
+        const unsigned gu = group_mask_bits(__ballot_sync(0xffffffffu, in && k < vh));
+        const int at = cnt + __popc(gm & ((1u << a.l) - 1u));
+        if (in && at < s.max_nb) row[at] = j;
+        cnt += __popc(gm);
+        nh += __popc(gu);
     }
     if (a.ok && a.l == 0) {
         if (cnt > s.max_nb) set_err(s, kErrCapacity);
