@@ -44,11 +44,13 @@ WORKLOAD = ("1M-atom half-wurtzite/half-RSA-liquid periodic box (228.6 A), 2 CVs
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # Algorithmic work per unordered neighbour pair (one evaluation; the kernels
 # evaluate each pair from both ends, which is not counted).
-FLOP_PER_PAIR = {"force": 340.0, "cv_fwd": 130.0, "cv_avg": 45.0, "adjoint": 45.0, "neighbors": 0.0}
-# Algorithmic bytes per atom of each stage (compulsory traffic, FP32 state).
+FLOP_PER_PAIR = {"force_pairs": 340.0, "cv_fwd": 130.0, "cv_avg": 45.0, "adjoint": 45.0, "neighbors": 0.0}
+# Algorithmic bytes per atom of each stage (compulsory traffic, FP32 state;
+# 15.4 row entries and 7.7 unordered pairs per atom).
 BYTES_PER_ATOM = {"bin": 16 + 16 + 4 * 6, "neighbors": 16 + 4 + 4 * 15.45, "cv_fwd": 16 + 4 + 4 * 15.45 + 60,
                   "cv_avg": 16 + 4 + 4 * 15.45 + 56 + 60, "adjoint": 16 + 4 + 4 * 15.45 + 56 + 56,
-                  "force": 16 + 4 + 4 * 15.45 + 160 + 12 + 4}
+                  "force_pairs": 16 + 4 + 4 * 7.7 + 3 * 64 + 16 * 7.7,
+                  "force_gather": 8 + 4 * 15.45 + 16 * 15.45 + 12}
 
 
 def parse():
@@ -64,6 +66,9 @@ def parse():
     ap.add_argument("--hills", type=int, default=None, help="live hills (default: the workload's 20,000)")
     ap.add_argument("--hills-folded", type=int, default=None, help="hills folded into the grid (default 20,000)")
     ap.add_argument("--max-neighbors", type=int, default=64, help="per-atom neighbour-row capacity")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-system batched comparison")
+    ap.add_argument("--no-served", action="store_true", help="skip the served (continuous batching) trace")
+    ap.add_argument("--batched-steps", type=int, default=10)
     return ap.parse_args()
 
 
@@ -127,6 +132,23 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def max_over_ranks(x: float, device) -> float:
+    """The largest value of x over all ranks (the job's time is its slowest
+    replica's); x itself when not distributed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world_size: int, units_per_rank: int, steps: int, seconds: float) -> float:
+    """Whole-job atom-steps/s: every replica's units over the slowest time."""
+    return world_size * units_per_rank * steps / seconds
 
 
 def kbdt(mp):
@@ -291,11 +313,8 @@ def run_metad(args):
     clk = clocks.stop()
     stages = ctx.profile_end()
     launches = ctx.launch_count - launches0
-    if ws > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * n * args.steps / (ms / 1e3)
+    ms = max_over_ranks(ms, dev)
+    value = job_throughput(ws, n, args.steps, ms / 1e3)
     # ---- dominant kernel roofline from the live per-stage events
     dom = max((k for k in stages if stages[k][1] > 0 and k != "other"), key=lambda k: stages[k][0])
     dom_ms, dom_cnt = stages[dom]
@@ -333,12 +352,8 @@ def run_metad(args):
         for k in range(args.e2e_steps):
             ctx.step_host(pin_pos[k % len(pin_pos)], pin_F, deposit=((frame_no + 1) % every == 0))
             frame_no += 1
-        dt = time.perf_counter() - t0
-        if ws > 1:
-            t = torch.tensor([dt], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": ws * n * args.e2e_steps / dt, "unit": UNIT, "h2d_bytes_per_step": 16 * n,
+        dt = max_over_ranks(time.perf_counter() - t0, dev)
+        e2e = {"value": job_throughput(ws, n, args.e2e_steps, dt), "unit": UNIT, "h2d_bytes_per_step": 16 * n,
                "d2h_bytes_per_step": 12 * n + 24, "steps": args.e2e_steps,
                "call": "metad_step_host (pinned host positions in, host forces + CVs + bias out)"}
     ctx.sync()
@@ -347,6 +362,12 @@ def run_metad(args):
         v, cores, dt = oracle_sample(n, 2)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"2 frames of the same {n}-atom workload (oracle hills/grid set up untimed), {dt:.1f} s"}
+    forms = {}
+    if rank == 0 and ws == 1:
+        if not args.no_batched:
+            forms["batched"] = run_batched(args, dev, stream, metad)
+        if not args.no_served:
+            forms["served"] = run_served(args, dev, stream, metad)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": max(3, args.warmup), "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
@@ -361,12 +382,138 @@ def run_metad(args):
                                                "achieved_gbs": step_bytes / (step_ms / 1e3) / 1e9,
                                                "peak_gbs": peaks_hbm,
                                                "frac": step_bytes / (step_ms / 1e3) / 1e9 / peaks_hbm},
-                "stages": stage_line, "gpu_launches": launches, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
+                "stages": stage_line, "gpu_launches": launches, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
+                **forms}
         print(json.dumps(line), flush=True)
     ctx.close()
     if ws > 1:
         dist.destroy_process_group()
     return 0
+
+
+# ---------------------------------------------------------------- batched and served forms
+def _seeded_hills(metad, system, mp, cfg, count, stream, dev, params):
+    """Hill centres around the CUDA path's own CVs of the base frame and their
+    well-tempered heights, deposited by the CUDA path (host copies back)."""
+    import torch
+    ctx = metad.Metad(params)
+    ctx.build_neighbors(torch.from_numpy(system.base).to(dev))
+    s_ref = ctx.cv_forward()
+    cen = synth.hill_centres(cfg, system.sys, s_ref, mp.sigma, count)
+    w = ctx.deposit_hills(cen)
+    return ctx, cen, w
+
+
+def run_batched(args, dev, stream, metad):
+    """64 systems (1k-200k atoms, 100-10,000 hills): one batched step per
+    frame against 64 plain per-context steps, same contexts and frames."""
+    import torch
+    from paper_2510_06873_gb300 import tune
+    mp = synth.method_params(4)
+    cfgp = synth.CONFIG_PARAMS[4]
+    nsys = cfgp["systems"]
+    n, k, dens = synth.batch_layout(4, n_systems=nsys)
+    systems = [synth.wurtzite_system(int(n[s]), cfg=4, sys=s, density_scale=float(dens[s])) for s in range(nsys)]
+    ctxs = []
+    for s, sysm in enumerate(systems):
+        p = metad.params_for(sysm.n, sysm.box, n_cv=2, sigma=mp.sigma, stream=stream.cuda_stream,
+                             hill_capacity=int(k[s]) + 64)
+        ctx, _, _ = _seeded_hills(metad, sysm, mp, 4, int(k[s]), stream, dev, p)
+        ctxs.append(ctx)
+    nfr = 4  # 4 resident frames per system: about 150 MB of positions, more than L2
+    frames = [[torch.from_numpy(synth.perturbed_frame(sysm, f)).to(dev) for f in range(nfr)] for sysm in systems]
+    F = [torch.zeros((sysm.n, 3), dtype=torch.float32, device=dev) for sysm in systems]
+    steps = max(1, args.batched_steps)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def plain(t):
+        for s, ctx in enumerate(ctxs):
+            ctx.step(frames[s][t % nfr], F[s])
+
+    batch = metad.Batch(ctxs)
+
+    def batched(t):
+        batch.step([fr[t % nfr] for fr in frames], F)
+
+    for t in range(3):
+        plain(t)
+    torch.cuda.synchronize(dev)
+    l0 = sum(c.launch_count for c in ctxs)
+    ev0.record(stream)
+    for t in range(steps):
+        plain(t)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    plain_ms = ev0.elapsed_time(ev1) / steps
+    plain_launches = (sum(c.launch_count for c in ctxs) - l0) / steps
+    tuned = tune.tune_batch(batch, [fr[0] for fr in frames], F, stream)
+    for t in range(3):
+        batched(t)
+    torch.cuda.synchronize(dev)
+    b0 = batch.launch_count
+    ev0.record(stream)
+    for t in range(steps):
+        batched(t)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    batch_ms = ev0.elapsed_time(ev1) / steps
+    batch_launches = (batch.launch_count - b0) / steps
+    atoms = int(sum(sysm.n for sysm in systems))
+    batch.close()
+    for c in ctxs:
+        c.close()
+    return {"systems": nsys, "atoms": atoms, "hills": int(np.sum(k)), "steps": steps,
+            "plain_ms_per_step": plain_ms, "batched_ms_per_step": batch_ms,
+            "plain_atom_steps_per_s": atoms / (plain_ms / 1e3), "batched_atom_steps_per_s": atoms / (batch_ms / 1e3),
+            "speedup": plain_ms / batch_ms, "kernels_per_step": {"plain": plain_launches, "batched": batch_launches},
+            "tile": tuned["tile"], "tile_ms": {str(c): v for c, v in tuned["ms_per_step"].items()},
+            "inputs": f"{nfr} resident frames per system cycled (positions > L2)"}
+
+
+def run_served(args, dev, stream, metad):
+    """32 walkers (2k-500k atoms, 1,000 hills each), 2,000 Poisson requests at
+    5,000/s: continuous batching against sequential plain evaluation."""
+    import torch
+    from paper_2510_06873_gb300 import serve
+    mp = synth.method_params(5)
+    cfgp = synth.CONFIG_PARAMS[5]
+    n_w, arrivals, walker_of = synth.served_trace(5, n_walkers=cfgp["walkers"], n_requests=cfgp["requests"],
+                                                  rate_hz=cfgp["rate_hz"])
+    systems = [synth.wurtzite_system(int(n_w[w]), cfg=5, sys=w) for w in range(len(n_w))]
+
+    def make_walkers():
+        out = []
+        for w, sysm in enumerate(systems):
+            p = metad.params_for(sysm.n, sysm.box, n_cv=2, sigma=mp.sigma, stream=stream.cuda_stream,
+                                 hill_capacity=cfgp["hills"] + cfgp["requests"] // cfgp["deposit_every"] + 64)
+            out.append(serve.Walker(params=p, centres=hill_sets[w][0], heights=hill_sets[w][1], frames=frames[w]))
+        return out
+
+    hill_sets, frames = [], []
+    for w, sysm in enumerate(systems):
+        p = metad.params_for(sysm.n, sysm.box, n_cv=2, sigma=mp.sigma, stream=stream.cuda_stream,
+                             hill_capacity=cfgp["hills"] + 64)
+        ctx, cen, hw = _seeded_hills(metad, sysm, mp, 5, cfgp["hills"], stream, dev, p)
+        ctx.close()
+        hill_sets.append((cen, hw))
+        frames.append([torch.from_numpy(synth.perturbed_frame(sysm, f)).pin_memory() for f in range(3)])
+    srv = serve.Server(make_walkers(), stream, budget_bytes=cfgp["budget_bytes"],
+                       deposit_every=cfgp["deposit_every"])
+    srv.preload()
+    served = srv.run(arrivals, walker_of)
+    srv.close()
+    plain_walkers = make_walkers()
+    plain = serve.run_plain(plain_walkers, stream, arrivals, walker_of, deposit_every=cfgp["deposit_every"])
+    for wk in plain_walkers:
+        wk.ctx.close()
+    agree = all(np.array_equal(a.cv, b.cv) and a.V == b.V for a, b in zip(served.requests, plain.requests))
+    s, q = served.summary(), plain.summary()
+    return {"walkers": len(n_w), "atoms_resident": int(sum(sysm.n for sysm in systems)),
+            "requests": len(arrivals), "rate_hz": cfgp["rate_hz"], "budget_bytes": cfgp["budget_bytes"],
+            "served": s, "plain": q, "p99_ratio_plain_over_served": q["p99_ms"] / s["p99_ms"],
+            "throughput_ratio": s["atom_steps_per_s"] / q["atom_steps_per_s"],
+            "results_identical_to_plain": bool(agree), "kernels": served.launches,
+            "h2d": "positions from page-locked host memory per request; forces and CVs back per request"}
 
 
 def main():

@@ -179,7 +179,7 @@ metad_status metad_step_host(metad_ctx *ctx, const float *pos_host, float *force
  * stages are recorded).  end synchronises and writes, per stage index
  * 0..METAD_NUM_STAGES-1 (names from metad_stage_name), the summed device
  * milliseconds and the number of records (either pointer may be NULL). */
-#define METAD_NUM_STAGES 9
+#define METAD_NUM_STAGES 10
 metad_status metad_profile_begin(metad_ctx *ctx, int32_t max_records);
 metad_status metad_profile_end(metad_ctx *ctx, double *ms_per_stage, int32_t *records_per_stage);
 const char *metad_stage_name(int32_t stage);
@@ -192,6 +192,15 @@ metad_status metad_neighbor_stats(metad_ctx *ctx, int64_t *entries, int32_t *max
 /* Number of cell-order / Verlet-list rebuilds since creation (the first
  * build_neighbors always rebuilds).  Synchronises. */
 metad_status metad_rebuild_count(metad_ctx *ctx, int64_t *count);
+
+/* Device bytes a context with these parameters allocates at creation (the
+ * sum of its requests; the allocator may round each up).  No GPU needed.
+ * Errors: those of metad_create's parameter checks. */
+metad_status metad_estimate_bytes(const metad_params *params, int64_t *bytes);
+
+/* Device bytes this context has requested so far (creation plus the
+ * buffers allocated on first use by export and host-buffer steps). */
+int64_t metad_device_bytes(const metad_ctx *ctx);
 
 /* Number of kernels this context has launched since creation. */
 int64_t metad_launch_count(const metad_ctx *ctx);
@@ -244,6 +253,71 @@ const char *metad_status_string(metad_status s);
 
 /* Text of the last error recorded on this context (never NULL). */
 const char *metad_last_error(const metad_ctx *ctx);
+
+/* ------------------------------------------------------------------ batches
+ * Many independent systems stepped together: each stage of the step
+ * (gather, rebuild chain, CVs, bias, adjoint and forces, deposit) is ONE
+ * kernel launch whose grid is the concatenation of every system's own grid,
+ * instead of one launch per stage per system.  (No counterpart in the
+ * paper, which runs one system per process; it serves many small walkers or
+ * replicas on one GPU, where per-system launches leave the GPU idle.)
+ *
+ * A batch refers to existing contexts; it owns none of them.  Every context
+ * must be on the same device and stream, with the same n_cv and precision.
+ * Each system keeps its own neighbour state, hills, grid and reductions, so
+ * with the default tile (0) a batched step gives every system the same bits
+ * as metad_step on that context alone.  Destroy the batch before its
+ * contexts; per-context calls may be interleaved with batched steps (same
+ * stream, so they are ordered). */
+typedef struct metad_batch metad_batch;
+
+/* ctxs: host array of n >= 1 context pointers.  Allocates the descriptor
+ * tables (device) and a small pinned ring (host).
+ * Errors: METAD_ERR_INVALID (NULL, n < 1, contexts that differ in device,
+ * stream, n_cv or precision, a failed context), METAD_ERR_OOM. */
+metad_status metad_batch_create(metad_ctx *const *ctxs, int32_t n, metad_batch **out);
+
+metad_status metad_batch_destroy(metad_batch *batch);
+
+/* Tile setting of the per-atom kernels: at most `blocks_per_system` blocks
+ * of 16 atoms' lane groups per system (0 = the single-context grid).  A
+ * setting other than 0 changes the order of the FP64 block partials of the
+ * CV sums (last-bit differences from metad_step), not any per-atom value.
+ * Errors: METAD_ERR_INVALID (negative). */
+metad_status metad_batch_set_tile(metad_batch *batch, int32_t blocks_per_system);
+
+/* One full step (metad_step: neighbours, CVs, bias, forces, then an optional
+ * deposit) for every active system of the batch.
+ * pos_dev: host array of n device pointers, float32 [N_k][4] each;
+ * forces_dev: host array of n device pointers, float32 [N_k][3] each, written
+ * (accumulate = 0) or added to (accumulate = 1);
+ * deposit: host int32[n] (1 = deposit a hill at that system's CVs after its
+ * forces) or NULL for none;
+ * active: host int32[n] (0 = leave system k out of this step; its pointers
+ * may then be NULL) or NULL for all.  Asynchronous; stream-ordered.
+ * Errors: METAD_ERR_INVALID (NULL pointers), METAD_ERR_STATE (a context has
+ * failed), METAD_ERR_CAPACITY (a deposit into a full hill list),
+ * METAD_ERR_CUDA. */
+metad_status metad_batch_step(metad_batch *batch, const float *const *pos_dev, float *const *forces_dev,
+                              int32_t accumulate, const int32_t *deposit, const int32_t *active);
+
+/* CVs (host double [n][2], s2 = 0 when n_cv == 1) and biases (host double
+ * [n]) of the last batched step; either may be NULL.  Synchronises and
+ * reports the first device error of any system (that context then fails). */
+metad_status metad_batch_read(metad_batch *batch, double *cv_host, double *V_host);
+
+/* Asynchronous form of metad_batch_read: enqueues the copy of, per system,
+ * {s1, s2, V, device error word} (double [n][4]) into out_host (page-locked
+ * memory for a true asynchronous copy) and returns.  The values are valid
+ * once the batch's stream has passed this call; a non-zero error word means
+ * that system's context has failed (its next call reports it). */
+metad_status metad_batch_collect(metad_batch *batch, double *out_host);
+
+/* Kernels launched by batched steps since creation. */
+int64_t metad_batch_launch_count(const metad_batch *batch);
+
+/* Text of the last error recorded on this batch (never NULL). */
+const char *metad_batch_last_error(const metad_batch *batch);
 
 #ifdef __cplusplus
 }

@@ -19,7 +19,12 @@ OUT_DIR = os.path.join(HERE, "_lib")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmetad.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "k_neighbors.cu", "k_cv.cu", "k_bias.cu", "k_batch.cu", "k_static.cu"]
+SOURCES = ["api.cu", "k_neighbors.cu", "k_cv.cu", "k_bias.cu", "k_static.cu"]
+# The FP64 hill and grid arithmetic is compiled without multiply-add
+# contraction: every product and sum rounds on its own, so the single-system
+# and batched instantiations of the hill kernel give the same bits (the
+# compiler may otherwise fuse differently in each).
+FILE_FLAGS = {"k_bias.cu": ["-fmad=false"]}
 
 
 def nvcc() -> str:
@@ -56,7 +61,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         obj = os.path.join(BUILD_DIR, s.replace(".cu", ".o"))
         objs.append(obj)
         if force or _stale(obj, [src] + headers):
-            jobs.append([cc, "-c", src, "-o", obj] + _flags(extra_flags))
+            jobs.append([cc, "-c", src, "-o", obj] + _flags(list(extra_flags) + FILE_FLAGS.get(s, [])))
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -42,6 +42,7 @@ struct metad_ctx {
     std::vector<cudaEvent_t> prof_ev;
     std::vector<int> prof_stage;
     int64_t launches = 0;
+    int64_t device_bytes = 0;  // requested by cudaMalloc for this context
 };
 
 namespace {
@@ -63,12 +64,24 @@ metad_status cuda_check(metad_ctx *c, cudaError_t e, const char *what)
 
 metad_status launched(metad_ctx *c, const char *what) { return cuda_check(c, cudaGetLastError(), what); }
 
-enum Stage { ST_BIN, ST_NBR, ST_CV_FWD, ST_CV_AVG, ST_BIAS, ST_ADJ, ST_FORCE, ST_DEPOSIT, ST_OTHER, ST_COUNT };
+enum Stage {
+    ST_BIN,
+    ST_NBR,
+    ST_CV_FWD,
+    ST_CV_AVG,
+    ST_BIAS,
+    ST_ADJ,
+    ST_FORCE,
+    ST_FGATHER,
+    ST_DEPOSIT,
+    ST_OTHER,
+    ST_COUNT
+};
 // "gather": positions into cell order + rebuild test; "neighbors": the
 // conditional rebuild chain (and a stand-alone exact filter); "cv_fwd" holds
 // the fused exact filter.
-const char *kStageNames[ST_COUNT] = {"gather",  "neighbors", "cv_fwd",  "cv_avg", "bias",
-                                     "adjoint", "force",     "deposit", "other"};
+const char *kStageNames[ST_COUNT] = {"gather",  "neighbors",   "cv_fwd",       "cv_avg",  "bias",
+                                     "adjoint", "force_pairs", "force_gather", "deposit", "other"};
 
 // Brackets the kernels of one stage with CUDA events while profiling is on,
 // and counts the kernels launched.
@@ -101,6 +114,7 @@ metad_status dalloc(metad_ctx *c, T **ptr, size_t count)
         return fail(c, METAD_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
     }
     c->allocs.push_back(p);
+    c->device_bytes += (int64_t)bytes;
     *ptr = static_cast<T *>(p);
     return METAD_OK;
 }
@@ -136,6 +150,8 @@ metad_status check_usable(metad_ctx *c)
     return METAD_OK;
 }
 
+metad_status error_word_status(metad_ctx *c, int e);
+
 // Wait for the stream and turn a recorded device error into a status.
 metad_status sync_and_check(metad_ctx *c)
 {
@@ -144,7 +160,12 @@ metad_status sync_and_check(metad_ctx *c)
     if (s != METAD_OK) return s;
     s = cuda_check(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
     if (s != METAD_OK) return s;
-    int e = *c->err_pinned;
+    return error_word_status(c, *c->err_pinned);
+}
+
+// Turn a device error word into a status (the context fails on any bit).
+metad_status error_word_status(metad_ctx *c, int e)
+{
     if (e) c->failed = true;
     if (e & metad::kErrNonFinite) return fail(c, METAD_ERR_INVALID, "non-finite position");
     if (e & metad::kErrCapacity)
@@ -187,9 +208,136 @@ metad_status validate(const metad_params *p, std::string &why)
     return METAD_OK;
 }
 
+// Host-side geometry and constants of a context's system (no allocation).
+metad_status setup_system(metad_ctx *c)
+{
+    Sys &y = c->sys;
+    const int n = c->p.n_atoms;
+    y.n = n;
+    y.ncv = c->p.n_cv;
+    y.cn_unlike = c->p.cn_pairs ? 1 : 0;
+    y.max_nb = c->p.max_neighbors;
+    for (int a = 0; a < 3; ++a) {
+        const double L = c->p.box[a];
+        y.L[a] = L;
+        split(L, y.Lhi[a], y.Llo[a]);
+        y.halfL[a] = (float)(0.5 * L);
+        // cell edge >= (rc + skin)(1 + 1e-4): float32 cell assignment can
+        // never split a Verlet pair across non-adjacent cells
+        int nc = (int)std::floor(L / ((c->p.rc + c->p.skin) * (1.0 + 1e-4)));
+        if (nc < 1) nc = 1;
+        if (nc > 1023) return METAD_ERR_INVALID;
+        y.nc[a] = nc;
+        y.inv_h[a] = (float)(nc / L);
+    }
+    y.ncell = y.nc[0] * y.nc[1] * y.nc[2];
+    y.rc = c->p.rc;
+    y.rc2 = c->p.rc * c->p.rc;
+    y.rc2_lo = (float)(y.rc2 * (1.0 - 3e-5));
+    y.rc2_hi = (float)(y.rc2 * (1.0 + 3e-5));
+    {
+        const double rv = c->p.rc + c->p.skin;
+        y.rv2 = (float)(rv * rv * (1.0 + 1e-4));
+        const double half = 0.5 * c->p.skin * (1.0 - 1e-3);
+        y.disp_thr2 = (float)(half * half);
+        y.always_rebuild = c->p.skin > 0.0 ? 0 : 1;
+        const double grow = std::pow(rv / c->p.rc, 3.0);
+        y.max_vnb = ((int)std::ceil(y.max_nb * grow) + 7) / 8 * 8;
+    }
+    y.sw_n = c->p.sw_n;
+    y.sw_m = c->p.sw_m;
+    y.sw_nf = (float)c->p.sw_n;
+    y.sw_nd = (double)c->p.sw_n;
+    y.n_f = (float)n;
+    y.n_d = (double)n;
+    y.stretch = c->p.stretch;
+    y.r0 = c->p.r0;
+    y.inv_r0_d = 1.0 / c->p.r0;
+    split(y.inv_r0_d, y.inv_r0_hi, y.inv_r0_lo);
+    const double sc = c->p.stretch ? switch_raw_host(c->p.rc / c->p.r0, c->p.sw_n, c->p.sw_m) : 0.0;
+    y.a_d = 1.0 / (1.0 - sc);
+    y.k_d = sc * y.a_d;
+    split(y.a_d, y.a_hi, y.a_lo);
+    split(y.k_d, y.k_hi, y.k_lo);
+    y.hill_cap = c->p.hill_capacity;
+    y.sigma[0] = c->p.sigma[0];
+    y.sigma[1] = c->p.n_cv == 2 ? c->p.sigma[1] : 1.0;
+    y.w0 = c->p.w0;
+    y.kbdt = c->p.kB * c->p.temperature * (c->p.biasfactor - 1.0);
+    y.grid_on = c->p.grid_on;
+    for (int a = 0; a < 2; ++a) {
+        y.gn[a] = c->p.grid_on ? c->p.grid_n[a] : 2;
+        y.glo[a] = c->p.grid_lo[a];
+        y.ghi[a] = c->p.grid_hi[a];
+        y.gh[a] = c->p.grid_on ? (y.ghi[a] - y.glo[a]) / (y.gn[a] - 1) : 1.0;
+    }
+    // one FP64 partial per block of the per-atom kernels (slot 0: CN, 1: Q6),
+    // three per block of the hill kernel (slot 2), the neighbour statistics
+    // (slot 3)
+    y.part_stride = std::max(metad::group_grid(n), metad::kMaxBiasBlocks * 3);
+    return METAD_OK;
+}
+
+struct Buffers {
+    int *rank_xyz = nullptr, *xyz_rank = nullptr;
+    char *rb = nullptr, *wlb = nullptr, *pfb = nullptr;
+};
+
+// Every device buffer of a context in one list: alloc(&ptr, count) allocates
+// count elements for ptr (or, for the size estimate, only counts them).
+template <class Alloc>
+metad_status state_buffers(metad_ctx *c, Buffers &b, Alloc &&alloc)
+{
+    Sys &y = c->sys;
+    const int n = c->p.n_atoms;
+    const size_t rs = c->fp64 ? sizeof(double) : sizeof(float);
+    const size_t nq = c->p.n_cv == 2 ? (size_t)16 * n : 16;
+    metad_status s;
+    if ((s = alloc(&y.pos_s, n)) || (s = alloc(&y.perm, n)) || (s = alloc(&y.scell, n)) ||
+        (s = alloc(&y.ucell, n)) || (s = alloc(&y.uslot, n)) || (s = alloc(&y.cell_count, y.ncell)) ||
+        (s = alloc(&y.cell_start, (size_t)y.ncell + 1)) || (s = alloc(&y.scan_part, y.ncell / 4096 + 2)) ||
+        (s = alloc(&b.rank_xyz, y.ncell)) || (s = alloc(&b.xyz_rank, y.ncell)) ||
+        (s = alloc(&y.nbr, (size_t)y.max_nb * n)) || (s = alloc(&y.nn, n)) || (s = alloc(&y.nh, n)) ||
+        (s = alloc(&y.vnh, n)) || (s = alloc(&b.wlb, rs * (size_t)y.max_nb * n)) ||
+        (s = alloc(&b.pfb, rs * 4 * (size_t)y.max_nb * n)) || (s = alloc(&y.pos_ref, n)) ||
+        (s = alloc(&y.vnbr, (size_t)y.max_vnb * n)) || (s = alloc(&y.vnn, n)) || (s = alloc(&y.flag, 1)) ||
+        (s = alloc(&y.rebuilds, 1)) || (s = alloc(&b.rb, rs * (nq * 3 + (size_t)n * 4 + 64))) ||
+        (s = alloc(&y.part, (size_t)y.part_stride * 4)) || (s = alloc(&y.ticket, 8)) ||
+        (s = alloc(&y.scal, metad::kNumScal)) || (s = alloc(&y.err, 1)) ||
+        (s = alloc(&y.hc, 2 * (size_t)y.hill_cap + 2)) || (s = alloc(&y.hw, (size_t)y.hill_cap + 1)) ||
+        (s = alloc(&c->stage, 2 * (size_t)y.hill_cap + 2)) || (s = alloc(&y.grid, (size_t)y.gn[0] * y.gn[1] * 4)))
+        return s;
+    return METAD_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+metad_status metad_estimate_bytes(const metad_params *p, int64_t *bytes)
+{
+    if (!bytes) return METAD_ERR_INVALID;
+    *bytes = 0;
+    std::string why;
+    metad_status v = validate(p, why);
+    if (v != METAD_OK) return v;
+    metad_ctx c;
+    c.p = *p;
+    if (c.p.max_neighbors == 0) c.p.max_neighbors = 64;
+    c.p.max_neighbors = (c.p.max_neighbors + 3) / 4 * 4;
+    c.fp64 = c.p.precision == 1;
+    if ((v = setup_system(&c))) return v;
+    Buffers bf;
+    int64_t total = 0;
+    state_buffers(&c, bf, [&total](auto **ptr, size_t count) {
+        total += (int64_t)(sizeof(**ptr) * (count > 0 ? count : 1));
+        return METAD_OK;
+    });
+    *bytes = total;
+    return METAD_OK;
+}
+
+int64_t metad_device_bytes(const metad_ctx *c) { return c ? c->device_bytes : 0; }
 
 void metad_params_default(metad_params *p)
 {
@@ -278,87 +426,21 @@ metad_status metad_create(const metad_params *p, metad_ctx **out)
         if (s != METAD_OK) { metad_destroy(c); return s; }
         c->own_stream = true;
     }
-    Sys &y = c->sys;
-    const int n = c->p.n_atoms;
-    y.n = n;
-    y.ncv = c->p.n_cv;
-    y.cn_unlike = c->p.cn_pairs ? 1 : 0;
-    y.max_nb = c->p.max_neighbors;
-    for (int a = 0; a < 3; ++a) {
-        const double L = c->p.box[a];
-        y.L[a] = L;
-        split(L, y.Lhi[a], y.Llo[a]);
-        y.halfL[a] = (float)(0.5 * L);
-        // cell edge >= (rc + skin)(1 + 1e-4): float32 cell assignment can
-        // never split a Verlet pair across non-adjacent cells
-        int nc = (int)std::floor(L / ((c->p.rc + c->p.skin) * (1.0 + 1e-4)));
-        if (nc < 1) nc = 1;
-        if (nc > 1023) { metad_destroy(c); return METAD_ERR_INVALID; }
-        y.nc[a] = nc;
-        y.inv_h[a] = (float)(nc / L);
-    }
-    y.ncell = y.nc[0] * y.nc[1] * y.nc[2];
-    y.rc = c->p.rc;
-    y.rc2 = c->p.rc * c->p.rc;
-    y.rc2_lo = (float)(y.rc2 * (1.0 - 3e-5));
-    y.rc2_hi = (float)(y.rc2 * (1.0 + 3e-5));
-    {
-        const double rv = c->p.rc + c->p.skin;
-        y.rv2 = (float)(rv * rv * (1.0 + 1e-4));
-        const double half = 0.5 * c->p.skin * (1.0 - 1e-3);
-        y.disp_thr2 = (float)(half * half);
-        y.always_rebuild = c->p.skin > 0.0 ? 0 : 1;
-        const double grow = std::pow(rv / c->p.rc, 3.0);
-        y.max_vnb = ((int)std::ceil(y.max_nb * grow) + 7) / 8 * 8;
-    }
-    y.sw_n = c->p.sw_n;
-    y.sw_m = c->p.sw_m;
-    y.stretch = c->p.stretch;
-    y.r0 = c->p.r0;
-    y.inv_r0_d = 1.0 / c->p.r0;
-    split(y.inv_r0_d, y.inv_r0_hi, y.inv_r0_lo);
-    const double sc = c->p.stretch ? switch_raw_host(c->p.rc / c->p.r0, c->p.sw_n, c->p.sw_m) : 0.0;
-    y.a_d = 1.0 / (1.0 - sc);
-    y.k_d = sc * y.a_d;
-    split(y.a_d, y.a_hi, y.a_lo);
-    split(y.k_d, y.k_hi, y.k_lo);
-    y.hill_cap = c->p.hill_capacity;
-    y.sigma[0] = c->p.sigma[0];
-    y.sigma[1] = c->p.n_cv == 2 ? c->p.sigma[1] : 1.0;
-    y.w0 = c->p.w0;
-    y.kbdt = c->p.kB * c->p.temperature * (c->p.biasfactor - 1.0);
-    y.grid_on = c->p.grid_on;
-    for (int a = 0; a < 2; ++a) {
-        y.gn[a] = c->p.grid_on ? c->p.grid_n[a] : 2;
-        y.glo[a] = c->p.grid_lo[a];
-        y.ghi[a] = c->p.grid_hi[a];
-        y.gh[a] = c->p.grid_on ? (y.ghi[a] - y.glo[a]) / (y.gn[a] - 1) : 1.0;
-    }
-    const size_t rs = c->fp64 ? sizeof(double) : sizeof(float);
-    // one FP64 partial per block of the per-atom kernels (slot 0: CN, 1: Q6),
-    // three per block of the hill kernel (slot 2), the neighbour statistics
-    // (slot 3)
-    y.part_stride = std::max(metad::group_grid(n), metad::kMaxBiasBlocks * 3);
-    const size_t nq = c->p.n_cv == 2 ? (size_t)16 * n : 16;
-    int *rank_xyz = nullptr, *xyz_rank = nullptr;
-    char *rb = nullptr, *wlb = nullptr, *pfb = nullptr;
-    if ((s = dalloc(c, &y.pos_s, n)) || (s = dalloc(c, &y.perm, n)) || (s = dalloc(c, &y.scell, n)) ||
-        (s = dalloc(c, &y.ucell, n)) || (s = dalloc(c, &y.uslot, n)) || (s = dalloc(c, &y.cell_count, y.ncell)) ||
-        (s = dalloc(c, &y.cell_start, (size_t)y.ncell + 1)) || (s = dalloc(c, &y.scan_part, y.ncell / 4096 + 2)) ||
-        (s = dalloc(c, &rank_xyz, y.ncell)) || (s = dalloc(c, &xyz_rank, y.ncell)) ||
-        (s = dalloc(c, &y.nbr, (size_t)y.max_nb * n)) || (s = dalloc(c, &y.nn, n)) || (s = dalloc(c, &y.nh, n)) ||
-        (s = dalloc(c, &y.vnh, n)) || (s = dalloc(c, &wlb, rs * (size_t)y.max_nb * n)) ||
-        (s = dalloc(c, &pfb, rs * 4 * (size_t)y.max_nb * n)) ||
-        (s = dalloc(c, &y.pos_ref, n)) || (s = dalloc(c, &y.vnbr, (size_t)y.max_vnb * n)) ||
-        (s = dalloc(c, &y.vnn, n)) || (s = dalloc(c, &y.flag, 1)) || (s = dalloc(c, &y.rebuilds, 1)) ||
-        (s = dalloc(c, &rb, rs * (nq * 3 + (size_t)n * 4 + 64))) || (s = dalloc(c, &y.part, (size_t)y.part_stride * 4)) ||
-        (s = dalloc(c, &y.ticket, 8)) || (s = dalloc(c, &y.scal, metad::kNumScal)) || (s = dalloc(c, &y.err, 1)) ||
-        (s = dalloc(c, &y.hc, 2 * (size_t)y.hill_cap + 2)) || (s = dalloc(c, &y.hw, (size_t)y.hill_cap + 1)) ||
-        (s = dalloc(c, &c->stage, 2 * (size_t)y.hill_cap + 2)) ||
-        (s = dalloc(c, &y.grid, (size_t)y.gn[0] * y.gn[1] * 4))) {
+    if ((s = setup_system(c))) {
         metad_destroy(c);
         return s;
     }
+    Sys &y = c->sys;
+    const int n = c->p.n_atoms;
+    const size_t rs = c->fp64 ? sizeof(double) : sizeof(float);
+    const size_t nq = c->p.n_cv == 2 ? (size_t)16 * n : 16;
+    Buffers bf;
+    if ((s = state_buffers(c, bf, [c](auto **ptr, size_t count) { return dalloc(c, ptr, count); }))) {
+        metad_destroy(c);
+        return s;
+    }
+    int *rank_xyz = bf.rank_xyz, *xyz_rank = bf.xyz_rank;
+    char *rb = bf.rb, *wlb = bf.wlb, *pfb = bf.pfb;
     // records first (16-element rows stay 64 / 128 B aligned), scalars after
     y.q = rb;
     y.b = rb + rs * nq;
@@ -530,8 +612,12 @@ metad_status metad_bias_forces(metad_ctx *c, float *forces_dev, int32_t accumula
         metad::launch_adjoint(c->sys, c->fp64, c->stream);
     }
     {
-        StageScope t(c, ST_FORCE, metad::force_kernels(c->sys));
-        metad::launch_force(c->sys, c->fp64, forces_dev, accumulate ? 1 : 0, scale, c->stream);
+        StageScope t(c, ST_FORCE, 1);
+        metad::launch_force_pairs(c->sys, c->fp64, scale, c->stream);
+    }
+    {
+        StageScope t(c, ST_FGATHER, 1);
+        metad::launch_force_gather(c->sys, c->fp64, forces_dev, accumulate ? 1 : 0, c->stream);
     }
     return launched(c, "bias_forces");
 }
@@ -864,5 +950,229 @@ metad_status metad_sync(metad_ctx *c)
     if (s) return s;
     return sync_and_check(c);
 }
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batches
+
+struct metad_batch {
+    std::vector<metad_ctx *> ctx;
+    int n = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0, fp64 = 0, ncv = 2;
+    int persist_cap = 0;
+    // device: descriptors [n], then the block prefix rows [kGridKinds][n + 1]
+    char *dev = nullptr;
+    size_t sys_bytes = 0, table_bytes = 0;
+    double *dout = nullptr;  // [n][4] collected results
+    // pinned host ring of descriptor tables: slot k is rewritten only after
+    // the copy that last read it has run
+    static constexpr int kRing = 4;
+    char *host[kRing] = {};
+    cudaEvent_t ev[kRing] = {};
+    int slot = 0;
+    double *hout = nullptr;
+    int64_t launches = 0;
+    bool stepped = false;  // the device table holds the last step's descriptors
+    std::string last_error;
+};
+
+namespace {
+
+metad_status batch_fail(metad_batch *b, metad_status s, const std::string &msg)
+{
+    if (b) b->last_error = msg;
+    return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+metad_status metad_batch_destroy(metad_batch *b)
+{
+    if (!b) return METAD_OK;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (int k = 0; k < metad_batch::kRing; ++k) {
+        if (b->ev[k]) cudaEventDestroy(b->ev[k]);
+        if (b->host[k]) cudaFreeHost(b->host[k]);
+    }
+    if (b->hout) cudaFreeHost(b->hout);
+    if (b->dev) cudaFree(b->dev);
+    if (b->dout) cudaFree(b->dout);
+    cudaGetLastError();
+    delete b;
+    return METAD_OK;
+}
+
+metad_status metad_batch_create(metad_ctx *const *ctxs, int32_t n, metad_batch **out)
+{
+    if (!out) return METAD_ERR_INVALID;
+    *out = nullptr;
+    if (!ctxs || n < 1) return METAD_ERR_INVALID;
+    for (int k = 0; k < n; ++k) {
+        const metad_ctx *c = ctxs[k];
+        if (!c || c->failed) return METAD_ERR_INVALID;
+        if (c->p.device != ctxs[0]->p.device || c->stream != ctxs[0]->stream || c->p.n_cv != ctxs[0]->p.n_cv ||
+            c->fp64 != ctxs[0]->fp64)
+            return METAD_ERR_INVALID;
+    }
+    metad_batch *b = new (std::nothrow) metad_batch();
+    if (!b) return METAD_ERR_OOM;
+    b->ctx.assign(ctxs, ctxs + n);
+    b->n = n;
+    b->stream = ctxs[0]->stream;
+    b->device = ctxs[0]->p.device;
+    b->fp64 = ctxs[0]->fp64;
+    b->ncv = ctxs[0]->p.n_cv;
+    if (cudaSetDevice(b->device) != cudaSuccess) {
+        metad_batch_destroy(b);
+        return METAD_ERR_CUDA;
+    }
+    b->sys_bytes = (sizeof(Sys) * (size_t)n + 255) / 256 * 256;
+    b->table_bytes = b->sys_bytes + sizeof(int) * (size_t)metad::kGridKinds * (n + 1);
+    bool ok = cudaMalloc(&b->dev, b->table_bytes) == cudaSuccess &&
+              cudaMalloc(&b->dout, sizeof(double) * 4 * (size_t)n) == cudaSuccess &&
+              cudaMallocHost(&b->hout, sizeof(double) * 4 * (size_t)n) == cudaSuccess;
+    for (int k = 0; ok && k < metad_batch::kRing; ++k)
+        ok = cudaMallocHost(&b->host[k], b->table_bytes) == cudaSuccess &&
+             cudaEventCreateWithFlags(&b->ev[k], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        metad_batch_destroy(b);
+        return METAD_ERR_OOM;
+    }
+    *out = b;
+    return METAD_OK;
+}
+
+metad_status metad_batch_set_tile(metad_batch *b, int32_t blocks_per_system)
+{
+    if (!b || blocks_per_system < 0) return METAD_ERR_INVALID;
+    b->persist_cap = blocks_per_system;
+    return METAD_OK;
+}
+
+metad_status metad_batch_step(metad_batch *b, const float *const *pos_dev, float *const *forces_dev,
+                              int32_t accumulate, const int32_t *deposit, const int32_t *active)
+{
+    if (!b || !pos_dev || !forces_dev) return METAD_ERR_INVALID;
+    const int n = b->n;
+    bool any_deposit = false, any_active = false;
+    for (int k = 0; k < n; ++k) {
+        if (active && !active[k]) continue;
+        any_active = true;
+        metad_ctx *c = b->ctx[k];
+        if (c->failed) return batch_fail(b, METAD_ERR_STATE, "system " + std::to_string(k) + " has failed");
+        if (!pos_dev[k] || !forces_dev[k]) return batch_fail(b, METAD_ERR_INVALID, "NULL buffer");
+        if (deposit && deposit[k]) {
+            if (c->K >= c->p.hill_capacity)
+                return batch_fail(b, METAD_ERR_CAPACITY, "hill list of system " + std::to_string(k) + " full");
+            any_deposit = true;
+        }
+    }
+    if (!any_active) return METAD_OK;
+    if (cudaSetDevice(b->device) != cudaSuccess) return batch_fail(b, METAD_ERR_CUDA, "cudaSetDevice");
+    const int slot = b->slot;
+    b->slot = (slot + 1) % metad_batch::kRing;
+    if (cudaEventSynchronize(b->ev[slot]) != cudaSuccess) return batch_fail(b, METAD_ERR_CUDA, "ring event");
+    Sys *hs = reinterpret_cast<Sys *>(b->host[slot]);
+    int *pre = reinterpret_cast<int *>(b->host[slot] + b->sys_bytes);
+    int totals[metad::kGridKinds];
+    for (int g = 0; g < metad::kGridKinds; ++g) pre[g * (n + 1)] = 0;
+    for (int k = 0; k < n; ++k) {
+        metad_ctx *c = b->ctx[k];
+        const bool on = !active || active[k];
+        if (on) c->sys.pos_in = reinterpret_cast<const float4 *>(pos_dev[k]);
+        Sys y = c->sys;
+        y.K = c->K;
+        y.deposit = on && deposit && deposit[k] ? 1 : 0;
+        y.F_out = on ? forces_dev[k] : nullptr;
+        y.accumulate = accumulate ? 1 : 0;
+        y.fscale = 1.0;
+        hs[k] = y;
+        for (int g = 0; g < metad::kGridKinds; ++g)
+            pre[g * (n + 1) + k + 1] = pre[g * (n + 1) + k] + (on ? metad::grid_blocks(y, g, b->persist_cap) : 0);
+    }
+    for (int g = 0; g < metad::kGridKinds; ++g) totals[g] = pre[g * (n + 1) + n];
+    if (cudaMemcpyAsync(b->dev, b->host[slot], b->table_bytes, cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+        cudaEventRecord(b->ev[slot], b->stream) != cudaSuccess)
+        return batch_fail(b, METAD_ERR_CUDA, "descriptor upload");
+    const Sys *dsys = reinterpret_cast<const Sys *>(b->dev);
+    const int *dpre = reinterpret_cast<const int *>(b->dev + b->sys_bytes);
+    metad::BatchView rows[metad::kGridKinds];
+    for (int g = 0; g < metad::kGridKinds; ++g) rows[g] = metad::BatchView{dsys, dpre + g * (n + 1), n};
+    metad::launch_batch_gather(rows[metad::GK_ATOM256], totals[metad::GK_ATOM256], b->stream);
+    metad::launch_batch_rebuild(rows, totals, b->stream);
+    metad::launch_batch_cv(rows[metad::GK_PERSIST], totals[metad::GK_PERSIST], b->fp64, b->ncv, b->stream);
+    metad::launch_batch_bias(rows[metad::GK_HILLS], totals[metad::GK_HILLS], 0, b->stream);
+    metad::launch_batch_force(rows[metad::GK_PERSIST], totals[metad::GK_PERSIST], b->fp64, b->ncv, b->stream);
+    if (any_deposit) metad::launch_batch_bias(rows[metad::GK_DEPOSIT], totals[metad::GK_DEPOSIT], 1, b->stream);
+    b->launches += 1 + 8 + (b->ncv == 2 ? 2 : 1) + 1 + (b->ncv == 2 ? 3 : 2) + (any_deposit ? 1 : 0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        for (metad_ctx *c : b->ctx) c->failed = true;
+        return batch_fail(b, METAD_ERR_CUDA, std::string("batched launch: ") + cudaGetErrorString(e));
+    }
+    for (int k = 0; k < n; ++k) {
+        if (active && !active[k]) continue;
+        metad_ctx *c = b->ctx[k];
+        c->have_nbr = c->have_cv = c->have_bias = true;
+        c->filter_pending = false;
+        if (deposit && deposit[k]) c->K += 1;
+    }
+    b->stepped = true;
+    return METAD_OK;
+}
+
+metad_status metad_batch_read(metad_batch *b, double *cv_host, double *V_host)
+{
+    if (!b) return METAD_ERR_INVALID;
+    if (!b->stepped) return batch_fail(b, METAD_ERR_STATE, "batch_read before batch_step");
+    if (cudaSetDevice(b->device) != cudaSuccess) return batch_fail(b, METAD_ERR_CUDA, "cudaSetDevice");
+    const metad::BatchView v{reinterpret_cast<const Sys *>(b->dev), nullptr, b->n};
+    metad::launch_batch_collect(v, b->dout, b->stream);
+    b->launches += 1;
+    if (cudaMemcpyAsync(b->hout, b->dout, sizeof(double) * 4 * (size_t)b->n, cudaMemcpyDeviceToHost, b->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess)
+        return batch_fail(b, METAD_ERR_CUDA, "batch read");
+    metad_status first = METAD_OK;
+    for (int k = 0; k < b->n; ++k) {
+        const int e = (int)b->hout[4 * k + 3];
+        if (e) {
+            metad_status s = error_word_status(b->ctx[k], e);
+            if (first == METAD_OK) {
+                first = s;
+                b->last_error = "system " + std::to_string(k) + ": " + b->ctx[k]->last_error;
+            }
+        }
+        if (cv_host) {
+            cv_host[2 * k] = b->hout[4 * k];
+            cv_host[2 * k + 1] = b->ncv == 2 ? b->hout[4 * k + 1] : 0.0;
+        }
+        if (V_host) V_host[k] = b->hout[4 * k + 2];
+    }
+    return first;
+}
+
+metad_status metad_batch_collect(metad_batch *b, double *out_host)
+{
+    if (!b || !out_host) return METAD_ERR_INVALID;
+    if (!b->stepped) return batch_fail(b, METAD_ERR_STATE, "batch_collect before batch_step");
+    if (cudaSetDevice(b->device) != cudaSuccess) return batch_fail(b, METAD_ERR_CUDA, "cudaSetDevice");
+    const metad::BatchView v{reinterpret_cast<const Sys *>(b->dev), nullptr, b->n};
+    metad::launch_batch_collect(v, b->dout, b->stream);
+    b->launches += 1;
+    if (cudaMemcpyAsync(out_host, b->dout, sizeof(double) * 4 * (size_t)b->n, cudaMemcpyDeviceToHost, b->stream) !=
+        cudaSuccess)
+        return batch_fail(b, METAD_ERR_CUDA, "batch collect");
+    return METAD_OK;
+}
+
+int64_t metad_batch_launch_count(const metad_batch *b) { return b ? b->launches : 0; }
+
+const char *metad_batch_last_error(const metad_batch *b) { return b ? b->last_error.c_str() : "null batch"; }
 
 }  // extern "C"

@@ -7,6 +7,8 @@
 // The hill sum is spread over many blocks (FP64 throughput per SM is low on
 // this part) and finished by the last block to arrive, which adds the
 // partials in block order, so the result is independent of scheduling.
+// This file is compiled with -fmad=false: no multiply-add contraction, so
+// the single-system and batched kernels round every operation alike.
 #include "metad_impl.cuh"
 
 namespace metad {
@@ -57,13 +59,16 @@ __device__ void grid_value(const Sys &s, double x0, double x1, double &V, double
     g1 /= h1;
 }
 
-__global__ void __launch_bounds__(kBlockBias) k_bias(Sys s, int K, const double *x_dev, double *out, int deposit)
+// V and dV/ds at s.bias_x into s.bias_out; with s.deposit, also appends the
+// well-tempered hill there as hill s.K.
+__device__ __forceinline__ void bias(const Sys &s, Blk blk)
 {
-    const double x0 = x_dev[0];
-    const double x1 = s.ncv == 2 ? x_dev[1] : 0.0;
+    const int K = s.K;
+    const double x0 = s.bias_x[0];
+    const double x1 = s.ncv == 2 ? s.bias_x[1] : 0.0;
     const double inv2v0 = 0.5 / (s.sigma[0] * s.sigma[0]), inv2v1 = 0.5 / (s.sigma[1] * s.sigma[1]);
     double V = 0.0, g0 = 0.0, g1 = 0.0;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
+    for (int k = blk.b * blockDim.x + threadIdx.x; k < K; k += blk.nb * blockDim.x) {
         const double d0 = x0 - s.hc[2 * (size_t)k];
         double e = d0 * d0 * inv2v0;
         double d1 = 0.0;
@@ -92,18 +97,18 @@ __global__ void __launch_bounds__(kBlockBias) k_bias(Sys s, int K, const double 
     if (threadIdx.x == 0) {
         double a = 0.0, b = 0.0, c = 0.0;
         for (int w = 0; w < kBlockBias / 32; ++w) { a += sh[0][w]; b += sh[1][w]; c += sh[2][w]; }
-        part[3 * blockIdx.x + 0] = a;
-        part[3 * blockIdx.x + 1] = b;
-        part[3 * blockIdx.x + 2] = c;
+        part[3 * blk.b + 0] = a;
+        part[3 * blk.b + 1] = b;
+        part[3 * blk.b + 2] = c;
         __threadfence();
         unsigned prev = atomicAdd(&s.ticket[2], 1u);
-        am_last = (prev == gridDim.x - 1);
+        am_last = (prev == (unsigned)blk.nb - 1u);
     }
     __syncthreads();
     if (!am_last || threadIdx.x != 0) return;
     __threadfence();
     double a = 0.0, b = 0.0, c = 0.0;
-    for (int q = 0; q < (int)gridDim.x; ++q) {
+    for (int q = 0; q < blk.nb; ++q) {
         a += __ldcg(part + 3 * q);
         b += __ldcg(part + 3 * q + 1);
         c += __ldcg(part + 3 * q + 2);
@@ -115,17 +120,44 @@ __global__ void __launch_bounds__(kBlockBias) k_bias(Sys s, int K, const double 
         b += gg0;
         c += gg1;
     }
+    double *out = s.bias_out;
     out[0] = a;
     out[1] = b;
     out[2] = c;
     s.ticket[2] = 0u;
-    if (deposit) {
+    if (s.deposit) {
         const double w = s.w0 * exp(-a / s.kbdt);
         s.hc[2 * (size_t)K] = x0;
         s.hc[2 * (size_t)K + 1] = x1;
         s.hw[K] = w;
         s.scal[kDepW] = w;
     }
+}
+
+__global__ void __launch_bounds__(kBlockBias) k_bias(Sys s) { bias(s, own_blk()); }
+
+// Batched: every system evaluates at its own CVs (deposit 0) or deposits a
+// hill there (deposit 1; only systems with s.deposit have blocks).
+__global__ void __launch_bounds__(kBlockBias) kb_bias(BatchView v, int deposit)
+{
+    Blk k;
+    Sys s = v.sys[batch_system(v, k)];
+    s.bias_x = s.scal + kS0;
+    s.bias_out = s.scal + (deposit ? kDepV : kV);
+    s.deposit = deposit;
+    bias(s, k);
+}
+
+// One thread per system: s1, s2, V and the error word, for one copy to the host.
+__global__ void kb_collect(const Sys *sys, int nsys, double *out)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nsys) return;
+    const Sys &s = sys[k];
+    out[4 * k + 0] = s.scal[kS0];
+    out[4 * k + 1] = s.scal[kS1];
+    out[4 * k + 2] = s.scal[kV];
+    out[4 * k + 3] = (double)*s.err;
 }
 
 // One thread per grid node: exact sums over hills [0, K).
@@ -164,7 +196,22 @@ int bias_blocks(int K)
 
 void launch_bias(const Sys &s, int K, const double *x_dev, double *out_dev, int deposit, cudaStream_t st)
 {
-    k_bias<<<bias_blocks(K), kBlockBias, 0, st>>>(s, K, x_dev, out_dev, deposit);
+    Sys t = s;
+    t.K = K;
+    t.bias_x = x_dev;
+    t.bias_out = out_dev;
+    t.deposit = deposit;
+    k_bias<<<bias_blocks(K), kBlockBias, 0, st>>>(t);
+}
+
+void launch_batch_bias(const BatchView &v, int total, int deposit, cudaStream_t st)
+{
+    if (total > 0) kb_bias<<<total, kBlockBias, 0, st>>>(v, deposit);
+}
+
+void launch_batch_collect(const BatchView &v, double *out, cudaStream_t st)
+{
+    kb_collect<<<(v.nsys + 127) / 128, 128, 0, st>>>(v.sys, v.nsys, out);
 }
 
 void launch_grid_fold(const Sys &s, int K, cudaStream_t st)

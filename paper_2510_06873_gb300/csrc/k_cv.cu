@@ -251,21 +251,21 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
 // Block partial -> part[slot * part_stride + block]; the last block to finish
 // sums all partials in block order (fixed, independent of completion order)
 // and stores total * scale in *dst.
-__device__ void last_block_reduce(const Sys &s, double v, int slot, double *dst, double scale)
+__device__ void last_block_reduce(const Sys &s, Blk k, double v, int slot, double *dst, double scale)
 {
     __shared__ double sh[32];
     __shared__ bool am_last;
-    if (gridDim.x > (unsigned)s.part_stride) {  // never with group_grid(); refuse rather than overrun
-        if (blockIdx.x == 0 && threadIdx.x == 0) set_err(s, kErrInternal);
+    if (k.nb > s.part_stride) {  // never with group_grid(); refuse rather than overrun
+        if (k.b == 0 && threadIdx.x == 0) set_err(s, kErrInternal);
         return;
     }
     double t = block_sum(v, sh);
     double *part = s.part + (size_t)slot * s.part_stride;
     if (threadIdx.x == 0) {
-        part[blockIdx.x] = t;
+        part[k.b] = t;
         __threadfence();
         unsigned prev = atomicAdd(&s.ticket[slot], 1u);
-        am_last = (prev == gridDim.x - 1);
+        am_last = (prev == (unsigned)k.nb - 1u);
     }
     __syncthreads();
     if (!am_last) return;
@@ -273,7 +273,7 @@ __device__ void last_block_reduce(const Sys &s, double v, int slot, double *dst,
     double acc = 0.0;
     // each thread sums a contiguous chunk in order; chunks are then added in
     // thread order: a fixed association for a given grid size
-    const int nb = gridDim.x, per = (nb + blockDim.x - 1) / blockDim.x;
+    const int nb = k.nb, per = (nb + blockDim.x - 1) / blockDim.x;
     for (int b = threadIdx.x * per; b < min(nb, (int)(threadIdx.x + 1) * per); ++b) acc += __ldcg(part + b);
     __shared__ double all[kBlockAtoms];
     all[threadIdx.x] = acc;
@@ -440,13 +440,23 @@ __device__ __forceinline__ double cv_fwd_group(const Sys &s, const AtomLane a)
 }
 
 template <typename real, bool kFilter>
-__global__ void __launch_bounds__(kBlockAtoms) k_cv_fwd(Sys s)
+__device__ __forceinline__ void cv_fwd(const Sys &s, Blk k)
 {
     double acc = 0.0;
-    int b0, b1;
-    group_chunk(s.n, b0, b1);
-    for (int blk = b0; blk < b1; blk += gridDim.x) acc += cv_fwd_group<real, kFilter>(s, atom_lane_at(s, blk));
-    last_block_reduce(s, acc, 0, s.scal + kS0, 1.0 / s.n);
+    const int groups = group_grid(s.n);
+    for (int blk = k.b; blk < groups; blk += k.nb) acc += cv_fwd_group<real, kFilter>(s, atom_lane_at(s, blk));
+    last_block_reduce(s, k, acc, 0, s.scal + kS0, 1.0 / s.n);
+}
+
+template <typename real, bool kFilter>
+__global__ void __launch_bounds__(kBlockAtoms) k_cv_fwd(Sys s) { cv_fwd<real, kFilter>(s, own_blk()); }
+
+template <typename real>
+__global__ void __launch_bounds__(kBlockAtoms) kb_cv_fwd(BatchView v)
+{
+    Blk k;
+    const Sys &s = v.sys[batch_system(v, k)];
+    cv_fwd<real, true>(s, k);
 }
 
 // a5: qbar_m(i), qbar6(i), s2.  Record b: b_m(i) = K_m qbar_m(i) / (N qbar6
@@ -485,7 +495,7 @@ __device__ __forceinline__ double cv_avg_group(const Sys &s, const AtomLane a)
     }
     sq = group_sum<real>(sq);
     const real qb6 = sqrt(sq);
-    const real ci = qb6 > real(0) ? inv_D / (real(s.n) * qb6) : real(0);
+    const real ci = qb6 > real(0) ? inv_D / (n_real<real>(s) * qb6) : real(0);
     const int m0 = 2 * a.l, m1 = 2 * a.l + 1;
     real b0 = m0 < kNY ? ci * kweight<real>(m0) * qb0 : real(0);
     real b1 = m1 < kNY ? ci * kweight<real>(m1) * qb1 : real(0);
@@ -502,13 +512,23 @@ __device__ __forceinline__ double cv_avg_group(const Sys &s, const AtomLane a)
 }
 
 template <typename real>
-__global__ void __launch_bounds__(kBlockAtoms) k_cv_avg(Sys s)
+__device__ __forceinline__ void cv_avg(const Sys &s, Blk k)
 {
     double acc = 0.0;
-    int b0, b1;
-    group_chunk(s.n, b0, b1);
-    for (int blk = b0; blk < b1; blk += gridDim.x) acc += cv_avg_group<real>(s, atom_lane_at(s, blk));
-    last_block_reduce(s, acc, 1, s.scal + kS1, 1.0 / s.n);
+    const int groups = group_grid(s.n);
+    for (int blk = k.b; blk < groups; blk += k.nb) acc += cv_avg_group<real>(s, atom_lane_at(s, blk));
+    last_block_reduce(s, k, acc, 1, s.scal + kS1, 1.0 / s.n);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kBlockAtoms) k_cv_avg(Sys s) { cv_avg<real>(s, own_blk()); }
+
+template <typename real>
+__global__ void __launch_bounds__(kBlockAtoms) kb_cv_avg(BatchView v)
+{
+    Blk k;
+    const Sys &s = v.sys[batch_system(v, k)];
+    cv_avg<real>(s, k);
 }
 
 // a7: g_m(k) = b_m(k) + sum_i w_ik b_m(i) ; h = g / W ; record h holds h_m
@@ -565,11 +585,21 @@ __device__ __forceinline__ void adjoint_group(const Sys &s, const AtomLane a)
 }
 
 template <typename real>
-__global__ void __launch_bounds__(kBlockAtoms) k_adjoint(Sys s)
+__device__ __forceinline__ void adjoint(const Sys &s, Blk k)
 {
-    int b0, b1;
-    group_chunk(s.n, b0, b1);
-    for (int blk = b0; blk < b1; blk += gridDim.x) adjoint_group<real>(s, atom_lane_at(s, blk));
+    const int groups = group_grid(s.n);
+    for (int blk = k.b; blk < groups; blk += k.nb) adjoint_group<real>(s, atom_lane_at(s, blk));
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kBlockAtoms) k_adjoint(Sys s) { adjoint<real>(s, own_blk()); }
+
+template <typename real>
+__global__ void __launch_bounds__(kBlockAtoms) kb_adjoint(BatchView v)
+{
+    Blk k;
+    const Sys &s = v.sys[batch_system(v, k)];
+    adjoint<real>(s, k);
 }
 
 // a8, pass 1: for every unordered pair, from the row of its lower index i
@@ -593,14 +623,12 @@ __device__ __forceinline__ void store_pair_force<double>(double *slot, double fx
 }
 
 template <typename real>
-__device__ __forceinline__ void force_pairs_group(const Sys &s, const AtomLane a, double scale)
+__device__ __forceinline__ void force_pairs_group(const Sys &s, const AtomLane a, real cn_fac, real V2)
 {
     if (!a.ok) return;
     const int nh = s.nh[a.i];
     if (a.l >= nh) return;
-    const real cn_fac = (real)(s.scal[kDV0] * scale * 2.0 / s.n);
     const bool q6 = s.ncv == 2;
-    const real V2 = q6 ? (real)(s.scal[kDV1] * scale) : real(0);
     const real *hh = R<real>(s.h), *qq = R<real>(s.q), *qbb = R<real>(s.b);
     const float4 pi = s.pos_s[a.i];
     real hi[kRec], qi[kRec], qbi[kRec];
@@ -649,11 +677,24 @@ __device__ __forceinline__ void force_pairs_group(const Sys &s, const AtomLane a
 }
 
 template <typename real>
-__global__ void __launch_bounds__(kBlockAtoms) k_force_pairs(Sys s, double scale)
+__device__ __forceinline__ void force_pairs(const Sys &s, Blk k)
 {
-    int b0, b1;
-    group_chunk(s.n, b0, b1);
-    for (int blk = b0; blk < b1; blk += gridDim.x) force_pairs_group<real>(s, atom_lane_at(s, blk), scale);
+    // the chain-rule factors of the two CVs, once per thread (FP64 is slow here)
+    const real cn_fac = (real)(s.scal[kDV0] * s.fscale * 2.0 / s.n);
+    const real V2 = s.ncv == 2 ? (real)(s.scal[kDV1] * s.fscale) : real(0);
+    const int groups = group_grid(s.n);
+    for (int blk = k.b; blk < groups; blk += k.nb) force_pairs_group<real>(s, atom_lane_at(s, blk), cn_fac, V2);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kBlockAtoms) k_force_pairs(Sys s) { force_pairs<real>(s, own_blk()); }
+
+template <typename real>
+__global__ void __launch_bounds__(kBlockAtoms) kb_force_pairs(BatchView v)
+{
+    Blk k;
+    const Sys &s = v.sys[batch_system(v, k)];
+    force_pairs<real>(s, k);
 }
 
 template <typename real>
@@ -736,11 +777,21 @@ __device__ __forceinline__ void force_gather_group(const Sys &s, const AtomLane 
 }
 
 template <typename real>
-__global__ void __launch_bounds__(kBlockAtoms) k_force_gather(Sys s, float *F, int accumulate)
+__device__ __forceinline__ void force_gather(const Sys &s, Blk k)
 {
-    int b0, b1;
-    group_chunk(s.n, b0, b1);
-    for (int blk = b0; blk < b1; blk += gridDim.x) force_gather_group<real>(s, atom_lane_at(s, blk), F, accumulate);
+    const int groups = group_grid(s.n);
+    for (int blk = k.b; blk < groups; blk += k.nb) force_gather_group<real>(s, atom_lane_at(s, blk), s.F_out, s.accumulate);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kBlockAtoms) k_force_gather(Sys s) { force_gather<real>(s, own_blk()); }
+
+template <typename real>
+__global__ void __launch_bounds__(kBlockAtoms) kb_force_gather(BatchView v)
+{
+    Blk k;
+    const Sys &s = v.sys[batch_system(v, k)];
+    force_gather<real>(s, k);
 }
 
 template <typename real>
@@ -789,19 +840,52 @@ void launch_adjoint(const Sys &s, int fp64, cudaStream_t st)
         k_adjoint<float><<<atom_blocks(s.n), kBlockAtoms, 0, st>>>(s);
 }
 
-void launch_force(const Sys &s, int fp64, float *F, int accumulate, double scale, cudaStream_t st)
+void launch_force_pairs(const Sys &s, int fp64, double scale, cudaStream_t st)
 {
-    const int nb = atom_blocks(s.n);
+    Sys t = s;
+    t.fscale = scale;
+    if (fp64)
+        k_force_pairs<double><<<atom_blocks(s.n), kBlockAtoms, 0, st>>>(t);
+    else
+        k_force_pairs<float><<<atom_blocks(s.n), kBlockAtoms, 0, st>>>(t);
+}
+
+void launch_force_gather(const Sys &s, int fp64, float *F, int accumulate, cudaStream_t st)
+{
+    Sys t = s;
+    t.F_out = F;
+    t.accumulate = accumulate;
+    if (fp64)
+        k_force_gather<double><<<atom_blocks(s.n), kBlockAtoms, 0, st>>>(t);
+    else
+        k_force_gather<float><<<atom_blocks(s.n), kBlockAtoms, 0, st>>>(t);
+}
+
+void launch_batch_cv(const BatchView &v, int total, int fp64, int ncv, cudaStream_t st)
+{
+    if (total <= 0) return;
     if (fp64) {
-        k_force_pairs<double><<<nb, kBlockAtoms, 0, st>>>(s, scale);
-        k_force_gather<double><<<nb, kBlockAtoms, 0, st>>>(s, F, accumulate);
+        kb_cv_fwd<double><<<total, kBlockAtoms, 0, st>>>(v);
+        if (ncv == 2) kb_cv_avg<double><<<total, kBlockAtoms, 0, st>>>(v);
     } else {
-        k_force_pairs<float><<<nb, kBlockAtoms, 0, st>>>(s, scale);
-        k_force_gather<float><<<nb, kBlockAtoms, 0, st>>>(s, F, accumulate);
+        kb_cv_fwd<float><<<total, kBlockAtoms, 0, st>>>(v);
+        if (ncv == 2) kb_cv_avg<float><<<total, kBlockAtoms, 0, st>>>(v);
     }
 }
 
-int force_kernels(const Sys &) { return 2; }
+void launch_batch_force(const BatchView &v, int total, int fp64, int ncv, cudaStream_t st)
+{
+    if (total <= 0) return;
+    if (fp64) {
+        if (ncv == 2) kb_adjoint<double><<<total, kBlockAtoms, 0, st>>>(v);
+        kb_force_pairs<double><<<total, kBlockAtoms, 0, st>>>(v);
+        kb_force_gather<double><<<total, kBlockAtoms, 0, st>>>(v);
+    } else {
+        if (ncv == 2) kb_adjoint<float><<<total, kBlockAtoms, 0, st>>>(v);
+        kb_force_pairs<float><<<total, kBlockAtoms, 0, st>>>(v);
+        kb_force_gather<float><<<total, kBlockAtoms, 0, st>>>(v);
+    }
+}
 
 // The gather kernels without shared memory prefer the SM's unified storage
 // as L1.  (Kernels with even a small static shared array are left to the
@@ -812,6 +896,9 @@ void configure_kernels()
     cudaFuncSetAttribute(k_adjoint<float>, cudaFuncAttributePreferredSharedMemoryCarveout, l1);
     cudaFuncSetAttribute(k_force_pairs<float>, cudaFuncAttributePreferredSharedMemoryCarveout, l1);
     cudaFuncSetAttribute(k_force_gather<float>, cudaFuncAttributePreferredSharedMemoryCarveout, l1);
+    cudaFuncSetAttribute(kb_adjoint<float>, cudaFuncAttributePreferredSharedMemoryCarveout, l1);
+    cudaFuncSetAttribute(kb_force_pairs<float>, cudaFuncAttributePreferredSharedMemoryCarveout, l1);
+    cudaFuncSetAttribute(kb_force_gather<float>, cudaFuncAttributePreferredSharedMemoryCarveout, l1);
     cudaGetLastError();
 }
 

@@ -50,9 +50,9 @@ __device__ __forceinline__ int cell_axis(float x, float inv_h, int nc)
 
 // Current positions in the cell order of the last rebuild, and the rebuild
 // test.  Before the first rebuild the flag is already set.
-__global__ void k_gather_check(Sys s)
+__device__ __forceinline__ void gather_check(const Sys &s, Blk k)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = k.b * blockDim.x + threadIdx.x;
     bool move = false;
     if (t < s.n) {
         bool bad;
@@ -68,11 +68,12 @@ __global__ void k_gather_check(Sys s)
     if (__any_sync(0xffffffffu, move) && (threadIdx.x & 31) == 0) atomicOr(s.flag, 1);
 }
 
-__global__ void k_rebuild_zero(Sys s)
+__global__ void k_gather_check(Sys s) { gather_check(s, own_blk()); }
+
+__device__ __forceinline__ void rebuild_zero(const Sys &s, Blk k)
 {
     if (!*s.flag) return;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < s.ncell; c += gridDim.x * blockDim.x)
-        s.cell_count[c] = 0;
+    for (int c = k.b * blockDim.x + threadIdx.x; c < s.ncell; c += k.nb * blockDim.x) s.cell_count[c] = 0;
 }
 
 __device__ __forceinline__ void bin_one(const Sys &s, int u)
@@ -87,11 +88,10 @@ __device__ __forceinline__ void bin_one(const Sys &s, int u)
     s.uslot[u] = atomicAdd(&s.cell_count[c], 1);
 }
 
-__global__ void k_bin_count(Sys s)
+__device__ __forceinline__ void bin_count(const Sys &s, Blk k)
 {
     if (!*s.flag) return;
-    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < s.n; u += gridDim.x * blockDim.x)
-        bin_one(s, u);
+    for (int u = k.b * blockDim.x + threadIdx.x; u < s.n; u += k.nb * blockDim.x) bin_one(s, u);
 }
 
 constexpr int kScanThreads = 1024;
@@ -127,55 +127,55 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *warp_sums, int &
     return r;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(Sys s)
+__device__ __forceinline__ void scan_reduce(const Sys &s, Blk k)
 {
     if (!*s.flag) return;
     __shared__ int ws[33];
-    int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    int base = k.b * kScanTile + threadIdx.x * kScanItems;
     int v = 0;
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k)
-        if (base + k < s.ncell) v += s.cell_count[base + k];
+    for (int t = 0; t < kScanItems; ++t)
+        if (base + t < s.ncell) v += s.cell_count[base + t];
     int total;
     block_exclusive_scan(v, ws, total);
-    if (threadIdx.x == 0) s.scan_part[blockIdx.x] = total;
+    if (threadIdx.x == 0) s.scan_part[k.b] = total;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_down(Sys s)
+__device__ __forceinline__ void scan_down(const Sys &s, Blk k)
 {
     if (!*s.flag) return;
     __shared__ int ws[33];
     __shared__ int prefix;
     if (threadIdx.x < 32) {
         int acc = 0;
-        for (int b = threadIdx.x; b < (int)blockIdx.x; b += 32) acc += s.scan_part[b];
+        for (int b = threadIdx.x; b < k.b; b += 32) acc += s.scan_part[b];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (threadIdx.x == 0) prefix = acc;
     }
     __syncthreads();
-    int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    int base = k.b * kScanTile + threadIdx.x * kScanItems;
     int c[kScanItems];
     int v = 0;
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        c[k] = (base + k < s.ncell) ? s.cell_count[base + k] : 0;
-        v += c[k];
+    for (int t = 0; t < kScanItems; ++t) {
+        c[t] = (base + t < s.ncell) ? s.cell_count[base + t] : 0;
+        v += c[t];
     }
     int total;
     int ex = block_exclusive_scan(v, ws, total) + prefix;
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        if (base + k < s.ncell) s.cell_start[base + k] = ex;
-        ex += c[k];
+    for (int t = 0; t < kScanItems; ++t) {
+        if (base + t < s.ncell) s.cell_start[base + t] = ex;
+        ex += c[t];
     }
     if (base <= s.ncell - 1 && s.ncell - 1 < base + kScanItems) s.cell_start[s.ncell] = s.n;
 }
 
-__global__ void k_bin_scatter(Sys s)
+__device__ __forceinline__ void bin_scatter(const Sys &s, Blk k)
 {
     if (!*s.flag) return;
-    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < s.n; u += gridDim.x * blockDim.x)
+    for (int u = k.b * blockDim.x + threadIdx.x; u < s.n; u += k.nb * blockDim.x)
         s.perm[s.cell_start[s.ucell[u]] + s.uslot[u]] = u;
 }
 
@@ -203,11 +203,10 @@ __device__ __forceinline__ void sort_gather_cell(const Sys &s, int c)
     }
 }
 
-__global__ void k_cell_sort_gather(Sys s)
+__device__ __forceinline__ void cell_sort_gather(const Sys &s, Blk k)
 {
     if (!*s.flag) return;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < s.ncell; c += gridDim.x * blockDim.x)
-        sort_gather_cell(s, c);
+    for (int c = k.b * blockDim.x + threadIdx.x; c < s.ncell; c += k.nb * blockDim.x) sort_gather_cell(s, c);
 }
 
 __device__ __forceinline__ int axis_offsets(int nc, int *off)
@@ -230,14 +229,13 @@ __device__ __forceinline__ int wrap_cell(int c, int nc)
 // group of kG lanes per atom, lanes over the atoms of each cell,
 // ballot-compacted in cell order; grid-stride over atom groups so an idle
 // launch (no rebuild) retires at once.
-__global__ void __launch_bounds__(kBlockAtoms) k_verlet(Sys s)
+__device__ __forceinline__ void verlet(const Sys &s, Blk k)
 {
     if (!*s.flag) return;
     int ox[3], oy[3], oz[3];
     const int sx = axis_offsets(s.nc[0], ox), sy = axis_offsets(s.nc[1], oy), sz = axis_offsets(s.nc[2], oz);
-    int b0, b1;
-    group_chunk(s.n, b0, b1);
-    for (int blk = b0; blk < b1; blk += gridDim.x) {
+    const int groups = group_grid(s.n);
+    for (int blk = k.b; blk < groups; blk += k.nb) {
         const AtomLane a = atom_lane_at(s, blk);
         const int i = a.ok ? a.i : 0;
         const float4 pi = s.pos_s[i];
@@ -282,17 +280,83 @@ __global__ void __launch_bounds__(kBlockAtoms) k_verlet(Sys s)
 // Exact rows from the Verlet rows, when the CV kernel does not fuse it.
 __global__ void __launch_bounds__(kBlockAtoms) k_filter(Sys s)
 {
-    int b0, b1;
-    group_chunk(s.n, b0, b1);
-    for (int blk = b0; blk < b1; blk += gridDim.x) filter_row(s, atom_lane_at(s, blk));
+    const int groups = group_grid(s.n);
+    for (int blk = blockIdx.x; blk < groups; blk += gridDim.x) filter_row(s, atom_lane_at(s, blk));
 }
 
 // End of a rebuild: the flag is cleared for the next step (kept set when the
 // skin is zero, so every step rebuilds).
-__global__ void k_clear_flag(Sys s)
+__device__ __forceinline__ void clear_flag(const Sys &s)
 {
+    if (threadIdx.x != 0) return;
     if (*s.flag) *s.rebuilds += 1ull;
     *s.flag = s.always_rebuild ? 1 : 0;
+}
+
+// Single-system kernels of the rebuild chain.
+__global__ void k_rebuild_zero(Sys s) { rebuild_zero(s, own_blk()); }
+__global__ void k_bin_count(Sys s) { bin_count(s, own_blk()); }
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(Sys s) { scan_reduce(s, own_blk()); }
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(Sys s) { scan_down(s, own_blk()); }
+__global__ void k_bin_scatter(Sys s) { bin_scatter(s, own_blk()); }
+__global__ void k_cell_sort_gather(Sys s) { cell_sort_gather(s, own_blk()); }
+__global__ void __launch_bounds__(kBlockAtoms) k_verlet(Sys s) { verlet(s, own_blk()); }
+__global__ void k_clear_flag(Sys s) { clear_flag(s); }
+
+// The same kernels over every system of a batch.
+__global__ void kb_gather_check(BatchView v)
+{
+    Blk k;
+    const Sys &s = v.sys[batch_system(v, k)];
+    gather_check(s, k);
+}
+__global__ void kb_rebuild_zero(BatchView v)
+{
+    Blk k;
+    const Sys &s = v.sys[batch_system(v, k)];
+    rebuild_zero(s, k);
+}
+__global__ void kb_bin_count(BatchView v)
+{
+    Blk k;
+    const Sys &s = v.sys[batch_system(v, k)];
+    bin_count(s, k);
+}
+__global__ void __launch_bounds__(kScanThreads) kb_scan_reduce(BatchView v)
+{
+    Blk k;
+    const Sys &s = v.sys[batch_system(v, k)];
+    scan_reduce(s, k);
+}
+__global__ void __launch_bounds__(kScanThreads) kb_scan_down(BatchView v)
+{
+    Blk k;
+    const Sys &s = v.sys[batch_system(v, k)];
+    scan_down(s, k);
+}
+__global__ void kb_bin_scatter(BatchView v)
+{
+    Blk k;
+    const Sys &s = v.sys[batch_system(v, k)];
+    bin_scatter(s, k);
+}
+__global__ void kb_cell_sort_gather(BatchView v)
+{
+    Blk k;
+    const Sys &s = v.sys[batch_system(v, k)];
+    cell_sort_gather(s, k);
+}
+__global__ void __launch_bounds__(kBlockAtoms) kb_verlet(BatchView v)
+{
+    Blk k;
+    const Sys &s = v.sys[batch_system(v, k)];
+    verlet(s, k);
+}
+__global__ void kb_clear_flag(BatchView v)
+{
+    Blk k;
+    const Sys &s = v.sys[batch_system(v, k)];
+    clear_flag(s);
 }
 
 // Pairs (i < j) in caller indices, for export: one thread per sorted atom,
@@ -330,14 +394,7 @@ __global__ void k_nn_stats(Sys s, unsigned long long *sum, int *mx)
     }
 }
 
-inline int group_blocks(int n) { return persist_grid(n); }
-
 }  // namespace
-
-void launch_gather_check(const Sys &s, cudaStream_t st)
-{
-    k_gather_check<<<(s.n + 255) / 256, 256, 0, st>>>(s);
-}
 
 // Grids of the rebuild chain are capped (grid-stride loops inside) so that
 // the common no-rebuild step pays a few microseconds of launches.
@@ -345,22 +402,63 @@ constexpr int kRebuildGrid = 152 * 8;
 
 inline int capped(int blocks) { return blocks < kRebuildGrid ? (blocks < 1 ? 1 : blocks) : kRebuildGrid; }
 
+int grid_blocks(const Sys &s, int kind, int persist_cap)
+{
+    switch (kind) {
+    case GK_ATOM256: return (s.n + 255) / 256;
+    case GK_CELL1024_CAP: return capped((s.ncell + 1023) / 1024);
+    case GK_ATOM256_CAP: return capped((s.n + 255) / 256);
+    case GK_SCAN_TILES: return (s.ncell + kScanTile - 1) / kScanTile;
+    case GK_CELL128_CAP: return capped((s.ncell + 127) / 128);
+    case GK_GROUPS_CAP: return capped(persist_grid(s.n));
+    case GK_ONE: return 1;
+    case GK_PERSIST: {
+        const int g = persist_grid(s.n);
+        return persist_cap > 0 && persist_cap < g ? persist_cap : g;
+    }
+    case GK_HILLS: return bias_blocks(s.K);
+    case GK_DEPOSIT: return s.deposit ? bias_blocks(s.K) : 0;
+    }
+    return 0;
+}
+
+void launch_gather_check(const Sys &s, cudaStream_t st)
+{
+    k_gather_check<<<grid_blocks(s, GK_ATOM256, 0), 256, 0, st>>>(s);
+}
+
 void launch_rebuild(const Sys &s, cudaStream_t st)
 {
-    const int tiles = (s.ncell + kScanTile - 1) / kScanTile;
-    k_rebuild_zero<<<capped((s.ncell + 1023) / 1024), 1024, 0, st>>>(s);
-    k_bin_count<<<capped((s.n + 255) / 256), 256, 0, st>>>(s);
-    k_scan_reduce<<<tiles, kScanThreads, 0, st>>>(s);
-    k_scan_down<<<tiles, kScanThreads, 0, st>>>(s);
-    k_bin_scatter<<<capped((s.n + 255) / 256), 256, 0, st>>>(s);
-    k_cell_sort_gather<<<capped((s.ncell + 127) / 128), 128, 0, st>>>(s);
-    k_verlet<<<capped(group_blocks(s.n)), kBlockAtoms, 0, st>>>(s);
+    k_rebuild_zero<<<grid_blocks(s, GK_CELL1024_CAP, 0), 1024, 0, st>>>(s);
+    k_bin_count<<<grid_blocks(s, GK_ATOM256_CAP, 0), 256, 0, st>>>(s);
+    k_scan_reduce<<<grid_blocks(s, GK_SCAN_TILES, 0), kScanThreads, 0, st>>>(s);
+    k_scan_down<<<grid_blocks(s, GK_SCAN_TILES, 0), kScanThreads, 0, st>>>(s);
+    k_bin_scatter<<<grid_blocks(s, GK_ATOM256_CAP, 0), 256, 0, st>>>(s);
+    k_cell_sort_gather<<<grid_blocks(s, GK_CELL128_CAP, 0), 128, 0, st>>>(s);
+    k_verlet<<<grid_blocks(s, GK_GROUPS_CAP, 0), kBlockAtoms, 0, st>>>(s);
     k_clear_flag<<<1, 1, 0, st>>>(s);
+}
+
+void launch_batch_gather(const BatchView &v, int total, cudaStream_t st)
+{
+    if (total > 0) kb_gather_check<<<total, 256, 0, st>>>(v);
+}
+
+void launch_batch_rebuild(const BatchView *rows, const int *totals, cudaStream_t st)
+{
+    kb_rebuild_zero<<<totals[GK_CELL1024_CAP], 1024, 0, st>>>(rows[GK_CELL1024_CAP]);
+    kb_bin_count<<<totals[GK_ATOM256_CAP], 256, 0, st>>>(rows[GK_ATOM256_CAP]);
+    kb_scan_reduce<<<totals[GK_SCAN_TILES], kScanThreads, 0, st>>>(rows[GK_SCAN_TILES]);
+    kb_scan_down<<<totals[GK_SCAN_TILES], kScanThreads, 0, st>>>(rows[GK_SCAN_TILES]);
+    kb_bin_scatter<<<totals[GK_ATOM256_CAP], 256, 0, st>>>(rows[GK_ATOM256_CAP]);
+    kb_cell_sort_gather<<<totals[GK_CELL128_CAP], 128, 0, st>>>(rows[GK_CELL128_CAP]);
+    kb_verlet<<<totals[GK_GROUPS_CAP], kBlockAtoms, 0, st>>>(rows[GK_GROUPS_CAP]);
+    kb_clear_flag<<<totals[GK_ONE], 32, 0, st>>>(rows[GK_ONE]);
 }
 
 void launch_filter(const Sys &s, cudaStream_t st)
 {
-    k_filter<<<group_blocks(s.n), kBlockAtoms, 0, st>>>(s);
+    k_filter<<<persist_grid(s.n), kBlockAtoms, 0, st>>>(s);
 }
 
 void launch_nn_stats(const Sys &s, unsigned long long *sum, int *mx, cudaStream_t st)

@@ -11,7 +11,6 @@
 namespace metad {
 
 constexpr int kNY = 13;          // real Y_6^m, m = -6..6
-constexpr int kMaxBatch = 256;   // systems per batched launch
 constexpr int kBlockAtoms = 128; // threads per block of the per-atom kernels
 constexpr int kBlockBias = 256;  // threads per block of the hill kernels
 constexpr int kMaxBiasBlocks = 304;  // two per SM
@@ -50,6 +49,10 @@ struct Sys {
     float rc2_lo, rc2_hi;
     // switch
     int sw_n, sw_m, stretch;
+    float sw_nf;                 // sw_n and N as floating point: an int
+    double sw_nd;                // conversion in a per-pair loop runs on
+    float n_f;                   // the slow FP64 pipe of this part
+    double n_d;
     double r0, rc;
     float inv_r0_hi, inv_r0_lo;  // 1/r0 as a float pair
     float a_hi, a_lo;            // 1/(1 - s_raw(rc)) (1 when not stretched)
@@ -100,7 +103,75 @@ struct Sys {
     int gn[2];
     double glo[2], ghi[2], gh[2];
     double *grid;          // [gn0][gn1][4]
+    // per-step arguments, set on the copy of the descriptor a launch takes
+    int K;                 // live hills
+    const double *bias_x;  // CV point of the hill kernel
+    double *bias_out;      // V, dV/ds1, dV/ds2 of the hill kernel
+    int deposit;           // hill kernel: 1 = append a hill at bias_x
+    float *F_out;          // caller's forces [n][3]
+    int accumulate;        // 1: F_out += force, 0: F_out = force
+    double fscale;         // forces are scaled by this
 };
+
+// Where a block works: block b of a grid of nb blocks of its system.  A
+// single-system launch is that grid; a batched launch concatenates the grids
+// of all its systems.
+struct Blk {
+    int b, nb;
+};
+
+__device__ __forceinline__ Blk own_blk() { return Blk{(int)blockIdx.x, (int)gridDim.x}; }
+
+// A batched launch: block x belongs to system k with pre[k] <= x < pre[k + 1]
+// (systems with no block in this launch have pre[k] == pre[k + 1]).
+struct BatchView {
+    const Sys *sys;  // device [nsys]
+    const int *pre;  // device [nsys + 1], this launch's row
+    int nsys;
+};
+
+__device__ __forceinline__ int batch_system(const BatchView &v, Blk &k)
+{
+    const int x = (int)blockIdx.x;
+    int lo = 0, hi = v.nsys - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(v.pre + mid) <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    const int p0 = __ldg(v.pre + lo);
+    k.b = x - p0;
+    k.nb = __ldg(v.pre + lo + 1) - p0;
+    return lo;
+}
+
+// Grids of a step, one row of block counts per launch kind.
+enum GridKind : int {
+    GK_ATOM256 = 0,    // one thread per atom, 256 per block
+    GK_CELL1024_CAP,   // rebuild: cell counters
+    GK_ATOM256_CAP,    // rebuild: binning and scatter
+    GK_SCAN_TILES,     // rebuild: cell scan
+    GK_CELL128_CAP,    // rebuild: cell sort
+    GK_GROUPS_CAP,     // rebuild: Verlet rows
+    GK_ONE,            // one block per system
+    GK_PERSIST,        // per-atom lane-group kernels
+    GK_HILLS,          // hill kernel, evaluation
+    GK_DEPOSIT,        // hill kernel, deposit (systems that deposit)
+    kGridKinds
+};
+
+// Block count of one system for a grid kind (host side; shared by the
+// single-system launches and the batch tables).  persist_cap > 0 caps the
+// lane-group grids (a batch tile setting), 0 keeps the default.
+int grid_blocks(const Sys &s, int kind, int persist_cap);
+
+// Batched stage launches (one launch each over every system of the view).
+void launch_batch_gather(const BatchView &v, int total, cudaStream_t st);
+void launch_batch_rebuild(const BatchView *rows, const int *totals, cudaStream_t st);
+void launch_batch_cv(const BatchView &v, int total, int fp64, int ncv, cudaStream_t st);
+void launch_batch_bias(const BatchView &v, int total, int deposit, cudaStream_t st);
+void launch_batch_force(const BatchView &v, int total, int fp64, int ncv, cudaStream_t st);
+void launch_batch_collect(const BatchView &v, double *out, cudaStream_t st);
 
 // Launch entry points (stream-ordered, no host synchronisation).
 void launch_gather_check(const Sys &s, cudaStream_t st);
@@ -110,8 +181,8 @@ void launch_cv_fwd(const Sys &s, int fp64, int fused_filter, cudaStream_t st);
 void launch_cv_avg(const Sys &s, int fp64, cudaStream_t st);
 void launch_bias(const Sys &s, int K, const double *s_dev, double *out_dev, int deposit, cudaStream_t st);
 void launch_adjoint(const Sys &s, int fp64, cudaStream_t st);
-void launch_force(const Sys &s, int fp64, float *F, int accumulate, double scale, cudaStream_t st);
-int force_kernels(const Sys &s);
+void launch_force_pairs(const Sys &s, int fp64, double scale, cudaStream_t st);
+void launch_force_gather(const Sys &s, int fp64, float *F, int accumulate, cudaStream_t st);
 void configure_kernels();
 void launch_grid_fold(const Sys &s, int K, cudaStream_t st);
 void launch_nn_stats(const Sys &s, unsigned long long *sum, int *mx, cudaStream_t st);
@@ -233,15 +304,35 @@ __device__ __forceinline__ void geom_sum(real x, int k, real &S, real &dS)
 }
 
 template <typename real>
+__device__ __forceinline__ real sw_n_real(const Sys &s);
+template <>
+__device__ __forceinline__ float sw_n_real<float>(const Sys &s) { return s.sw_nf; }
+template <>
+__device__ __forceinline__ double sw_n_real<double>(const Sys &s) { return s.sw_nd; }
+
+template <typename real>
+__device__ __forceinline__ real n_real(const Sys &s);
+template <>
+__device__ __forceinline__ float n_real<float>(const Sys &s) { return s.n_f; }
+template <>
+__device__ __forceinline__ double n_real<double>(const Sys &s) { return s.n_d; }
+
+template <typename real>
 __device__ __forceinline__ void switch_raw(const Sys &s, real x, real &f, real &dfdx)
 {
     const int n = s.sw_n, m = s.sw_m;
     if (m == 2 * n) {
-        real xn1 = ipow<real>(x, n - 1);
+        real xn1;
+        if (n == 6) {  // the common 6-12 switch: x^5 without the power loop
+            const real x2 = x * x;
+            xn1 = x2 * x2 * x;
+        } else {
+            xn1 = ipow<real>(x, n - 1);
+        }
         real xn = xn1 * x;
         real inv = recip_r<real>(real(1) + xn);
         f = inv;
-        dfdx = -real(n) * xn1 * inv * inv;
+        dfdx = -sw_n_real<real>(s) * xn1 * inv * inv;
         return;
     }
     real Sn, dSn, Sm, dSm;
@@ -293,14 +384,9 @@ __host__ __device__ inline int group_grid(int n) { return (n + kAtomsPerBlock - 
 // last block's fixed-order sum of them is short.
 constexpr int kPersistBlocks = 152 * 16;
 
-// Block b walks atom groups b, b + G, b + 2G, ... (G = gridDim.x): at any
-// moment all SMs work on one compact window of the Morton order, so the
-// records they gather stay in L2.
-__device__ __forceinline__ void group_chunk(int n, int &b0, int &b1)
-{
-    b0 = (int)blockIdx.x;
-    b1 = group_grid(n);
-}
+// Block b of nb walks atom groups b, b + nb, b + 2 nb, ...: at any moment
+// all SMs work on one compact window of the Morton order, so the records
+// they gather stay in L2.
 __host__ __device__ inline int persist_grid(int n)
 {
     const int g = group_grid(n);
@@ -322,7 +408,6 @@ __device__ __forceinline__ AtomLane atom_lane_at(const Sys &s, int blk)
     return a;
 }
 
-__device__ __forceinline__ AtomLane atom_lane(const Sys &s) { return atom_lane_at(s, blockIdx.x); }
 
 __device__ __forceinline__ unsigned group_mask_bits(unsigned ballot)
 {

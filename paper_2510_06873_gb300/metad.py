@@ -73,8 +73,18 @@ _SIGS = {
     "metad_rebuild_count": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
     "metad_bias_eval_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.c_int32, _P, _P, ctypes.c_int32,
                                                _P]),
+    "metad_estimate_bytes": (ctypes.c_int, [ctypes.POINTER(metad_params), ctypes.POINTER(ctypes.c_int64)]),
+    "metad_device_bytes": (ctypes.c_int64, [_P]),
+    "metad_batch_create": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)]),
+    "metad_batch_destroy": (ctypes.c_int, [_P]),
+    "metad_batch_set_tile": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "metad_batch_step": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, _P, _P]),
+    "metad_batch_collect": (ctypes.c_int, [_P, _P]),
+    "metad_batch_read": (ctypes.c_int, [_P, _P, _P]),
+    "metad_batch_launch_count": (ctypes.c_int64, [_P]),
+    "metad_batch_last_error": (ctypes.c_char_p, [_P]),
 }
-METAD_NUM_STAGES = 9
+METAD_NUM_STAGES = 10
 OPTIONAL = {}
 
 
@@ -421,3 +431,106 @@ class Metad:
     @property
     def hill_count(self) -> int:
         return metad_hill_count(self.ctx)
+
+    @property
+    def device_bytes(self) -> int:
+        return metad_device_bytes(self.ctx)
+
+
+def metad_estimate_bytes(p: metad_params) -> int:
+    out = ctypes.c_int64(0)
+    _check(None, lib().metad_estimate_bytes(ctypes.byref(p), ctypes.byref(out)), "metad_estimate_bytes")
+    return int(out.value)
+
+
+def metad_device_bytes(ctx) -> int:
+    return int(lib().metad_device_bytes(ctx))
+
+
+# ------------------------------------------------------------------ batches
+
+def _bcheck(batch, s, where):
+    if s != METAD_OK:
+        detail = lib().metad_batch_last_error(batch).decode() if batch else ""
+        raise MetadError(s, where, detail)
+
+
+def metad_batch_create(ctxs):
+    arr = (ctypes.c_void_p * len(ctxs))(*[c.value if isinstance(c, ctypes.c_void_p) else c for c in ctxs])
+    out = ctypes.c_void_p()
+    _bcheck(None, lib().metad_batch_create(arr, len(ctxs), ctypes.byref(out)), "metad_batch_create")
+    return out
+
+
+def metad_batch_destroy(batch):
+    lib().metad_batch_destroy(batch)
+
+
+def metad_batch_set_tile(batch, blocks_per_system):
+    _bcheck(batch, lib().metad_batch_set_tile(batch, int(blocks_per_system)), "metad_batch_set_tile")
+
+
+def metad_batch_step(batch, pos_list, force_list, accumulate=False, deposit=None, active=None):
+    """pos_list / force_list: one tensor (or None when inactive) per system."""
+    n = len(pos_list)
+    pos = (ctypes.c_void_p * n)(*[_dptr(t) for t in pos_list])
+    frc = (ctypes.c_void_p * n)(*[_dptr(t) for t in force_list])
+    dep_a = None if deposit is None else np.ascontiguousarray(np.asarray(deposit, dtype=np.int32))
+    act_a = None if active is None else np.ascontiguousarray(np.asarray(active, dtype=np.int32))
+    _bcheck(batch, lib().metad_batch_step(batch, pos, frc, 1 if accumulate else 0, _hptr(dep_a), _hptr(act_a)),
+            "metad_batch_step")
+
+
+def metad_batch_collect(batch, out_host):
+    """out_host: float64 numpy array [n, 4] (page-locked for an asynchronous copy)."""
+    _bcheck(batch, lib().metad_batch_collect(batch, _hptr(out_host)), "metad_batch_collect")
+
+
+def metad_batch_read(batch, n):
+    cv = np.zeros((n, 2), dtype=np.float64)
+    V = np.zeros(n, dtype=np.float64)
+    _bcheck(batch, lib().metad_batch_read(batch, _hptr(cv), _hptr(V)), "metad_batch_read")
+    return cv, V
+
+
+def metad_batch_launch_count(batch) -> int:
+    return lib().metad_batch_launch_count(batch)
+
+
+class Batch:
+    """Many contexts stepped together, one launch per stage (metad_batch_*).
+
+    The contexts stay owned by the caller and must outlive the batch."""
+
+    def __init__(self, contexts):
+        self.contexts = list(contexts)
+        self.n = len(self.contexts)
+        self.batch = metad_batch_create([c.ctx for c in self.contexts])
+
+    def close(self):
+        if getattr(self, "batch", None):
+            metad_batch_destroy(self.batch)
+            self.batch = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_tile(self, blocks_per_system):
+        metad_batch_set_tile(self.batch, blocks_per_system)
+
+    def step(self, pos_list, force_list, accumulate=False, deposit=None, active=None):
+        metad_batch_step(self.batch, pos_list, force_list, accumulate, deposit, active)
+
+    def collect(self, out_host):
+        metad_batch_collect(self.batch, out_host)
+
+    def read(self):
+        """(cv [n, 2], V [n]) of the last batched step; synchronises."""
+        return metad_batch_read(self.batch, self.n)
+
+    @property
+    def launch_count(self) -> int:
+        return metad_batch_launch_count(self.batch)

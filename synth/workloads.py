@@ -287,6 +287,9 @@ CONFIG_PARAMS = {
     2: dict(n_cv=2, sigma=(0.05, 0.02), hills=5000, frames=100, fp64=False),
     3: dict(n_cv=2, sigma=(0.05, 0.02), hills_folded=20000, hills=20000, frames=10000,
             deposit_every=500, grid_n=(200, 200), fp64=False),
+    4: dict(n_cv=2, sigma=(0.05, 0.02), systems=64, steps=10, fp64=False),
+    5: dict(n_cv=2, sigma=(0.05, 0.02), walkers=32, requests=2000, rate_hz=5000.0, hills=1000,
+            deposit_every=20, budget_bytes=120 * 10**9, fp64=False),
 }
 
 

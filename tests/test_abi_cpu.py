@@ -77,7 +77,7 @@ def test_grid_needs_two_cvs(metad):
 def test_status_strings_and_stage_names(metad):
     assert metad.status_string(0) == "ok"
     assert metad.status_string(4) == "capacity exceeded"
-    assert [metad.metad_stage_name(k) for k in range(metad.METAD_NUM_STAGES)][6] == "force"
+    assert [metad.metad_stage_name(k) for k in range(metad.METAD_NUM_STAGES)][6:8] == ["force_pairs", "force_gather"]
     assert metad.lib().metad_destroy(None) == 0
 
 
@@ -87,3 +87,29 @@ def test_package_import_does_not_load_oracle():
     code = ("import sys; import paper_2510_06873_gb300.metad as m; m.lib(); "
             "assert 'oracle' not in sys.modules, 'oracle imported by the library path'")
     subprocess.check_call([sys.executable, "-c", code], cwd=ROOT)
+
+
+def test_estimate_bytes_needs_no_gpu_and_grows_with_size(metad):
+    small = metad.metad_estimate_bytes(metad.params_for(1000, [23.2, 23.2, 23.2]))
+    big = metad.metad_estimate_bytes(metad.params_for(100_000, [106.0, 106.0, 106.0]))
+    assert 0 < small < big
+    # a few KB per atom (neighbour rows, pair slots, Verlet rows, records)
+    per_atom = (big - small) / 99_000
+    assert 1000 < per_atom < 4000, per_atom
+    with pytest.raises(metad.MetadError) as e:
+        metad.metad_estimate_bytes(metad.params_for(10, [1.0, 10.0, 10.0]))
+    assert e.value.status == metad.METAD_ERR_INVALID
+
+
+def test_batch_entry_points_reject_null_without_a_gpu(metad):
+    import ctypes
+    L = metad.lib()
+    out = ctypes.c_void_p()
+    assert L.metad_batch_create(None, 1, ctypes.byref(out)) == metad.METAD_ERR_INVALID
+    arr = (ctypes.c_void_p * 1)(None)
+    assert L.metad_batch_create(arr, 1, ctypes.byref(out)) == metad.METAD_ERR_INVALID
+    assert L.metad_batch_create(arr, 0, ctypes.byref(out)) == metad.METAD_ERR_INVALID
+    assert L.metad_batch_step(None, None, None, 0, None, None) == metad.METAD_ERR_INVALID
+    assert L.metad_batch_read(None, None, None) == metad.METAD_ERR_INVALID
+    assert L.metad_batch_set_tile(None, 0) == metad.METAD_ERR_INVALID
+    assert L.metad_batch_destroy(None) == metad.METAD_OK
