@@ -134,6 +134,39 @@ def dist_env():
     return ws, rank, local
 
 
+# Sources that make up the per-atom kernels; a profile summary records their
+# SHA-1 when its counters were taken.
+KERNEL_SOURCES = ("paper_2510_06873_gb300/csrc/k_cv.cu", "paper_2510_06873_gb300/csrc/metad_impl.cuh")
+
+
+def kernel_sources_sha1() -> str:
+    import hashlib
+    h = hashlib.sha1()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def profiled_traffic(kernel: str, n_atoms: int):
+    """DRAM bytes (read + write) per launch of `kernel` at n_atoms, from the
+    ncu capture summarised in profiles/<kernel>.md (bytes per atom of the
+    captured case times n_atoms); None when the summary is missing or the
+    kernel sources changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}.md")
+    if not os.path.exists(path):
+        return None
+    per_atom, sha = None, None
+    for line in open(path):
+        if line.startswith("traffic_bytes_per_atom ="):
+            per_atom = float(line.split("=", 1)[1])
+        elif line.startswith("sources_sha1 ="):
+            sha = line.split("=", 1)[1].strip()
+    if per_atom is None or sha != kernel_sources_sha1():
+        return None
+    return per_atom * n_atoms
+
+
 def max_over_ranks(x: float, device) -> float:
     """The largest value of x over all ranks (the job's time is its slowest
     replica's); x itself when not distributed."""
@@ -322,7 +355,7 @@ def run_metad(args):
     if FLOP_PER_PAIR.get(dom, 0) > 0:
         achieved = FLOP_PER_PAIR[dom] * pairs / avg_s / 1e12
         roof = {"kernel": f"k_{dom}", "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": profiled_traffic(f"k_{dom}", n),
                 "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 flop x 2.07 GHz",
                 "algorithmic": f"{FLOP_PER_PAIR[dom]:.0f} flop per unordered pair x {pairs:.0f} pairs"}
     else:
@@ -330,7 +363,7 @@ def run_metad(args):
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
         achieved = BYTES_PER_ATOM[dom] * n / avg_s / 1e9
         roof = {"kernel": f"k_{dom}", "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None}
+                "frac": achieved / peaks["hbm_gbs"], "traffic": profiled_traffic(f"k_{dom}", n)}
     step_bytes = sum(BYTES_PER_ATOM.values()) * n
     peaks_hbm = 6787.2
     try:

@@ -1107,7 +1107,8 @@ metad_status metad_batch_step(metad_batch *b, const float *const *pos_dev, float
     metad::launch_batch_rebuild(rows, totals, b->stream);
     metad::launch_batch_cv(rows[metad::GK_PERSIST], totals[metad::GK_PERSIST], b->fp64, b->ncv, b->stream);
     metad::launch_batch_bias(rows[metad::GK_HILLS], totals[metad::GK_HILLS], 0, b->stream);
-    metad::launch_batch_force(rows[metad::GK_PERSIST], totals[metad::GK_PERSIST], b->fp64, b->ncv, b->stream);
+    metad::launch_batch_force(rows[metad::GK_GROUPS], totals[metad::GK_GROUPS], rows[metad::GK_ATOM128],
+                              totals[metad::GK_ATOM128], b->fp64, b->ncv, b->stream);
     if (any_deposit) metad::launch_batch_bias(rows[metad::GK_DEPOSIT], totals[metad::GK_DEPOSIT], 1, b->stream);
     b->launches += 1 + 8 + (b->ncv == 2 ? 2 : 1) + 1 + (b->ncv == 2 ? 3 : 2) + (any_deposit ? 1 : 0);
     cudaError_t e = cudaGetLastError();

@@ -444,7 +444,7 @@ __device__ __forceinline__ void cv_fwd(const Sys &s, Blk k)
 {
     double acc = 0.0;
     const int groups = group_grid(s.n);
-    for (int blk = k.b; blk < groups; blk += k.nb) acc += cv_fwd_group<real, kFilter>(s, atom_lane_at(s, blk));
+    for (int it = 0, g; (g = work_item(k, it)) < groups; ++it) acc += cv_fwd_group<real, kFilter>(s, atom_lane_at(s, g));
     last_block_reduce(s, k, acc, 0, s.scal + kS0, 1.0 / s.n);
 }
 
@@ -516,7 +516,7 @@ __device__ __forceinline__ void cv_avg(const Sys &s, Blk k)
 {
     double acc = 0.0;
     const int groups = group_grid(s.n);
-    for (int blk = k.b; blk < groups; blk += k.nb) acc += cv_avg_group<real>(s, atom_lane_at(s, blk));
+    for (int it = 0, g; (g = work_item(k, it)) < groups; ++it) acc += cv_avg_group<real>(s, atom_lane_at(s, g));
     last_block_reduce(s, k, acc, 1, s.scal + kS1, 1.0 / s.n);
 }
 
@@ -588,7 +588,7 @@ template <typename real>
 __device__ __forceinline__ void adjoint(const Sys &s, Blk k)
 {
     const int groups = group_grid(s.n);
-    for (int blk = k.b; blk < groups; blk += k.nb) adjoint_group<real>(s, atom_lane_at(s, blk));
+    for (int it = 0, g; (g = work_item(k, it)) < groups; ++it) adjoint_group<real>(s, atom_lane_at(s, g));
 }
 
 template <typename real>
@@ -622,58 +622,79 @@ __device__ __forceinline__ void store_pair_force<double>(double *slot, double fx
     reinterpret_cast<double2 *>(slot)[1] = make_double2(fz, 0.0);
 }
 
+// Pair-parallel: the half-row entries (k < nh_i) of a chunk of kPairChunk
+// atoms are numbered in atom order and thread t of the block evaluates
+// entries t, t + blockDim, ...: every lane has a pair while the chunk lasts,
+// whatever the spread of the atoms' half-row lengths.
+//
+// G_ij goes to the slot of entry k in i's row and -G_ij to the slot of i in
+// the j < i part of j's row (rows are symmetric: the neighbour predicate is),
+// so pass 2 sums each atom's own slots in row order.
+constexpr int kPairChunk = 32;
+
 template <typename real>
-__device__ __forceinline__ void force_pairs_group(const Sys &s, const AtomLane a, real cn_fac, real V2)
+__device__ __forceinline__ void pair_force(const Sys &s, int i, int k, real cn_fac, real V2)
 {
-    if (!a.ok) return;
-    const int nh = s.nh[a.i];
-    if (a.l >= nh) return;
-    const bool q6 = s.ncv == 2;
-    const real *hh = R<real>(s.h), *qq = R<real>(s.q), *qbb = R<real>(s.b);
-    const float4 pi = s.pos_s[a.i];
-    real hi[kRec], qi[kRec], qbi[kRec];
-    if (q6) {
-        load_rec<real>(hh, a.i, hi);
-        load_rec<real>(qq, a.i, qi);
-        load_rec<real>(qbb, a.i, qbi);
-    }
-    const int *row = nbr_row(s, a.i);
-    real *slots = R<real>(s.pairF) + (size_t)a.i * s.max_nb * 4;
-    for (int k = a.l; k < nh; k += kG) {
-        const int j = row[k];
-        const float4 pj = s.pos_s[j];
-        Vec3<real> d;
-        real inv_r, w, dw;
-        pair_geometry<real>(s, pi, pj, d, inv_r, w, dw);
-        const real ux = d.x * inv_r, uy = d.y * inv_r, uz = d.z * inv_r;
-        real radial = (!s.cn_unlike || pj.w != pi.w) ? cn_fac * dw : real(0);
-        real fx = real(0), fy = real(0), fz = real(0);
-        if (q6) {
-            real hj[kRec], qj[kRec], qbj[kRec];
-            load_rec<real>(hh, j, hj);
-            load_rec<real>(qq, j, qj);
-            load_rec<real>(qbb, j, qbj);
-            real hs[kNY], cvec[kNY];
+    const int j = nbr_row(s, i)[k];
+    const int nhj = s.nh[j], nnj = s.nn[j];
+    const float4 pi = s.pos_s[i];
+    const float4 pj = s.pos_s[j];
+    Vec3<real> d;
+    real inv_r, w, dw;
+    pair_geometry<real>(s, pi, pj, d, inv_r, w, dw);
+    const real ux = d.x * inv_r, uy = d.y * inv_r, uz = d.z * inv_r;
+    real radial = (!s.cn_unlike || pj.w != pi.w) ? cn_fac * dw : real(0);
+    real fx = real(0), fy = real(0), fz = real(0);
+    if (s.ncv == 2) {
+        const real *hh = R<real>(s.h), *qq = R<real>(s.q), *qbb = R<real>(s.b);
+        // cross term b_i.q_j + b_j.q_i first, so the q and b records die early
+        real qi[kRec], qj[kRec], bi[kRec], bj[kRec];
+        load_rec<real>(qq, i, qi);
+        load_rec<real>(qq, j, qj);
+        load_rec<real>(qbb, i, bi);
+        load_rec<real>(qbb, j, bj);
+        real t = real(0);
 #pragma unroll
-            for (int m = 0; m < kNY; ++m) {
-                hs[m] = hi[m] + hj[m];
-                cvec[m] = w * hs[m];
-            }
-            real Y[kNY], gY[3];
-            ylm13_grad<real>(ux, uy, uz, inv_r, cvec, Y, gY);
-            real t = -(hi[13] + hj[13]);
+        for (int m = 0; m < kNY; ++m) t += bi[m] * qj[m] + bj[m] * qi[m];
+        real hi[kRec], hj[kRec];
+        load_rec<real>(hh, i, hi);
+        load_rec<real>(hh, j, hj);
+        t -= hi[13] + hj[13];
+        real hs[kNY], cvec[kNY];
 #pragma unroll
-            for (int m = 0; m < kNY; ++m) t += hs[m] * Y[m] + qbi[m] * qj[m] + qbj[m] * qi[m];
-            radial += V2 * t * dw;
-            fx = V2 * gY[0];
-            fy = V2 * gY[1];
-            fz = V2 * gY[2];
+        for (int m = 0; m < kNY; ++m) {
+            hs[m] = hi[m] + hj[m];
+            cvec[m] = w * hs[m];
         }
-        fx += radial * ux;
-        fy += radial * uy;
-        fz += radial * uz;
-        store_pair_force<real>(slots + 4 * (size_t)k, fx, fy, fz);
+        real Y[kNY], gY[3];
+        ylm13_grad<real>(ux, uy, uz, inv_r, cvec, Y, gY);
+#pragma unroll
+        for (int m = 0; m < kNY; ++m) t += hs[m] * Y[m];
+        radial += V2 * t * dw;
+        fx = V2 * gY[0];
+        fy = V2 * gY[1];
+        fz = V2 * gY[2];
     }
+    fx += radial * ux;
+    fy += radial * uy;
+    fz += radial * uz;
+    real *pf = R<real>(s.pairF);
+    store_pair_force<real>(pf + ((size_t)i * s.max_nb + k) * 4, fx, fy, fz);
+    // position of i in the j < i part [nh_j, nn_j) of j's row, four entries per load
+    const int *rj = nbr_row(s, j);
+    int kk = -1;
+    for (int b = nhj & ~3; b < nnj && kk < 0; b += 4) {
+        const int4 v = *reinterpret_cast<const int4 *>(rj + b);
+        if (v.x == i && b >= nhj) kk = b;
+        else if (v.y == i && b + 1 >= nhj && b + 1 < nnj) kk = b + 1;
+        else if (v.z == i && b + 2 >= nhj && b + 2 < nnj) kk = b + 2;
+        else if (v.w == i && b + 3 >= nhj && b + 3 < nnj) kk = b + 3;
+    }
+    if (kk < 0) {
+        set_err(s, kErrInternal);  // rows not symmetric: never expected
+        return;
+    }
+    store_pair_force<real>(pf + ((size_t)j * s.max_nb + kk) * 4, -fx, -fy, -fz);
 }
 
 template <typename real>
@@ -682,8 +703,37 @@ __device__ __forceinline__ void force_pairs(const Sys &s, Blk k)
     // the chain-rule factors of the two CVs, once per thread (FP64 is slow here)
     const real cn_fac = (real)(s.scal[kDV0] * s.fscale * 2.0 / s.n);
     const real V2 = s.ncv == 2 ? (real)(s.scal[kDV1] * s.fscale) : real(0);
-    const int groups = group_grid(s.n);
-    for (int blk = k.b; blk < groups; blk += k.nb) force_pairs_group<real>(s, atom_lane_at(s, blk), cn_fac, V2);
+    // each warp takes its own chunk of 32 atoms (a block of kBlockAtoms/32
+    // warps is one work item, one per 128 atoms of the grid): no barrier
+    constexpr int kWarps = kBlockAtoms / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int items = (s.n + kPairChunk * kWarps - 1) / (kPairChunk * kWarps);
+    for (int it = 0, g; (g = work_item(k, it)) < items; ++it) {
+        const int i0 = (g * kWarps + warp) * kPairChunk;
+        if (i0 >= s.n) continue;  // warp-uniform
+        // inclusive prefix of the half-row lengths, one lane per atom
+        int off = i0 + lane < s.n ? s.nh[i0 + lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, off, o);
+            if (lane >= o) off += y;
+        }
+        const int T = __shfl_sync(0xffffffffu, off, 31);
+        for (int p0 = 0; p0 < T; p0 += 32) {
+            const int p = p0 + lane;
+            // the atom of entry p: the first a whose inclusive prefix exceeds p
+            int lo = 0, hi = 31;
+#pragma unroll
+            for (int step = 0; step < 5; ++step) {
+                const int mid = (lo + hi) >> 1;
+                if (__shfl_sync(0xffffffffu, off, mid) > p) hi = mid;
+                else lo = mid + 1;
+            }
+            const int prev = __shfl_sync(0xffffffffu, off, lo > 0 ? lo - 1 : 0);  // every lane shuffles
+            const int start = lo > 0 ? prev : 0;
+            if (p < T) pair_force<real>(s, i0 + lo, p - start, cn_fac, V2);
+        }
+    }
 }
 
 template <typename real>
@@ -717,46 +767,23 @@ __device__ __forceinline__ void load_pair_force<double>(const double *slot, doub
     fz = b.x;
 }
 
-// a8, pass 2: F_i = sum_{j > i} G_ij - sum_{j < i} G_ji over i's row, in row
-// order per lane and a fixed shuffle tree across lanes: deterministic, no
-// atomics.  G_ji sits in j's slot of i, found in the j > i part of j's row.
+// a8, pass 2: F_i = sum_{j > i} G_ij - sum_{j < i} G_ji: the slots of i's
+// row hold exactly those terms (pass 1 wrote both ends of every pair), summed
+// in row order per lane and a fixed shuffle tree across lanes: deterministic,
+// no atomics, and contiguous reads.
 template <typename real>
 __device__ __forceinline__ void force_gather_group(const Sys &s, const AtomLane a, float *F, int accumulate)
 {
     real fx = real(0), fy = real(0), fz = real(0);
     if (a.ok) {
-        const int nn = s.nn[a.i], nh = s.nh[a.i];
-        const int *row = nbr_row(s, a.i);
-        const real *pf = R<real>(s.pairF);
+        const int nn = s.nn[a.i];
+        const real *pf = R<real>(s.pairF) + (size_t)a.i * s.max_nb * 4;
         for (int k = a.l; k < nn; k += kG) {
             real gx, gy, gz;
-            if (k < nh) {
-                load_pair_force<real>(pf + ((size_t)a.i * s.max_nb + k) * 4, gx, gy, gz);
-                fx += gx;
-                fy += gy;
-                fz += gz;
-            } else {
-                const int j = row[k];
-                const int *rj = nbr_row(s, j);
-                const int nhj = s.nh[j];
-                // position of i in the j > i part of j's row, four entries per load
-                int kk = -1;
-                for (int b = 0; b < nhj && kk < 0; b += 4) {
-                    const int4 v = *reinterpret_cast<const int4 *>(rj + b);
-                    if (v.x == a.i && b < nhj) kk = b;
-                    else if (v.y == a.i && b + 1 < nhj) kk = b + 1;
-                    else if (v.z == a.i && b + 2 < nhj) kk = b + 2;
-                    else if (v.w == a.i && b + 3 < nhj) kk = b + 3;
-                }
-                if (kk < 0) {
-                    set_err(s, kErrInternal);  // rows not symmetric: never expected
-                    continue;
-                }
-                load_pair_force<real>(pf + ((size_t)j * s.max_nb + kk) * 4, gx, gy, gz);
-                fx -= gx;
-                fy -= gy;
-                fz -= gz;
-            }
+            load_pair_force<real>(pf + 4 * (size_t)k, gx, gy, gz);
+            fx += gx;
+            fy += gy;
+            fz += gz;
         }
     }
     fx = group_sum<real>(fx);
@@ -780,7 +807,8 @@ template <typename real>
 __device__ __forceinline__ void force_gather(const Sys &s, Blk k)
 {
     const int groups = group_grid(s.n);
-    for (int blk = k.b; blk < groups; blk += k.nb) force_gather_group<real>(s, atom_lane_at(s, blk), s.F_out, s.accumulate);
+    for (int it = 0, g; (g = work_item(k, it)) < groups; ++it)
+        force_gather_group<real>(s, atom_lane_at(s, g), s.F_out, s.accumulate);
 }
 
 template <typename real>
@@ -835,19 +863,20 @@ void launch_cv_avg(const Sys &s, int fp64, cudaStream_t st)
 void launch_adjoint(const Sys &s, int fp64, cudaStream_t st)
 {
     if (fp64)
-        k_adjoint<double><<<atom_blocks(s.n), kBlockAtoms, 0, st>>>(s);
+        k_adjoint<double><<<group_grid(s.n), kBlockAtoms, 0, st>>>(s);
     else
-        k_adjoint<float><<<atom_blocks(s.n), kBlockAtoms, 0, st>>>(s);
+        k_adjoint<float><<<group_grid(s.n), kBlockAtoms, 0, st>>>(s);
 }
 
 void launch_force_pairs(const Sys &s, int fp64, double scale, cudaStream_t st)
 {
     Sys t = s;
     t.fscale = scale;
+    const int nb = grid_blocks(s, GK_ATOM128, 0);
     if (fp64)
-        k_force_pairs<double><<<atom_blocks(s.n), kBlockAtoms, 0, st>>>(t);
+        k_force_pairs<double><<<nb, kBlockAtoms, 0, st>>>(t);
     else
-        k_force_pairs<float><<<atom_blocks(s.n), kBlockAtoms, 0, st>>>(t);
+        k_force_pairs<float><<<nb, kBlockAtoms, 0, st>>>(t);
 }
 
 void launch_force_gather(const Sys &s, int fp64, float *F, int accumulate, cudaStream_t st)
@@ -856,9 +885,9 @@ void launch_force_gather(const Sys &s, int fp64, float *F, int accumulate, cudaS
     t.F_out = F;
     t.accumulate = accumulate;
     if (fp64)
-        k_force_gather<double><<<atom_blocks(s.n), kBlockAtoms, 0, st>>>(t);
+        k_force_gather<double><<<group_grid(s.n), kBlockAtoms, 0, st>>>(t);
     else
-        k_force_gather<float><<<atom_blocks(s.n), kBlockAtoms, 0, st>>>(t);
+        k_force_gather<float><<<group_grid(s.n), kBlockAtoms, 0, st>>>(t);
 }
 
 void launch_batch_cv(const BatchView &v, int total, int fp64, int ncv, cudaStream_t st)
@@ -873,17 +902,18 @@ void launch_batch_cv(const BatchView &v, int total, int fp64, int ncv, cudaStrea
     }
 }
 
-void launch_batch_force(const BatchView &v, int total, int fp64, int ncv, cudaStream_t st)
+void launch_batch_force(const BatchView &groups, int group_total, const BatchView &pairs, int pair_total, int fp64,
+                        int ncv, cudaStream_t st)
 {
-    if (total <= 0) return;
+    if (group_total <= 0) return;
     if (fp64) {
-        if (ncv == 2) kb_adjoint<double><<<total, kBlockAtoms, 0, st>>>(v);
-        kb_force_pairs<double><<<total, kBlockAtoms, 0, st>>>(v);
-        kb_force_gather<double><<<total, kBlockAtoms, 0, st>>>(v);
+        if (ncv == 2) kb_adjoint<double><<<group_total, kBlockAtoms, 0, st>>>(groups);
+        kb_force_pairs<double><<<pair_total, kBlockAtoms, 0, st>>>(pairs);
+        kb_force_gather<double><<<group_total, kBlockAtoms, 0, st>>>(groups);
     } else {
-        if (ncv == 2) kb_adjoint<float><<<total, kBlockAtoms, 0, st>>>(v);
-        kb_force_pairs<float><<<total, kBlockAtoms, 0, st>>>(v);
-        kb_force_gather<float><<<total, kBlockAtoms, 0, st>>>(v);
+        if (ncv == 2) kb_adjoint<float><<<group_total, kBlockAtoms, 0, st>>>(groups);
+        kb_force_pairs<float><<<pair_total, kBlockAtoms, 0, st>>>(pairs);
+        kb_force_gather<float><<<group_total, kBlockAtoms, 0, st>>>(groups);
     }
 }
 

@@ -235,7 +235,7 @@ __device__ __forceinline__ void verlet(const Sys &s, Blk k)
     int ox[3], oy[3], oz[3];
     const int sx = axis_offsets(s.nc[0], ox), sy = axis_offsets(s.nc[1], oy), sz = axis_offsets(s.nc[2], oz);
     const int groups = group_grid(s.n);
-    for (int blk = k.b; blk < groups; blk += k.nb) {
+    for (int it = 0, blk; (blk = work_item(k, it)) < groups; ++it) {
         const AtomLane a = atom_lane_at(s, blk);
         const int i = a.ok ? a.i : 0;
         const float4 pi = s.pos_s[i];
@@ -416,6 +416,8 @@ int grid_blocks(const Sys &s, int kind, int persist_cap)
         const int g = persist_grid(s.n);
         return persist_cap > 0 && persist_cap < g ? persist_cap : g;
     }
+    case GK_ATOM128: return (s.n + 127) / 128;
+    case GK_GROUPS: return group_grid(s.n);
     case GK_HILLS: return bias_blocks(s.K);
     case GK_DEPOSIT: return s.deposit ? bias_blocks(s.K) : 0;
     }

@@ -155,6 +155,8 @@ enum GridKind : int {
     GK_GROUPS_CAP,     // rebuild: Verlet rows
     GK_ONE,            // one block per system
     GK_PERSIST,        // per-atom lane-group kernels
+    GK_ATOM128,        // one block per 128 atoms (pair-parallel force)
+    GK_GROUPS,         // one block per lane-group block of atoms (no reduction)
     GK_HILLS,          // hill kernel, evaluation
     GK_DEPOSIT,        // hill kernel, deposit (systems that deposit)
     kGridKinds
@@ -170,7 +172,8 @@ void launch_batch_gather(const BatchView &v, int total, cudaStream_t st);
 void launch_batch_rebuild(const BatchView *rows, const int *totals, cudaStream_t st);
 void launch_batch_cv(const BatchView &v, int total, int fp64, int ncv, cudaStream_t st);
 void launch_batch_bias(const BatchView &v, int total, int deposit, cudaStream_t st);
-void launch_batch_force(const BatchView &v, int total, int fp64, int ncv, cudaStream_t st);
+void launch_batch_force(const BatchView &groups, int group_total, const BatchView &pairs, int pair_total, int fp64,
+                        int ncv, cudaStream_t st);
 void launch_batch_collect(const BatchView &v, double *out, cudaStream_t st);
 
 // Launch entry points (stream-ordered, no host synchronisation).
@@ -384,9 +387,13 @@ __host__ __device__ inline int group_grid(int n) { return (n + kAtomsPerBlock - 
 // last block's fixed-order sum of them is short.
 constexpr int kPersistBlocks = 152 * 16;
 
-// Block b of nb walks atom groups b, b + nb, b + 2 nb, ...: at any moment
-// all SMs work on one compact window of the Morton order, so the records
-// they gather stay in L2.
+// The it-th work item (atom group or chunk) of block b of nb: items b,
+// b + nb, b + 2 nb, ...  The items of one sweep form one compact window of
+// the Morton order, so the records they gather stay in L2.  (Mapping the
+// blocks that share an SM to consecutive items, for L1 reuse, measured
+// slower: the gather kernels lost more to L2 misses than they won in L1.)
+__device__ __forceinline__ int work_item(Blk k, int it) { return k.b + it * k.nb; }
+
 __host__ __device__ inline int persist_grid(int n)
 {
     const int g = group_grid(n);
@@ -416,15 +423,23 @@ __device__ __forceinline__ unsigned group_mask_bits(unsigned ballot)
 }
 
 // Exact FP64 pair test: r^2 = (dx*dx + dy*dy) + dz*dz < rc^2 on the
-// minimum-image displacement, no contraction.
-__device__ __forceinline__ bool pair_exact(const Sys &s, float4 pi, float4 pj)
+// minimum-image displacement, no contraction.  Kept out of line and given
+// plain values (no reference to the kernel's descriptor): it runs only for
+// candidates inside the guard band, and inlined the compiler may evaluate
+// it for every candidate under a predicate, on the slow FP64 pipe.
+static __device__ __noinline__ bool pair_exact_fp64(float4 pi, float4 pj, double L0, double L1, double L2, double rc2)
 {
-    double dx = mi_d(__dadd_rn((double)pj.x, -(double)pi.x), s.L[0]);
-    double dy = mi_d(__dadd_rn((double)pj.y, -(double)pi.y), s.L[1]);
-    double dz = mi_d(__dadd_rn((double)pj.z, -(double)pi.z), s.L[2]);
+    double dx = mi_d(__dadd_rn((double)pj.x, -(double)pi.x), L0);
+    double dy = mi_d(__dadd_rn((double)pj.y, -(double)pi.y), L1);
+    double dz = mi_d(__dadd_rn((double)pj.z, -(double)pi.z), L2);
     double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
     r2 = __dadd_rn(r2, __dmul_rn(dz, dz));
-    return r2 < s.rc2;
+    return r2 < rc2;
+}
+
+__device__ __forceinline__ bool pair_exact(const Sys &s, float4 pi, float4 pj)
+{
+    return pair_exact_fp64(pi, pj, s.L[0], s.L[1], s.L[2], s.rc2);
 }
 
 // The float32 estimate decides every candidate outside a relative guard band
