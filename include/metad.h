@@ -179,7 +179,7 @@ metad_status metad_step_host(metad_ctx *ctx, const float *pos_host, float *force
  * stages are recorded).  end synchronises and writes, per stage index
  * 0..METAD_NUM_STAGES-1 (names from metad_stage_name), the summed device
  * milliseconds and the number of records (either pointer may be NULL). */
-#define METAD_NUM_STAGES 10
+#define METAD_NUM_STAGES 11
 metad_status metad_profile_begin(metad_ctx *ctx, int32_t max_records);
 metad_status metad_profile_end(metad_ctx *ctx, double *ms_per_stage, int32_t *records_per_stage);
 const char *metad_stage_name(int32_t stage);
@@ -280,9 +280,10 @@ metad_status metad_batch_create(metad_ctx *const *ctxs, int32_t n, metad_batch *
 metad_status metad_batch_destroy(metad_batch *batch);
 
 /* Tile setting of the per-atom kernels: at most `blocks_per_system` blocks
- * of 16 atoms' lane groups per system (0 = the single-context grid).  A
- * setting other than 0 changes the order of the FP64 block partials of the
- * CV sums (last-bit differences from metad_step), not any per-atom value.
+ * per system for each of them (0 = the single-context grid); the blocks
+ * then walk the system's atoms grid-stride.  It changes no result: those
+ * kernels carry no reduction, and the pass holding the CV sums keeps its
+ * own grid, fixed by N.
  * Errors: METAD_ERR_INVALID (negative). */
 metad_status metad_batch_set_tile(metad_batch *batch, int32_t blocks_per_system);
 

@@ -69,6 +69,7 @@ enum Stage {
     ST_NBR,
     ST_CV_FWD,
     ST_CV_AVG,
+    ST_CV_SUM,
     ST_BIAS,
     ST_ADJ,
     ST_FORCE,
@@ -80,8 +81,8 @@ enum Stage {
 // "gather": positions into cell order + rebuild test; "neighbors": the
 // conditional rebuild chain (and a stand-alone exact filter); "cv_fwd" holds
 // the fused exact filter.
-const char *kStageNames[ST_COUNT] = {"gather",  "neighbors",   "cv_fwd",       "cv_avg",  "bias",
-                                     "adjoint", "force_pairs", "force_gather", "deposit", "other"};
+const char *kStageNames[ST_COUNT] = {"gather",      "neighbors",    "cv_fwd",  "cv_avg", "cv_sum", "bias", "adjoint",
+                                     "force_pairs", "force_gather", "deposit", "other"};
 
 // Brackets the kernels of one stage with CUDA events while profiling is on,
 // and counts the kernels launched.
@@ -280,7 +281,7 @@ metad_status setup_system(metad_ctx *c)
 
 struct Buffers {
     int *rank_xyz = nullptr, *xyz_rank = nullptr;
-    char *rb = nullptr, *wlb = nullptr, *pfb = nullptr;
+    char *rb = nullptr, *wlb = nullptr, *pfb = nullptr, *geob = nullptr;
 };
 
 // Every device buffer of a context in one list: alloc(&ptr, count) allocates
@@ -299,7 +300,8 @@ metad_status state_buffers(metad_ctx *c, Buffers &b, Alloc &&alloc)
         (s = alloc(&b.rank_xyz, y.ncell)) || (s = alloc(&b.xyz_rank, y.ncell)) ||
         (s = alloc(&y.nbr, (size_t)y.max_nb * n)) || (s = alloc(&y.nn, n)) || (s = alloc(&y.nh, n)) ||
         (s = alloc(&y.vnh, n)) || (s = alloc(&b.wlb, rs * (size_t)y.max_nb * n)) ||
-        (s = alloc(&b.pfb, rs * 4 * (size_t)y.max_nb * n)) || (s = alloc(&y.pos_ref, n)) ||
+        (s = alloc(&b.pfb, rs * 4 * (size_t)y.max_nb * n)) || (s = alloc(&b.geob, rs * 4 * (size_t)y.max_nb * n)) ||
+        (s = alloc(&y.pos_ref, n)) ||
         (s = alloc(&y.vnbr, (size_t)y.max_vnb * n)) || (s = alloc(&y.vnn, n)) || (s = alloc(&y.flag, 1)) ||
         (s = alloc(&y.rebuilds, 1)) || (s = alloc(&b.rb, rs * (nq * 3 + (size_t)n * 4 + 64))) ||
         (s = alloc(&y.part, (size_t)y.part_stride * 4)) || (s = alloc(&y.ticket, 8)) ||
@@ -450,6 +452,7 @@ metad_status metad_create(const metad_params *p, metad_ctx **out)
     y.qb6 = rb + rs * (3 * nq + 2 * (size_t)n);
     y.wl = wlb;
     y.pairF = pfb;
+    y.geo = bf.geob;
     y.rank_of_xyz = rank_xyz;
     y.xyz_of_rank = xyz_rank;
     // Morton ranks of the cells: sort cell coordinates by interleaved bits
@@ -545,8 +548,11 @@ metad_status metad_cv_forward(metad_ctx *c, double *cv_host, double *per_atom_de
         c->filter_pending = false;
     }
     if (c->p.n_cv == 2) {
-        StageScope t(c, ST_CV_AVG, 1);
+        StageScope t(c, ST_CV_AVG, 1);  // with the CV sums
         metad::launch_cv_avg(c->sys, c->fp64, c->stream);
+    } else {
+        StageScope t(c, ST_CV_SUM, 1);
+        metad::launch_cv_sum(c->sys, c->fp64, c->stream);
     }
     if (per_atom_dev) {
         StageScope t(c, ST_OTHER, 1);
@@ -773,7 +779,7 @@ metad_status metad_export_neighbors(metad_ctx *c, int64_t *pairs_host, int64_t c
     }
     if (c->filter_pending) {
         StageScope t(c, ST_NBR, 1);
-        metad::launch_filter(c->sys, c->stream);
+        metad::launch_filter(c->sys, c->fp64, c->stream);
         c->filter_pending = false;
     }
     {
@@ -910,7 +916,7 @@ metad_status metad_neighbor_stats(metad_ctx *c, int64_t *entries, int32_t *max_p
     int *mx = reinterpret_cast<int *>(sum + 1);
     if (c->filter_pending) {
         StageScope t(c, ST_NBR, 1);
-        metad::launch_filter(c->sys, c->stream);
+        metad::launch_filter(c->sys, c->fp64, c->stream);
         c->filter_pending = false;
     }
     {
@@ -1105,12 +1111,13 @@ metad_status metad_batch_step(metad_batch *b, const float *const *pos_dev, float
     for (int g = 0; g < metad::kGridKinds; ++g) rows[g] = metad::BatchView{dsys, dpre + g * (n + 1), n};
     metad::launch_batch_gather(rows[metad::GK_ATOM256], totals[metad::GK_ATOM256], b->stream);
     metad::launch_batch_rebuild(rows, totals, b->stream);
-    metad::launch_batch_cv(rows[metad::GK_PERSIST], totals[metad::GK_PERSIST], b->fp64, b->ncv, b->stream);
+    metad::launch_batch_cv(rows[metad::GK_GROUPS], totals[metad::GK_GROUPS], rows[metad::GK_CV], totals[metad::GK_CV],
+                           rows[metad::GK_SUM], totals[metad::GK_SUM], b->fp64, b->ncv, b->stream);
     metad::launch_batch_bias(rows[metad::GK_HILLS], totals[metad::GK_HILLS], 0, b->stream);
     metad::launch_batch_force(rows[metad::GK_GROUPS], totals[metad::GK_GROUPS], rows[metad::GK_ATOM128],
                               totals[metad::GK_ATOM128], b->fp64, b->ncv, b->stream);
     if (any_deposit) metad::launch_batch_bias(rows[metad::GK_DEPOSIT], totals[metad::GK_DEPOSIT], 1, b->stream);
-    b->launches += 1 + 8 + (b->ncv == 2 ? 2 : 1) + 1 + (b->ncv == 2 ? 3 : 2) + (any_deposit ? 1 : 0);
+    b->launches += 1 + 8 + 2 + 1 + (b->ncv == 2 ? 3 : 2) + (any_deposit ? 1 : 0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         for (metad_ctx *c : b->ctx) c->failed = true;

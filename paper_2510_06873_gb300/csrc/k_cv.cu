@@ -248,49 +248,13 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
     return t;
 }
 
-// Block partial -> part[slot * part_stride + block]; the last block to finish
-// sums all partials in block order (fixed, independent of completion order)
-// and stores total * scale in *dst.
-__device__ void last_block_reduce(const Sys &s, Blk k, double v, int slot, double *dst, double scale)
-{
-    __shared__ double sh[32];
-    __shared__ bool am_last;
-    if (k.nb > s.part_stride) {  // never with group_grid(); refuse rather than overrun
-        if (k.b == 0 && threadIdx.x == 0) set_err(s, kErrInternal);
-        return;
-    }
-    double t = block_sum(v, sh);
-    double *part = s.part + (size_t)slot * s.part_stride;
-    if (threadIdx.x == 0) {
-        part[k.b] = t;
-        __threadfence();
-        unsigned prev = atomicAdd(&s.ticket[slot], 1u);
-        am_last = (prev == (unsigned)k.nb - 1u);
-    }
-    __syncthreads();
-    if (!am_last) return;
-    __threadfence();
-    double acc = 0.0;
-    // each thread sums a contiguous chunk in order; chunks are then added in
-    // thread order: a fixed association for a given grid size
-    const int nb = k.nb, per = (nb + blockDim.x - 1) / blockDim.x;
-    for (int b = threadIdx.x * per; b < min(nb, (int)(threadIdx.x + 1) * per); ++b) acc += __ldcg(part + b);
-    __shared__ double all[kBlockAtoms];
-    all[threadIdx.x] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double tot = 0.0;
-        for (int k = 0; k < (int)blockDim.x; ++k) tot += all[k];
-        *dst = tot * scale;
-        s.ticket[slot] = 0u;
-    }
-}
-
+// Displacement (cached by the exact filter), 1/r, switch weight and its
+// derivative of one exact entry.
 template <typename real>
-__device__ __forceinline__ void pair_geometry(const Sys &s, float4 pi, float4 pj, Vec3<real> &d, real &inv_r,
-                                              real &w, real &dw)
+__device__ __forceinline__ void cached_geometry(const Sys &s, size_t slot, Vec3<real> &d, real &inv_r, real &w,
+                                                real &dw, bool &cn)
 {
-    d = displacement<real>(s, pi, pj);
+    load_geo<real>(s, slot, d, cn);
     real r2 = d.x * d.x + d.y * d.y + d.z * d.z;
     inv_r = rsqrt_r<real>(r2);
     switch_eval<real>(s, r2 * inv_r, w, dw);
@@ -393,22 +357,20 @@ template <typename real, bool kFilter>
 __device__ __forceinline__ double cv_fwd_group(const Sys &s, const AtomLane a)
 {
     int nn_f = 0;
-    if (kFilter) nn_f = filter_row(s, a);
+    if (kFilter) nn_f = filter_row<real>(s, a);
     real v[kRec];  // 0..12: sum w Y_m ; 13: W ; 14: CN
 #pragma unroll
     for (int m = 0; m < kRec; ++m) v[m] = real(0);
     if (a.ok) {
-        const float4 pi = s.pos_s[a.i];
         const int nn = kFilter ? nn_f : s.nn[a.i];
-        const int *row = nbr_row(s, a.i);
         real *wrow = R<real>(s.wl) + (size_t)a.i * s.max_nb;
         for (int k = a.l; k < nn; k += kG) {
-            const float4 pj = s.pos_s[row[k]];
             Vec3<real> d;
             real inv_r, w, dw;
-            pair_geometry<real>(s, pi, pj, d, inv_r, w, dw);
+            bool cn;
+            cached_geometry<real>(s, (size_t)a.i * s.max_nb + k, d, inv_r, w, dw, cn);
             wrow[k] = w;
-            if (!s.cn_unlike || pj.w != pi.w) v[14] += w;
+            if (cn) v[14] += w;
             v[13] += w;
             if (s.ncv == 2) {
                 real Y[kNY];
@@ -442,10 +404,8 @@ __device__ __forceinline__ double cv_fwd_group(const Sys &s, const AtomLane a)
 template <typename real, bool kFilter>
 __device__ __forceinline__ void cv_fwd(const Sys &s, Blk k)
 {
-    double acc = 0.0;
     const int groups = group_grid(s.n);
-    for (int it = 0, g; (g = work_item(k, it)) < groups; ++it) acc += cv_fwd_group<real, kFilter>(s, atom_lane_at(s, g));
-    last_block_reduce(s, k, acc, 0, s.scal + kS0, 1.0 / s.n);
+    for (int it = 0, g; (g = work_item(k, it)) < groups; ++it) cv_fwd_group<real, kFilter>(s, atom_lane_at(s, g));
 }
 
 template <typename real, bool kFilter>
@@ -462,12 +422,11 @@ __global__ void __launch_bounds__(kBlockAtoms) kb_cv_fwd(BatchView v)
 // a5: qbar_m(i), qbar6(i), s2.  Record b: b_m(i) = K_m qbar_m(i) / (N qbar6
 // (1 + W_i)) (slots 0..12) and beta_i = b(i).qbar(i) (slot 13).
 template <typename real>
-__device__ __forceinline__ double cv_avg_group(const Sys &s, const AtomLane a)
+__device__ __forceinline__ void cv_avg_group(const Sys &s, const AtomLane a, double &cn_sum, double &q6_sum)
 {
     // lane l owns components 2l, 2l + 1 and walks every neighbour of the atom
     const real *q = R<real>(s.q);
     real a0 = real(0), a1 = real(0);
-    double q6_out = 0.0;
     if (a.ok) {
         const int nn = s.nn[a.i];
         const int *row = nbr_row(s, a.i);
@@ -505,19 +464,79 @@ __device__ __forceinline__ double cv_avg_group(const Sys &s, const AtomLane a)
         store_pair<real>(R<real>(s.b), a.i, a.l, b0, b1);
         if (a.l == 0) {
             R<real>(s.qb6)[a.i] = qb6;
-            q6_out = (double)qb6;
+            cn_sum += (double)R<real>(s.cn)[a.i];
+            q6_sum += (double)qb6;
         }
     }
-    return q6_out;
 }
 
+// Block sums c, q -> part[b], part[part_stride + b]; the last block to finish
+// adds them (thread t takes blocks t, t + blockDim, ... in order, then a
+// fixed tree): s1 = C / N, s2 = Q / N.  A fixed association for a given grid.
+__device__ void last_block_cv(const Sys &s, Blk k, double c, double q)
+{
+    __shared__ double sh[32];
+    __shared__ bool am_last;
+    if (k.nb > s.part_stride) {  // never with the grids used; refuse rather than overrun
+        if (k.b == 0 && threadIdx.x == 0) set_err(s, kErrInternal);
+        return;
+    }
+    c = block_sum(c, sh);
+    q = block_sum(q, sh);
+    double *pc = s.part, *pq = s.part + s.part_stride;
+    if (threadIdx.x == 0) {
+        pc[k.b] = c;
+        pq[k.b] = q;
+        __threadfence();
+        am_last = atomicAdd(&s.ticket[0], 1u) == (unsigned)k.nb - 1u;
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    double C = 0.0, Q = 0.0;
+    for (int b = threadIdx.x; b < k.nb; b += blockDim.x) {
+        C += __ldcg(pc + b);
+        Q += __ldcg(pq + b);
+    }
+    C = block_sum(C, sh);
+    Q = block_sum(Q, sh);
+    if (threadIdx.x == 0) {
+        s.scal[kS0] = C / s.n;
+        s.scal[kS1] = s.ncv == 2 ? Q / s.n : 0.0;
+        s.ticket[0] = 0u;
+    }
+}
+
+// a5 with the CV sums: persistent (the block partials are few).
 template <typename real>
 __device__ __forceinline__ void cv_avg(const Sys &s, Blk k)
 {
-    double acc = 0.0;
+    double c = 0.0, q = 0.0;
     const int groups = group_grid(s.n);
-    for (int it = 0, g; (g = work_item(k, it)) < groups; ++it) acc += cv_avg_group<real>(s, atom_lane_at(s, g));
-    last_block_reduce(s, k, acc, 1, s.scal + kS1, 1.0 / s.n);
+    for (int it = 0, g; (g = work_item(k, it)) < groups; ++it) cv_avg_group<real>(s, atom_lane_at(s, g), c, q);
+    last_block_cv(s, k, c, q);
+}
+
+// The CV sum when there is no Q6 pass (n_cv == 1): thread t of block b sums
+// the CN of atoms b kSumThreads + t, + blocks kSumThreads, ... in order.
+template <typename real>
+__device__ __forceinline__ void cv_sum(const Sys &s, Blk k)
+{
+    double c = 0.0;
+    const real *cn = R<real>(s.cn);
+    for (int i = k.b * blockDim.x + threadIdx.x; i < s.n; i += k.nb * blockDim.x) c += (double)cn[i];
+    last_block_cv(s, k, c, 0.0);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kSumThreads) k_cv_sum(Sys s) { cv_sum<real>(s, own_blk()); }
+
+template <typename real>
+__global__ void __launch_bounds__(kSumThreads) kb_cv_sum(BatchView v)
+{
+    Blk k;
+    const Sys &s = v.sys[batch_system(v, k)];
+    cv_sum<real>(s, k);
 }
 
 template <typename real>
@@ -637,13 +656,12 @@ __device__ __forceinline__ void pair_force(const Sys &s, int i, int k, real cn_f
 {
     const int j = nbr_row(s, i)[k];
     const int nhj = s.nh[j], nnj = s.nn[j];
-    const float4 pi = s.pos_s[i];
-    const float4 pj = s.pos_s[j];
     Vec3<real> d;
     real inv_r, w, dw;
-    pair_geometry<real>(s, pi, pj, d, inv_r, w, dw);
+    bool cn;
+    cached_geometry<real>(s, (size_t)i * s.max_nb + k, d, inv_r, w, dw, cn);
     const real ux = d.x * inv_r, uy = d.y * inv_r, uz = d.z * inv_r;
-    real radial = (!s.cn_unlike || pj.w != pi.w) ? cn_fac * dw : real(0);
+    real radial = cn ? cn_fac * dw : real(0);
     real fx = real(0), fy = real(0), fz = real(0);
     if (s.ncv == 2) {
         const real *hh = R<real>(s.h), *qq = R<real>(s.q), *qbb = R<real>(s.b);
@@ -832,13 +850,12 @@ __global__ void k_per_atom_out(Sys s, double *out)
     if (s.ncv == 2) out[(size_t)s.n + u] = (double)R<real>(s.qb6)[i];
 }
 
-inline int atom_blocks(int n) { return persist_grid(n); }
 
 }  // namespace
 
 void launch_cv_fwd(const Sys &s, int fp64, int fused_filter, cudaStream_t st)
 {
-    const int nb = atom_blocks(s.n);
+    const int nb = group_grid(s.n);
     if (fp64) {
         if (fused_filter)
             k_cv_fwd<double, true><<<nb, kBlockAtoms, 0, st>>>(s);
@@ -855,9 +872,17 @@ void launch_cv_fwd(const Sys &s, int fp64, int fused_filter, cudaStream_t st)
 void launch_cv_avg(const Sys &s, int fp64, cudaStream_t st)
 {
     if (fp64)
-        k_cv_avg<double><<<atom_blocks(s.n), kBlockAtoms, 0, st>>>(s);
+        k_cv_avg<double><<<grid_blocks(s, GK_CV, 0), kBlockAtoms, 0, st>>>(s);
     else
-        k_cv_avg<float><<<atom_blocks(s.n), kBlockAtoms, 0, st>>>(s);
+        k_cv_avg<float><<<grid_blocks(s, GK_CV, 0), kBlockAtoms, 0, st>>>(s);
+}
+
+void launch_cv_sum(const Sys &s, int fp64, cudaStream_t st)
+{
+    if (fp64)
+        k_cv_sum<double><<<grid_blocks(s, GK_SUM, 0), kSumThreads, 0, st>>>(s);
+    else
+        k_cv_sum<float><<<grid_blocks(s, GK_SUM, 0), kSumThreads, 0, st>>>(s);
 }
 
 void launch_adjoint(const Sys &s, int fp64, cudaStream_t st)
@@ -890,15 +915,22 @@ void launch_force_gather(const Sys &s, int fp64, float *F, int accumulate, cudaS
         k_force_gather<float><<<group_grid(s.n), kBlockAtoms, 0, st>>>(t);
 }
 
-void launch_batch_cv(const BatchView &v, int total, int fp64, int ncv, cudaStream_t st)
+void launch_batch_cv(const BatchView &groups, int group_total, const BatchView &cv, int cv_total,
+                     const BatchView &sums, int sum_total, int fp64, int ncv, cudaStream_t st)
 {
-    if (total <= 0) return;
+    if (group_total <= 0) return;
     if (fp64) {
-        kb_cv_fwd<double><<<total, kBlockAtoms, 0, st>>>(v);
-        if (ncv == 2) kb_cv_avg<double><<<total, kBlockAtoms, 0, st>>>(v);
+        kb_cv_fwd<double><<<group_total, kBlockAtoms, 0, st>>>(groups);
+        if (ncv == 2)
+            kb_cv_avg<double><<<cv_total, kBlockAtoms, 0, st>>>(cv);
+        else
+            kb_cv_sum<double><<<sum_total, kSumThreads, 0, st>>>(sums);
     } else {
-        kb_cv_fwd<float><<<total, kBlockAtoms, 0, st>>>(v);
-        if (ncv == 2) kb_cv_avg<float><<<total, kBlockAtoms, 0, st>>>(v);
+        kb_cv_fwd<float><<<group_total, kBlockAtoms, 0, st>>>(groups);
+        if (ncv == 2)
+            kb_cv_avg<float><<<cv_total, kBlockAtoms, 0, st>>>(cv);
+        else
+            kb_cv_sum<float><<<sum_total, kSumThreads, 0, st>>>(sums);
     }
 }
 

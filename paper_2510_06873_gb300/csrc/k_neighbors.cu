@@ -278,10 +278,11 @@ __device__ __forceinline__ void verlet(const Sys &s, Blk k)
 }
 
 // Exact rows from the Verlet rows, when the CV kernel does not fuse it.
+template <typename real>
 __global__ void __launch_bounds__(kBlockAtoms) k_filter(Sys s)
 {
     const int groups = group_grid(s.n);
-    for (int blk = blockIdx.x; blk < groups; blk += gridDim.x) filter_row(s, atom_lane_at(s, blk));
+    for (int blk = blockIdx.x; blk < groups; blk += gridDim.x) filter_row<real>(s, atom_lane_at(s, blk));
 }
 
 // End of a rebuild: the flag is cleared for the next step (kept set when the
@@ -412,12 +413,16 @@ int grid_blocks(const Sys &s, int kind, int persist_cap)
     case GK_CELL128_CAP: return capped((s.ncell + 127) / 128);
     case GK_GROUPS_CAP: return capped(persist_grid(s.n));
     case GK_ONE: return 1;
-    case GK_PERSIST: {
-        const int g = persist_grid(s.n);
+    case GK_GROUPS: {
+        const int g = group_grid(s.n);
         return persist_cap > 0 && persist_cap < g ? persist_cap : g;
     }
-    case GK_ATOM128: return (s.n + 127) / 128;
-    case GK_GROUPS: return group_grid(s.n);
+    case GK_CV: return persist_grid(s.n);  // not tiled: its grid fixes the CV sums' order
+    case GK_ATOM128: {
+        const int g = (s.n + 127) / 128;
+        return persist_cap > 0 && persist_cap < g ? persist_cap : g;
+    }
+    case GK_SUM: return sum_blocks(s.n);
     case GK_HILLS: return bias_blocks(s.K);
     case GK_DEPOSIT: return s.deposit ? bias_blocks(s.K) : 0;
     }
@@ -458,9 +463,12 @@ void launch_batch_rebuild(const BatchView *rows, const int *totals, cudaStream_t
     kb_clear_flag<<<totals[GK_ONE], 32, 0, st>>>(rows[GK_ONE]);
 }
 
-void launch_filter(const Sys &s, cudaStream_t st)
+void launch_filter(const Sys &s, int fp64, cudaStream_t st)
 {
-    k_filter<<<persist_grid(s.n), kBlockAtoms, 0, st>>>(s);
+    if (fp64)
+        k_filter<double><<<group_grid(s.n), kBlockAtoms, 0, st>>>(s);
+    else
+        k_filter<float><<<group_grid(s.n), kBlockAtoms, 0, st>>>(s);
 }
 
 void launch_nn_stats(const Sys &s, unsigned long long *sum, int *mx, cudaStream_t st)

@@ -74,7 +74,9 @@ struct Sys {
     int *nn;               // [n]
     int *nh;               // [n] entries with j > i
     void *wl;              // real [n][max_nb]: switch weight w_ij of each entry
-    void *pairF;           // real [n][max_nb][4]: force of pair (i, j > i), slot of i's entry
+    void *pairF;           // real [n][max_nb][4]: G_ij in i's entry of j, -G_ji in the others
+    void *geo;             // real [n][max_nb][4]: r_j - r_i (minimum image) and the CN mask
+                           // of each exact entry, written by the exact filter
     // Verlet list (cutoff rc + skin, built at the reference positions)
     float4 *pos_ref;       // sorted positions at the last rebuild
     int *vnbr;             // [n][max_vnb]
@@ -154,9 +156,10 @@ enum GridKind : int {
     GK_CELL128_CAP,    // rebuild: cell sort
     GK_GROUPS_CAP,     // rebuild: Verlet rows
     GK_ONE,            // one block per system
-    GK_PERSIST,        // per-atom lane-group kernels
-    GK_ATOM128,        // one block per 128 atoms (pair-parallel force)
-    GK_GROUPS,         // one block per lane-group block of atoms (no reduction)
+    GK_GROUPS,         // one block per 16 atoms (lane-group kernels); a batch tile caps it
+    GK_CV,             // the Q6 pass with the CV sums: persistent, by N only
+    GK_ATOM128,        // one block per 128 atoms (pair-parallel force); a batch tile caps it
+    GK_SUM,            // the CV sums: blocks by N only
     GK_HILLS,          // hill kernel, evaluation
     GK_DEPOSIT,        // hill kernel, deposit (systems that deposit)
     kGridKinds
@@ -170,7 +173,9 @@ int grid_blocks(const Sys &s, int kind, int persist_cap);
 // Batched stage launches (one launch each over every system of the view).
 void launch_batch_gather(const BatchView &v, int total, cudaStream_t st);
 void launch_batch_rebuild(const BatchView *rows, const int *totals, cudaStream_t st);
-void launch_batch_cv(const BatchView &v, int total, int fp64, int ncv, cudaStream_t st);
+void launch_batch_cv(const BatchView &groups, int group_total, const BatchView &cv, int cv_total,
+                     const BatchView &sums, int sum_total, int fp64, int ncv, cudaStream_t st);
+void launch_cv_sum(const Sys &s, int fp64, cudaStream_t st);
 void launch_batch_bias(const BatchView &v, int total, int deposit, cudaStream_t st);
 void launch_batch_force(const BatchView &groups, int group_total, const BatchView &pairs, int pair_total, int fp64,
                         int ncv, cudaStream_t st);
@@ -179,7 +184,7 @@ void launch_batch_collect(const BatchView &v, double *out, cudaStream_t st);
 // Launch entry points (stream-ordered, no host synchronisation).
 void launch_gather_check(const Sys &s, cudaStream_t st);
 void launch_rebuild(const Sys &s, cudaStream_t st);  // kernels early-exit unless *flag
-void launch_filter(const Sys &s, cudaStream_t st);
+void launch_filter(const Sys &s, int fp64, cudaStream_t st);
 void launch_cv_fwd(const Sys &s, int fp64, int fused_filter, cudaStream_t st);
 void launch_cv_avg(const Sys &s, int fp64, cudaStream_t st);
 void launch_bias(const Sys &s, int K, const double *s_dev, double *out_dev, int deposit, cudaStream_t st);
@@ -382,9 +387,18 @@ constexpr int kAtomsPerBlock = kBlockAtoms / kG;
 // it, so launches and allocations can never disagree.
 __host__ __device__ inline int group_grid(int n) { return (n + kAtomsPerBlock - 1) / kAtomsPerBlock; }
 
-// The per-atom kernels are persistent: at most kPersistBlocks blocks walk the
-// atom groups grid-stride, so a launch's FP64 block partials are few and the
-// last block's fixed-order sum of them is short.
+// Without a Q6 pass the CN sum runs in its own kernel: kSumThreads threads
+// per block, one block per kSumAtoms atoms (at most kMaxBiasBlocks blocks).
+constexpr int kSumThreads = 256;
+constexpr int kSumAtoms = 2048;
+__host__ __device__ inline int sum_blocks(int n)
+{
+    const int b = (n + kSumAtoms - 1) / kSumAtoms;
+    return b < 1 ? 1 : (b > kMaxBiasBlocks ? kMaxBiasBlocks : b);
+}
+
+// Persistent grids (the CV kernels, and the capped rebuild kernels) have at
+// most kPersistBlocks blocks, walking their work grid-stride.
 constexpr int kPersistBlocks = 152 * 16;
 
 // The it-th work item (atom group or chunk) of block b of nb: items b,
@@ -443,19 +457,66 @@ __device__ __forceinline__ bool pair_exact(const Sys &s, float4 pi, float4 pj)
 }
 
 // The float32 estimate decides every candidate outside a relative guard band
-// of 3e-5 around rc^2; inside it the FP64 definition decides.
-__device__ __forceinline__ bool pair_in(const Sys &s, float4 pi, float4 pj)
+// of 3e-5 around rc^2; inside it the FP64 definition decides.  d returns the
+// float32 displacement.
+__device__ __forceinline__ bool pair_in(const Sys &s, float4 pi, float4 pj, Vec3<float> &d)
 {
-    Vec3<float> d = displacement<float>(s, pi, pj);
+    d = displacement<float>(s, pi, pj);
     float r2 = fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z));
     if (r2 < s.rc2_lo) return true;
     if (r2 > s.rc2_hi) return false;
     return pair_exact(s, pi, pj);
 }
 
+// The geometry of an exact entry, cached by the filter so the CV and force
+// passes read one contiguous record per entry instead of gathering the
+// neighbour's position again.
+template <typename real>
+__device__ __forceinline__ void store_geo(const Sys &s, size_t slot, const Vec3<float> &df, float4 pi, float4 pj);
+template <>
+__device__ __forceinline__ void store_geo<float>(const Sys &s, size_t slot, const Vec3<float> &df, float4 pi,
+                                                 float4 pj)
+{
+    const float cn = (!s.cn_unlike || pj.w != pi.w) ? 1.0f : 0.0f;
+    reinterpret_cast<float4 *>(s.geo)[slot] = make_float4(df.x, df.y, df.z, cn);
+}
+template <>
+__device__ __forceinline__ void store_geo<double>(const Sys &s, size_t slot, const Vec3<float> &, float4 pi,
+                                                  float4 pj)
+{
+    const Vec3<double> d = displacement<double>(s, pi, pj);
+    const double cn = (!s.cn_unlike || pj.w != pi.w) ? 1.0 : 0.0;
+    double2 *g = reinterpret_cast<double2 *>(s.geo) + 2 * slot;
+    g[0] = make_double2(d.x, d.y);
+    g[1] = make_double2(d.z, cn);
+}
+
+template <typename real>
+__device__ __forceinline__ void load_geo(const Sys &s, size_t slot, Vec3<real> &d, bool &cn);
+template <>
+__device__ __forceinline__ void load_geo<float>(const Sys &s, size_t slot, Vec3<float> &d, bool &cn)
+{
+    const float4 g = reinterpret_cast<const float4 *>(s.geo)[slot];
+    d.x = g.x;
+    d.y = g.y;
+    d.z = g.z;
+    cn = g.w != 0.0f;
+}
+template <>
+__device__ __forceinline__ void load_geo<double>(const Sys &s, size_t slot, Vec3<double> &d, bool &cn)
+{
+    const double2 *g = reinterpret_cast<const double2 *>(s.geo) + 2 * slot;
+    const double2 a = g[0], b = g[1];
+    d.x = a.x;
+    d.y = a.y;
+    d.z = b.x;
+    cn = b.y != 0.0;
+}
+
 // Compact atom a.i's Verlet row into its exact row, the j > i part first (the
 // Verlet row is ordered the same way), order kept within each part.  Every
 // lane of the warp must call this (loop counts are made warp-uniform).
+template <typename real>
 __device__ __forceinline__ int filter_row(const Sys &s, const AtomLane &a)
 {
     const int vn = a.ok ? s.vnn[a.i] : 0;
@@ -471,15 +532,21 @@ __device__ __forceinline__ int filter_row(const Sys &s, const AtomLane &a)
         const int k = base + a.l;
         bool in = false;
         int j = 0;
+        float4 pj = make_float4(0.f, 0.f, 0.f, 0.f);
+        Vec3<float> d;
         if (k < vn) {
             j = vrow[k];
-            in = pair_in(s, pi, s.pos_s[j]);
+            pj = s.pos_s[j];
+            in = pair_in(s, pi, pj, d);
         }
         const unsigned ball = __ballot_sync(0xffffffffu, in);
         const unsigned gm = group_mask_bits(ball);
         const unsigned gu = group_mask_bits(__ballot_sync(0xffffffffu, in && k < vh));
         const int at = cnt + __popc(gm & ((1u << a.l) - 1u));
-        if (in && at < s.max_nb) row[at] = j;
+        if (in && at < s.max_nb) {
+            row[at] = j;
+            store_geo<real>(s, (size_t)a.i * s.max_nb + at, d, pi, pj);
+        }
         cnt += __popc(gm);
         nh += __popc(gu);
     }

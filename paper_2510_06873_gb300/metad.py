@@ -84,7 +84,7 @@ _SIGS = {
     "metad_batch_launch_count": (ctypes.c_int64, [_P]),
     "metad_batch_last_error": (ctypes.c_char_p, [_P]),
 }
-METAD_NUM_STAGES = 10
+METAD_NUM_STAGES = 11
 OPTIONAL = {}
 
 

@@ -1,18 +1,19 @@
 """Tile autotuner of the batched step.
 
 A batched step concatenates every system's grid in one launch per stage.
-Its one free shape parameter is the tile: how many blocks (of 16 atoms'
-lane groups each) the per-atom kernels give one system at most.  The
-default (0) is the single-context grid, which keeps every system's result
-bit-identical to stepping it alone; smaller tiles put more atoms on each
-block, which trades parallelism inside a large system for fewer, fuller
-blocks across many small ones (and changes only the order of the FP64 block
-partials of the CV sums).
+Its one free shape parameter is the tile: how many blocks the per-atom
+kernels give one system at most (the blocks then walk that system's atoms
+grid-stride).  The default (0) is the single-context grid; smaller tiles
+put more atoms on each block, trading parallelism inside a large system for
+fewer, fuller blocks across many small ones.  No setting changes a result:
+those kernels carry no reduction and the pass with the CV sums keeps a grid
+fixed by the atom count, so every system stays bit-identical to stepping it
+alone.
 
 `tune_batch` times each candidate over a few batched steps of the caller's
 own inputs with CUDA events on the batch's stream and keeps the fastest.
-The steps it runs deposit nothing, so the only state they change is the
-neighbour list (rebuilt for the same positions: the same list).
+The steps it runs deposit nothing and reuse the same positions, so they
+change no state (the neighbour lists are not rebuilt).
 """
 from __future__ import annotations
 

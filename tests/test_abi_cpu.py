@@ -77,7 +77,7 @@ def test_grid_needs_two_cvs(metad):
 def test_status_strings_and_stage_names(metad):
     assert metad.status_string(0) == "ok"
     assert metad.status_string(4) == "capacity exceeded"
-    assert [metad.metad_stage_name(k) for k in range(metad.METAD_NUM_STAGES)][6:8] == ["force_pairs", "force_gather"]
+    assert [metad.metad_stage_name(k) for k in range(metad.METAD_NUM_STAGES)][7:9] == ["force_pairs", "force_gather"]
     assert metad.lib().metad_destroy(None) == 0
 
 
