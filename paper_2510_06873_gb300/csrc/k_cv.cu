@@ -250,11 +250,11 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
 
 // Displacement (cached by the exact filter), 1/r, switch weight and its
 // derivative of one exact entry.
-template <typename real>
+template <typename real, bool kLast = false>
 __device__ __forceinline__ void cached_geometry(const Sys &s, size_t slot, Vec3<real> &d, real &inv_r, real &w,
                                                 real &dw, bool &cn)
 {
-    load_geo<real>(s, slot, d, cn);
+    load_geo<real, kLast>(s, slot, d, cn);
     real r2 = d.x * d.x + d.y * d.y + d.z * d.z;
     inv_r = rsqrt_r<real>(r2);
     switch_eval<real>(s, r2 * inv_r, w, dw);
@@ -627,18 +627,20 @@ __global__ void __launch_bounds__(kBlockAtoms) kb_adjoint(BatchView v)
 //   ds2/dw = (h_i + h_j).Y - gamma_i - gamma_j + b_i.q_j + b_j.q_i
 //   ds2/dd = ds2/dw w' d/r + w sum_m (h_i + h_j)_m dY_m/dd
 //   ds1/dd = (2/N) w' d/r [unlike]
+// The pair slots are a stream (written once, read once by pass 2): stored
+// and loaded evict-first, so they leave the gathered records in L2.
 template <typename real>
 __device__ __forceinline__ void store_pair_force(real *slot, real fx, real fy, real fz);
 template <>
 __device__ __forceinline__ void store_pair_force<float>(float *slot, float fx, float fy, float fz)
 {
-    *reinterpret_cast<float4 *>(slot) = make_float4(fx, fy, fz, 0.0f);
+    __stcs(reinterpret_cast<float4 *>(slot), make_float4(fx, fy, fz, 0.0f));
 }
 template <>
 __device__ __forceinline__ void store_pair_force<double>(double *slot, double fx, double fy, double fz)
 {
-    reinterpret_cast<double2 *>(slot)[0] = make_double2(fx, fy);
-    reinterpret_cast<double2 *>(slot)[1] = make_double2(fz, 0.0);
+    __stcs(reinterpret_cast<double2 *>(slot), make_double2(fx, fy));
+    __stcs(reinterpret_cast<double2 *>(slot) + 1, make_double2(fz, 0.0));
 }
 
 // Pair-parallel: the half-row entries (k < nh_i) of a chunk of kPairChunk
@@ -659,7 +661,7 @@ __device__ __forceinline__ void pair_force(const Sys &s, int i, int k, real cn_f
     Vec3<real> d;
     real inv_r, w, dw;
     bool cn;
-    cached_geometry<real>(s, (size_t)i * s.max_nb + k, d, inv_r, w, dw, cn);
+    cached_geometry<real, true>(s, (size_t)i * s.max_nb + k, d, inv_r, w, dw, cn);
     const real ux = d.x * inv_r, uy = d.y * inv_r, uz = d.z * inv_r;
     real radial = cn ? cn_fac * dw : real(0);
     real fx = real(0), fy = real(0), fz = real(0);
@@ -770,7 +772,7 @@ __device__ __forceinline__ void load_pair_force(const real *slot, real &fx, real
 template <>
 __device__ __forceinline__ void load_pair_force<float>(const float *slot, float &fx, float &fy, float &fz)
 {
-    const float4 t = *reinterpret_cast<const float4 *>(slot);
+    const float4 t = __ldcs(reinterpret_cast<const float4 *>(slot));
     fx = t.x;
     fy = t.y;
     fz = t.z;
@@ -778,8 +780,8 @@ __device__ __forceinline__ void load_pair_force<float>(const float *slot, float 
 template <>
 __device__ __forceinline__ void load_pair_force<double>(const double *slot, double &fx, double &fy, double &fz)
 {
-    const double2 a = reinterpret_cast<const double2 *>(slot)[0];
-    const double2 b = reinterpret_cast<const double2 *>(slot)[1];
+    const double2 a = __ldcs(reinterpret_cast<const double2 *>(slot));
+    const double2 b = __ldcs(reinterpret_cast<const double2 *>(slot) + 1);
     fx = a.x;
     fy = a.y;
     fz = b.x;

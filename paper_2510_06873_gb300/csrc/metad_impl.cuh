@@ -456,12 +456,23 @@ __device__ __forceinline__ bool pair_exact(const Sys &s, float4 pi, float4 pj)
     return pair_exact_fp64(pi, pj, s.L[0], s.L[1], s.L[2], s.rc2);
 }
 
-// The float32 estimate decides every candidate outside a relative guard band
-// of 3e-5 around rc^2; inside it the FP64 definition decides.  d returns the
-// float32 displacement.
-__device__ __forceinline__ bool pair_in(const Sys &s, float4 pi, float4 pj, Vec3<float> &d)
+// displacement<float> for code where the whole warp is converged: the plain
+// difference, and the boundary fix only when some lane of the warp needs it
+// (a vote), instead of both fixes evaluated for every pair.  The same bits:
+// mi_axis returns the plain difference exactly when |d| <= L/2.
+__device__ __forceinline__ Vec3<float> displacement_warp(const Sys &s, float4 pi, float4 pj)
 {
-    d = displacement<float>(s, pi, pj);
+    Vec3<float> d{pj.x - pi.x, pj.y - pi.y, pj.z - pi.z};
+    const bool wrap = fabsf(d.x) > s.halfL[0] || fabsf(d.y) > s.halfL[1] || fabsf(d.z) > s.halfL[2];
+    if (__any_sync(0xffffffffu, wrap)) d = displacement<float>(s, pi, pj);
+    return d;
+}
+
+// The float32 estimate decides every candidate outside a relative guard band
+// of 3e-5 around rc^2; inside it the FP64 definition decides.  d is the
+// float32 displacement of the pair.
+__device__ __forceinline__ bool pair_in(const Sys &s, float4 pi, float4 pj, const Vec3<float> &d)
+{
     float r2 = fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z));
     if (r2 < s.rc2_lo) return true;
     if (r2 > s.rc2_hi) return false;
@@ -470,7 +481,9 @@ __device__ __forceinline__ bool pair_in(const Sys &s, float4 pi, float4 pj, Vec3
 
 // The geometry of an exact entry, cached by the filter so the CV and force
 // passes read one contiguous record per entry instead of gathering the
-// neighbour's position again.
+// neighbour's position again.  The force pass reads it for the last time
+// (kLast: an evict-first load, so the stream does not push the gathered
+// per-atom records out of L2).
 template <typename real>
 __device__ __forceinline__ void store_geo(const Sys &s, size_t slot, const Vec3<float> &df, float4 pi, float4 pj);
 template <>
@@ -491,10 +504,10 @@ __device__ __forceinline__ void store_geo<double>(const Sys &s, size_t slot, con
     g[1] = make_double2(d.z, cn);
 }
 
-template <typename real>
+template <typename real, bool kLast = false>
 __device__ __forceinline__ void load_geo(const Sys &s, size_t slot, Vec3<real> &d, bool &cn);
 template <>
-__device__ __forceinline__ void load_geo<float>(const Sys &s, size_t slot, Vec3<float> &d, bool &cn)
+__device__ __forceinline__ void load_geo<float, false>(const Sys &s, size_t slot, Vec3<float> &d, bool &cn)
 {
     const float4 g = reinterpret_cast<const float4 *>(s.geo)[slot];
     d.x = g.x;
@@ -503,7 +516,26 @@ __device__ __forceinline__ void load_geo<float>(const Sys &s, size_t slot, Vec3<
     cn = g.w != 0.0f;
 }
 template <>
-__device__ __forceinline__ void load_geo<double>(const Sys &s, size_t slot, Vec3<double> &d, bool &cn)
+__device__ __forceinline__ void load_geo<float, true>(const Sys &s, size_t slot, Vec3<float> &d, bool &cn)
+{
+    const float4 g = __ldcs(reinterpret_cast<const float4 *>(s.geo) + slot);
+    d.x = g.x;
+    d.y = g.y;
+    d.z = g.z;
+    cn = g.w != 0.0f;
+}
+template <>
+__device__ __forceinline__ void load_geo<double, true>(const Sys &s, size_t slot, Vec3<double> &d, bool &cn)
+{
+    const double2 *g = reinterpret_cast<const double2 *>(s.geo) + 2 * slot;
+    const double2 a = __ldcs(g), b = __ldcs(g + 1);
+    d.x = a.x;
+    d.y = a.y;
+    d.z = b.x;
+    cn = b.y != 0.0;
+}
+template <>
+__device__ __forceinline__ void load_geo<double, false>(const Sys &s, size_t slot, Vec3<double> &d, bool &cn)
 {
     const double2 *g = reinterpret_cast<const double2 *>(s.geo) + 2 * slot;
     const double2 a = g[0], b = g[1];
@@ -530,15 +562,11 @@ __device__ __forceinline__ int filter_row(const Sys &s, const AtomLane &a)
     const int vmax = __reduce_max_sync(0xffffffffu, vn);
     for (int base = 0; base < vmax; base += kG) {
         const int k = base + a.l;
-        bool in = false;
-        int j = 0;
-        float4 pj = make_float4(0.f, 0.f, 0.f, 0.f);
-        Vec3<float> d;
-        if (k < vn) {
-            j = vrow[k];
-            pj = s.pos_s[j];
-            in = pair_in(s, pi, pj, d);
-        }
+        const bool valid = k < vn;
+        const int j = valid ? vrow[k] : 0;
+        const float4 pj = valid ? s.pos_s[j] : pi;
+        const Vec3<float> d = displacement_warp(s, pi, pj);  // every lane: a warp vote inside
+        const bool in = valid && pair_in(s, pi, pj, d);
         const unsigned ball = __ballot_sync(0xffffffffu, in);
         const unsigned gm = group_mask_bits(ball);
         const unsigned gu = group_mask_bits(__ballot_sync(0xffffffffu, in && k < vh));
