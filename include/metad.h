@@ -78,7 +78,11 @@ typedef struct {
     int32_t max_neighbors;  /* per-atom capacity of the neighbour list (0: 64;
                                rounded up to a multiple of 4) */
     int32_t device;         /* CUDA device ordinal */
-    int32_t reserved;
+    int32_t step_graph;     /* 1: metad_step replays a captured CUDA graph of
+                               its kernels, one per combination of buffers,
+                               flags and hill count (up to 16 kept, least
+                               recently used replaced; not while profiling).
+                               0 (default): direct launches */
     void *stream;           /* cudaStream_t, or NULL */
     double skin;            /* Verlet skin in Angstrom (1.0): the cell order and
                                the rc + skin candidate list are rebuilt only
@@ -201,6 +205,10 @@ metad_status metad_estimate_bytes(const metad_params *params, int64_t *bytes);
 /* Device bytes this context has requested so far (creation plus the
  * buffers allocated on first use by export and host-buffer steps). */
 int64_t metad_device_bytes(const metad_ctx *ctx);
+
+/* Turn the CUDA-graph replay of metad_step on (1) or off (0) after creation
+ * (params.step_graph sets it at creation).  Errors: METAD_ERR_INVALID. */
+metad_status metad_set_step_graph(metad_ctx *ctx, int32_t on);
 
 /* Number of kernels this context has launched since creation. */
 int64_t metad_launch_count(const metad_ctx *ctx);

@@ -43,6 +43,23 @@ struct metad_ctx {
     std::vector<int> prof_stage;
     int64_t launches = 0;
     int64_t device_bytes = 0;  // requested by cudaMalloc for this context
+    // metad_step as captured CUDA graphs, each valid for the buffers, flags
+    // and hill count it was captured with; a few are kept (least recently
+    // used replaced) so that a caller cycling through several position
+    // buffers replays instead of recapturing
+    struct StepGraph {
+        cudaGraphExec_t exec = nullptr;
+        const float *pos = nullptr;
+        float *forces = nullptr;
+        int accumulate = -1;
+        int deposit = -1;
+        int K = -1;
+        int64_t kernels = 0;
+        int64_t last_use = 0;
+    };
+    static constexpr int kGraphs = 16;
+    StepGraph graphs[kGraphs];
+    int64_t graph_clock = 0;
 };
 
 namespace {
@@ -341,6 +358,13 @@ metad_status metad_estimate_bytes(const metad_params *p, int64_t *bytes)
 
 int64_t metad_device_bytes(const metad_ctx *c) { return c ? c->device_bytes : 0; }
 
+metad_status metad_set_step_graph(metad_ctx *c, int32_t on)
+{
+    if (!c) return METAD_ERR_INVALID;
+    c->p.step_graph = on ? 1 : 0;
+    return METAD_OK;
+}
+
 void metad_params_default(metad_params *p)
 {
     if (!p) return;
@@ -399,6 +423,8 @@ metad_status metad_destroy(metad_ctx *c)
     for (void *ptr : c->allocs) cudaFree(ptr);
     if (c->host_pinned) cudaFreeHost(c->host_pinned);
     if (c->err_pinned) cudaFreeHost(c->err_pinned);
+    for (auto &g : c->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     cudaGetLastError();
     delete c;
@@ -810,7 +836,9 @@ metad_status metad_export_neighbors(metad_ctx *c, int64_t *pairs_host, int64_t c
     return METAD_OK;
 }
 
-metad_status metad_step(metad_ctx *c, const float *pos_dev, float *forces_dev, int32_t accumulate, int32_t deposit)
+namespace {
+
+metad_status step_direct(metad_ctx *c, const float *pos_dev, float *forces_dev, int32_t accumulate, int32_t deposit)
 {
     metad_status s;
     if ((s = metad_build_neighbors(c, pos_dev))) return s;
@@ -819,6 +847,73 @@ metad_status metad_step(metad_ctx *c, const float *pos_dev, float *forces_dev, i
     if ((s = metad_bias_forces(c, forces_dev, accumulate, 1.0))) return s;
     if (deposit && (s = metad_deposit_hill(c, nullptr, nullptr))) return s;
     return METAD_OK;
+}
+
+// The step's kernels take the hill count and the buffers as launch
+// arguments, so a captured graph is valid only for the values it was
+// captured with; anything else triggers a new capture.  The rebuild
+// decision is taken on the device, so one graph serves every step.
+metad_status step_graph(metad_ctx *c, const float *pos_dev, float *forces_dev, int32_t accumulate, int32_t deposit)
+{
+    metad_status s = check_usable(c);
+    if (s) return s;
+    if (!pos_dev || !forces_dev) return fail(c, METAD_ERR_INVALID, "NULL buffer");
+    if (deposit && c->K >= c->p.hill_capacity) return fail(c, METAD_ERR_CAPACITY, "hill list full");
+    const int acc = accumulate ? 1 : 0, dep = deposit ? 1 : 0;
+    metad_ctx::StepGraph *hit = nullptr, *lru = &c->graphs[0];
+    for (auto &x : c->graphs) {
+        if (x.exec && x.pos == pos_dev && x.forces == forces_dev && x.accumulate == acc && x.deposit == dep &&
+            x.K == c->K)
+            hit = &x;
+        if (!x.exec || (lru->exec && x.last_use < lru->last_use)) lru = &x;
+    }
+    metad_ctx::StepGraph &g = hit ? *hit : *lru;
+    g.last_use = ++c->graph_clock;
+    if (!hit) {
+        if (g.exec) {
+            cudaGraphExecDestroy(g.exec);
+            g.exec = nullptr;
+        }
+        const int K0 = c->K;
+        const int64_t l0 = c->launches;
+        if ((s = cuda_check(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "capture")))
+            return s;
+        metad_status st = step_direct(c, pos_dev, forces_dev, accumulate, deposit);  // records, and moves the
+                                                                                  // host state one step on
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+        if (st) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if ((s = cuda_check(c, e, "end capture"))) return s;
+        e = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if ((s = cuda_check(c, e, "graph instantiate"))) return s;
+        g.pos = pos_dev;
+        g.forces = forces_dev;
+        g.accumulate = acc;
+        g.deposit = dep;
+        g.K = K0;
+        g.kernels = c->launches - l0;
+        c->launches = l0;
+    } else {
+        // the host state a direct step would leave
+        c->sys.pos_in = reinterpret_cast<const float4 *>(pos_dev);
+        c->have_nbr = c->have_cv = c->have_bias = true;
+        c->filter_pending = false;
+        if (deposit) c->K += 1;
+    }
+    c->launches += g.kernels;
+    return cuda_check(c, cudaGraphLaunch(g.exec, c->stream), "graph launch");
+}
+
+}  // namespace
+
+metad_status metad_step(metad_ctx *c, const float *pos_dev, float *forces_dev, int32_t accumulate, int32_t deposit)
+{
+    if (c && c->p.step_graph && !c->prof_on) return step_graph(c, pos_dev, forces_dev, accumulate, deposit);
+    return step_direct(c, pos_dev, forces_dev, accumulate, deposit);
 }
 
 metad_status metad_step_host(metad_ctx *c, const float *pos_host, float *forces_host, int32_t accumulate,

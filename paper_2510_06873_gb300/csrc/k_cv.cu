@@ -330,25 +330,6 @@ __device__ __forceinline__ void load_pair<double>(const double *base, int i, int
     b = t.y;
 }
 
-// A group's row entries k0 .. k0+15, staged with two coalesced loads: lane l
-// holds entries k0 + l and k0 + l + kG; entry t is then shuffled out of lane
-// t % kG, so the dependent record loads of all 16 entries can be issued back
-// to back.
-__device__ __forceinline__ unsigned group_lane_mask()
-{
-    return 0xFFu << ((threadIdx.x & 31) & ~(kG - 1));
-}
-
-template <typename real>
-__device__ __forceinline__ void stage_row(const int *row, const real *wrow, int k0, int nn, int l, int &j0, int &j1,
-                                          real &w0, real &w1)
-{
-    j0 = k0 + l < nn ? row[k0 + l] : 0;
-    j1 = k0 + l + kG < nn ? row[k0 + l + kG] : 0;
-    w0 = k0 + l < nn ? wrow[k0 + l] : real(0);
-    w1 = k0 + l + kG < nn ? wrow[k0 + l + kG] : real(0);
-}
-
 __device__ __forceinline__ const int *nbr_row(const Sys &s, int i) { return s.nbr + (size_t)i * s.max_nb; }
 
 // a4: CN_i, W_i and q_m(i) = sum_j w_ij Y_m(rhat_ij) / W_i.
@@ -409,10 +390,10 @@ __device__ __forceinline__ void cv_fwd(const Sys &s, Blk k)
 }
 
 template <typename real, bool kFilter>
-__global__ void __launch_bounds__(kBlockAtoms) k_cv_fwd(Sys s) { cv_fwd<real, kFilter>(s, own_blk()); }
+__global__ void __launch_bounds__(kBlockAtoms, 12) k_cv_fwd(Sys s) { cv_fwd<real, kFilter>(s, own_blk()); }
 
 template <typename real>
-__global__ void __launch_bounds__(kBlockAtoms) kb_cv_fwd(BatchView v)
+__global__ void __launch_bounds__(kBlockAtoms, 12) kb_cv_fwd(BatchView v)
 {
     Blk k;
     const Sys &s = v.sys[batch_system(v, k)];
@@ -562,24 +543,14 @@ __device__ __forceinline__ void adjoint_group(const Sys &s, const AtomLane a)
         const int nn = s.nn[a.i];
         const int *row = nbr_row(s, a.i);
         const real *wrow = R<real>(s.wl) + (size_t)a.i * s.max_nb;
-        const unsigned gm = group_lane_mask();
-        for (int k0 = 0; k0 < nn; k0 += 2 * kG) {
-            int j0, j1;
-            real w0, w1;
-            stage_row<real>(row, wrow, k0, nn, a.l, j0, j1, w0, w1);
-            real x0[2 * kG], x1[2 * kG], wt[2 * kG];
-#pragma unroll
-            for (int t = 0; t < 2 * kG; ++t) {
-                const int jt = __shfl_sync(gm, t < kG ? j0 : j1, t & (kG - 1), kG);
-                wt[t] = __shfl_sync(gm, t < kG ? w0 : w1, t & (kG - 1), kG);
-                x0[t] = x1[t] = real(0);
-                if (k0 + t < nn) load_pair<real>(bb, jt, a.l, x0[t], x1[t]);
-            }
-#pragma unroll
-            for (int t = 0; t < 2 * kG; ++t) {
-                g0 += wt[t] * x0[t];
-                g1 += wt[t] * x1[t];
-            }
+#pragma unroll 4
+        for (int k = 0; k < nn; ++k) {
+            const int j = row[k];
+            const real w = wrow[k];
+            real x0, x1;
+            load_pair<real>(bb, j, a.l, x0, x1);
+            g0 += w * x0;
+            g1 += w * x1;
         }
     }
     real h0 = real(0), h1 = real(0), alpha = real(0), beta = real(0);

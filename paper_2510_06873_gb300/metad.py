@@ -29,7 +29,7 @@ class metad_params(ctypes.Structure):
         ("kB", ctypes.c_double), ("grid_on", ctypes.c_int32), ("grid_n", ctypes.c_int32 * 2),
         ("hill_capacity", ctypes.c_int32), ("grid_lo", ctypes.c_double * 2), ("grid_hi", ctypes.c_double * 2),
         ("precision", ctypes.c_int32), ("max_neighbors", ctypes.c_int32), ("device", ctypes.c_int32),
-        ("reserved", ctypes.c_int32), ("stream", ctypes.c_void_p), ("skin", ctypes.c_double),
+        ("step_graph", ctypes.c_int32), ("stream", ctypes.c_void_p), ("skin", ctypes.c_double),
     ]
 
 
@@ -75,6 +75,7 @@ _SIGS = {
                                                _P]),
     "metad_estimate_bytes": (ctypes.c_int, [ctypes.POINTER(metad_params), ctypes.POINTER(ctypes.c_int64)]),
     "metad_device_bytes": (ctypes.c_int64, [_P]),
+    "metad_set_step_graph": (ctypes.c_int, [_P, ctypes.c_int32]),
     "metad_batch_create": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)]),
     "metad_batch_destroy": (ctypes.c_int, [_P]),
     "metad_batch_set_tile": (ctypes.c_int, [_P, ctypes.c_int32]),
@@ -309,7 +310,7 @@ def metad_hill_count(ctx) -> int:
 # --------------------------------------------------------------------- helper
 def params_for(n_atoms, box, n_cv=2, sigma=(0.05, 0.02), rc=3.5, r0=2.5, sw_n=6, sw_m=12, cn_unlike=True,
                w0=1.0, biasfactor=10.0, temperature=300.0, kB=0.0083144626, grid=None, hill_capacity=65536,
-               fp64=False, max_neighbors=64, device=0, stream=None, skin=1.0) -> metad_params:
+               fp64=False, max_neighbors=64, device=0, stream=None, skin=1.0, step_graph=False) -> metad_params:
     """metad_params from keyword values; grid = (n, lo, hi) or None."""
     p = metad_params_default()
     p.n_atoms = int(n_atoms)
@@ -333,6 +334,7 @@ def params_for(n_atoms, box, n_cv=2, sigma=(0.05, 0.02), rc=3.5, r0=2.5, sw_n=6,
     p.device = int(device)
     p.stream = stream
     p.skin = float(skin)
+    p.step_graph = 1 if step_graph else 0
     return p
 
 
@@ -436,6 +438,9 @@ class Metad:
     def device_bytes(self) -> int:
         return metad_device_bytes(self.ctx)
 
+    def set_step_graph(self, on: bool):
+        metad_set_step_graph(self.ctx, on)
+
 
 def metad_estimate_bytes(p: metad_params) -> int:
     out = ctypes.c_int64(0)
@@ -445,6 +450,10 @@ def metad_estimate_bytes(p: metad_params) -> int:
 
 def metad_device_bytes(ctx) -> int:
     return int(lib().metad_device_bytes(ctx))
+
+
+def metad_set_step_graph(ctx, on: bool):
+    _check(ctx, lib().metad_set_step_graph(ctx, 1 if on else 0), "metad_set_step_graph")
 
 
 # ------------------------------------------------------------------ batches

@@ -333,6 +333,38 @@ def test_accumulate_scale_and_determinism(dev):
     assert torch.allclose(base, 0.25 - 2.0 * F1, rtol=1e-6, atol=1e-9)
 
 
+def test_graph_replay_matches_direct_steps(dev):
+    """metad_step from a captured CUDA graph gives the direct launches' bits,
+    through buffer changes (recapture), a deposit (the hill count changes)
+    and an accumulate flag change."""
+    system = synth.wurtzite_system(5000, cfg=94)
+    mp = synth.MethodParams(n_cv=2)
+    p = oracle.params_from(mp, system.box)
+    s0, _, _ = oracle.cv(system.base, p)
+    c = synth.hill_centres(94, 0, s0, mp.sigma, 300)
+    direct = make_ctx(dev, system, mp)
+    graph = make_ctx(dev, system, mp)
+    graph.set_step_graph(True)
+    direct.deposit_hills(c, want_heights=False)
+    graph.deposit_hills(c, want_heights=False)
+    frames = [torch.from_numpy(synth.perturbed_frame(system, f)).to(dev) for f in range(2)]
+    FA = torch.zeros((system.n, 3), dtype=torch.float32, device=dev)
+    FB = torch.zeros_like(FA)
+    launches0 = (direct.launch_count, graph.launch_count)
+    for step in range(8):
+        pos = frames[step % 2]
+        dep = step == 3
+        acc = step >= 6
+        direct.step(pos, FA, accumulate=acc, deposit=dep)
+        graph.step(pos, FB, accumulate=acc, deposit=dep)
+        cvA, VA, _ = direct.read_results()
+        cvB, VB, _ = graph.read_results()
+        assert np.array_equal(cvA, cvB) and VA == VB, step
+        assert torch.equal(FA, FB), step
+    assert graph.hill_count == direct.hill_count == 301
+    assert graph.launch_count - launches0[1] == direct.launch_count - launches0[0]
+
+
 def test_call_order_and_capacity_errors(dev):
     metad = _metad()
     system = synth.wurtzite_system(3000, cfg=93)
