@@ -328,6 +328,32 @@ int64_t metad_batch_launch_count(const metad_batch *batch);
 /* Text of the last error recorded on this batch (never NULL). */
 const char *metad_batch_last_error(const metad_batch *batch);
 
+/* -------------------------------------------------------------- free energy
+ * Analysis passes (not per step; each call allocates a device buffer for
+ * its own use and synchronises).  The grid is regular: n[d] bins over
+ * [lo[d], hi[d]) per CV (n[1], lo[1], hi[1] unused when n_cv == 1), laid
+ * out row-major with the first CV slowest; F_host is double [n0 (x n1)].
+ *
+ * metad_fes_grid: the well-tempered sum-of-hills estimate at the bin centres
+ * s_d = lo_d + (i_d + 1/2)(hi_d - lo_d)/n_d,
+ *     F(s) = -(gamma / (gamma - 1)) V(s),  gamma = params.biasfactor,
+ * with V this context's bias (live hills + grid), shifted so the minimum
+ * over the grid is 0 (Methods: the bias fills the FES; the well-tempered
+ * limit is read here as the standard one, the paper prints no formula).
+ *
+ * metad_fes_reweight: Eqs. 4-5 on the grid's histogram: for T samples
+ * (samples_host: double [T][n_cv] CV values; V_host: double [T] the bias at
+ * each, as a biased run records them),
+ *     P_b = sum_{t in b} exp(beta V_t) / sum_{t inside the grid} exp(beta V_t),
+ *     F_b = -(1/beta) log P_b,  beta = 1 / (params.kB params.temperature),
+ * shifted to minimum 0 over the non-empty bins; empty bins are +inf.  Every
+ * sum runs in sample order (bit-reproducible).
+ * Errors: METAD_ERR_INVALID (NULL pointers, n < 1, hi <= lo, more than 2^24
+ * bins, T < 1), METAD_ERR_OOM / METAD_ERR_CUDA. */
+metad_status metad_fes_grid(metad_ctx *ctx, const double *lo, const double *hi, const int32_t *n, double *F_host);
+metad_status metad_fes_reweight(metad_ctx *ctx, const double *samples_host, const double *V_host, int64_t T,
+                                const double *lo, const double *hi, const int32_t *n, double *F_host);
+
 #ifdef __cplusplus
 }
 #endif

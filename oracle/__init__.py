@@ -244,3 +244,61 @@ def step(pos4, p: Params, centres, heights, sigma, grid: HillGrid | None = None,
     if rc != 0:
         raise MemoryError("orc_step failed")
     return {"s": s[:ncv].copy(), "V": V.value, "dV": dV[:ncv].copy(), "F": F}
+
+
+# ------------------------------------------------------------------ free energy
+# Methods, after Eqs. 2-3: the bias fills the free-energy surface; the FES is
+# recovered by reweighting the biased ensemble (Eq. 4: P_unbias(s) =
+# <delta(s - s(R)) exp(beta V)> / <exp(beta V)>, Eq. 5: F = -(1/beta) log P).
+# For a well-tempered bias the deposited bias itself estimates it: V(s) ->
+# -(1 - 1/gamma) F(s) + const (the standard well-tempered limit; the paper
+# names well-tempered MetaD but prints no formula, read here as that limit).
+
+def fes_points(points, centres, heights, sigma, biasfactor, grid: HillGrid | None = None):
+    """Sum-of-hills FES at each point: F = -(gamma / (gamma - 1)) V, shifted
+    so that its minimum over the points is 0."""
+    pts = np.atleast_2d(np.asarray(points, dtype=np.float64))
+    V = np.array([bias(p, centres, heights, sigma, grid)[0] for p in pts])
+    F = -(biasfactor / (biasfactor - 1.0)) * V
+    return F - F.min()
+
+
+def bin_index(s, lo, hi, n):
+    """Bin of CV point s on the regular grid [lo, hi) with n bins per
+    dimension (row-major, the first CV slowest); -1 when outside."""
+    idx = 0
+    for d in range(len(n)):
+        h = (hi[d] - lo[d]) / n[d]
+        if not (s[d] >= lo[d] and s[d] < hi[d]):
+            return -1
+        b = int(np.floor((s[d] - lo[d]) / h))
+        if b >= n[d]:
+            return -1
+        idx = idx * n[d] + b
+    return idx
+
+
+def fes_reweight(samples, V, beta, lo, hi, n):
+    """Eqs. 4-5 on a histogram: P_b = sum_{t in b} exp(beta V_t) / sum_t
+    exp(beta V_t) over the samples inside the grid, F_b = -(1/beta) log P_b,
+    shifted to minimum 0; empty bins are +inf.  Sums run in sample order,
+    with exp(beta (V_t - max V)) for range."""
+    S = np.atleast_2d(np.asarray(samples, dtype=np.float64))
+    V = np.asarray(V, dtype=np.float64)
+    nb = int(np.prod(n))
+    vmax = V.max()
+    acc = np.zeros(nb)
+    tot = 0.0
+    for t in range(S.shape[0]):
+        b = bin_index(S[t], lo, hi, n)
+        if b < 0:
+            continue
+        wt = np.exp(beta * (V[t] - vmax))
+        acc[b] += wt
+        tot += wt
+    F = np.full(nb, np.inf)
+    nz = acc > 0
+    F[nz] = -np.log(acc[nz] / tot) / beta
+    if nz.any():
+        F[nz] -= F[nz].min()
+    return F

@@ -1278,4 +1278,82 @@ int64_t metad_batch_launch_count(const metad_batch *b) { return b ? b->launches 
 
 const char *metad_batch_last_error(const metad_batch *b) { return b ? b->last_error.c_str() : "null batch"; }
 
+
+// ------------------------------------------------------------------ free energy
+
+namespace {
+
+metad_status fes_grid_args(metad_ctx *c, const double *lo, const double *hi, const int32_t *n, int64_t &bins)
+{
+    if (!lo || !hi || !n) return fail(c, METAD_ERR_INVALID, "NULL grid argument");
+    bins = 1;
+    for (int d = 0; d < c->p.n_cv; ++d) {
+        if (n[d] < 1 || !(hi[d] > lo[d])) return fail(c, METAD_ERR_INVALID, "grid shape");
+        bins *= n[d];
+    }
+    if (bins > (1 << 24)) return fail(c, METAD_ERR_INVALID, "more than 2^24 grid points");
+    return METAD_OK;
+}
+
+// A device buffer that lives for one call.
+struct Scratch {
+    void *p = nullptr;
+    ~Scratch()
+    {
+        if (p) cudaFree(p);
+    }
+};
+
+}  // namespace
+
+metad_status metad_fes_grid(metad_ctx *c, const double *lo, const double *hi, const int32_t *n, double *F_host)
+{
+    metad_status s = check_usable(c);
+    if (s) return s;
+    int64_t bins = 0;
+    if ((s = fes_grid_args(c, lo, hi, n, bins))) return s;
+    if (!F_host) return fail(c, METAD_ERR_INVALID, "F_host is NULL");
+    Scratch buf;
+    if ((s = cuda_check(c, cudaMalloc(&buf.p, sizeof(double) * 2 * bins), "fes buffer"))) return s;
+    double *V = static_cast<double *>(buf.p), *F = V + bins;
+    const int nn[2] = {n[0], c->p.n_cv == 2 ? n[1] : 1};
+    const double fac = c->p.biasfactor / (c->p.biasfactor - 1.0);
+    metad::launch_fes_points(c->sys, c->K, lo, hi, nn, V, F, fac, c->stream);
+    c->launches += 2;
+    if ((s = launched(c, "fes_grid"))) return s;
+    if ((s = cuda_check(c, cudaMemcpyAsync(F_host, F, sizeof(double) * bins, cudaMemcpyDeviceToHost, c->stream),
+                        "fes copy")))
+        return s;
+    return sync_and_check(c);
+}
+
+metad_status metad_fes_reweight(metad_ctx *c, const double *samples_host, const double *V_host, int64_t T,
+                                const double *lo, const double *hi, const int32_t *n, double *F_host)
+{
+    metad_status s = check_usable(c);
+    if (s) return s;
+    int64_t bins = 0;
+    if ((s = fes_grid_args(c, lo, hi, n, bins))) return s;
+    if (T < 1 || !samples_host || !V_host || !F_host) return fail(c, METAD_ERR_INVALID, "bad samples");
+    const int ncv = c->p.n_cv;
+    Scratch buf;
+    const size_t doubles = (size_t)T * (ncv + 1) + 1 + 2 * (size_t)bins;
+    if ((s = cuda_check(c, cudaMalloc(&buf.p, sizeof(double) * doubles), "reweight buffer"))) return s;
+    double *S = static_cast<double *>(buf.p), *V = S + (size_t)T * ncv, *scratch = V + T, *F = scratch + 1 + bins;
+    if ((s = cuda_check(c, cudaMemcpyAsync(S, samples_host, sizeof(double) * T * ncv, cudaMemcpyHostToDevice,
+                                           c->stream), "sample upload")) ||
+        (s = cuda_check(c, cudaMemcpyAsync(V, V_host, sizeof(double) * T, cudaMemcpyHostToDevice, c->stream),
+                        "bias upload")))
+        return s;
+    const int nn[2] = {n[0], ncv == 2 ? n[1] : 1};
+    const double beta = 1.0 / (c->p.kB * c->p.temperature);
+    metad::launch_fes_reweight(S, V, T, ncv, lo, hi, nn, beta, scratch, F, c->stream);
+    c->launches += 3;
+    if ((s = launched(c, "fes_reweight"))) return s;
+    if ((s = cuda_check(c, cudaMemcpyAsync(F_host, F, sizeof(double) * bins, cudaMemcpyDeviceToHost, c->stream),
+                        "fes copy")))
+        return s;
+    return sync_and_check(c);
+}
+
 }  // extern "C"

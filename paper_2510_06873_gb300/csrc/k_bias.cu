@@ -15,50 +15,6 @@ namespace metad {
 
 namespace {
 
-__device__ __forceinline__ void hermite(double t, double A[2], double B[2], double dA[2], double dB[2])
-{
-    const double t2 = t * t, t3 = t2 * t;
-    A[0] = 2.0 * t3 - 3.0 * t2 + 1.0;
-    A[1] = 3.0 * t2 - 2.0 * t3;
-    B[0] = t3 - 2.0 * t2 + t;
-    B[1] = t3 - t2;
-    dA[0] = 6.0 * (t2 - t);
-    dA[1] = 6.0 * (t - t2);
-    dB[0] = 3.0 * t2 - 4.0 * t + 1.0;
-    dB[1] = 3.0 * t2 - 2.0 * t;
-}
-
-// Bicubic Hermite patch of the node grid; zero outside [lo, hi].
-__device__ void grid_value(const Sys &s, double x0, double x1, double &V, double &g0, double &g1)
-{
-    V = g0 = g1 = 0.0;
-    if (!s.grid_on) return;
-    const double x[2] = {x0, x1};
-    int c[2];
-    double t[2];
-    for (int a = 0; a < 2; ++a) {
-        if (!(x[a] >= s.glo[a] && x[a] <= s.ghi[a])) return;
-        int k = (int)floor((x[a] - s.glo[a]) / s.gh[a]);
-        k = k < 0 ? 0 : (k > s.gn[a] - 2 ? s.gn[a] - 2 : k);
-        c[a] = k;
-        t[a] = (x[a] - (s.glo[a] + k * s.gh[a])) / s.gh[a];
-    }
-    double A0[2], B0[2], dA0[2], dB0[2], A1[2], B1[2], dA1[2], dB1[2];
-    hermite(t[0], A0, B0, dA0, dB0);
-    hermite(t[1], A1, B1, dA1, dB1);
-    const double h0 = s.gh[0], h1 = s.gh[1];
-    for (int a = 0; a < 2; ++a)
-        for (int b = 0; b < 2; ++b) {
-            const double *nd = s.grid + ((size_t)(c[0] + a) * s.gn[1] + (c[1] + b)) * 4;
-            const double f = nd[0], fx = h0 * nd[1], fy = h1 * nd[2], fxy = h0 * h1 * nd[3];
-            V += A0[a] * A1[b] * f + B0[a] * A1[b] * fx + A0[a] * B1[b] * fy + B0[a] * B1[b] * fxy;
-            g0 += dA0[a] * A1[b] * f + dB0[a] * A1[b] * fx + dA0[a] * B1[b] * fy + dB0[a] * B1[b] * fxy;
-            g1 += A0[a] * dA1[b] * f + B0[a] * dA1[b] * fx + A0[a] * dB1[b] * fy + B0[a] * dB1[b] * fxy;
-        }
-    g0 /= h0;
-    g1 /= h1;
-}
-
 // V and dV/ds at s.bias_x into s.bias_out; with s.deposit, also appends the
 // well-tempered hill there as hill s.K.
 __device__ __forceinline__ void bias(const Sys &s, Blk blk)

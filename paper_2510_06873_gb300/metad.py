@@ -76,6 +76,8 @@ _SIGS = {
     "metad_estimate_bytes": (ctypes.c_int, [ctypes.POINTER(metad_params), ctypes.POINTER(ctypes.c_int64)]),
     "metad_device_bytes": (ctypes.c_int64, [_P]),
     "metad_set_step_graph": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "metad_fes_grid": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "metad_fes_reweight": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P, _P, _P, _P]),
     "metad_batch_create": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)]),
     "metad_batch_destroy": (ctypes.c_int, [_P]),
     "metad_batch_set_tile": (ctypes.c_int, [_P, ctypes.c_int32]),
@@ -441,6 +443,12 @@ class Metad:
     def set_step_graph(self, on: bool):
         metad_set_step_graph(self.ctx, on)
 
+    def fes_grid(self, lo, hi, n):
+        return metad_fes_grid(self.ctx, lo, hi, n)
+
+    def fes_reweight(self, samples, V, lo, hi, n):
+        return metad_fes_reweight(self.ctx, samples, V, lo, hi, n)
+
 
 def metad_estimate_bytes(p: metad_params) -> int:
     out = ctypes.c_int64(0)
@@ -454,6 +462,34 @@ def metad_device_bytes(ctx) -> int:
 
 def metad_set_step_graph(ctx, on: bool):
     _check(ctx, lib().metad_set_step_graph(ctx, 1 if on else 0), "metad_set_step_graph")
+
+
+def _grid_args(lo, hi, n):
+    lo_a = np.zeros(2)
+    hi_a = np.zeros(2)
+    n_a = np.ones(2, dtype=np.int32)
+    k = len(n)
+    lo_a[:k], hi_a[:k], n_a[:k] = lo, hi, n
+    return lo_a, hi_a, n_a
+
+
+def metad_fes_grid(ctx, lo, hi, n):
+    """F at the bin centres of the grid, shape tuple(n)."""
+    lo_a, hi_a, n_a = _grid_args(lo, hi, n)
+    F = np.zeros(int(np.prod(n)))
+    _check(ctx, lib().metad_fes_grid(ctx, _hptr(lo_a), _hptr(hi_a), _hptr(n_a), _hptr(F)), "metad_fes_grid")
+    return F.reshape(tuple(n))
+
+
+def metad_fes_reweight(ctx, samples, V, lo, hi, n):
+    """Reweighted F on the grid's bins, shape tuple(n) (+inf where empty)."""
+    lo_a, hi_a, n_a = _grid_args(lo, hi, n)
+    S = np.ascontiguousarray(samples, dtype=np.float64)
+    Va = np.ascontiguousarray(V, dtype=np.float64)
+    F = np.zeros(int(np.prod(n)))
+    _check(ctx, lib().metad_fes_reweight(ctx, _hptr(S), _hptr(Va), len(Va), _hptr(lo_a), _hptr(hi_a), _hptr(n_a),
+                                         _hptr(F)), "metad_fes_reweight")
+    return F.reshape(tuple(n))
 
 
 # ------------------------------------------------------------------ batches

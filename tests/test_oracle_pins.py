@@ -450,3 +450,49 @@ def test_generator_shapes_and_constraints():
     d = f0[:, :3].astype(np.float64) - s.base[:, :3]
     d = d - s.box * np.round(d / s.box)
     assert 0.04 < d.std() < 0.06
+
+
+# ------------------------------------------------------------------ free energy
+def test_fes_points_single_hill_closed_form(oracle_mod):
+    """One hill: F(s) - F_min = gamma/(gamma-1) w (1 - exp(-(s-c)^2/2sigma^2)) over
+    points that include the centre (where F is lowest)."""
+    c = np.array([[1.0, 0.3]])
+    w = np.array([2.5])
+    sig = np.array([0.05, 0.02])
+    gamma = 10.0
+    pts = np.array([[1.0, 0.3], [1.05, 0.3], [1.0, 0.32], [1.1, 0.26]])
+    F = oracle_mod.fes_points(pts, c, w, sig, gamma)
+    e = np.exp(-((pts - c[0]) ** 2 / (2 * sig ** 2)).sum(axis=1))
+    assert np.allclose(F, gamma / (gamma - 1) * w[0] * (1 - e), rtol=1e-13, atol=1e-14)
+
+
+def test_fes_reweight_unbiased_is_log_histogram(oracle_mod):
+    """With V = 0 the reweighted F is -(1/beta) log of the plain histogram
+    fractions (numpy's histogram as the independent count)."""
+    g = np.random.default_rng(11)
+    S = np.column_stack([g.normal(1.0, 0.2, 4000), g.normal(0.3, 0.05, 4000)])
+    lo, hi, n = (0.2, 0.1), (1.8, 0.5), (8, 5)
+    beta = 1 / 2.494
+    F = oracle_mod.fes_reweight(S, np.zeros(len(S)), beta, lo, hi, n)
+    H, _, _ = np.histogram2d(S[:, 0], S[:, 1], bins=n, range=[(lo[0], hi[0]), (lo[1], hi[1])])
+    P = H.ravel() / H.sum()
+    ref = np.full(P.size, np.inf)
+    ref[P > 0] = -np.log(P[P > 0]) / beta
+    ref[P > 0] -= ref[P > 0].min()
+    assert np.array_equal(np.isinf(F), np.isinf(ref))
+    fin = ~np.isinf(F)
+    assert np.allclose(F[fin], ref[fin], rtol=1e-12, atol=1e-12)
+
+
+def test_fes_reweight_weights_and_shift_invariance(oracle_mod):
+    """Two bins, samples with known biases: F difference is -(1/beta) log of
+    the weight ratio; a constant added to every V changes nothing."""
+    beta = 0.5
+    S = np.array([[0.1], [0.1], [0.7]])
+    V = np.array([0.0, 2.0, 1.0])
+    F = oracle_mod.fes_reweight(S, V, beta, (0.0,), (1.0,), (2,))
+    w0 = np.exp(beta * 0.0) + np.exp(beta * 2.0)
+    w1 = np.exp(beta * 1.0)
+    assert abs((F[1] - F[0]) - (-(1 / beta) * np.log(w1 / w0))) < 1e-13
+    F2 = oracle_mod.fes_reweight(S, V + 7.5, beta, (0.0,), (1.0,), (2,))
+    assert np.allclose(F, F2, rtol=0, atol=1e-13)
