@@ -351,6 +351,16 @@ const char *metad_batch_last_error(const metad_batch *batch);
  * Errors: METAD_ERR_INVALID (NULL pointers, n < 1, hi <= lo, more than 2^24
  * bins, T < 1), METAD_ERR_OOM / METAD_ERR_CUDA. */
 metad_status metad_fes_grid(metad_ctx *ctx, const double *lo, const double *hi, const int32_t *n, double *F_host);
+
+/* CVs of a stored trajectory (offline analysis, no bias or forces; the
+ * paper's trajectory-analysis module aligns CV outputs with the MD frames,
+ * Section "Frameworks of GPU-MetaD").  frames_dev: device float32 [T][N][4]
+ * (N = params.n_atoms), frame t at frames_dev + 4 N t; cv_host: double
+ * [T][2] (s2 = 0 when n_cv == 1).  Runs build_neighbors and cv_forward per
+ * frame (the neighbour list carries over between frames as in a run) and
+ * copies all CVs back once; synchronises.
+ * Errors: METAD_ERR_INVALID (NULL, T < 1), those of the per-frame calls. */
+metad_status metad_cv_trajectory(metad_ctx *ctx, const float *frames_dev, int64_t T, double *cv_host);
 metad_status metad_fes_reweight(metad_ctx *ctx, const double *samples_host, const double *V_host, int64_t T,
                                 const double *lo, const double *hi, const int32_t *n, double *F_host);
 

@@ -1209,8 +1209,9 @@ metad_status metad_batch_step(metad_batch *b, const float *const *pos_dev, float
     metad::launch_batch_cv(rows[metad::GK_GROUPS], totals[metad::GK_GROUPS], rows[metad::GK_CV], totals[metad::GK_CV],
                            rows[metad::GK_SUM], totals[metad::GK_SUM], b->fp64, b->ncv, b->stream);
     metad::launch_batch_bias(rows[metad::GK_HILLS], totals[metad::GK_HILLS], 0, b->stream);
-    metad::launch_batch_force(rows[metad::GK_GROUPS], totals[metad::GK_GROUPS], rows[metad::GK_ATOM128],
-                              totals[metad::GK_ATOM128], b->fp64, b->ncv, b->stream);
+    metad::launch_batch_force(rows[metad::GK_GROUPS], totals[metad::GK_GROUPS], rows[metad::GK_ATOM32],
+                              totals[metad::GK_ATOM32], rows[metad::GK_ATOM128], totals[metad::GK_ATOM128], b->fp64,
+                              b->ncv, b->stream);
     if (any_deposit) metad::launch_batch_bias(rows[metad::GK_DEPOSIT], totals[metad::GK_DEPOSIT], 1, b->stream);
     b->launches += 1 + 8 + 2 + 1 + (b->ncv == 2 ? 3 : 2) + (any_deposit ? 1 : 0);
     cudaError_t e = cudaGetLastError();
@@ -1354,6 +1355,31 @@ metad_status metad_fes_reweight(metad_ctx *c, const double *samples_host, const 
                         "fes copy")))
         return s;
     return sync_and_check(c);
+}
+
+metad_status metad_cv_trajectory(metad_ctx *c, const float *frames_dev, int64_t T, double *cv_host)
+{
+    metad_status s = check_usable(c);
+    if (s) return s;
+    if (!frames_dev || !cv_host || T < 1) return fail(c, METAD_ERR_INVALID, "bad trajectory arguments");
+    Scratch buf;
+    if ((s = cuda_check(c, cudaMalloc(&buf.p, sizeof(double) * 2 * T), "trajectory buffer"))) return s;
+    double *out = static_cast<double *>(buf.p);
+    const size_t stride = 4 * (size_t)c->p.n_atoms;
+    for (int64_t t = 0; t < T; ++t) {
+        if ((s = metad_build_neighbors(c, frames_dev + stride * t))) return s;
+        if ((s = metad_cv_forward(c, nullptr, nullptr))) return s;
+        if ((s = cuda_check(c, cudaMemcpyAsync(out + 2 * t, c->sys.scal + metad::kS0, 2 * sizeof(double),
+                                               cudaMemcpyDeviceToDevice, c->stream), "cv copy")))
+            return s;
+    }
+    if ((s = cuda_check(c, cudaMemcpyAsync(cv_host, out, sizeof(double) * 2 * T, cudaMemcpyDeviceToHost, c->stream),
+                        "trajectory copy")))
+        return s;
+    if ((s = sync_and_check(c))) return s;
+    if (c->p.n_cv == 1)
+        for (int64_t t = 0; t < T; ++t) cv_host[2 * t + 1] = 0.0;
+    return METAD_OK;
 }
 
 }  // extern "C"

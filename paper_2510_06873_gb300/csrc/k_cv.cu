@@ -533,52 +533,110 @@ __global__ void __launch_bounds__(kBlockAtoms) kb_cv_avg(BatchView v)
 
 // a7: g_m(k) = b_m(k) + sum_i w_ik b_m(i) ; h = g / W ; record h holds h_m
 // (0..12) and gamma_k = h(k).q(k) + beta_k (slot 13).
+// a7 with four lanes per atom, four record components per lane (one 16 B
+// load of each neighbour record per lane): a warp has eight atoms' gathers in
+// flight.  (Measured faster than eight lanes of two components here; the Q6
+// average keeps eight lanes, where four cost it occupancy.)
+constexpr int kG4 = 4;
+constexpr int kAtoms4 = kBlockAtoms / kG4;
+
 template <typename real>
-__device__ __forceinline__ void adjoint_group(const Sys &s, const AtomLane a)
+__device__ __forceinline__ void load4(const real *base, int i, int l, real v[4]);
+template <>
+__device__ __forceinline__ void load4<float>(const float *base, int i, int l, float v[4])
 {
-    // lane l owns components 2l, 2l + 1; record b holds b_m (0..12), beta (13)
+    const float4 t = reinterpret_cast<const float4 *>(base + (size_t)i * kRec)[l];
+    v[0] = t.x;
+    v[1] = t.y;
+    v[2] = t.z;
+    v[3] = t.w;
+}
+template <>
+__device__ __forceinline__ void load4<double>(const double *base, int i, int l, double v[4])
+{
+    const double2 *p = reinterpret_cast<const double2 *>(base + (size_t)i * kRec) + 2 * l;
+    const double2 a = p[0], b = p[1];
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = b.x;
+    v[3] = b.y;
+}
+template <typename real>
+__device__ __forceinline__ void store4(real *base, int i, int l, const real v[4]);
+template <>
+__device__ __forceinline__ void store4<float>(float *base, int i, int l, const float v[4])
+{
+    reinterpret_cast<float4 *>(base + (size_t)i * kRec)[l] = make_float4(v[0], v[1], v[2], v[3]);
+}
+template <>
+__device__ __forceinline__ void store4<double>(double *base, int i, int l, const double v[4])
+{
+    double2 *p = reinterpret_cast<double2 *>(base + (size_t)i * kRec) + 2 * l;
+    p[0] = make_double2(v[0], v[1]);
+    p[1] = make_double2(v[2], v[3]);
+}
+
+template <typename real>
+__device__ __forceinline__ real group4_sum(real v)
+{
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    return v;
+}
+
+template <typename real>
+__device__ __forceinline__ void adjoint_group(const Sys &s, int g)
+{
+    // lane l owns components 4l .. 4l + 3; record b holds b_m (0..12), beta (13)
+    const int i = g * kAtoms4 + (threadIdx.x / kG4), l = threadIdx.x & (kG4 - 1);
+    const bool ok = i < s.n;
     const real *bb = R<real>(s.b);
-    real g0 = real(0), g1 = real(0);
-    if (a.ok) {
-        const int nn = s.nn[a.i];
-        const int *row = nbr_row(s, a.i);
-        const real *wrow = R<real>(s.wl) + (size_t)a.i * s.max_nb;
+    real acc[4] = {real(0), real(0), real(0), real(0)};
+    if (ok) {
+        const int nn = s.nn[i];
+        const int *row = nbr_row(s, i);
+        const real *wrow = R<real>(s.wl) + (size_t)i * s.max_nb;
 #pragma unroll 4
         for (int k = 0; k < nn; ++k) {
             const int j = row[k];
             const real w = wrow[k];
-            real x0, x1;
-            load_pair<real>(bb, j, a.l, x0, x1);
-            g0 += w * x0;
-            g1 += w * x1;
+            real x[4];
+            load4<real>(bb, j, l, x);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[c] += w * x[c];
         }
     }
-    real h0 = real(0), h1 = real(0), alpha = real(0), beta = real(0);
-    if (a.ok) {
-        const real W = R<real>(s.W)[a.i];
+    real h[4] = {real(0), real(0), real(0), real(0)};
+    real alpha = real(0), beta = real(0);
+    if (ok) {
+        const real W = R<real>(s.W)[i];
         const real inv_W = W > real(0) ? real(1) / W : real(0);
-        real o0, o1, q0, q1;
-        load_pair<real>(bb, a.i, a.l, o0, o1);
-        load_pair<real>(R<real>(s.q), a.i, a.l, q0, q1);
-        const int m0 = 2 * a.l, m1 = 2 * a.l + 1;
-        if (m0 < kNY) h0 = (o0 + g0) * inv_W;
-        if (m1 < kNY) h1 = (o1 + g1) * inv_W;
-        alpha = h0 * q0 + (m1 < kNY ? h1 * q1 : real(0));
-        if (m1 == 13) beta = o1;
+        real o[4], q[4];
+        load4<real>(bb, i, l, o);
+        load4<real>(R<real>(s.q), i, l, q);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int m = 4 * l + c;
+            if (m < kNY) {
+                h[c] = (o[c] + acc[c]) * inv_W;
+                alpha += h[c] * q[c];
+            }
+            if (m == 13) beta = o[c];
+        }
     }
-    alpha = group_sum<real>(alpha);
-    beta = group_sum<real>(beta);
-    if (a.ok) {
-        if (a.l == 6) h1 = alpha + beta;  // slot 13: gamma = h.q + b.qbar
-        store_pair<real>(R<real>(s.h), a.i, a.l, h0, h1);
+    alpha = group4_sum<real>(alpha);
+    beta = group4_sum<real>(beta);
+    if (ok) {
+        if (l == 3) h[1] = alpha + beta;  // slot 13: gamma = h.q + b.qbar
+        store4<real>(R<real>(s.h), i, l, h);
     }
 }
 
 template <typename real>
 __device__ __forceinline__ void adjoint(const Sys &s, Blk k)
 {
-    const int groups = group_grid(s.n);
-    for (int it = 0, g; (g = work_item(k, it)) < groups; ++it) adjoint_group<real>(s, atom_lane_at(s, g));
+    const int groups = (s.n + kAtoms4 - 1) / kAtoms4;
+    for (int it = 0, g; (g = work_item(k, it)) < groups; ++it) adjoint_group<real>(s, g);
 }
 
 template <typename real>
@@ -861,9 +919,9 @@ void launch_cv_sum(const Sys &s, int fp64, cudaStream_t st)
 void launch_adjoint(const Sys &s, int fp64, cudaStream_t st)
 {
     if (fp64)
-        k_adjoint<double><<<group_grid(s.n), kBlockAtoms, 0, st>>>(s);
+        k_adjoint<double><<<grid_blocks(s, GK_ATOM32, 0), kBlockAtoms, 0, st>>>(s);
     else
-        k_adjoint<float><<<group_grid(s.n), kBlockAtoms, 0, st>>>(s);
+        k_adjoint<float><<<grid_blocks(s, GK_ATOM32, 0), kBlockAtoms, 0, st>>>(s);
 }
 
 void launch_force_pairs(const Sys &s, int fp64, double scale, cudaStream_t st)
@@ -907,16 +965,16 @@ void launch_batch_cv(const BatchView &groups, int group_total, const BatchView &
     }
 }
 
-void launch_batch_force(const BatchView &groups, int group_total, const BatchView &pairs, int pair_total, int fp64,
-                        int ncv, cudaStream_t st)
+void launch_batch_force(const BatchView &groups, int group_total, const BatchView &adj, int adj_total,
+                        const BatchView &pairs, int pair_total, int fp64, int ncv, cudaStream_t st)
 {
     if (group_total <= 0) return;
     if (fp64) {
-        if (ncv == 2) kb_adjoint<double><<<group_total, kBlockAtoms, 0, st>>>(groups);
+        if (ncv == 2) kb_adjoint<double><<<adj_total, kBlockAtoms, 0, st>>>(adj);
         kb_force_pairs<double><<<pair_total, kBlockAtoms, 0, st>>>(pairs);
         kb_force_gather<double><<<group_total, kBlockAtoms, 0, st>>>(groups);
     } else {
-        if (ncv == 2) kb_adjoint<float><<<group_total, kBlockAtoms, 0, st>>>(groups);
+        if (ncv == 2) kb_adjoint<float><<<adj_total, kBlockAtoms, 0, st>>>(adj);
         kb_force_pairs<float><<<pair_total, kBlockAtoms, 0, st>>>(pairs);
         kb_force_gather<float><<<group_total, kBlockAtoms, 0, st>>>(groups);
     }

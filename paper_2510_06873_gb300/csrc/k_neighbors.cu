@@ -418,6 +418,10 @@ int grid_blocks(const Sys &s, int kind, int persist_cap)
         return persist_cap > 0 && persist_cap < g ? persist_cap : g;
     }
     case GK_CV: return persist_grid(s.n);  // not tiled: its grid fixes the CV sums' order
+    case GK_ATOM32: {
+        const int g = (s.n + 31) / 32;
+        return persist_cap > 0 && persist_cap < g ? persist_cap : g;
+    }
     case GK_ATOM128: {
         const int g = (s.n + 127) / 128;
         return persist_cap > 0 && persist_cap < g ? persist_cap : g;

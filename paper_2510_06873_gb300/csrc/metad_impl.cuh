@@ -158,6 +158,7 @@ enum GridKind : int {
     GK_ONE,            // one block per system
     GK_GROUPS,         // one block per 16 atoms (lane-group kernels); a batch tile caps it
     GK_CV,             // the Q6 pass with the CV sums: persistent, by N only
+    GK_ATOM32,         // one block per 32 atoms (four-lane adjoint); a batch tile caps it
     GK_ATOM128,        // one block per 128 atoms (pair-parallel force); a batch tile caps it
     GK_SUM,            // the CV sums: blocks by N only
     GK_HILLS,          // hill kernel, evaluation
@@ -177,8 +178,8 @@ void launch_batch_cv(const BatchView &groups, int group_total, const BatchView &
                      const BatchView &sums, int sum_total, int fp64, int ncv, cudaStream_t st);
 void launch_cv_sum(const Sys &s, int fp64, cudaStream_t st);
 void launch_batch_bias(const BatchView &v, int total, int deposit, cudaStream_t st);
-void launch_batch_force(const BatchView &groups, int group_total, const BatchView &pairs, int pair_total, int fp64,
-                        int ncv, cudaStream_t st);
+void launch_batch_force(const BatchView &groups, int group_total, const BatchView &adj, int adj_total,
+                        const BatchView &pairs, int pair_total, int fp64, int ncv, cudaStream_t st);
 void launch_batch_collect(const BatchView &v, double *out, cudaStream_t st);
 
 // Launch entry points (stream-ordered, no host synchronisation).

@@ -77,6 +77,7 @@ _SIGS = {
     "metad_device_bytes": (ctypes.c_int64, [_P]),
     "metad_set_step_graph": (ctypes.c_int, [_P, ctypes.c_int32]),
     "metad_fes_grid": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "metad_cv_trajectory": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P]),
     "metad_fes_reweight": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P, _P, _P, _P]),
     "metad_batch_create": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)]),
     "metad_batch_destroy": (ctypes.c_int, [_P]),
@@ -443,6 +444,9 @@ class Metad:
     def set_step_graph(self, on: bool):
         metad_set_step_graph(self.ctx, on)
 
+    def cv_trajectory(self, frames):
+        return metad_cv_trajectory(self.ctx, frames, self.n_cv)
+
     def fes_grid(self, lo, hi, n):
         return metad_fes_grid(self.ctx, lo, hi, n)
 
@@ -479,6 +483,14 @@ def metad_fes_grid(ctx, lo, hi, n):
     F = np.zeros(int(np.prod(n)))
     _check(ctx, lib().metad_fes_grid(ctx, _hptr(lo_a), _hptr(hi_a), _hptr(n_a), _hptr(F)), "metad_fes_grid")
     return F.reshape(tuple(n))
+
+
+def metad_cv_trajectory(ctx, frames, n_cv):
+    """CVs of every frame of a device tensor [T, N, 4]; returns [T, n_cv]."""
+    T = int(frames.shape[0])
+    out = np.zeros((T, 2))
+    _check(ctx, lib().metad_cv_trajectory(ctx, _dptr(frames), T, _hptr(out)), "metad_cv_trajectory")
+    return out[:, :n_cv]
 
 
 def metad_fes_reweight(ctx, samples, V, lo, hi, n):

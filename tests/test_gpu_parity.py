@@ -418,3 +418,22 @@ def test_unwrapped_positions_are_wrapped(dev):
     ctx = make_ctx(dev, system, synth.MethodParams(n_cv=1, sigma=(0.05,)))
     ctx.build_neighbors(torch.from_numpy(shifted).to(dev))
     assert np.array_equal(ctx.export_neighbors(), oracle.pairs_cells(wrapped, system.box, RC))
+
+
+def test_cv_trajectory_matches_oracle_and_single_frames(dev):
+    """Offline CVs of a stored trajectory: each frame against the oracle, and
+    bit for bit against stepping the frames one by one."""
+    system = synth.wurtzite_system(20000, cfg=95)
+    mp = synth.MethodParams(n_cv=2)
+    p = oracle.params_from(mp, system.box)
+    T = 6
+    frames_h = np.stack([synth.perturbed_frame(system, f) for f in range(T)])
+    frames = torch.from_numpy(frames_h).to(dev)
+    ctx = make_ctx(dev, system, mp)
+    cvs = ctx.cv_trajectory(frames)
+    one = make_ctx(dev, system, mp)
+    for t in range(T):
+        ref, _, _ = oracle.cv(frames_h[t], p)
+        check_cv(cvs[t], ref)
+        one.build_neighbors(frames[t])
+        assert np.array_equal(one.cv_forward(), cvs[t])
