@@ -624,14 +624,14 @@ __device__ __forceinline__ int filter_row(const Sys &s, const AtomLane &a)
         const bool in = valid && pair_in(s, pi, pj, d);
         const unsigned ball = __ballot_sync(0xffffffffu, in);
         const unsigned gm = group_mask_bits(ball);
-        const unsigned gu = group_mask_bits(__ballot_sync(0xffffffffu, in && k < vh));
+        const int below = min(max(vh - base, 0), kG);  // lanes of this round in the j > i part
         const int at = cnt + __popc(gm & ((1u << a.l) - 1u));
         if (in && at < s.max_nb) {
             row[at] = j;
             store_geo<real>(s, (size_t)a.i * s.max_nb + at, d, pi, pj);
         }
         cnt += __popc(gm);
-        nh += __popc(gu);
+        nh += __popc(gm & ((1u << below) - 1u));
     }
     if (a.ok && a.l == 0) {
         if (cnt > s.max_nb) set_err(s, kErrCapacity);

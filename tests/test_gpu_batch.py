@@ -255,3 +255,38 @@ def test_full_batched_workload(dev):
         check_bias(VA[k], dV, ref["V"], ref["dV"], mp)
         check_forces(FA[k].cpu().numpy().astype(np.float64), ref["F"])
     batch.close()
+
+
+def test_batched_fp64_single_cv_systems(dev):
+    """The FP64, coordination-number-only configuration batched: bitwise the
+    single steps, and the oracle's CVs and forces."""
+    metad = _metad()
+    mp = synth.method_params(1)
+    systems = [synth.rsa_liquid_system(n, 0.08, 1.8, cfg=96, sys=k) for k, n in enumerate((500, 1000, 1700))]
+    A, B = [], []
+    for s in systems:
+        for lst in (A, B):
+            p = metad.params_for(s.n, s.box, n_cv=1, sigma=mp.sigma, fp64=True,
+                                 stream=torch.cuda.current_stream(dev).cuda_stream)
+            lst.append(metad.Metad(p))
+    hills = [setup_hills(s, mp, 150, cfg=96)[0] for s in systems]
+    for a, b, c in zip(A, B, hills):
+        a.deposit_hills(c, want_heights=False)
+        b.deposit_hills(c, want_heights=False)
+    batch = metad.Batch(A)
+    FA = [torch.zeros((s.n, 3), dtype=torch.float32, device=dev) for s in systems]
+    FB = [torch.zeros((s.n, 3), dtype=torch.float32, device=dev) for s in systems]
+    pos = frames_for(systems, 3, dev)
+    batch.step(pos, FA, deposit=[0, 1, 0])
+    cvA, VA = batch.read()
+    for k, (s, b) in enumerate(zip(systems, B)):
+        b.step(pos[k], FB[k], deposit=(k == 1))
+        cvB, VB, _ = b.read_results()
+        assert cvA[k][0] == cvB[0] and cvA[k][1] == 0.0 and VA[k] == VB
+        assert torch.equal(FA[k], FB[k])
+        w_ref = oracle.deposit_sequence(hills[k], mp.sigma, mp.w0, kbdt(mp))
+        ref = oracle.step(synth.perturbed_frame(s, 3), oracle.params_from(mp, s.box), hills[k], w_ref, mp.sigma)
+        check_cv(cvA[k][:1], ref["s"])
+        check_forces(FA[k].cpu().numpy().astype(np.float64), ref["F"])
+    assert A[1].hill_count == 151
+    batch.close()
