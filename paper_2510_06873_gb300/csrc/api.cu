@@ -316,7 +316,7 @@ metad_status state_buffers(metad_ctx *c, Buffers &b, Alloc &&alloc)
         (s = alloc(&y.cell_start, (size_t)y.ncell + 1)) || (s = alloc(&y.scan_part, y.ncell / 4096 + 2)) ||
         (s = alloc(&b.rank_xyz, y.ncell)) || (s = alloc(&b.xyz_rank, y.ncell)) ||
         (s = alloc(&y.nbr, (size_t)y.max_nb * n)) || (s = alloc(&y.nn, n)) || (s = alloc(&y.nh, n)) ||
-        (s = alloc(&y.vnh, n)) || (s = alloc(&b.wlb, rs * (size_t)y.max_nb * n)) ||
+        (s = alloc(&y.vnh, n)) || (s = alloc(&b.wlb, 2 * rs * (size_t)y.max_nb * n)) ||
         (s = alloc(&b.pfb, rs * 4 * (size_t)y.max_nb * n)) || (s = alloc(&b.geob, rs * 4 * (size_t)y.max_nb * n)) ||
         (s = alloc(&y.pos_ref, n)) ||
         (s = alloc(&y.vnbr, (size_t)y.max_vnb * n)) || (s = alloc(&y.vnn, n)) || (s = alloc(&y.flag, 1)) ||

@@ -252,9 +252,9 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
 // derivative of one exact entry.
 template <typename real, bool kLast = false>
 __device__ __forceinline__ void cached_geometry(const Sys &s, size_t slot, Vec3<real> &d, real &inv_r, real &w,
-                                                real &dw, bool &cn)
+                                                real &dw, bool &cn, int &j)
 {
-    load_geo<real, kLast>(s, slot, d, cn);
+    load_geo<real, kLast>(s, slot, d, cn, j);
     real r2 = d.x * d.x + d.y * d.y + d.z * d.z;
     inv_r = rsqrt_r<real>(r2);
     switch_eval<real>(s, r2 * inv_r, w, dw);
@@ -344,13 +344,14 @@ __device__ __forceinline__ double cv_fwd_group(const Sys &s, const AtomLane a)
     for (int m = 0; m < kRec; ++m) v[m] = real(0);
     if (a.ok) {
         const int nn = kFilter ? nn_f : s.nn[a.i];
-        real *wrow = R<real>(s.wl) + (size_t)a.i * s.max_nb;
+        JW<real> *jwrow = reinterpret_cast<JW<real> *>(s.wl) + (size_t)a.i * s.max_nb;
         for (int k = a.l; k < nn; k += kG) {
             Vec3<real> d;
             real inv_r, w, dw;
             bool cn;
-            cached_geometry<real>(s, (size_t)a.i * s.max_nb + k, d, inv_r, w, dw, cn);
-            wrow[k] = w;
+            int j;
+            cached_geometry<real>(s, (size_t)a.i * s.max_nb + k, d, inv_r, w, dw, cn, j);
+            jwrow[k] = JW<real>{j, w};
             if (cn) v[14] += w;
             v[13] += w;
             if (s.ncv == 2) {
@@ -410,12 +411,12 @@ __device__ __forceinline__ void cv_avg_group(const Sys &s, const AtomLane a, dou
     real a0 = real(0), a1 = real(0);
     if (a.ok) {
         const int nn = s.nn[a.i];
-        const int *row = nbr_row(s, a.i);
-        const real *wrow = R<real>(s.wl) + (size_t)a.i * s.max_nb;
+        const JW<real> *jwrow = reinterpret_cast<const JW<real> *>(s.wl) + (size_t)a.i * s.max_nb;
 #pragma unroll 4
         for (int k = 0; k < nn; ++k) {
-            const int j = row[k];
-            const real w = wrow[k];
+            const JW<real> e = jwrow[k];
+            const int j = e.j;
+            const real w = e.w;
             real x0, x1;
             load_pair<real>(q, j, a.l, x0, x1);
             a0 += w * x0;
@@ -594,12 +595,12 @@ __device__ __forceinline__ void adjoint_group(const Sys &s, int g)
     real acc[4] = {real(0), real(0), real(0), real(0)};
     if (ok) {
         const int nn = s.nn[i];
-        const int *row = nbr_row(s, i);
-        const real *wrow = R<real>(s.wl) + (size_t)i * s.max_nb;
+        const JW<real> *jwrow = reinterpret_cast<const JW<real> *>(s.wl) + (size_t)i * s.max_nb;
 #pragma unroll 4
         for (int k = 0; k < nn; ++k) {
-            const int j = row[k];
-            const real w = wrow[k];
+            const JW<real> e = jwrow[k];
+            const int j = e.j;
+            const real w = e.w;
             real x[4];
             load4<real>(bb, j, l, x);
 #pragma unroll
@@ -685,12 +686,12 @@ constexpr int kPairChunk = 32;
 template <typename real>
 __device__ __forceinline__ void pair_force(const Sys &s, int i, int k, real cn_fac, real V2)
 {
-    const int j = nbr_row(s, i)[k];
-    const int nhj = s.nh[j], nnj = s.nn[j];
     Vec3<real> d;
     real inv_r, w, dw;
     bool cn;
-    cached_geometry<real, true>(s, (size_t)i * s.max_nb + k, d, inv_r, w, dw, cn);
+    int j;
+    cached_geometry<real, true>(s, (size_t)i * s.max_nb + k, d, inv_r, w, dw, cn, j);
+    const int nhj = s.nh[j], nnj = s.nn[j];
     const real ux = d.x * inv_r, uy = d.y * inv_r, uz = d.z * inv_r;
     real radial = cn ? cn_fac * dw : real(0);
     real fx = real(0), fy = real(0), fz = real(0);

@@ -73,7 +73,7 @@ struct Sys {
                            // entries j > i first (nh of them), then j < i
     int *nn;               // [n]
     int *nh;               // [n] entries with j > i
-    void *wl;              // real [n][max_nb]: switch weight w_ij of each entry
+    void *wl;              // JW<real> [n][max_nb]: neighbour and switch weight of each entry
     void *pairF;           // real [n][max_nb][4]: G_ij in i's entry of j, -G_ji in the others
     void *geo;             // real [n][max_nb][4]: r_j - r_i (minimum image) and the CN mask
                            // of each exact entry, written by the exact filter
@@ -536,73 +536,88 @@ __device__ __forceinline__ bool pair_in(const Sys &s, float4 pi, float4 pj, cons
 
 // The geometry of an exact entry, cached by the filter so the CV and force
 // passes read one contiguous record per entry instead of gathering the
-// neighbour's position again.  The force pass reads it for the last time
-// (kLast: an evict-first load, so the stream does not push the gathered
-// per-atom records out of L2).
+// neighbour's position again: r_j - r_i, and in the fourth slot the bits of
+// j with the CN mask in bit 31 (carried through float registers unchanged).
+// The force pass reads it for the last time (kLast: an evict-first load, so
+// the stream does not push the gathered per-atom records out of L2).
+constexpr unsigned kCnBit = 0x80000000u;
+
 template <typename real>
-__device__ __forceinline__ void store_geo(const Sys &s, size_t slot, const Vec3<float> &df, float4 pi, float4 pj);
+__device__ __forceinline__ void store_geo(const Sys &s, size_t slot, const Vec3<float> &df, float4 pi, float4 pj,
+                                          int j);
 template <>
 __device__ __forceinline__ void store_geo<float>(const Sys &s, size_t slot, const Vec3<float> &df, float4 pi,
-                                                 float4 pj)
+                                                 float4 pj, int j)
 {
-    const float cn = (!s.cn_unlike || pj.w != pi.w) ? 1.0f : 0.0f;
-    reinterpret_cast<float4 *>(s.geo)[slot] = make_float4(df.x, df.y, df.z, cn);
+    const unsigned tag = (unsigned)j | ((!s.cn_unlike || pj.w != pi.w) ? kCnBit : 0u);
+    reinterpret_cast<float4 *>(s.geo)[slot] = make_float4(df.x, df.y, df.z, __uint_as_float(tag));
 }
 template <>
 __device__ __forceinline__ void store_geo<double>(const Sys &s, size_t slot, const Vec3<float> &, float4 pi,
-                                                  float4 pj)
+                                                  float4 pj, int j)
 {
     const Vec3<double> d = displacement<double>(s, pi, pj);
-    const double cn = (!s.cn_unlike || pj.w != pi.w) ? 1.0 : 0.0;
+    const unsigned tag = (unsigned)j | ((!s.cn_unlike || pj.w != pi.w) ? kCnBit : 0u);
     double2 *g = reinterpret_cast<double2 *>(s.geo) + 2 * slot;
     g[0] = make_double2(d.x, d.y);
-    g[1] = make_double2(d.z, cn);
+    g[1] = make_double2(d.z, __longlong_as_double((long long)tag));
+}
+
+__device__ __forceinline__ void untag(unsigned tag, int &j, bool &cn)
+{
+    j = (int)(tag & ~kCnBit);
+    cn = (tag & kCnBit) != 0u;
 }
 
 template <typename real, bool kLast = false>
-__device__ __forceinline__ void load_geo(const Sys &s, size_t slot, Vec3<real> &d, bool &cn);
+__device__ __forceinline__ void load_geo(const Sys &s, size_t slot, Vec3<real> &d, bool &cn, int &j);
 template <>
-__device__ __forceinline__ void load_geo<float, false>(const Sys &s, size_t slot, Vec3<float> &d, bool &cn)
+__device__ __forceinline__ void load_geo<float, false>(const Sys &s, size_t slot, Vec3<float> &d, bool &cn, int &j)
 {
     const float4 g = reinterpret_cast<const float4 *>(s.geo)[slot];
     d.x = g.x;
     d.y = g.y;
     d.z = g.z;
-    cn = g.w != 0.0f;
+    untag(__float_as_uint(g.w), j, cn);
 }
 template <>
-__device__ __forceinline__ void load_geo<float, true>(const Sys &s, size_t slot, Vec3<float> &d, bool &cn)
+__device__ __forceinline__ void load_geo<float, true>(const Sys &s, size_t slot, Vec3<float> &d, bool &cn, int &j)
 {
     const float4 g = __ldcs(reinterpret_cast<const float4 *>(s.geo) + slot);
     d.x = g.x;
     d.y = g.y;
     d.z = g.z;
-    cn = g.w != 0.0f;
+    untag(__float_as_uint(g.w), j, cn);
 }
 template <>
-__device__ __forceinline__ void load_geo<double, true>(const Sys &s, size_t slot, Vec3<double> &d, bool &cn)
+__device__ __forceinline__ void load_geo<double, true>(const Sys &s, size_t slot, Vec3<double> &d, bool &cn, int &j)
 {
     const double2 *g = reinterpret_cast<const double2 *>(s.geo) + 2 * slot;
     const double2 a = __ldcs(g), b = __ldcs(g + 1);
     d.x = a.x;
     d.y = a.y;
     d.z = b.x;
-    cn = b.y != 0.0;
+    untag((unsigned)__double_as_longlong(b.y), j, cn);
 }
 template <>
-__device__ __forceinline__ void load_geo<double, false>(const Sys &s, size_t slot, Vec3<double> &d, bool &cn)
+__device__ __forceinline__ void load_geo<double, false>(const Sys &s, size_t slot, Vec3<double> &d, bool &cn, int &j)
 {
     const double2 *g = reinterpret_cast<const double2 *>(s.geo) + 2 * slot;
     const double2 a = g[0], b = g[1];
     d.x = a.x;
     d.y = a.y;
     d.z = b.x;
-    cn = b.y != 0.0;
+    untag((unsigned)__double_as_longlong(b.y), j, cn);
 }
 
-// Compact atom a.i's Verlet row into its exact row, the j > i part first (the
-// Verlet row is ordered the same way), order kept within each part.  Every
-// lane of the warp must call this (loop counts are made warp-uniform).
+// One exact entry for the gather passes: the neighbour and the switch
+// weight side by side, read with one load.
+template <typename real>
+struct alignas(2 * sizeof(real)) JW {
+    int j;
+    real w;
+};
+
 template <typename real>
 __device__ __forceinline__ int filter_row(const Sys &s, const AtomLane &a)
 {
@@ -628,7 +643,7 @@ __device__ __forceinline__ int filter_row(const Sys &s, const AtomLane &a)
         const int at = cnt + __popc(gm & ((1u << a.l) - 1u));
         if (in && at < s.max_nb) {
             row[at] = j;
-            store_geo<real>(s, (size_t)a.i * s.max_nb + at, d, pi, pj);
+            store_geo<real>(s, (size_t)a.i * s.max_nb + at, d, pi, pj, j);
         }
         cnt += __popc(gm);
         nh += __popc(gm & ((1u << below) - 1u));
