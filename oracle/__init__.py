@@ -57,8 +57,8 @@ def _L():
             "orc_cv": (ctypes.c_int, [I32, P, P, P, P, P, ctypes.c_int]),
             "orc_forces": (ctypes.c_int, [I32, P, P, P, P, P, ctypes.c_int]),
             "orc_grid_fold": (ctypes.c_int, [P, I32, P, P, P, ctypes.c_int]),
-            "orc_bias": (ctypes.c_int, [I32, P, I32, P, P, P, P, P, P]),
-            "orc_deposit_sequence": (ctypes.c_int, [I32, I32, I32, P, P, P, D, D, P]),
+            "orc_bias": (ctypes.c_int, [I32, P, I32, P, P, P, P, P, P, P]),
+            "orc_deposit_sequence": (ctypes.c_int, [I32, I32, I32, P, P, P, P, D, D, P]),
             "orc_step": (ctypes.c_int, [I32, P, P, I32, P, P, P, P, P, P, P, P, ctypes.c_int]),
             "orc_max_threads": (ctypes.c_int, []),
         }
@@ -201,20 +201,29 @@ def _grid_ref(grid):
     return None if grid is None else ctypes.byref(grid.struct())
 
 
-def bias(s, centres, heights, sigma, grid: HillGrid | None = None):
-    """V(s) and dV/ds from hills (and grid)."""
+def _period(period, ncv):
+    if period is None:
+        return None
+    return np.ascontiguousarray(np.broadcast_to(np.asarray(period, dtype=np.float64), (ncv,)))
+
+
+def bias(s, centres, heights, sigma, grid: HillGrid | None = None, period=None):
+    """V(s) and dV/ds from hills (and grid).  period: None, or one period per
+    CV (0 = not periodic; 2 pi for a torsion angle)."""
     s = np.ascontiguousarray(np.atleast_1d(s), dtype=np.float64)
     ncv = s.size
     c = np.ascontiguousarray(centres, dtype=np.float64).reshape(-1, ncv)
     w = np.ascontiguousarray(heights, dtype=np.float64)
     sg = np.ascontiguousarray(sigma, dtype=np.float64)
+    pr = _period(period, ncv)
     V = ctypes.c_double(0.0)
     dV = np.zeros(2)
-    _L().orc_bias(ncv, _ptr(s), c.shape[0], _ptr(c), _ptr(w), _ptr(sg), _grid_ref(grid), ctypes.byref(V), _ptr(dV))
+    _L().orc_bias(ncv, _ptr(s), c.shape[0], _ptr(c), _ptr(w), _ptr(sg), _ptr(pr), _grid_ref(grid), ctypes.byref(V),
+                  _ptr(dV))
     return V.value, dV[:ncv].copy()
 
 
-def deposit_sequence(centres, sigma, w0, kbdt, grid: HillGrid | None = None, heights_prefix=None):
+def deposit_sequence(centres, sigma, w0, kbdt, grid: HillGrid | None = None, heights_prefix=None, period=None):
     """Well-tempered heights of hills deposited in order at the given centres."""
     sg = np.ascontiguousarray(sigma, dtype=np.float64)
     ncv = sg.size
@@ -225,7 +234,9 @@ def deposit_sequence(centres, sigma, w0, kbdt, grid: HillGrid | None = None, hei
     if heights_prefix is not None:
         k0 = len(heights_prefix)
         w[:k0] = heights_prefix
-    _L().orc_deposit_sequence(ncv, K, k0, _ptr(c), _ptr(w), _ptr(sg), float(w0), float(kbdt), _grid_ref(grid))
+    pr = _period(period, ncv)
+    _L().orc_deposit_sequence(ncv, K, k0, _ptr(c), _ptr(w), _ptr(sg), _ptr(pr), float(w0), float(kbdt),
+                              _grid_ref(grid))
     return w
 
 
@@ -254,12 +265,14 @@ def step(pos4, p: Params, centres, heights, sigma, grid: HillGrid | None = None,
 # -(1 - 1/gamma) F(s) + const (the standard well-tempered limit; the paper
 # names well-tempered MetaD but prints no formula, read here as that limit).
 
-def fes_points(points, centres, heights, sigma, biasfactor, grid: HillGrid | None = None):
+def fes_points(points, centres, heights, sigma, biasfactor, grid: HillGrid | None = None, period=None):
     """Sum-of-hills FES at each point: F = -(gamma / (gamma - 1)) V, shifted
-    so that its minimum over the points is 0."""
+    so that its minimum over the points is 0 (gamma = inf, plain
+    metadynamics: F = -V)."""
     pts = np.atleast_2d(np.asarray(points, dtype=np.float64))
-    V = np.array([bias(p, centres, heights, sigma, grid)[0] for p in pts])
-    F = -(biasfactor / (biasfactor - 1.0)) * V
+    V = np.array([bias(p, centres, heights, sigma, grid, period=period)[0] for p in pts])
+    fac = 1.0 if np.isinf(biasfactor) else biasfactor / (biasfactor - 1.0)
+    F = -fac * V
     return F - F.min()
 
 

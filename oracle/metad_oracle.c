@@ -727,21 +727,32 @@ int orc_grid_fold(orc_grid *G, int32_t K, const double *c, const double *w, cons
 /* -------------------------------------------------------------------- bias
  * V(s) = grid(s) + sum_k w_k exp(-sum_d (s_d - c_kd)^2 / (2 sigma_d^2))
  * dV/ds_d = grid' + sum_k w_k g_k (-(s_d - c_kd) / sigma_d^2)
- * (Eqs. 2-3 with a per-dimension sigma; hills in deposition order). */
+ * (Eqs. 2-3 with a per-dimension sigma; hills in deposition order).
+ * period (NULL, or double[ncv] with 0 for a non-periodic CV): a periodic CV
+ * such as a torsion angle (Section "Alanine dipeptide torsion") sees the
+ * difference s_d - c_kd wrapped into [-P/2, P/2], nearest image only
+ * (reading: x - P * round-half-even(x / P)). */
+static double hill_diff(double x, const double *period, int d)
+{
+    if (period && period[d] > 0.0) x -= period[d] * nearbyint(x / period[d]);
+    return x;
+}
+
 int orc_bias(int32_t ncv, const double *s, int32_t K, const double *c, const double *w, const double *sigma,
-             const orc_grid *G, double *V, double *dV)
+             const double *period, const orc_grid *G, double *V, double *dV)
 {
     double v = 0.0, g[2] = {0.0, 0.0};
     if (G && G->data && ncv == 2) grid_eval(G, s, &v, g);
     for (int32_t k = 0; k < K; ++k) {
         double e = 0.0;
         for (int d = 0; d < ncv; ++d) {
-            double x = s[d] - c[(int64_t)ncv * k + d];
+            double x = hill_diff(s[d] - c[(int64_t)ncv * k + d], period, d);
             e += x * x / (2.0 * sigma[d] * sigma[d]);
         }
         double gk = w[k] * exp(-e);
         v += gk;
-        for (int d = 0; d < ncv; ++d) g[d] += gk * (-(s[d] - c[(int64_t)ncv * k + d]) / (sigma[d] * sigma[d]));
+        for (int d = 0; d < ncv; ++d)
+            g[d] += gk * (-hill_diff(s[d] - c[(int64_t)ncv * k + d], period, d) / (sigma[d] * sigma[d]));
     }
     *V = v;
     for (int d = 0; d < ncv; ++d) dV[d] = g[d];
@@ -754,11 +765,11 @@ int orc_bias(int32_t ncv, const double *s, int32_t K, const double *c, const dou
  * where V_{k-1} is the grid plus hills 0..k-1.  Hills 0..k_first-1 already
  * carry heights in w; hills k_first..K-1 get theirs here. */
 int orc_deposit_sequence(int32_t ncv, int32_t K, int32_t k_first, const double *c, double *w,
-                         const double *sigma, double w0, double kbdt, const orc_grid *G)
+                         const double *sigma, const double *period, double w0, double kbdt, const orc_grid *G)
 {
     for (int32_t k = k_first; k < K; ++k) {
         double V, dV[2];
-        orc_bias(ncv, c + (int64_t)ncv * k, k, c, w, sigma, G, &V, dV);
+        orc_bias(ncv, c + (int64_t)ncv * k, k, c, w, sigma, period, G, &V, dV);
         w[k] = w0 * exp(-V / kbdt);
     }
     return 0;
@@ -773,7 +784,7 @@ int orc_step(int32_t n, const float *pos4, const orc_params *p, int32_t K, const
     if (cv_forward(n, pos4, p, &S, nthreads) != 0) { cv_free(&S); return -1; }
     s[0] = S.s[0];
     if (p->n_cv >= 2) s[1] = S.s[1];
-    orc_bias(p->n_cv, S.s, K, c, w, sigma, G, V, dV);
+    orc_bias(p->n_cv, S.s, K, c, w, sigma, NULL, G, V, dV);
     int rc = cv_reverse(pos4, p, &S, dV, F);
     cv_free(&S);
     return rc;
