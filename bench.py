@@ -68,6 +68,7 @@ def parse():
     ap.add_argument("--max-neighbors", type=int, default=64, help="per-atom neighbour-row capacity")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-system batched comparison")
     ap.add_argument("--no-served", action="store_true", help="skip the served (continuous batching) trace")
+    ap.add_argument("--no-small", action="store_true", help="skip the torsion / nearest-distance walker forms")
     ap.add_argument("--batched-steps", type=int, default=10)
     return ap.parse_args()
 
@@ -416,6 +417,8 @@ def run_metad(args):
             forms["batched"] = run_batched(args, dev, stream, metad)
         if not args.no_served:
             forms["served"] = run_served(args, dev, stream, metad)
+        if not args.no_small:
+            forms["small_cvs"] = run_small_cvs(args, dev, stream, metad)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": max(3, args.warmup), "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
@@ -517,6 +520,97 @@ def run_batched(args, dev, stream, metad):
             "speedup": plain_ms / batch_ms, "kernels_per_step": {"plain": plain_launches, "batched": batch_launches},
             "tile": tuned["tile"], "tile_ms": {str(c): v for c, v in tuned["ms_per_step"].items()},
             "inputs": f"{nfr} resident frames per system cycled (positions > L2)"}
+
+
+def run_small_cvs(args, dev, stream, metad):
+    """The torsion and nearest-distance CV families on many small walkers:
+    256 chain-molecule walkers (22 atoms, two backbone torsions, 10,000 hills
+    each, plain metadynamics, sigma 0.35 rad) and 32 slab + water walkers
+    (717 atoms, surface-oxygen to nearest-hydrogen distance, 1,500
+    well-tempered hills each): one batched step per frame against plain
+    per-walker steps, plus one walker's step latency replayed from a CUDA
+    graph.  The hill sums (FP64) are the dominant work; hill evaluations per
+    second are reported beside walker-steps per second."""
+    import torch
+    out = {}
+    steps = max(1, args.batched_steps)
+    specs = []
+    pp = synth.SMALL_PARAMS["peptide"]
+    pep = []
+    for w in range(256):
+        p = metad.params_for(synth.PEPTIDE_ATOMS, synth.peptide_box(), n_cv=2, sigma=pp["sigma"], w0=pp["w0"],
+                             biasfactor=pp["biasfactor"], cv_kind="torsion", hill_capacity=pp["hills"] + 64,
+                             stream=stream.cuda_stream)
+        c = metad.Metad(p)
+        c.set_cv_atoms(synth.PEPTIDE_TORSIONS)
+        cen = synth.torus_centres(w, pp["hills"])
+        c.load_hills(cen, np.full(len(cen), pp["w0"]))
+        pep.append((c, [synth.peptide_frame(4 * w + f, sys=w) for f in range(4)]))
+    specs.append(("torsion_walkers", pep, pp["hills"]))
+    sp = synth.SMALL_PARAMS["surface_water"]
+    surf = []
+    layouts = [synth.SurfaceWater(sys=k) for k in range(4)]  # 8 walkers per layout, own frames and hills
+    for w in range(32):
+        sw = layouts[w % 4]
+        p = metad.params_for(sw.n, sw.box, n_cv=1, sigma=sp["sigma"], w0=sp["w0"], biasfactor=sp["biasfactor"],
+                             cv_kind="nearest", hill_capacity=sp["hills"] + 64, stream=stream.cuda_stream)
+        c = metad.Metad(p)
+        c.set_cv_atoms(sw.cv_atoms())
+        cen = synth.interval_centres(synth.SURFACE_CFG, w, sp["hills"], sp["cv_lo"], sp["cv_hi"])
+        c.deposit_hills(cen, want_heights=False)
+        surf.append((c, [sw.frame(4 * w + f) for f in range(4)]))
+    specs.append(("nearest_distance_walkers", surf, sp["hills"]))
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for name, walkers, hills in specs:
+        ctxs = [c for c, _ in walkers]
+        frames = [[torch.from_numpy(f).to(dev) for f in fr] for _, fr in walkers]
+        F = [torch.zeros((fr[0].shape[0], 3), dtype=torch.float32, device=dev) for fr in frames]
+        batch = metad.Batch(ctxs)
+
+        def plain(t):
+            for k, c in enumerate(ctxs):
+                c.step(frames[k][t % 4], F[k])
+
+        def batched(t):
+            batch.step([fr[t % 4] for fr in frames], F)
+
+        res = {}
+        for label, fn, count in (("plain", plain, lambda: sum(c.launch_count for c in ctxs)),
+                                 ("batched", batched, lambda: batch.launch_count)):
+            for t in range(3):
+                fn(t)
+            torch.cuda.synchronize(dev)
+            l0 = count()
+            ev0.record(stream)
+            for t in range(steps):
+                fn(t)
+            ev1.record(stream)
+            torch.cuda.synchronize(dev)
+            res[label] = (ev0.elapsed_time(ev1) / steps, (count() - l0) / steps)
+        batch.close()
+        # one walker alone, its step replayed from a captured CUDA graph
+        c0 = ctxs[0]
+        c0.set_step_graph(True)
+        for t in range(3):
+            c0.step(frames[0][0], F[0])
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        for t in range(200):
+            c0.step(frames[0][0], F[0])
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        alone_us = ev0.elapsed_time(ev1) / 200 * 1e3
+        nw = len(ctxs)
+        pm, pk = res["plain"]
+        bm, bk = res["batched"]
+        out[name] = {"walkers": nw, "atoms_per_walker": int(frames[0][0].shape[0]), "hills_per_walker": hills,
+                     "steps": steps, "plain_ms_per_step": pm, "batched_ms_per_step": bm,
+                     "plain_walker_steps_per_s": nw / (pm / 1e3), "batched_walker_steps_per_s": nw / (bm / 1e3),
+                     "batched_hill_evals_per_s": nw * hills / (bm / 1e3), "speedup": pm / bm,
+                     "kernels_per_step": {"plain": pk, "batched": bk}, "one_walker_graph_step_us": alone_us}
+        for c in ctxs:
+            c.close()
+    return out
 
 
 def run_served(args, dev, stream, metad):

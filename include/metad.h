@@ -56,8 +56,11 @@ typedef enum {
 /* Parameters of one context.  Fill with metad_params_default, then edit. */
 typedef struct {
     int32_t n_atoms;        /* N >= 1 */
-    int32_t n_cv;           /* 1: coordination number; 2: CN and averaged Q6 */
-    double box[3];          /* orthorhombic box lengths, each >= 2 rc */
+    int32_t n_cv;           /* 1: coordination number; 2: CN and averaged Q6
+                               (torsion / nearest-distance families: 1 or 2
+                               CVs of the family) */
+    double box[3];          /* orthorhombic box lengths, each >= 2 rc (> 0 for
+                               the torsion and nearest-distance families) */
     double rc;              /* neighbour cutoff (3.5) */
     double r0;              /* switch length (2.5) */
     int32_t sw_n, sw_m;     /* rational switch exponents (6, 12) */
@@ -65,10 +68,12 @@ typedef struct {
     int32_t cn_pairs;       /* 1: CN counts unlike-species pairs only; 0: all */
     double sigma[2];        /* hill widths per CV */
     double w0;              /* initial hill height, kJ/mol */
-    double biasfactor;      /* well-tempered gamma > 1 */
+    double biasfactor;      /* well-tempered gamma > 1; +infinity gives plain
+                               metadynamics (every height w0) */
     double temperature;     /* K */
     double kB;              /* kJ/mol/K (0.0083144626) */
-    int32_t grid_on;        /* 1: bicubic Hermite bias grid (n_cv == 2 only) */
+    int32_t grid_on;        /* 1: bicubic Hermite bias grid (n_cv == 2 only;
+                               not for torsions) */
     int32_t grid_n[2];      /* nodes per axis, both ends included (>= 2) */
     int32_t hill_capacity;  /* maximum live hills */
     double grid_lo[2];
@@ -89,7 +94,41 @@ typedef struct {
                                when an atom has moved more than skin/2 since
                                the last rebuild; 0 rebuilds every step.  The
                                exact rc list is recomputed every step. */
+    int32_t cv_kind;        /* METAD_CV_COORDINATION (default), METAD_CV_TORSION
+                               or METAD_CV_NEAREST (below) */
+    int32_t reserved0;      /* 0 */
+    double softmin_beta;    /* METAD_CV_NEAREST: 0 (default) = the exact nearest
+                               distance; > 0 = its soft minimum with this beta
+                               (1/Angstrom), see metad_set_cv_atoms */
 } metad_params;
+
+/* CV families (metad_params.cv_kind).
+ *
+ * METAD_CV_COORDINATION: s1 = mean coordination number, s2 = mean locally
+ *   averaged Q6, over the rc neighbour list (the paper's GaN runs, Section
+ *   "B4-B1 phase transition in Large-scale systems").
+ * METAD_CV_TORSION: n_cv torsion (dihedral) angles of atom quadruplets, the
+ *   backbone Phi / Psi of the paper's alanine-dipeptide runs (Section
+ *   "Alanine dipeptide torsion").  IUPAC sign, values in [-pi, pi], bond
+ *   vectors by the minimum image; collinear atoms give 0 and no force.  The
+ *   CVs are periodic: every hill sees s_d - c_kd wrapped into [-pi, pi]
+ *   (nearest image).  No grid.
+ * METAD_CV_NEAREST: n_cv distances, each from a reference atom to the
+ *   nearest atom of one candidate group (minimum image), the surface-oxygen
+ *   to nearest-hydrogen CV of the paper's rutile runs (Section "Water
+ *   dissociation on rutile (110) surface").  The nearest candidate is the
+ *   argmin of the FP64 squared distance (first in list order on a tie); with
+ *   softmin_beta > 0 the CV is instead the soft minimum
+ *     s = r_min - (1/beta) log sum_j exp(-beta (r_j - r_min)).
+ *
+ * The torsion and nearest-distance families use no neighbour list: rc, r0,
+ * the switch, skin and max_neighbors are ignored, each box length need only
+ * be positive, and the atoms come from metad_set_cv_atoms, which must be
+ * called before the first cv_forward.  Bond and distance vectors are exact
+ * FP64 differences of the float32 positions; a torsion's angle and gradient
+ * then run in FP32 (precision 0) or FP64 (precision 1); the nearest distance
+ * is FP64 in both.  Hills and forces are as for every family. */
+enum { METAD_CV_COORDINATION = 0, METAD_CV_TORSION = 1, METAD_CV_NEAREST = 2 };
 
 /* Defaults of the paper's GaN-style workloads: rc 3.5, r0 2.5, n 6, m 12,
  * stretched switch, unlike-pair CN, two CVs, sigma (0.05, 0.02), w0 1,
@@ -129,6 +168,16 @@ metad_status metad_bias_eval(metad_ctx *ctx, const double *s_host, double *V_hos
  * accumulate 0: forces_dev = F; 1: forces_dev += F.  Deterministic: no
  * floating-point atomics. */
 metad_status metad_bias_forces(metad_ctx *ctx, float *forces_dev, int32_t accumulate, double scale);
+
+/* Atoms of the torsion and nearest-distance CVs, caller indices (host int32):
+ *   METAD_CV_TORSION: count = 4 n_cv, quadruplets (a, b, c, d) in CV order;
+ *   METAD_CV_NEAREST: count = n_cv + M, the n_cv reference atoms, then the
+ *     M >= 1 candidate atoms shared by every CV.
+ * Copied to the device (stream-ordered); may be called again between steps.
+ * Errors: METAD_ERR_INVALID (NULL, wrong count, an index outside [0, N), an
+ * atom repeated within a quadruplet or in the candidate group, a reference
+ * atom that is also a candidate, a context of the coordination family). */
+metad_status metad_set_cv_atoms(metad_ctx *ctx, const int32_t *atoms_host, int32_t count);
 
 /* Step a9: deposit one hill at c (center_host double[n_cv], or NULL for the
  * last CVs) with the well-tempered height

@@ -19,13 +19,14 @@ OUT_DIR = os.path.join(HERE, "_lib")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmetad.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "k_neighbors.cu", "k_cv.cu", "k_bias.cu", "k_fes.cu", "k_static.cu"]
-# The FP64 hill and grid arithmetic (bias and free-energy kernels) is
-# compiled without multiply-add contraction: every product and sum rounds on
-# its own, so the single-system and batched instantiations of the hill
-# kernel give the same bits (the compiler may otherwise fuse differently in
-# each).
-FILE_FLAGS = {"k_bias.cu": ["-fmad=false"], "k_fes.cu": ["-fmad=false"]}
+SOURCES = ["api.cu", "k_neighbors.cu", "k_cv.cu", "k_bias.cu", "k_fes.cu", "k_gcv.cu", "k_static.cu"]
+# The FP64 hill and grid arithmetic (bias and free-energy kernels) and the
+# FP64 torsion / nearest-distance CVs are compiled without multiply-add
+# contraction: every product and sum rounds on its own, so the single-system
+# and batched instantiations give the same bits (the compiler may otherwise
+# fuse differently in each) and a squared distance rounds as its plain
+# definition.
+FILE_FLAGS = {"k_bias.cu": ["-fmad=false"], "k_fes.cu": ["-fmad=false"], "k_gcv.cu": ["-fmad=false"]}
 
 
 def nvcc() -> str:

@@ -23,6 +23,7 @@ struct metad_ctx {
     int fp64 = 0;
     int K = 0;
     bool have_nbr = false, have_cv = false, have_bias = false;
+    bool atoms_set = false;       // torsion / nearest-distance: metad_set_cv_atoms done
     bool filter_pending = false;  // exact rows not yet compacted from the Verlet rows
     bool failed = false;
     std::string last_error;
@@ -198,13 +199,31 @@ metad_status validate(const metad_params *p, std::string &why)
     if (!p) { why = "params is NULL"; return METAD_ERR_INVALID; }
     if (p->n_atoms < 1) { why = "n_atoms < 1"; return METAD_ERR_INVALID; }
     if (p->n_cv != 1 && p->n_cv != 2) { why = "n_cv must be 1 or 2"; return METAD_ERR_INVALID; }
-    if (!(p->rc > 0) || !(p->r0 > 0)) { why = "rc and r0 must be positive"; return METAD_ERR_INVALID; }
-    for (int a = 0; a < 3; ++a)
-        if (!(p->box[a] >= 2.0 * p->rc) || !std::isfinite(p->box[a])) {
-            why = "every box length must be >= 2 rc";
+    if (p->cv_kind != METAD_CV_COORDINATION && p->cv_kind != METAD_CV_TORSION && p->cv_kind != METAD_CV_NEAREST) {
+        why = "unknown cv_kind";
+        return METAD_ERR_INVALID;
+    }
+    if (p->cv_kind != METAD_CV_COORDINATION) {
+        for (int a = 0; a < 3; ++a)
+            if (!(p->box[a] > 0.0) || !std::isfinite(p->box[a])) {
+                why = "every box length must be positive";
+                return METAD_ERR_INVALID;
+            }
+        if (p->n_atoms < (p->cv_kind == METAD_CV_TORSION ? 4 : 2)) { why = "too few atoms"; return METAD_ERR_INVALID; }
+        if (p->cv_kind == METAD_CV_TORSION && p->grid_on) { why = "no grid for torsions"; return METAD_ERR_INVALID; }
+        if (!(p->softmin_beta >= 0.0) || !std::isfinite(p->softmin_beta)) {
+            why = "softmin_beta must be >= 0";
             return METAD_ERR_INVALID;
         }
-    if (p->sw_n < 1 || p->sw_m < 1 || p->sw_n == p->sw_m) { why = "switch exponents"; return METAD_ERR_INVALID; }
+    } else {
+        if (!(p->rc > 0) || !(p->r0 > 0)) { why = "rc and r0 must be positive"; return METAD_ERR_INVALID; }
+        for (int a = 0; a < 3; ++a)
+            if (!(p->box[a] >= 2.0 * p->rc) || !std::isfinite(p->box[a])) {
+                why = "every box length must be >= 2 rc";
+                return METAD_ERR_INVALID;
+            }
+        if (p->sw_n < 1 || p->sw_m < 1 || p->sw_n == p->sw_m) { why = "switch exponents"; return METAD_ERR_INVALID; }
+    }
     for (int d = 0; d < p->n_cv; ++d)
         if (!(p->sigma[d] > 0)) { why = "sigma must be positive"; return METAD_ERR_INVALID; }
     if (!(p->biasfactor > 1.0) || !(p->temperature > 0) || !(p->kB > 0)) {
@@ -226,6 +245,8 @@ metad_status validate(const metad_params *p, std::string &why)
     return METAD_OK;
 }
 
+constexpr double kTwoPi = 6.283185307179586476925286766559;  // the period of a torsion angle
+
 // Host-side geometry and constants of a context's system (no allocation).
 metad_status setup_system(metad_ctx *c)
 {
@@ -233,6 +254,10 @@ metad_status setup_system(metad_ctx *c)
     const int n = c->p.n_atoms;
     y.n = n;
     y.ncv = c->p.n_cv;
+    y.kind = c->p.cv_kind;
+    y.period[0] = y.period[1] = c->p.cv_kind == METAD_CV_TORSION ? kTwoPi : 0.0;
+    y.inv_period[0] = y.inv_period[1] = c->p.cv_kind == METAD_CV_TORSION ? 1.0 / kTwoPi : 0.0;
+    y.sm_beta = c->p.softmin_beta;
     y.cn_unlike = c->p.cn_pairs ? 1 : 0;
     y.max_nb = c->p.max_neighbors;
     for (int a = 0; a < 3; ++a) {
@@ -240,11 +265,17 @@ metad_status setup_system(metad_ctx *c)
         y.L[a] = L;
         split(L, y.Lhi[a], y.Llo[a]);
         y.halfL[a] = (float)(0.5 * L);
+        float lin = (float)L;
+        if ((double)lin >= L) lin = std::nextafter(lin, 0.0f);
+        y.Lin[a] = lin;
         // cell edge >= (rc + skin)(1 + 1e-4): float32 cell assignment can
         // never split a Verlet pair across non-adjacent cells
         int nc = (int)std::floor(L / ((c->p.rc + c->p.skin) * (1.0 + 1e-4)));
         if (nc < 1) nc = 1;
-        if (nc > 1023) return METAD_ERR_INVALID;
+        if (nc > 1023) {
+            if (c->p.cv_kind != METAD_CV_COORDINATION) nc = 1;  // no cells
+            else return METAD_ERR_INVALID;
+        }
         y.nc[a] = nc;
         y.inv_h[a] = (float)(nc / L);
     }
@@ -311,6 +342,20 @@ metad_status state_buffers(metad_ctx *c, Buffers &b, Alloc &&alloc)
     const size_t rs = c->fp64 ? sizeof(double) : sizeof(float);
     const size_t nq = c->p.n_cv == 2 ? (size_t)16 * n : 16;
     metad_status s;
+    if (c->p.cv_kind != METAD_CV_COORDINATION) {
+        // no neighbour list: CV atoms, gradient terms, reductions and hills
+        int *atoms = nullptr, *slot = nullptr;
+        if ((s = alloc(&atoms, 4 * (size_t)2 + n)) || (s = alloc(&slot, n)) || (s = alloc(&y.gcv, 32)) ||
+            (s = alloc(&y.part, (size_t)y.part_stride * 4)) || (s = alloc(&y.ticket, 8)) ||
+            (s = alloc(&y.scal, metad::kNumScal)) || (s = alloc(&y.err, 1)) ||
+            (s = alloc(&y.hc, 2 * (size_t)y.hill_cap + 2)) || (s = alloc(&y.hw, (size_t)y.hill_cap + 1)) ||
+            (s = alloc(&c->stage, 2 * (size_t)y.hill_cap + 2)) ||
+            (s = alloc(&y.grid, (size_t)y.gn[0] * y.gn[1] * 4)))
+            return s;
+        y.cv_atoms = atoms;
+        y.cand_slot = slot;
+        return METAD_OK;
+    }
     if ((s = alloc(&y.pos_s, n)) || (s = alloc(&y.perm, n)) || (s = alloc(&y.scell, n)) ||
         (s = alloc(&y.ucell, n)) || (s = alloc(&y.uslot, n)) || (s = alloc(&y.cell_count, y.ncell)) ||
         (s = alloc(&y.cell_start, (size_t)y.ncell + 1)) || (s = alloc(&y.scan_part, y.ncell / 4096 + 2)) ||
@@ -467,6 +512,24 @@ metad_status metad_create(const metad_params *p, metad_ctx **out)
         metad_destroy(c);
         return s;
     }
+    if (c->p.cv_kind != METAD_CV_COORDINATION) {
+        if (cudaMallocHost(&c->host_pinned, 64 * sizeof(double)) != cudaSuccess ||
+            cudaMallocHost(&c->err_pinned, sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            metad_destroy(c);
+            return METAD_ERR_OOM;
+        }
+        cudaMemsetAsync(y.ticket, 0, 8 * sizeof(unsigned), c->stream);
+        cudaMemsetAsync(y.scal, 0, metad::kNumScal * sizeof(double), c->stream);
+        cudaMemsetAsync(y.err, 0, sizeof(int), c->stream);
+        cudaMemsetAsync(y.gcv, 0, 32 * sizeof(double), c->stream);
+        cudaMemsetAsync(y.grid, 0, sizeof(double) * (size_t)y.gn[0] * y.gn[1] * 4, c->stream);
+        cudaMemsetAsync(const_cast<int *>(y.cand_slot), 0xff, sizeof(int) * (size_t)n, c->stream);  // -1
+        s = cuda_check(c, cudaStreamSynchronize(c->stream), "create");
+        if (s != METAD_OK) { metad_destroy(c); return s; }
+        *out = c;
+        return METAD_OK;
+    }
     int *rank_xyz = bf.rank_xyz, *xyz_rank = bf.xyz_rank;
     char *rb = bf.rb, *wlb = bf.wlb, *pfb = bf.pfb;
     // records first (16-element rows stay 64 / 128 B aligned), scalars after
@@ -547,6 +610,11 @@ metad_status metad_build_neighbors(metad_ctx *c, const float *pos_dev)
     if (s) return s;
     if (!pos_dev) return fail(c, METAD_ERR_INVALID, "pos_dev is NULL");
     c->sys.pos_in = reinterpret_cast<const float4 *>(pos_dev);
+    if (c->p.cv_kind != METAD_CV_COORDINATION) {  // no list: the positions are read by the CV pass
+        c->have_nbr = true;
+        c->have_cv = c->have_bias = false;
+        return METAD_OK;
+    }
     {
         StageScope t(c, ST_BIN, 1);
         metad::launch_gather_check(c->sys, c->stream);
@@ -568,6 +636,12 @@ metad_status metad_cv_forward(metad_ctx *c, double *cv_host, double *per_atom_de
     metad_status s = check_usable(c);
     if (s) return s;
     if (!c->have_nbr) return fail(c, METAD_ERR_STATE, "cv_forward before build_neighbors");
+    if (c->p.cv_kind != METAD_CV_COORDINATION) {
+        if (per_atom_dev) return fail(c, METAD_ERR_INVALID, "no per-atom CVs for this CV family");
+        if (!c->atoms_set) return fail(c, METAD_ERR_STATE, "cv_forward before set_cv_atoms");
+        StageScope t(c, ST_CV_FWD, 1);
+        metad::launch_gcv_forward(c->sys, c->fp64, c->stream);
+    } else {
     {
         StageScope t(c, ST_CV_FWD, 1);
         metad::launch_cv_fwd(c->sys, c->fp64, c->filter_pending ? 1 : 0, c->stream);
@@ -583,6 +657,7 @@ metad_status metad_cv_forward(metad_ctx *c, double *cv_host, double *per_atom_de
     if (per_atom_dev) {
         StageScope t(c, ST_OTHER, 1);
         metad::launch_per_atom_out(c->sys, c->fp64, per_atom_dev, c->stream);
+    }
     }
     s = launched(c, "cv_forward");
     if (s) return s;
@@ -639,6 +714,13 @@ metad_status metad_bias_forces(metad_ctx *c, float *forces_dev, int32_t accumula
     if (s) return s;
     if (!forces_dev) return fail(c, METAD_ERR_INVALID, "forces_dev is NULL");
     if (!c->have_bias || !c->have_cv) return fail(c, METAD_ERR_STATE, "bias_forces before bias_eval");
+    if (c->p.cv_kind != METAD_CV_COORDINATION) {
+        {
+            StageScope t(c, ST_FORCE, 1);
+            metad::launch_gcv_forces(c->sys, forces_dev, accumulate ? 1 : 0, scale, c->stream);
+        }
+        return launched(c, "bias_forces");
+    }
     if (c->p.n_cv == 2) {
         StageScope t(c, ST_ADJ, 1);
         metad::launch_adjoint(c->sys, c->fp64, c->stream);
@@ -652,6 +734,51 @@ metad_status metad_bias_forces(metad_ctx *c, float *forces_dev, int32_t accumula
         metad::launch_force_gather(c->sys, c->fp64, forces_dev, accumulate ? 1 : 0, c->stream);
     }
     return launched(c, "bias_forces");
+}
+
+metad_status metad_set_cv_atoms(metad_ctx *c, const int32_t *atoms_host, int32_t count)
+{
+    metad_status s = check_usable(c);
+    if (s) return s;
+    if (c->p.cv_kind == METAD_CV_COORDINATION) return fail(c, METAD_ERR_INVALID, "the coordination CVs take no atoms");
+    if (!atoms_host) return fail(c, METAD_ERR_INVALID, "atoms is NULL");
+    const int n = c->p.n_atoms, ncv = c->p.n_cv;
+    for (int k = 0; k < count; ++k)
+        if (atoms_host[k] < 0 || atoms_host[k] >= n) return fail(c, METAD_ERR_INVALID, "atom index out of range");
+    std::vector<int> slot(n, -1);
+    if (c->p.cv_kind == METAD_CV_TORSION) {
+        if (count != 4 * ncv) return fail(c, METAD_ERR_INVALID, "a torsion takes 4 atoms");
+        for (int d = 0; d < ncv; ++d)
+            for (int a = 0; a < 4; ++a)
+                for (int b = 0; b < a; ++b)
+                    if (atoms_host[4 * d + a] == atoms_host[4 * d + b])
+                        return fail(c, METAD_ERR_INVALID, "an atom repeated within a torsion");
+    } else {
+        if (count < ncv + 1) return fail(c, METAD_ERR_INVALID, "no candidate atoms");
+        for (int m = 0; m < count - ncv; ++m) {
+            const int j = atoms_host[ncv + m];
+            if (slot[j] >= 0) return fail(c, METAD_ERR_INVALID, "a candidate repeated");
+            slot[j] = m;
+        }
+        for (int d = 0; d < ncv; ++d)
+            if (slot[atoms_host[d]] >= 0) return fail(c, METAD_ERR_INVALID, "a reference atom is also a candidate");
+        c->sys.n_cand = count - ncv;
+    }
+    // the buffers are sized for 8 + N entries; stream-ordered after earlier steps
+    if ((s = cuda_check(c, cudaMemcpyAsync(const_cast<int *>(c->sys.cv_atoms), atoms_host, sizeof(int) * count,
+                                           cudaMemcpyHostToDevice, c->stream), "atom upload")) ||
+        (s = cuda_check(c, cudaMemcpyAsync(const_cast<int *>(c->sys.cand_slot), slot.data(), sizeof(int) * n,
+                                           cudaMemcpyHostToDevice, c->stream), "slot upload")) ||
+        (s = sync_and_check(c)))
+        return s;
+    c->atoms_set = true;
+    c->have_cv = c->have_bias = false;
+    for (auto &g : c->graphs)  // captured steps hold the old descriptor
+        if (g.exec) {
+            cudaGraphExecDestroy(g.exec);
+            g.exec = nullptr;
+        }
+    return METAD_OK;
 }
 
 metad_status metad_deposit_hill(metad_ctx *c, const double *center_host, double *height_host)
@@ -797,6 +924,7 @@ metad_status metad_export_neighbors(metad_ctx *c, int64_t *pairs_host, int64_t c
 {
     metad_status s = check_usable(c);
     if (s) return s;
+    if (c->p.cv_kind != METAD_CV_COORDINATION) return fail(c, METAD_ERR_INVALID, "no neighbour list");
     if (!c->have_nbr) return fail(c, METAD_ERR_STATE, "export before build_neighbors");
     const int64_t need = (int64_t)c->sys.n * c->sys.max_nb / 2 + 1;
     if (c->pairs_cap < need) {
@@ -993,6 +1121,7 @@ metad_status metad_rebuild_count(metad_ctx *c, int64_t *count)
 {
     metad_status s = check_usable(c);
     if (s) return s;
+    if (c->p.cv_kind != METAD_CV_COORDINATION) return fail(c, METAD_ERR_INVALID, "no neighbour list");
     unsigned long long v = 0;
     if ((s = cuda_check(c, cudaMemcpyAsync(&v, c->sys.rebuilds, sizeof(v), cudaMemcpyDeviceToHost, c->stream),
                         "rebuild count")))
@@ -1006,6 +1135,7 @@ metad_status metad_neighbor_stats(metad_ctx *c, int64_t *entries, int32_t *max_p
 {
     metad_status s = check_usable(c);
     if (s) return s;
+    if (c->p.cv_kind != METAD_CV_COORDINATION) return fail(c, METAD_ERR_INVALID, "no neighbour list");
     if (!c->have_nbr) return fail(c, METAD_ERR_STATE, "neighbor_stats before build_neighbors");
     unsigned long long *sum = reinterpret_cast<unsigned long long *>(c->sys.part + 3 * (size_t)c->sys.part_stride);
     int *mx = reinterpret_cast<int *>(sum + 1);
@@ -1060,7 +1190,7 @@ struct metad_batch {
     std::vector<metad_ctx *> ctx;
     int n = 0;
     cudaStream_t stream = nullptr;
-    int device = 0, fp64 = 0, ncv = 2;
+    int device = 0, fp64 = 0, ncv = 2, kind = 0;
     int persist_cap = 0;
     // device: descriptors [n], then the block prefix rows [kGridKinds][n + 1]
     char *dev = nullptr;
@@ -1116,7 +1246,7 @@ metad_status metad_batch_create(metad_ctx *const *ctxs, int32_t n, metad_batch *
         const metad_ctx *c = ctxs[k];
         if (!c || c->failed) return METAD_ERR_INVALID;
         if (c->p.device != ctxs[0]->p.device || c->stream != ctxs[0]->stream || c->p.n_cv != ctxs[0]->p.n_cv ||
-            c->fp64 != ctxs[0]->fp64)
+            c->fp64 != ctxs[0]->fp64 || c->p.cv_kind != ctxs[0]->p.cv_kind)
             return METAD_ERR_INVALID;
     }
     metad_batch *b = new (std::nothrow) metad_batch();
@@ -1127,6 +1257,7 @@ metad_status metad_batch_create(metad_ctx *const *ctxs, int32_t n, metad_batch *
     b->device = ctxs[0]->p.device;
     b->fp64 = ctxs[0]->fp64;
     b->ncv = ctxs[0]->p.n_cv;
+    b->kind = ctxs[0]->p.cv_kind;
     if (cudaSetDevice(b->device) != cudaSuccess) {
         metad_batch_destroy(b);
         return METAD_ERR_CUDA;
@@ -1167,6 +1298,8 @@ metad_status metad_batch_step(metad_batch *b, const float *const *pos_dev, float
         metad_ctx *c = b->ctx[k];
         if (c->failed) return batch_fail(b, METAD_ERR_STATE, "system " + std::to_string(k) + " has failed");
         if (!pos_dev[k] || !forces_dev[k]) return batch_fail(b, METAD_ERR_INVALID, "NULL buffer");
+        if (b->kind != METAD_CV_COORDINATION && !c->atoms_set)
+            return batch_fail(b, METAD_ERR_STATE, "system " + std::to_string(k) + " has no CV atoms");
         if (deposit && deposit[k]) {
             if (c->K >= c->p.hill_capacity)
                 return batch_fail(b, METAD_ERR_CAPACITY, "hill list of system " + std::to_string(k) + " full");
@@ -1204,6 +1337,13 @@ metad_status metad_batch_step(metad_batch *b, const float *const *pos_dev, float
     const int *dpre = reinterpret_cast<const int *>(b->dev + b->sys_bytes);
     metad::BatchView rows[metad::kGridKinds];
     for (int g = 0; g < metad::kGridKinds; ++g) rows[g] = metad::BatchView{dsys, dpre + g * (n + 1), n};
+    if (b->kind != METAD_CV_COORDINATION) {
+        metad::launch_batch_gcv(rows[metad::GK_ONE], totals[metad::GK_ONE], b->fp64, b->stream);
+        metad::launch_batch_bias(rows[metad::GK_HILLS], totals[metad::GK_HILLS], 0, b->stream);
+        metad::launch_batch_gcv_forces(rows[metad::GK_ATOM256], totals[metad::GK_ATOM256], b->stream);
+        if (any_deposit) metad::launch_batch_bias(rows[metad::GK_DEPOSIT], totals[metad::GK_DEPOSIT], 1, b->stream);
+        b->launches += 3 + (any_deposit ? 1 : 0);
+    } else {
     metad::launch_batch_gather(rows[metad::GK_ATOM256], totals[metad::GK_ATOM256], b->stream);
     metad::launch_batch_rebuild(rows, totals, b->stream);
     metad::launch_batch_cv(rows[metad::GK_GROUPS], totals[metad::GK_GROUPS], rows[metad::GK_CV], totals[metad::GK_CV],
@@ -1214,6 +1354,7 @@ metad_status metad_batch_step(metad_batch *b, const float *const *pos_dev, float
                               b->ncv, b->stream);
     if (any_deposit) metad::launch_batch_bias(rows[metad::GK_DEPOSIT], totals[metad::GK_DEPOSIT], 1, b->stream);
     b->launches += 1 + 8 + 2 + 1 + (b->ncv == 2 ? 3 : 2) + (any_deposit ? 1 : 0);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         for (metad_ctx *c : b->ctx) c->failed = true;
@@ -1318,7 +1459,7 @@ metad_status metad_fes_grid(metad_ctx *c, const double *lo, const double *hi, co
     if ((s = cuda_check(c, cudaMalloc(&buf.p, sizeof(double) * 2 * bins), "fes buffer"))) return s;
     double *V = static_cast<double *>(buf.p), *F = V + bins;
     const int nn[2] = {n[0], c->p.n_cv == 2 ? n[1] : 1};
-    const double fac = c->p.biasfactor / (c->p.biasfactor - 1.0);
+    const double fac = std::isinf(c->p.biasfactor) ? 1.0 : c->p.biasfactor / (c->p.biasfactor - 1.0);
     metad::launch_fes_points(c->sys, c->K, lo, hi, nn, V, F, fac, c->stream);
     c->launches += 2;
     if ((s = launched(c, "fes_grid"))) return s;

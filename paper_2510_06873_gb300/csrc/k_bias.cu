@@ -4,6 +4,8 @@
 //   V(s) = grid(s) + sum_k w_k exp(-sum_d (s_d - c_kd)^2 / (2 sigma_d^2))
 //   w_new = w0 exp(-V(c_new) / (kB T (gamma - 1)))
 //
+// A periodic CV (a torsion angle) sees s_d - c_kd wrapped into [-pi, pi].
+//
 // The hill sum is spread over many blocks (FP64 throughput per SM is low on
 // this part) and finished by the last block to arrive, which adds the
 // partials in block order, so the result is independent of scheduling.
@@ -25,11 +27,11 @@ __device__ __forceinline__ void bias(const Sys &s, Blk blk)
     const double inv2v0 = 0.5 / (s.sigma[0] * s.sigma[0]), inv2v1 = 0.5 / (s.sigma[1] * s.sigma[1]);
     double V = 0.0, g0 = 0.0, g1 = 0.0;
     for (int k = blk.b * blockDim.x + threadIdx.x; k < K; k += blk.nb * blockDim.x) {
-        const double d0 = x0 - s.hc[2 * (size_t)k];
+        const double d0 = hill_diff(s, 0, x0 - s.hc[2 * (size_t)k]);
         double e = d0 * d0 * inv2v0;
         double d1 = 0.0;
         if (s.ncv == 2) {
-            d1 = x1 - s.hc[2 * (size_t)k + 1];
+            d1 = hill_diff(s, 1, x1 - s.hc[2 * (size_t)k + 1]);
             e += d1 * d1 * inv2v1;
         }
         const double gk = s.hw[k] * exp(-e);
@@ -61,14 +63,27 @@ __device__ __forceinline__ void bias(const Sys &s, Blk blk)
         am_last = (prev == (unsigned)blk.nb - 1u);
     }
     __syncthreads();
-    if (!am_last || threadIdx.x != 0) return;
+    if (!am_last) return;
     __threadfence();
+    // the last block adds the partials: thread t takes blocks t, t + blockDim,
+    // ... in order, then the same fixed tree as above
     double a = 0.0, b = 0.0, c = 0.0;
-    for (int q = 0; q < blk.nb; ++q) {
+    for (int q = threadIdx.x; q < blk.nb; q += blockDim.x) {
         a += __ldcg(part + 3 * q);
         b += __ldcg(part + 3 * q + 1);
         c += __ldcg(part + 3 * q + 2);
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+        c += __shfl_down_sync(0xffffffffu, c, o);
+    }
+    if (lane == 0) { sh[0][wid] = a; sh[1][wid] = b; sh[2][wid] = c; }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    a = b = c = 0.0;
+    for (int w = 0; w < kBlockBias / 32; ++w) { a += sh[0][w]; b += sh[1][w]; c += sh[2][w]; }
     if (s.ncv == 2) {
         double gv, gg0, gg1;
         grid_value(s, x0, x1, gv, gg0, gg1);

@@ -401,10 +401,36 @@ __global__ void __launch_bounds__(kBlockAtoms, 12) kb_cv_fwd(BatchView v)
     cv_fwd<real, true>(s, k);
 }
 
+// Per-thread running sum of a per-atom CV.  With FP32 records it is a
+// compensated pair (Knuth's TwoSum: s + c holds the sum with only c's own
+// rounding), so no FP64 instruction runs per atom (their pipe is narrow on
+// this part); it enters the FP64 block and grid sums once per thread.
+template <typename real>
+struct RunSum;
+template <>
+struct RunSum<float> {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float t = s + x;
+        const float bp = t - s;
+        c += (s - (t - bp)) + (x - bp);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+template <>
+struct RunSum<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+
 // a5: qbar_m(i), qbar6(i), s2.  Record b: b_m(i) = K_m qbar_m(i) / (N qbar6
 // (1 + W_i)) (slots 0..12) and beta_i = b(i).qbar(i) (slot 13).
 template <typename real>
-__device__ __forceinline__ void cv_avg_group(const Sys &s, const AtomLane a, double &cn_sum, double &q6_sum)
+__device__ __forceinline__ void cv_avg_group(const Sys &s, const AtomLane a, RunSum<real> &cn_sum,
+                                             RunSum<real> &q6_sum)
 {
     // lane l owns components 2l, 2l + 1 and walks every neighbour of the atom
     const real *q = R<real>(s.q);
@@ -446,8 +472,8 @@ __device__ __forceinline__ void cv_avg_group(const Sys &s, const AtomLane a, dou
         store_pair<real>(R<real>(s.b), a.i, a.l, b0, b1);
         if (a.l == 0) {
             R<real>(s.qb6)[a.i] = qb6;
-            cn_sum += (double)R<real>(s.cn)[a.i];
-            q6_sum += (double)qb6;
+            cn_sum.add(R<real>(s.cn)[a.i]);
+            q6_sum.add(qb6);
         }
     }
 }
@@ -493,21 +519,22 @@ __device__ void last_block_cv(const Sys &s, Blk k, double c, double q)
 template <typename real>
 __device__ __forceinline__ void cv_avg(const Sys &s, Blk k)
 {
-    double c = 0.0, q = 0.0;
+    RunSum<real> c, q;
     const int groups = group_grid(s.n);
     for (int it = 0, g; (g = work_item(k, it)) < groups; ++it) cv_avg_group<real>(s, atom_lane_at(s, g), c, q);
-    last_block_cv(s, k, c, q);
+    last_block_cv(s, k, c.value(), q.value());
 }
 
 // The CV sum when there is no Q6 pass (n_cv == 1): thread t of block b sums
-// the CN of atoms b kSumThreads + t, + blocks kSumThreads, ... in order.
+// the CN of atoms b kSumThreads + t, + blocks kSumThreads, ... in order
+// (a compensated FP32 pair with FP32 records).
 template <typename real>
 __device__ __forceinline__ void cv_sum(const Sys &s, Blk k)
 {
-    double c = 0.0;
+    RunSum<real> c;
     const real *cn = R<real>(s.cn);
-    for (int i = k.b * blockDim.x + threadIdx.x; i < s.n; i += k.nb * blockDim.x) c += (double)cn[i];
-    last_block_cv(s, k, c, 0.0);
+    for (int i = k.b * blockDim.x + threadIdx.x; i < s.n; i += k.nb * blockDim.x) c.add(cn[i]);
+    last_block_cv(s, k, c.value(), 0.0);
 }
 
 template <typename real>
@@ -750,9 +777,15 @@ __device__ __forceinline__ void pair_force(const Sys &s, int i, int k, real cn_f
 template <typename real>
 __device__ __forceinline__ void force_pairs(const Sys &s, Blk k)
 {
-    // the chain-rule factors of the two CVs, once per thread (FP64 is slow here)
-    const real cn_fac = (real)(s.scal[kDV0] * s.fscale * 2.0 / s.n);
-    const real V2 = s.ncv == 2 ? (real)(s.scal[kDV1] * s.fscale) : real(0);
+    // the chain-rule factors of the two CVs, once per block: an FP64 chain is
+    // long and its pipe narrow on this part, so no thread repeats it
+    __shared__ real fac[2];
+    if (threadIdx.x == 0) {
+        fac[0] = (real)(s.scal[kDV0] * s.fscale * 2.0 / s.n);
+        fac[1] = s.ncv == 2 ? (real)(s.scal[kDV1] * s.fscale) : real(0);
+    }
+    __syncthreads();
+    const real cn_fac = fac[0], V2 = fac[1];
     // each warp takes its own chunk of 32 atoms (a block of kBlockAtoms/32
     // warps is one work item, one per 128 atoms of the grid): no barrier
     constexpr int kWarps = kBlockAtoms / 32;

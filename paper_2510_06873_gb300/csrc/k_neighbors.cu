@@ -18,16 +18,6 @@ namespace metad {
 
 namespace {
 
-__device__ __forceinline__ float wrap_coord(float x, double L)
-{
-    double xd = (double)x;
-    if (xd >= 0.0 && xd < L) return x;
-    double w = xd - L * floor(xd / L);
-    float f = (float)w;
-    if ((double)f >= L) f = 0.0f;
-    return f;
-}
-
 __device__ __forceinline__ float4 load_wrapped(const Sys &s, int u, bool &bad)
 {
     float4 p = s.pos_in[u];
@@ -36,9 +26,9 @@ __device__ __forceinline__ float4 load_wrapped(const Sys &s, int u, bool &bad)
         p.x = p.y = p.z = 0.0f;
         return p;
     }
-    p.x = wrap_coord(p.x, s.L[0]);
-    p.y = wrap_coord(p.y, s.L[1]);
-    p.z = wrap_coord(p.z, s.L[2]);
+    p.x = wrap_coord(p.x, s.Lin[0], s.L[0]);
+    p.y = wrap_coord(p.y, s.Lin[1], s.L[1]);
+    p.z = wrap_coord(p.z, s.Lin[2], s.L[2]);
     return p;
 }
 
@@ -405,6 +395,15 @@ inline int capped(int blocks) { return blocks < kRebuildGrid ? (blocks < 1 ? 1 :
 
 int grid_blocks(const Sys &s, int kind, int persist_cap)
 {
+    if (s.kind != kKindCoord) {  // no neighbour list: a CV block, an atom grid, hills
+        switch (kind) {
+        case GK_ONE: return 1;
+        case GK_ATOM256: return (s.n + 255) / 256;
+        case GK_HILLS: return bias_blocks(s.K);
+        case GK_DEPOSIT: return s.deposit ? bias_blocks(s.K) : 0;
+        }
+        return 0;
+    }
     switch (kind) {
     case GK_ATOM256: return (s.n + 255) / 256;
     case GK_CELL1024_CAP: return capped((s.ncell + 1023) / 1024);

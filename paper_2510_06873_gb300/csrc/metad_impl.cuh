@@ -32,14 +32,19 @@ enum Scal : int {
     kNumScal = 16
 };
 
+// CV families (the metad_params.cv_kind values).
+enum CvKind : int { kKindCoord = 0, kKindTorsion = 1, kKindNearest = 2 };
+
 struct Sys {
     int n;          // atoms
     int ncv;        // 1 or 2
+    int kind;       // CvKind
     int cn_unlike;  // CN mask
     int max_nb;     // ELL capacity per atom
     // box
     double L[3];
     float Lhi[3], Llo[3], halfL[3];
+    float Lin[3];          // the largest float below L: x < L  <=>  x <= Lin
     // cells (edge >= rc, Morton-ranked)
     int nc[3];
     int ncell;
@@ -113,7 +118,40 @@ struct Sys {
     float *F_out;          // caller's forces [n][3]
     int accumulate;        // 1: F_out += force, 0: F_out = force
     double fscale;         // forces are scaled by this
+    // torsion and nearest-distance families (no neighbour list)
+    double period[2];      // 0, or the period of a periodic CV (2 pi for a torsion)
+    double inv_period[2];  // 1 / period (0 when not periodic)
+    const int *cv_atoms;   // torsion: [ncv][4]; nearest: [ncv] references, then n_cand candidates
+    const int *cand_slot;  // nearest: [n] position of each atom in the candidate group, or -1
+    int n_cand;
+    double sm_beta;        // nearest: 0 = exact, > 0 = soft minimum
+    double *gcv;           // [ncv][16] per-CV gradient terms of the last CV pass
 };
+
+// The difference s - c a hill sees along CV d: wrapped into [-P/2, P/2]
+// (nearest image) for a periodic CV, x - P rint(x / P), with x / P taken as
+// x * (1 / P) (no division per hill; the two can pick different images only
+// within an ulp of a half period, where both images are equally near).
+__device__ __forceinline__ double hill_diff(const Sys &s, int d, double x)
+{
+    const double P = s.period[d];
+    if (P > 0.0) x -= P * rint(x * s.inv_period[d]);
+    return x;
+}
+
+// A coordinate wrapped into [0, L): x - L floor(x / L) in FP64, rounded to
+// float32; a result that rounds up to L becomes 0.  The in-box test is the
+// FP32 comparison with Lin (exact: x < L iff x <= Lin for a float x), so a
+// wrapped input costs no FP64 instruction (their pipe is narrow here).
+__device__ __forceinline__ float wrap_coord(float x, float Lin, double L)
+{
+    if (x >= 0.0f && x <= Lin) return x;
+    double xd = (double)x;
+    double w = xd - L * floor(xd / L);
+    float f = (float)w;
+    if ((double)f >= L) f = 0.0f;
+    return f;
+}
 
 // Where a block works: block b of a grid of nb blocks of its system.  A
 // single-system launch is that grid; a batched launch concatenates the grids
@@ -198,6 +236,12 @@ void launch_nn_stats(const Sys &s, unsigned long long *sum, int *mx, cudaStream_
 void launch_export_pairs(const Sys &s, long long *pairs, int *count, cudaStream_t st);
 void launch_per_atom_out(const Sys &s, int fp64, double *out, cudaStream_t st);
 void set_ylm_constants(cudaStream_t st);
+// Torsion and nearest-distance families: the CV pass (one block per system)
+// and the force pass (one thread per atom).
+void launch_gcv_forward(const Sys &s, int fp64, cudaStream_t st);
+void launch_gcv_forces(const Sys &s, float *F, int accumulate, double scale, cudaStream_t st);
+void launch_batch_gcv(const BatchView &one, int one_total, int fp64, cudaStream_t st);
+void launch_batch_gcv_forces(const BatchView &atoms, int atom_total, cudaStream_t st);
 
 int bias_blocks(int K);
 

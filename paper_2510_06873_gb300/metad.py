@@ -18,6 +18,8 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libmetad.so")
 
 METAD_OK, METAD_ERR_INVALID, METAD_ERR_OOM, METAD_ERR_CUDA, METAD_ERR_CAPACITY, METAD_ERR_TIMEOUT, \
     METAD_ERR_STATE = range(7)
+METAD_CV_COORDINATION, METAD_CV_TORSION, METAD_CV_NEAREST = range(3)
+CV_KINDS = {"coordination": METAD_CV_COORDINATION, "torsion": METAD_CV_TORSION, "nearest": METAD_CV_NEAREST}
 
 
 class metad_params(ctypes.Structure):
@@ -30,6 +32,7 @@ class metad_params(ctypes.Structure):
         ("hill_capacity", ctypes.c_int32), ("grid_lo", ctypes.c_double * 2), ("grid_hi", ctypes.c_double * 2),
         ("precision", ctypes.c_int32), ("max_neighbors", ctypes.c_int32), ("device", ctypes.c_int32),
         ("step_graph", ctypes.c_int32), ("stream", ctypes.c_void_p), ("skin", ctypes.c_double),
+        ("cv_kind", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("softmin_beta", ctypes.c_double),
     ]
 
 
@@ -51,6 +54,7 @@ _SIGS = {
     "metad_bias_eval": (ctypes.c_int, [_P, _P, _P, _P]),
     "metad_bias_forces": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_double]),
     "metad_deposit_hill": (ctypes.c_int, [_P, _P, _P]),
+    "metad_set_cv_atoms": (ctypes.c_int, [_P, _P, ctypes.c_int32]),
     "metad_deposit_hills": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P]),
     "metad_load_hills": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32]),
     "metad_get_hills": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
@@ -187,6 +191,11 @@ def metad_bias_forces(ctx, forces, accumulate=False, scale=1.0):
            "metad_bias_forces")
 
 
+def metad_set_cv_atoms(ctx, atoms):
+    a = np.ascontiguousarray(np.asarray(atoms).ravel(), dtype=np.int32)
+    _check(ctx, lib().metad_set_cv_atoms(ctx, _hptr(a), int(a.size)), "metad_set_cv_atoms")
+
+
 def metad_deposit_hill(ctx, center=None, want_height=True):
     c = None if center is None else np.ascontiguousarray(np.atleast_1d(center), dtype=np.float64)
     h = ctypes.c_double(0.0)
@@ -313,8 +322,10 @@ def metad_hill_count(ctx) -> int:
 # --------------------------------------------------------------------- helper
 def params_for(n_atoms, box, n_cv=2, sigma=(0.05, 0.02), rc=3.5, r0=2.5, sw_n=6, sw_m=12, cn_unlike=True,
                w0=1.0, biasfactor=10.0, temperature=300.0, kB=0.0083144626, grid=None, hill_capacity=65536,
-               fp64=False, max_neighbors=64, device=0, stream=None, skin=1.0, step_graph=False) -> metad_params:
-    """metad_params from keyword values; grid = (n, lo, hi) or None."""
+               fp64=False, max_neighbors=64, device=0, stream=None, skin=1.0, step_graph=False,
+               cv_kind="coordination", softmin_beta=0.0) -> metad_params:
+    """metad_params from keyword values; grid = (n, lo, hi) or None; cv_kind
+    "coordination", "torsion" or "nearest" (or the METAD_CV_* value)."""
     p = metad_params_default()
     p.n_atoms = int(n_atoms)
     p.n_cv = int(n_cv)
@@ -338,6 +349,8 @@ def params_for(n_atoms, box, n_cv=2, sigma=(0.05, 0.02), rc=3.5, r0=2.5, sw_n=6,
     p.stream = stream
     p.skin = float(skin)
     p.step_graph = 1 if step_graph else 0
+    p.cv_kind = CV_KINDS[cv_kind] if isinstance(cv_kind, str) else int(cv_kind)
+    p.softmin_beta = float(softmin_beta)
     return p
 
 
@@ -376,6 +389,9 @@ class Metad:
 
     def bias_forces(self, forces, accumulate=False, scale=1.0):
         metad_bias_forces(self.ctx, forces, accumulate, scale)
+
+    def set_cv_atoms(self, atoms):
+        metad_set_cv_atoms(self.ctx, atoms)
 
     def deposit_hill(self, center=None, want_height=True):
         return metad_deposit_hill(self.ctx, center, want_height)

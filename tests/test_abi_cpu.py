@@ -41,12 +41,13 @@ def test_every_declared_symbol_is_exported(metad):
 
 def test_params_struct_round_trips(metad):
     p = metad.metad_params_default()
-    assert ctypes.sizeof(metad.metad_params) == 192
+    assert ctypes.sizeof(metad.metad_params) == 208
     assert (p.n_atoms, p.n_cv, p.sw_n, p.sw_m, p.stretch, p.cn_pairs) == (1, 2, 6, 12, 1, 1)
     assert (p.rc, p.r0, p.w0, p.biasfactor, p.temperature) == (3.5, 2.5, 1.0, 10.0, 300.0)
     assert list(p.sigma) == [0.05, 0.02] and p.kB == 0.0083144626
     assert p.hill_capacity == 65536 and p.max_neighbors == 64 and list(p.grid_n) == [200, 200]
     assert p.skin == 1.0
+    assert p.cv_kind == metad.METAD_CV_COORDINATION and p.softmin_beta == 0.0
 
 
 @pytest.mark.parametrize("field,value", [("n_atoms", 0), ("n_cv", 3), ("box", 6.9), ("sigma", 0.0),
@@ -113,3 +114,30 @@ def test_batch_entry_points_reject_null_without_a_gpu(metad):
     assert L.metad_batch_read(None, None, None) == metad.METAD_ERR_INVALID
     assert L.metad_batch_set_tile(None, 0) == metad.METAD_ERR_INVALID
     assert L.metad_batch_destroy(None) == metad.METAD_OK
+
+
+@pytest.mark.parametrize("kind,field,value", [("torsion", "n_atoms", 3), ("torsion", "grid_on", 1),
+                                              ("nearest", "softmin_beta", -1.0), ("nearest", "box", 0.0),
+                                              ("coordination", "cv_kind", 3)])
+def test_small_cv_families_reject_bad_params(metad, kind, field, value):
+    p = metad.params_for(22, [24.0, 24.0, 24.0], sigma=(0.35, 0.35), cv_kind=kind)
+    if field == "box":
+        p.box[1] = value
+    elif field == "grid_on":
+        p.grid_on, p.grid_n[0], p.grid_n[1], p.grid_hi[0], p.grid_hi[1] = 1, 10, 10, 1.0, 1.0
+    else:
+        setattr(p, field, value)
+    with pytest.raises(metad.MetadError) as e:
+        metad.metad_estimate_bytes(p)
+    assert e.value.status == metad.METAD_ERR_INVALID
+
+
+def test_small_cv_families_allocate_no_neighbour_state(metad):
+    # a box far below 2 rc is fine without a neighbour list
+    p = metad.params_for(22, [5.0, 5.0, 5.0], sigma=(0.35, 0.35), cv_kind="torsion", hill_capacity=1000)
+    b = metad.metad_estimate_bytes(p)
+    # hills (centres twice: live + staging), hill-block partials, scalars; no per-atom rows
+    assert b < 128 * 1024, b
+    big = metad.params_for(100_000, [50.0, 50.0, 50.0], sigma=(0.1,), n_cv=1, cv_kind="nearest",
+                           hill_capacity=1000)
+    assert metad.metad_estimate_bytes(big) < 100_000 * 16 + 64 * 1024
