@@ -61,6 +61,7 @@ def _L():
             "orc_deposit_sequence": (ctypes.c_int, [I32, I32, I32, P, P, P, P, D, D, P]),
             "orc_step": (ctypes.c_int, [I32, P, P, I32, P, P, P, P, P, P, P, P, ctypes.c_int]),
             "orc_max_threads": (ctypes.c_int, []),
+            "orc_step_box": (ctypes.c_int, [I32, P, P, I32, I32, P, P, P, P, P, P, P, P, ctypes.c_int]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -217,7 +218,7 @@ def bias(s, centres, heights, sigma, grid: HillGrid | None = None, period=None):
     sg = np.ascontiguousarray(sigma, dtype=np.float64)
     pr = _period(period, ncv)
     V = ctypes.c_double(0.0)
-    dV = np.zeros(2)
+    dV = np.zeros(5)
     _L().orc_bias(ncv, _ptr(s), c.shape[0], _ptr(c), _ptr(w), _ptr(sg), _ptr(pr), _grid_ref(grid), ctypes.byref(V),
                   _ptr(dV))
     return V.value, dV[:ncv].copy()
@@ -255,6 +256,30 @@ def step(pos4, p: Params, centres, heights, sigma, grid: HillGrid | None = None,
     if rc != 0:
         raise MemoryError("orc_step failed")
     return {"s": s[:ncv].copy(), "V": V.value, "dV": dV[:ncv].copy(), "F": F}
+
+
+def step_box(pos4, p: Params, centres, heights, sigma, lattice=True, nthreads=0):
+    """One frame with the box derivative a barostat needs (Section "B4-B1
+    phase transition in Large-scale systems": CN and the triaxial lattice
+    parameters as CVs under NPT).  With lattice, the CVs are (s1 [, s2],
+    L_x, L_y, L_z) and the hills D = n_cv + 3 dimensional.
+    -> dict(s, V, dV, F, box_grad) with box_grad = dV/dL_a at fixed
+    fractional coordinates (the explicit lattice term plus the bias virial
+    over L_a)."""
+    pos4 = _f32x4(pos4)
+    n = pos4.shape[0]
+    D = p.n_cv + (3 if lattice else 0)
+    c = np.ascontiguousarray(centres, dtype=np.float64).reshape(-1, D)
+    w = np.ascontiguousarray(heights, dtype=np.float64)
+    sg = np.ascontiguousarray(sigma, dtype=np.float64)
+    assert sg.size == D
+    s, dV, F, bg = np.zeros(5), np.zeros(5), np.zeros((n, 3)), np.zeros(3)
+    V = ctypes.c_double(0.0)
+    rc = _L().orc_step_box(n, _ptr(pos4), ctypes.byref(p), 1 if lattice else 0, c.shape[0], _ptr(c), _ptr(w),
+                           _ptr(sg), _ptr(s), ctypes.byref(V), _ptr(dV), _ptr(F), _ptr(bg), int(nthreads))
+    if rc != 0:
+        raise MemoryError("orc_step_box failed")
+    return {"s": s[:D].copy(), "V": V.value, "dV": dV[:D].copy(), "F": F, "box_grad": bg}
 
 
 # ------------------------------------------------------------------ free energy

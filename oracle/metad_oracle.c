@@ -36,6 +36,7 @@
 
 #define ORC_L 6
 #define ORC_NM (2 * ORC_L + 1)
+#define ORC_MAXCV 5 /* CN, Q6 and the three lattice parameters */
 
 typedef struct {
     double box[3];
@@ -552,7 +553,7 @@ int orc_cv(int32_t n, const float *pos4, const orc_params *p, double *s, double 
  * forward pass above, each step the adjoint of one forward line, taken in
  * reverse order.  Complex adjoints carry (dL/dRe, dL/dIm) as re + i im. */
 static int cv_reverse(const float *pos4, const orc_params *p, const cvstate *S, const double *dVds,
-                      double *F)
+                      double *F, double *vir)
 {
     const int32_t n = S->n;
     const int q6 = p->n_cv >= 2;
@@ -600,6 +601,10 @@ static int cv_reverse(const float *pos4, const orc_params *p, const cvstate *S, 
     }
     ylm_tab T;
     ylm_init(&T);
+    /* per-atom shares of the virial sum_{directed entries} (dL/dd)_c d_c, added
+     * in atom order afterwards */
+    double *vi = vir ? (double *)calloc(3 * (size_t)n + 1, sizeof(double)) : NULL;
+    if (vir && !vi) { free(Wbar); free(Abar); free(Qbar); return -1; }
     /* adjoint of one directed entry i -> j (d = r_j - r_i), returned as dL/dd */
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
@@ -632,9 +637,18 @@ static int cv_reverse(const float *pos4, const orc_params *p, const cvstate *S, 
                 for (int c = 0; c < 3; ++c) dd[c] += wbar * ds * d[c] / r;
                 /* d = r_b - r_a : dL/dr_a = -dd, dL/dr_b = +dd; keep atom i's share */
                 for (int c = 0; c < 3; ++c) g[c] += (side == 0 ? -dd[c] : dd[c]);
+                /* every directed entry is side 0 exactly once (from its own row) */
+                if (vi && side == 0)
+                    for (int c = 0; c < 3; ++c) vi[3 * i + c] += dd[c] * d[c];
             }
         }
         for (int c = 0; c < 3; ++c) F[3 * i + c] = -g[c];
+    }
+    if (vir) {
+        vir[0] = vir[1] = vir[2] = 0.0;
+        for (int64_t i = 0; i < n; ++i)
+            for (int c = 0; c < 3; ++c) vir[c] += vi[3 * i + c];
+        free(vi);
     }
     free(Wbar); free(Abar); free(Qbar);
     return 0;
@@ -647,7 +661,7 @@ int orc_forces(int32_t n, const float *pos4, const orc_params *p, const double *
     cvstate S;
     if (cv_forward(n, pos4, p, &S, nthreads) != 0) { cv_free(&S); return -1; }
     if (s) { s[0] = S.s[0]; if (p->n_cv >= 2) s[1] = S.s[1]; }
-    int rc = cv_reverse(pos4, p, &S, dVds, F);
+    int rc = cv_reverse(pos4, p, &S, dVds, F, NULL);
     cv_free(&S);
     return rc;
 }
@@ -741,7 +755,7 @@ static double hill_diff(double x, const double *period, int d)
 int orc_bias(int32_t ncv, const double *s, int32_t K, const double *c, const double *w, const double *sigma,
              const double *period, const orc_grid *G, double *V, double *dV)
 {
-    double v = 0.0, g[2] = {0.0, 0.0};
+    double v = 0.0, g[ORC_MAXCV] = {0.0, 0.0, 0.0, 0.0, 0.0};
     if (G && G->data && ncv == 2) grid_eval(G, s, &v, g);
     for (int32_t k = 0; k < K; ++k) {
         double e = 0.0;
@@ -768,7 +782,7 @@ int orc_deposit_sequence(int32_t ncv, int32_t K, int32_t k_first, const double *
                          const double *sigma, const double *period, double w0, double kbdt, const orc_grid *G)
 {
     for (int32_t k = k_first; k < K; ++k) {
-        double V, dV[2];
+        double V, dV[ORC_MAXCV];
         orc_bias(ncv, c + (int64_t)ncv * k, k, c, w, sigma, period, G, &V, dV);
         w[k] = w0 * exp(-V / kbdt);
     }
@@ -785,7 +799,40 @@ int orc_step(int32_t n, const float *pos4, const orc_params *p, int32_t K, const
     s[0] = S.s[0];
     if (p->n_cv >= 2) s[1] = S.s[1];
     orc_bias(p->n_cv, S.s, K, c, w, sigma, NULL, G, V, dV);
-    int rc = cv_reverse(pos4, p, &S, dV, F);
+    int rc = cv_reverse(pos4, p, &S, dV, F, NULL);
     cv_free(&S);
+    return rc;
+}
+
+/* ------------------------------------------------------ lattice parameters
+ * The GaN runs bias the coordination number together with the triaxial
+ * lattice parameters under NPT (Section "B4-B1 phase transition in
+ * Large-scale systems").  With lattice = 1 the CVs are
+ *     s = (s1 [, s2], L_x, L_y, L_z)   (D = n_cv + 3 dimensions)
+ * and hills are D-dimensional.  A barostat needs the derivative of the bias
+ * with respect to each box length at fixed fractional coordinates (positions
+ * scale with the box):
+ *     dV/dL_a = dV/ds_{L_a} [lattice] + (1/L_a) sum_pairs (dV/dd_ij)_a (d_ij)_a
+ * since every per-atom CV depends on the positions only through the pair
+ * displacements d_ij, and d_ij,a = L_a (f_j - f_i - n_ij)_a under scaling.
+ * The pair sum (the bias virial) is accumulated by the reverse pass.
+ * box_grad receives dV/dL (the explicit term only with lattice = 1). */
+int orc_step_box(int32_t n, const float *pos4, const orc_params *p, int32_t lattice, int32_t K, const double *c,
+                 const double *w, const double *sigma, double *s, double *V, double *dV, double *F,
+                 double *box_grad, int nthreads)
+{
+    cvstate S;
+    if (cv_forward(n, pos4, p, &S, nthreads) != 0) { cv_free(&S); return -1; }
+    const int D = p->n_cv + (lattice ? 3 : 0);
+    double sv[ORC_MAXCV];
+    for (int d = 0; d < p->n_cv; ++d) sv[d] = S.s[d];
+    if (lattice)
+        for (int a = 0; a < 3; ++a) sv[p->n_cv + a] = p->box[a];
+    for (int d = 0; d < D; ++d) s[d] = sv[d];
+    orc_bias(D, sv, K, c, w, sigma, NULL, NULL, V, dV);
+    double vir[3];
+    int rc = cv_reverse(pos4, p, &S, dV, F, vir);
+    cv_free(&S);
+    for (int a = 0; a < 3; ++a) box_grad[a] = (lattice ? dV[p->n_cv + a] : 0.0) + vir[a] / p->box[a];
     return rc;
 }

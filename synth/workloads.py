@@ -318,3 +318,19 @@ def served_trace(cfg: int = 5, n_walkers: int = 32, n_requests: int = 2000, rate
     arrivals = np.cumsum(gaps)
     walker = g.integers(0, n_walkers, n_requests)
     return n, arrivals, walker
+
+
+def npt_frame(system: System, frame: int, strain_sigma: float = 1e-3, sigma: float = 0.05):
+    """A frame of a triaxial NPT run: each box length scaled by 1 + e_a,
+    e_a ~ N(0, strain_sigma^2) independently per axis and frame, positions
+    scaled with it (fixed fractional coordinates) plus N(0, sigma^2) noise,
+    wrapped into the new box.  Returns (float32 [N, 4] frame, float64 [3] box)."""
+    g = rng(system.cfg, system.sys, 5, frame)
+    e = g.normal(0.0, strain_sigma, size=3)
+    box = system.box * (1.0 + e)
+    eps = g.normal(0.0, sigma, size=(system.n, 3))
+    xyz = wrap_to_box(system.base[:, :3].astype(np.float64) * (1.0 + e) + eps, box)
+    out = np.empty_like(system.base)
+    out[:, :3] = xyz
+    out[:, 3] = system.base[:, 3]
+    return out, box
