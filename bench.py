@@ -69,6 +69,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-system batched comparison")
     ap.add_argument("--no-served", action="store_true", help="skip the served (continuous batching) trace")
     ap.add_argument("--no-small", action="store_true", help="skip the torsion / nearest-distance walker forms")
+    ap.add_argument("--no-npt", action="store_true", help="skip the NPT (lattice CVs, box gradient) form")
     ap.add_argument("--batched-steps", type=int, default=10)
     return ap.parse_args()
 
@@ -419,6 +420,8 @@ def run_metad(args):
             forms["served"] = run_served(args, dev, stream, metad)
         if not args.no_small:
             forms["small_cvs"] = run_small_cvs(args, dev, stream, metad)
+        if not args.no_npt:
+            forms["npt"] = run_npt(args, dev, stream, metad, n)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": max(3, args.warmup), "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
@@ -611,6 +614,55 @@ def run_small_cvs(args, dev, stream, metad):
         for c in ctxs:
             c.close()
     return out
+
+
+def run_npt(args, dev, stream, metad, n_atoms):
+    """The same system under triaxial NPT with the lattice-parameter CVs of
+    the GaN runs: CVs (s1, s2, L_x, L_y, L_z), 5-D well-tempered hills
+    (20,000, deposited by the CUDA path), a new box every step
+    (metad_set_box: the neighbour structures are rebuilt every step) and the
+    box gradient (bias virial) beside the forces.  Timed with CUDA events
+    like the main step."""
+    import torch
+    system = make_system(n_atoms)
+    mp = synth.method_params(3)
+    nfr, hills = 4, 20000
+    frames = [synth.npt_frame(system, f, strain_sigma=1e-3) for f in range(nfr)]
+    pos = [torch.from_numpy(fr).to(dev) for fr, _ in frames]
+    F = torch.zeros((system.n, 3), dtype=torch.float32, device=dev)
+    sig_l = (0.05, 0.05, 0.05)
+    p = metad.params_for(system.n, system.box, n_cv=2, sigma=mp.sigma, lattice_cvs=True, sigma_lattice=sig_l,
+                         hill_capacity=hills + 64, stream=stream.cuda_stream)
+    ctx = metad.Metad(p)
+    ctx.set_box(frames[0][1])
+    ctx.build_neighbors(pos[0])
+    s_ref = ctx.cv_forward()
+    cen = synth.hill_centres(3, system.sys, s_ref, tuple(mp.sigma) + sig_l, hills, half_width_sigmas=4.0)
+    ctx.deposit_hills(cen, want_heights=False)
+
+    def one(t):
+        ctx.set_box(frames[t % nfr][1])
+        ctx.step(pos[t % nfr], F)
+
+    for t in range(3):
+        one(t)
+    torch.cuda.synchronize(dev)
+    steps = max(1, args.batched_steps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for t in range(steps):
+        one(t)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    bg = ctx.box_gradient()
+    reb = ctx.rebuild_count()
+    ctx.close()
+    return {"atoms": system.n, "cvs": "s1, s2, L_x, L_y, L_z", "hills": hills, "steps": steps,
+            "ms_per_step": ms, "atom_steps_per_s": system.n / (ms / 1e3),
+            "box_gradient_last": [float(x) for x in bg], "rebuilds": int(reb),
+            "note": "a new box every step (strain N(0, 1e-3) per axis): every step rebuilds the cell order "
+                    "and Verlet rows; the box gradient is the lattice term plus the bias virial"}
 
 
 def run_served(args, dev, stream, metad):

@@ -100,6 +100,17 @@ typedef struct {
     double softmin_beta;    /* METAD_CV_NEAREST: 0 (default) = the exact nearest
                                distance; > 0 = its soft minimum with this beta
                                (1/Angstrom), see metad_set_cv_atoms */
+    int32_t lattice_cvs;    /* 1: the three box lengths are CVs too, after the
+                               per-atom ones: s = (s1 [, s2], L_x, L_y, L_z),
+                               D = n_cv + 3 CVs, D-dimensional hills (the GaN
+                               NPT runs bias the coordination number with the
+                               triaxial lattice parameters, Section "B4-B1
+                               phase transition in Large-scale systems").
+                               Coordination family only; no grid.  Implies
+                               virial. */
+    int32_t virial;         /* 1: bias_forces also sums the bias virial and the
+                               box gradient (metad_box_gradient) */
+    double sigma_lattice[3];/* hill widths of the lattice CVs, Angstrom */
 } metad_params;
 
 /* CV families (metad_params.cv_kind).
@@ -178,6 +189,29 @@ metad_status metad_bias_forces(metad_ctx *ctx, float *forces_dev, int32_t accumu
  * atom repeated within a quadruplet or in the candidate group, a reference
  * atom that is also a candidate, a context of the coordination family). */
 metad_status metad_set_cv_atoms(metad_ctx *ctx, const int32_t *atoms_host, int32_t count);
+
+/* Number of CVs D the hills see: n_cv, plus 3 with lattice_cvs.  Every CV
+ * vector a call takes or returns (cv_host, s_host, dVds_host, centres) has
+ * D entries per point; hill centres are [K][D]. */
+
+/* NPT: the orthorhombic box of the next steps (host double[3]; each length
+ * >= 2 rc, > 0 for the torsion and nearest-distance families).  Positions
+ * passed afterwards must lie in (or are wrapped into) the new box.  The cell
+ * grid follows the box (never more cells than at creation) and every
+ * neighbour structure is rebuilt at the next step; captured step graphs are
+ * dropped.  Asynchronous unless the number of cells changes.
+ * Errors: METAD_ERR_INVALID (NULL, a length out of range). */
+metad_status metad_set_box(metad_ctx *ctx, const double *box_host);
+
+/* The derivative a barostat needs, from the last bias_forces: for each box
+ * length, at fixed fractional coordinates (positions scaling with the box),
+ *     dV/dL_a = dV/ds_{L_a} [lattice CVs] + (1/L_a) sum_pairs (dV/dd_ij)_a (d_ij)_a
+ * (every per-atom CV depends on the positions only through the pair
+ * displacements d_ij, which scale with the box), times the scale that
+ * bias_forces was given.  dVdL_host: double[3].  Synchronises.
+ * Errors: METAD_ERR_INVALID (NULL, a context without virial or lattice_cvs),
+ * METAD_ERR_STATE (no bias_forces since creation). */
+metad_status metad_box_gradient(metad_ctx *ctx, double *dVdL_host);
 
 /* Step a9: deposit one hill at c (center_host double[n_cv], or NULL for the
  * last CVs) with the well-tempered height

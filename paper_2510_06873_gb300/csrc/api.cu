@@ -24,6 +24,9 @@ struct metad_ctx {
     int K = 0;
     bool have_nbr = false, have_cv = false, have_bias = false;
     bool atoms_set = false;       // torsion / nearest-distance: metad_set_cv_atoms done
+    bool forces_done = false;     // a bias_forces ran since the last box or CV change
+    int nc_created[3] = {1, 1, 1};  // cells per axis at creation (the allocation)
+    int ncell_alloc = 1;
     bool filter_pending = false;  // exact rows not yet compacted from the Verlet rows
     bool failed = false;
     std::string last_error;
@@ -240,12 +243,27 @@ metad_status validate(const metad_params *p, std::string &why)
             }
     }
     if (p->precision != 0 && p->precision != 1) { why = "precision must be 0 or 1"; return METAD_ERR_INVALID; }
+    if (p->lattice_cvs != 0 && p->lattice_cvs != 1) { why = "lattice_cvs must be 0 or 1"; return METAD_ERR_INVALID; }
+    if (p->virial != 0 && p->virial != 1) { why = "virial must be 0 or 1"; return METAD_ERR_INVALID; }
+    if ((p->lattice_cvs || p->virial) && p->cv_kind != METAD_CV_COORDINATION) {
+        why = "lattice CVs and the virial need the coordination family";
+        return METAD_ERR_INVALID;
+    }
+    if (p->lattice_cvs) {
+        if (p->grid_on) { why = "no grid with lattice CVs"; return METAD_ERR_INVALID; }
+        for (int a = 0; a < 3; ++a)
+            if (!(p->sigma_lattice[a] > 0)) { why = "sigma_lattice must be positive"; return METAD_ERR_INVALID; }
+    }
     if (p->max_neighbors < 0) { why = "max_neighbors < 0"; return METAD_ERR_INVALID; }
     if (!(p->skin >= 0.0) || !std::isfinite(p->skin)) { why = "skin must be >= 0"; return METAD_ERR_INVALID; }
     return METAD_OK;
 }
 
 constexpr double kTwoPi = 6.283185307179586476925286766559;  // the period of a torsion angle
+
+// CVs the hills see: the per-atom CVs, then the three box lengths when they
+// are CVs too.
+int cv_dims(const metad_params &p) { return p.n_cv + (p.lattice_cvs ? 3 : 0); }
 
 // Host-side geometry and constants of a context's system (no allocation).
 metad_status setup_system(metad_ctx *c)
@@ -309,8 +327,15 @@ metad_status setup_system(metad_ctx *c)
     split(y.a_d, y.a_hi, y.a_lo);
     split(y.k_d, y.k_hi, y.k_lo);
     y.hill_cap = c->p.hill_capacity;
+    y.lattice = c->p.lattice_cvs;
+    y.virial = c->p.virial || c->p.lattice_cvs;
+    y.D = cv_dims(c->p);
+    y.hstride = std::max(y.D, 2);
+    for (int d = 0; d < metad::kMaxCv; ++d) y.sigma[d] = 1.0;
     y.sigma[0] = c->p.sigma[0];
-    y.sigma[1] = c->p.n_cv == 2 ? c->p.sigma[1] : 1.0;
+    if (c->p.n_cv == 2) y.sigma[1] = c->p.sigma[1];
+    if (c->p.lattice_cvs)
+        for (int a = 0; a < 3; ++a) y.sigma[c->p.n_cv + a] = c->p.sigma_lattice[a];
     y.w0 = c->p.w0;
     y.kbdt = c->p.kB * c->p.temperature * (c->p.biasfactor - 1.0);
     y.grid_on = c->p.grid_on;
@@ -323,8 +348,48 @@ metad_status setup_system(metad_ctx *c)
     // one FP64 partial per block of the per-atom kernels (slot 0: CN, 1: Q6),
     // three per block of the hill kernel (slot 2), the neighbour statistics
     // (slot 3)
-    y.part_stride = std::max(metad::group_grid(n), metad::kMaxBiasBlocks * 3);
+    y.part_stride = std::max(metad::group_grid(n), metad::kMaxBiasBlocks * (metad::kMaxCv + 1));
     return METAD_OK;
+}
+
+// Morton ranks of the cells (sort cell coordinates by interleaved bits) and
+// their inverse, uploaded to the rank tables (sized for the cells at
+// creation; a box change never asks for more).
+metad_status upload_cell_ranks(metad_ctx *c)
+{
+    const Sys &y = c->sys;
+    std::vector<std::pair<uint32_t, int>> key(y.ncell);
+    for (int z = 0; z < y.nc[2]; ++z)
+        for (int yy = 0; yy < y.nc[1]; ++yy)
+            for (int x = 0; x < y.nc[0]; ++x) {
+                int id = (z * y.nc[1] + yy) * y.nc[0] + x;
+                key[id] = {spread3(x) | (spread3(yy) << 1) | (spread3(z) << 2), id};
+            }
+    std::sort(key.begin(), key.end());
+    std::vector<int> r(y.ncell), xr(y.ncell);
+    for (int k = 0; k < y.ncell; ++k) {
+        int id = key[k].second;
+        int x = id % y.nc[0], yy = (id / y.nc[0]) % y.nc[1], z = id / (y.nc[0] * y.nc[1]);
+        r[id] = k;
+        xr[k] = x | (yy << 10) | (z << 20);
+    }
+    metad_status s;
+    if ((s = cuda_check(c, cudaMemcpy(const_cast<int *>(y.rank_of_xyz), r.data(), sizeof(int) * y.ncell,
+                                      cudaMemcpyHostToDevice), "rank upload")) ||
+        (s = cuda_check(c, cudaMemcpy(const_cast<int *>(y.xyz_of_rank), xr.data(), sizeof(int) * y.ncell,
+                                      cudaMemcpyHostToDevice), "rank upload")))
+        return s;
+    return METAD_OK;
+}
+
+// Caller centres [K][D] -> the device layout [K][hstride] (zero padded).
+std::vector<double> pack_centres(const metad_ctx *c, const double *centers, int K)
+{
+    const int hs = c->sys.hstride, D = c->sys.D;
+    std::vector<double> out((size_t)hs * K, 0.0);
+    for (int k = 0; k < K; ++k)
+        for (int d = 0; d < D; ++d) out[(size_t)hs * k + d] = centers[(size_t)D * k + d];
+    return out;
 }
 
 struct Buffers {
@@ -348,8 +413,9 @@ metad_status state_buffers(metad_ctx *c, Buffers &b, Alloc &&alloc)
         if ((s = alloc(&atoms, 4 * (size_t)2 + n)) || (s = alloc(&slot, n)) || (s = alloc(&y.gcv, 32)) ||
             (s = alloc(&y.part, (size_t)y.part_stride * 4)) || (s = alloc(&y.ticket, 8)) ||
             (s = alloc(&y.scal, metad::kNumScal)) || (s = alloc(&y.err, 1)) ||
-            (s = alloc(&y.hc, 2 * (size_t)y.hill_cap + 2)) || (s = alloc(&y.hw, (size_t)y.hill_cap + 1)) ||
-            (s = alloc(&c->stage, 2 * (size_t)y.hill_cap + 2)) ||
+            (s = alloc(&y.hc, (size_t)y.hstride * ((size_t)y.hill_cap + 1))) ||
+            (s = alloc(&y.hw, (size_t)y.hill_cap + 1)) ||
+            (s = alloc(&c->stage, (size_t)y.hstride * ((size_t)y.hill_cap + 1))) ||
             (s = alloc(&y.grid, (size_t)y.gn[0] * y.gn[1] * 4)))
             return s;
         y.cv_atoms = atoms;
@@ -368,8 +434,10 @@ metad_status state_buffers(metad_ctx *c, Buffers &b, Alloc &&alloc)
         (s = alloc(&y.rebuilds, 1)) || (s = alloc(&b.rb, rs * (nq * 3 + (size_t)n * 4 + 64))) ||
         (s = alloc(&y.part, (size_t)y.part_stride * 4)) || (s = alloc(&y.ticket, 8)) ||
         (s = alloc(&y.scal, metad::kNumScal)) || (s = alloc(&y.err, 1)) ||
-        (s = alloc(&y.hc, 2 * (size_t)y.hill_cap + 2)) || (s = alloc(&y.hw, (size_t)y.hill_cap + 1)) ||
-        (s = alloc(&c->stage, 2 * (size_t)y.hill_cap + 2)) || (s = alloc(&y.grid, (size_t)y.gn[0] * y.gn[1] * 4)))
+        (s = alloc(&y.hc, (size_t)y.hstride * ((size_t)y.hill_cap + 1))) ||
+        (s = alloc(&y.hw, (size_t)y.hill_cap + 1)) ||
+        (s = alloc(&c->stage, (size_t)y.hstride * ((size_t)y.hill_cap + 1))) ||
+        (s = alloc(&y.grid, (size_t)y.gn[0] * y.gn[1] * 4)))
         return s;
     return METAD_OK;
 }
@@ -425,6 +493,7 @@ void metad_params_default(metad_params *p)
     p->cn_pairs = 1;
     p->sigma[0] = 0.05;
     p->sigma[1] = 0.02;
+    for (int a = 0; a < 3; ++a) p->sigma_lattice[a] = 0.1;
     p->w0 = 1.0;
     p->biasfactor = 10.0;
     p->temperature = 300.0;
@@ -544,30 +613,11 @@ metad_status metad_create(const metad_params *p, metad_ctx **out)
     y.geo = bf.geob;
     y.rank_of_xyz = rank_xyz;
     y.xyz_of_rank = xyz_rank;
-    // Morton ranks of the cells: sort cell coordinates by interleaved bits
-    {
-        std::vector<std::pair<uint32_t, int>> key(y.ncell);
-        for (int z = 0; z < y.nc[2]; ++z)
-            for (int yy = 0; yy < y.nc[1]; ++yy)
-                for (int x = 0; x < y.nc[0]; ++x) {
-                    int id = (z * y.nc[1] + yy) * y.nc[0] + x;
-                    key[id] = {spread3(x) | (spread3(yy) << 1) | (spread3(z) << 2), id};
-                }
-        std::sort(key.begin(), key.end());
-        std::vector<int> r(y.ncell), xr(y.ncell);
-        for (int k = 0; k < y.ncell; ++k) {
-            int id = key[k].second;
-            int x = id % y.nc[0], yy = (id / y.nc[0]) % y.nc[1], z = id / (y.nc[0] * y.nc[1]);
-            r[id] = k;
-            xr[k] = x | (yy << 10) | (z << 20);
-        }
-        if ((s = cuda_check(c, cudaMemcpy(rank_xyz, r.data(), sizeof(int) * y.ncell, cudaMemcpyHostToDevice),
-                            "rank upload")) ||
-            (s = cuda_check(c, cudaMemcpy(xyz_rank, xr.data(), sizeof(int) * y.ncell, cudaMemcpyHostToDevice),
-                            "rank upload"))) {
-            metad_destroy(c);
-            return s;
-        }
+    for (int a = 0; a < 3; ++a) c->nc_created[a] = y.nc[a];
+    c->ncell_alloc = y.ncell;
+    if ((s = upload_cell_ranks(c))) {
+        metad_destroy(c);
+        return s;
     }
     if (cudaMallocHost(&c->host_pinned, 64 * sizeof(double)) != cudaSuccess ||
         cudaMallocHost(&c->err_pinned, sizeof(int)) != cudaSuccess) {
@@ -664,11 +714,11 @@ metad_status metad_cv_forward(metad_ctx *c, double *cv_host, double *per_atom_de
     c->have_cv = true;
     c->have_bias = false;
     if (cv_host) {
-        s = cuda_check(c, cudaMemcpyAsync(c->host_pinned, c->sys.scal + metad::kS0, 2 * sizeof(double),
+        s = cuda_check(c, cudaMemcpyAsync(c->host_pinned, c->sys.scal + metad::kS0, metad::kMaxCv * sizeof(double),
                                           cudaMemcpyDeviceToHost, c->stream), "cv copy");
         if (s) return s;
         if ((s = sync_and_check(c))) return s;
-        for (int d = 0; d < c->p.n_cv; ++d) cv_host[d] = c->host_pinned[d];
+        for (int d = 0; d < c->sys.D; ++d) cv_host[d] = c->host_pinned[d];
     }
     return METAD_OK;
 }
@@ -679,7 +729,8 @@ metad_status metad_bias_eval(metad_ctx *c, const double *s_host, double *V_host,
     if (s) return s;
     const double *x = c->sys.scal + metad::kS0;
     if (s_host) {
-        double tmp[2] = {s_host[0], c->p.n_cv == 2 ? s_host[1] : 0.0};
+        double tmp[metad::kMaxCv] = {};
+        for (int d = 0; d < c->sys.D; ++d) tmp[d] = s_host[d];
         // a user-given CV point: evaluate into the deposit slots so the step's
         // own CVs stay untouched
         s = cuda_check(c, cudaMemcpyAsync(c->sys.scal + metad::kDepC0, tmp, sizeof(tmp), cudaMemcpyHostToDevice,
@@ -697,13 +748,13 @@ metad_status metad_bias_eval(metad_ctx *c, const double *s_host, double *V_host,
     if (s) return s;
     c->have_bias = !s_host ? true : false;
     if (V_host || dVds_host) {
-        s = cuda_check(c, cudaMemcpyAsync(c->host_pinned, c->sys.scal + metad::kV, 3 * sizeof(double),
+        s = cuda_check(c, cudaMemcpyAsync(c->host_pinned, c->sys.scal + metad::kV, (1 + metad::kMaxCv) * sizeof(double),
                                           cudaMemcpyDeviceToHost, c->stream), "bias copy");
         if (s) return s;
         if ((s = sync_and_check(c))) return s;
         if (V_host) *V_host = c->host_pinned[0];
         if (dVds_host)
-            for (int d = 0; d < c->p.n_cv; ++d) dVds_host[d] = c->host_pinned[1 + d];
+            for (int d = 0; d < c->sys.D; ++d) dVds_host[d] = c->host_pinned[1 + d];
     }
     return METAD_OK;
 }
@@ -721,6 +772,7 @@ metad_status metad_bias_forces(metad_ctx *c, float *forces_dev, int32_t accumula
         }
         return launched(c, "bias_forces");
     }
+    c->forces_done = true;
     if (c->p.n_cv == 2) {
         StageScope t(c, ST_ADJ, 1);
         metad::launch_adjoint(c->sys, c->fp64, c->stream);
@@ -781,6 +833,71 @@ metad_status metad_set_cv_atoms(metad_ctx *c, const int32_t *atoms_host, int32_t
     return METAD_OK;
 }
 
+metad_status metad_set_box(metad_ctx *c, const double *box_host)
+{
+    metad_status s = check_usable(c);
+    if (s) return s;
+    if (!box_host) return fail(c, METAD_ERR_INVALID, "box is NULL");
+    if (c->p.cv_kind != METAD_CV_COORDINATION) {
+        for (int a = 0; a < 3; ++a)
+            if (!(box_host[a] > 0.0) || !std::isfinite(box_host[a])) return fail(c, METAD_ERR_INVALID, "box");
+    } else {
+        for (int a = 0; a < 3; ++a)
+            if (!(box_host[a] >= 2.0 * c->p.rc) || !std::isfinite(box_host[a]))
+                return fail(c, METAD_ERR_INVALID, "every box length must be >= 2 rc");
+    }
+    Sys &y = c->sys;
+    const int nc_before[3] = {y.nc[0], y.nc[1], y.nc[2]};
+    const metad_params old = c->p;
+    for (int a = 0; a < 3; ++a) c->p.box[a] = box_host[a];
+    if ((s = setup_system(c))) {
+        c->p = old;
+        setup_system(c);
+        return fail(c, s, "box");
+    }
+    if (c->p.cv_kind == METAD_CV_COORDINATION) {
+        // cells no smaller than rc + skin, no more than allocated
+        if (y.ncell > c->ncell_alloc) {
+            for (int a = 0; a < 3; ++a) y.nc[a] = std::min(y.nc[a], c->nc_created[a]);
+            y.ncell = y.nc[0] * y.nc[1] * y.nc[2];
+            for (int a = 0; a < 3; ++a) y.inv_h[a] = (float)(y.nc[a] / c->p.box[a]);
+        }
+        if (y.nc[0] != nc_before[0] || y.nc[1] != nc_before[1] || y.nc[2] != nc_before[2]) {
+            // new cell ranks: wait for steps in flight that read the old ones
+            if ((s = cuda_check(c, cudaStreamSynchronize(c->stream), "set_box")) || (s = upload_cell_ranks(c)))
+                return s;
+        }
+        // every neighbour structure is rebuilt at the next step
+        const int one = 1;
+        if ((s = cuda_check(c, cudaMemcpyAsync(y.flag, &one, sizeof(int), cudaMemcpyHostToDevice, c->stream),
+                            "rebuild flag")))
+            return s;
+        c->have_nbr = false;
+    }
+    c->have_cv = c->have_bias = false;
+    for (auto &g : c->graphs)  // captured steps hold the old box
+        if (g.exec) {
+            cudaGraphExecDestroy(g.exec);
+            g.exec = nullptr;
+        }
+    return METAD_OK;
+}
+
+metad_status metad_box_gradient(metad_ctx *c, double *dVdL_host)
+{
+    metad_status s = check_usable(c);
+    if (s) return s;
+    if (!dVdL_host) return fail(c, METAD_ERR_INVALID, "output is NULL");
+    if (!c->sys.virial) return fail(c, METAD_ERR_INVALID, "needs params.virial or params.lattice_cvs");
+    if (!c->forces_done) return fail(c, METAD_ERR_STATE, "box_gradient before bias_forces");
+    if ((s = cuda_check(c, cudaMemcpyAsync(c->host_pinned, c->sys.scal + metad::kBoxG0, 3 * sizeof(double),
+                                           cudaMemcpyDeviceToHost, c->stream), "box gradient copy")) ||
+        (s = sync_and_check(c)))
+        return s;
+    for (int a = 0; a < 3; ++a) dVdL_host[a] = c->host_pinned[a];
+    return METAD_OK;
+}
+
 metad_status metad_deposit_hill(metad_ctx *c, const double *center_host, double *height_host)
 {
     metad_status s = check_usable(c);
@@ -788,7 +905,8 @@ metad_status metad_deposit_hill(metad_ctx *c, const double *center_host, double 
     if (c->K >= c->p.hill_capacity) return fail(c, METAD_ERR_CAPACITY, "hill list full");
     const double *x = c->sys.scal + metad::kS0;
     if (center_host) {
-        double tmp[2] = {center_host[0], c->p.n_cv == 2 ? center_host[1] : 0.0};
+        double tmp[metad::kMaxCv] = {};
+        for (int d = 0; d < c->sys.D; ++d) tmp[d] = center_host[d];
         s = cuda_check(c, cudaMemcpyAsync(c->sys.scal + metad::kDepC0, tmp, sizeof(tmp), cudaMemcpyHostToDevice,
                                           c->stream), "centre upload");
         if (s) return s;
@@ -820,18 +938,15 @@ metad_status metad_deposit_hills(metad_ctx *c, const double *centers_host, int32
     if (K < 0 || (K > 0 && !centers_host)) return fail(c, METAD_ERR_INVALID, "bad hill arguments");
     if ((int64_t)c->K + K > c->p.hill_capacity) return fail(c, METAD_ERR_CAPACITY, "hill list full");
     if (K == 0) return METAD_OK;
-    std::vector<double> tmp(2 * (size_t)K);
-    for (int k = 0; k < K; ++k) {
-        tmp[2 * k] = centers_host[(size_t)c->p.n_cv * k];
-        tmp[2 * k + 1] = c->p.n_cv == 2 ? centers_host[(size_t)c->p.n_cv * k + 1] : 0.0;
-    }
+    const std::vector<double> tmp = pack_centres(c, centers_host, K);
     s = cuda_check(c, cudaMemcpyAsync(c->stage, tmp.data(), sizeof(double) * tmp.size(), cudaMemcpyHostToDevice,
                                       c->stream), "centre upload");
     if (s) return s;
     const int k0 = c->K;
     for (int k = 0; k < K; ++k) {
         StageScope t(c, ST_DEPOSIT, 1);
-        metad::launch_bias(c->sys, c->K, c->stage + 2 * (size_t)k, c->sys.scal + metad::kDepV, 1, c->stream);
+        metad::launch_bias(c->sys, c->K, c->stage + (size_t)c->sys.hstride * k, c->sys.scal + metad::kDepV, 1,
+                           c->stream);
         c->K += 1;
     }
     s = launched(c, "deposit_hills");
@@ -851,14 +966,10 @@ metad_status metad_load_hills(metad_ctx *c, const double *centers_host, const do
     if (s) return s;
     if (K < 0 || (K > 0 && (!centers_host || !heights_host))) return fail(c, METAD_ERR_INVALID, "bad hills");
     if (K > c->p.hill_capacity) return fail(c, METAD_ERR_CAPACITY, "hill list full");
-    std::vector<double> tmp(2 * (size_t)K + 2);
-    for (int k = 0; k < K; ++k) {
-        tmp[2 * k] = centers_host[(size_t)c->p.n_cv * k];
-        tmp[2 * k + 1] = c->p.n_cv == 2 ? centers_host[(size_t)c->p.n_cv * k + 1] : 0.0;
-    }
+    const std::vector<double> tmp = pack_centres(c, centers_host, K);
     if (K > 0) {
-        if ((s = cuda_check(c, cudaMemcpyAsync(c->sys.hc, tmp.data(), sizeof(double) * 2 * K, cudaMemcpyHostToDevice,
-                                               c->stream), "hill upload")))
+        if ((s = cuda_check(c, cudaMemcpyAsync(c->sys.hc, tmp.data(), sizeof(double) * tmp.size(),
+                                               cudaMemcpyHostToDevice, c->stream), "hill upload")))
             return s;
         if ((s = cuda_check(c, cudaMemcpyAsync(c->sys.hw, heights_host, sizeof(double) * K, cudaMemcpyHostToDevice,
                                                c->stream), "hill upload")))
@@ -875,9 +986,10 @@ metad_status metad_get_hills(metad_ctx *c, double *centers_host, double *heights
     if (K) *K = c->K;
     const int m = std::min(cap, c->K);
     if (m <= 0) return sync_and_check(c);
-    std::vector<double> tmp(2 * (size_t)m);
+    const int hs = c->sys.hstride, D = c->sys.D;
+    std::vector<double> tmp((size_t)hs * m);
     if (centers_host &&
-        (s = cuda_check(c, cudaMemcpyAsync(tmp.data(), c->sys.hc, sizeof(double) * 2 * m, cudaMemcpyDeviceToHost,
+        (s = cuda_check(c, cudaMemcpyAsync(tmp.data(), c->sys.hc, sizeof(double) * tmp.size(), cudaMemcpyDeviceToHost,
                                            c->stream), "hill copy")))
         return s;
     if (heights_host &&
@@ -886,10 +998,8 @@ metad_status metad_get_hills(metad_ctx *c, double *centers_host, double *heights
         return s;
     if ((s = sync_and_check(c))) return s;
     if (centers_host)
-        for (int k = 0; k < m; ++k) {
-            centers_host[(size_t)c->p.n_cv * k] = tmp[2 * k];
-            if (c->p.n_cv == 2) centers_host[(size_t)c->p.n_cv * k + 1] = tmp[2 * k + 1];
-        }
+        for (int k = 0; k < m; ++k)
+            for (int d = 0; d < D; ++d) centers_host[(size_t)D * k + d] = tmp[(size_t)hs * k + d];
     return METAD_OK;
 }
 
@@ -1029,6 +1139,7 @@ metad_status step_graph(metad_ctx *c, const float *pos_dev, float *forces_dev, i
         // the host state a direct step would leave
         c->sys.pos_in = reinterpret_cast<const float4 *>(pos_dev);
         c->have_nbr = c->have_cv = c->have_bias = true;
+        c->forces_done = c->p.cv_kind == METAD_CV_COORDINATION;
         c->filter_pending = false;
         if (deposit) c->K += 1;
     }
@@ -1065,12 +1176,12 @@ metad_status metad_step_host(metad_ctx *c, const float *pos_host, float *forces_
     if ((s = cuda_check(c, cudaMemcpyAsync(forces_host, c->force_stage, sizeof(float) * 3 * n,
                                            cudaMemcpyDeviceToHost, c->stream), "force download")))
         return s;
-    if ((s = cuda_check(c, cudaMemcpyAsync(c->host_pinned, c->sys.scal, 5 * sizeof(double), cudaMemcpyDeviceToHost,
-                                           c->stream), "result copy")))
+    if ((s = cuda_check(c, cudaMemcpyAsync(c->host_pinned, c->sys.scal, metad::kNumScal * sizeof(double),
+                                           cudaMemcpyDeviceToHost, c->stream), "result copy")))
         return s;
     if ((s = sync_and_check(c))) return s;
     if (cv_host)
-        for (int d = 0; d < c->p.n_cv; ++d) cv_host[d] = c->host_pinned[metad::kS0 + d];
+        for (int d = 0; d < c->sys.D; ++d) cv_host[d] = c->host_pinned[metad::kS0 + d];
     if (V_host) *V_host = c->host_pinned[metad::kV];
     return METAD_OK;
 }
@@ -1163,11 +1274,11 @@ metad_status metad_read_results(metad_ctx *c, double *cv_host, double *V_host, d
 {
     metad_status s = check_usable(c);
     if (s) return s;
-    s = cuda_check(c, cudaMemcpyAsync(c->host_pinned, c->sys.scal, 5 * sizeof(double), cudaMemcpyDeviceToHost,
-                                      c->stream), "result copy");
+    s = cuda_check(c, cudaMemcpyAsync(c->host_pinned, c->sys.scal, metad::kNumScal * sizeof(double),
+                                      cudaMemcpyDeviceToHost, c->stream), "result copy");
     if (s) return s;
     if ((s = sync_and_check(c))) return s;
-    for (int d = 0; d < c->p.n_cv; ++d) {
+    for (int d = 0; d < c->sys.D; ++d) {
         if (cv_host) cv_host[d] = c->host_pinned[metad::kS0 + d];
         if (dVds_host) dVds_host[d] = c->host_pinned[metad::kDV0 + d];
     }
@@ -1246,7 +1357,8 @@ metad_status metad_batch_create(metad_ctx *const *ctxs, int32_t n, metad_batch *
         const metad_ctx *c = ctxs[k];
         if (!c || c->failed) return METAD_ERR_INVALID;
         if (c->p.device != ctxs[0]->p.device || c->stream != ctxs[0]->stream || c->p.n_cv != ctxs[0]->p.n_cv ||
-            c->fp64 != ctxs[0]->fp64 || c->p.cv_kind != ctxs[0]->p.cv_kind)
+            c->fp64 != ctxs[0]->fp64 || c->p.cv_kind != ctxs[0]->p.cv_kind ||
+            c->sys.virial != ctxs[0]->sys.virial)
             return METAD_ERR_INVALID;
     }
     metad_batch *b = new (std::nothrow) metad_batch();
@@ -1351,7 +1463,7 @@ metad_status metad_batch_step(metad_batch *b, const float *const *pos_dev, float
     metad::launch_batch_bias(rows[metad::GK_HILLS], totals[metad::GK_HILLS], 0, b->stream);
     metad::launch_batch_force(rows[metad::GK_GROUPS], totals[metad::GK_GROUPS], rows[metad::GK_ATOM32],
                               totals[metad::GK_ATOM32], rows[metad::GK_ATOM128], totals[metad::GK_ATOM128], b->fp64,
-                              b->ncv, b->stream);
+                              b->ncv, b->ctx[0]->sys.virial, b->stream);
     if (any_deposit) metad::launch_batch_bias(rows[metad::GK_DEPOSIT], totals[metad::GK_DEPOSIT], 1, b->stream);
     b->launches += 1 + 8 + 2 + 1 + (b->ncv == 2 ? 3 : 2) + (any_deposit ? 1 : 0);
     }
@@ -1364,6 +1476,7 @@ metad_status metad_batch_step(metad_batch *b, const float *const *pos_dev, float
         if (active && !active[k]) continue;
         metad_ctx *c = b->ctx[k];
         c->have_nbr = c->have_cv = c->have_bias = true;
+        c->forces_done = b->kind == METAD_CV_COORDINATION;
         c->filter_pending = false;
         if (deposit && deposit[k]) c->K += 1;
     }
@@ -1428,6 +1541,7 @@ namespace {
 metad_status fes_grid_args(metad_ctx *c, const double *lo, const double *hi, const int32_t *n, int64_t &bins)
 {
     if (!lo || !hi || !n) return fail(c, METAD_ERR_INVALID, "NULL grid argument");
+    if (c->sys.D > 2) return fail(c, METAD_ERR_INVALID, "free-energy grids take one or two CVs");
     bins = 1;
     for (int d = 0; d < c->p.n_cv; ++d) {
         if (n[d] < 1 || !(hi[d] > lo[d])) return fail(c, METAD_ERR_INVALID, "grid shape");

@@ -18,46 +18,61 @@ namespace metad {
 namespace {
 
 // V and dV/ds at s.bias_x into s.bias_out; with s.deposit, also appends the
-// well-tempered hill there as hill s.K.
+// well-tempered hill there as hill s.K.  s.D dimensions (at most kMaxCv).
 __device__ __forceinline__ void bias(const Sys &s, Blk blk)
 {
-    const int K = s.K;
-    const double x0 = s.bias_x[0];
-    const double x1 = s.ncv == 2 ? s.bias_x[1] : 0.0;
-    const double inv2v0 = 0.5 / (s.sigma[0] * s.sigma[0]), inv2v1 = 0.5 / (s.sigma[1] * s.sigma[1]);
-    double V = 0.0, g0 = 0.0, g1 = 0.0;
+    const int K = s.K, D = s.D, hs = s.hstride;
+    double x[kMaxCv], inv2v[kMaxCv], g[kMaxCv];
+#pragma unroll
+    for (int d = 0; d < kMaxCv; ++d) {
+        x[d] = d < D ? s.bias_x[d] : 0.0;
+        inv2v[d] = d < D ? 0.5 / (s.sigma[d] * s.sigma[d]) : 0.0;
+        g[d] = 0.0;
+    }
+    double V = 0.0;
     for (int k = blk.b * blockDim.x + threadIdx.x; k < K; k += blk.nb * blockDim.x) {
-        const double d0 = hill_diff(s, 0, x0 - s.hc[2 * (size_t)k]);
-        double e = d0 * d0 * inv2v0;
-        double d1 = 0.0;
-        if (s.ncv == 2) {
-            d1 = hill_diff(s, 1, x1 - s.hc[2 * (size_t)k + 1]);
-            e += d1 * d1 * inv2v1;
+        const double *c = s.hc + (size_t)hs * k;
+        double dd[kMaxCv];
+        double e = 0.0;
+#pragma unroll
+        for (int d = 0; d < kMaxCv; ++d) {
+            if (d >= D) break;
+            dd[d] = hill_diff(s, d, x[d] - c[d]);
+            e = d == 0 ? dd[d] * dd[d] * inv2v[d] : e + dd[d] * dd[d] * inv2v[d];
         }
         const double gk = s.hw[k] * exp(-e);
         V += gk;
-        g0 -= gk * d0 * (2.0 * inv2v0);
-        g1 -= gk * d1 * (2.0 * inv2v1);
+#pragma unroll
+        for (int d = 0; d < kMaxCv; ++d) {
+            if (d >= D) break;
+            g[d] -= gk * dd[d] * (2.0 * inv2v[d]);
+        }
     }
-    // block sums in a fixed order
-    __shared__ double sh[3][kBlockBias / 32];
+    // block sums in a fixed order: V, then dV/ds_d
+    constexpr int kW = kBlockBias / 32;
+    __shared__ double sh[kMaxCv + 1][kW];
     __shared__ bool am_last;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         V += __shfl_down_sync(0xffffffffu, V, o);
-        g0 += __shfl_down_sync(0xffffffffu, g0, o);
-        g1 += __shfl_down_sync(0xffffffffu, g1, o);
+#pragma unroll
+        for (int d = 0; d < kMaxCv; ++d)
+            if (d < D) g[d] += __shfl_down_sync(0xffffffffu, g[d], o);
     }
-    if (lane == 0) { sh[0][wid] = V; sh[1][wid] = g0; sh[2][wid] = g1; }
+    if (lane == 0) {
+        sh[0][wid] = V;
+#pragma unroll
+        for (int d = 0; d < kMaxCv; ++d) sh[1 + d][wid] = g[d];
+    }
     __syncthreads();
     double *part = s.part + 2 * (size_t)s.part_stride;
     if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0, c = 0.0;
-        for (int w = 0; w < kBlockBias / 32; ++w) { a += sh[0][w]; b += sh[1][w]; c += sh[2][w]; }
-        part[3 * blk.b + 0] = a;
-        part[3 * blk.b + 1] = b;
-        part[3 * blk.b + 2] = c;
+        for (int q = 0; q <= D; ++q) {
+            double a = 0.0;
+            for (int w = 0; w < kW; ++w) a += sh[q][w];
+            part[(D + 1) * blk.b + q] = a;
+        }
         __threadfence();
         unsigned prev = atomicAdd(&s.ticket[2], 1u);
         am_last = (prev == (unsigned)blk.nb - 1u);
@@ -67,39 +82,46 @@ __device__ __forceinline__ void bias(const Sys &s, Blk blk)
     __threadfence();
     // the last block adds the partials: thread t takes blocks t, t + blockDim,
     // ... in order, then the same fixed tree as above
-    double a = 0.0, b = 0.0, c = 0.0;
-    for (int q = threadIdx.x; q < blk.nb; q += blockDim.x) {
-        a += __ldcg(part + 3 * q);
-        b += __ldcg(part + 3 * q + 1);
-        c += __ldcg(part + 3 * q + 2);
+    double a[kMaxCv + 1];
+#pragma unroll
+    for (int q = 0; q <= kMaxCv; ++q) a[q] = 0.0;
+    for (int b = threadIdx.x; b < blk.nb; b += blockDim.x) {
+#pragma unroll
+        for (int q = 0; q <= kMaxCv; ++q)
+            if (q <= D) a[q] += __ldcg(part + (D + 1) * b + q);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_down_sync(0xffffffffu, a, o);
-        b += __shfl_down_sync(0xffffffffu, b, o);
-        c += __shfl_down_sync(0xffffffffu, c, o);
+#pragma unroll
+        for (int q = 0; q <= kMaxCv; ++q)
+            if (q <= D) a[q] += __shfl_down_sync(0xffffffffu, a[q], o);
     }
-    if (lane == 0) { sh[0][wid] = a; sh[1][wid] = b; sh[2][wid] = c; }
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q <= kMaxCv; ++q) sh[q][wid] = a[q];
+    }
     __syncthreads();
     if (threadIdx.x != 0) return;
-    a = b = c = 0.0;
-    for (int w = 0; w < kBlockBias / 32; ++w) { a += sh[0][w]; b += sh[1][w]; c += sh[2][w]; }
-    if (s.ncv == 2) {
+    double out_v[kMaxCv + 1];
+    for (int q = 0; q <= kMaxCv; ++q) {
+        double t = 0.0;
+        if (q <= D)
+            for (int w = 0; w < kW; ++w) t += sh[q][w];
+        out_v[q] = t;
+    }
+    if (s.ncv == 2 && D == 2) {
         double gv, gg0, gg1;
-        grid_value(s, x0, x1, gv, gg0, gg1);
-        a += gv;
-        b += gg0;
-        c += gg1;
+        grid_value(s, x[0], x[1], gv, gg0, gg1);
+        out_v[0] += gv;
+        out_v[1] += gg0;
+        out_v[2] += gg1;
     }
     double *out = s.bias_out;
-    out[0] = a;
-    out[1] = b;
-    out[2] = c;
+    for (int q = 0; q <= kMaxCv; ++q) out[q] = out_v[q];
     s.ticket[2] = 0u;
     if (s.deposit) {
-        const double w = s.w0 * exp(-a / s.kbdt);
-        s.hc[2 * (size_t)K] = x0;
-        s.hc[2 * (size_t)K + 1] = x1;
+        const double w = s.w0 * exp(-out_v[0] / s.kbdt);
+        for (int d = 0; d < hs; ++d) s.hc[(size_t)hs * K + d] = x[d];
         s.hw[K] = w;
         s.scal[kDepW] = w;
     }
@@ -119,14 +141,15 @@ __global__ void __launch_bounds__(kBlockBias) kb_bias(BatchView v, int deposit)
     bias(s, k);
 }
 
-// One thread per system: s1, s2, V and the error word, for one copy to the host.
+// One thread per system: s1, s2 (0 with one per-atom CV), V and the error
+// word, for one copy to the host.
 __global__ void kb_collect(const Sys *sys, int nsys, double *out)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nsys) return;
     const Sys &s = sys[k];
     out[4 * k + 0] = s.scal[kS0];
-    out[4 * k + 1] = s.scal[kS1];
+    out[4 * k + 1] = s.ncv == 2 ? s.scal[kS1] : 0.0;
     out[4 * k + 2] = s.scal[kV];
     out[4 * k + 3] = (double)*s.err;
 }
@@ -141,7 +164,7 @@ __global__ void k_grid_fold(Sys s, int K)
     const double v0 = s.sigma[0] * s.sigma[0], v1 = s.sigma[1] * s.sigma[1];
     double f = 0.0, fx = 0.0, fy = 0.0, fxy = 0.0;
     for (int k = 0; k < K; ++k) {
-        const double dx = x - s.hc[2 * (size_t)k], dy = y - s.hc[2 * (size_t)k + 1];
+        const double dx = x - s.hc[(size_t)s.hstride * k], dy = y - s.hc[(size_t)s.hstride * k + 1];
         const double g = s.hw[k] * exp(-(dx * dx / (2.0 * v0) + dy * dy / (2.0 * v1)));
         f += g;
         fx -= g * dx / v0;

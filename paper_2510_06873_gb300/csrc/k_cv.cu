@@ -426,6 +426,26 @@ struct RunSum<double> {
     __device__ __forceinline__ double value() const { return s; }
 };
 
+// Warp tree over RunSum values (lane 0 ends with the warp's sum): FP32
+// pairs combine by TwoSum on s and a plain sum of the c terms.
+__device__ __forceinline__ void warp_sum(RunSum<float> &v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float os = __shfl_down_sync(0xffffffffu, v.s, o);
+        const float oc = __shfl_down_sync(0xffffffffu, v.c, o);
+        const float t = v.s + os;
+        const float bp = t - v.s;
+        v.c += oc + ((v.s - (t - bp)) + (os - bp));
+        v.s = t;
+    }
+}
+__device__ __forceinline__ void warp_sum(RunSum<double> &v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v.s += __shfl_down_sync(0xffffffffu, v.s, o);
+}
+
 // a5: qbar_m(i), qbar6(i), s2.  Record b: b_m(i) = K_m qbar_m(i) / (N qbar6
 // (1 + W_i)) (slots 0..12) and beta_i = b(i).qbar(i) (slot 13).
 template <typename real>
@@ -510,7 +530,10 @@ __device__ void last_block_cv(const Sys &s, Blk k, double c, double q)
     Q = block_sum(Q, sh);
     if (threadIdx.x == 0) {
         s.scal[kS0] = C / s.n;
-        s.scal[kS1] = s.ncv == 2 ? Q / s.n : 0.0;
+        if (s.ncv == 2) s.scal[kS1] = Q / s.n;
+        else if (!s.lattice) s.scal[kS1] = 0.0;
+        if (s.lattice)  // the triaxial lattice parameters follow the per-atom CVs
+            for (int a = 0; a < 3; ++a) s.scal[kS0 + s.ncv + a] = s.L[a];
         s.ticket[0] = 0u;
     }
 }
@@ -710,8 +733,9 @@ __device__ __forceinline__ void store_pair_force<double>(double *slot, double fx
 // so pass 2 sums each atom's own slots in row order.
 constexpr int kPairChunk = 32;
 
-template <typename real>
-__device__ __forceinline__ void pair_force(const Sys &s, int i, int k, real cn_fac, real V2)
+template <typename real, bool kVir>
+__device__ __forceinline__ void pair_force(const Sys &s, int i, int k, real cn_fac, real V2, RunSum<real> &vx,
+                                           RunSum<real> &vy, RunSum<real> &vz)
 {
     Vec3<real> d;
     real inv_r, w, dw;
@@ -755,6 +779,11 @@ __device__ __forceinline__ void pair_force(const Sys &s, int i, int k, real cn_f
     fx += radial * ux;
     fy += radial * uy;
     fz += radial * uz;
+    if (kVir) {  // (dV/dd)_a d_a of this pair
+        vx.add(fx * d.x);
+        vy.add(fy * d.y);
+        vz.add(fz * d.z);
+    }
     real *pf = R<real>(s.pairF);
     store_pair_force<real>(pf + ((size_t)i * s.max_nb + k) * 4, fx, fy, fz);
     // position of i in the j < i part [nh_j, nn_j) of j's row, four entries per load
@@ -774,7 +803,79 @@ __device__ __forceinline__ void pair_force(const Sys &s, int i, int k, real cn_f
     store_pair_force<real>(pf + ((size_t)j * s.max_nb + kk) * 4, -fx, -fy, -fz);
 }
 
+// The bias virial W_a = sum_pairs (dV/dd)_a d_a, which a barostat needs: it
+// gives dV/dL_a at fixed fractional coordinates as W_a / L_a, plus dV/ds of
+// a lattice CV.  Per-thread compensated sums, a warp tree, FP64 block
+// partials in slot 1 of `part` (free once the CV sums are taken), and the
+// last block to finish adds them in block order.
 template <typename real>
+__device__ void virial_finish(const Sys &s, Blk k, RunSum<real> &vx, RunSum<real> &vy, RunSum<real> &vz)
+{
+    constexpr int kW = kBlockAtoms / 32;
+    __shared__ double sh[3][kW];
+    __shared__ bool am_last;
+    if (3 * k.nb > s.part_stride) {  // never with the grids used; refuse rather than overrun
+        if (k.b == 0 && threadIdx.x == 0) set_err(s, kErrInternal);
+        return;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    warp_sum(vx);
+    warp_sum(vy);
+    warp_sum(vz);
+    if (lane == 0) {
+        sh[0][wid] = vx.value();
+        sh[1][wid] = vy.value();
+        sh[2][wid] = vz.value();
+    }
+    __syncthreads();
+    double *part = s.part + s.part_stride;
+    if (threadIdx.x == 0) {
+        for (int a = 0; a < 3; ++a) {
+            double t = 0.0;
+            for (int w = 0; w < kW; ++w) t += sh[a][w];
+            part[3 * k.b + a] = t;
+        }
+        __threadfence();
+        am_last = atomicAdd(&s.ticket[3], 1u) == (unsigned)k.nb - 1u;
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    // thread t adds partials t, t + blockDim, ... in order into four
+    // interleaved accumulators (a short FP64 chain), combined in order
+    double acc[3][4] = {};
+    for (int b0 = threadIdx.x; b0 < k.nb; b0 += 4 * blockDim.x) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int b = b0 + r * blockDim.x;
+            if (b < k.nb) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) acc[a][r] += __ldcg(part + 3 * b + a);
+            }
+        }
+    }
+    double v[3];
+    for (int a = 0; a < 3; ++a) {
+        v[a] = (acc[a][0] + acc[a][1]) + (acc[a][2] + acc[a][3]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[a] += __shfl_down_sync(0xffffffffu, v[a], o);
+    }
+    __syncthreads();
+    if (lane == 0)
+        for (int a = 0; a < 3; ++a) sh[a][wid] = v[a];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int a = 0; a < 3; ++a) {
+            double t = 0.0;
+            for (int w = 0; w < kW; ++w) t += sh[a][w];
+            s.scal[kVir0 + a] = t;
+            s.scal[kBoxG0 + a] = (s.lattice ? s.fscale * s.scal[kDV0 + s.ncv + a] : 0.0) + t / s.L[a];
+        }
+        s.ticket[3] = 0u;
+    }
+}
+
+template <typename real, bool kVir>
 __device__ __forceinline__ void force_pairs(const Sys &s, Blk k)
 {
     // the chain-rule factors of the two CVs, once per block: an FP64 chain is
@@ -791,6 +892,7 @@ __device__ __forceinline__ void force_pairs(const Sys &s, Blk k)
     constexpr int kWarps = kBlockAtoms / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int items = (s.n + kPairChunk * kWarps - 1) / (kPairChunk * kWarps);
+    RunSum<real> vx, vy, vz;
     for (int it = 0, g; (g = work_item(k, it)) < items; ++it) {
         const int i0 = (g * kWarps + warp) * kPairChunk;
         if (i0 >= s.n) continue;  // warp-uniform
@@ -814,20 +916,21 @@ __device__ __forceinline__ void force_pairs(const Sys &s, Blk k)
             }
             const int prev = __shfl_sync(0xffffffffu, off, lo > 0 ? lo - 1 : 0);  // every lane shuffles
             const int start = lo > 0 ? prev : 0;
-            if (p < T) pair_force<real>(s, i0 + lo, p - start, cn_fac, V2);
+            if (p < T) pair_force<real, kVir>(s, i0 + lo, p - start, cn_fac, V2, vx, vy, vz);
         }
     }
+    if (kVir) virial_finish<real>(s, k, vx, vy, vz);
 }
 
-template <typename real>
-__global__ void __launch_bounds__(kBlockAtoms) k_force_pairs(Sys s) { force_pairs<real>(s, own_blk()); }
+template <typename real, bool kVir = false>
+__global__ void __launch_bounds__(kBlockAtoms) k_force_pairs(Sys s) { force_pairs<real, kVir>(s, own_blk()); }
 
-template <typename real>
+template <typename real, bool kVir = false>
 __global__ void __launch_bounds__(kBlockAtoms) kb_force_pairs(BatchView v)
 {
     Blk k;
     const Sys &s = v.sys[batch_system(v, k)];
-    force_pairs<real>(s, k);
+    force_pairs<real, kVir>(s, k);
 }
 
 template <typename real>
@@ -963,10 +1066,13 @@ void launch_force_pairs(const Sys &s, int fp64, double scale, cudaStream_t st)
     Sys t = s;
     t.fscale = scale;
     const int nb = grid_blocks(s, GK_ATOM128, 0);
-    if (fp64)
-        k_force_pairs<double><<<nb, kBlockAtoms, 0, st>>>(t);
-    else
-        k_force_pairs<float><<<nb, kBlockAtoms, 0, st>>>(t);
+    if (fp64) {
+        if (s.virial) k_force_pairs<double, true><<<nb, kBlockAtoms, 0, st>>>(t);
+        else k_force_pairs<double><<<nb, kBlockAtoms, 0, st>>>(t);
+    } else {
+        if (s.virial) k_force_pairs<float, true><<<nb, kBlockAtoms, 0, st>>>(t);
+        else k_force_pairs<float><<<nb, kBlockAtoms, 0, st>>>(t);
+    }
 }
 
 void launch_force_gather(const Sys &s, int fp64, float *F, int accumulate, cudaStream_t st)
@@ -1000,16 +1106,18 @@ void launch_batch_cv(const BatchView &groups, int group_total, const BatchView &
 }
 
 void launch_batch_force(const BatchView &groups, int group_total, const BatchView &adj, int adj_total,
-                        const BatchView &pairs, int pair_total, int fp64, int ncv, cudaStream_t st)
+                        const BatchView &pairs, int pair_total, int fp64, int ncv, int virial, cudaStream_t st)
 {
     if (group_total <= 0) return;
     if (fp64) {
         if (ncv == 2) kb_adjoint<double><<<adj_total, kBlockAtoms, 0, st>>>(adj);
-        kb_force_pairs<double><<<pair_total, kBlockAtoms, 0, st>>>(pairs);
+        if (virial) kb_force_pairs<double, true><<<pair_total, kBlockAtoms, 0, st>>>(pairs);
+        else kb_force_pairs<double><<<pair_total, kBlockAtoms, 0, st>>>(pairs);
         kb_force_gather<double><<<group_total, kBlockAtoms, 0, st>>>(groups);
     } else {
         if (ncv == 2) kb_adjoint<float><<<adj_total, kBlockAtoms, 0, st>>>(adj);
-        kb_force_pairs<float><<<pair_total, kBlockAtoms, 0, st>>>(pairs);
+        if (virial) kb_force_pairs<float, true><<<pair_total, kBlockAtoms, 0, st>>>(pairs);
+        else kb_force_pairs<float><<<pair_total, kBlockAtoms, 0, st>>>(pairs);
         kb_force_gather<float><<<group_total, kBlockAtoms, 0, st>>>(groups);
     }
 }

@@ -46,10 +46,10 @@ __global__ void __launch_bounds__(kFesThreads) k_fes_points(Sys s, int K, FesGri
     const double inv2v0 = 0.5 / (s.sigma[0] * s.sigma[0]), inv2v1 = 0.5 / (s.sigma[1] * s.sigma[1]);
     double acc = 0.0;
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        const double d0 = hill_diff(s, 0, x0 - s.hc[2 * (size_t)k]);
+        const double d0 = hill_diff(s, 0, x0 - s.hc[(size_t)s.hstride * k]);
         double e = d0 * d0 * inv2v0;
         if (s.ncv == 2) {
-            const double d1 = hill_diff(s, 1, x1 - s.hc[2 * (size_t)k + 1]);
+            const double d1 = hill_diff(s, 1, x1 - s.hc[(size_t)s.hstride * k + 1]);
             e += d1 * d1 * inv2v1;
         }
         acc += s.hw[k] * exp(-e);

@@ -14,6 +14,7 @@ constexpr int kNY = 13;          // real Y_6^m, m = -6..6
 constexpr int kBlockAtoms = 128; // threads per block of the per-atom kernels
 constexpr int kBlockBias = 256;  // threads per block of the hill kernels
 constexpr int kMaxBiasBlocks = 304;  // two per SM
+constexpr int kMaxCv = 5;        // CN, Q6 and the three lattice parameters
 
 enum ErrBits : int {
     kErrCapacity = 1,   // an atom had more neighbours than max_nb
@@ -22,14 +23,17 @@ enum ErrBits : int {
     kErrInternal = 8,   // a launch shape the buffers were not sized for
 };
 
-// Slots of the per-system FP64 scalar block `scal`.
+// Slots of the per-system FP64 scalar block `scal` (D = ncv + 3 lattice CVs
+// at most kMaxCv; each vector slot holds kMaxCv entries).
 enum Scal : int {
-    kS0 = 0, kS1 = 1,            // CVs s1, s2
-    kV = 2, kDV0 = 3, kDV1 = 4,  // bias and its gradient at (s1, s2)
-    kDepV = 5, kDepDV0 = 6, kDepDV1 = 7,  // bias and gradient at the last deposit centre
-    kDepW = 8,                   // height of the last deposited hill
-    kDepC0 = 9, kDepC1 = 10,     // the last deposit centre (or a caller's CV point)
-    kNumScal = 16
+    kS0 = 0, kS1 = 1,            // CVs s1, s2 (then the lattice CVs, if any)
+    kV = 5, kDV0 = 6, kDV1 = 7,  // bias and its gradient at the CVs
+    kDepV = 11, kDepDV0 = 12,    // bias and gradient at the last deposit centre
+    kDepW = 17,                  // height of the last deposited hill
+    kDepC0 = 18,                 // the last deposit centre (or a caller's CV point)
+    kVir0 = 23,                  // bias virial sum_pairs (dV/dd)_a d_a, a = x, y, z
+    kBoxG0 = 26,                 // dV/dL_a at fixed fractional coordinates
+    kNumScal = 32
 };
 
 // CV families (the metad_params.cv_kind values).
@@ -101,10 +105,14 @@ struct Sys {
     double *scal;          // kNumScal doubles
     int *err;
     // hills and grid
-    double *hc;            // [cap][2]
+    double *hc;            // [cap][hstride]
     double *hw;            // [cap]
     int hill_cap;
-    double sigma[2];
+    double sigma[kMaxCv];  // per CV (the lattice CVs last)
+    int D;                 // CVs the hills see: ncv (+ 3 lattice parameters)
+    int hstride;           // doubles per hill centre: max(D, 2)
+    int lattice;           // 1: the box lengths are CVs ncv .. ncv + 2
+    int virial;            // 1: the force pass also sums the bias virial
     double w0, kbdt;
     int grid_on;
     int gn[2];
@@ -119,8 +127,8 @@ struct Sys {
     int accumulate;        // 1: F_out += force, 0: F_out = force
     double fscale;         // forces are scaled by this
     // torsion and nearest-distance families (no neighbour list)
-    double period[2];      // 0, or the period of a periodic CV (2 pi for a torsion)
-    double inv_period[2];  // 1 / period (0 when not periodic)
+    double period[kMaxCv];      // 0, or the period of a periodic CV (2 pi for a torsion)
+    double inv_period[kMaxCv];  // 1 / period (0 when not periodic)
     const int *cv_atoms;   // torsion: [ncv][4]; nearest: [ncv] references, then n_cand candidates
     const int *cand_slot;  // nearest: [n] position of each atom in the candidate group, or -1
     int n_cand;
@@ -217,7 +225,7 @@ void launch_batch_cv(const BatchView &groups, int group_total, const BatchView &
 void launch_cv_sum(const Sys &s, int fp64, cudaStream_t st);
 void launch_batch_bias(const BatchView &v, int total, int deposit, cudaStream_t st);
 void launch_batch_force(const BatchView &groups, int group_total, const BatchView &adj, int adj_total,
-                        const BatchView &pairs, int pair_total, int fp64, int ncv, cudaStream_t st);
+                        const BatchView &pairs, int pair_total, int fp64, int ncv, int virial, cudaStream_t st);
 void launch_batch_collect(const BatchView &v, double *out, cudaStream_t st);
 
 // Launch entry points (stream-ordered, no host synchronisation).
@@ -228,7 +236,7 @@ void launch_cv_fwd(const Sys &s, int fp64, int fused_filter, cudaStream_t st);
 void launch_cv_avg(const Sys &s, int fp64, cudaStream_t st);
 void launch_bias(const Sys &s, int K, const double *s_dev, double *out_dev, int deposit, cudaStream_t st);
 void launch_adjoint(const Sys &s, int fp64, cudaStream_t st);
-void launch_force_pairs(const Sys &s, int fp64, double scale, cudaStream_t st);
+void launch_force_pairs(const Sys &s, int fp64, double scale, cudaStream_t st);  // + virial if s.virial
 void launch_force_gather(const Sys &s, int fp64, float *F, int accumulate, cudaStream_t st);
 void configure_kernels();
 void launch_grid_fold(const Sys &s, int K, cudaStream_t st);

@@ -33,6 +33,7 @@ class metad_params(ctypes.Structure):
         ("precision", ctypes.c_int32), ("max_neighbors", ctypes.c_int32), ("device", ctypes.c_int32),
         ("step_graph", ctypes.c_int32), ("stream", ctypes.c_void_p), ("skin", ctypes.c_double),
         ("cv_kind", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("softmin_beta", ctypes.c_double),
+        ("lattice_cvs", ctypes.c_int32), ("virial", ctypes.c_int32), ("sigma_lattice", ctypes.c_double * 3),
     ]
 
 
@@ -55,6 +56,8 @@ _SIGS = {
     "metad_bias_forces": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_double]),
     "metad_deposit_hill": (ctypes.c_int, [_P, _P, _P]),
     "metad_set_cv_atoms": (ctypes.c_int, [_P, _P, ctypes.c_int32]),
+    "metad_set_box": (ctypes.c_int, [_P, _P]),
+    "metad_box_gradient": (ctypes.c_int, [_P, _P]),
     "metad_deposit_hills": (ctypes.c_int, [_P, _P, ctypes.c_int32, _P]),
     "metad_load_hills": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32]),
     "metad_get_hills": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
@@ -170,7 +173,8 @@ def metad_build_neighbors(ctx, pos):
 
 
 def metad_cv_forward(ctx, n_cv=None, per_atom=None, want_host=True):
-    out = np.zeros(2) if want_host else None
+    """n_cv: the number of CVs D to return (n_cv, + 3 with lattice CVs)."""
+    out = np.zeros(5) if want_host else None
     _check(ctx, lib().metad_cv_forward(ctx, _hptr(out), _dptr(per_atom)), "metad_cv_forward")
     return None if out is None else out[: (n_cv or 2)]
 
@@ -178,7 +182,7 @@ def metad_cv_forward(ctx, n_cv=None, per_atom=None, want_host=True):
 def metad_bias_eval(ctx, s=None, want_host=True):
     sh = None if s is None else np.ascontiguousarray(np.atleast_1d(s), dtype=np.float64)
     V = ctypes.c_double(0.0)
-    dV = np.zeros(2)
+    dV = np.zeros(5)
     if want_host:
         _check(ctx, lib().metad_bias_eval(ctx, _hptr(sh), ctypes.byref(V), _hptr(dV)), "metad_bias_eval")
         return V.value, dV
@@ -194,6 +198,17 @@ def metad_bias_forces(ctx, forces, accumulate=False, scale=1.0):
 def metad_set_cv_atoms(ctx, atoms):
     a = np.ascontiguousarray(np.asarray(atoms).ravel(), dtype=np.int32)
     _check(ctx, lib().metad_set_cv_atoms(ctx, _hptr(a), int(a.size)), "metad_set_cv_atoms")
+
+
+def metad_set_box(ctx, box):
+    b = np.ascontiguousarray(np.asarray(box, dtype=np.float64).ravel()[:3])
+    _check(ctx, lib().metad_set_box(ctx, _hptr(b)), "metad_set_box")
+
+
+def metad_box_gradient(ctx):
+    out = np.zeros(3)
+    _check(ctx, lib().metad_box_gradient(ctx, _hptr(out)), "metad_box_gradient")
+    return out
 
 
 def metad_deposit_hill(ctx, center=None, want_height=True):
@@ -252,7 +267,7 @@ def metad_step(ctx, pos, forces, accumulate=False, deposit=False):
 
 def metad_step_host(ctx, pos_host, forces_host, accumulate=False, deposit=False):
     """pos_host float32 [N,4], forces_host float32 [N,3] (numpy, ideally pinned)."""
-    cv = np.zeros(2)
+    cv = np.zeros(5)
     V = ctypes.c_double(0.0)
     _check(ctx, lib().metad_step_host(ctx, _hptr(pos_host), _hptr(forces_host), int(bool(accumulate)),
                                       int(bool(deposit)), _hptr(cv), ctypes.byref(V)), "metad_step_host")
@@ -301,7 +316,7 @@ def metad_bias_eval_noalloc(s, centers, heights, sigma, out, device=0, stream=No
 
 
 def metad_read_results(ctx):
-    cv, dV = np.zeros(2), np.zeros(2)
+    cv, dV = np.zeros(5), np.zeros(5)
     V = ctypes.c_double(0.0)
     _check(ctx, lib().metad_read_results(ctx, _hptr(cv), ctypes.byref(V), _hptr(dV)), "metad_read_results")
     return cv, V.value, dV
@@ -323,7 +338,8 @@ def metad_hill_count(ctx) -> int:
 def params_for(n_atoms, box, n_cv=2, sigma=(0.05, 0.02), rc=3.5, r0=2.5, sw_n=6, sw_m=12, cn_unlike=True,
                w0=1.0, biasfactor=10.0, temperature=300.0, kB=0.0083144626, grid=None, hill_capacity=65536,
                fp64=False, max_neighbors=64, device=0, stream=None, skin=1.0, step_graph=False,
-               cv_kind="coordination", softmin_beta=0.0) -> metad_params:
+               cv_kind="coordination", softmin_beta=0.0, lattice_cvs=False, virial=False,
+               sigma_lattice=(0.1, 0.1, 0.1)) -> metad_params:
     """metad_params from keyword values; grid = (n, lo, hi) or None; cv_kind
     "coordination", "torsion" or "nearest" (or the METAD_CV_* value)."""
     p = metad_params_default()
@@ -351,6 +367,10 @@ def params_for(n_atoms, box, n_cv=2, sigma=(0.05, 0.02), rc=3.5, r0=2.5, sw_n=6,
     p.step_graph = 1 if step_graph else 0
     p.cv_kind = CV_KINDS[cv_kind] if isinstance(cv_kind, str) else int(cv_kind)
     p.softmin_beta = float(softmin_beta)
+    p.lattice_cvs = 1 if lattice_cvs else 0
+    p.virial = 1 if virial else 0
+    for a in range(3):
+        p.sigma_lattice[a] = float(sigma_lattice[a])
     return p
 
 
@@ -360,7 +380,9 @@ class Metad:
     def __init__(self, params: metad_params):
         self.params = params
         self.n = params.n_atoms
-        self.n_cv = params.n_cv
+        # CVs the hills see (and every CV vector in and out): the per-atom
+        # CVs, then the box lengths with lattice CVs
+        self.n_cv = params.n_cv + (3 if params.lattice_cvs else 0)
         self.ctx = metad_create(params)
 
     def close(self):
@@ -392,6 +414,12 @@ class Metad:
 
     def set_cv_atoms(self, atoms):
         metad_set_cv_atoms(self.ctx, atoms)
+
+    def set_box(self, box):
+        metad_set_box(self.ctx, box)
+
+    def box_gradient(self):
+        return metad_box_gradient(self.ctx)
 
     def deposit_hill(self, center=None, want_height=True):
         return metad_deposit_hill(self.ctx, center, want_height)
@@ -461,7 +489,7 @@ class Metad:
         metad_set_step_graph(self.ctx, on)
 
     def cv_trajectory(self, frames):
-        return metad_cv_trajectory(self.ctx, frames, self.n_cv)
+        return metad_cv_trajectory(self.ctx, frames, self.params.n_cv)
 
     def fes_grid(self, lo, hi, n):
         return metad_fes_grid(self.ctx, lo, hi, n)

@@ -41,13 +41,14 @@ def test_every_declared_symbol_is_exported(metad):
 
 def test_params_struct_round_trips(metad):
     p = metad.metad_params_default()
-    assert ctypes.sizeof(metad.metad_params) == 208
+    assert ctypes.sizeof(metad.metad_params) == 240
     assert (p.n_atoms, p.n_cv, p.sw_n, p.sw_m, p.stretch, p.cn_pairs) == (1, 2, 6, 12, 1, 1)
     assert (p.rc, p.r0, p.w0, p.biasfactor, p.temperature) == (3.5, 2.5, 1.0, 10.0, 300.0)
     assert list(p.sigma) == [0.05, 0.02] and p.kB == 0.0083144626
     assert p.hill_capacity == 65536 and p.max_neighbors == 64 and list(p.grid_n) == [200, 200]
     assert p.skin == 1.0
     assert p.cv_kind == metad.METAD_CV_COORDINATION and p.softmin_beta == 0.0
+    assert (p.lattice_cvs, p.virial) == (0, 0) and list(p.sigma_lattice) == [0.1, 0.1, 0.1]
 
 
 @pytest.mark.parametrize("field,value", [("n_atoms", 0), ("n_cv", 3), ("box", 6.9), ("sigma", 0.0),
@@ -141,3 +142,26 @@ def test_small_cv_families_allocate_no_neighbour_state(metad):
     big = metad.params_for(100_000, [50.0, 50.0, 50.0], sigma=(0.1,), n_cv=1, cv_kind="nearest",
                            hill_capacity=1000)
     assert metad.metad_estimate_bytes(big) < 100_000 * 16 + 64 * 1024
+
+
+@pytest.mark.parametrize("field,value", [("lattice_cvs", 2), ("virial", -1), ("sigma_lattice", 0.0),
+                                         ("grid_on", 1), ("cv_kind", 1)])
+def test_lattice_cvs_reject_bad_params(metad, field, value):
+    p = metad.params_for(5000, [40.0, 40.0, 40.0], lattice_cvs=True)
+    if field == "sigma_lattice":
+        p.sigma_lattice[2] = value
+    elif field == "grid_on":
+        p.grid_on, p.grid_n[0], p.grid_n[1], p.grid_hi[0], p.grid_hi[1] = 1, 10, 10, 1.0, 1.0
+    else:
+        setattr(p, field, value)
+    with pytest.raises(metad.MetadError) as e:
+        metad.metad_estimate_bytes(p)
+    assert e.value.status == metad.METAD_ERR_INVALID
+
+
+def test_lattice_hills_take_five_doubles(metad):
+    base = metad.metad_estimate_bytes(metad.params_for(5000, [40.0, 40.0, 40.0], hill_capacity=10000))
+    lat = metad.metad_estimate_bytes(metad.params_for(5000, [40.0, 40.0, 40.0], hill_capacity=10000,
+                                                      lattice_cvs=True))
+    # centres (live + staging) grow from 2 to 5 doubles per hill
+    assert lat - base == 2 * 3 * 8 * 10001
