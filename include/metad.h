@@ -197,9 +197,11 @@ metad_status metad_set_cv_atoms(metad_ctx *ctx, const int32_t *atoms_host, int32
 /* NPT: the orthorhombic box of the next steps (host double[3]; each length
  * >= 2 rc, > 0 for the torsion and nearest-distance families).  Positions
  * passed afterwards must lie in (or are wrapped into) the new box.  The cell
- * grid follows the box (never more cells than at creation) and every
- * neighbour structure is rebuilt at the next step; captured step graphs are
- * dropped.  Asynchronous unless the number of cells changes.
+ * grid follows the box (never more cells than at creation).  The Verlet rows
+ * are kept while every atom's move since the last rebuild stays within
+ * (skin - |L - L_rebuild|) / 2, else rebuilt (decided on the device).
+ * Captured step graphs are dropped.  Asynchronous unless the number of cells
+ * changes.
  * Errors: METAD_ERR_INVALID (NULL, a length out of range). */
 metad_status metad_set_box(metad_ctx *ctx, const double *box_host);
 

@@ -307,6 +307,7 @@ metad_status setup_system(metad_ctx *c)
         y.rv2 = (float)(rv * rv * (1.0 + 1e-4));
         const double half = 0.5 * c->p.skin * (1.0 - 1e-3);
         y.disp_thr2 = (float)(half * half);
+        y.skin_eff = (float)(c->p.skin * (1.0 - 1e-3));
         y.always_rebuild = c->p.skin > 0.0 ? 0 : 1;
         const double grow = std::pow(rv / c->p.rc, 3.0);
         y.max_vnb = ((int)std::ceil(y.max_nb * grow) + 7) / 8 * 8;
@@ -431,7 +432,7 @@ metad_status state_buffers(metad_ctx *c, Buffers &b, Alloc &&alloc)
         (s = alloc(&b.pfb, rs * 4 * (size_t)y.max_nb * n)) || (s = alloc(&b.geob, rs * 4 * (size_t)y.max_nb * n)) ||
         (s = alloc(&y.pos_ref, n)) ||
         (s = alloc(&y.vnbr, (size_t)y.max_vnb * n)) || (s = alloc(&y.vnn, n)) || (s = alloc(&y.flag, 1)) ||
-        (s = alloc(&y.rebuilds, 1)) || (s = alloc(&b.rb, rs * (nq * 3 + (size_t)n * 4 + 64))) ||
+        (s = alloc(&y.rebuilds, 1)) || (s = alloc(&y.Lref, 4)) || (s = alloc(&b.rb, rs * (nq * 3 + (size_t)n * 4 + 64))) ||
         (s = alloc(&y.part, (size_t)y.part_stride * 4)) || (s = alloc(&y.ticket, 8)) ||
         (s = alloc(&y.scal, metad::kNumScal)) || (s = alloc(&y.err, 1)) ||
         (s = alloc(&y.hc, (size_t)y.hstride * ((size_t)y.hill_cap + 1))) ||
@@ -634,6 +635,13 @@ metad_status metad_create(const metad_params *p, metad_ctx **out)
     cudaMemsetAsync(y.vnh, 0, sizeof(int) * (size_t)n, c->stream);
     cudaMemsetAsync(y.vnn, 0, sizeof(int) * (size_t)n, c->stream);
     cudaMemsetAsync(y.rebuilds, 0, sizeof(unsigned long long), c->stream);
+    {
+        const float Lr[4] = {y.Lhi[0], y.Lhi[1], y.Lhi[2], 0.0f};
+        if ((s = cuda_check(c, cudaMemcpy(y.Lref, Lr, sizeof(Lr), cudaMemcpyHostToDevice), "box upload"))) {
+            metad_destroy(c);
+            return s;
+        }
+    }
     cudaMemsetAsync(y.pos_ref, 0, sizeof(float4) * (size_t)n, c->stream);
     {
         // identity order until the first rebuild, which the set flag forces
@@ -867,11 +875,8 @@ metad_status metad_set_box(metad_ctx *c, const double *box_host)
             if ((s = cuda_check(c, cudaStreamSynchronize(c->stream), "set_box")) || (s = upload_cell_ranks(c)))
                 return s;
         }
-        // every neighbour structure is rebuilt at the next step
-        const int one = 1;
-        if ((s = cuda_check(c, cudaMemcpyAsync(y.flag, &one, sizeof(int), cudaMemcpyHostToDevice, c->stream),
-                            "rebuild flag")))
-            return s;
+        // the Verlet rows stay while the atoms' moves and the box change fit in
+        // the skin (tested on the device at the next step)
         c->have_nbr = false;
     }
     c->have_cv = c->have_bias = false;

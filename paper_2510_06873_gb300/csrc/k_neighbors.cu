@@ -39,11 +39,24 @@ __device__ __forceinline__ int cell_axis(float x, float inv_h, int nc)
 }
 
 // Current positions in the cell order of the last rebuild, and the rebuild
-// test.  Before the first rebuild the flag is already set.
+// test.  Before the first rebuild the flag is already set.  The Verlet rows
+// hold every pair within rc + skin at the last rebuild; a pair's
+// displacement has since changed by at most |dr_i| + |dr_j| + |L - L_ref|
+// (the last term for pairs across the box faces when the box changed), so
+// the rows stay valid while every |dr| <= (skin - |L - L_ref|) / 2.
 __device__ __forceinline__ void gather_check(const Sys &s, Blk k)
 {
     const int t = k.b * blockDim.x + threadIdx.x;
     bool move = false;
+    float thr2 = s.disp_thr2;
+    {
+        const float ex = s.Lhi[0] - __ldg(s.Lref), ey = s.Lhi[1] - __ldg(s.Lref + 1), ez = s.Lhi[2] - __ldg(s.Lref + 2);
+        const float dL2 = ex * ex + ey * ey + ez * ez;
+        if (dL2 > 0.0f) {
+            const float half = 0.5f * (s.skin_eff - sqrtf(dL2));
+            thr2 = half > 0.0f ? half * half : -1.0f;
+        }
+    }
     if (t < s.n) {
         bool bad;
         float4 p = load_wrapped(s, s.perm[t], bad);
@@ -53,7 +66,7 @@ __device__ __forceinline__ void gather_check(const Sys &s, Blk k)
         float dx = mi_f(p.x - r.x, s.halfL[0], s.Lhi[0], s.Llo[0]);
         float dy = mi_f(p.y - r.y, s.halfL[1], s.Lhi[1], s.Llo[1]);
         float dz = mi_f(p.z - r.z, s.halfL[2], s.Lhi[2], s.Llo[2]);
-        move = !(dx * dx + dy * dy + dz * dz <= s.disp_thr2) || p.w != r.w;
+        move = !(dx * dx + dy * dy + dz * dz <= thr2) || p.w != r.w;
     }
     if (__any_sync(0xffffffffu, move) && (threadIdx.x & 31) == 0) atomicOr(s.flag, 1);
 }
@@ -280,7 +293,10 @@ __global__ void __launch_bounds__(kBlockAtoms) k_filter(Sys s)
 __device__ __forceinline__ void clear_flag(const Sys &s)
 {
     if (threadIdx.x != 0) return;
-    if (*s.flag) *s.rebuilds += 1ull;
+    if (*s.flag) {
+        *s.rebuilds += 1ull;
+        for (int a = 0; a < 3; ++a) s.Lref[a] = s.Lhi[a];  // the box of these rows
+    }
     *s.flag = s.always_rebuild ? 1 : 0;
 }
 

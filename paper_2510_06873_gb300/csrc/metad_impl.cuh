@@ -94,6 +94,8 @@ struct Sys {
     int max_vnb;
     int *flag;             // 1: rebuild the cell order and Verlet list this step
     float disp_thr2;       // (skin / 2)^2 with margin: rebuild above it
+    float skin_eff;        // skin with margin
+    float *Lref;           // [3] the box at the last rebuild (float)
     float rv2;             // (rc + skin)^2 with margin: Verlet cutoff
     int always_rebuild;    // skin == 0
     unsigned long long *rebuilds;  // number of rebuilds done

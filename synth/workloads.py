@@ -320,13 +320,21 @@ def served_trace(cfg: int = 5, n_walkers: int = 32, n_requests: int = 2000, rate
     return n, arrivals, walker
 
 
-def npt_frame(system: System, frame: int, strain_sigma: float = 1e-3, sigma: float = 0.05):
+def npt_frame(system: System, frame: int, strain_sigma: float = 1e-3, sigma: float = 0.05, period: int = 0):
     """A frame of a triaxial NPT run: each box length scaled by 1 + e_a,
-    e_a ~ N(0, strain_sigma^2) independently per axis and frame, positions
-    scaled with it (fixed fractional coordinates) plus N(0, sigma^2) noise,
-    wrapped into the new box.  Returns (float32 [N, 4] frame, float64 [3] box)."""
+    positions scaled with it (fixed fractional coordinates) plus N(0, sigma^2)
+    noise, wrapped into the new box.  e_a ~ N(0, strain_sigma^2)
+    independently per axis and frame, or with period > 0 a slow oscillation
+    e_a = strain_sigma sin(2 pi frame / period + phi_a) (phases fixed per
+    system), as a barostat moves the box.  Returns (float32 [N, 4] frame,
+    float64 [3] box)."""
     g = rng(system.cfg, system.sys, 5, frame)
-    e = g.normal(0.0, strain_sigma, size=3)
+    if period > 0:
+        phi = 2.0 * math.pi * rng(system.cfg, system.sys, 6).random(3)
+        e = strain_sigma * np.sin(2.0 * math.pi * frame / period + phi)
+        g.normal(0.0, strain_sigma, size=3)  # keep the noise stream of the iid form
+    else:
+        e = g.normal(0.0, strain_sigma, size=3)
     box = system.box * (1.0 + e)
     eps = g.normal(0.0, sigma, size=(system.n, 3))
     xyz = wrap_to_box(system.base[:, :3].astype(np.float64) * (1.0 + e) + eps, box)

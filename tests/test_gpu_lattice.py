@@ -144,6 +144,24 @@ def test_cells_follow_the_box(dev, system):
     ctx.close()
 
 
+def test_rows_survive_small_box_changes(dev, system):
+    """A slowly moving box keeps the Verlet rows (no rebuild) and the exact
+    neighbour sets; a large jump rebuilds them."""
+    ctx = make_ctx(dev, system, 1, hills=lattice_hills(system, 1, count=50)[:2])
+    for f in range(6):
+        fr, box = synth.npt_frame(system, f, strain_sigma=1e-3, period=400)
+        run(ctx, fr, dev, box)
+        assert np.array_equal(ctx.export_neighbors(), oracle.pairs_cells(fr, box, 3.5))
+    assert ctx.rebuild_count == 1  # the first step only
+    box = system.box * 0.97
+    fr = system.base.copy()
+    fr[:, :3] = synth.wrap_to_box(system.base[:, :3].astype(np.float64) * 0.97, box)
+    run(ctx, fr, dev, box)
+    assert ctx.rebuild_count == 2
+    assert np.array_equal(ctx.export_neighbors(), oracle.pairs_cells(fr, box, 3.5))
+    ctx.close()
+
+
 def test_batched_lattice_systems_equal_single_steps(dev):
     from paper_2510_06873_gb300 import metad
     systems = [synth.wurtzite_system(n, cfg=8, sys=k) for k, n in enumerate((3000, 5000, 7000))]
