@@ -212,14 +212,6 @@ __device__ __forceinline__ void cell_sort_gather(const Sys &s, Blk k)
     for (int c = k.b * blockDim.x + threadIdx.x; c < s.ncell; c += k.nb * blockDim.x) sort_gather_cell(s, c);
 }
 
-__device__ __forceinline__ int axis_offsets(int nc, int *off)
-{
-    if (nc >= 3) { off[0] = -1; off[1] = 0; off[2] = 1; return 3; }
-    if (nc == 2) { off[0] = 0; off[1] = 1; return 2; }
-    off[0] = 0;
-    return 1;
-}
-
 __device__ __forceinline__ int wrap_cell(int c, int nc)
 {
     c += (c < 0) ? nc : 0;
@@ -227,41 +219,125 @@ __device__ __forceinline__ int wrap_cell(int c, int nc)
     return c;
 }
 
+// Stencil offsets along one axis: -1, 0, 1 with three or more cells (each
+// distinct cell once with fewer).
+__device__ __forceinline__ int axis_span(int nc) { return nc >= 3 ? 3 : nc; }
+__device__ __forceinline__ int axis_off(int nc, int idx) { return nc >= 3 ? idx - 1 : idx; }
+
+constexpr int kStencil = 27;
+constexpr int kVerletBatch = 4;  // candidate rounds whose loads are issued together
+
 // Verlet rows {j : r_ij^2 < (rc + skin)^2 (1 + 1e-4)} over the 27 surrounding
-// cells (each distinct cell once): entries with j > i first, then j < i.  A
-// group of kG lanes per atom, lanes over the atoms of each cell,
-// ballot-compacted in cell order; grid-stride over atom groups so an idle
-// launch (no rebuild) retires at once.
+// cells (each distinct cell once): entries with j > i first, then j < i, in
+// stencil-cell order, atoms in cell order.  A group of kG lanes per atom.
+// Atoms are sorted by cell rank, so a cell ranked below the atom's own holds
+// only j < i and one ranked above only j > i: each part walks only its
+// cells (the own cell in both).  The group stages the part's cell starts
+// and the prefix of their counts in shared memory (the lanes look the cells
+// up in parallel); the candidates are then one flat range that the lanes
+// walk kG at a time, each lane finding its cell by advancing along the
+// prefix, so every position load is independent of the others and
+// kVerletBatch rounds are loaded at once.  Ballot compaction keeps the
+// order.  Grid-stride over atom groups so an idle launch (no rebuild)
+// retires at once.
 __device__ __forceinline__ void verlet(const Sys &s, Blk k)
 {
     if (!*s.flag) return;
-    int ox[3], oy[3], oz[3];
-    const int sx = axis_offsets(s.nc[0], ox), sy = axis_offsets(s.nc[1], oy), sz = axis_offsets(s.nc[2], oz);
+    __shared__ int sh_base[kAtomsPerBlock][kStencil];  // start - prefix: j = p + base
+    __shared__ int sh_pre[kAtomsPerBlock][kStencil + 1];
+    const int sx = axis_span(s.nc[0]), sy = axis_span(s.nc[1]), sz = axis_span(s.nc[2]);
+    const int nq = sx * sy * sz;
+    const int g = threadIdx.x / kG;
+    int *base = sh_base[g], *pre = sh_pre[g];
+    // lane l owns the stencil cells q = 4l .. 4l + 3 (in order), so the
+    // prefix of their counts is a local sum plus a scan over the lanes
+    constexpr int kPerLane = (kStencil + kG - 1) / kG;
+    static_assert(kPerLane * kG >= kStencil, "stencil cells per lane");
+    int qoff[kPerLane];
+#pragma unroll
+    for (int r = 0; r < kPerLane; ++r) {
+        const int q = (threadIdx.x & (kG - 1)) * kPerLane + r;
+        const int e = q % sx, b = (q / sx) % sy, c3 = q / (sx * sy);  // once per launch
+        qoff[r] = q < nq ? (axis_off(s.nc[0], e) + 1) | ((axis_off(s.nc[1], b) + 1) << 2) |
+                               ((axis_off(s.nc[2], c3) + 1) << 4)
+                         : -1;
+    }
     const int groups = group_grid(s.n);
     for (int it = 0, blk; (blk = work_item(k, it)) < groups; ++it) {
         const AtomLane a = atom_lane_at(s, blk);
         const int i = a.ok ? a.i : 0;
         const float4 pi = s.pos_s[i];
-        const int xyz = s.xyz_of_rank[s.scell[i]];
+        const int own = s.scell[i];
+        const int xyz = s.xyz_of_rank[own];
         const int cx = xyz & 1023, cy = (xyz >> 10) & 1023, cz = xyz >> 20;
+        int cell_r[kPerLane], start_r[kPerLane], count_r[kPerLane];
+#pragma unroll
+        for (int r = 0; r < kPerLane; ++r) {
+            cell_r[r] = -1;
+            start_r[r] = count_r[r] = 0;
+            if (qoff[r] >= 0) {
+                const int o = qoff[r];
+                const int c = s.rank_of_xyz[(wrap_cell(cz + ((o >> 4) & 3) - 1, s.nc[2]) * s.nc[1] +
+                                             wrap_cell(cy + ((o >> 2) & 3) - 1, s.nc[1])) * s.nc[0] +
+                                            wrap_cell(cx + (o & 3) - 1, s.nc[0])];
+                cell_r[r] = c;
+                start_r[r] = s.cell_start[c];
+                count_r[r] = s.cell_start[c + 1] - start_r[r];
+            }
+        }
         int *vrow = s.vnbr + (size_t)i * s.max_vnb;
         int cnt = 0, nup = 0;
 #pragma unroll 1
         for (int part = 0; part < 2; ++part) {
-            for (int q = 0; q < sx * sy * sz; ++q) {
-                const int e = q % sx, b = (q / sx) % sy, c3 = q / (sx * sy);
-                const int c = s.rank_of_xyz[(wrap_cell(cz + oz[c3], s.nc[2]) * s.nc[1] +
-                                             wrap_cell(cy + oy[b], s.nc[1])) * s.nc[0] +
-                                            wrap_cell(cx + ox[e], s.nc[0])];
-                const int j0 = s.cell_start[c], j1 = s.cell_start[c + 1];
-                const int span = a.ok ? j1 - j0 : 0;
-                const int smax = __reduce_max_sync(0xffffffffu, span);
-                for (int base = 0; base < smax; base += kG) {
-                    const int j = j0 + base + a.l;
+            // the part's cells: ranks >= own (j > i), then <= own (j < i)
+            int loc[kPerLane], tot = 0;
+#pragma unroll
+            for (int r = 0; r < kPerLane; ++r) {
+                const bool mine = cell_r[r] >= 0 && (part == 0 ? cell_r[r] >= own : cell_r[r] <= own);
+                loc[r] = tot;
+                tot += mine ? count_r[r] : 0;
+            }
+            int incl = tot;  // inclusive scan of the lane totals within the group
+#pragma unroll
+            for (int o = 1; o < kG; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o, kG);
+                if (a.l >= o) incl += y;
+            }
+            const int excl = incl - tot;
+            __syncwarp();  // the previous part's table is no longer read
+#pragma unroll
+            for (int r = 0; r < kPerLane; ++r) {
+                const int q = a.l * kPerLane + r;
+                if (q < nq) {
+                    pre[q] = excl + loc[r];
+                    base[q] = start_r[r] - (excl + loc[r]);
+                }
+            }
+            if (a.l == kG - 1) pre[nq] = incl;
+            __syncwarp();
+            const int T = a.ok ? pre[nq] : 0;
+            const int tmax = __reduce_max_sync(0xffffffffu, T);
+            int q = 0;
+            for (int base0 = 0; base0 < tmax; base0 += kG * kVerletBatch) {
+                int jb[kVerletBatch];
+                float4 pb[kVerletBatch];
+#pragma unroll
+                for (int u = 0; u < kVerletBatch; ++u) {
+                    const int p = base0 + u * kG + a.l;
+                    jb[u] = -1;
+                    if (p < T) {
+                        while (p >= pre[q + 1]) ++q;
+                        jb[u] = p + base[q];
+                        pb[u] = s.pos_s[jb[u]];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kVerletBatch; ++u) {
+                    if (base0 + u * kG >= tmax) break;  // warp-uniform
+                    const int j = jb[u];
                     bool in = false;
-                    if (base + a.l < span && (part == 0 ? j > i : j < i)) {
-                        const float4 pj = s.pos_s[j];
-                        Vec3<float> d = displacement<float>(s, pi, pj);
+                    if (j >= 0 && (part == 0 ? j > i : j < i)) {
+                        Vec3<float> d = displacement<float>(s, pi, pb[u]);
                         in = fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z)) < s.rv2;
                     }
                     const unsigned gm = group_mask_bits(__ballot_sync(0xffffffffu, in));
@@ -426,7 +502,7 @@ int grid_blocks(const Sys &s, int kind, int persist_cap)
     case GK_ATOM256_CAP: return capped((s.n + 255) / 256);
     case GK_SCAN_TILES: return (s.ncell + kScanTile - 1) / kScanTile;
     case GK_CELL128_CAP: return capped((s.ncell + 127) / 128);
-    case GK_GROUPS_CAP: return capped(persist_grid(s.n));
+    case GK_GROUPS_CAP: return persist_grid(s.n);  // Verlet rows: up to 16 blocks per SM
     case GK_ONE: return 1;
     case GK_GROUPS: {
         const int g = group_grid(s.n);
