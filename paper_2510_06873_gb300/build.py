@@ -54,7 +54,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
     os.makedirs(BUILD_DIR, exist_ok=True)
     cc = nvcc()
-    headers = [os.path.join(CSRC, "metad_impl.cuh"), os.path.join(INCLUDE, "metad.h")]
+    headers = [os.path.join(CSRC, "metad_impl.cuh"), os.path.join(CSRC, "hills.cuh"), os.path.join(INCLUDE, "metad.h")]
     srcs = [s for s in SOURCES if os.path.exists(os.path.join(CSRC, s))]
     jobs = []
     objs = []

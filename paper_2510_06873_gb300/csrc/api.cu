@@ -1081,9 +1081,32 @@ metad_status metad_export_neighbors(metad_ctx *c, int64_t *pairs_host, int64_t c
 
 namespace {
 
+// The torsion and nearest-distance families' whole step as one launch
+// (systems of at most kFuseAtoms atoms): CVs, bias, deposit and forces.
+metad_status gcv_step_fused(metad_ctx *c, const float *pos_dev, float *forces_dev, int32_t accumulate,
+                            int32_t deposit)
+{
+    metad_status s = check_usable(c);
+    if (s) return s;
+    if (!pos_dev || !forces_dev) return fail(c, METAD_ERR_INVALID, "NULL buffer");
+    if (!c->atoms_set) return fail(c, METAD_ERR_STATE, "step before set_cv_atoms");
+    if (deposit && c->K >= c->p.hill_capacity) return fail(c, METAD_ERR_CAPACITY, "hill list full");
+    c->sys.pos_in = reinterpret_cast<const float4 *>(pos_dev);
+    {
+        StageScope t(c, ST_CV_FWD, 1);
+        metad::launch_gcv_step(c->sys, c->K, forces_dev, accumulate ? 1 : 0, deposit ? 1 : 0, c->fp64, c->stream);
+    }
+    if ((s = launched(c, "step"))) return s;
+    c->have_nbr = c->have_cv = c->have_bias = true;
+    if (deposit) c->K += 1;
+    return METAD_OK;
+}
+
 metad_status step_direct(metad_ctx *c, const float *pos_dev, float *forces_dev, int32_t accumulate, int32_t deposit)
 {
     metad_status s;
+    if (c && !c->failed && c->p.cv_kind != METAD_CV_COORDINATION && c->p.n_atoms <= metad::kFuseAtoms)
+        return gcv_step_fused(c, pos_dev, forces_dev, accumulate, deposit);
     if ((s = metad_build_neighbors(c, pos_dev))) return s;
     if ((s = metad_cv_forward(c, nullptr, nullptr))) return s;
     if ((s = metad_bias_eval(c, nullptr, nullptr, nullptr))) return s;
@@ -1455,11 +1478,19 @@ metad_status metad_batch_step(metad_batch *b, const float *const *pos_dev, float
     metad::BatchView rows[metad::kGridKinds];
     for (int g = 0; g < metad::kGridKinds; ++g) rows[g] = metad::BatchView{dsys, dpre + g * (n + 1), n};
     if (b->kind != METAD_CV_COORDINATION) {
-        metad::launch_batch_gcv(rows[metad::GK_ONE], totals[metad::GK_ONE], b->fp64, b->stream);
-        metad::launch_batch_bias(rows[metad::GK_HILLS], totals[metad::GK_HILLS], 0, b->stream);
-        metad::launch_batch_gcv_forces(rows[metad::GK_ATOM256], totals[metad::GK_ATOM256], b->stream);
-        if (any_deposit) metad::launch_batch_bias(rows[metad::GK_DEPOSIT], totals[metad::GK_DEPOSIT], 1, b->stream);
-        b->launches += 3 + (any_deposit ? 1 : 0);
+        bool fuse = true;
+        for (int k = 0; k < n; ++k) fuse = fuse && b->ctx[k]->p.n_atoms <= metad::kFuseAtoms;
+        if (fuse) {  // one launch: CVs, hills, deposits and forces
+            metad::launch_batch_gcv_step(rows[metad::GK_HILLS], totals[metad::GK_HILLS], b->fp64, b->stream);
+            b->launches += 1;
+        } else {
+            metad::launch_batch_gcv(rows[metad::GK_ONE], totals[metad::GK_ONE], b->fp64, b->stream);
+            metad::launch_batch_bias(rows[metad::GK_HILLS], totals[metad::GK_HILLS], 0, b->stream);
+            metad::launch_batch_gcv_forces(rows[metad::GK_ATOM256], totals[metad::GK_ATOM256], b->stream);
+            if (any_deposit)
+                metad::launch_batch_bias(rows[metad::GK_DEPOSIT], totals[metad::GK_DEPOSIT], 1, b->stream);
+            b->launches += 3 + (any_deposit ? 1 : 0);
+        }
     } else {
     metad::launch_batch_gather(rows[metad::GK_ATOM256], totals[metad::GK_ATOM256], b->stream);
     metad::launch_batch_rebuild(rows, totals, b->stream);

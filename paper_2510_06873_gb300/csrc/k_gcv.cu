@@ -21,7 +21,7 @@
 #include <float.h>
 #include <limits.h>
 
-#include "metad_impl.cuh"
+#include "hills.cuh"
 
 namespace metad {
 
@@ -95,7 +95,7 @@ __device__ __forceinline__ double real_atan2(double y, double x) { return atan2(
 // in `real` (float: a dependent FP64 chain is long on this part, and the
 // angle of float32 positions needs no more).
 template <typename real>
-__device__ void torsion(const Sys &s, int d, bool &bad)
+__device__ void torsion(const Sys &s, int d, bool &bad, double *xo, double *go)
 {
     const int *q = s.cv_atoms + 4 * d;
     double ra[3], rb[3], rc[3], rd[3], e1[3], e2[3], e3[3];
@@ -121,13 +121,13 @@ __device__ void torsion(const Sys &s, int d, bool &bad)
     const real T = dot3(b1, n2);
     const real y = m * T;
     const real D = x * x + y * y;
-    double *g = s.gcv + 16 * d;
+    double *g = go + 16 * d;
     if (D == (real)0 || m == (real)0) {
-        s.scal[kS0 + d] = 0.0;
+        xo[d] = 0.0;
         for (int k = 0; k < 12; ++k) g[k] = 0.0;
         return;
     }
-    s.scal[kS0 + d] = (double)real_atan2(y, x);
+    xo[d] = (double)real_atan2(y, x);
     const real b12 = dot3(b1, b2), b23 = dot3(b2, b3), b13 = dot3(b1, b3);
     const real invD = (real)1 / D, inv_m = (real)1 / m;
     const real cx = x * invD, cy = y * invD;  // dphi = cx dy - cy dx
@@ -202,9 +202,9 @@ __device__ __forceinline__ double soft_weight(const Sys &s, double r, double rmi
     return exp(-s.sm_beta * (r - rmin));
 }
 
-// Nearest-distance CV d (all threads of the block): gcv[16 d] holds the
+// Nearest-distance CV d (all threads of the block): go[16 d] holds the
 // nearest slot, r_min, the soft-minimum normaliser Z and d s/d r_ref.
-__device__ void nearest(const Sys &s, int d, bool &bad)
+__device__ void nearest(const Sys &s, int d, bool &bad, double *xo, double *go)
 {
     __shared__ double shv[kGcvThreads / 32];
     __shared__ int sha[kGcvThreads / 32];
@@ -223,13 +223,13 @@ __device__ void nearest(const Sys &s, int d, bool &bad)
     }
     block_argmin(best, arg, shv, sha);
     const double rmin = sqrt(best);
-    double *g = s.gcv + 16 * d;
+    double *g = go + 16 * d;
     if (s.sm_beta <= 0.0) {
         if (threadIdx.x == 0) {
             double pj[3], dv[3];
             atom_pos(s, cand[arg], pj, bad);
             disp(s, po, pj, dv);
-            s.scal[kS0 + d] = rmin;
+            xo[d] = rmin;
             g[0] = (double)arg;
             g[1] = rmin;
             g[2] = 1.0;
@@ -255,7 +255,7 @@ __device__ void nearest(const Sys &s, int d, bool &bad)
     block_sum4(acc, sh4);
     if (threadIdx.x == 0) {
         const double Z = acc[0];
-        s.scal[kS0 + d] = rmin - log(Z) / s.sm_beta;
+        xo[d] = rmin - log(Z) / s.sm_beta;
         g[0] = (double)arg;
         g[1] = rmin;
         g[2] = Z;
@@ -265,28 +265,37 @@ __device__ void nearest(const Sys &s, int d, bool &bad)
     }
 }
 
+// The CVs into xo[d] and their gradient terms into go[16 d ...] (shared or
+// global memory).
 template <typename real>
-__device__ void gcv_forward(const Sys &s)
+__device__ void gcv_eval(const Sys &s, double *xo, double *go)
 {
     bool bad = false;
     if (s.kind == kKindTorsion) {
-        if (threadIdx.x < s.ncv) torsion<real>(s, threadIdx.x, bad);
+        if (threadIdx.x < s.ncv) torsion<real>(s, threadIdx.x, bad, xo, go);
     } else {
-        for (int d = 0; d < s.ncv; ++d) nearest(s, d, bad);
+        for (int d = 0; d < s.ncv; ++d) nearest(s, d, bad, xo, go);
     }
-    if (threadIdx.x == 0 && s.ncv == 1) s.scal[kS1] = 0.0;
     if (bad) atomicOr(s.err, kErrNonFinite);
 }
 
-// F_i = (accumulate ? F_i : 0) - scale sum_d dV/ds_d ds_d/dr_i.
-__device__ void gcv_forces(const Sys &s, Blk blk)
+template <typename real>
+__device__ void gcv_forward(const Sys &s)
+{
+    gcv_eval<real>(s, s.scal + kS0, s.gcv);
+    if (threadIdx.x == 0 && s.ncv == 1) s.scal[kS1] = 0.0;
+}
+
+// F_i = (accumulate ? F_i : 0) - scale sum_d dV/ds_d ds_d/dr_i, with the
+// gradient terms gterms of the CV pass.
+__device__ void gcv_forces(const Sys &s, Blk blk, const double *gterms)
 {
     const int *cand = s.cv_atoms + s.ncv;
     for (int i = blk.b * kGcvThreads + threadIdx.x; i < s.n; i += blk.nb * kGcvThreads) {
         double f[3] = {0.0, 0.0, 0.0};
         for (int d = 0; d < s.ncv; ++d) {
             const double dv = s.scal[kDV0 + d];
-            const double *g = s.gcv + 16 * d;
+            const double *g = gterms + 16 * d;
             if (s.kind == kKindTorsion) {
                 for (int q = 0; q < 4; ++q)
                     if (s.cv_atoms[4 * d + q] == i)
@@ -320,7 +329,44 @@ __device__ void gcv_forces(const Sys &s, Blk blk)
 template <typename real>
 __global__ void __launch_bounds__(kGcvThreads) k_gcv_forward(Sys s) { gcv_forward<real>(s); }
 
-__global__ void __launch_bounds__(kGcvThreads) k_gcv_forces(Sys s) { gcv_forces(s, own_blk()); }
+__global__ void __launch_bounds__(kGcvThreads) k_gcv_forces(Sys s) { gcv_forces(s, own_blk(), s.gcv); }
+
+// The whole step in one launch (systems of up to kFuseAtoms atoms): every
+// block evaluates the CVs (a few atoms, or one pass over the candidates)
+// into shared memory and sums its share of the hills there; block 0
+// publishes the CVs; the last block to finish the hill sum (which also
+// deposits, if asked) writes every atom's force from its own copy of the
+// CV gradient terms.  The same arithmetic as the three-kernel path, so the
+// same bits.
+template <typename real>
+__device__ void gcv_step(const Sys &s, Blk blk)
+{
+    __shared__ double xs[kMaxCv];
+    __shared__ double gs[16 * 2];
+    if (threadIdx.x < kMaxCv) xs[threadIdx.x] = 0.0;
+    if (threadIdx.x < 16 * 2) gs[threadIdx.x] = 0.0;
+    __syncthreads();
+    gcv_eval<real>(s, xs, gs);
+    __syncthreads();
+    if (blk.b == 0) {
+        if (threadIdx.x < kMaxCv) s.scal[kS0 + threadIdx.x] = xs[threadIdx.x];
+        if (threadIdx.x < 16 * s.ncv) s.gcv[threadIdx.x] = gs[threadIdx.x];
+    }
+    if (!hill_sum(s, blk, xs, s.scal + kV, s.deposit)) return;
+    __syncthreads();  // thread 0 of this block wrote dV/ds
+    gcv_forces(s, Blk{0, 1}, gs);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kGcvThreads) k_gcv_step(Sys s) { gcv_step<real>(s, own_blk()); }
+
+template <typename real>
+__global__ void __launch_bounds__(kGcvThreads) kb_gcv_step(BatchView v)
+{
+    Blk k;
+    const Sys &s = v.sys[batch_system(v, k)];
+    gcv_step<real>(s, k);
+}
 
 template <typename real>
 __global__ void __launch_bounds__(kGcvThreads) kb_gcv_forward(BatchView v)
@@ -334,7 +380,7 @@ __global__ void __launch_bounds__(kGcvThreads) kb_gcv_forces(BatchView v)
 {
     Blk k;
     const Sys &s = v.sys[batch_system(v, k)];
-    gcv_forces(s, k);
+    gcv_forces(s, k, s.gcv);
 }
 
 }  // namespace
@@ -368,6 +414,30 @@ void launch_batch_gcv(const BatchView &one, int one_total, int fp64, cudaStream_
 void launch_batch_gcv_forces(const BatchView &atoms, int atom_total, cudaStream_t st)
 {
     if (atom_total > 0) kb_gcv_forces<<<atom_total, kGcvThreads, 0, st>>>(atoms);
+}
+
+void launch_gcv_step(const Sys &s, int K, float *F, int accumulate, int deposit, int fp64, cudaStream_t st)
+{
+    Sys t = s;
+    t.K = K;
+    t.F_out = F;
+    t.accumulate = accumulate;
+    t.fscale = 1.0;
+    t.deposit = deposit;
+    const int nb = bias_blocks(K);
+    if (fp64)
+        k_gcv_step<double><<<nb, kGcvThreads, 0, st>>>(t);
+    else
+        k_gcv_step<float><<<nb, kGcvThreads, 0, st>>>(t);
+}
+
+void launch_batch_gcv_step(const BatchView &hills, int hill_total, int fp64, cudaStream_t st)
+{
+    if (hill_total <= 0) return;
+    if (fp64)
+        kb_gcv_step<double><<<hill_total, kGcvThreads, 0, st>>>(hills);
+    else
+        kb_gcv_step<float><<<hill_total, kGcvThreads, 0, st>>>(hills);
 }
 
 }  // namespace metad

@@ -252,6 +252,11 @@ void launch_gcv_forward(const Sys &s, int fp64, cudaStream_t st);
 void launch_gcv_forces(const Sys &s, float *F, int accumulate, double scale, cudaStream_t st);
 void launch_batch_gcv(const BatchView &one, int one_total, int fp64, cudaStream_t st);
 void launch_batch_gcv_forces(const BatchView &atoms, int atom_total, cudaStream_t st);
+// The whole small-system step in one launch (CVs, hills, deposit, forces),
+// for systems of at most kFuseAtoms atoms.
+constexpr int kFuseAtoms = 32768;
+void launch_gcv_step(const Sys &s, int K, float *F, int accumulate, int deposit, int fp64, cudaStream_t st);
+void launch_batch_gcv_step(const BatchView &hills, int hill_total, int fp64, cudaStream_t st);
 
 int bias_blocks(int K);
 

@@ -225,7 +225,7 @@ def test_batched_walkers_equal_single_steps(dev):
             assert torch.equal(Fb[k], Fs[k])
     for k in range(n):
         assert all(np.array_equal(a, b) for a, b in zip(ctxs[k].get_hills(), solo[k].get_hills()))
-    assert batch.launch_count <= 3 * 4 + 3
+    assert batch.launch_count == 3 * 1 + 3  # one fused launch per step, one collect per read
     batch.close()
     for c in ctxs + solo:
         c.close()
@@ -285,6 +285,34 @@ def test_trajectory_fes_and_graph_replay(dev):
         assert all(np.array_equal(x, y) for x, y in zip(a, b))
     g.close()
     d.close()
+
+
+def test_large_system_takes_the_three_kernel_path(dev):
+    """Above the fused-step size the step runs as CV pass, hill kernel and
+    force pass; it agrees with the oracle and with the separate calls."""
+    from paper_2510_06873_gb300 import metad
+    n = 40000
+    g = np.random.default_rng(8)
+    box = np.array([80.0, 80.0, 80.0])
+    fr = np.zeros((n, 4), dtype=np.float32)
+    fr[:, :3] = g.uniform(0, 80, (n, 3))
+    atoms = np.concatenate([[7], g.choice(np.arange(100, n), 3000, replace=False)]).astype(np.int32)
+    p = metad.params_for(n, box, n_cv=1, sigma=(0.1,), cv_kind="nearest", softmin_beta=3.0,
+                         stream=_stream(dev).cuda_stream)
+    ctx = metad.Metad(p)
+    ctx.set_cv_atoms(atoms)
+    s0 = og.cvs(fr, box, "min_dist", atoms, 1, 3.0)[0][0]
+    c = (s0 + np.linspace(-1.0, 1.0, 60))[:, None]  # hills around the CV
+    w = oracle.deposit_sequence(c, (0.1,), 1.0, kbdt_of(10.0))
+    ctx.load_hills(c, w)
+    l0 = ctx.launch_count
+    cv, V, dV, F = run_step(ctx, fr, dev)
+    assert ctx.launch_count - l0 == 3
+    ref = og.step(fr, box, "min_dist", atoms, 1, c, w, (0.1,), beta=3.0)
+    assert abs(cv[0] - ref["s"][0]) <= TOL * ref["s"][0]
+    check_bias(V, dV, ref["V"], ref["dV"], 1.0, (0.1,))
+    check_forces(F, ref["F"])
+    ctx.close()
 
 
 def test_small_family_errors(dev):
