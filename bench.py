@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--atoms", type=int, default=1_000_000, help="workload size (1M is the reported config)")
+    ap.add_argument("--skin", type=float, default=1.0,
+                    help="Verlet skin in A (1.0 is the reported config; 0 rebuilds the rows every step)")
     ap.add_argument("--hills", type=int, default=None, help="live hills (default: the workload's 20,000)")
     ap.add_argument("--hills-folded", type=int, default=None, help="hills folded into the grid (default 20,000)")
     ap.add_argument("--max-neighbors", type=int, default=64, help="per-atom neighbour-row capacity")
@@ -298,7 +300,7 @@ def run_metad(args):
     lo, hi = s_ref - 16 * sig, s_ref + 16 * sig
     params = metad.params_for(n, system.box, n_cv=2, sigma=mp.sigma, grid=(cfgp["grid_n"], lo, hi),
                               hill_capacity=cfgp["hills"] + 1024, stream=stream.cuda_stream,
-                              max_neighbors=args.max_neighbors)
+                              max_neighbors=args.max_neighbors, skin=args.skin)
     ctx = metad.Metad(params)
     K1 = cfgp["hills_folded"] if args.hills_folded is None else args.hills_folded
     K2 = cfgp["hills"] if args.hills is None else args.hills
