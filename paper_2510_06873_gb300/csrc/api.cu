@@ -19,6 +19,10 @@ struct metad_ctx {
     metad_params p{};
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // metad_step runs the hill kernel on a side stream, concurrently with the
+    // adjoint (which does not need dV/ds), joined before the pair forces
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     Sys sys{};
     int fp64 = 0;
     int K = 0;
@@ -109,19 +113,20 @@ const char *kStageNames[ST_COUNT] = {"gather",      "neighbors",    "cv_fwd",  "
 // and counts the kernels launched.
 struct StageScope {
     metad_ctx *c;
+    cudaStream_t st;
     int idx = -1;
-    StageScope(metad_ctx *ctx, int stage, int kernels) : c(ctx)
+    StageScope(metad_ctx *ctx, int stage, int kernels, cudaStream_t on = nullptr) : c(ctx), st(on ? on : ctx->stream)
     {
         c->launches += kernels;
         if (c->prof_on && c->prof_used < c->prof_cap) {
             idx = c->prof_used++;
             c->prof_stage[idx] = stage;
-            cudaEventRecord(c->prof_ev[2 * idx], c->stream);
+            cudaEventRecord(c->prof_ev[2 * idx], st);
         }
     }
     ~StageScope()
     {
-        if (idx >= 0) cudaEventRecord(c->prof_ev[2 * idx + 1], c->stream);
+        if (idx >= 0) cudaEventRecord(c->prof_ev[2 * idx + 1], st);
     }
 };
 
@@ -540,6 +545,9 @@ metad_status metad_destroy(metad_ctx *c)
     if (c->err_pinned) cudaFreeHost(c->err_pinned);
     for (auto &g : c->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->side) cudaStreamDestroy(c->side);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     cudaGetLastError();
     delete c;
@@ -570,6 +578,14 @@ metad_status metad_create(const metad_params *p, metad_ctx **out)
         c->own_stream = true;
     }
     if ((s = setup_system(c))) {
+        metad_destroy(c);
+        return s;
+    }
+    int prio_low = 0, prio_high = 0;  // the side stream outranks the adjoint's blocks
+    cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
+    if ((s = cuda_check(c, cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_high), "side stream")) ||
+        (s = cuda_check(c, cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming), "event")) ||
+        (s = cuda_check(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming), "event"))) {
         metad_destroy(c);
         return s;
     }
@@ -1102,11 +1118,52 @@ metad_status gcv_step_fused(metad_ctx *c, const float *pos_dev, float *forces_de
     return METAD_OK;
 }
 
+// The coordination family's step with the hill kernel on the side stream,
+// concurrent with the adjoint pass: the adjoint needs only the CV pass's
+// records, and the pair forces (which need dV/ds) wait for the join.  The
+// same kernels and arguments as the sequential calls, so the same bits.
+metad_status step_overlapped(metad_ctx *c, const float *pos_dev, float *forces_dev, int32_t accumulate,
+                             int32_t deposit)
+{
+    metad_status s;
+    if ((s = metad_build_neighbors(c, pos_dev))) return s;
+    if ((s = metad_cv_forward(c, nullptr, nullptr))) return s;
+    if (!forces_dev) return fail(c, METAD_ERR_INVALID, "forces_dev is NULL");
+    if ((s = cuda_check(c, cudaEventRecord(c->ev_fork, c->stream), "fork")) ||
+        (s = cuda_check(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0), "fork")))
+        return s;
+    {
+        StageScope t(c, ST_BIAS, 1, c->side);
+        metad::launch_bias(c->sys, c->K, c->sys.scal + metad::kS0, c->sys.scal + metad::kV, 0, c->side);
+    }
+    if ((s = cuda_check(c, cudaEventRecord(c->ev_join, c->side), "join"))) return s;
+    if (c->p.n_cv == 2) {
+        StageScope t(c, ST_ADJ, 1);
+        metad::launch_adjoint(c->sys, c->fp64, c->stream);
+    }
+    if ((s = cuda_check(c, cudaStreamWaitEvent(c->stream, c->ev_join, 0), "join"))) return s;
+    {
+        StageScope t(c, ST_FORCE, 1);
+        metad::launch_force_pairs(c->sys, c->fp64, 1.0, c->stream);
+    }
+    {
+        StageScope t(c, ST_FGATHER, 1);
+        metad::launch_force_gather(c->sys, c->fp64, forces_dev, accumulate ? 1 : 0, c->stream);
+    }
+    if ((s = launched(c, "step"))) return s;
+    c->have_bias = true;
+    c->forces_done = true;
+    if (deposit && (s = metad_deposit_hill(c, nullptr, nullptr))) return s;
+    return METAD_OK;
+}
+
 metad_status step_direct(metad_ctx *c, const float *pos_dev, float *forces_dev, int32_t accumulate, int32_t deposit)
 {
     metad_status s;
     if (c && !c->failed && c->p.cv_kind != METAD_CV_COORDINATION && c->p.n_atoms <= metad::kFuseAtoms)
         return gcv_step_fused(c, pos_dev, forces_dev, accumulate, deposit);
+    if (c && !c->failed && c->p.cv_kind == METAD_CV_COORDINATION)
+        return step_overlapped(c, pos_dev, forces_dev, accumulate, deposit);
     if ((s = metad_build_neighbors(c, pos_dev))) return s;
     if ((s = metad_cv_forward(c, nullptr, nullptr))) return s;
     if ((s = metad_bias_eval(c, nullptr, nullptr, nullptr))) return s;
@@ -1342,6 +1399,8 @@ struct metad_batch {
     cudaEvent_t ev[kRing] = {};
     int slot = 0;
     double *hout = nullptr;
+    cudaStream_t side = nullptr;  // the hill kernel, concurrent with the adjoint
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int64_t launches = 0;
     bool stepped = false;  // the device table holds the last step's descriptors
     std::string last_error;
@@ -1369,6 +1428,9 @@ metad_status metad_batch_destroy(metad_batch *b)
         if (b->host[k]) cudaFreeHost(b->host[k]);
     }
     if (b->hout) cudaFreeHost(b->hout);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
+    if (b->side) cudaStreamDestroy(b->side);
     if (b->dev) cudaFree(b->dev);
     if (b->dout) cudaFree(b->dout);
     cudaGetLastError();
@@ -1410,6 +1472,11 @@ metad_status metad_batch_create(metad_ctx *const *ctxs, int32_t n, metad_batch *
     for (int k = 0; ok && k < metad_batch::kRing; ++k)
         ok = cudaMallocHost(&b->host[k], b->table_bytes) == cudaSuccess &&
              cudaEventCreateWithFlags(&b->ev[k], cudaEventDisableTiming) == cudaSuccess;
+    int prio_low = 0, prio_high = 0;  // the side stream outranks the adjoint's blocks
+    cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
+    ok = ok && cudaStreamCreateWithPriority(&b->side, cudaStreamNonBlocking, prio_high) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         metad_batch_destroy(b);
@@ -1496,10 +1563,18 @@ metad_status metad_batch_step(metad_batch *b, const float *const *pos_dev, float
     metad::launch_batch_rebuild(rows, totals, b->stream);
     metad::launch_batch_cv(rows[metad::GK_GROUPS], totals[metad::GK_GROUPS], rows[metad::GK_CV], totals[metad::GK_CV],
                            rows[metad::GK_SUM], totals[metad::GK_SUM], b->fp64, b->ncv, b->stream);
-    metad::launch_batch_bias(rows[metad::GK_HILLS], totals[metad::GK_HILLS], 0, b->stream);
+    // the hill kernel on the side stream, concurrent with the adjoint
+    cudaEventRecord(b->ev_fork, b->stream);
+    cudaStreamWaitEvent(b->side, b->ev_fork, 0);
+    metad::launch_batch_bias(rows[metad::GK_HILLS], totals[metad::GK_HILLS], 0, b->side);
+    cudaEventRecord(b->ev_join, b->side);
     metad::launch_batch_force(rows[metad::GK_GROUPS], totals[metad::GK_GROUPS], rows[metad::GK_ATOM32],
                               totals[metad::GK_ATOM32], rows[metad::GK_ATOM128], totals[metad::GK_ATOM128], b->fp64,
-                              b->ncv, b->ctx[0]->sys.virial, b->stream);
+                              b->ncv, b->ctx[0]->sys.virial, b->stream, 1);
+    cudaStreamWaitEvent(b->stream, b->ev_join, 0);
+    metad::launch_batch_force(rows[metad::GK_GROUPS], totals[metad::GK_GROUPS], rows[metad::GK_ATOM32],
+                              totals[metad::GK_ATOM32], rows[metad::GK_ATOM128], totals[metad::GK_ATOM128], b->fp64,
+                              b->ncv, b->ctx[0]->sys.virial, b->stream, 2);
     if (any_deposit) metad::launch_batch_bias(rows[metad::GK_DEPOSIT], totals[metad::GK_DEPOSIT], 1, b->stream);
     b->launches += 1 + 8 + 2 + 1 + (b->ncv == 2 ? 3 : 2) + (any_deposit ? 1 : 0);
     }

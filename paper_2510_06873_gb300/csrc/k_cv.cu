@@ -1106,16 +1106,20 @@ void launch_batch_cv(const BatchView &groups, int group_total, const BatchView &
 }
 
 void launch_batch_force(const BatchView &groups, int group_total, const BatchView &adj, int adj_total,
-                        const BatchView &pairs, int pair_total, int fp64, int ncv, int virial, cudaStream_t st)
+                        const BatchView &pairs, int pair_total, int fp64, int ncv, int virial, cudaStream_t st,
+                        int part)
 {
     if (group_total <= 0) return;
+    const bool adjoint = part != 2 && ncv == 2, forces = part != 1;
     if (fp64) {
-        if (ncv == 2) kb_adjoint<double><<<adj_total, kBlockAtoms, 0, st>>>(adj);
+        if (adjoint) kb_adjoint<double><<<adj_total, kBlockAtoms, 0, st>>>(adj);
+        if (!forces) return;
         if (virial) kb_force_pairs<double, true><<<pair_total, kBlockAtoms, 0, st>>>(pairs);
         else kb_force_pairs<double><<<pair_total, kBlockAtoms, 0, st>>>(pairs);
         kb_force_gather<double><<<group_total, kBlockAtoms, 0, st>>>(groups);
     } else {
-        if (ncv == 2) kb_adjoint<float><<<adj_total, kBlockAtoms, 0, st>>>(adj);
+        if (adjoint) kb_adjoint<float><<<adj_total, kBlockAtoms, 0, st>>>(adj);
+        if (!forces) return;
         if (virial) kb_force_pairs<float, true><<<pair_total, kBlockAtoms, 0, st>>>(pairs);
         else kb_force_pairs<float><<<pair_total, kBlockAtoms, 0, st>>>(pairs);
         kb_force_gather<float><<<group_total, kBlockAtoms, 0, st>>>(groups);

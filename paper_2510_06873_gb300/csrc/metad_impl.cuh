@@ -226,8 +226,10 @@ void launch_batch_cv(const BatchView &groups, int group_total, const BatchView &
                      const BatchView &sums, int sum_total, int fp64, int ncv, cudaStream_t st);
 void launch_cv_sum(const Sys &s, int fp64, cudaStream_t st);
 void launch_batch_bias(const BatchView &v, int total, int deposit, cudaStream_t st);
+// part 0: adjoint, pair forces and gather; 1: the adjoint only; 2: the rest
 void launch_batch_force(const BatchView &groups, int group_total, const BatchView &adj, int adj_total,
-                        const BatchView &pairs, int pair_total, int fp64, int ncv, int virial, cudaStream_t st);
+                        const BatchView &pairs, int pair_total, int fp64, int ncv, int virial, cudaStream_t st,
+                        int part = 0);
 void launch_batch_collect(const BatchView &v, double *out, cudaStream_t st);
 
 // Launch entry points (stream-ordered, no host synchronisation).
