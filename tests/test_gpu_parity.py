@@ -324,6 +324,15 @@ def test_accumulate_scale_and_determinism(dev):
     ctx.step(pos, F2)
     ctx.sync()
     assert torch.equal(F1, F2)
+    # the separate calls (sequential) give the step's bits (its hill kernel
+    # runs concurrently with the adjoint on a side stream)
+    F3 = torch.zeros_like(F1)
+    ctx.build_neighbors(pos)
+    ctx.cv_forward(want_host=False)
+    ctx.bias_eval(want_host=False)
+    ctx.bias_forces(F3)
+    ctx.sync()
+    assert torch.equal(F3, F1)
     base = torch.full_like(F1, 0.25)
     ctx.build_neighbors(pos)
     ctx.cv_forward(want_host=False)
