@@ -342,6 +342,7 @@ metad_status setup_system(metad_ctx *c)
     if (c->p.n_cv == 2) y.sigma[1] = c->p.sigma[1];
     if (c->p.lattice_cvs)
         for (int a = 0; a < 3; ++a) y.sigma[c->p.n_cv + a] = c->p.sigma_lattice[a];
+    for (int d = 0; d < metad::kMaxCv; ++d) y.inv2v[d] = 0.5 / (y.sigma[d] * y.sigma[d]);
     y.w0 = c->p.w0;
     y.kbdt = c->p.kB * c->p.temperature * (c->p.biasfactor - 1.0);
     y.grid_on = c->p.grid_on;

@@ -10,7 +10,7 @@ namespace metad {
 
 // V and dV/ds at xin into out (V, then dV/ds_d, kMaxCv of them); with
 // deposit, also appends the well-tempered hill there as hill s.K.  s.D
-// dimensions (at most kMaxCv).  Every block sums its share of the hills; the
+// dimensions (at most kMaxCv).  Every block sums its chunk of the hills; the
 // last block to finish adds the block partials in block order and its
 // thread 0 writes out.  Returns true in every thread of that last block.
 static __device__ __forceinline__ bool hill_sum(const Sys &s, Blk blk, const double *xin, double *out, int deposit)
@@ -20,11 +20,14 @@ static __device__ __forceinline__ bool hill_sum(const Sys &s, Blk blk, const dou
 #pragma unroll
     for (int d = 0; d < kMaxCv; ++d) {
         x[d] = d < D ? xin[d] : 0.0;
-        inv2v[d] = d < D ? 0.5 / (s.sigma[d] * s.sigma[d]) : 0.0;
+        inv2v[d] = d < D ? s.inv2v[d] : 0.0;  // 0.5 / sigma_d^2, formed on the host
         g[d] = 0.0;
     }
     double V = 0.0;
-    for (int k = blk.b * blockDim.x + threadIdx.x; k < K; k += blk.nb * blockDim.x) {
+    // block b takes the contiguous chunk [b chunk, (b + 1) chunk) of the hills
+    const int chunk = (K + blk.nb - 1) / blk.nb;
+    const int k1 = min(K, (blk.b + 1) * chunk);
+    for (int k = blk.b * chunk + threadIdx.x; k < k1; k += blockDim.x) {
         const double *c = s.hc + (size_t)hs * k;
         double dd[kMaxCv];
         double e = 0.0;
@@ -61,13 +64,15 @@ static __device__ __forceinline__ bool hill_sum(const Sys &s, Blk blk, const dou
     }
     __syncthreads();
     double *part = s.part + 2 * (size_t)s.part_stride;
-    if (threadIdx.x == 0) {
-        for (int q = 0; q <= D; ++q) {
-            double a = 0.0;
-            for (int w = 0; w < kW; ++w) a += sh[q][w];
-            part[(D + 1) * blk.b + q] = a;
-        }
+    if (threadIdx.x <= D) {  // thread q sums value q over the warps, in warp order
+        const int q = threadIdx.x;
+        double a = 0.0;
+        for (int w = 0; w < kW; ++w) a += sh[q][w];
+        part[(D + 1) * blk.b + q] = a;
         __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
         unsigned prev = atomicAdd(&s.ticket[2], 1u);
         am_last = (prev == (unsigned)blk.nb - 1u);
     }
@@ -95,14 +100,18 @@ static __device__ __forceinline__ bool hill_sum(const Sys &s, Blk blk, const dou
         for (int q = 0; q <= kMaxCv; ++q) sh[q][wid] = a[q];
     }
     __syncthreads();
-    if (threadIdx.x != 0) return true;
-    double out_v[kMaxCv + 1];
-    for (int q = 0; q <= kMaxCv; ++q) {
+    __shared__ double tot[kMaxCv + 1];
+    if (threadIdx.x <= kMaxCv) {  // thread q: value q over the warps, in warp order
+        const int q = threadIdx.x;
         double t = 0.0;
         if (q <= D)
             for (int w = 0; w < kW; ++w) t += sh[q][w];
-        out_v[q] = t;
+        tot[q] = t;
     }
+    __syncthreads();
+    if (threadIdx.x != 0) return true;
+    double out_v[kMaxCv + 1];
+    for (int q = 0; q <= kMaxCv; ++q) out_v[q] = tot[q];
     if (s.ncv == 2 && D == 2) {
         double gv, gg0, gg1;
         grid_value(s, x[0], x[1], gv, gg0, gg1);

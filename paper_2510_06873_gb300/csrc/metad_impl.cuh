@@ -14,6 +14,7 @@ constexpr int kNY = 13;          // real Y_6^m, m = -6..6
 constexpr int kBlockAtoms = 128; // threads per block of the per-atom kernels
 constexpr int kBlockBias = 256;  // threads per block of the hill kernels
 constexpr int kMaxBiasBlocks = 304;  // two per SM
+constexpr int kHillsPerBlock = 256;  // hill kernel: blocks of kBlockBias threads take this many hills each
 constexpr int kMaxCv = 5;        // CN, Q6 and the three lattice parameters
 
 enum ErrBits : int {
@@ -111,6 +112,7 @@ struct Sys {
     double *hw;            // [cap]
     int hill_cap;
     double sigma[kMaxCv];  // per CV (the lattice CVs last)
+    double inv2v[kMaxCv];  // 0.5 / sigma^2 per CV
     int D;                 // CVs the hills see: ncv (+ 3 lattice parameters)
     int hstride;           // doubles per hill centre: max(D, 2)
     int lattice;           // 1: the box lengths are CVs ncv .. ncv + 2
