@@ -217,3 +217,27 @@ def test_small_generators():
     assert fr.shape == (sw.n, 4) and np.all((fr[:, :3] >= 0) & (fr[:, :3] < sw.box))
     assert sw.ref not in set(sw.hydrogens.tolist()) and len(set(sw.hydrogens.tolist())) == len(sw.hydrogens)
     assert np.all(fr[sw.hydrogens, 3] == 2.0) and fr[sw.ref, 3] == 1.0
+
+
+def _golden():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "paper_parameters.txt")
+    out = {}
+    for line in open(path):
+        line = line.split("#")[0].strip()
+        if line:
+            k, v = (x.strip() for x in line.split("="))
+            out[k] = float(v)
+    return out
+
+
+def test_small_workloads_use_the_papers_parameters():
+    """The torsion workload's hill width and height are the paper's; the
+    molecule carries two four-atom torsions; the slab workload has one CV."""
+    g = _golden()
+    pp = synth.SMALL_PARAMS["peptide"]
+    assert pp["sigma"] == (g["alanine.sigma_rad"],) * 2 and pp["w0"] == g["alanine.hill_height_kjmol"]
+    assert pp["n_cv"] == g["alanine.torsions"]
+    assert len(synth.PEPTIDE_TORSIONS) == g["alanine.torsions"] * g["alanine.torsion_atoms"]
+    assert synth.SMALL_PARAMS["surface_water"]["n_cv"] == g["rutile.cvs"]
+    assert synth.MethodParams().temperature == g["gan.temperature_k"]
