@@ -648,6 +648,8 @@ metad_status metad_create(const metad_params *p, metad_ctx **out)
     cudaMemsetAsync(y.err, 0, sizeof(int), c->stream);
     cudaMemsetAsync(y.grid, 0, sizeof(double) * (size_t)y.gn[0] * y.gn[1] * 4, c->stream);
     cudaMemsetAsync(y.nn, 0, sizeof(int) * (size_t)n, c->stream);
+    // the cell counters start at zero; every rebuild's scan leaves them zero
+    cudaMemsetAsync(y.cell_count, 0, sizeof(int) * (size_t)c->ncell_alloc, c->stream);
     cudaMemsetAsync(y.nh, 0, sizeof(int) * (size_t)n, c->stream);
     cudaMemsetAsync(y.vnh, 0, sizeof(int) * (size_t)n, c->stream);
     cudaMemsetAsync(y.vnn, 0, sizeof(int) * (size_t)n, c->stream);
@@ -695,7 +697,7 @@ metad_status metad_build_neighbors(metad_ctx *c, const float *pos_dev)
         metad::launch_gather_check(c->sys, c->stream);
     }
     {
-        StageScope t(c, ST_NBR, 8);
+        StageScope t(c, ST_NBR, 6);
         metad::launch_rebuild(c->sys, c->stream);
     }
     s = launched(c, "build_neighbors");
@@ -1577,7 +1579,7 @@ metad_status metad_batch_step(metad_batch *b, const float *const *pos_dev, float
                               totals[metad::GK_ATOM32], rows[metad::GK_ATOM128], totals[metad::GK_ATOM128], b->fp64,
                               b->ncv, b->ctx[0]->sys.virial, b->stream, 2);
     if (any_deposit) metad::launch_batch_bias(rows[metad::GK_DEPOSIT], totals[metad::GK_DEPOSIT], 1, b->stream);
-    b->launches += 1 + 8 + 2 + 1 + (b->ncv == 2 ? 3 : 2) + (any_deposit ? 1 : 0);
+    b->launches += 1 + 6 + 2 + 1 + (b->ncv == 2 ? 3 : 2) + (any_deposit ? 1 : 0);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {

@@ -73,12 +73,6 @@ __device__ __forceinline__ void gather_check(const Sys &s, Blk k)
 
 __global__ void k_gather_check(Sys s) { gather_check(s, own_blk()); }
 
-__device__ __forceinline__ void rebuild_zero(const Sys &s, Blk k)
-{
-    if (!*s.flag) return;
-    for (int c = k.b * blockDim.x + threadIdx.x; c < s.ncell; c += k.nb * blockDim.x) s.cell_count[c] = 0;
-}
-
 __device__ __forceinline__ void bin_one(const Sys &s, int u)
 {
     bool bad;
@@ -160,9 +154,15 @@ __device__ __forceinline__ void scan_down(const Sys &s, Blk k)
     int base = k.b * kScanTile + threadIdx.x * kScanItems;
     int c[kScanItems];
     int v = 0;
+    // the counters' last reader: they are left zero for the next rebuild
+    // (zero from creation on, so no pass of their own clears them)
 #pragma unroll
     for (int t = 0; t < kScanItems; ++t) {
-        c[t] = (base + t < s.ncell) ? s.cell_count[base + t] : 0;
+        c[t] = 0;
+        if (base + t < s.ncell) {
+            c[t] = s.cell_count[base + t];
+            s.cell_count[base + t] = 0;
+        }
         v += c[t];
     }
     int total;
@@ -237,6 +237,22 @@ constexpr int kVerletBatch = 4;  // candidate rounds whose loads are issued toge
 // up in parallel); the candidates are then one flat range that the lanes
 // walk kG at a time, each lane finding its cell by advancing along the
 // prefix, so every position load is independent of the others and
+// End of a rebuild, run once by the last Verlet block to finish: the rows'
+// box becomes the reference and the flag is cleared for the next step (kept
+// set when the skin is zero, so every step rebuilds).
+__device__ __forceinline__ void finish_rebuild(const Sys &s, Blk k)
+{
+    __shared__ bool am_last;
+    __syncthreads();
+    if (threadIdx.x == 0) am_last = atomicAdd(&s.ticket[4], 1u) == (unsigned)k.nb - 1u;
+    __syncthreads();
+    if (!am_last || threadIdx.x != 0) return;
+    s.ticket[4] = 0u;
+    *s.rebuilds += 1ull;
+    for (int a = 0; a < 3; ++a) s.Lref[a] = s.Lhi[a];
+    *s.flag = s.always_rebuild ? 1 : 0;
+}
+
 // kVerletBatch rounds are loaded at once.  Ballot compaction keeps the
 // order.  Grid-stride over atom groups so an idle launch (no rebuild)
 // retires at once.
@@ -354,6 +370,7 @@ __device__ __forceinline__ void verlet(const Sys &s, Blk k)
             s.vnh[i] = min(nup, s.max_vnb);
         }
     }
+    finish_rebuild(s, k);
 }
 
 // Exact rows from the Verlet rows, when the CV kernel does not fuse it.
@@ -364,27 +381,14 @@ __global__ void __launch_bounds__(kBlockAtoms) k_filter(Sys s)
     for (int blk = blockIdx.x; blk < groups; blk += gridDim.x) filter_row<real>(s, atom_lane_at(s, blk));
 }
 
-// End of a rebuild: the flag is cleared for the next step (kept set when the
-// skin is zero, so every step rebuilds).
-__device__ __forceinline__ void clear_flag(const Sys &s)
-{
-    if (threadIdx.x != 0) return;
-    if (*s.flag) {
-        *s.rebuilds += 1ull;
-        for (int a = 0; a < 3; ++a) s.Lref[a] = s.Lhi[a];  // the box of these rows
-    }
-    *s.flag = s.always_rebuild ? 1 : 0;
-}
 
 // Single-system kernels of the rebuild chain.
-__global__ void k_rebuild_zero(Sys s) { rebuild_zero(s, own_blk()); }
 __global__ void k_bin_count(Sys s) { bin_count(s, own_blk()); }
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(Sys s) { scan_reduce(s, own_blk()); }
 __global__ void __launch_bounds__(kScanThreads) k_scan_down(Sys s) { scan_down(s, own_blk()); }
 __global__ void k_bin_scatter(Sys s) { bin_scatter(s, own_blk()); }
 __global__ void k_cell_sort_gather(Sys s) { cell_sort_gather(s, own_blk()); }
 __global__ void __launch_bounds__(kBlockAtoms) k_verlet(Sys s) { verlet(s, own_blk()); }
-__global__ void k_clear_flag(Sys s) { clear_flag(s); }
 
 // The same kernels over every system of a batch.
 __global__ void kb_gather_check(BatchView v)
@@ -392,12 +396,6 @@ __global__ void kb_gather_check(BatchView v)
     Blk k;
     const Sys &s = v.sys[batch_system(v, k)];
     gather_check(s, k);
-}
-__global__ void kb_rebuild_zero(BatchView v)
-{
-    Blk k;
-    const Sys &s = v.sys[batch_system(v, k)];
-    rebuild_zero(s, k);
 }
 __global__ void kb_bin_count(BatchView v)
 {
@@ -434,12 +432,6 @@ __global__ void __launch_bounds__(kBlockAtoms) kb_verlet(BatchView v)
     Blk k;
     const Sys &s = v.sys[batch_system(v, k)];
     verlet(s, k);
-}
-__global__ void kb_clear_flag(BatchView v)
-{
-    Blk k;
-    const Sys &s = v.sys[batch_system(v, k)];
-    clear_flag(s);
 }
 
 // Pairs (i < j) in caller indices, for export: one thread per sorted atom,
@@ -498,7 +490,6 @@ int grid_blocks(const Sys &s, int kind, int persist_cap)
     }
     switch (kind) {
     case GK_ATOM256: return (s.n + 255) / 256;
-    case GK_CELL1024_CAP: return capped((s.ncell + 1023) / 1024);
     case GK_ATOM256_CAP: return capped((s.n + 255) / 256);
     case GK_SCAN_TILES: return (s.ncell + kScanTile - 1) / kScanTile;
     case GK_CELL128_CAP: return capped((s.ncell + 127) / 128);
@@ -531,14 +522,12 @@ void launch_gather_check(const Sys &s, cudaStream_t st)
 
 void launch_rebuild(const Sys &s, cudaStream_t st)
 {
-    k_rebuild_zero<<<grid_blocks(s, GK_CELL1024_CAP, 0), 1024, 0, st>>>(s);
     k_bin_count<<<grid_blocks(s, GK_ATOM256_CAP, 0), 256, 0, st>>>(s);
     k_scan_reduce<<<grid_blocks(s, GK_SCAN_TILES, 0), kScanThreads, 0, st>>>(s);
     k_scan_down<<<grid_blocks(s, GK_SCAN_TILES, 0), kScanThreads, 0, st>>>(s);
     k_bin_scatter<<<grid_blocks(s, GK_ATOM256_CAP, 0), 256, 0, st>>>(s);
     k_cell_sort_gather<<<grid_blocks(s, GK_CELL128_CAP, 0), 128, 0, st>>>(s);
     k_verlet<<<grid_blocks(s, GK_GROUPS_CAP, 0), kBlockAtoms, 0, st>>>(s);
-    k_clear_flag<<<1, 1, 0, st>>>(s);
 }
 
 void launch_batch_gather(const BatchView &v, int total, cudaStream_t st)
@@ -548,14 +537,12 @@ void launch_batch_gather(const BatchView &v, int total, cudaStream_t st)
 
 void launch_batch_rebuild(const BatchView *rows, const int *totals, cudaStream_t st)
 {
-    kb_rebuild_zero<<<totals[GK_CELL1024_CAP], 1024, 0, st>>>(rows[GK_CELL1024_CAP]);
     kb_bin_count<<<totals[GK_ATOM256_CAP], 256, 0, st>>>(rows[GK_ATOM256_CAP]);
     kb_scan_reduce<<<totals[GK_SCAN_TILES], kScanThreads, 0, st>>>(rows[GK_SCAN_TILES]);
     kb_scan_down<<<totals[GK_SCAN_TILES], kScanThreads, 0, st>>>(rows[GK_SCAN_TILES]);
     kb_bin_scatter<<<totals[GK_ATOM256_CAP], 256, 0, st>>>(rows[GK_ATOM256_CAP]);
     kb_cell_sort_gather<<<totals[GK_CELL128_CAP], 128, 0, st>>>(rows[GK_CELL128_CAP]);
     kb_verlet<<<totals[GK_GROUPS_CAP], kBlockAtoms, 0, st>>>(rows[GK_GROUPS_CAP]);
-    kb_clear_flag<<<totals[GK_ONE], 32, 0, st>>>(rows[GK_ONE]);
 }
 
 void launch_filter(const Sys &s, int fp64, cudaStream_t st)
