@@ -316,6 +316,10 @@ metad_status setup_system(metad_ctx *c)
         y.always_rebuild = c->p.skin > 0.0 ? 0 : 1;
         const double grow = std::pow(rv / c->p.rc, 3.0);
         y.max_vnb = ((int)std::ceil(y.max_nb * grow) + 7) / 8 * 8;
+        // mirror slots put i's Verlet position (8 bits) beside j (23 bits)
+        // in an entry's tag, and count exact entries in a byte
+        y.mirror = (n < (1 << metad::kMirrorShift) && y.max_vnb <= 256 && y.max_nb <= 255) ? 1 : 0;
+        y.vround_stride = y.max_vnb / 8;  // one u16 per 8 Verlet entries, rows packed
     }
     y.sw_n = c->p.sw_n;
     y.sw_m = c->p.sw_m;
@@ -438,6 +442,8 @@ metad_status state_buffers(metad_ctx *c, Buffers &b, Alloc &&alloc)
         (s = alloc(&b.pfb, rs * 4 * (size_t)y.max_nb * n)) || (s = alloc(&b.geob, rs * 4 * (size_t)y.max_nb * n)) ||
         (s = alloc(&y.pos_ref, n)) ||
         (s = alloc(&y.vnbr, (size_t)y.max_vnb * n)) || (s = alloc(&y.vnn, n)) || (s = alloc(&y.flag, 1)) ||
+        (s = alloc(&y.vmirror, y.mirror ? (size_t)y.max_vnb * n + 32 : 1)) ||  // + the last row's sector
+        (s = alloc(&y.vround, y.mirror ? (size_t)y.vround_stride * n : 1)) || (s = alloc(&y.rows_fresh, 1)) ||
         (s = alloc(&y.rebuilds, 1)) || (s = alloc(&y.Lref, 4)) || (s = alloc(&b.rb, rs * (nq * 3 + (size_t)n * 4 + 64))) ||
         (s = alloc(&y.part, (size_t)y.part_stride * 4)) || (s = alloc(&y.ticket, 8)) ||
         (s = alloc(&y.scal, metad::kNumScal)) || (s = alloc(&y.err, 1)) ||
@@ -654,6 +660,7 @@ metad_status metad_create(const metad_params *p, metad_ctx **out)
     cudaMemsetAsync(y.vnh, 0, sizeof(int) * (size_t)n, c->stream);
     cudaMemsetAsync(y.vnn, 0, sizeof(int) * (size_t)n, c->stream);
     cudaMemsetAsync(y.rebuilds, 0, sizeof(unsigned long long), c->stream);
+    cudaMemsetAsync(y.rows_fresh, 0, sizeof(int), c->stream);
     {
         const float Lr[4] = {y.Lhi[0], y.Lhi[1], y.Lhi[2], 0.0f};
         if ((s = cuda_check(c, cudaMemcpy(y.Lref, Lr, sizeof(Lr), cudaMemcpyHostToDevice), "box upload"))) {

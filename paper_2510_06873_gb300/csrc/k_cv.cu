@@ -249,12 +249,13 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
 }
 
 // Displacement (cached by the exact filter), 1/r, switch weight and its
-// derivative of one exact entry.
+// derivative of one exact entry, with its neighbour, CN mask and mirror
+// position.
 template <typename real, bool kLast = false>
 __device__ __forceinline__ void cached_geometry(const Sys &s, size_t slot, Vec3<real> &d, real &inv_r, real &w,
-                                                real &dw, bool &cn, int &j)
+                                                real &dw, bool &cn, int &j, unsigned &vm)
 {
-    load_geo<real, kLast>(s, slot, d, cn, j);
+    load_geo<real, kLast>(s, slot, d, cn, j, vm);
     real r2 = d.x * d.x + d.y * d.y + d.z * d.z;
     inv_r = rsqrt_r<real>(r2);
     switch_eval<real>(s, r2 * inv_r, w, dw);
@@ -350,7 +351,8 @@ __device__ __forceinline__ double cv_fwd_group(const Sys &s, const AtomLane a)
             real inv_r, w, dw;
             bool cn;
             int j;
-            cached_geometry<real>(s, (size_t)a.i * s.max_nb + k, d, inv_r, w, dw, cn, j);
+            unsigned vm;
+            cached_geometry<real>(s, (size_t)a.i * s.max_nb + k, d, inv_r, w, dw, cn, j, vm);
             jwrow[k] = JW<real>{j, w};
             if (cn) v[14] += w;
             v[13] += w;
@@ -539,9 +541,16 @@ __device__ void last_block_cv(const Sys &s, Blk k, double c, double q)
 }
 
 // a5 with the CV sums: persistent (the block partials are few).
+// The filter of the last kernel saw the rows' mirror positions stored.
+__device__ __forceinline__ void rows_used(const Sys &s, Blk k)
+{
+    if (k.b == 0 && threadIdx.x == 0 && s.mirror) *s.rows_fresh = 0;
+}
+
 template <typename real>
 __device__ __forceinline__ void cv_avg(const Sys &s, Blk k)
 {
+    rows_used(s, k);
     RunSum<real> c, q;
     const int groups = group_grid(s.n);
     for (int it = 0, g; (g = work_item(k, it)) < groups; ++it) cv_avg_group<real>(s, atom_lane_at(s, g), c, q);
@@ -554,6 +563,7 @@ __device__ __forceinline__ void cv_avg(const Sys &s, Blk k)
 template <typename real>
 __device__ __forceinline__ void cv_sum(const Sys &s, Blk k)
 {
+    rows_used(s, k);
     RunSum<real> c;
     const real *cn = R<real>(s.cn);
     for (int i = k.b * blockDim.x + threadIdx.x; i < s.n; i += k.nb * blockDim.x) c.add(cn[i]);
@@ -741,8 +751,19 @@ __device__ __forceinline__ void pair_force(const Sys &s, int i, int k, real cn_f
     real inv_r, w, dw;
     bool cn;
     int j;
-    cached_geometry<real, true>(s, (size_t)i * s.max_nb + k, d, inv_r, w, dw, cn, j);
-    const int nhj = s.nh[j], nnj = s.nn[j];
+    unsigned vm;
+    cached_geometry<real, true>(s, (size_t)i * s.max_nb + k, d, inv_r, w, dw, cn, j, vm);
+    // the slot of i in j's exact row: with mirror slots, the exact entries
+    // of j's Verlet row before i's position vm there (one 2 B load);
+    // otherwise a search of the j < i part of j's row
+    int kk = -1, nhj = 0, nnj = 0;
+    if (s.mirror) {
+        const unsigned e = s.vround[(size_t)j * s.vround_stride + (vm >> 3)];
+        kk = (int)(e & 0xffu) + __popc((e >> 8) & ((1u << (vm & 7u)) - 1u));
+    } else {
+        nhj = s.nh[j];
+        nnj = s.nn[j];
+    }
     const real ux = d.x * inv_r, uy = d.y * inv_r, uz = d.z * inv_r;
     real radial = cn ? cn_fac * dw : real(0);
     real fx = real(0), fy = real(0), fz = real(0);
@@ -786,9 +807,9 @@ __device__ __forceinline__ void pair_force(const Sys &s, int i, int k, real cn_f
     }
     real *pf = R<real>(s.pairF);
     store_pair_force<real>(pf + ((size_t)i * s.max_nb + k) * 4, fx, fy, fz);
-    // position of i in the j < i part [nh_j, nn_j) of j's row, four entries per load
+    // without mirror slots: position of i in the j < i part [nh_j, nn_j) of
+    // j's row, four entries per load
     const int *rj = nbr_row(s, j);
-    int kk = -1;
     for (int b = nhj & ~3; b < nnj && kk < 0; b += 4) {
         const int4 v = *reinterpret_cast<const int4 *>(rj + b);
         if (v.x == i && b >= nhj) kk = b;
@@ -796,7 +817,7 @@ __device__ __forceinline__ void pair_force(const Sys &s, int i, int k, real cn_f
         else if (v.z == i && b + 2 >= nhj && b + 2 < nnj) kk = b + 2;
         else if (v.w == i && b + 3 >= nhj && b + 3 < nnj) kk = b + 3;
     }
-    if (kk < 0) {
+    if (kk < 0 || kk >= s.max_nb) {
         set_err(s, kErrInternal);  // rows not symmetric: never expected
         return;
     }

@@ -238,8 +238,9 @@ constexpr int kVerletBatch = 4;  // candidate rounds whose loads are issued toge
 // walk kG at a time, each lane finding its cell by advancing along the
 // prefix, so every position load is independent of the others and
 // End of a rebuild, run once by the last Verlet block to finish: the rows'
-// box becomes the reference and the flag is cleared for the next step (kept
-// set when the skin is zero, so every step rebuilds).
+// box becomes the reference, the rows are marked new, and the flag is
+// cleared for the next step (kept set when the skin is zero, so every step
+// rebuilds).
 __device__ __forceinline__ void finish_rebuild(const Sys &s, Blk k)
 {
     __shared__ bool am_last;
@@ -250,6 +251,7 @@ __device__ __forceinline__ void finish_rebuild(const Sys &s, Blk k)
     s.ticket[4] = 0u;
     *s.rebuilds += 1ull;
     for (int a = 0; a < 3; ++a) s.Lref[a] = s.Lhi[a];
+    if (s.mirror) *s.rows_fresh = 1;  // the next filter finds the mirror positions
     *s.flag = s.always_rebuild ? 1 : 0;
 }
 

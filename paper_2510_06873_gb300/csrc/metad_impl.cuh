@@ -93,6 +93,14 @@ struct Sys {
     int *vnn;              // [n]
     int *vnh;              // [n] Verlet entries with j > i (stored first)
     int max_vnb;
+    // mirror slots: where the pair force of i's entry j > i goes in j's row,
+    // without searching j's row in the force pass
+    int mirror;                // 1: in use (n < 2^23, rows of at most 255 entries)
+    unsigned char *vmirror;    // [n][max_vnb]: for j = vnbr[i][k] > i, i's position in j's Verlet row
+    unsigned short *vround;    // [n][vround_stride]: per filter round r (Verlet entries 8r .. 8r + 7),
+                               // the exact entries before it | the round's exact bits << 8
+    int vround_stride;
+    int *rows_fresh;           // 1 from a rebuild until the CV pass after the next filter
     int *flag;             // 1: rebuild the cell order and Verlet list this step
     float disp_thr2;       // (skin / 2)^2 with margin: rebuild above it
     float skin_eff;        // skin with margin
@@ -200,7 +208,6 @@ __device__ __forceinline__ int batch_system(const BatchView &v, Blk &k)
 // Grids of a step, one row of block counts per launch kind.
 enum GridKind : int {
     GK_ATOM256 = 0,    // one thread per atom, 256 per block
-    GK_CELL1024_CAP,   // rebuild: cell counters
     GK_ATOM256_CAP,    // rebuild: binning and scatter
     GK_SCAN_TILES,     // rebuild: cell scan
     GK_CELL128_CAP,    // rebuild: cell sort
@@ -599,78 +606,111 @@ __device__ __forceinline__ bool pair_in(const Sys &s, float4 pi, float4 pj, cons
 
 // The geometry of an exact entry, cached by the filter so the CV and force
 // passes read one contiguous record per entry instead of gathering the
-// neighbour's position again: r_j - r_i, and in the fourth slot the bits of
-// j with the CN mask in bit 31 (carried through float registers unchanged).
-// The force pass reads it for the last time (kLast: an evict-first load, so
-// the stream does not push the gathered per-atom records out of L2).
+// neighbour's position again: r_j - r_i, and in the fourth slot a tag
+// (carried through float registers unchanged): the bits of j, the CN mask in
+// bit 31, and with mirror slots, for an entry j > i, i's position in j's
+// Verlet row in bits 23..30.  The force pass reads it for the last time
+// (kLast: an evict-first load, so the stream does not push the gathered
+// per-atom records out of L2).
 constexpr unsigned kCnBit = 0x80000000u;
+constexpr int kMirrorShift = 23;
+constexpr unsigned kMirrorJ = (1u << kMirrorShift) - 1u;
+
+__device__ __forceinline__ unsigned make_tag(const Sys &s, int j, float4 pi, float4 pj, unsigned vm)
+{
+    return (unsigned)j | (vm << kMirrorShift) | ((!s.cn_unlike || pj.w != pi.w) ? kCnBit : 0u);
+}
 
 template <typename real>
 __device__ __forceinline__ void store_geo(const Sys &s, size_t slot, const Vec3<float> &df, float4 pi, float4 pj,
-                                          int j);
+                                          int j, unsigned vm);
 template <>
 __device__ __forceinline__ void store_geo<float>(const Sys &s, size_t slot, const Vec3<float> &df, float4 pi,
-                                                 float4 pj, int j)
+                                                 float4 pj, int j, unsigned vm)
 {
-    const unsigned tag = (unsigned)j | ((!s.cn_unlike || pj.w != pi.w) ? kCnBit : 0u);
+    const unsigned tag = make_tag(s, j, pi, pj, vm);
     reinterpret_cast<float4 *>(s.geo)[slot] = make_float4(df.x, df.y, df.z, __uint_as_float(tag));
 }
 template <>
 __device__ __forceinline__ void store_geo<double>(const Sys &s, size_t slot, const Vec3<float> &, float4 pi,
-                                                  float4 pj, int j)
+                                                  float4 pj, int j, unsigned vm)
 {
     const Vec3<double> d = displacement<double>(s, pi, pj);
-    const unsigned tag = (unsigned)j | ((!s.cn_unlike || pj.w != pi.w) ? kCnBit : 0u);
+    const unsigned tag = make_tag(s, j, pi, pj, vm);
     double2 *g = reinterpret_cast<double2 *>(s.geo) + 2 * slot;
     g[0] = make_double2(d.x, d.y);
     g[1] = make_double2(d.z, __longlong_as_double((long long)tag));
 }
 
-__device__ __forceinline__ void untag(unsigned tag, int &j, bool &cn)
+// j, the CN mask and the mirror position (0 without mirror slots) of a tag.
+__device__ __forceinline__ void untag(const Sys &s, unsigned tag, int &j, bool &cn, unsigned &vm)
 {
-    j = (int)(tag & ~kCnBit);
+    j = (int)(tag & (s.mirror ? kMirrorJ : ~kCnBit));
     cn = (tag & kCnBit) != 0u;
+    vm = s.mirror ? (tag & ~kCnBit) >> kMirrorShift : 0u;
 }
 
 template <typename real, bool kLast = false>
-__device__ __forceinline__ void load_geo(const Sys &s, size_t slot, Vec3<real> &d, bool &cn, int &j);
+__device__ __forceinline__ void load_geo(const Sys &s, size_t slot, Vec3<real> &d, bool &cn, int &j, unsigned &vm);
 template <>
-__device__ __forceinline__ void load_geo<float, false>(const Sys &s, size_t slot, Vec3<float> &d, bool &cn, int &j)
+__device__ __forceinline__ void load_geo<float, false>(const Sys &s, size_t slot, Vec3<float> &d, bool &cn, int &j,
+                                                       unsigned &vm)
 {
     const float4 g = reinterpret_cast<const float4 *>(s.geo)[slot];
     d.x = g.x;
     d.y = g.y;
     d.z = g.z;
-    untag(__float_as_uint(g.w), j, cn);
+    untag(s, __float_as_uint(g.w), j, cn, vm);
 }
 template <>
-__device__ __forceinline__ void load_geo<float, true>(const Sys &s, size_t slot, Vec3<float> &d, bool &cn, int &j)
+__device__ __forceinline__ void load_geo<float, true>(const Sys &s, size_t slot, Vec3<float> &d, bool &cn, int &j,
+                                                      unsigned &vm)
 {
     const float4 g = __ldcs(reinterpret_cast<const float4 *>(s.geo) + slot);
     d.x = g.x;
     d.y = g.y;
     d.z = g.z;
-    untag(__float_as_uint(g.w), j, cn);
+    untag(s, __float_as_uint(g.w), j, cn, vm);
 }
 template <>
-__device__ __forceinline__ void load_geo<double, true>(const Sys &s, size_t slot, Vec3<double> &d, bool &cn, int &j)
+__device__ __forceinline__ void load_geo<double, true>(const Sys &s, size_t slot, Vec3<double> &d, bool &cn, int &j,
+                                                       unsigned &vm)
 {
     const double2 *g = reinterpret_cast<const double2 *>(s.geo) + 2 * slot;
     const double2 a = __ldcs(g), b = __ldcs(g + 1);
     d.x = a.x;
     d.y = a.y;
     d.z = b.x;
-    untag((unsigned)__double_as_longlong(b.y), j, cn);
+    untag(s, (unsigned)__double_as_longlong(b.y), j, cn, vm);
 }
 template <>
-__device__ __forceinline__ void load_geo<double, false>(const Sys &s, size_t slot, Vec3<double> &d, bool &cn, int &j)
+__device__ __forceinline__ void load_geo<double, false>(const Sys &s, size_t slot, Vec3<double> &d, bool &cn, int &j,
+                                                        unsigned &vm)
 {
     const double2 *g = reinterpret_cast<const double2 *>(s.geo) + 2 * slot;
     const double2 a = g[0], b = g[1];
     d.x = a.x;
     d.y = a.y;
     d.z = b.x;
-    untag((unsigned)__double_as_longlong(b.y), j, cn);
+    untag(s, (unsigned)__double_as_longlong(b.y), j, cn, vm);
+}
+
+// i's position in the j < i part of j's Verlet row (rows are symmetric: the
+// Verlet predicate is), four entries per load.  Run by the filter of the
+// first step on new rows only; the later steps read the stored result.
+__device__ __forceinline__ unsigned mirror_position(const Sys &s, int j, int i)
+{
+    const int *rj = s.vnbr + (size_t)j * s.max_vnb;
+    const int lo = s.vnh[j], hi = s.vnn[j];
+    for (int b = lo & ~3; b < hi; b += 4) {
+        const int4 v = *reinterpret_cast<const int4 *>(rj + b);
+        if (v.x == i && b >= lo) return (unsigned)b;
+        if (v.y == i && b + 1 >= lo && b + 1 < hi) return (unsigned)(b + 1);
+        if (v.z == i && b + 2 >= lo && b + 2 < hi) return (unsigned)(b + 2);
+        if (v.w == i && b + 3 >= lo && b + 3 < hi) return (unsigned)(b + 3);
+    }
+    set_err(s, kErrInternal);  // rows not symmetric: never expected
+    return 0u;
 }
 
 // One exact entry for the gather passes: the neighbour and the switch
@@ -689,6 +729,21 @@ __device__ __forceinline__ int filter_row(const Sys &s, const AtomLane &a)
     const float4 pi = a.ok ? s.pos_s[a.i] : make_float4(0.f, 0.f, 0.f, 0.f);
     const int *vrow = s.vnbr + (size_t)(a.ok ? a.i : 0) * s.max_vnb;
     int *row = s.nbr + (size_t)(a.ok ? a.i : 0) * s.max_nb;
+    // mirror slots: each round records the exact entries before it and its
+    // exact bits, and each entry j > i carries i's Verlet position in j's
+    // row (searched once on new rows, stored for the steps after)
+    unsigned mw = 0u;
+    if (s.mirror) {
+        // new rows: find each j > i entry's mirror position once
+        if (*s.rows_fresh) {
+            for (int k = a.l; k < vh; k += kG)
+                s.vmirror[(size_t)a.i * s.max_vnb + k] = (unsigned char)mirror_position(s, vrow[k], a.i);
+            __syncwarp();
+        }
+        // the positions of the first four rounds in one sector: lane l holds
+        // bytes 4l .. 4l + 3 of the atom's row (rows are padded for it)
+        if (a.ok) mw = reinterpret_cast<const unsigned *>(s.vmirror + (size_t)a.i * s.max_vnb)[a.l];
+    }
     int cnt = 0, nh = 0;
     // one pass: the Verlet row already has its j > i part first, so accepted
     // entries come out in the same order; nh counts those from that part
@@ -697,6 +752,16 @@ __device__ __forceinline__ int filter_row(const Sys &s, const AtomLane &a)
         const int k = base + a.l;
         const bool valid = k < vn;
         const int j = valid ? vrow[k] : 0;
+        // the mirror position of entry k: byte k & 3 of word k / 4 = 2 r + l / 4
+        // of the preloaded sector for the first four rounds r
+        unsigned vm = 0u;
+        if (s.mirror) {
+            unsigned w = 0u;
+            if (base < 4 * kG)  // warp-uniform
+                w = __shfl_sync(0xffffffffu, mw, ((threadIdx.x & 31) & ~(kG - 1)) + 2 * (base / kG) + (a.l >> 2));
+            if (valid && k < vh)
+                vm = base < 4 * kG ? (w >> (8 * (a.l & 3))) & 0xffu : (unsigned)s.vmirror[(size_t)a.i * s.max_vnb + k];
+        }
         const float4 pj = valid ? s.pos_s[j] : pi;
         const Vec3<float> d = displacement_warp(s, pi, pj);  // every lane: a warp vote inside
         const bool in = valid && pair_in(s, pi, pj, d);
@@ -704,9 +769,12 @@ __device__ __forceinline__ int filter_row(const Sys &s, const AtomLane &a)
         const unsigned gm = group_mask_bits(ball);
         const int below = min(max(vh - base, 0), kG);  // lanes of this round in the j > i part
         const int at = cnt + __popc(gm & ((1u << a.l) - 1u));
+        // only rounds that reach the j < i part are ever looked up
+        if (s.mirror && a.l == 0 && base < vn && base + kG > vh)
+            s.vround[(size_t)a.i * s.vround_stride + base / kG] = (unsigned short)(min(cnt, 255) | (gm << 8));
         if (in && at < s.max_nb) {
             row[at] = j;
-            store_geo<real>(s, (size_t)a.i * s.max_nb + at, d, pi, pj, j);
+            store_geo<real>(s, (size_t)a.i * s.max_nb + at, d, pi, pj, j, vm);
         }
         cnt += __popc(gm);
         nh += __popc(gm & ((1u << below) - 1u));

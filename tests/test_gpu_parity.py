@@ -342,6 +342,50 @@ def test_accumulate_scale_and_determinism(dev):
     assert torch.allclose(base, 0.25 - 2.0 * F1, rtol=1e-6, atol=1e-9)
 
 
+@pytest.mark.parametrize("fp64", [False, True])
+def test_mirror_slots_equal_the_row_search(dev, fp64):
+    """The force pass finds each pair's slot in the higher atom's exact row
+    from the mirror positions found at a rebuild (Verlet rows of at most 255
+    entries), or by searching that row (larger rows).  Both give the same
+    slots, so the same bits: 64 neighbours per atom (rows of up to 136
+    Verlet entries: mirror slots) against 128 (up to 272: the search), over
+    frames that reuse the rows, frames that rebuild them, and an export of
+    the neighbour list between a rebuild and the CV pass."""
+    system = synth.wurtzite_system(6000, cfg=93)
+    mp = synth.MethodParams(n_cv=2)
+    p = oracle.params_from(mp, system.box)
+    s0, _, _ = oracle.cv(system.base, p)
+    c = synth.hill_centres(93, 0, s0, mp.sigma, 200)
+    ctxs = [make_ctx(dev, system, mp, fp64=fp64), make_ctx(dev, system, mp, fp64=fp64, max_nb=128)]
+    w = [ctx.deposit_hills(c) for ctx in ctxs][0]
+    # small moves reuse the rows; sigma 0.4 moves atoms past skin / 2
+    for f, sig in enumerate((0.05, 0.05, 0.4, 0.05, 0.4, 0.4, 0.05)):
+        frame = synth.perturbed_frame(system, f, sigma=sig)
+        pos = torch.from_numpy(frame).to(dev)
+        out = []
+        for ctx in ctxs:
+            F = torch.zeros((system.n, 3), dtype=torch.float32, device=dev)
+            if f == 4:  # the filter runs for the export, the CV pass reuses its rows
+                ctx.build_neighbors(pos)
+                pairs = ctx.export_neighbors()
+                ctx.cv_forward(want_host=False)
+                ctx.bias_eval(want_host=False)
+                ctx.bias_forces(F)
+                assert np.array_equal(pairs, oracle.pairs_cells(frame, system.box, RC))
+            else:
+                ctx.step(pos, F)
+            ctx.sync()
+            out.append((F, ctx.read_results()))
+        (Fa, ra), (Fb, rb) = out
+        assert torch.equal(Fa, Fb), f
+        assert np.array_equal(ra[0], rb[0]) and ra[1] == rb[1], f
+    assert ctxs[0].rebuild_count == ctxs[1].rebuild_count >= 4
+    ref = oracle.step(frame, p, c, w, mp.sigma)
+    check_forces(Fa.cpu().numpy().astype(np.float64), ref["F"])
+    for ctx in ctxs:
+        ctx.close()
+
+
 def test_graph_replay_matches_direct_steps(dev):
     """metad_step from a captured CUDA graph gives the direct launches' bits,
     through buffer changes (recapture), a deposit (the hill count changes)
