@@ -342,21 +342,25 @@ def test_accumulate_scale_and_determinism(dev):
     assert torch.allclose(base, 0.25 - 2.0 * F1, rtol=1e-6, atol=1e-9)
 
 
-@pytest.mark.parametrize("fp64", [False, True])
-def test_mirror_slots_equal_the_row_search(dev, fp64):
+@pytest.mark.parametrize("fp64,skin", [(False, 1.0), (True, 1.0), (False, 2.0), (False, 0.0)])
+def test_mirror_slots_equal_the_row_search(dev, fp64, skin):
     """The force pass finds each pair's slot in the higher atom's exact row
-    from the mirror positions found at a rebuild (Verlet rows of at most 255
+    from the mirror positions found at a rebuild (Verlet rows of at most 256
     entries), or by searching that row (larger rows).  Both give the same
     slots, so the same bits: 64 neighbours per atom (rows of up to 136
-    Verlet entries: mirror slots) against 128 (up to 272: the search), over
-    frames that reuse the rows, frames that rebuild them, and an export of
-    the neighbour list between a rebuild and the CV pass."""
+    Verlet entries at skin 1: mirror slots) against 128 (up to 272: the
+    search), over frames that reuse the rows, frames that rebuild them, and
+    an export of the neighbour list between a rebuild and the CV pass.  Skin
+    2 gives rows of up to 248 entries, more than 32 of them j > i (positions
+    past the first preloaded sector); skin 0 rebuilds every step (rows of 64
+    and 128 entries: both contexts use mirror slots, found anew each step)."""
     system = synth.wurtzite_system(6000, cfg=93)
     mp = synth.MethodParams(n_cv=2)
     p = oracle.params_from(mp, system.box)
     s0, _, _ = oracle.cv(system.base, p)
     c = synth.hill_centres(93, 0, s0, mp.sigma, 200)
-    ctxs = [make_ctx(dev, system, mp, fp64=fp64), make_ctx(dev, system, mp, fp64=fp64, max_nb=128)]
+    ctxs = [make_ctx(dev, system, mp, fp64=fp64, skin=skin),
+            make_ctx(dev, system, mp, fp64=fp64, max_nb=128, skin=skin)]
     w = [ctx.deposit_hills(c) for ctx in ctxs][0]
     # small moves reuse the rows; sigma 0.4 moves atoms past skin / 2
     for f, sig in enumerate((0.05, 0.05, 0.4, 0.05, 0.4, 0.4, 0.05)):
@@ -379,7 +383,7 @@ def test_mirror_slots_equal_the_row_search(dev, fp64):
         (Fa, ra), (Fb, rb) = out
         assert torch.equal(Fa, Fb), f
         assert np.array_equal(ra[0], rb[0]) and ra[1] == rb[1], f
-    assert ctxs[0].rebuild_count == ctxs[1].rebuild_count >= 4
+    assert ctxs[0].rebuild_count == ctxs[1].rebuild_count >= (7 if skin == 0.0 else 4)
     ref = oracle.step(frame, p, c, w, mp.sigma)
     check_forces(Fa.cpu().numpy().astype(np.float64), ref["F"])
     for ctx in ctxs:
