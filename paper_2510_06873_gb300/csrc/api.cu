@@ -442,7 +442,9 @@ metad_status state_buffers(metad_ctx *c, Buffers &b, Alloc &&alloc)
         (s = alloc(&b.pfb, rs * 4 * (size_t)y.max_nb * n)) || (s = alloc(&b.geob, rs * 4 * (size_t)y.max_nb * n)) ||
         (s = alloc(&y.pos_ref, n)) ||
         (s = alloc(&y.vnbr, (size_t)y.max_vnb * n)) || (s = alloc(&y.vnn, n)) || (s = alloc(&y.flag, 1)) ||
-        (s = alloc(&y.vmirror, y.mirror ? (size_t)y.max_vnb * n + 32 : 1)) ||  // + the last row's sector
+        // the filter reads each row's first 32 bytes: rows shorter than that
+        // read into the next row, the last one into this padding
+        (s = alloc(&y.vmirror, y.mirror ? (size_t)y.max_vnb * n + 32 : 1)) ||
         (s = alloc(&y.vround, y.mirror ? (size_t)y.vround_stride * n : 1)) || (s = alloc(&y.rows_fresh, 1)) ||
         (s = alloc(&y.rebuilds, 1)) || (s = alloc(&y.Lref, 4)) || (s = alloc(&b.rb, rs * (nq * 3 + (size_t)n * 4 + 64))) ||
         (s = alloc(&y.part, (size_t)y.part_stride * 4)) || (s = alloc(&y.ticket, 8)) ||
