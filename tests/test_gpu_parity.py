@@ -342,6 +342,43 @@ def test_accumulate_scale_and_determinism(dev):
     assert torch.allclose(base, 0.25 - 2.0 * F1, rtol=1e-6, atol=1e-9)
 
 
+def test_host_step_equals_the_device_step(dev):
+    """metad_step_host with page-locked host buffers, pageable ones, and
+    page-locked ones off a 16-byte boundary gives the device step's bits,
+    with and without accumulation into the caller's forces."""
+    system = synth.wurtzite_system(5000, cfg=97)
+    mp = synth.MethodParams(n_cv=2)
+    p = oracle.params_from(mp, system.box)
+    s0, _, _ = oracle.cv(system.base, p)
+    ctx = make_ctx(dev, system, mp)
+    ctx.deposit_hills(synth.hill_centres(97, 0, s0, mp.sigma, 200))
+    frame = synth.perturbed_frame(system, 1)
+    F = torch.zeros((system.n, 3), dtype=torch.float32, device=dev)
+    ctx.step(torch.from_numpy(frame).to(dev), F)
+    ctx.sync()
+    ref = F.cpu().numpy()
+    cv_ref, V_ref, _ = ctx.read_results()
+    n = system.n
+
+    def pinned(cols, offset):
+        t = torch.zeros(n * cols + offset, dtype=torch.float32).pin_memory()
+        return t.numpy()[offset:].reshape(n, cols)
+
+    cases = {"page-locked": (pinned(4, 0), pinned(3, 0)),
+             "pageable": (np.zeros((n, 4), np.float32), np.zeros((n, 3), np.float32)),
+             "page-locked, 4-byte offset": (pinned(4, 1), pinned(3, 1))}
+    for name, (ph, fh) in cases.items():
+        ph[...] = frame
+        fh[...] = 7.0
+        cv, V = ctx.step_host(ph, fh)
+        assert np.array_equal(fh, ref), name
+        assert V == V_ref and np.array_equal(cv, cv_ref), name
+        fh[...] = 0.5
+        ctx.step_host(ph, fh, accumulate=True)
+        assert np.array_equal(fh, np.float32(0.5) + ref), name
+    ctx.close()
+
+
 @pytest.mark.parametrize("fp64,skin", [(False, 1.0), (True, 1.0), (False, 2.0), (False, 0.0)])
 def test_mirror_slots_equal_the_row_search(dev, fp64, skin):
     """The force pass finds each pair's slot in the higher atom's exact row
