@@ -375,6 +375,19 @@ def run_metad(args):
     except (OSError, KeyError, ValueError):
         pass
     step_ms = ms / args.steps
+    # every per-atom kernel against both ceilings: algorithmic flops against
+    # the FP32 peak, profiled DRAM bytes (ncu, per launch) against HBM
+    per_kernel = {}
+    for k in ("cv_fwd", "cv_avg", "adjoint", "force_pairs", "force_gather"):
+        if stages.get(k, (0.0, 0))[1] == 0:
+            continue
+        t = stages[k][0] / stages[k][1] / 1e3
+        tf = FLOP_PER_PAIR.get(k, 0.0) * pairs / t / 1e12
+        dram = profiled_traffic(f"k_{k}", n)
+        per_kernel[k] = {"us": t * 1e6, "tflops": tf, "frac_fp32": tf / FP32_PEAK_TFLOPS,
+                         "algorithmic_gbs": BYTES_PER_ATOM[k] * n / t / 1e9,
+                         "dram_gbs": dram / t / 1e9 if dram else None,
+                         "frac_hbm_dram": dram / t / 1e9 / peaks_hbm if dram else None}
     # ---- the same steps replayed from captured CUDA graphs (no stage events)
     ctx.set_step_graph(True)
     for _ in range(nfr + 3):  # one capture per resident frame buffer, then replays
@@ -434,7 +447,7 @@ def run_metad(args):
                            "frames_resident": nfr, "parallelism": f"replica x{ws}" if ws > 1 else "single GPU",
                            "l2": f"inputs larger than L2: {nfr} resident frames cycled, per-step working set "
                                  f"~{step_bytes / 1e6:.0f} MB > 129 MB"},
-                "roofline": roof, "step_hbm": {"algorithmic_bytes": step_bytes,
+                "roofline": roof, "kernel_rooflines": per_kernel, "step_hbm": {"algorithmic_bytes": step_bytes,
                                                "achieved_gbs": step_bytes / (step_ms / 1e3) / 1e9,
                                                "peak_gbs": peaks_hbm,
                                                "frac": step_bytes / (step_ms / 1e3) / 1e9 / peaks_hbm},
