@@ -71,7 +71,25 @@ __device__ __forceinline__ void gather_check(const Sys &s, Blk k)
     if (__any_sync(0xffffffffu, move) && (threadIdx.x & 31) == 0) atomicOr(s.flag, 1);
 }
 
-__global__ void k_gather_check(Sys s) { gather_check(s, own_blk()); }
+// Programmatic dependent launch along the rebuild chain.  A kernel of the
+// chain lets the next one be scheduled once all its own blocks have started
+// (so the next launch overlaps its run instead of following it), and waits
+// for the previous kernel to complete, its memory visible, before it reads
+// anything.  A step without a rebuild then pays little more than the
+// blocks' early exits.  (Without a programmatic launch the wait returns at
+// once: the previous kernel has completed.)
+__device__ __forceinline__ void chain_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void chain_enter()
+{
+    chain_next();
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+__global__ void k_gather_check(Sys s)
+{
+    chain_next();
+    gather_check(s, own_blk());
+}
 
 __device__ __forceinline__ void bin_one(const Sys &s, int u)
 {
@@ -385,52 +403,83 @@ __global__ void __launch_bounds__(kBlockAtoms) k_filter(Sys s)
 
 
 // Single-system kernels of the rebuild chain.
-__global__ void k_bin_count(Sys s) { bin_count(s, own_blk()); }
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(Sys s) { scan_reduce(s, own_blk()); }
-__global__ void __launch_bounds__(kScanThreads) k_scan_down(Sys s) { scan_down(s, own_blk()); }
-__global__ void k_bin_scatter(Sys s) { bin_scatter(s, own_blk()); }
-__global__ void k_cell_sort_gather(Sys s) { cell_sort_gather(s, own_blk()); }
-__global__ void __launch_bounds__(kBlockAtoms) k_verlet(Sys s) { verlet(s, own_blk()); }
+__global__ void k_bin_count(Sys s)
+{
+    chain_enter();
+    bin_count(s, own_blk());
+}
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(Sys s)
+{
+    chain_enter();
+    scan_reduce(s, own_blk());
+}
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(Sys s)
+{
+    chain_enter();
+    scan_down(s, own_blk());
+}
+__global__ void k_bin_scatter(Sys s)
+{
+    chain_enter();
+    bin_scatter(s, own_blk());
+}
+__global__ void k_cell_sort_gather(Sys s)
+{
+    chain_enter();
+    cell_sort_gather(s, own_blk());
+}
+__global__ void __launch_bounds__(kBlockAtoms) k_verlet(Sys s)
+{
+    chain_enter();
+    verlet(s, own_blk());
+}
 
 // The same kernels over every system of a batch.
 __global__ void kb_gather_check(BatchView v)
 {
+    chain_next();
     Blk k;
     const Sys &s = v.sys[batch_system(v, k)];
     gather_check(s, k);
 }
 __global__ void kb_bin_count(BatchView v)
 {
+    chain_enter();
     Blk k;
     const Sys &s = v.sys[batch_system(v, k)];
     bin_count(s, k);
 }
 __global__ void __launch_bounds__(kScanThreads) kb_scan_reduce(BatchView v)
 {
+    chain_enter();
     Blk k;
     const Sys &s = v.sys[batch_system(v, k)];
     scan_reduce(s, k);
 }
 __global__ void __launch_bounds__(kScanThreads) kb_scan_down(BatchView v)
 {
+    chain_enter();
     Blk k;
     const Sys &s = v.sys[batch_system(v, k)];
     scan_down(s, k);
 }
 __global__ void kb_bin_scatter(BatchView v)
 {
+    chain_enter();
     Blk k;
     const Sys &s = v.sys[batch_system(v, k)];
     bin_scatter(s, k);
 }
 __global__ void kb_cell_sort_gather(BatchView v)
 {
+    chain_enter();
     Blk k;
     const Sys &s = v.sys[batch_system(v, k)];
     cell_sort_gather(s, k);
 }
 __global__ void __launch_bounds__(kBlockAtoms) kb_verlet(BatchView v)
 {
+    chain_enter();
     Blk k;
     const Sys &s = v.sys[batch_system(v, k)];
     verlet(s, k);
@@ -522,14 +571,31 @@ void launch_gather_check(const Sys &s, cudaStream_t st)
     k_gather_check<<<grid_blocks(s, GK_ATOM256, 0), 256, 0, st>>>(s);
 }
 
+// A kernel of the rebuild chain, launched so it may be scheduled while the
+// previous kernel of the stream still runs (it waits for it on the device).
+template <typename Arg>
+void chained(void (*kern)(Arg), int grid, int block, cudaStream_t st, const Arg &arg)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, arg);
+}
+
 void launch_rebuild(const Sys &s, cudaStream_t st)
 {
-    k_bin_count<<<grid_blocks(s, GK_ATOM256_CAP, 0), 256, 0, st>>>(s);
-    k_scan_reduce<<<grid_blocks(s, GK_SCAN_TILES, 0), kScanThreads, 0, st>>>(s);
-    k_scan_down<<<grid_blocks(s, GK_SCAN_TILES, 0), kScanThreads, 0, st>>>(s);
-    k_bin_scatter<<<grid_blocks(s, GK_ATOM256_CAP, 0), 256, 0, st>>>(s);
-    k_cell_sort_gather<<<grid_blocks(s, GK_CELL128_CAP, 0), 128, 0, st>>>(s);
-    k_verlet<<<grid_blocks(s, GK_GROUPS_CAP, 0), kBlockAtoms, 0, st>>>(s);
+    chained(k_bin_count, grid_blocks(s, GK_ATOM256_CAP, 0), 256, st, s);
+    chained(k_scan_reduce, grid_blocks(s, GK_SCAN_TILES, 0), kScanThreads, st, s);
+    chained(k_scan_down, grid_blocks(s, GK_SCAN_TILES, 0), kScanThreads, st, s);
+    chained(k_bin_scatter, grid_blocks(s, GK_ATOM256_CAP, 0), 256, st, s);
+    chained(k_cell_sort_gather, grid_blocks(s, GK_CELL128_CAP, 0), 128, st, s);
+    chained(k_verlet, grid_blocks(s, GK_GROUPS_CAP, 0), kBlockAtoms, st, s);
 }
 
 void launch_batch_gather(const BatchView &v, int total, cudaStream_t st)
@@ -539,12 +605,12 @@ void launch_batch_gather(const BatchView &v, int total, cudaStream_t st)
 
 void launch_batch_rebuild(const BatchView *rows, const int *totals, cudaStream_t st)
 {
-    kb_bin_count<<<totals[GK_ATOM256_CAP], 256, 0, st>>>(rows[GK_ATOM256_CAP]);
-    kb_scan_reduce<<<totals[GK_SCAN_TILES], kScanThreads, 0, st>>>(rows[GK_SCAN_TILES]);
-    kb_scan_down<<<totals[GK_SCAN_TILES], kScanThreads, 0, st>>>(rows[GK_SCAN_TILES]);
-    kb_bin_scatter<<<totals[GK_ATOM256_CAP], 256, 0, st>>>(rows[GK_ATOM256_CAP]);
-    kb_cell_sort_gather<<<totals[GK_CELL128_CAP], 128, 0, st>>>(rows[GK_CELL128_CAP]);
-    kb_verlet<<<totals[GK_GROUPS_CAP], kBlockAtoms, 0, st>>>(rows[GK_GROUPS_CAP]);
+    chained(kb_bin_count, totals[GK_ATOM256_CAP], 256, st, rows[GK_ATOM256_CAP]);
+    chained(kb_scan_reduce, totals[GK_SCAN_TILES], kScanThreads, st, rows[GK_SCAN_TILES]);
+    chained(kb_scan_down, totals[GK_SCAN_TILES], kScanThreads, st, rows[GK_SCAN_TILES]);
+    chained(kb_bin_scatter, totals[GK_ATOM256_CAP], 256, st, rows[GK_ATOM256_CAP]);
+    chained(kb_cell_sort_gather, totals[GK_CELL128_CAP], 128, st, rows[GK_CELL128_CAP]);
+    chained(kb_verlet, totals[GK_GROUPS_CAP], kBlockAtoms, st, rows[GK_GROUPS_CAP]);
 }
 
 void launch_filter(const Sys &s, int fp64, cudaStream_t st)
