@@ -585,7 +585,14 @@ void chained(void (*kern)(Arg), int grid, int block, cudaStream_t st, const Arg 
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, kern, arg);
+    if (cudaLaunchKernelEx(&cfg, kern, arg) != cudaSuccess) {
+        // a stream that refuses the attribute gets a plain launch (the
+        // device-side wait is then already satisfied); any other launch
+        // error repeats and is reported by the caller's check
+        cudaGetLastError();
+        cfg.numAttrs = 0;
+        cudaLaunchKernelEx(&cfg, kern, arg);
+    }
 }
 
 void launch_rebuild(const Sys &s, cudaStream_t st)
