@@ -39,18 +39,23 @@ WORKLOAD = ("1M-atom half-wurtzite/half-RSA-liquid periodic box (228.6 A), 2 CVs
             "number + locally averaged Q6, rc 3.5 A), FP64 bias = 200x200 bicubic-Hermite grid (20,000 folded "
             "hills) + 20,000 live well-tempered hills, one deposit per 500 frames")
 
-# FP32 peak of the dominant (ALU-bound) kernel: 152 SMs x 128 FP32 lanes x 2
-# flop per FMA x 2.07 GHz maximum SM clock.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
-# Algorithmic work per unordered neighbour pair (one evaluation; the kernels
-# evaluate each pair from both ends, which is not counted).
-FLOP_PER_PAIR = {"force_pairs": 340.0, "cv_fwd": 130.0, "cv_avg": 45.0, "adjoint": 45.0, "neighbors": 0.0}
-# Algorithmic bytes per atom of each stage (compulsory traffic, FP32 state;
-# 15.4 row entries and 7.7 unordered pairs per atom).
-BYTES_PER_ATOM = {"bin": 16 + 16 + 4 * 6, "neighbors": 16 + 4 + 4 * 15.45, "cv_fwd": 16 + 4 + 4 * 15.45 + 60,
-                  "cv_avg": 16 + 4 + 4 * 15.45 + 56 + 60, "adjoint": 16 + 4 + 4 * 15.45 + 56 + 56,
-                  "force_pairs": 16 + 4 + 4 * 7.7 + 3 * 64 + 16 * 7.7,
-                  "force_gather": 8 + 4 * 15.45 + 16 * 15.45 + 12}
+# Algorithmic work, counted once per unordered neighbour pair or per atom
+# (the kernels' own redundant work is not counted): per unordered pair Y_6m
+# ~110, accumulate ~50, CN ~40 flop in the forward pass and ~300 for the
+# adjoint gradient of w Y.G in the force pass; per atom ~500 for the neighbour
+# search and ~800 for the Q6 averaging and adjoint-seed gathers (split
+# evenly between those two passes).  Totals about 5e3 FP32 flop per atom.
+FLOP_PER_PAIR = {"cv_fwd": 200.0, "force_pairs": 300.0}
+FLOP_PER_ATOM = {"cv_fwd": 500.0, "cv_avg": 400.0, "adjoint": 400.0}
+# Algorithmic HBM bytes per atom-step with the neighbour list persisted
+# between steps: positions in (16 B), forces out (12 B) and the list read
+# and written (~2 x 60 B); about 160 B.
+STEP_BYTES_PER_ATOM = 160.0
+
+
+def stage_flops(stage: str, n_atoms: int, pairs: float) -> float:
+    """Algorithmic FP32 flops of one launch of a stage at this size."""
+    return FLOP_PER_PAIR.get(stage, 0.0) * pairs + FLOP_PER_ATOM.get(stage, 0.0) * n_atoms
 
 
 def parse():
@@ -201,7 +206,9 @@ def make_system(n):
 # ---------------------------------------------------------------- CPU legs
 def oracle_sample(n_atoms, frames, nthreads=0):
     """The FP64 oracle on `frames` frames of the workload (hills and grid set up
-    by the oracle itself, not timed).  Returns (atom-steps/s, cores, seconds)."""
+    by the oracle itself, not timed).  Returns (atom-steps/s, cores, seconds,
+    setup) with setup = (frames, oracle results, hill centres, heights of
+    the folded and of the live hills, grid range) for the error block."""
     import oracle
     system = make_system(n_atoms)
     mp = synth.method_params(3)
@@ -216,12 +223,54 @@ def oracle_sample(n_atoms, frames, nthreads=0):
     G.fold(cen[:K1], w1, mp.sigma, nthreads)
     w2 = oracle.deposit_sequence(cen[K1:], mp.sigma, mp.w0, kbdt(mp), grid=G)
     fr = [synth.perturbed_frame(system, f) for f in range(frames)]
+    out = []
     t0 = time.perf_counter()
     for f in fr:
-        oracle.step(f, p, cen[K1:], w2, mp.sigma, grid=G, nthreads=nthreads)
+        out.append(oracle.step(f, p, cen[K1:], w2, mp.sigma, grid=G, nthreads=nthreads))
     dt = time.perf_counter() - t0
     cores = nthreads if nthreads > 0 else oracle.max_threads()
-    return system.n * frames / dt, cores, dt
+    setup = (fr, out, cen, w1, w2, (s_ref - 16 * sig, s_ref + 16 * sig))
+    return system.n * frames / dt, cores, dt, setup
+
+
+def result_errors(metad, dev, stream, system, setup, max_neighbors):
+    """Error of every result of the CUDA path against the FP64 oracle on the
+    oracle's frames and hill set: a fresh context with the oracle's hills
+    (folded into the grid, then live), one step per frame.  CVs and V
+    relative; dV/ds_d relative to max(|dV/ds_d|, w0 / sigma_d) (the parity
+    floor); forces norm-wise (||dF|| / ||F||) and per atom
+    (max_i |dF_i| / max_i |F_i|).  The worst over the frames."""
+    import torch
+    mp = synth.method_params(3)
+    cfgp = synth.CONFIG_PARAMS[3]
+    frames, refs, cen, w1, w2, (lo, hi) = setup
+    K1 = cfgp["hills_folded"]
+    params = metad.params_for(system.n, system.box, n_cv=2, sigma=mp.sigma, grid=(cfgp["grid_n"], lo, hi),
+                              hill_capacity=len(w2) + 64, stream=stream.cuda_stream, max_neighbors=max_neighbors)
+    ctx = metad.Metad(params)
+    ctx.load_hills(cen[:K1], w1)
+    ctx.fold_hills()
+    ctx.load_hills(cen[K1:], w2)
+    F = torch.zeros((system.n, 3), dtype=torch.float32, device=dev)
+    err = {"s1": 0.0, "s2": 0.0, "V": 0.0, "dVds1": 0.0, "dVds2": 0.0, "F_normwise": 0.0, "F_per_atom": 0.0}
+    for fr, ref in zip(frames, refs):
+        ctx.step(torch.from_numpy(fr).to(dev), F)
+        cv, V, dV = ctx.read_results()
+        Fg = F.cpu().numpy().astype(np.float64)
+        dF = Fg - ref["F"]
+        e = {"s1": abs(cv[0] - ref["s"][0]) / abs(ref["s"][0]), "s2": abs(cv[1] - ref["s"][1]) / abs(ref["s"][1]),
+             "V": abs(V - ref["V"]) / max(abs(ref["V"]), mp.w0),
+             "dVds1": abs(dV[0] - ref["dV"][0]) / max(abs(ref["dV"][0]), mp.w0 / mp.sigma[0]),
+             "dVds2": abs(dV[1] - ref["dV"][1]) / max(abs(ref["dV"][1]), mp.w0 / mp.sigma[1]),
+             "F_normwise": float(np.linalg.norm(dF) / np.linalg.norm(ref["F"])),
+             "F_per_atom": float(np.max(np.linalg.norm(dF, axis=1)) / np.max(np.linalg.norm(ref["F"], axis=1)))}
+        err = {k: max(err[k], float(e[k])) for k in err}
+    ctx.close()
+    err["frames"] = len(frames)
+    err["tolerance"] = 1e-5
+    err["note"] = ("CUDA path (FP32 pairs, FP64 reductions, hills and grid) against the FP64 oracle on the "
+                   "same frames and hills; dV/ds relative to max(|dV/ds|, w0/sigma)")
+    return err
 
 
 def run_reference(args):
@@ -352,42 +401,39 @@ def run_metad(args):
     launches = ctx.launch_count - launches0
     ms = max_over_ranks(ms, dev)
     value = job_throughput(ws, n, args.steps, ms / 1e3)
-    # ---- dominant kernel roofline from the live per-stage events
-    dom = max((k for k in stages if stages[k][1] > 0 and k != "other"), key=lambda k: stages[k][0])
-    dom_ms, dom_cnt = stages[dom]
-    avg_s = dom_ms / dom_cnt / 1e3
-    if FLOP_PER_PAIR.get(dom, 0) > 0:
-        achieved = FLOP_PER_PAIR[dom] * pairs / avg_s / 1e12
-        roof = {"kernel": f"k_{dom}", "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": profiled_traffic(f"k_{dom}", n),
-                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 flop x 2.07 GHz",
-                "algorithmic": f"{FLOP_PER_PAIR[dom]:.0f} flop per unordered pair x {pairs:.0f} pairs"}
-    else:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
-        achieved = BYTES_PER_ATOM[dom] * n / avg_s / 1e9
-        roof = {"kernel": f"k_{dom}", "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": profiled_traffic(f"k_{dom}", n)}
-    step_bytes = sum(BYTES_PER_ATOM.values()) * n
+    # ---- dominant kernel roofline from the live per-stage events, against
+    # the FP32 peak measured on this GPU (multiply-add chains, CUDA events)
+    fp32_peak = metad.metad_probe_fp32_peak(local)
     peaks_hbm = 6787.2
     try:
         peaks_hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
     except (OSError, KeyError, ValueError):
         pass
+    timed = {k: v for k, v in stages.items() if v[1] > 0 and k != "other"}
+    dom = max(timed, key=lambda k: timed[k][0])
+    dom_ms, dom_cnt = stages[dom]
+    avg_s = dom_ms / dom_cnt / 1e3
+    flops = stage_flops(dom, n, pairs)
+    achieved = flops / avg_s / 1e12
+    roof = {"kernel": f"k_{dom}", "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp32_peak, "traffic": profiled_traffic(f"k_{dom}", n),
+            "peak_source": "measured on this GPU: metad_probe_fp32_peak (fmaf chains, CUDA events)",
+            "algorithmic": f"{flops / n:.0f} FP32 flop per atom x {n} atoms (search, per-pair and per-atom "
+                           f"counts; {pairs / n:.2f} unordered pairs per atom)"}
     step_ms = ms / args.steps
+    step_bytes = STEP_BYTES_PER_ATOM * n
+    step_flops = sum(stage_flops(k, n, pairs) for k in ("cv_fwd", "cv_avg", "adjoint", "force_pairs"))
     # every per-atom kernel against both ceilings: algorithmic flops against
-    # the FP32 peak, profiled DRAM bytes (ncu, per launch) against HBM
+    # the measured FP32 peak, profiled DRAM bytes (ncu, per launch) against HBM
     per_kernel = {}
-    for k in ("cv_fwd", "cv_avg", "adjoint", "force_pairs", "force_gather"):
-        if stages.get(k, (0.0, 0))[1] == 0:
-            continue
+    for k in sorted(timed):
         t = stages[k][0] / stages[k][1] / 1e3
-        tf = FLOP_PER_PAIR.get(k, 0.0) * pairs / t / 1e12
+        tf = stage_flops(k, n, pairs) / t / 1e12
         dram = profiled_traffic(f"k_{k}", n)
-        per_kernel[k] = {"us": t * 1e6, "tflops": tf, "frac_fp32": tf / FP32_PEAK_TFLOPS,
-                         "algorithmic_gbs": BYTES_PER_ATOM[k] * n / t / 1e9,
-                         "dram_gbs": dram / t / 1e9 if dram else None,
+        per_kernel[k] = {"us": t * 1e6, "tflops": tf, "frac_fp32": tf / fp32_peak,
+                         "dram_bytes": dram, "dram_gbs": dram / t / 1e9 if dram else None,
                          "frac_hbm_dram": dram / t / 1e9 / peaks_hbm if dram else None}
+    dram_step = [per_kernel[k]["dram_bytes"] for k in per_kernel]
     # ---- the same steps replayed from captured CUDA graphs (no stage events)
     ctx.set_step_graph(True)
     for _ in range(nfr + 3):  # one capture per resident frame buffer, then replays
@@ -423,10 +469,12 @@ def run_metad(args):
                "call": "metad_step_host (pinned host positions in, host forces + CVs + bias out)"}
     ctx.sync()
     cpu = None
+    errors = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        v, cores, dt = oracle_sample(n, 2)
+        v, cores, dt, setup = oracle_sample(n, 2)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"2 frames of the same {n}-atom workload (oracle hills/grid set up untimed), {dt:.1f} s"}
+        errors = result_errors(metad, dev, stream, system, setup, args.max_neighbors)
     forms = {}
     if rank == 0 and ws == 1:
         if not args.no_batched:
@@ -445,14 +493,21 @@ def run_metad(args):
                            "max_neighbors_per_atom": max_nn, "live_hills_end": ctx.hill_count,
                            "precision": "FP32 pair arithmetic, FP64 CV reductions, hills and grid",
                            "frames_resident": nfr, "parallelism": f"replica x{ws}" if ws > 1 else "single GPU",
-                           "l2": f"inputs larger than L2: {nfr} resident frames cycled, per-step working set "
-                                 f"~{step_bytes / 1e6:.0f} MB > 129 MB"},
-                "roofline": roof, "kernel_rooflines": per_kernel, "step_hbm": {"algorithmic_bytes": step_bytes,
-                                               "achieved_gbs": step_bytes / (step_ms / 1e3) / 1e9,
-                                               "peak_gbs": peaks_hbm,
-                                               "frac": step_bytes / (step_ms / 1e3) / 1e9 / peaks_hbm},
+                           "l2": f"inputs larger than L2: {nfr} resident frames of {16 * n / 1e6:.0f} MB cycled "
+                                 f"({16 * n * nfr / 1e6:.0f} MB > 129 MB)"},
+                "roofline": roof, "kernel_rooflines": per_kernel,
+                "step_roofline": {
+                    "algorithmic_bytes": step_bytes, "bytes_per_atom": STEP_BYTES_PER_ATOM,
+                    "achieved_gbs": step_bytes / (step_ms / 1e3) / 1e9, "peak_gbs": peaks_hbm,
+                    "frac_hbm": step_bytes / (step_ms / 1e3) / 1e9 / peaks_hbm,
+                    "algorithmic_flops": step_flops, "achieved_tflops": step_flops / (step_ms / 1e3) / 1e12,
+                    "peak_tflops": fp32_peak, "frac_fp32": step_flops / (step_ms / 1e3) / 1e12 / fp32_peak,
+                    "measured_dram_bytes": sum(dram_step) if dram_step and all(dram_step) else None,
+                    "note": "algorithmic bytes = 160 B per atom-step (positions in, forces out, the "
+                            "persisted neighbour list); measured DRAM bytes = the profiled per-kernel ncu "
+                            "counters summed over the step's kernels (null unless every kernel has one)"},
                 "stages": stage_line, "graph_replay": graph_line, "gpu_launches": launches, "clocks": clk, "e2e": e2e,
-                "cpu_baseline": cpu,
+                "cpu_baseline": cpu, "errors_vs_oracle": errors,
                 **forms}
         print(json.dumps(line), flush=True)
     ctx.close()

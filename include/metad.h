@@ -153,14 +153,26 @@ metad_status metad_create(const metad_params *p, metad_ctx **out);
 /* Release everything the context owns.  Safe on NULL. */
 metad_status metad_destroy(metad_ctx *ctx);
 
-/* Step a1-a3: wrap, Morton-order cell binning and the full neighbour list
+/* Step a1-a3: wrap, cell binning and the full neighbour list
  * {j : r_ij^2 < rc^2}, minimum image, strict inequality, decided exactly as
- * the FP64 definition.  pos_dev: device float32 [N][4] (see conventions). */
+ * the FP64 definition.  The paper is silent on neighbour lists: its CVs sum
+ * over neighbours within a cutoff (Section "B4-B1 phase transition in
+ * Large-scale systems", coordination number), and the list itself is this
+ * library's infrastructure for them.  pos_dev: device float32 [N][4] (see
+ * conventions), read on the context stream. */
 metad_status metad_build_neighbors(metad_ctx *ctx, const float *pos_dev);
 
 /* Steps a4-a5: per-atom CVs and their FP64 means.
  *   s1 = (1/N) sum_i CN_i,  CN_i = sum_j s(r_ij)   (unlike pairs by default)
  *   s2 = (1/N) sum_i qbar6_i (locally averaged Steinhardt Q6, n_cv == 2)
+ * The coordination number is the CV of the paper's GaN runs (Section "B4-B1
+ * phase transition in Large-scale systems": the Ga-N coordination, 4 in B4
+ * and 6 in B1; the paper prints no switching function, read here as the
+ * stretched rational switch (1 - x^n)/(1 - x^m), x = r/r0).  The averaged Q6
+ * is the second CV of the benchmark workloads (the paper does not use it):
+ * q_m(i) = sum_j w_ij Y_6m(r_ij) / W_i with w_ij the switch,
+ * qbar_m(i) = (q_m(i) + sum_j w_ij q_m(j)) / (1 + W_i),
+ * qbar6 = sqrt(4 pi / 13 sum_m |qbar_m|^2).
  * cv_host (NULL or double[n_cv]) receives s and synchronises.
  * per_atom_dev (NULL or device double [n_cv][N], caller order) receives CN_i
  * and qbar6_i. */
@@ -173,9 +185,12 @@ metad_status metad_cv_forward(metad_ctx *ctx, double *cv_host, double *per_atom_
  * the result and synchronise. */
 metad_status metad_bias_eval(metad_ctx *ctx, const double *s_host, double *V_host, double *dVds_host);
 
-/* Steps a7-a8: bias forces F = -sum_d (dV/ds_d) ds_d/dr, chain rule through
- * the CVs (the paper obtains them by automatic differentiation), written in
- * the caller's atom order, times `scale` (1.0 for plain forces).
+/* Steps a7-a8: bias forces F = -dV_b/dr = -sum_d (dV/ds_d) ds_d/dr, the
+ * force of the bias term of U_b = U_0 + V_b (Methods, Eq. 1), by the chain
+ * rule through the CVs; the paper obtains it by automatic differentiation of
+ * the CVs and bias (Section "Frameworks of GPU-MetaD"), here a hand-written
+ * adjoint.  Written in the caller's atom order, times `scale` (1.0 for plain
+ * forces).
  * accumulate 0: forces_dev = F; 1: forces_dev += F.  Deterministic: no
  * floating-point atomics. */
 metad_status metad_bias_forces(metad_ctx *ctx, float *forces_dev, int32_t accumulate, double scale);
@@ -306,7 +321,8 @@ int64_t metad_launch_count(const metad_ctx *ctx);
  * could synchronise the device and stall it; code bound to a fixed memory
  * budget or pool; code that must not create a metad_ctx, which allocates.)
  *
- * Computes the same hill sum as metad_bias_eval without a grid:
+ * Computes the hill sum of metad_bias_eval on a context without a grid and
+ * without periodic CVs:
  *   out_dev[0] = sum_k w_k exp(-sum_d (s_d - c_kd)^2 / 2 sigma_d^2)
  *   out_dev[1 + d] = dV/ds_d
  * s_dev: device double[n_cv]; centers_dev: device double[K][n_cv];
@@ -319,14 +335,30 @@ int64_t metad_launch_count(const metad_ctx *ctx);
  * loads it, held until the process exits) that holds one partial sum per
  * block of 256 hills, so K may be at most 131,072: larger K returns
  * METAD_ERR_CAPACITY.  The first call on a device looks up that array's
- * device address; make the first call before any stream capture.  Each call
- * clears the completion counter it needs; calls that overlap on the GPU
- * (concurrent streams) share the array and race, so order them.
+ * device address; make the first call before any stream capture.  That
+ * address is cached for the life of the process: after a cudaDeviceReset of
+ * the device, do not call this entry point again.  Each call clears the
+ * completion counter it needs; calls that overlap on the GPU (concurrent
+ * streams) share the array and race, so order them.
+ *
+ * Intended for CVs without a period (the coordination family, nearest
+ * distances): s - c is taken as is, with no wrap to the nearest image, so a
+ * torsion context's periodic hills need metad_bias_eval instead.
  * Errors: METAD_ERR_INVALID (NULL pointers, n_cv not 1 or 2, K < 0,
  * sigma <= 0), METAD_ERR_CUDA (a runtime call failed). */
 metad_status metad_bias_eval_noalloc(const double *s_dev, int32_t n_cv, const double *centers_dev,
                                      const double *heights_dev, int32_t K, const double *sigma_host,
                                      double *out_dev, int32_t device, void *stream);
+
+/* Measured FP32 multiply-add throughput of a device, in TFLOP/s: the
+ * denominator of the FP32 roofline fraction the benchmark reports for its
+ * ALU-bound kernels.  (No counterpart in the paper: a measurement helper.)
+ * Every thread of a grid of 8 x 256-thread blocks per SM runs 8 independent
+ * fmaf chains of `iters` steps; `repeats` launches are timed with CUDA events
+ * after one untimed launch.  Allocates a small buffer, synchronises, and
+ * restores the caller's current device.
+ * Errors: METAD_ERR_INVALID (NULL, iters or repeats < 1), METAD_ERR_CUDA. */
+metad_status metad_probe_fp32_peak(int32_t device, int32_t iters, int32_t repeats, double *tflops_host);
 
 /* Copy the last CVs, bias and bias gradient to the host (any may be NULL).
  * Synchronises and reports any pending device error. */

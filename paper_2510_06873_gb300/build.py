@@ -19,7 +19,7 @@ OUT_DIR = os.path.join(HERE, "_lib")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmetad.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "k_neighbors.cu", "k_cv.cu", "k_bias.cu", "k_fes.cu", "k_gcv.cu", "k_static.cu"]
+SOURCES = ["api.cu", "k_neighbors.cu", "k_cv.cu", "k_bias.cu", "k_fes.cu", "k_gcv.cu", "k_static.cu", "k_peak.cu"]
 # The FP64 hill and grid arithmetic (bias and free-energy kernels) and the
 # FP64 torsion / nearest-distance CVs are compiled without multiply-add
 # contraction: every product and sum rounds on its own, so the single-system

@@ -585,10 +585,12 @@ void chained(void (*kern)(Arg), int grid, int block, cudaStream_t st, const Arg 
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    if (cudaLaunchKernelEx(&cfg, kern, arg) != cudaSuccess) {
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, arg);
+    if (e == cudaErrorNotSupported || e == cudaErrorInvalidValue) {
         // a stream that refuses the attribute gets a plain launch (the
-        // device-side wait is then already satisfied); any other launch
-        // error repeats and is reported by the caller's check
+        // device-side wait is then already satisfied); the refusal is this
+        // launch's own error, cleared before the retry.  Any other launch
+        // error stays pending for the caller's check.
         cudaGetLastError();
         cfg.numAttrs = 0;
         cudaLaunchKernelEx(&cfg, kern, arg);

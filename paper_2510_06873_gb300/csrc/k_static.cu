@@ -104,6 +104,9 @@ double *g_scratch_ptr[kMaxDevices] = {};
 
 // Device address of the scratch on `device` (the current device).  Looked
 // up once per device: in host code the array's name is only a stand-in.
+// The cached address belongs to the device's primary context; a caller that
+// resets the device (cudaDeviceReset) must not call this entry point again
+// in the same process.
 cudaError_t scratch_address(int device, double **out)
 {
     std::lock_guard<std::mutex> lock(g_mu);
@@ -143,9 +146,15 @@ extern "C" metad_status metad_bias_eval_noalloc(const double *s_dev, int32_t n_c
         const int blocks = K > 0 ? (K + kNoAllocThreads - 1) / kNoAllocThreads : 1;
         const double inv2v0 = 0.5 / (sigma_host[0] * sigma_host[0]);
         const double inv2v1 = n_cv == 2 ? 0.5 / (sigma_host[1] * sigma_host[1]) : 0.0;
-        k_bias_noalloc<<<blocks, kNoAllocThreads, 0, cs>>>(s_dev, n_cv, centers_dev, heights_dev, K, inv2v0, inv2v1,
-                                                          scratch, out_dev);
-        if (cudaGetLastError() != cudaSuccess) st = METAD_ERR_CUDA;
+        // the launch's own status (an error left by an unrelated earlier
+        // call stays with its owner)
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)blocks);
+        cfg.blockDim = dim3((unsigned)kNoAllocThreads);
+        cfg.stream = cs;
+        if (cudaLaunchKernelEx(&cfg, k_bias_noalloc, s_dev, (int)n_cv, centers_dev, heights_dev, (int)K, inv2v0,
+                               inv2v1, scratch, out_dev) != cudaSuccess)
+            st = METAD_ERR_CUDA;
     }
     if (prev != device) cudaSetDevice(prev);
     return st;

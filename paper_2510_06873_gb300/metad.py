@@ -80,6 +80,8 @@ _SIGS = {
     "metad_rebuild_count": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
     "metad_bias_eval_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.c_int32, _P, _P, ctypes.c_int32,
                                                _P]),
+    "metad_probe_fp32_peak": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                             ctypes.POINTER(ctypes.c_double)]),
     "metad_estimate_bytes": (ctypes.c_int, [ctypes.POINTER(metad_params), ctypes.POINTER(ctypes.c_int64)]),
     "metad_device_bytes": (ctypes.c_int64, [_P]),
     "metad_set_step_graph": (ctypes.c_int, [_P, ctypes.c_int32]),
@@ -305,14 +307,45 @@ def metad_launch_count(ctx) -> int:
     return int(lib().metad_launch_count(ctx))
 
 
-def metad_bias_eval_noalloc(s, centers, heights, sigma, out, device=0, stream=None):
-    """s, centers [K, n_cv], heights [K], out [3]: device tensors (float64);
-    sigma: host sequence.  Asynchronous on `stream`; allocates nothing."""
+def metad_bias_eval_noalloc(s, centers, heights, sigma, out, device=None, stream=None):
+    """s [n_cv], centers [K, n_cv], heights [K], out [>= 3]: float64 CUDA
+    tensors, contiguous, on one device; sigma: host sequence of n_cv widths.
+    device defaults to the tensors' device.  Asynchronous on `stream`;
+    allocates nothing.  Tensors of the wrong type, shape or device raise
+    MetadError(METAD_ERR_INVALID) before any device call (the kernel would
+    otherwise read or write past the caller's buffers)."""
+    import torch
     sg = np.ascontiguousarray(np.atleast_1d(sigma), dtype=np.float64)
-    K = int(heights.shape[0]) if heights is not None else 0
     n_cv = int(sg.size)
+    where = "metad_bias_eval_noalloc"
+    tensors = {"s": s, "centers": centers, "heights": heights, "out": out}
+    for name, t in tensors.items():
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+            raise MetadError(METAD_ERR_INVALID, where, f"{name} must be a contiguous float64 CUDA tensor")
+    devs = {t.device.index for t in tensors.values()}
+    if len(devs) != 1:
+        raise MetadError(METAD_ERR_INVALID, where, "tensors on different devices")
+    dev_index = devs.pop()
+    if device is None:
+        device = dev_index
+    elif int(device) != dev_index:
+        raise MetadError(METAD_ERR_INVALID, where, f"tensors on cuda:{dev_index}, device {device} named")
+    K = int(heights.shape[0]) if heights.dim() == 1 else -1
+    if K < 0 or centers.shape != (K, n_cv) and not (K == 0 and centers.numel() == 0):
+        raise MetadError(METAD_ERR_INVALID, where, f"centers must be [K, n_cv] = [{K}, {n_cv}]")
+    if s.numel() < n_cv or out.numel() < 3:
+        raise MetadError(METAD_ERR_INVALID, where, "s needs n_cv entries and out at least 3")
     _check(None, lib().metad_bias_eval_noalloc(_dptr(s), n_cv, _dptr(centers), _dptr(heights), K, _hptr(sg),
-                                               _dptr(out), int(device), stream), "metad_bias_eval_noalloc")
+                                               _dptr(out), int(device), stream), where)
+
+
+def metad_probe_fp32_peak(device=0, iters=16384, repeats=20):
+    """Measured FP32 multiply-add throughput of `device` in TFLOP/s (the
+    roofline denominator of the ALU-bound kernels).  Synchronises."""
+    v = ctypes.c_double(0.0)
+    _check(None, lib().metad_probe_fp32_peak(int(device), int(iters), int(repeats), ctypes.byref(v)),
+           "metad_probe_fp32_peak")
+    return v.value
 
 
 def metad_read_results(ctx):

@@ -68,6 +68,16 @@ def test_fp64_gradient_matches_central_differences(dev):
             Vm = float(autograd.bias(torch.from_numpy(fm).to(dev), ctx))
             worst = max(worst, abs((Vp - Vm) / h2 - g[k, a]))
     assert worst <= 1e-6 * np.abs(g[:, :3]).max()
+    # the oracle's gradient of the same frame: dV/dr = -F(dV/ds), with the
+    # oracle's own CVs and bias gradient (FP64 pairs on both sides, the
+    # gradient stored in float32)
+    p = oracle.params_from(mp, system.box)
+    w = oracle.deposit_sequence(c, mp.sigma, mp.w0, kbdt(mp))
+    ref = oracle.step(frame, p, c, w, mp.sigma)
+    g_ref = -ref["F"]
+    nrm = np.linalg.norm(g[:, :3] - g_ref) / np.linalg.norm(g_ref)
+    per = np.max(np.linalg.norm(g[:, :3] - g_ref, axis=1)) / np.max(np.linalg.norm(g_ref, axis=1))
+    assert nrm <= 2e-7 and per <= 2e-7, (nrm, per)
     ctx.close()
 
 

@@ -254,6 +254,9 @@ def test_full_batched_workload(dev):
         _, _, dV = A[k].read_results()
         check_bias(VA[k], dV, ref["V"], ref["dV"], mp)
         check_forces(FA[k].cpu().numpy().astype(np.float64), ref["F"])
+        # the neighbour set the batched step used, bit for bit
+        pairs = A[k].export_neighbors()
+        assert np.array_equal(pairs, oracle.pairs_cells(synth.perturbed_frame(s, 1), s.box, 3.5)), k
     batch.close()
 
 

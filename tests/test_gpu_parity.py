@@ -180,6 +180,26 @@ def test_config2_frames(dev):
 
 # ------------------------------------------------------------------ config 3 (1M, grid)
 @pytest.mark.slow
+def test_config3_neighbours_bit_exact(dev):
+    """The 1M-atom neighbour set, as the benchmark's step uses it, against the
+    oracle's cell search: the first frame (a rebuild), then a frame that
+    reuses the rows (within skin/2), bit for bit as sorted pair lists."""
+    system = synth.config3_system()
+    mp = synth.method_params(3)
+    ctx = make_ctx(dev, system, mp)
+    F = torch.zeros((system.n, 3), dtype=torch.float32, device=dev)
+    for f in (0, 499):
+        frame = synth.perturbed_frame(system, f)
+        ctx.step(torch.from_numpy(frame).to(dev), F)
+        got = ctx.export_neighbors()
+        ref = oracle.pairs_cells(frame, system.box, RC)
+        print(f"frame {f}: {ref.shape[0]} pairs")
+        assert np.array_equal(got, ref), f
+    assert ctx.rebuild_count == 1
+    ctx.close()
+
+
+@pytest.mark.slow
 def test_config3_grid_deposit_and_frames(dev):
     system = synth.config3_system()
     mp = synth.method_params(3)
@@ -229,12 +249,22 @@ def test_config3_grid_deposit_and_frames(dev):
 
 
 # ------------------------------------------------------------------ variants and edges
-@pytest.mark.parametrize("n,fp64", [(1, False), (1, True), (2, True), (129, False), (129, True), (1023, False),
-                                    (1023, True), (4097, False), (4097, True)])
+@pytest.mark.parametrize("n,fp64", [(1, False), (1, True), (2, False), (2, True), (129, False), (129, True),
+                                    (1023, False), (1023, True), (4097, False), (4097, True)])
 def test_ragged_and_tiny_systems(dev, n, fp64):
-    """Ragged sizes around the block shape.  Two atoms run in FP64 only: with a
-    single bond the float32 CV is one rounding sample (~1e-7), which hills
-    within a few sigma amplify past the bias-gradient floor."""
+    """Ragged sizes around the block shape.
+
+    Two atoms in FP32: the CVs are single rounded terms (one switch value,
+    one averaged Q6 of a lone bond, exactly 1 in exact arithmetic), so their
+    relative error is one float32 rounding, ~1e-7, with nothing to average it
+    out.  The CVs meet 1e-5; dV/ds does not always: it moves by
+    (d2V/ds2) ds, and 200 hills of width 0.02 within a few sigma give
+    d2V/ds2 ~ V / sigma^2 ~ 1e4-1e5, so ds ~ 1e-7 shifts dV/ds by up to ~1e-3
+    against the floor 1e-5 w0 / sigma = 5e-4.  That is the CV's own float32
+    rounding, amplified by the bias curvature, not an error of the bias or
+    force arithmetic; the test checks each part against the oracle at the
+    CUDA path's own CVs (the bias FP64 at 1e-10, the forces at the CUDA
+    path's dV/ds at 1e-5) and prints the end-to-end dV/ds error."""
     box = np.array([9.0, 9.5, 10.0]) * max(1.0, (n / 60.0) ** (1 / 3))
     if n <= 2:
         box = np.array([12.0, 12.0, 12.0])
@@ -256,6 +286,15 @@ def test_ragged_and_tiny_systems(dev, n, fp64):
     got = gpu_step(ctx, dev, pos)
     if n == 1:
         assert np.all(got["s"] == 0.0) and np.all(got["F"] == 0.0)
+        return
+    if n == 2 and not fp64:
+        check_cv(got["s"], ref["s"])
+        V_at, dV_at = oracle.bias(got["s"], c, w, mp.sigma)
+        check_bias(got["V"], got["dV"], V_at, dV_at, mp, tol=1e-10)
+        F_at, _ = oracle.forces(pos, p, got["dV"])
+        check_forces(got["F"], F_at)
+        rel = [abs(got["dV"][d] - ref["dV"][d]) / max(abs(ref["dV"][d]), mp.w0 / mp.sigma[d]) for d in range(2)]
+        print(f"N=2 FP32: ds/s {(got['s'] - ref['s']) / ref['s']}, dV/ds error over the floor {rel}")
         return
     tol = 1e-10 if fp64 else 1e-5
     check_cv(got["s"], ref["s"], tol=tol)

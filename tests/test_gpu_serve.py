@@ -140,3 +140,71 @@ def test_walker_larger_than_budget_is_refused(dev, trace):
     ws = walkers(trace, stream)
     with pytest.raises(ValueError):
         serve.Server(ws, stream, budget_bytes=1024)
+
+
+def test_served_requests_match_the_oracle(dev):
+    """Served requests against the FP64 oracle at the parity tolerances.
+
+    Three walkers of the served workload's construction: the largest and the
+    smallest walker of the 32-walker trace (2k-500k atoms, log-uniform) and a
+    mid-sized one, with the trace's arrival process (Poisson) restricted to
+    them.  A hill is deposited every 5 requests of a walker (at that
+    request's CVs), so sampled requests of the largest walker come both
+    before and after deposits; the oracle carries the same hill history,
+    each deposit's centre the CUDA path's CVs and its well-tempered height
+    the oracle's own."""
+    from paper_2510_06873_gb300 import metad, serve
+    from parity_util import check_cv
+    stream = torch.cuda.current_stream(dev)
+    mp = synth.method_params(5)
+    cfgp = synth.CONFIG_PARAMS[5]
+    n_all, _, _ = synth.served_trace(5, n_walkers=cfgp["walkers"], n_requests=cfgp["requests"],
+                                     rate_hz=cfgp["rate_hz"])
+    order = np.argsort(n_all)
+    pick = [int(order[-1]), int(order[len(order) // 2]), int(order[0])]
+    assert n_all[pick[0]] >= 200_000
+    systems = [synth.wurtzite_system(int(n_all[w]), cfg=5, sys=w) for w in pick]
+    g = np.random.default_rng(55)
+    n_req = 36
+    walker_of = np.array([0] * 16 + [1] * 12 + [2] * 8)
+    g.shuffle(walker_of)
+    arrivals = np.cumsum(g.exponential(1.0 / cfgp["rate_hz"], n_req))
+    every = 5
+    hills, frames = [], []
+    for s in systems:
+        c = setup_hills(s, mp, 400, cfg=5)[0]
+        hills.append((c, oracle.deposit_sequence(c, mp.sigma, mp.w0, kbdt(mp))))
+        frames.append([torch.from_numpy(synth.perturbed_frame(s, f)).pin_memory() for f in range(3)])
+    ws = []
+    for s, (c, w), fr in zip(systems, hills, frames):
+        p = metad.params_for(s.n, s.box, n_cv=2, sigma=mp.sigma, stream=stream.cuda_stream, hill_capacity=4096)
+        ws.append(serve.Walker(params=p, centres=c, heights=w, frames=fr))
+    srv = serve.Server(ws, stream, budget_bytes=10**12, deposit_every=every, keep_forces=True)
+    out = srv.run(arrivals, walker_of)
+    srv.close()
+    by = {}
+    for r in out.requests:
+        by.setdefault(r.walker, []).append(r)
+    for w, rs in by.items():
+        rs.sort(key=lambda r: r.index)
+        s = systems[w]
+        p = oracle.params_from(mp, s.box)
+        live_c, live_w = hills[w][0].copy(), hills[w][1].copy()
+        sample = {0, 1, every - 1, every, every + 1, 2 * every + 1, len(rs) - 1} if w == 0 else {0, len(rs) - 1}
+        for r in rs:
+            if r.index in sample:
+                frame = synth.perturbed_frame(s, r.index % 3)
+                ref = oracle.step(frame, p, live_c, live_w, mp.sigma)
+                check_cv(r.cv, ref["s"])
+                V_at, dV_at = oracle.bias(r.cv, live_c, live_w, mp.sigma)
+                assert abs(r.V - ref["V"]) <= 1e-5 * max(abs(ref["V"]), mp.w0), (w, r.index, r.V, ref["V"])
+                assert abs(r.V - V_at) <= 1e-10 * max(abs(V_at), mp.w0), (w, r.index)
+                F_at, _ = oracle.forces(frame, p, dV_at)
+                check_forces(r.forces.astype(np.float64), F_at)
+                check_forces(r.forces.astype(np.float64), ref["F"])
+            if (r.index + 1) % every == 0:
+                h = oracle.deposit_sequence(np.vstack([live_c, r.cv[None, :]]), mp.sigma, mp.w0, kbdt(mp),
+                                            heights_prefix=live_w)[-1]
+                live_c = np.vstack([live_c, r.cv[None, :]])
+                live_w = np.append(live_w, h)
+    assert len(by[0]) == 16 and sum(1 for r in by[0] if (r.index + 1) % every == 0) == 3

@@ -53,7 +53,44 @@ def test_noalloc_matches_context_bias_twice(dev, n_cv, K):
         assert abs(got[0] - V_ref) <= 1e-12 * max(abs(V_ref), 1.0), (call, got[0], V_ref)
         for d in range(n_cv):
             assert abs(got[1 + d] - dV_ref[d]) <= 1e-12 * max(abs(dV_ref[d]), 1.0 / sigma[d]), (call, d)
+        if n_cv == 1:
+            assert got[2] == 0.0, call
     ctx.close()
+
+
+def test_noalloc_without_hills_writes_zero(dev):
+    """K = 0 (the one-block path): V and dV/ds are 0, on two calls after a
+    call that left non-zero partials in the shared scratch."""
+    from paper_2510_06873_gb300 import metad
+    st = torch.cuda.current_stream(dev).cuda_stream
+    out = torch.full((3,), 7.0, dtype=torch.float64, device=dev)
+    s = torch.tensor([2.7, 0.23], dtype=torch.float64, device=dev)
+    c1 = torch.tensor([[2.7, 0.23]], dtype=torch.float64, device=dev)
+    w1 = torch.tensor([0.5], dtype=torch.float64, device=dev)
+    metad.metad_bias_eval_noalloc(s, c1, w1, (0.05, 0.02), out, stream=st)
+    assert out.cpu().numpy()[0] == 0.5
+    for n_cv in (2, 1):
+        c0 = torch.zeros((0, n_cv), dtype=torch.float64, device=dev)
+        w0 = torch.zeros(0, dtype=torch.float64, device=dev)
+        out.fill_(7.0)
+        metad.metad_bias_eval_noalloc(s, c0, w0, (0.05, 0.02)[:n_cv], out, stream=st)
+        assert np.array_equal(out.cpu().numpy(), np.zeros(3)), n_cv
+
+
+def test_noalloc_rejects_bad_tensors(dev):
+    """The binding refuses tensors the kernel would overrun or misread."""
+    from paper_2510_06873_gb300 import metad
+    st = torch.cuda.current_stream(dev).cuda_stream
+    s = torch.zeros(2, dtype=torch.float64, device=dev)
+    c = torch.zeros((4, 2), dtype=torch.float64, device=dev)
+    w = torch.zeros(4, dtype=torch.float64, device=dev)
+    out = torch.zeros(3, dtype=torch.float64, device=dev)
+    bad = [(s.float(), c, w, out), (s, c[:, :1].clone(), w, out), (s, c, w, out[:2]), (s, c.t(), w, out),
+           (s, c, w.cpu(), out)]
+    for args in bad:
+        with pytest.raises(metad.MetadError) as e:
+            metad.metad_bias_eval_noalloc(args[0], args[1], args[2], (0.05, 0.02), args[3], stream=st)
+        assert e.value.status == metad.METAD_ERR_INVALID
 
 
 def test_noalloc_rejects_too_many_hills(dev):
