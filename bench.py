@@ -45,7 +45,7 @@ WORKLOAD = ("1M-atom half-wurtzite/half-RSA-liquid periodic box (228.6 A), 2 CVs
 # adjoint gradient of w Y.G in the force pass; per atom ~500 for the neighbour
 # search and ~800 for the Q6 averaging and adjoint-seed gathers (split
 # evenly between those two passes).  Totals about 5e3 FP32 flop per atom.
-FLOP_PER_PAIR = {"cv_fwd": 200.0, "force_pairs": 300.0}
+FLOP_PER_PAIR = {"cv_fwd": 200.0, "forces": 300.0}
 FLOP_PER_ATOM = {"cv_fwd": 500.0, "cv_avg": 400.0, "adjoint": 400.0}
 # Algorithmic HBM bytes per atom-step with the neighbour list persisted
 # between steps: positions in (16 B), forces out (12 B) and the list read
@@ -145,7 +145,11 @@ def dist_env():
 
 # Sources that make up the per-atom kernels; a profile summary records their
 # SHA-1 when its counters were taken.
-KERNEL_SOURCES = ("paper_2510_06873_gb300/csrc/k_cv.cu", "paper_2510_06873_gb300/csrc/metad_impl.cuh")
+KERNEL_SOURCES = ("paper_2510_06873_gb300/csrc/k_cv.cu", "paper_2510_06873_gb300/csrc/metad_impl.cuh",
+                  "paper_2510_06873_gb300/csrc/tiles.cuh")
+# The kernel each timed stage launches (its ncu summary is profiles/<kernel>.md).
+STAGE_KERNEL = {"cv_fwd": "k_tile_fwd", "cv_avg": "k_tile_avg", "adjoint": "k_tile_adj", "forces": "k_tile_force",
+                "neighbors": "k_verlet", "gather": "k_gather_check", "bias": "k_bias"}
 
 
 def kernel_sources_sha1() -> str:
@@ -415,22 +419,22 @@ def run_metad(args):
     avg_s = dom_ms / dom_cnt / 1e3
     flops = stage_flops(dom, n, pairs)
     achieved = flops / avg_s / 1e12
-    roof = {"kernel": f"k_{dom}", "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-            "frac": achieved / fp32_peak, "traffic": profiled_traffic(f"k_{dom}", n),
+    roof = {"kernel": STAGE_KERNEL.get(dom, dom), "bound": "alu", "achieved": achieved, "peak": fp32_peak,
+            "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": profiled_traffic(STAGE_KERNEL.get(dom, dom), n),
             "peak_source": "measured on this GPU: metad_probe_fp32_peak (fmaf chains, CUDA events)",
             "algorithmic": f"{flops / n:.0f} FP32 flop per atom x {n} atoms (search, per-pair and per-atom "
                            f"counts; {pairs / n:.2f} unordered pairs per atom)"}
     step_ms = ms / args.steps
     step_bytes = STEP_BYTES_PER_ATOM * n
-    step_flops = sum(stage_flops(k, n, pairs) for k in ("cv_fwd", "cv_avg", "adjoint", "force_pairs"))
+    step_flops = sum(stage_flops(k, n, pairs) for k in ("cv_fwd", "cv_avg", "adjoint", "forces"))
     # every per-atom kernel against both ceilings: algorithmic flops against
     # the measured FP32 peak, profiled DRAM bytes (ncu, per launch) against HBM
     per_kernel = {}
     for k in sorted(timed):
         t = stages[k][0] / stages[k][1] / 1e3
         tf = stage_flops(k, n, pairs) / t / 1e12
-        dram = profiled_traffic(f"k_{k}", n)
-        per_kernel[k] = {"us": t * 1e6, "tflops": tf, "frac_fp32": tf / fp32_peak,
+        dram = profiled_traffic(STAGE_KERNEL.get(k, k), n)
+        per_kernel[k] = {"kernel": STAGE_KERNEL.get(k, k), "us": t * 1e6, "tflops": tf, "frac_fp32": tf / fp32_peak,
                          "dram_bytes": dram, "dram_gbs": dram / t / 1e9 if dram else None,
                          "frac_hbm_dram": dram / t / 1e9 / peaks_hbm if dram else None}
     dram_step = [per_kernel[k]["dram_bytes"] for k in per_kernel]
