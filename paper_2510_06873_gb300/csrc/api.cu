@@ -431,7 +431,7 @@ std::vector<double> pack_centres(const metad_ctx *c, const double *centers, int 
 struct Buffers {
     int *rank_xyz = nullptr, *tile_xyz = nullptr;
     int4 *tile_tab = nullptr;
-    char *rec = nullptr, *vec = nullptr;
+    char *rec = nullptr, *vec = nullptr, *ent = nullptr;
 };
 
 // Every device buffer of a context in one list: alloc(&ptr, count) allocates
@@ -462,7 +462,9 @@ metad_status state_buffers(metad_ctx *c, Buffers &b, Alloc &&alloc)
     // per-atom records [n][16] (rq; rb, rh with the Q6 CV) and 4-vectors
     // [n][4] (fc; fb with the Q6 CV; wc, wb with the virial)
     const size_t nrec = (c->p.n_cv == 2 ? 3 : 1) * (size_t)16 * n;
-    const size_t nvec = ((c->p.n_cv == 2 ? 3 : 1) * (y.virial || c->p.lattice_cvs ? 2 : 1)) * (size_t)4 * n;
+    const size_t nvec = (y.virial || c->p.lattice_cvs ? 2 : 1) * (size_t)4 * n;
+    // per-entry weights and cross terms (Q6 CV only): [max_nb / 4][n][4] each
+    const size_t nent = c->p.n_cv == 2 ? 3 * (size_t)y.max_nb * n : 4;
     if ((s = alloc(&y.pos_s, n)) || (s = alloc(&y.perm, n)) ||
         (s = alloc(&y.ucell, n)) || (s = alloc(&y.uslot, n)) || (s = alloc(&y.cell_count, y.ncell)) ||
         (s = alloc(&y.cell_start, (size_t)y.ncell + 1)) || (s = alloc(&y.scan_part, y.ncell / 4096 + 2)) ||
@@ -471,7 +473,7 @@ metad_status state_buffers(metad_ctx *c, Buffers &b, Alloc &&alloc)
         (s = alloc(&y.elist, (size_t)y.max_nb * n)) || (s = alloc(&y.nn, n)) ||
         (s = alloc(&y.pos_ref, n)) || (s = alloc(&y.vlist, (size_t)y.max_vnb * n)) || (s = alloc(&y.vnn, n)) ||
         (s = alloc(&y.flag, 1)) || (s = alloc(&y.rebuilds, 1)) || (s = alloc(&y.Lref, 4)) ||
-        (s = alloc(&b.rec, rs * nrec)) || (s = alloc(&b.vec, rs * nvec)) ||
+        (s = alloc(&b.rec, rs * nrec)) || (s = alloc(&b.vec, rs * nvec)) || (s = alloc(&b.ent, rs * nent)) ||
         (s = alloc(&y.part, (size_t)y.part_stride * 4)) || (s = alloc(&y.ticket, 8)) ||
         (s = alloc(&y.scal, metad::kNumScal)) || (s = alloc(&y.err, 1)) ||
         (s = alloc(&y.hc, (size_t)y.hstride * ((size_t)y.hill_cap + 1))) ||
@@ -663,11 +665,11 @@ metad_status metad_create(const metad_params *p, metad_ctx **out)
             return p;
         };
         y.fc = take(true);
-        y.fb = take(q6);
-        y.fbt = take(q6);
         y.wc = take(vir);
-        y.wb = take(vir && q6);
-        y.wbt = take(vir && q6);
+        const size_t nent = (size_t)y.max_nb * n;
+        y.wl = q6 ? bf.ent : nullptr;
+        y.eq = q6 ? bf.ent + rs * nent : nullptr;
+        y.dq = q6 ? bf.ent + rs * 2 * nent : nullptr;
     }
     y.tile_tab = bf.tile_tab;
     y.rank_of_xyz = bf.rank_xyz;

@@ -243,6 +243,14 @@ __device__ __forceinline__ void st4<double>(double *p, double a, double b, doubl
     reinterpret_cast<double2 *>(p)[1] = make_double2(c, d);
 }
 
+// Component c (0..3, not a compile-time constant) of a 4-array in registers,
+// by selection (no local-memory indexing).
+template <typename real>
+__device__ __forceinline__ real quad_pick(const real v[4], int c)
+{
+    return c == 0 ? v[0] : (c == 1 ? v[1] : (c == 2 ? v[2] : v[3]));
+}
+
 // Displacement r_j - r_i in the pair precision.  The float32 form takes a
 // warp vote: every lane of the warp must call it.
 template <typename real>
@@ -265,6 +273,43 @@ __device__ __forceinline__ void pair_switch(const Sys &s, const Vec3<real> &d, r
     const real r2 = fma_r(d.x, d.x, fma_r(d.y, d.y, d.z * d.z));
     inv_r = rsqrt_r<real>(r2);
     switch_eval<real>(s, r2 * inv_r, w, dw);
+}
+
+// The same quantities with the hardware's approximate reciprocal square root
+// and reciprocal (relative error ~1e-7, not correctly rounded): for the force
+// pass, whose results are derivatives (the CV values, whose rounding must be
+// unbiased, use pair_switch).  FP64 keeps the exact form.
+template <typename real>
+__device__ __forceinline__ void pair_switch_fast(const Sys &s, const Vec3<real> &d, real &inv_r, real &w, real &dw);
+template <>
+__device__ __forceinline__ void pair_switch_fast<double>(const Sys &s, const Vec3<double> &d, double &inv_r, double &w,
+                                                         double &dw)
+{
+    pair_switch<double>(s, d, inv_r, w, dw);
+}
+template <>
+__device__ __forceinline__ void pair_switch_fast<float>(const Sys &s, const Vec3<float> &d, float &inv_r, float &w,
+                                                        float &dw)
+{
+    const float r2 = fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z));
+    inv_r = rsqrtf(r2);
+    const float x = (r2 * inv_r) * s.inv_r0_hi;
+    float f, dfdx;
+    if (s.sw_m == 2 * s.sw_n) {
+        const float xn1 = s.sw_n == 6 ? (x * x) * (x * x) * x : ipow<float>(x, s.sw_n - 1);
+        const float inv = __fdividef(1.0f, fmaf(xn1, x, 1.0f));
+        f = inv;
+        dfdx = -s.sw_nf * xn1 * inv * inv;
+    } else {
+        float Sn, dSn, Sm, dSm;
+        geom_sum<float>(x, s.sw_n, Sn, dSn);
+        geom_sum<float>(x, s.sw_m, Sm, dSm);
+        const float inv = __fdividef(1.0f, Sm);
+        f = Sn * inv;
+        dfdx = (dSn * Sm - Sn * dSm) * inv * inv;
+    }
+    w = fmaf(f, s.a_hi, -s.k_hi);
+    dw = dfdx * s.a_hi * s.inv_r0_hi;
 }
 
 // Where a pass reads the tile's atoms: shared memory, or, for a tile larger
@@ -483,6 +528,15 @@ __device__ __forceinline__ real group4_sum(real v)
 
 constexpr int kGroups4 = kTileThreads / 4;  // atoms a block's 4-lane groups take at once
 
+// Per-entry scalars in quad-major order, like the rows: entries 4q .. 4q + 3
+// of atom i are four reals at [q][i].
+template <typename real>
+__device__ __forceinline__ real *quad_real(void *base, size_t n, int q, int i)
+{
+    return reinterpret_cast<real *>(base) + (((size_t)q * n + i) << 2);
+}
+
+
 // ------------------------------------------------------------------ a3-a4
 // The exact rows of the tile's atoms from their Verlet rows (r^2 < rc^2,
 // decided as the FP64 definition), kept in shared memory (slist, a column
@@ -530,8 +584,10 @@ __device__ __forceinline__ void fwd_tile(const Sys &s, const TileTable &T, const
             // atoms: each quad row is one contiguous store per warp)
             for (int q = 0; 4 * q < nn; ++q) {
                 const unsigned short *col = slist + 4 * q * kTileThreads + threadIdx.x;
+                const int m = nn - 4 * q;  // entries of this quad in the row (the rest are 0)
                 quad_ref(s.elist, N, q, i) =
-                    make_ushort4(col[0], col[kTileThreads], col[2 * kTileThreads], col[3 * kTileThreads]);
+                    make_ushort4(col[0], m > 1 ? col[kTileThreads] : 0, m > 2 ? col[2 * kTileThreads] : 0,
+                                 m > 3 ? col[3 * kTileThreads] : 0);
             }
         }
         if (!kCompute) continue;
@@ -541,26 +597,36 @@ __device__ __forceinline__ void fwd_tile(const Sys &s, const TileTable &T, const
         for (int m = 0; m < kNY; ++m) Q[m] = real(0);
         real W = real(0), CN = real(0);
         real f3[3] = {real(0), real(0), real(0)}, w3[3] = {real(0), real(0), real(0)};
-        for (int k = 0; k < nmax; ++k) {
-            const bool valid = k < nn;
-            const int jl = valid ? (int)slist[k * kTileThreads + threadIdx.x] : 0;
-            const float4 pj = valid ? src.pos(jl) : pi;
-            const Vec3<real> d = pair_disp<real>(s, pi, pj);
-            if (valid) {
+        for (int k0 = 0; k0 < nmax; k0 += 4) {
+            // a quad of entries, unrolled and predicated (an entry past the
+            // row is evaluated at a dummy displacement and not added)
+            real wq[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int k = k0 + c;
+                const bool valid = k < nn;
+                const int jl = valid ? (int)slist[k * kTileThreads + threadIdx.x] : 0;
+                const float4 pj = valid ? src.pos(jl) : pi;
+                Vec3<real> d = pair_disp<real>(s, pi, pj);
+                if (!valid) {
+                    d.x = real(s.r0);
+                    d.y = d.z = real(0);
+                }
                 real inv_r, w, dw;
                 pair_switch<real>(s, d, inv_r, w, dw);
+                w = valid ? w : real(0);
+                wq[c] = w;
                 W += w;
-                if (!s.cn_unlike || pj.w != pi.w) {
-                    CN += w;
-                    const real f = dw * inv_r;
-                    f3[0] = fma_r(f, d.x, f3[0]);
-                    f3[1] = fma_r(f, d.y, f3[1]);
-                    f3[2] = fma_r(f, d.z, f3[2]);
-                    if (kVir) {
-                        w3[0] = fma_r(f * d.x, d.x, w3[0]);
-                        w3[1] = fma_r(f * d.y, d.y, w3[1]);
-                        w3[2] = fma_r(f * d.z, d.z, w3[2]);
-                    }
+                const bool cn = valid && (!s.cn_unlike || pj.w != pi.w);
+                CN += cn ? w : real(0);
+                const real f = cn ? dw * inv_r : real(0);
+                f3[0] = fma_r(f, d.x, f3[0]);
+                f3[1] = fma_r(f, d.y, f3[1]);
+                f3[2] = fma_r(f, d.z, f3[2]);
+                if (kVir) {
+                    w3[0] = fma_r(f * d.x, d.x, w3[0]);
+                    w3[1] = fma_r(f * d.y, d.y, w3[1]);
+                    w3[2] = fma_r(f * d.z, d.z, w3[2]);
                 }
                 if (s.ncv == 2) {
                     real Y[kNY];
@@ -569,6 +635,9 @@ __device__ __forceinline__ void fwd_tile(const Sys &s, const TileTable &T, const
                     for (int m = 0; m < kNY; ++m) Q[m] = fma_r(w, Y[m], Q[m]);
                 }
             }
+            // the quad's weights, for the passes that need w_ij without the
+            // geometry (entries past the row are 0)
+            if (s.ncv == 2 && k0 < nn) st4<real>(quad_real<real>(s.wl, N, k0 >> 2, i), wq[0], wq[1], wq[2], wq[3]);
         }
         if (!ok) continue;
         real *rq = R<real>(s.rq) + (size_t)i * 16;
@@ -587,225 +656,170 @@ __device__ __forceinline__ void fwd_tile(const Sys &s, const TileTable &T, const
     }
 }
 
+// Where the Q6 and adjoint passes read an own atom's row quads and weights:
+// the tile's staged copy, or global memory.
+template <typename real, bool kStaged>
+struct RowSrc {
+    const OwnRows<real> &o;
+    const unsigned short *elist;
+    void *wl;
+    size_t n;
+    int atom0;
+    __device__ __forceinline__ ushort4 jq(int a, int q) const
+    {
+        return kStaged ? o.jq[o.qoff[a] + q] : quad_at(elist, n, q, atom0 + a);
+    }
+    __device__ __forceinline__ void w(int a, int q, real x[4]) const
+    {
+        ld4<real>(kStaged ? o.wq + 4 * (o.qoff[a] + q) : quad_real<real>(wl, n, q, atom0 + a), x);
+    }
+};
+
 // ------------------------------------------------------------------ a5
 // qbar_m(i), qbar6(i), the CV sums, record b (b_m(i) in 0..12, beta_i =
-// b(i).qbar(i) in 13, qbar6 in 14) and FB_i's first part
-// sum_m b_m(i) M_m(i), M_m(i) = sum_j q_m(j) v_ij (accumulated before b_i is
-// known).  Four lanes per atom; lane l owns components 4l .. 4l + 3 (lane 3:
-// component 12).  Each round the four lanes take the geometry of four
-// entries, and all four read every entry's neighbour record (one 16-byte
-// load each).
-template <typename real, bool kStaged, bool kVir>
+// b(i).qbar(i) in 13, qbar6 in 14), and per entry e_ij = b_i.q_j (the half
+// of the cross term b_i.q_j + b_j.q_i this pass can form).  One thread per
+// atom: each neighbour's 13 q components from shared memory, the entry's
+// weight w_ij from the forward pass (no geometry here), rows a quad at a
+// time.
+template <typename real, bool kStaged>
 __device__ __forceinline__ void avg_tile(const Sys &s, const TileTable &T, const Src<real, kStaged> &src,
-                                         RunSum<real> &cn_sum, RunSum<real> &q6_sum)
+                                         const RowSrc<real, kStaged> &rows, RunSum<real> &cn_sum,
+                                         RunSum<real> &q6_sum)
 {
     const size_t N = (size_t)s.n;
-    const int l = threadIdx.x & 3, gbase = (threadIdx.x & 31) & ~3;
-    for (int a0 = 0; a0 < T.n_own; a0 += kGroups4) {
-        const int a = a0 + (threadIdx.x >> 2);
-        const bool ok = a < T.n_own;
-        const int i = T.atom0 + (ok ? a : 0);
-        const int nn = ok ? s.nn[i] : 0;
-        const float4 pi = ok ? src.pos(a) : make_float4(0.f, 0.f, 0.f, 0.f);
-        const int rounds = __reduce_max_sync(0xffffffffu, (nn + 3) >> 2);
-        real A[4] = {real(0), real(0), real(0), real(0)};
-        real M[4][3] = {}, MV[4][3] = {};
-        ushort4 nxt = nn > 0 ? quad_at(s.elist, N, 0, i) : make_ushort4(0, 0, 0, 0);
-        for (int r = 0; r < rounds; ++r) {
-            const ushort4 cur = nxt;  // the round's four entries (every lane of the group)
-            if (r + 1 < rounds) nxt = 4 * (r + 1) < nn ? quad_at(s.elist, N, r + 1, i) : make_ushort4(0, 0, 0, 0);
-            const bool valid = 4 * r + l < nn;
-            const int jl = valid ? quad_get(cur, l) : 0;
-            const float4 pj = valid ? src.pos(jl) : pi;
-            const Vec3<real> d = pair_disp<real>(s, pi, pj);
-            real w = real(0), v[3] = {real(0), real(0), real(0)};
-            if (valid) {
-                real inv_r, dw;
-                pair_switch<real>(s, d, inv_r, w, dw);
-                const real f = dw * inv_r;
-                v[0] = f * d.x;
-                v[1] = f * d.y;
-                v[2] = f * d.z;
-            }
-            const real dd[3] = {d.x, d.y, d.z};
+    for (int a = threadIdx.x; a < T.n_own; a += kTileThreads) {
+        const int i = T.atom0 + a;
+        const int nn = s.nn[i];
+        real A[kNY];
+#pragma unroll
+        for (int m = 0; m < kNY; ++m) A[m] = real(0);
+        for (int q = 0; 4 * q < nn; ++q) {
+            const ushort4 jq = rows.jq(a, q);
+            real wq[4];
+            rows.w(a, q, wq);
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const real we = __shfl_sync(0xffffffffu, w, gbase + e);
-                const int je = quad_get(cur, e);
-                real ve[3], de[3];
+                if (4 * q + e < nn) {
+                    real x[14];
+                    src.all(quad_get(jq, e), x);
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    ve[c] = __shfl_sync(0xffffffffu, v[c], gbase + e);
-                    if (kVir) de[c] = __shfl_sync(0xffffffffu, dd[c], gbase + e);
-                }
-                if (4 * r + e < nn) {
-                    real x[4];
-                    src.quad(je, l, x);
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        A[c] = fma_r(we, x[c], A[c]);
-#pragma unroll
-                        for (int z = 0; z < 3; ++z) {
-                            M[c][z] = fma_r(x[c], ve[z], M[c][z]);
-                            if (kVir) MV[c][z] = fma_r(x[c] * ve[z], de[z], MV[c][z]);
-                        }
-                    }
+                    for (int m = 0; m < kNY; ++m) A[m] = fma_r(wq[e], x[m], A[m]);
                 }
             }
         }
-        real qo[4];
-        src.quad(ok ? a : 0, l, qo);
-        const real W = ok ? src.c13(a) : real(0);
-        const real inv_D = real(1) / (real(1) + W);
-        real qb[4], sq = real(0);
+        real qo[16];
+        const real *rq = R<real>(s.rq) + (size_t)i * 16;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int m = 4 * l + c;
-            qb[c] = m < kNY ? (qo[c] + A[c]) * inv_D : real(0);
-            if (m < kNY) sq += weighted_term<real>(m, qb[c]);
+        for (int u = 0; u < 4; ++u) ld4<real>(rq + 4 * u, qo + 4 * u);
+        const real W = qo[13], CN = qo[14];
+        const real inv_D = real(1) / (real(1) + W);
+        real qb[kNY], sq = real(0);
+#pragma unroll
+        for (int m = 0; m < kNY; ++m) {
+            qb[m] = (qo[m] + A[m]) * inv_D;
+            sq += weighted_term<real>(m, qb[m]);
         }
-        sq = group4_sum<real>(sq);
         const real qb6 = sqrt(sq);
         const real ci = qb6 > real(0) ? inv_D / (n_real<real>(s) * qb6) : real(0);
-        real b[4], beta = real(0), F1[3] = {real(0), real(0), real(0)}, V1[3] = {real(0), real(0), real(0)};
+        real b[kNY], beta = real(0);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int m = 4 * l + c;
-            b[c] = m < kNY ? ci * kweight<real>(m) * qb[c] : real(0);
-            beta = fma_r(b[c], qb[c], beta);
+        for (int m = 0; m < kNY; ++m) {
+            b[m] = ci * kweight<real>(m) * qb[m];
+            beta = fma_r(b[m], qb[m], beta);
+        }
+        // e_ij = b_i.q_j for every entry, a quad at a time
+        for (int q = 0; 4 * q < nn; ++q) {
+            const ushort4 jq = rows.jq(a, q);
+            real eo[4] = {real(0), real(0), real(0), real(0)};
 #pragma unroll
-            for (int z = 0; z < 3; ++z) {
-                F1[z] = fma_r(b[c], M[c][z], F1[z]);
-                if (kVir) V1[z] = fma_r(b[c], MV[c][z], V1[z]);
+            for (int e = 0; e < 4; ++e) {
+                if (4 * q + e < nn) {
+                    real x[14];
+                    src.all(quad_get(jq, e), x);
+                    real p = b[0] * x[0];
+#pragma unroll
+                    for (int m = 1; m < kNY; ++m) p = fma_r(b[m], x[m], p);
+                    eo[e] = p;
+                }
             }
+            st4<real>(quad_real<real>(s.eq, N, q, i), eo[0], eo[1], eo[2], eo[3]);
         }
-        beta = group4_sum<real>(beta);
-#pragma unroll
-        for (int z = 0; z < 3; ++z) {
-            F1[z] = group4_sum<real>(F1[z]);
-            if (kVir) V1[z] = group4_sum<real>(V1[z]);
-        }
-        if (!ok) continue;
         real *rb = R<real>(s.rb) + (size_t)i * 16;
-        if (l < 3) st4<real>(rb + 4 * l, b[0], b[1], b[2], b[3]);
-        else st4<real>(rb + 12, b[0], beta, qb6, real(0));
-        if (l == 0) {
-            st4<real>(R<real>(s.fb) + 4 * (size_t)i, F1[0], F1[1], F1[2], real(0));
-            if (kVir) st4<real>(R<real>(s.wb) + 4 * (size_t)i, V1[0], V1[1], V1[2], real(0));
-            cn_sum.add(R<real>(s.rq)[(size_t)i * 16 + 14]);
-            q6_sum.add(qb6);
-        }
+        st4<real>(rb, b[0], b[1], b[2], b[3]);
+        st4<real>(rb + 4, b[4], b[5], b[6], b[7]);
+        st4<real>(rb + 8, b[8], b[9], b[10], b[11]);
+        st4<real>(rb + 12, b[12], beta, qb6, real(0));
+        cn_sum.add(CN);
+        q6_sum.add(qb6);
     }
 }
 
 // ------------------------------------------------------------------ a7
 // g_m(k) = b_m(k) + sum_i w_ik b_m(i), h = g / W, record h (h_m in 0..12,
-// gamma_k = h(k).q(k) + beta_k in 13), and FB_k += sum_i (q_k.b_i) v_ki.
-// Four lanes per atom as in the Q6 pass.
-template <typename real, bool kStaged, bool kVir>
-__device__ __forceinline__ void adj_tile(const Sys &s, const TileTable &T, const Src<real, kStaged> &src)
+// gamma_k = h(k).q(k) + beta_k in 13), and per entry the other half of the
+// cross term, d_ki = q_k.b_i.  One thread per atom as in the Q6 pass.
+template <typename real, bool kStaged>
+__device__ __forceinline__ void adj_tile(const Sys &s, const TileTable &T, const Src<real, kStaged> &src,
+                                         const RowSrc<real, kStaged> &rows)
 {
     const size_t N = (size_t)s.n;
-    const int l = threadIdx.x & 3, gbase = (threadIdx.x & 31) & ~3;
-    for (int a0 = 0; a0 < T.n_own; a0 += kGroups4) {
-        const int a = a0 + (threadIdx.x >> 2);
-        const bool ok = a < T.n_own;
-        const int i = T.atom0 + (ok ? a : 0);
-        const int nn = ok ? s.nn[i] : 0;
-        const float4 pi = ok ? src.pos(a) : make_float4(0.f, 0.f, 0.f, 0.f);
-        // own q (global record q; lane 3's load holds q_12, W, CN)
-        real qi[4];
-        ld4<real>(R<real>(s.rq) + (size_t)i * 16 + 4 * l, qi);
-        const real W = __shfl_sync(0xffffffffu, qi[1], gbase + 3);
-        if (l == 3) qi[1] = qi[2] = qi[3] = real(0);
-        const int rounds = __reduce_max_sync(0xffffffffu, (nn + 3) >> 2);
-        real acc[4] = {real(0), real(0), real(0), real(0)};
-        real P[3] = {real(0), real(0), real(0)}, PV[3] = {real(0), real(0), real(0)};
-        ushort4 nxt = nn > 0 ? quad_at(s.elist, N, 0, i) : make_ushort4(0, 0, 0, 0);
-        for (int r = 0; r < rounds; ++r) {
-            const ushort4 cur = nxt;
-            if (r + 1 < rounds) nxt = 4 * (r + 1) < nn ? quad_at(s.elist, N, r + 1, i) : make_ushort4(0, 0, 0, 0);
-            const bool valid = 4 * r + l < nn;
-            const int jl = valid ? quad_get(cur, l) : 0;
-            const float4 pj = valid ? src.pos(jl) : pi;
-            const Vec3<real> d = pair_disp<real>(s, pi, pj);
-            real w = real(0), v[3] = {real(0), real(0), real(0)};
-            if (valid) {
-                real inv_r, dw;
-                pair_switch<real>(s, d, inv_r, w, dw);
-                const real f = dw * inv_r;
-                v[0] = f * d.x;
-                v[1] = f * d.y;
-                v[2] = f * d.z;
-            }
-            const real dd[3] = {d.x, d.y, d.z};
+    for (int a = threadIdx.x; a < T.n_own; a += kTileThreads) {
+        const int i = T.atom0 + a;
+        const int nn = s.nn[i];
+        real qi[16];
+        const real *rq = R<real>(s.rq) + (size_t)i * 16;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) ld4<real>(rq + 4 * u, qi + 4 * u);
+        real acc[kNY];
+#pragma unroll
+        for (int m = 0; m < kNY; ++m) acc[m] = real(0);
+        for (int q = 0; 4 * q < nn; ++q) {
+            const ushort4 jq = rows.jq(a, q);
+            real wq[4], dout[4] = {real(0), real(0), real(0), real(0)};
+            rows.w(a, q, wq);
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const real we = __shfl_sync(0xffffffffu, w, gbase + e);
-                const int je = quad_get(cur, e);
-                real ve[3], de[3];
+                if (4 * q + e < nn) {
+                    real x[14];
+                    src.all(quad_get(jq, e), x);
+                    real p = qi[0] * x[0];
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    ve[c] = __shfl_sync(0xffffffffu, v[c], gbase + e);
-                    if (kVir) de[c] = __shfl_sync(0xffffffffu, dd[c], gbase + e);
-                }
-                if (4 * r + e < nn) {
-                    real x[4];
-                    src.quad(je, l, x);
-                    real p = real(0);
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        acc[c] = fma_r(we, x[c], acc[c]);
-                        p = fma_r(qi[c], x[c], p);
+                    for (int m = 0; m < kNY; ++m) {
+                        acc[m] = fma_r(wq[e], x[m], acc[m]);
+                        if (m > 0) p = fma_r(qi[m], x[m], p);
                     }
-#pragma unroll
-                    for (int z = 0; z < 3; ++z) {
-                        P[z] = fma_r(p, ve[z], P[z]);
-                        if (kVir) PV[z] = fma_r(p * ve[z], de[z], PV[z]);
-                    }
+                    dout[e] = p;
                 }
             }
+            st4<real>(quad_real<real>(s.dq, N, q, i), dout[0], dout[1], dout[2], dout[3]);
         }
-        real bo[4];
-        src.quad(ok ? a : 0, l, bo);
-        const real beta = ok ? src.c13(a) : real(0);
+        real bo[14];
+        src.all(a, bo);
+        const real W = qi[13];
         const real inv_W = W > real(0) ? real(1) / W : real(0);
-        real h[4], alpha = real(0);
+        real h[kNY], alpha = real(0);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int m = 4 * l + c;
-            h[c] = m < kNY ? (bo[c] + acc[c]) * inv_W : real(0);
-            alpha = fma_r(h[c], qi[c], alpha);
+        for (int m = 0; m < kNY; ++m) {
+            h[m] = (bo[m] + acc[m]) * inv_W;
+            alpha = fma_r(h[m], qi[m], alpha);
         }
-        alpha = group4_sum<real>(alpha);
-#pragma unroll
-        for (int z = 0; z < 3; ++z) {
-            P[z] = group4_sum<real>(P[z]);
-            if (kVir) PV[z] = group4_sum<real>(PV[z]);
-        }
-        if (!ok) continue;
         real *rh = R<real>(s.rh) + (size_t)i * 16;
-        if (l < 3) st4<real>(rh + 4 * l, h[0], h[1], h[2], h[3]);
-        else st4<real>(rh + 12, h[0], alpha + beta, real(0), real(0));
-        if (l == 0) {  // FB_k in full (the Q6 pass's part + this one), into its own array
-            real f0[4];
-            ld4<real>(R<real>(s.fb) + 4 * (size_t)i, f0);
-            st4<real>(R<real>(s.fbt) + 4 * (size_t)i, f0[0] + P[0], f0[1] + P[1], f0[2] + P[2], real(0));
-            if (kVir) {
-                ld4<real>(R<real>(s.wb) + 4 * (size_t)i, f0);
-                st4<real>(R<real>(s.wbt) + 4 * (size_t)i, f0[0] + PV[0], f0[1] + PV[1], f0[2] + PV[2], real(0));
-            }
-        }
+        st4<real>(rh, h[0], h[1], h[2], h[3]);
+        st4<real>(rh + 4, h[4], h[5], h[6], h[7]);
+        st4<real>(rh + 8, h[8], h[9], h[10], h[11]);
+        st4<real>(rh + 12, h[12], alpha + bo[13], real(0), real(0));
     }
 }
 
 // ------------------------------------------------------------------ a8
-// F_i = V1 (2/N) FC_i + V2 FB_i + V2 sum_j { [(h_i + h_j).Y - gam_i - gam_j]
+// F_i = V1 (2/N) FC_i + V2 sum_j { [(h_i + h_j).Y - gam_i - gam_j + c_ij]
 // v_ij + w grad_d((h_i + h_j).Y) }, written in the caller's order.  One
 // thread per atom; the neighbour's h record (14 components) and position
-// come from shared memory, the row a quad at a time (the next one loaded
-// ahead).  With kVir each thread also sums the bias virial of its atom's
-// entries (every pair appears in both rows: half of it).
+// come from shared memory, the row and its cross terms a quad at a time
+// (the next quad loaded ahead).  With kVir each thread also sums the bias
+// virial of its atom's entries (every pair appears in both rows: half of
+// it).
 template <typename real, bool kStaged, bool kVir>
 __device__ __forceinline__ void force_tile(const Sys &s, const TileTable &T, const Src<real, kStaged> &src,
                                            real cn_fac, real V2, RunSum<real> vir[3])
@@ -827,51 +841,63 @@ __device__ __forceinline__ void force_tile(const Sys &s, const TileTable &T, con
         for (int q = 0; q < qmax; ++q) {
             const ushort4 cur = nxt;
             if (q + 1 < qmax) nxt = 4 * (q + 1) < nn ? quad_at(s.elist, N, q + 1, i) : none;
-#pragma unroll 1
+            real cq[4] = {real(0), real(0), real(0), real(0)};
+            if (4 * q < nn) {  // the cross terms c = b_i.q_j + b_j.q_i of the quad
+                real dq[4];
+                ld4<real>(quad_real<real>(s.eq, N, q, i), cq);
+                ld4<real>(quad_real<real>(s.dq, N, q, i), dq);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) cq[c] += dq[c];
+            }
+            // the quad's four entries, unrolled and predicated (an entry past
+            // the row is evaluated at a dummy displacement and not added)
+#pragma unroll
             for (int c = 0; c < 4; ++c) {
                 const bool valid = 4 * q + c < nn;
                 const int jl = valid ? quad_get(cur, c) : 0;
                 const float4 pj = valid ? src.pos(jl) : pi;
-                const Vec3<real> d = pair_disp<real>(s, pi, pj);
-                if (valid) {
-                    real inv_r, w, dw;
-                    pair_switch<real>(s, d, inv_r, w, dw);
-                    real hj[14];
-                    src.all(jl, hj);
-                    const real ux = d.x * inv_r, uy = d.y * inv_r, uz = d.z * inv_r;
-                    real hs[kNY], cvec[kNY];
+                Vec3<real> d = pair_disp<real>(s, pi, pj);
+                if (!valid) {
+                    d.x = real(s.r0);
+                    d.y = d.z = real(0);
+                }
+                real inv_r, w, dw;
+                pair_switch_fast<real>(s, d, inv_r, w, dw);
+                real hj[14];
+                src.all(jl, hj);
+                const real ux = d.x * inv_r, uy = d.y * inv_r, uz = d.z * inv_r;
+                real hs[kNY], cvec[kNY];
 #pragma unroll
-                    for (int m = 0; m < kNY; ++m) {
-                        hs[m] = hi[m] + hj[m];
-                        cvec[m] = w * hs[m];
-                    }
-                    real Y[kNY], gY[3];
-                    ylm13_grad<real>(ux, uy, uz, inv_r, cvec, Y, gY);
-                    real t = -(hi[13] + hj[13]);
+                for (int m = 0; m < kNY; ++m) {
+                    hs[m] = hi[m] + hj[m];
+                    cvec[m] = w * hs[m];
+                }
+                real Y[kNY], gY[3];
+                ylm13_grad<real>(ux, uy, uz, inv_r, cvec, Y, gY);
+                real t = cq[c] - (hi[13] + hj[13]);
 #pragma unroll
-                    for (int m = 0; m < kNY; ++m) t = fma_r(hs[m], Y[m], t);
-                    const real radial = V2 * t * dw;
-                    const real G[3] = {fma_r(radial, ux, V2 * gY[0]), fma_r(radial, uy, V2 * gY[1]),
-                                       fma_r(radial, uz, V2 * gY[2])};
-                    F[0] += G[0];
-                    F[1] += G[1];
-                    F[2] += G[2];
-                    if (kVir) {
-                        Wv[0] = fma_r(G[0], d.x, Wv[0]);
-                        Wv[1] = fma_r(G[1], d.y, Wv[1]);
-                        Wv[2] = fma_r(G[2], d.z, Wv[2]);
-                    }
+                for (int m = 0; m < kNY; ++m) t = fma_r(hs[m], Y[m], t);
+                const real radial = valid ? V2 * t * dw : real(0);
+                const real V2v = valid ? V2 : real(0);
+                const real G[3] = {fma_r(radial, ux, V2v * gY[0]), fma_r(radial, uy, V2v * gY[1]),
+                                   fma_r(radial, uz, V2v * gY[2])};
+                F[0] += G[0];
+                F[1] += G[1];
+                F[2] += G[2];
+                if (kVir) {
+                    Wv[0] = fma_r(G[0], d.x, Wv[0]);
+                    Wv[1] = fma_r(G[1], d.y, Wv[1]);
+                    Wv[2] = fma_r(G[2], d.z, Wv[2]);
                 }
             }
         }
         if (!ok) continue;
-        real fc[4], fb[4];
+        real fc[4];
         ld4<real>(R<real>(s.fc) + 4 * (size_t)i, fc);
-        ld4<real>(R<real>(s.fbt) + 4 * (size_t)i, fb);
         float *o = s.F_out + 3 * (size_t)s.perm[i];
         real Ft[3];
 #pragma unroll
-        for (int z = 0; z < 3; ++z) Ft[z] = fma_r(cn_fac, fc[z], fma_r(V2, fb[z], F[z]));
+        for (int z = 0; z < 3; ++z) Ft[z] = fma_r(cn_fac, fc[z], F[z]);
         if (s.accumulate) {
             o[0] += (float)Ft[0];
             o[1] += (float)Ft[1];
@@ -882,11 +908,10 @@ __device__ __forceinline__ void force_tile(const Sys &s, const TileTable &T, con
             o[2] = (float)Ft[2];
         }
         if (kVir) {
-            real wc[4], wb[4];
+            real wc[4];
             ld4<real>(R<real>(s.wc) + 4 * (size_t)i, wc);
-            ld4<real>(R<real>(s.wbt) + 4 * (size_t)i, wb);
 #pragma unroll
-            for (int z = 0; z < 3; ++z) vir[z].add(real(0.5) * fma_r(cn_fac, wc[z], fma_r(V2, wb[z], Wv[z])));
+            for (int z = 0; z < 3; ++z) vir[z].add(real(0.5) * fma_r(cn_fac, wc[z], Wv[z]));
         }
     }
 }
@@ -910,11 +935,13 @@ __device__ __forceinline__ void force_factors(const Sys &s, real &cn_fac, real &
 // Each block walks tiles b, b + nb, ...; per tile: the staging table, the
 // staged atoms (when they fit), the pass, a barrier before the next tile.
 
+// Shared-memory layout of a staged pass: with positions, [cap] float4 then
+// the records; without, the records alone.
 template <typename real>
-__device__ __forceinline__ void stage_pointers(const Sys &s, float4 *&spos, real *&srec, real *&spair)
+__device__ __forceinline__ void stage_pointers(const Sys &s, bool with_pos, float4 *&spos, real *&srec, real *&spair)
 {
-    spos = reinterpret_cast<float4 *>(tile_dyn);
-    srec = reinterpret_cast<real *>(tile_dyn + (size_t)s.stage_cap * 16);
+    spos = with_pos ? reinterpret_cast<float4 *>(tile_dyn) : nullptr;
+    srec = reinterpret_cast<real *>(tile_dyn + (with_pos ? (size_t)s.stage_cap * 16 : 0));
     spair = srec + (size_t)s.stage_cap * kRecQ;
 }
 
@@ -941,50 +968,36 @@ __device__ __forceinline__ void fwd_block(const Sys &s, Blk k)
     if (kCompute && s.ncv == 1) last_block_cv(s, k, cn.value(), 0.0);
 }
 
-template <typename real, bool kVir>
-__device__ __forceinline__ void avg_block(const Sys &s, Blk k)
+// The Q6 and adjoint passes: records and the own rows staged (both must
+// fit), else both read from global memory.
+template <typename real, bool kAvg>
+__device__ __forceinline__ void records_block(const Sys &s, Blk k)
 {
     __shared__ __align__(16) TileTable T;
     float4 *spos;
     real *srec, *spair;
-    stage_pointers<real>(s, spos, srec, spair);
-    const real *rq = R<real>(s.rq);
+    stage_pointers<real>(s, false, spos, srec, spair);
+    const OwnRows<real> o = own_rows_at<real>(reinterpret_cast<unsigned char *>(spair + (size_t)s.stage_cap * 2));
+    const real *rec = R<real>(kAvg ? s.rq : s.rb);
+    const size_t N = (size_t)s.n;
     RunSum<real> cn, q6;
     for (int t = k.b; t < s.tiles; t += k.nb) {
         tile_load(s, t, T);
-        if (T.total <= s.stage_cap) {
-            stage_tile<real>(T, s.pos_s, rq, spos, srec, spair);
-            const Src<real, true> src{T, spos, srec, spair, s.pos_s, rq};
-            avg_tile<real, true, kVir>(s, T, src, cn, q6);
+        if (T.total <= s.stage_cap && stage_own_rows<real>(s, T, o)) {
+            stage_tile<real>(T, nullptr, rec, nullptr, srec, spair);  // waits for the rows' copies too
+            const Src<real, true> src{T, nullptr, srec, spair, s.pos_s, rec};
+            const RowSrc<real, true> rows{o, s.elist, s.wl, N, T.atom0};
+            if (kAvg) avg_tile<real, true>(s, T, src, rows, cn, q6);
+            else adj_tile<real, true>(s, T, src, rows);
         } else {
-            const Src<real, false> src{T, nullptr, nullptr, nullptr, s.pos_s, rq};
-            avg_tile<real, false, kVir>(s, T, src, cn, q6);
+            const Src<real, false> src{T, nullptr, nullptr, nullptr, s.pos_s, rec};
+            const RowSrc<real, false> rows{o, s.elist, s.wl, N, T.atom0};
+            if (kAvg) avg_tile<real, false>(s, T, src, rows, cn, q6);
+            else adj_tile<real, false>(s, T, src, rows);
         }
         __syncthreads();
     }
-    last_block_cv(s, k, cn.value(), q6.value());
-}
-
-template <typename real, bool kVir>
-__device__ __forceinline__ void adj_block(const Sys &s, Blk k)
-{
-    __shared__ __align__(16) TileTable T;
-    float4 *spos;
-    real *srec, *spair;
-    stage_pointers<real>(s, spos, srec, spair);
-    const real *rb = R<real>(s.rb);
-    for (int t = k.b; t < s.tiles; t += k.nb) {
-        tile_load(s, t, T);
-        if (T.total <= s.stage_cap) {
-            stage_tile<real>(T, s.pos_s, rb, spos, srec, spair);
-            const Src<real, true> src{T, spos, srec, spair, s.pos_s, rb};
-            adj_tile<real, true, kVir>(s, T, src);
-        } else {
-            const Src<real, false> src{T, nullptr, nullptr, nullptr, s.pos_s, rb};
-            adj_tile<real, false, kVir>(s, T, src);
-        }
-        __syncthreads();
-    }
+    if (kAvg) last_block_cv(s, k, cn.value(), q6.value());
 }
 
 template <typename real, bool kVir>
@@ -993,7 +1006,7 @@ __device__ __forceinline__ void force_block(const Sys &s, Blk k)
     __shared__ __align__(16) TileTable T;
     float4 *spos;
     real *srec, *spair;
-    stage_pointers<real>(s, spos, srec, spair);
+    stage_pointers<real>(s, true, spos, srec, spair);
     real cn_fac, V2;
     force_factors<real>(s, cn_fac, V2);
     const real *rh = R<real>(s.rh);
@@ -1061,10 +1074,10 @@ __device__ __forceinline__ void force_cn(const Sys &s, Blk k)
 
 template <typename real, bool kCompute, bool kVir>
 __device__ __forceinline__ void fwd_body(const Sys &s, Blk k) { fwd_block<real, kCompute, kVir>(s, k); }
-template <typename real, bool kVir, bool kUnused>
-__device__ __forceinline__ void avg_body(const Sys &s, Blk k) { avg_block<real, kVir>(s, k); }
-template <typename real, bool kVir, bool kUnused>
-__device__ __forceinline__ void adj_body(const Sys &s, Blk k) { adj_block<real, kVir>(s, k); }
+template <typename real, bool kUnusedA, bool kUnusedB>
+__device__ __forceinline__ void avg_body(const Sys &s, Blk k) { records_block<real, true>(s, k); }
+template <typename real, bool kUnusedA, bool kUnusedB>
+__device__ __forceinline__ void adj_body(const Sys &s, Blk k) { records_block<real, false>(s, k); }
 template <typename real, bool kVir, bool kUnused>
 __device__ __forceinline__ void force_body(const Sys &s, Blk k) { force_block<real, kVir>(s, k); }
 template <typename real, bool kVir, bool kUnused>
@@ -1102,8 +1115,8 @@ const void *pass_kernel(int pass, bool flag, bool vir, bool batched)
     case kPassFwd:
         if (!flag) return METAD_PICK(tile_fwd, false, false);
         return vir ? METAD_PICK(tile_fwd, true, true) : METAD_PICK(tile_fwd, true, false);
-    case kPassAvg: return vir ? METAD_PICK(tile_avg, true, false) : METAD_PICK(tile_avg, false, false);
-    case kPassAdj: return vir ? METAD_PICK(tile_adj, true, false) : METAD_PICK(tile_adj, false, false);
+    case kPassAvg: return METAD_PICK(tile_avg, false, false);
+    case kPassAdj: return METAD_PICK(tile_adj, false, false);
     case kPassForce: return vir ? METAD_PICK(tile_force, true, false) : METAD_PICK(tile_force, false, false);
     case kPassForceCn: return vir ? METAD_PICK(force_cn, true, false) : METAD_PICK(force_cn, false, false);
     }
@@ -1124,7 +1137,8 @@ int tile_smem(const Sys &s, int pass)
     switch (pass) {
     case kPassFwd: return s.stage_cap * 16 + s.max_nb * kTileThreads * 2;
     case kPassForceCn: return 0;
-    default: return s.stage_cap * (16 + (kRecQ + 2) * rs);
+    case kPassForce: return s.stage_cap * (16 + (kRecQ + 2) * rs);
+    default: return s.stage_cap * (kRecQ + 2) * rs + own_rows_bytes(rs);  // records and own rows
     }
 }
 
@@ -1233,3 +1247,4 @@ void set_ylm_constants(cudaStream_t st)
 
 
 }  // namespace metad
+

@@ -104,11 +104,14 @@ struct Sys {
     //   rq: q_m (0..12), W (13), CN (14)
     //   rb: b_m (0..12), beta (13), qbar6 (14)
     //   rh: h_m (0..12), gamma (13)
-    // and 4-vectors [n][4]: fc = FC, fb = FB's part from the Q6 pass, fbt =
-    // FB in full (the force sums that need no dV/ds); wc, wb, wbt their
-    // virial sums (with the virial only)
+    // 4-vectors [n][4]: fc = FC (the CN force sum, which needs no dV/ds) and
+    // wc its virial sum (with the virial only); and per exact entry, in the
+    // rows' quad-major order, the switch weight w_ij (wl) and the two halves
+    // of the cross term c_ij = b_i.q_j + b_j.q_i: e_ij = b_i.q_j (eq) and
+    // d_ij = q_i.b_j (dq)
     void *rq, *rb, *rh;
-    void *fc, *fb, *fbt, *wc, *wb, *wbt;
+    void *fc, *wc;
+    void *wl, *eq, *dq;
     double *part;          // per-block FP64 partial sums, slots of part_stride
     int part_stride;
     unsigned *ticket;      // completion counters of the last-block reductions
@@ -234,10 +237,11 @@ enum Pass : int {
     kNumPasses
 };
 constexpr int kMaxTileSmem = 224 * 1024;  // dynamic shared memory limit of a pass
-// Staged atoms per tile kept in shared memory: FP32 fits two blocks of the
-// heaviest pass per SM; FP64 one.
-constexpr int kStageCapF32 = 1536;
-constexpr int kStageCapF64 = 1728;
+// Staged atoms per tile kept in shared memory (a tile with its one-cell
+// shell holds about 1,000 atoms at the workloads' densities): in FP32 two
+// blocks of every pass fit on an SM.
+constexpr int kStageCapF32 = 1216;
+constexpr int kStageCapF64 = 1216;
 int tile_smem(const Sys &s, int pass);   // dynamic shared memory of a pass
 int pass_blocks(const Sys &s, int pass); // single-system grid of a pass
 void launch_tile_pass(const Sys &s, int pass, int flag, cudaStream_t st);

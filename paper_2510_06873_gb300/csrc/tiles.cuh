@@ -223,9 +223,10 @@ extern __shared__ __align__(16) unsigned char tile_dyn[];
 // components 0..11 (rec, 12 reals per atom) and 12..13 (pair, 2 per atom).
 constexpr int kRecQ = 12;
 
-// Stage the tile's atoms: positions (from `pos`, sorted order) and, when
-// rec != nullptr, components 0..13 of the records.  Each warp copies whole
-// cells, a cell's atoms in groups of lanes (one lane per 16-byte unit).
+// Stage the tile's atoms: positions (from `pos`, sorted order, unless
+// nullptr) and, unless rec is nullptr, components 0..13 of the records.
+// Each warp copies whole cells, a cell's atoms in groups of lanes (one lane
+// per 16-byte unit).
 template <typename real>
 __device__ __forceinline__ void stage_tile(const TileTable &T, const float4 *pos, const real *rec, float4 *spos,
                                            real *srec, real *spair)
@@ -233,7 +234,8 @@ __device__ __forceinline__ void stage_tile(const TileTable &T, const float4 *pos
     // units per atom: the position, the 16-byte pieces of components 0..11,
     // and components 12..13 (8 bytes in FP32, 16 in FP64)
     constexpr int kQuads = kRecQ * sizeof(real) / 16;
-    const int U = rec ? 2 + kQuads : 1;
+    const int P = pos ? 1 : 0;
+    const int U = P + (rec ? 1 + kQuads : 0);
     const int per = 32 / U;  // atoms per warp pass
     const int lane = threadIdx.x & 31;
     const int k = lane / U, u = lane - k * U;
@@ -241,11 +243,12 @@ __device__ __forceinline__ void stage_tile(const TileTable &T, const float4 *pos
         const int g0 = T.gstart[c], l0 = T.lstart[c], cnt = T.lstart[c + 1] - l0;
         for (int b = k; b < cnt && k < per; b += per) {
             const int g = g0 + b, l = l0 + b;
-            if (u == 0) {
+            if (u < P) {
                 cp_async16(spos + l, pos + g);
-            } else if (u <= kQuads) {
-                cp_async16(srec + (size_t)l * kRecQ + (u - 1) * (16 / sizeof(real)),
-                           rec + (size_t)g * 16 + (u - 1) * (16 / sizeof(real)));
+            } else if (u - P < kQuads) {
+                const int v = u - P;
+                cp_async16(srec + (size_t)l * kRecQ + v * (16 / sizeof(real)),
+                           rec + (size_t)g * 16 + v * (16 / sizeof(real)));
             } else if (sizeof(real) == 4) {
                 cp_async8(spair + 2 * (size_t)l, rec + (size_t)g * 16 + kRecQ);
             } else {
@@ -256,9 +259,83 @@ __device__ __forceinline__ void stage_tile(const TileTable &T, const float4 *pos
     stage_wait();
 }
 
-// Dynamic shared memory of a staged pass per staged atom: the position and
-// components 0..13 of one record.
+// The tile's own rows packed per atom in shared memory (the passes that
+// read them once per entry and need no positions): quad offsets of the own
+// atoms (a block scan of ceil(nn / 4)), the row quads and, per entry, the
+// switch weight from the forward pass.
+constexpr int kOwnCap = 512;    // own atoms of a tile whose rows are staged
+constexpr int kQuadCap = 1536;  // row quads of a tile staged
+__host__ __device__ constexpr int own_rows_bytes(int real_bytes)
+{
+    return ((kOwnCap + 1) * 4 + 15) / 16 * 16 + kQuadCap * (8 + 4 * real_bytes);
+}
+
 template <typename real>
-__host__ __device__ constexpr int staged_bytes() { return 16 + (kRecQ + 2) * (int)sizeof(real); }
+struct OwnRows {
+    int *qoff;    // [n_own + 1]
+    ushort4 *jq;  // [quads]
+    real *wq;     // [quads][4]
+};
+
+template <typename real>
+__device__ __forceinline__ OwnRows<real> own_rows_at(unsigned char *base)
+{
+    OwnRows<real> o;
+    o.qoff = reinterpret_cast<int *>(base);
+    o.jq = reinterpret_cast<ushort4 *>(base + ((kOwnCap + 1) * 4 + 15) / 16 * 16);
+    o.wq = reinterpret_cast<real *>(o.jq + kQuadCap);
+    return o;
+}
+
+// Stage the own rows and weights (cp.async, waited for by the next
+// stage_wait).  Returns false, the same in every thread, when they do not
+// fit (the pass then reads them from global memory).
+template <typename real>
+__device__ __forceinline__ bool stage_own_rows(const Sys &s, const TileTable &T, const OwnRows<real> &o)
+{
+    __shared__ int warp_sum[kTileThreads / 32];
+    __shared__ int qmax_sh;
+    if (T.n_own > kOwnCap) return false;
+    const size_t N = (size_t)s.n;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // each thread owns atoms 2t and 2t + 1 (kOwnCap = 2 kTileThreads)
+    const int a0 = 2 * threadIdx.x, a1 = a0 + 1;
+    const int q0 = a0 < T.n_own ? (s.nn[T.atom0 + a0] + 3) >> 2 : 0;
+    const int q1 = a1 < T.n_own ? (s.nn[T.atom0 + a1] + 3) >> 2 : 0;
+    int v = q0 + q1, incl = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
+    }
+    const int qm = __reduce_max_sync(0xffffffffu, max(q0, q1));
+    if (lane == 31) warp_sum[w] = incl;
+    if (threadIdx.x == 0) qmax_sh = 0;
+    __syncthreads();
+    if (lane == 0) atomicMax(&qmax_sh, qm);
+    int before = 0;
+    for (int k = 0; k < w; ++k) before += warp_sum[k];
+    const int ex = before + incl - v;
+    if (a0 <= T.n_own) o.qoff[a0] = ex;
+    if (a1 <= T.n_own) o.qoff[a1] = ex + q0;
+    __syncthreads();
+    const int total = o.qoff[T.n_own];
+    if (total > kQuadCap) return false;
+    const int qmax = qmax_sh;
+    // copy quad q of every own atom (quad rows are contiguous in the atoms)
+    for (int item = threadIdx.x; item < qmax * T.n_own; item += kTileThreads) {
+        const int q = item / T.n_own, a = item - q * T.n_own;
+        const int base = o.qoff[a];
+        if (q < o.qoff[a + 1] - base) {
+            const int slot = base + q;
+            const size_t src = (size_t)q * N + T.atom0 + a;
+            cp_async8(o.jq + slot, reinterpret_cast<const ushort4 *>(s.elist) + src);
+            const real *wsrc = reinterpret_cast<const real *>(s.wl) + 4 * src;
+            cp_async16(o.wq + 4 * slot, wsrc);
+            if (sizeof(real) == 8) cp_async16(o.wq + 4 * slot + 2, wsrc + 2);
+        }
+    }
+    return true;
+}
 
 }  // namespace metad

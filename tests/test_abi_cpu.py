@@ -96,10 +96,11 @@ def test_estimate_bytes_needs_no_gpu_and_grows_with_size(metad):
     small = metad.metad_estimate_bytes(metad.params_for(1000, [23.2, 23.2, 23.2]))
     big = metad.metad_estimate_bytes(metad.params_for(100_000, [106.0, 106.0, 106.0]))
     assert 0 < small < big
-    # under a KB per atom: 16-bit exact and Verlet rows (64 + 136 entries at
-    # most), three 64-byte records, positions, force sums
+    # under 2.5 KB per atom: 16-bit Verlet rows (136 entries), 16-bit exact
+    # rows (64 entries) with a weight and two cross-term halves per entry,
+    # three 64-byte records, positions
     per_atom = (big - small) / 99_000
-    assert 400 < per_atom < 1500, per_atom
+    assert 1000 < per_atom < 2500, per_atom
     with pytest.raises(metad.MetadError) as e:
         metad.metad_estimate_bytes(metad.params_for(10, [1.0, 10.0, 10.0]))
     assert e.value.status == metad.METAD_ERR_INVALID
@@ -166,5 +167,5 @@ def test_lattice_hills_take_five_doubles(metad):
     lat = metad.metad_estimate_bytes(metad.params_for(5000, [40.0, 40.0, 40.0], hill_capacity=10000,
                                                       lattice_cvs=True))
     # centres (live + staging) grow from 2 to 5 doubles per hill; lattice
-    # CVs imply the virial, whose three per-atom float 4-vector sums are added
-    assert lat - base == 2 * 3 * 8 * 10001 + 3 * 4 * 4 * 5000
+    # CVs imply the virial, whose per-atom float 4-vector sum is added
+    assert lat - base == 2 * 3 * 8 * 10001 + 4 * 4 * 5000
