@@ -45,7 +45,7 @@ WORKLOAD = ("1M-atom half-wurtzite/half-RSA-liquid periodic box (228.6 A), 2 CVs
 # adjoint gradient of w Y.G in the force pass; per atom ~500 for the neighbour
 # search and ~800 for the Q6 averaging and adjoint-seed gathers (split
 # evenly between those two passes).  Totals about 5e3 FP32 flop per atom.
-FLOP_PER_PAIR = {"cv_fwd": 200.0, "forces": 300.0}
+FLOP_PER_PAIR = {"cv_fwd": 200.0, "force_pairs": 300.0}
 FLOP_PER_ATOM = {"cv_fwd": 500.0, "cv_avg": 400.0, "adjoint": 400.0}
 # Algorithmic HBM bytes per atom-step with the neighbour list persisted
 # between steps: positions in (16 B), forces out (12 B) and the list read
@@ -145,11 +145,10 @@ def dist_env():
 
 # Sources that make up the per-atom kernels; a profile summary records their
 # SHA-1 when its counters were taken.
-KERNEL_SOURCES = ("paper_2510_06873_gb300/csrc/k_cv.cu", "paper_2510_06873_gb300/csrc/metad_impl.cuh",
-                  "paper_2510_06873_gb300/csrc/tiles.cuh")
+KERNEL_SOURCES = ("paper_2510_06873_gb300/csrc/k_cv.cu", "paper_2510_06873_gb300/csrc/metad_impl.cuh")
 # The kernel each timed stage launches (its ncu summary is profiles/<kernel>.md).
-STAGE_KERNEL = {"cv_fwd": "k_tile_fwd", "cv_avg": "k_tile_avg", "adjoint": "k_tile_adj", "forces": "k_tile_force",
-                "neighbors": "k_verlet", "gather": "k_gather_check", "bias": "k_bias"}
+STAGE_KERNEL = {"cv_fwd": "k_cv_fwd", "cv_avg": "k_cv_avg", "adjoint": "k_adjoint", "force_pairs": "k_force_pairs",
+                "force_gather": "k_force_gather", "neighbors": "k_verlet", "gather": "k_gather_check", "bias": "k_bias"}
 
 
 def kernel_sources_sha1() -> str:
@@ -426,7 +425,7 @@ def run_metad(args):
                            f"counts; {pairs / n:.2f} unordered pairs per atom)"}
     step_ms = ms / args.steps
     step_bytes = STEP_BYTES_PER_ATOM * n
-    step_flops = sum(stage_flops(k, n, pairs) for k in ("cv_fwd", "cv_avg", "adjoint", "forces"))
+    step_flops = sum(stage_flops(k, n, pairs) for k in ("cv_fwd", "cv_avg", "adjoint", "force_pairs"))
     # every per-atom kernel against both ceilings: algorithmic flops against
     # the measured FP32 peak, profiled DRAM bytes (ncu, per launch) against HBM
     per_kernel = {}

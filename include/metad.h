@@ -81,7 +81,7 @@ typedef struct {
     int32_t precision;      /* 0: FP32 pair arithmetic, FP64 reductions and
                                hills; 1: FP64 throughout */
     int32_t max_neighbors;  /* per-atom capacity of the neighbour list (0: 64;
-                               rounded up to a multiple of 4; at most 256) */
+                               rounded up to a multiple of 4) */
     int32_t device;         /* CUDA device ordinal */
     int32_t step_graph;     /* 1: metad_step replays a captured CUDA graph of
                                its kernels, one per combination of buffers,
@@ -96,11 +96,7 @@ typedef struct {
                                exact rc list is recomputed every step. */
     int32_t cv_kind;        /* METAD_CV_COORDINATION (default), METAD_CV_TORSION
                                or METAD_CV_NEAREST (below) */
-    int32_t tile_atoms;     /* 0 (default): the library's staging capacity;
-                               > 0: at most this many atoms of a tile and its
-                               one-cell shell are staged in shared memory per
-                               pass, a larger tile reads its atoms from global
-                               memory (same results, slower; for testing) */
+    int32_t reserved0;      /* 0 */
     double softmin_beta;    /* METAD_CV_NEAREST: 0 (default) = the exact nearest
                                distance; > 0 = its soft minimum with this beta
                                (1/Angstrom), see metad_set_cv_atoms */
@@ -287,7 +283,7 @@ metad_status metad_step_host(metad_ctx *ctx, const float *pos_host, float *force
  * stages are recorded).  end synchronises and writes, per stage index
  * 0..METAD_NUM_STAGES-1 (names from metad_stage_name), the summed device
  * milliseconds and the number of records (either pointer may be NULL). */
-#define METAD_NUM_STAGES 9
+#define METAD_NUM_STAGES 11
 metad_status metad_profile_begin(metad_ctx *ctx, int32_t max_records);
 metad_status metad_profile_end(metad_ctx *ctx, double *ms_per_stage, int32_t *records_per_stage);
 const char *metad_stage_name(int32_t stage);

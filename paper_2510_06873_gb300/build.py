@@ -20,15 +20,13 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmetad.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cu", "k_neighbors.cu", "k_cv.cu", "k_bias.cu", "k_fes.cu", "k_gcv.cu", "k_static.cu", "k_peak.cu"]
-# The FP64 hill and grid arithmetic (bias and free-energy kernels), the
-# FP64 torsion / nearest-distance CVs and the per-atom passes are compiled
-# without multiply-add contraction: every product and sum rounds as written
-# (the passes write their fused multiply-adds out), so the single-system and
-# batched instantiations, and a tile staged or not, give the same bits (the
-# compiler may otherwise fuse differently in each) and a squared distance
-# rounds as its plain definition.
-FILE_FLAGS = {"k_bias.cu": ["-fmad=false"], "k_fes.cu": ["-fmad=false"], "k_gcv.cu": ["-fmad=false"],
-              "k_cv.cu": ["-fmad=false"]}
+# The FP64 hill and grid arithmetic (bias and free-energy kernels) and the
+# FP64 torsion / nearest-distance CVs are compiled without multiply-add
+# contraction: every product and sum rounds on its own, so the single-system
+# and batched instantiations give the same bits (the compiler may otherwise
+# fuse differently in each) and a squared distance rounds as its plain
+# definition.
+FILE_FLAGS = {"k_bias.cu": ["-fmad=false"], "k_fes.cu": ["-fmad=false"], "k_gcv.cu": ["-fmad=false"]}
 
 
 def nvcc() -> str:
@@ -56,7 +54,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
     os.makedirs(BUILD_DIR, exist_ok=True)
     cc = nvcc()
-    headers = [os.path.join(CSRC, h) for h in ("metad_impl.cuh", "hills.cuh", "tiles.cuh")] + [os.path.join(INCLUDE, "metad.h")]
+    headers = [os.path.join(CSRC, "metad_impl.cuh"), os.path.join(CSRC, "hills.cuh"), os.path.join(INCLUDE, "metad.h")]
     srcs = [s for s in SOURCES if os.path.exists(os.path.join(CSRC, s))]
     jobs = []
     objs = []

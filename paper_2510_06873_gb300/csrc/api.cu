@@ -12,7 +12,6 @@
 
 #include "metad.h"
 #include "metad_impl.cuh"
-#include "tiles.cuh"
 
 using metad::Sys;
 
@@ -32,9 +31,7 @@ struct metad_ctx {
     bool forces_done = false;     // a bias_forces ran since the last box or CV change
     int nc_created[3] = {1, 1, 1};  // cells per axis at creation (the allocation)
     int ncell_alloc = 1;
-    bool filter_pending = false;  // exact rows not yet filtered from the Verlet rows
-    int part_stride_alloc = 0;    // partial-sum slots allocated at creation
-    int tiles_alloc = 0;          // tile table entries allocated at creation
+    bool filter_pending = false;  // exact rows not yet compacted from the Verlet rows
     bool failed = false;
     std::string last_error;
     std::vector<void *> allocs;
@@ -92,13 +89,25 @@ metad_status cuda_check(metad_ctx *c, cudaError_t e, const char *what)
 
 metad_status launched(metad_ctx *c, const char *what) { return cuda_check(c, cudaGetLastError(), what); }
 
-enum Stage { ST_BIN, ST_NBR, ST_CV_FWD, ST_CV_AVG, ST_BIAS, ST_ADJ, ST_FORCE, ST_DEPOSIT, ST_OTHER, ST_COUNT };
+enum Stage {
+    ST_BIN,
+    ST_NBR,
+    ST_CV_FWD,
+    ST_CV_AVG,
+    ST_CV_SUM,
+    ST_BIAS,
+    ST_ADJ,
+    ST_FORCE,
+    ST_FGATHER,
+    ST_DEPOSIT,
+    ST_OTHER,
+    ST_COUNT
+};
 // "gather": positions into cell order + rebuild test; "neighbors": the
 // conditional rebuild chain (and a stand-alone exact filter); "cv_fwd" holds
-// the exact filter with the forward CV pass; "cv_avg" the Q6 average with
-// the CV sums; "forces" the force pass.
-const char *kStageNames[ST_COUNT] = {"gather", "neighbors", "cv_fwd", "cv_avg", "bias",
-                                     "adjoint", "forces",   "deposit", "other"};
+// the fused exact filter.
+const char *kStageNames[ST_COUNT] = {"gather",      "neighbors",    "cv_fwd",  "cv_avg", "cv_sum", "bias", "adjoint",
+                                     "force_pairs", "force_gather", "deposit", "other"};
 
 // Brackets the kernels of one stage with CUDA events while profiling is on,
 // and counts the kernels launched.
@@ -120,18 +129,6 @@ struct StageScope {
         if (idx >= 0) cudaEventRecord(c->prof_ev[2 * idx + 1], st);
     }
 };
-
-// The force pass (a8): with the Q6 CV the tile force pass, else the
-// coordination-number forces alone.
-void launch_forces(metad_ctx *c, float *forces_dev, int32_t accumulate, double scale)
-{
-    Sys t = c->sys;
-    t.F_out = forces_dev;
-    t.accumulate = accumulate ? 1 : 0;
-    t.fscale = scale;
-    StageScope st(c, ST_FORCE, 1);
-    metad::launch_tile_pass(t, c->p.n_cv == 2 ? metad::kPassForce : metad::kPassForceCn, 0, c->stream);
-}
 
 template <typename T>
 metad_status dalloc(metad_ctx *c, T **ptr, size_t count)
@@ -262,11 +259,7 @@ metad_status validate(const metad_params *p, std::string &why)
         for (int a = 0; a < 3; ++a)
             if (!(p->sigma_lattice[a] > 0)) { why = "sigma_lattice must be positive"; return METAD_ERR_INVALID; }
     }
-    if (p->max_neighbors < 0 || p->max_neighbors > 256) {
-        why = "max_neighbors must be in [0, 256]";
-        return METAD_ERR_INVALID;
-    }
-    if (p->tile_atoms < 0) { why = "tile_atoms < 0"; return METAD_ERR_INVALID; }
+    if (p->max_neighbors < 0) { why = "max_neighbors < 0"; return METAD_ERR_INVALID; }
     if (!(p->skin >= 0.0) || !std::isfinite(p->skin)) { why = "skin must be >= 0"; return METAD_ERR_INVALID; }
     return METAD_OK;
 }
@@ -323,13 +316,11 @@ metad_status setup_system(metad_ctx *c)
         y.always_rebuild = c->p.skin > 0.0 ? 0 : 1;
         const double grow = std::pow(rv / c->p.rc, 3.0);
         y.max_vnb = ((int)std::ceil(y.max_nb * grow) + 7) / 8 * 8;
+        // mirror slots put i's Verlet position (8 bits) beside j (23 bits)
+        // in an entry's tag, and count exact entries in a byte
+        y.mirror = (n < (1 << metad::kMirrorShift) && y.max_vnb <= 256 && y.max_nb <= 255) ? 1 : 0;
+        y.vround_stride = y.max_vnb / 8;  // one u16 per 8 Verlet entries, rows packed
     }
-    y.fp64 = c->p.precision == 1 ? 1 : 0;
-    {
-        const int cap = y.fp64 ? metad::kStageCapF64 : metad::kStageCapF32;
-        y.stage_cap = c->p.tile_atoms > 0 ? std::min(c->p.tile_atoms, cap) : cap;
-    }
-    y.tiles = metad::tiles_axis(y.nc[0]) * metad::tiles_axis(y.nc[1]) * metad::tiles_axis(y.nc[2]);
     y.sw_n = c->p.sw_n;
     y.sw_m = c->p.sw_m;
     y.sw_nf = (float)c->p.sw_n;
@@ -365,55 +356,39 @@ metad_status setup_system(metad_ctx *c)
         y.ghi[a] = c->p.grid_hi[a];
         y.gh[a] = c->p.grid_on ? (y.ghi[a] - y.glo[a]) / (y.gn[a] - 1) : 1.0;
     }
-    // one FP64 partial per block of the pass holding the CV sums (a block per
-    // tile; slot 0: CN, 1: Q6), three per block of the force pass's virial
-    // (slot 1) and of the hill kernel (slot 2), the neighbour statistics
+    // one FP64 partial per block of the per-atom kernels (slot 0: CN, 1: Q6),
+    // three per block of the hill kernel (slot 2), the neighbour statistics
     // (slot 3)
-    y.part_stride = std::max({3 * y.tiles, 3 * ((n + metad::kTileThreads - 1) / metad::kTileThreads),
-                              metad::kMaxBiasBlocks * (metad::kMaxCv + 1)});
+    y.part_stride = std::max(metad::group_grid(n), metad::kMaxBiasBlocks * (metad::kMaxCv + 1));
     return METAD_OK;
 }
 
-// Cell ranks, tile by tile: tiles of up to 3 x 3 x 3 cells in Morton order
-// of their coordinates, the cells of a tile in z, y, x order, so the atoms
-// of a tile are one contiguous range of the sorted order.  Uploads the rank
-// table (sized for the cells at creation; a box change never asks for more)
-// and the tile coordinates.
+// Morton ranks of the cells (sort cell coordinates by interleaved bits) and
+// their inverse, uploaded to the rank tables (sized for the cells at
+// creation; a box change never asks for more).
 metad_status upload_cell_ranks(metad_ctx *c)
 {
-    Sys &y = c->sys;
-    int nt[3];
-    for (int a = 0; a < 3; ++a) nt[a] = metad::tiles_axis(y.nc[a]);
-    std::vector<std::pair<uint32_t, int>> key((size_t)nt[0] * nt[1] * nt[2]);
-    for (int z = 0; z < nt[2]; ++z)
-        for (int yy = 0; yy < nt[1]; ++yy)
-            for (int x = 0; x < nt[0]; ++x) {
-                const int id = (z * nt[1] + yy) * nt[0] + x;
+    const Sys &y = c->sys;
+    std::vector<std::pair<uint32_t, int>> key(y.ncell);
+    for (int z = 0; z < y.nc[2]; ++z)
+        for (int yy = 0; yy < y.nc[1]; ++yy)
+            for (int x = 0; x < y.nc[0]; ++x) {
+                int id = (z * y.nc[1] + yy) * y.nc[0] + x;
                 key[id] = {spread3(x) | (spread3(yy) << 1) | (spread3(z) << 2), id};
             }
     std::sort(key.begin(), key.end());
-    std::vector<int> r(y.ncell), txyz(key.size());
-    int base = 0;
-    for (size_t t = 0; t < key.size(); ++t) {
-        const int id = key[t].second;
-        const int tx = id % nt[0], ty = (id / nt[0]) % nt[1], tz = id / (nt[0] * nt[1]);
-        txyz[t] = tx | (ty << 10) | (tz << 20);
-        const int c0[3] = {tx * metad::kTileCells, ty * metad::kTileCells, tz * metad::kTileCells};
-        int e[3];
-        for (int a = 0; a < 3; ++a) e[a] = std::min(metad::kTileCells, y.nc[a] - c0[a]);
-        for (int lz = 0; lz < e[2]; ++lz)
-            for (int ly = 0; ly < e[1]; ++ly)
-                for (int lx = 0; lx < e[0]; ++lx)
-                    r[((c0[2] + lz) * y.nc[1] + (c0[1] + ly)) * y.nc[0] + (c0[0] + lx)] =
-                        base + (lz * e[1] + ly) * e[0] + lx;
-        base += e[0] * e[1] * e[2];
+    std::vector<int> r(y.ncell), xr(y.ncell);
+    for (int k = 0; k < y.ncell; ++k) {
+        int id = key[k].second;
+        int x = id % y.nc[0], yy = (id / y.nc[0]) % y.nc[1], z = id / (y.nc[0] * y.nc[1]);
+        r[id] = k;
+        xr[k] = x | (yy << 10) | (z << 20);
     }
-    y.tiles = (int)key.size();
     metad_status s;
     if ((s = cuda_check(c, cudaMemcpy(const_cast<int *>(y.rank_of_xyz), r.data(), sizeof(int) * y.ncell,
                                       cudaMemcpyHostToDevice), "rank upload")) ||
-        (s = cuda_check(c, cudaMemcpy(const_cast<int *>(y.tile_xyz), txyz.data(), sizeof(int) * txyz.size(),
-                                      cudaMemcpyHostToDevice), "tile upload")))
+        (s = cuda_check(c, cudaMemcpy(const_cast<int *>(y.xyz_of_rank), xr.data(), sizeof(int) * y.ncell,
+                                      cudaMemcpyHostToDevice), "rank upload")))
         return s;
     return METAD_OK;
 }
@@ -429,9 +404,8 @@ std::vector<double> pack_centres(const metad_ctx *c, const double *centers, int 
 }
 
 struct Buffers {
-    int *rank_xyz = nullptr, *tile_xyz = nullptr;
-    int4 *tile_tab = nullptr;
-    char *rec = nullptr, *vec = nullptr, *ent = nullptr;
+    int *rank_xyz = nullptr, *xyz_rank = nullptr;
+    char *rb = nullptr, *wlb = nullptr, *pfb = nullptr, *geob = nullptr;
 };
 
 // Every device buffer of a context in one list: alloc(&ptr, count) allocates
@@ -459,21 +433,20 @@ metad_status state_buffers(metad_ctx *c, Buffers &b, Alloc &&alloc)
         y.cand_slot = slot;
         return METAD_OK;
     }
-    // per-atom records [n][16] (rq; rb, rh with the Q6 CV) and 4-vectors
-    // [n][4] (fc; fb with the Q6 CV; wc, wb with the virial)
-    const size_t nrec = (c->p.n_cv == 2 ? 3 : 1) * (size_t)16 * n;
-    const size_t nvec = (y.virial || c->p.lattice_cvs ? 2 : 1) * (size_t)4 * n;
-    // per-entry weights and cross terms (Q6 CV only): [max_nb / 4][n][4] each
-    const size_t nent = c->p.n_cv == 2 ? 3 * (size_t)y.max_nb * n : 4;
-    if ((s = alloc(&y.pos_s, n)) || (s = alloc(&y.perm, n)) ||
+    if ((s = alloc(&y.pos_s, n)) || (s = alloc(&y.perm, n)) || (s = alloc(&y.scell, n)) ||
         (s = alloc(&y.ucell, n)) || (s = alloc(&y.uslot, n)) || (s = alloc(&y.cell_count, y.ncell)) ||
         (s = alloc(&y.cell_start, (size_t)y.ncell + 1)) || (s = alloc(&y.scan_part, y.ncell / 4096 + 2)) ||
-        (s = alloc(&b.rank_xyz, y.ncell)) || (s = alloc(&b.tile_xyz, std::max(y.tiles, 1))) ||
-        (s = alloc(&b.tile_tab, (size_t)metad::kTileTableWords * std::max(y.tiles, 1))) ||
-        (s = alloc(&y.elist, (size_t)y.max_nb * n)) || (s = alloc(&y.nn, n)) ||
-        (s = alloc(&y.pos_ref, n)) || (s = alloc(&y.vlist, (size_t)y.max_vnb * n)) || (s = alloc(&y.vnn, n)) ||
-        (s = alloc(&y.flag, 1)) || (s = alloc(&y.rebuilds, 1)) || (s = alloc(&y.Lref, 4)) ||
-        (s = alloc(&b.rec, rs * nrec)) || (s = alloc(&b.vec, rs * nvec)) || (s = alloc(&b.ent, rs * nent)) ||
+        (s = alloc(&b.rank_xyz, y.ncell)) || (s = alloc(&b.xyz_rank, y.ncell)) ||
+        (s = alloc(&y.nbr, (size_t)y.max_nb * n)) || (s = alloc(&y.nn, n)) || (s = alloc(&y.nh, n)) ||
+        (s = alloc(&y.vnh, n)) || (s = alloc(&b.wlb, 2 * rs * (size_t)y.max_nb * n)) ||
+        (s = alloc(&b.pfb, rs * 4 * (size_t)y.max_nb * n)) || (s = alloc(&b.geob, rs * 4 * (size_t)y.max_nb * n)) ||
+        (s = alloc(&y.pos_ref, n)) ||
+        (s = alloc(&y.vnbr, (size_t)y.max_vnb * n)) || (s = alloc(&y.vnn, n)) || (s = alloc(&y.flag, 1)) ||
+        // the filter reads each row's first 32 bytes: rows shorter than that
+        // read into the next row, the last one into this padding
+        (s = alloc(&y.vmirror, y.mirror ? (size_t)y.max_vnb * n + 32 : 1)) ||
+        (s = alloc(&y.vround, y.mirror ? (size_t)y.vround_stride * n : 1)) || (s = alloc(&y.rows_fresh, 1)) ||
+        (s = alloc(&y.rebuilds, 1)) || (s = alloc(&y.Lref, 4)) || (s = alloc(&b.rb, rs * (nq * 3 + (size_t)n * 4 + 64))) ||
         (s = alloc(&y.part, (size_t)y.part_stride * 4)) || (s = alloc(&y.ticket, 8)) ||
         (s = alloc(&y.scal, metad::kNumScal)) || (s = alloc(&y.err, 1)) ||
         (s = alloc(&y.hc, (size_t)y.hstride * ((size_t)y.hill_cap + 1))) ||
@@ -652,30 +625,20 @@ metad_status metad_create(const metad_params *p, metad_ctx **out)
         *out = c;
         return METAD_OK;
     }
-    {
-        const size_t nrec = (size_t)16 * n, nvec = (size_t)4 * n;
-        const bool q6 = c->p.n_cv == 2, vir = y.virial != 0;
-        y.rq = bf.rec;
-        y.rb = q6 ? bf.rec + rs * nrec : nullptr;
-        y.rh = q6 ? bf.rec + rs * 2 * nrec : nullptr;
-        char *v = bf.vec;
-        auto take = [&](bool on) {
-            char *p = on ? v : nullptr;
-            if (on) v += rs * nvec;
-            return p;
-        };
-        y.fc = take(true);
-        y.wc = take(vir);
-        const size_t nent = (size_t)y.max_nb * n;
-        y.wl = q6 ? bf.ent : nullptr;
-        y.eq = q6 ? bf.ent + rs * nent : nullptr;
-        y.dq = q6 ? bf.ent + rs * 2 * nent : nullptr;
-    }
-    y.tile_tab = bf.tile_tab;
-    y.rank_of_xyz = bf.rank_xyz;
-    y.tile_xyz = bf.tile_xyz;
-    c->tiles_alloc = y.tiles;
-    c->part_stride_alloc = y.part_stride;
+    int *rank_xyz = bf.rank_xyz, *xyz_rank = bf.xyz_rank;
+    char *rb = bf.rb, *wlb = bf.wlb, *pfb = bf.pfb;
+    // records first (16-element rows stay 64 / 128 B aligned), scalars after
+    y.q = rb;
+    y.b = rb + rs * nq;
+    y.h = rb + rs * 2 * nq;
+    y.cn = rb + rs * 3 * nq;
+    y.W = rb + rs * (3 * nq + n);
+    y.qb6 = rb + rs * (3 * nq + 2 * (size_t)n);
+    y.wl = wlb;
+    y.pairF = pfb;
+    y.geo = bf.geob;
+    y.rank_of_xyz = rank_xyz;
+    y.xyz_of_rank = xyz_rank;
     for (int a = 0; a < 3; ++a) c->nc_created[a] = y.nc[a];
     c->ncell_alloc = y.ncell;
     if ((s = upload_cell_ranks(c))) {
@@ -695,8 +658,11 @@ metad_status metad_create(const metad_params *p, metad_ctx **out)
     cudaMemsetAsync(y.nn, 0, sizeof(int) * (size_t)n, c->stream);
     // the cell counters start at zero; every rebuild's scan leaves them zero
     cudaMemsetAsync(y.cell_count, 0, sizeof(int) * (size_t)c->ncell_alloc, c->stream);
+    cudaMemsetAsync(y.nh, 0, sizeof(int) * (size_t)n, c->stream);
+    cudaMemsetAsync(y.vnh, 0, sizeof(int) * (size_t)n, c->stream);
     cudaMemsetAsync(y.vnn, 0, sizeof(int) * (size_t)n, c->stream);
     cudaMemsetAsync(y.rebuilds, 0, sizeof(unsigned long long), c->stream);
+    cudaMemsetAsync(y.rows_fresh, 0, sizeof(int), c->stream);
     {
         const float Lr[4] = {y.Lhi[0], y.Lhi[1], y.Lhi[2], 0.0f};
         if ((s = cuda_check(c, cudaMemcpy(y.Lref, Lr, sizeof(Lr), cudaMemcpyHostToDevice), "box upload"))) {
@@ -763,13 +729,16 @@ metad_status metad_cv_forward(metad_ctx *c, double *cv_host, double *per_atom_de
         metad::launch_gcv_forward(c->sys, c->fp64, c->stream);
     } else {
     {
-        StageScope t(c, ST_CV_FWD, 1);  // the exact rows, the CV forward pass (the CN sum without Q6)
-        metad::launch_tile_pass(c->sys, metad::kPassFwd, 1, c->stream);
+        StageScope t(c, ST_CV_FWD, 1);
+        metad::launch_cv_fwd(c->sys, c->fp64, c->filter_pending ? 1 : 0, c->stream);
         c->filter_pending = false;
     }
     if (c->p.n_cv == 2) {
         StageScope t(c, ST_CV_AVG, 1);  // with the CV sums
-        metad::launch_tile_pass(c->sys, metad::kPassAvg, 0, c->stream);
+        metad::launch_cv_avg(c->sys, c->fp64, c->stream);
+    } else {
+        StageScope t(c, ST_CV_SUM, 1);
+        metad::launch_cv_sum(c->sys, c->fp64, c->stream);
     }
     if (per_atom_dev) {
         StageScope t(c, ST_OTHER, 1);
@@ -842,9 +811,16 @@ metad_status metad_bias_forces(metad_ctx *c, float *forces_dev, int32_t accumula
     c->forces_done = true;
     if (c->p.n_cv == 2) {
         StageScope t(c, ST_ADJ, 1);
-        metad::launch_tile_pass(c->sys, metad::kPassAdj, 0, c->stream);
+        metad::launch_adjoint(c->sys, c->fp64, c->stream);
     }
-    launch_forces(c, forces_dev, accumulate, scale);
+    {
+        StageScope t(c, ST_FORCE, 1);
+        metad::launch_force_pairs(c->sys, c->fp64, scale, c->stream);
+    }
+    {
+        StageScope t(c, ST_FGATHER, 1);
+        metad::launch_force_gather(c->sys, c->fp64, forces_dev, accumulate ? 1 : 0, c->stream);
+    }
     return launched(c, "bias_forces");
 }
 
@@ -916,22 +892,15 @@ metad_status metad_set_box(metad_ctx *c, const double *box_host)
         return fail(c, s, "box");
     }
     if (c->p.cv_kind == METAD_CV_COORDINATION) {
-        // cells no smaller than rc + skin, no more than allocated (on every
-        // axis, so the tiles never outnumber their allocation either)
-        if (y.nc[0] > c->nc_created[0] || y.nc[1] > c->nc_created[1] || y.nc[2] > c->nc_created[2]) {
+        // cells no smaller than rc + skin, no more than allocated
+        if (y.ncell > c->ncell_alloc) {
             for (int a = 0; a < 3; ++a) y.nc[a] = std::min(y.nc[a], c->nc_created[a]);
             y.ncell = y.nc[0] * y.nc[1] * y.nc[2];
             for (int a = 0; a < 3; ++a) y.inv_h[a] = (float)(y.nc[a] / c->p.box[a]);
         }
-        y.part_stride = c->part_stride_alloc;
-        y.tiles = metad::tiles_axis(y.nc[0]) * metad::tiles_axis(y.nc[1]) * metad::tiles_axis(y.nc[2]);
         if (y.nc[0] != nc_before[0] || y.nc[1] != nc_before[1] || y.nc[2] != nc_before[2]) {
-            // new cell ranks and tiles: wait for steps in flight that read the
-            // old ones; the sorted order and the rows belong to the old cells,
-            // so the next step rebuilds them
-            const int one = 1;
-            if ((s = cuda_check(c, cudaStreamSynchronize(c->stream), "set_box")) || (s = upload_cell_ranks(c)) ||
-                (s = cuda_check(c, cudaMemcpy(y.flag, &one, sizeof(int), cudaMemcpyHostToDevice), "flag")))
+            // new cell ranks: wait for steps in flight that read the old ones
+            if ((s = cuda_check(c, cudaStreamSynchronize(c->stream), "set_box")) || (s = upload_cell_ranks(c)))
                 return s;
         }
         // the Verlet rows stay while the atoms' moves and the box change fit in
@@ -1107,7 +1076,7 @@ metad_status metad_export_neighbors(metad_ctx *c, int64_t *pairs_host, int64_t c
     }
     if (c->filter_pending) {
         StageScope t(c, ST_NBR, 1);
-        metad::launch_tile_pass(c->sys, metad::kPassFwd, 0, c->stream);
+        metad::launch_filter(c->sys, c->fp64, c->stream);
         c->filter_pending = false;
     }
     {
@@ -1182,10 +1151,17 @@ metad_status step_overlapped(metad_ctx *c, const float *pos_dev, float *forces_d
     if ((s = cuda_check(c, cudaEventRecord(c->ev_join, c->side), "join"))) return s;
     if (c->p.n_cv == 2) {
         StageScope t(c, ST_ADJ, 1);
-        metad::launch_tile_pass(c->sys, metad::kPassAdj, 0, c->stream);
+        metad::launch_adjoint(c->sys, c->fp64, c->stream);
     }
     if ((s = cuda_check(c, cudaStreamWaitEvent(c->stream, c->ev_join, 0), "join"))) return s;
-    launch_forces(c, forces_dev, accumulate, 1.0);
+    {
+        StageScope t(c, ST_FORCE, 1);
+        metad::launch_force_pairs(c->sys, c->fp64, 1.0, c->stream);
+    }
+    {
+        StageScope t(c, ST_FGATHER, 1);
+        metad::launch_force_gather(c->sys, c->fp64, forces_dev, accumulate ? 1 : 0, c->stream);
+    }
     if ((s = launched(c, "step"))) return s;
     c->have_bias = true;
     c->forces_done = true;
@@ -1373,7 +1349,7 @@ metad_status metad_neighbor_stats(metad_ctx *c, int64_t *entries, int32_t *max_p
     int *mx = reinterpret_cast<int *>(sum + 1);
     if (c->filter_pending) {
         StageScope t(c, ST_NBR, 1);
-        metad::launch_tile_pass(c->sys, metad::kPassFwd, 0, c->stream);
+        metad::launch_filter(c->sys, c->fp64, c->stream);
         c->filter_pending = false;
     }
     {
@@ -1595,41 +1571,24 @@ metad_status metad_batch_step(metad_batch *b, const float *const *pos_dev, float
             b->launches += 3 + (any_deposit ? 1 : 0);
         }
     } else {
-    // dynamic shared memory of each pass: the largest of the systems'
-    int smem[metad::kNumPasses] = {}, verlet_smem = 0;
-    for (int k = 0; k < n; ++k) {
-        if (active && !active[k]) continue;
-        for (int q = 0; q < metad::kNumPasses; ++q) smem[q] = std::max(smem[q], metad::tile_smem(hs[k], q));
-        verlet_smem = std::max(verlet_smem, hs[k].stage_cap * 16);
-    }
-    const int vir = b->ctx[0]->sys.virial;
-    const bool q6 = b->ncv == 2;
     metad::launch_batch_gather(rows[metad::GK_ATOM256], totals[metad::GK_ATOM256], b->stream);
-    metad::launch_batch_rebuild(rows, totals, verlet_smem, b->stream);
-    // the forward pass holds the CN sum without a Q6 pass: its grid stays
-    const int fwd_kind = q6 ? metad::GK_TILES : metad::GK_TILES_SUM;
-    metad::launch_batch_pass(rows[fwd_kind], totals[fwd_kind], metad::kPassFwd, b->fp64, 1, vir,
-                             smem[metad::kPassFwd], b->stream);
-    if (q6)
-        metad::launch_batch_pass(rows[metad::GK_TILES_SUM], totals[metad::GK_TILES_SUM], metad::kPassAvg, b->fp64, 0,
-                                 vir, smem[metad::kPassAvg], b->stream);
+    metad::launch_batch_rebuild(rows, totals, b->stream);
+    metad::launch_batch_cv(rows[metad::GK_GROUPS], totals[metad::GK_GROUPS], rows[metad::GK_CV], totals[metad::GK_CV],
+                           rows[metad::GK_SUM], totals[metad::GK_SUM], b->fp64, b->ncv, b->stream);
     // the hill kernel on the side stream, concurrent with the adjoint
     cudaEventRecord(b->ev_fork, b->stream);
     cudaStreamWaitEvent(b->side, b->ev_fork, 0);
     metad::launch_batch_bias(rows[metad::GK_HILLS], totals[metad::GK_HILLS], 0, b->side);
     cudaEventRecord(b->ev_join, b->side);
-    if (q6)
-        metad::launch_batch_pass(rows[metad::GK_TILES], totals[metad::GK_TILES], metad::kPassAdj, b->fp64, 0, vir,
-                                 smem[metad::kPassAdj], b->stream);
+    metad::launch_batch_force(rows[metad::GK_GROUPS], totals[metad::GK_GROUPS], rows[metad::GK_ATOM32],
+                              totals[metad::GK_ATOM32], rows[metad::GK_ATOM128], totals[metad::GK_ATOM128], b->fp64,
+                              b->ncv, b->ctx[0]->sys.virial, b->stream, 1);
     cudaStreamWaitEvent(b->stream, b->ev_join, 0);
-    if (q6)
-        metad::launch_batch_pass(rows[metad::GK_TILES], totals[metad::GK_TILES], metad::kPassForce, b->fp64, 0, vir,
-                                 smem[metad::kPassForce], b->stream);
-    else
-        metad::launch_batch_pass(rows[metad::GK_ATOM256], totals[metad::GK_ATOM256], metad::kPassForceCn, b->fp64, 0,
-                                 vir, 0, b->stream);
+    metad::launch_batch_force(rows[metad::GK_GROUPS], totals[metad::GK_GROUPS], rows[metad::GK_ATOM32],
+                              totals[metad::GK_ATOM32], rows[metad::GK_ATOM128], totals[metad::GK_ATOM128], b->fp64,
+                              b->ncv, b->ctx[0]->sys.virial, b->stream, 2);
     if (any_deposit) metad::launch_batch_bias(rows[metad::GK_DEPOSIT], totals[metad::GK_DEPOSIT], 1, b->stream);
-    b->launches += 1 + 6 + 1 + (q6 ? 4 : 2) + (any_deposit ? 1 : 0);
+    b->launches += 1 + 6 + 2 + 1 + (b->ncv == 2 ? 3 : 2) + (any_deposit ? 1 : 0);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {

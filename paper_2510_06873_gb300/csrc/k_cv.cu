@@ -1,8 +1,4 @@
-// Steps a3-a8 on spatial tiles: the exact neighbour rows with the CV
-// forward pass (a3-a4), the local Q6 average with the CV sums (a5), the
-// adjoint (a7) and the bias forces (a8).  One block per tile of cells; the
-// tile's atoms and its one-cell shell are staged in shared memory
-// (tiles.cuh), and every neighbour read of a pass comes from there.
+// Steps a4-a5 (CV forward) and a7-a8 (adjoint and bias forces).
 //
 // Per-atom definitions (sorted order i; N(i) the full neighbour list):
 //   w_ij = s(r_ij)                 rational switch, stretched to vanish at rc
@@ -16,18 +12,15 @@
 //   g_m(k) = b_m(k) + sum_i w_ik b_m(i)                        ds2/dq_m(k)
 //   h_m(k) = g_m(k) / W_k                                      ds2/dQ_m(k)
 //   gam_k  = h(k).q(k) + b(k).qb(k)                            -ds2/dW_k
-// Force on atom i from its own row, every directed entry (no pair slots and
-// no scatter; deterministic, no atomics), d = r_j - r_i, v_ij = w'(r) d / r:
-//   F_i = V1 (2/N) sum_j [unlike] v_ij
-//       + V2 sum_j { [(h_i + h_j).Y - gam_i - gam_j] v_ij + w grad_d((h_i + h_j).Y)
-//                    + [b_i.q_j + b_j.q_i] v_ij }
-// (V_d = dV/ds_d; F_i = sum_j dV/dd_ij).  The sums that need no dV/ds are
-// taken by the passes that hold their records:
-//   FC_i = sum_j [unlike] v_ij                     forward pass
-//   FB_i = sum_m b_m(i) sum_j q_m(j) v_ij          Q6 pass (before b_i is known)
-//        + sum_j (q_i.b_j) v_ij                    adjoint pass
-// and the force pass adds V1 (2/N) FC_i + V2 FB_i to its own sum.
-#include "tiles.cuh"
+//   per pair (i, j), d = r_j - r_i:
+//     ds2/dw = (h_i + h_j).Y - gam_i - gam_j + b(i).q(j) + b(j).q(i)
+//     ds2/dd = ds2/dw w'(r) d/r + w sum_m (h_m(i)+h_m(j)) dY_m/dd
+//     ds1/dd = (2/N) w'(r) d/r [unlike]
+//   F_i = sum_{j in N(i)} (V1 ds1/dd + V2 ds2/dd)
+// The CV passes walk full rows (each atom gathers its own sums); the force
+// evaluates each unordered pair once and gathers per atom in a fixed order:
+// no floating-point atomics, bit-reproducible.
+#include "metad_impl.cuh"
 
 namespace metad {
 
@@ -63,29 +56,17 @@ __device__ __forceinline__ float ylm_dc<float>(int m, int k) { return c_ylm.dpf[
 template <>
 __device__ __forceinline__ double ylm_dc<double>(int m, int k) { return c_ylm.dpd[m][k]; }
 
-// This file is compiled without multiply-add contraction (-fmad=false):
-// every fused multiply-add below is written out (fma_r), so the rounding of
-// every expression is the one the source states, identical in every kernel
-// that inlines it (single-system and batched launches, staged and unstaged
-// tiles give the same bits).
-template <typename real>
-__device__ __forceinline__ real fma_r(real a, real b, real c);
-template <>
-__device__ __forceinline__ float fma_r<float>(float a, float b, float c) { return fmaf(a, b, c); }
-template <>
-__device__ __forceinline__ double fma_r<double>(double a, double b, double c) { return fma(a, b, c); }
-
-// P_m(z): degree 6 - m with the parity of 6 - m (Horner in z^2).
+// P_m(z): degree 6 - m with the parity of 6 - m.
 template <typename real>
 __device__ __forceinline__ void legendre_parts(real z, real P[7])
 {
 #define C_(m, k) ylm_c<real>(m, k)
-    const real z2 = z * z;
-    P[0] = fma_r(fma_r(fma_r(C_(0, 0), z2, C_(0, 1)), z2, C_(0, 2)), z2, C_(0, 3));
-    P[1] = z * fma_r(fma_r(C_(1, 0), z2, C_(1, 1)), z2, C_(1, 2));
-    P[2] = fma_r(fma_r(C_(2, 0), z2, C_(2, 1)), z2, C_(2, 2));
-    P[3] = z * fma_r(C_(3, 0), z2, C_(3, 1));
-    P[4] = fma_r(C_(4, 0), z2, C_(4, 1));
+    real z2 = z * z;
+    P[0] = ((C_(0, 0) * z2 + C_(0, 1)) * z2 + C_(0, 2)) * z2 + C_(0, 3);
+    P[1] = z * ((C_(1, 0) * z2 + C_(1, 1)) * z2 + C_(1, 2));
+    P[2] = (C_(2, 0) * z2 + C_(2, 1)) * z2 + C_(2, 2);
+    P[3] = z * (C_(3, 0) * z2 + C_(3, 1));
+    P[4] = C_(4, 0) * z2 + C_(4, 1);
     P[5] = z * C_(5, 0);
     P[6] = C_(6, 0);
 #undef C_
@@ -95,29 +76,26 @@ template <typename real>
 __device__ __forceinline__ void legendre_dparts(real z, real D[7])
 {
 #define C_(m, k) ylm_dc<real>(m, k)
-    const real z2 = z * z;
-    D[0] = z * fma_r(fma_r(C_(0, 0), z2, C_(0, 1)), z2, C_(0, 2));
-    D[1] = fma_r(fma_r(C_(1, 0), z2, C_(1, 1)), z2, C_(1, 2));
-    D[2] = z * fma_r(C_(2, 0), z2, C_(2, 1));
-    D[3] = fma_r(C_(3, 0), z2, C_(3, 1));
+    real z2 = z * z;
+    D[0] = z * ((C_(0, 0) * z2 + C_(0, 1)) * z2 + C_(0, 2));
+    D[1] = (C_(1, 0) * z2 + C_(1, 1)) * z2 + C_(1, 2);
+    D[2] = z * (C_(2, 0) * z2 + C_(2, 1));
+    D[3] = C_(3, 0) * z2 + C_(3, 1);
     D[4] = z * C_(4, 0);
     D[5] = C_(5, 0);
     D[6] = real(0);
 #undef C_
 }
 
-// C_m + i S_m = (x + i y)^m.
 template <typename real>
 __device__ __forceinline__ void cs_powers(real x, real y, real C[7], real S[7])
 {
     C[0] = real(1);
     S[0] = real(0);
-    C[1] = x;
-    S[1] = y;
 #pragma unroll
-    for (int m = 2; m <= 6; ++m) {
-        C[m] = fma_r(x, C[m - 1], -(y * S[m - 1]));
-        S[m] = fma_r(x, S[m - 1], y * C[m - 1]);
+    for (int m = 1; m <= 6; ++m) {
+        C[m] = x * C[m - 1] - y * S[m - 1];
+        S[m] = x * S[m - 1] + y * C[m - 1];
     }
 }
 
@@ -148,18 +126,18 @@ __device__ __forceinline__ void ylm13_grad(real x, real y, real z, real inv_r, c
     real gx = real(0), gy = real(0), gz = c[0] * D[0];
 #pragma unroll
     for (int m = 1; m <= 6; ++m) {
-        const real cc = c[2 * m - 1], cs = c[2 * m];
+        real cc = c[2 * m - 1], cs = c[2 * m];
         Y[2 * m - 1] = P[m] * C[m];
         Y[2 * m] = P[m] * S[m];
-        const real pm = P[m] * real(m);
-        gx = fma_r(pm, fma_r(cc, C[m - 1], cs * S[m - 1]), gx);
-        gy = fma_r(pm, fma_r(cs, C[m - 1], -(cc * S[m - 1])), gy);
-        gz = fma_r(D[m], fma_r(cc, C[m], cs * S[m]), gz);
+        real pm = P[m] * real(m);
+        gx += pm * (cc * C[m - 1] + cs * S[m - 1]);
+        gy += pm * (cs * C[m - 1] - cc * S[m - 1]);
+        gz += D[m] * (cc * C[m] + cs * S[m]);
     }
-    const real ug = fma_r(x, gx, fma_r(y, gy, z * gz));
-    g[0] = fma_r(-ug, x, gx) * inv_r;
-    g[1] = fma_r(-ug, y, gy) * inv_r;
-    g[2] = fma_r(-ug, z, gz) * inv_r;
+    real ug = x * gx + y * gy + z * gz;
+    g[0] = (gx - ug * x) * inv_r;
+    g[1] = (gy - ug * y) * inv_r;
+    g[2] = (gz - ug * z) * inv_r;
 }
 
 // sum_k K_k a_k^2 with K as a float pair (FP32) or exact (FP64).
@@ -203,171 +181,229 @@ __device__ __forceinline__ float kweight<float>(int m) { return c_ylm.kf_hi[m]; 
 template <>
 __device__ __forceinline__ double kweight<double>(int m) { return c_ylm.kd[m]; }
 
+// 16-wide per-atom records (13 used): one 64 B (FP32) or 128 B (FP64) row
+// per atom, so a neighbour's record is two sectors, not thirteen.
+constexpr int kRec = 16;
+
+template <typename real>
+__device__ __forceinline__ void load_rec(const real *base, int i, real v[kRec]);
+template <>
+__device__ __forceinline__ void load_rec<float>(const float *base, int i, float v[kRec])
+{
+    const float4 *p = reinterpret_cast<const float4 *>(base + (size_t)i * kRec);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float4 t = p[k];
+        v[4 * k] = t.x;
+        v[4 * k + 1] = t.y;
+        v[4 * k + 2] = t.z;
+        v[4 * k + 3] = t.w;
+    }
+}
+template <>
+__device__ __forceinline__ void load_rec<double>(const double *base, int i, double v[kRec])
+{
+    const double2 *p = reinterpret_cast<const double2 *>(base + (size_t)i * kRec);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        double2 t = p[k];
+        v[2 * k] = t.x;
+        v[2 * k + 1] = t.y;
+    }
+}
+template <typename real>
+__device__ __forceinline__ void store_rec(real *base, int i, const real v[kRec]);
+template <>
+__device__ __forceinline__ void store_rec<float>(float *base, int i, const float v[kRec])
+{
+    float4 *p = reinterpret_cast<float4 *>(base + (size_t)i * kRec);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) p[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+}
+template <>
+__device__ __forceinline__ void store_rec<double>(double *base, int i, const double v[kRec])
+{
+    double2 *p = reinterpret_cast<double2 *>(base + (size_t)i * kRec);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) p[k] = make_double2(v[2 * k], v[2 * k + 1]);
+}
+
 namespace {
 
 template <typename real>
 __device__ __forceinline__ real *R(void *p) { return reinterpret_cast<real *>(p); }
 
-// Four consecutive reals (16-byte aligned), and a store of four.
-template <typename real>
-__device__ __forceinline__ void ld4(const real *p, real x[4]);
-template <>
-__device__ __forceinline__ void ld4<float>(const float *p, float x[4])
+// Fixed-order FP64 block sum (result valid in thread 0).
+__device__ __forceinline__ double block_sum(double v, double *sh)
 {
-    const float4 t = *reinterpret_cast<const float4 *>(p);
-    x[0] = t.x;
-    x[1] = t.y;
-    x[2] = t.z;
-    x[3] = t.w;
-}
-template <>
-__device__ __forceinline__ void ld4<double>(const double *p, double x[4])
-{
-    const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
-    x[0] = a.x;
-    x[1] = a.y;
-    x[2] = b.x;
-    x[3] = b.y;
-}
-template <typename real>
-__device__ __forceinline__ void st4(real *p, real a, real b, real c, real d);
-template <>
-__device__ __forceinline__ void st4<float>(float *p, float a, float b, float c, float d)
-{
-    *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
-}
-template <>
-__device__ __forceinline__ void st4<double>(double *p, double a, double b, double c, double d)
-{
-    reinterpret_cast<double2 *>(p)[0] = make_double2(a, b);
-    reinterpret_cast<double2 *>(p)[1] = make_double2(c, d);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    __syncthreads();
+    return t;
 }
 
-// Component c (0..3, not a compile-time constant) of a 4-array in registers,
-// by selection (no local-memory indexing).
-template <typename real>
-__device__ __forceinline__ real quad_pick(const real v[4], int c)
+// Displacement (cached by the exact filter), 1/r, switch weight and its
+// derivative of one exact entry, with its neighbour, CN mask and mirror
+// position.
+template <typename real, bool kLast = false>
+__device__ __forceinline__ void cached_geometry(const Sys &s, size_t slot, Vec3<real> &d, real &inv_r, real &w,
+                                                real &dw, bool &cn, int &j, unsigned &vm)
 {
-    return c == 0 ? v[0] : (c == 1 ? v[1] : (c == 2 ? v[2] : v[3]));
-}
-
-// Displacement r_j - r_i in the pair precision.  The float32 form takes a
-// warp vote: every lane of the warp must call it.
-template <typename real>
-__device__ __forceinline__ Vec3<real> pair_disp(const Sys &s, float4 pi, float4 pj);
-template <>
-__device__ __forceinline__ Vec3<float> pair_disp<float>(const Sys &s, float4 pi, float4 pj)
-{
-    return displacement_warp(s, pi, pj);
-}
-template <>
-__device__ __forceinline__ Vec3<double> pair_disp<double>(const Sys &s, float4 pi, float4 pj)
-{
-    return displacement<double>(s, pi, pj);
-}
-
-// 1/r, the switch weight and its derivative of one displacement.
-template <typename real>
-__device__ __forceinline__ void pair_switch(const Sys &s, const Vec3<real> &d, real &inv_r, real &w, real &dw)
-{
-    const real r2 = fma_r(d.x, d.x, fma_r(d.y, d.y, d.z * d.z));
+    load_geo<real, kLast>(s, slot, d, cn, j, vm);
+    real r2 = d.x * d.x + d.y * d.y + d.z * d.z;
     inv_r = rsqrt_r<real>(r2);
     switch_eval<real>(s, r2 * inv_r, w, dw);
 }
 
-// The same quantities with the hardware's approximate reciprocal square root
-// and reciprocal (relative error ~1e-7, not correctly rounded): for the force
-// pass, whose results are derivatives (the CV values, whose rounding must be
-// unbiased, use pair_switch).  FP64 keeps the exact form.
+// Butterfly reduce-scatter of 16 values over the kG lanes of a group:
+// afterwards lane l holds the group sums of values 2l and 2l + 1 in v[0], v[1].
 template <typename real>
-__device__ __forceinline__ void pair_switch_fast(const Sys &s, const Vec3<real> &d, real &inv_r, real &w, real &dw);
-template <>
-__device__ __forceinline__ void pair_switch_fast<double>(const Sys &s, const Vec3<double> &d, double &inv_r, double &w,
-                                                         double &dw)
+__device__ __forceinline__ void reduce_scatter16(real v[kRec], int l)
 {
-    pair_switch<double>(s, d, inv_r, w, dw);
-}
-template <>
-__device__ __forceinline__ void pair_switch_fast<float>(const Sys &s, const Vec3<float> &d, float &inv_r, float &w,
-                                                        float &dw)
-{
-    const float r2 = fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z));
-    inv_r = rsqrtf(r2);
-    const float x = (r2 * inv_r) * s.inv_r0_hi;
-    float f, dfdx;
-    if (s.sw_m == 2 * s.sw_n) {
-        const float xn1 = s.sw_n == 6 ? (x * x) * (x * x) * x : ipow<float>(x, s.sw_n - 1);
-        const float inv = __fdividef(1.0f, fmaf(xn1, x, 1.0f));
-        f = inv;
-        dfdx = -s.sw_nf * xn1 * inv * inv;
-    } else {
-        float Sn, dSn, Sm, dSm;
-        geom_sum<float>(x, s.sw_n, Sn, dSn);
-        geom_sum<float>(x, s.sw_m, Sm, dSm);
-        const float inv = __fdividef(1.0f, Sm);
-        f = Sn * inv;
-        dfdx = (dSn * Sm - Sn * dSm) * inv * inv;
-    }
-    w = fmaf(f, s.a_hi, -s.k_hi);
-    dw = dfdx * s.a_hi * s.inv_r0_hi;
-}
-
-// Where a pass reads the tile's atoms: shared memory, or, for a tile larger
-// than the staging capacity, global memory through the same local indices
-// (the same values, so the same bits).
-template <typename real, bool kStaged>
-struct Src {
-    const TileTable &T;
-    const float4 *spos;  // staged positions
-    const real *srec;    // staged record components 0..11
-    const real *spair;   // staged record components 12..13
-    const float4 *gpos;  // sorted positions (global)
-    const real *grec;    // records [n][16] (global)
-
-    __device__ __forceinline__ float4 pos(int a) const { return kStaged ? spos[a] : gpos[tile_global(T, a)]; }
-    // record components 4l .. 4l + 3 (l < 3), or component 12 then zeros (l == 3)
-    __device__ __forceinline__ void quad(int a, int l, real x[4]) const
-    {
-        if (kStaged) {
-            if (l < 3) {
-                ld4<real>(srec + (size_t)a * kRecQ + 4 * l, x);
-            } else {
-                x[0] = spair[2 * (size_t)a];
-                x[1] = x[2] = x[3] = real(0);
-            }
-        } else {
-            const real *r = grec + (size_t)tile_global(T, a) * 16;
-            if (l < 3) {
-                ld4<real>(r + 4 * l, x);
-            } else {
-                x[0] = r[12];
-                x[1] = x[2] = x[3] = real(0);
+    int len = kRec;
+#pragma unroll
+    for (int o = kG / 2; o >= 1; o >>= 1) {
+        len >>= 1;
+        const bool upper = (l & o) != 0;
+#pragma unroll
+        for (int t = 0; t < kRec / 2; ++t) {
+            if (t < len) {
+                real a = v[t], b = v[t + len];
+                real send = upper ? a : b;
+                real keep = upper ? b : a;
+                v[t] = keep + __shfl_xor_sync(0xffffffffu, send, o);
             }
         }
     }
-    // record component 13
-    __device__ __forceinline__ real c13(int a) const
-    {
-        return kStaged ? spair[2 * (size_t)a + 1] : grec[(size_t)tile_global(T, a) * 16 + 13];
-    }
-    // record components 0..13
-    __device__ __forceinline__ void all(int a, real x[14]) const
-    {
-        const real *r = kStaged ? srec + (size_t)a * kRecQ : grec + (size_t)tile_global(T, a) * 16;
-        ld4<real>(r, x);
-        ld4<real>(r + 4, x + 4);
-        ld4<real>(r + 8, x + 8);
-        if (kStaged) {
-            x[12] = spair[2 * (size_t)a];
-            x[13] = spair[2 * (size_t)a + 1];
-        } else {
-            x[12] = r[12];
-            x[13] = r[13];
+}
+
+// Sum over the kG lanes of a group, result in every lane.
+template <typename real>
+__device__ __forceinline__ real group_sum(real v)
+{
+#pragma unroll
+    for (int o = kG / 2; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename real>
+__device__ __forceinline__ real group_get(real v, int src_lane)
+{
+    const int base = (threadIdx.x & 31) & ~(kG - 1);
+    return __shfl_sync(0xffffffffu, v, base + src_lane);
+}
+
+template <typename real>
+__device__ __forceinline__ void store_pair(real *base, int i, int l, real a, real b);
+template <>
+__device__ __forceinline__ void store_pair<float>(float *base, int i, int l, float a, float b)
+{
+    reinterpret_cast<float2 *>(base + (size_t)i * kRec)[l] = make_float2(a, b);
+}
+template <>
+__device__ __forceinline__ void store_pair<double>(double *base, int i, int l, double a, double b)
+{
+    reinterpret_cast<double2 *>(base + (size_t)i * kRec)[l] = make_double2(a, b);
+}
+
+// Components (2l, 2l + 1) of record i: the kG lanes of a group together read
+// the whole 64 B (FP32) row with one coalesced access.
+template <typename real>
+__device__ __forceinline__ void load_pair(const real *base, int i, int l, real &a, real &b);
+template <>
+__device__ __forceinline__ void load_pair<float>(const float *base, int i, int l, float &a, float &b)
+{
+    const float2 t = reinterpret_cast<const float2 *>(base + (size_t)i * kRec)[l];
+    a = t.x;
+    b = t.y;
+}
+template <>
+__device__ __forceinline__ void load_pair<double>(const double *base, int i, int l, double &a, double &b)
+{
+    const double2 t = reinterpret_cast<const double2 *>(base + (size_t)i * kRec)[l];
+    a = t.x;
+    b = t.y;
+}
+
+__device__ __forceinline__ const int *nbr_row(const Sys &s, int i) { return s.nbr + (size_t)i * s.max_nb; }
+
+// a4: CN_i, W_i and q_m(i) = sum_j w_ij Y_m(rhat_ij) / W_i.
+// With kFilter the exact row is first compacted from the Verlet row.
+template <typename real, bool kFilter>
+__device__ __forceinline__ double cv_fwd_group(const Sys &s, const AtomLane a)
+{
+    int nn_f = 0;
+    if (kFilter) nn_f = filter_row<real>(s, a);
+    real v[kRec];  // 0..12: sum w Y_m ; 13: W ; 14: CN
+#pragma unroll
+    for (int m = 0; m < kRec; ++m) v[m] = real(0);
+    if (a.ok) {
+        const int nn = kFilter ? nn_f : s.nn[a.i];
+        JW<real> *jwrow = reinterpret_cast<JW<real> *>(s.wl) + (size_t)a.i * s.max_nb;
+        for (int k = a.l; k < nn; k += kG) {
+            Vec3<real> d;
+            real inv_r, w, dw;
+            bool cn;
+            int j;
+            unsigned vm;
+            cached_geometry<real>(s, (size_t)a.i * s.max_nb + k, d, inv_r, w, dw, cn, j, vm);
+            jwrow[k] = JW<real>{j, w};
+            if (cn) v[14] += w;
+            v[13] += w;
+            if (s.ncv == 2) {
+                real Y[kNY];
+                ylm13<real>(d.x * inv_r, d.y * inv_r, d.z * inv_r, Y);
+#pragma unroll
+                for (int m = 0; m < kNY; ++m) v[m] += w * Y[m];
+            }
         }
     }
-};
+    reduce_scatter16<real>(v, a.l);
+    // lane 6 holds (13: W, ...) in v[1]; lane 7 holds (14: CN, 15) in v[0]
+    const real W = group_get<real>(v[1], 6);
+    double cn_out = 0.0;
+    if (a.ok) {
+        if (a.l == 7) {
+            R<real>(s.cn)[a.i] = v[0];
+            cn_out = (double)v[0];
+        }
+        if (a.l == 6) R<real>(s.W)[a.i] = W;
+        if (s.ncv == 2) {
+            const real inv_W = W > real(0) ? real(1) / W : real(0);
+            real q0 = v[0] * inv_W, q1 = v[1] * inv_W;
+            if (a.l == 6) q1 = real(0);
+            if (a.l == 7) q0 = q1 = real(0);
+            store_pair<real>(R<real>(s.q), a.i, a.l, q0, q1);
+        }
+    }
+    return cn_out;
+}
 
-// Per-thread running sum of a per-atom value.  With FP32 records it is a
+template <typename real, bool kFilter>
+__device__ __forceinline__ void cv_fwd(const Sys &s, Blk k)
+{
+    const int groups = group_grid(s.n);
+    for (int it = 0, g; (g = work_item(k, it)) < groups; ++it) cv_fwd_group<real, kFilter>(s, atom_lane_at(s, g));
+}
+
+template <typename real, bool kFilter>
+__global__ void __launch_bounds__(kBlockAtoms, 12) k_cv_fwd(Sys s) { cv_fwd<real, kFilter>(s, own_blk()); }
+
+template <typename real>
+__global__ void __launch_bounds__(kBlockAtoms, 12) kb_cv_fwd(BatchView v)
+{
+    Blk k;
+    const Sys &s = v.sys[batch_system(v, k)];
+    cv_fwd<real, true>(s, k);
+}
+
+// Per-thread running sum of a per-atom CV.  With FP32 records it is a
 // compensated pair (Knuth's TwoSum: s + c holds the sum with only c's own
 // rounding), so no FP64 instruction runs per atom (their pipe is narrow on
 // this part); it enters the FP64 block and grid sums once per thread.
@@ -392,19 +428,76 @@ struct RunSum<double> {
     __device__ __forceinline__ double value() const { return s; }
 };
 
-// Fixed-order FP64 block sum (result valid in thread 0).
-__device__ __forceinline__ double block_sum(double v, double *sh)
+// Warp tree over RunSum values (lane 0 ends with the warp's sum): FP32
+// pairs combine by TwoSum on s and a plain sum of the c terms.
+__device__ __forceinline__ void warp_sum(RunSum<float> &v)
 {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-    __syncthreads();
-    return t;
+    for (int o = 16; o > 0; o >>= 1) {
+        const float os = __shfl_down_sync(0xffffffffu, v.s, o);
+        const float oc = __shfl_down_sync(0xffffffffu, v.c, o);
+        const float t = v.s + os;
+        const float bp = t - v.s;
+        v.c += oc + ((v.s - (t - bp)) + (os - bp));
+        v.s = t;
+    }
+}
+__device__ __forceinline__ void warp_sum(RunSum<double> &v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v.s += __shfl_down_sync(0xffffffffu, v.s, o);
+}
+
+// a5: qbar_m(i), qbar6(i), s2.  Record b: b_m(i) = K_m qbar_m(i) / (N qbar6
+// (1 + W_i)) (slots 0..12) and beta_i = b(i).qbar(i) (slot 13).
+template <typename real>
+__device__ __forceinline__ void cv_avg_group(const Sys &s, const AtomLane a, RunSum<real> &cn_sum,
+                                             RunSum<real> &q6_sum)
+{
+    // lane l owns components 2l, 2l + 1 and walks every neighbour of the atom
+    const real *q = R<real>(s.q);
+    real a0 = real(0), a1 = real(0);
+    if (a.ok) {
+        const int nn = s.nn[a.i];
+        const JW<real> *jwrow = reinterpret_cast<const JW<real> *>(s.wl) + (size_t)a.i * s.max_nb;
+#pragma unroll 4
+        for (int k = 0; k < nn; ++k) {
+            const JW<real> e = jwrow[k];
+            const int j = e.j;
+            const real w = e.w;
+            real x0, x1;
+            load_pair<real>(q, j, a.l, x0, x1);
+            a0 += w * x0;
+            a1 += w * x1;
+        }
+    }
+    real qb0 = real(0), qb1 = real(0), sq = real(0), inv_D = real(0);
+    if (a.ok) {
+        inv_D = real(1) / (real(1) + R<real>(s.W)[a.i]);
+        real o0, o1;
+        load_pair<real>(q, a.i, a.l, o0, o1);
+        const int m0 = 2 * a.l, m1 = 2 * a.l + 1;
+        if (m0 < kNY) qb0 = (o0 + a0) * inv_D;
+        if (m1 < kNY) qb1 = (o1 + a1) * inv_D;
+        if (m0 < kNY) sq += weighted_term<real>(m0, qb0);
+        if (m1 < kNY) sq += weighted_term<real>(m1, qb1);
+    }
+    sq = group_sum<real>(sq);
+    const real qb6 = sqrt(sq);
+    const real ci = qb6 > real(0) ? inv_D / (n_real<real>(s) * qb6) : real(0);
+    const int m0 = 2 * a.l, m1 = 2 * a.l + 1;
+    real b0 = m0 < kNY ? ci * kweight<real>(m0) * qb0 : real(0);
+    real b1 = m1 < kNY ? ci * kweight<real>(m1) * qb1 : real(0);
+    const real beta = group_sum<real>(b0 * qb0 + b1 * qb1);
+    if (a.ok) {
+        if (a.l == 6) b1 = beta;  // slot 13
+        store_pair<real>(R<real>(s.b), a.i, a.l, b0, b1);
+        if (a.l == 0) {
+            R<real>(s.qb6)[a.i] = qb6;
+            cn_sum.add(R<real>(s.cn)[a.i]);
+            q6_sum.add(qb6);
+        }
+    }
 }
 
 // Block sums c, q -> part[b], part[part_stride + b]; the last block to finish
@@ -447,6 +540,290 @@ __device__ void last_block_cv(const Sys &s, Blk k, double c, double q)
     }
 }
 
+// a5 with the CV sums: persistent (the block partials are few).
+// The filter of the last kernel saw the rows' mirror positions stored.
+__device__ __forceinline__ void rows_used(const Sys &s, Blk k)
+{
+    if (k.b == 0 && threadIdx.x == 0 && s.mirror) *s.rows_fresh = 0;
+}
+
+template <typename real>
+__device__ __forceinline__ void cv_avg(const Sys &s, Blk k)
+{
+    rows_used(s, k);
+    RunSum<real> c, q;
+    const int groups = group_grid(s.n);
+    for (int it = 0, g; (g = work_item(k, it)) < groups; ++it) cv_avg_group<real>(s, atom_lane_at(s, g), c, q);
+    last_block_cv(s, k, c.value(), q.value());
+}
+
+// The CV sum when there is no Q6 pass (n_cv == 1): thread t of block b sums
+// the CN of atoms b kSumThreads + t, + blocks kSumThreads, ... in order
+// (a compensated FP32 pair with FP32 records).
+template <typename real>
+__device__ __forceinline__ void cv_sum(const Sys &s, Blk k)
+{
+    rows_used(s, k);
+    RunSum<real> c;
+    const real *cn = R<real>(s.cn);
+    for (int i = k.b * blockDim.x + threadIdx.x; i < s.n; i += k.nb * blockDim.x) c.add(cn[i]);
+    last_block_cv(s, k, c.value(), 0.0);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kSumThreads) k_cv_sum(Sys s) { cv_sum<real>(s, own_blk()); }
+
+template <typename real>
+__global__ void __launch_bounds__(kSumThreads) kb_cv_sum(BatchView v)
+{
+    Blk k;
+    const Sys &s = v.sys[batch_system(v, k)];
+    cv_sum<real>(s, k);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kBlockAtoms) k_cv_avg(Sys s) { cv_avg<real>(s, own_blk()); }
+
+template <typename real>
+__global__ void __launch_bounds__(kBlockAtoms) kb_cv_avg(BatchView v)
+{
+    Blk k;
+    const Sys &s = v.sys[batch_system(v, k)];
+    cv_avg<real>(s, k);
+}
+
+// a7: g_m(k) = b_m(k) + sum_i w_ik b_m(i) ; h = g / W ; record h holds h_m
+// (0..12) and gamma_k = h(k).q(k) + beta_k (slot 13).
+// a7 with four lanes per atom, four record components per lane (one 16 B
+// load of each neighbour record per lane): a warp has eight atoms' gathers in
+// flight.  (Measured faster than eight lanes of two components here; the Q6
+// average keeps eight lanes, where four cost it occupancy.)
+constexpr int kG4 = 4;
+constexpr int kAtoms4 = kBlockAtoms / kG4;
+
+template <typename real>
+__device__ __forceinline__ void load4(const real *base, int i, int l, real v[4]);
+template <>
+__device__ __forceinline__ void load4<float>(const float *base, int i, int l, float v[4])
+{
+    const float4 t = reinterpret_cast<const float4 *>(base + (size_t)i * kRec)[l];
+    v[0] = t.x;
+    v[1] = t.y;
+    v[2] = t.z;
+    v[3] = t.w;
+}
+template <>
+__device__ __forceinline__ void load4<double>(const double *base, int i, int l, double v[4])
+{
+    const double2 *p = reinterpret_cast<const double2 *>(base + (size_t)i * kRec) + 2 * l;
+    const double2 a = p[0], b = p[1];
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = b.x;
+    v[3] = b.y;
+}
+template <typename real>
+__device__ __forceinline__ void store4(real *base, int i, int l, const real v[4]);
+template <>
+__device__ __forceinline__ void store4<float>(float *base, int i, int l, const float v[4])
+{
+    reinterpret_cast<float4 *>(base + (size_t)i * kRec)[l] = make_float4(v[0], v[1], v[2], v[3]);
+}
+template <>
+__device__ __forceinline__ void store4<double>(double *base, int i, int l, const double v[4])
+{
+    double2 *p = reinterpret_cast<double2 *>(base + (size_t)i * kRec) + 2 * l;
+    p[0] = make_double2(v[0], v[1]);
+    p[1] = make_double2(v[2], v[3]);
+}
+
+template <typename real>
+__device__ __forceinline__ real group4_sum(real v)
+{
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    return v;
+}
+
+template <typename real>
+__device__ __forceinline__ void adjoint_group(const Sys &s, int g)
+{
+    // lane l owns components 4l .. 4l + 3; record b holds b_m (0..12), beta (13)
+    const int i = g * kAtoms4 + (threadIdx.x / kG4), l = threadIdx.x & (kG4 - 1);
+    const bool ok = i < s.n;
+    const real *bb = R<real>(s.b);
+    real acc[4] = {real(0), real(0), real(0), real(0)};
+    if (ok) {
+        const int nn = s.nn[i];
+        const JW<real> *jwrow = reinterpret_cast<const JW<real> *>(s.wl) + (size_t)i * s.max_nb;
+#pragma unroll 4
+        for (int k = 0; k < nn; ++k) {
+            const JW<real> e = jwrow[k];
+            const int j = e.j;
+            const real w = e.w;
+            real x[4];
+            load4<real>(bb, j, l, x);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[c] += w * x[c];
+        }
+    }
+    real h[4] = {real(0), real(0), real(0), real(0)};
+    real alpha = real(0), beta = real(0);
+    if (ok) {
+        const real W = R<real>(s.W)[i];
+        const real inv_W = W > real(0) ? real(1) / W : real(0);
+        real o[4], q[4];
+        load4<real>(bb, i, l, o);
+        load4<real>(R<real>(s.q), i, l, q);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int m = 4 * l + c;
+            if (m < kNY) {
+                h[c] = (o[c] + acc[c]) * inv_W;
+                alpha += h[c] * q[c];
+            }
+            if (m == 13) beta = o[c];
+        }
+    }
+    alpha = group4_sum<real>(alpha);
+    beta = group4_sum<real>(beta);
+    if (ok) {
+        if (l == 3) h[1] = alpha + beta;  // slot 13: gamma = h.q + b.qbar
+        store4<real>(R<real>(s.h), i, l, h);
+    }
+}
+
+template <typename real>
+__device__ __forceinline__ void adjoint(const Sys &s, Blk k)
+{
+    const int groups = (s.n + kAtoms4 - 1) / kAtoms4;
+    for (int it = 0, g; (g = work_item(k, it)) < groups; ++it) adjoint_group<real>(s, g);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kBlockAtoms) k_adjoint(Sys s) { adjoint<real>(s, own_blk()); }
+
+template <typename real>
+__global__ void __launch_bounds__(kBlockAtoms) kb_adjoint(BatchView v)
+{
+    Blk k;
+    const Sys &s = v.sys[batch_system(v, k)];
+    adjoint<real>(s, k);
+}
+
+// a8, pass 1: for every unordered pair, from the row of its lower index i
+// (entries k < nh_i, j > i), G_ij = V1 ds1/dd + V2 ds2/dd at d = r_j - r_i,
+// stored in the pair's slot.  Each pair is evaluated once.
+//   ds2/dw = (h_i + h_j).Y - gamma_i - gamma_j + b_i.q_j + b_j.q_i
+//   ds2/dd = ds2/dw w' d/r + w sum_m (h_i + h_j)_m dY_m/dd
+//   ds1/dd = (2/N) w' d/r [unlike]
+// The pair slots are a stream (written once, read once by pass 2): stored
+// and loaded evict-first, so they leave the gathered records in L2.
+template <typename real>
+__device__ __forceinline__ void store_pair_force(real *slot, real fx, real fy, real fz);
+template <>
+__device__ __forceinline__ void store_pair_force<float>(float *slot, float fx, float fy, float fz)
+{
+    __stcs(reinterpret_cast<float4 *>(slot), make_float4(fx, fy, fz, 0.0f));
+}
+template <>
+__device__ __forceinline__ void store_pair_force<double>(double *slot, double fx, double fy, double fz)
+{
+    __stcs(reinterpret_cast<double2 *>(slot), make_double2(fx, fy));
+    __stcs(reinterpret_cast<double2 *>(slot) + 1, make_double2(fz, 0.0));
+}
+
+// Pair-parallel: the half-row entries (k < nh_i) of a chunk of kPairChunk
+// atoms are numbered in atom order and thread t of the block evaluates
+// entries t, t + blockDim, ...: every lane has a pair while the chunk lasts,
+// whatever the spread of the atoms' half-row lengths.
+//
+// G_ij goes to the slot of entry k in i's row and -G_ij to the slot of i in
+// the j < i part of j's row (rows are symmetric: the neighbour predicate is),
+// so pass 2 sums each atom's own slots in row order.
+constexpr int kPairChunk = 32;
+
+template <typename real, bool kVir>
+__device__ __forceinline__ void pair_force(const Sys &s, int i, int k, real cn_fac, real V2, RunSum<real> &vx,
+                                           RunSum<real> &vy, RunSum<real> &vz)
+{
+    Vec3<real> d;
+    real inv_r, w, dw;
+    bool cn;
+    int j;
+    unsigned vm;
+    cached_geometry<real, true>(s, (size_t)i * s.max_nb + k, d, inv_r, w, dw, cn, j, vm);
+    // the slot of i in j's exact row: with mirror slots, the exact entries
+    // of j's Verlet row before i's position vm there (one 2 B load);
+    // otherwise a search of the j < i part of j's row
+    int kk = -1, nhj = 0, nnj = 0;
+    if (s.mirror) {
+        const unsigned e = s.vround[(size_t)j * s.vround_stride + (vm >> 3)];
+        kk = (int)(e & 0xffu) + __popc((e >> 8) & ((1u << (vm & 7u)) - 1u));
+    } else {
+        nhj = s.nh[j];
+        nnj = s.nn[j];
+    }
+    const real ux = d.x * inv_r, uy = d.y * inv_r, uz = d.z * inv_r;
+    real radial = cn ? cn_fac * dw : real(0);
+    real fx = real(0), fy = real(0), fz = real(0);
+    if (s.ncv == 2) {
+        const real *hh = R<real>(s.h), *qq = R<real>(s.q), *qbb = R<real>(s.b);
+        // cross term b_i.q_j + b_j.q_i first, so the q and b records die early
+        real qi[kRec], qj[kRec], bi[kRec], bj[kRec];
+        load_rec<real>(qq, i, qi);
+        load_rec<real>(qq, j, qj);
+        load_rec<real>(qbb, i, bi);
+        load_rec<real>(qbb, j, bj);
+        real t = real(0);
+#pragma unroll
+        for (int m = 0; m < kNY; ++m) t += bi[m] * qj[m] + bj[m] * qi[m];
+        real hi[kRec], hj[kRec];
+        load_rec<real>(hh, i, hi);
+        load_rec<real>(hh, j, hj);
+        t -= hi[13] + hj[13];
+        real hs[kNY], cvec[kNY];
+#pragma unroll
+        for (int m = 0; m < kNY; ++m) {
+            hs[m] = hi[m] + hj[m];
+            cvec[m] = w * hs[m];
+        }
+        real Y[kNY], gY[3];
+        ylm13_grad<real>(ux, uy, uz, inv_r, cvec, Y, gY);
+#pragma unroll
+        for (int m = 0; m < kNY; ++m) t += hs[m] * Y[m];
+        radial += V2 * t * dw;
+        fx = V2 * gY[0];
+        fy = V2 * gY[1];
+        fz = V2 * gY[2];
+    }
+    fx += radial * ux;
+    fy += radial * uy;
+    fz += radial * uz;
+    if (kVir) {  // (dV/dd)_a d_a of this pair
+        vx.add(fx * d.x);
+        vy.add(fy * d.y);
+        vz.add(fz * d.z);
+    }
+    real *pf = R<real>(s.pairF);
+    store_pair_force<real>(pf + ((size_t)i * s.max_nb + k) * 4, fx, fy, fz);
+    // without mirror slots: position of i in the j < i part [nh_j, nn_j) of
+    // j's row, four entries per load
+    const int *rj = nbr_row(s, j);
+    for (int b = nhj & ~3; b < nnj && kk < 0; b += 4) {
+        const int4 v = *reinterpret_cast<const int4 *>(rj + b);
+        if (v.x == i && b >= nhj) kk = b;
+        else if (v.y == i && b + 1 >= nhj && b + 1 < nnj) kk = b + 1;
+        else if (v.z == i && b + 2 >= nhj && b + 2 < nnj) kk = b + 2;
+        else if (v.w == i && b + 3 >= nhj && b + 3 < nnj) kk = b + 3;
+    }
+    if (kk < 0 || kk >= s.max_nb) {
+        set_err(s, kErrInternal);  // rows not symmetric: never expected
+        return;
+    }
+    store_pair_force<real>(pf + ((size_t)j * s.max_nb + kk) * 4, -fx, -fy, -fz);
+}
+
 // The bias virial W_a = sum_pairs (dV/dd)_a d_a, which a barostat needs: it
 // gives dV/dL_a at fixed fractional coordinates as W_a / L_a, plus dV/ds of
 // a lattice CV.  Per-thread compensated sums, a warp tree, FP64 block
@@ -455,7 +832,7 @@ __device__ void last_block_cv(const Sys &s, Blk k, double c, double q)
 template <typename real>
 __device__ void virial_finish(const Sys &s, Blk k, RunSum<real> &vx, RunSum<real> &vy, RunSum<real> &vz)
 {
-    constexpr int kW = kTileThreads / 32;
+    constexpr int kW = kBlockAtoms / 32;
     __shared__ double sh[3][kW];
     __shared__ bool am_last;
     if (3 * k.nb > s.part_stride) {  // never with the grids used; refuse rather than overrun
@@ -463,13 +840,14 @@ __device__ void virial_finish(const Sys &s, Blk k, RunSum<real> &vx, RunSum<real
         return;
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    double v3[3] = {vx.value(), vy.value(), vz.value()};
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v3[a] += __shfl_down_sync(0xffffffffu, v3[a], o);
-    if (lane == 0)
-        for (int a = 0; a < 3; ++a) sh[a][wid] = v3[a];
+    warp_sum(vx);
+    warp_sum(vy);
+    warp_sum(vz);
+    if (lane == 0) {
+        sh[0][wid] = vx.value();
+        sh[1][wid] = vy.value();
+        sh[2][wid] = vz.value();
+    }
     __syncthreads();
     double *part = s.part + s.part_stride;
     if (threadIdx.x == 0) {
@@ -518,577 +896,138 @@ __device__ void virial_finish(const Sys &s, Blk k, RunSum<real> &vx, RunSum<real
     }
 }
 
-template <typename real>
-__device__ __forceinline__ real group4_sum(real v)
+template <typename real, bool kVir>
+__device__ __forceinline__ void force_pairs(const Sys &s, Blk k)
 {
-    v += __shfl_xor_sync(0xffffffffu, v, 2);
-    v += __shfl_xor_sync(0xffffffffu, v, 1);
-    return v;
-}
-
-constexpr int kGroups4 = kTileThreads / 4;  // atoms a block's 4-lane groups take at once
-
-// Per-entry scalars in quad-major order, like the rows: entries 4q .. 4q + 3
-// of atom i are four reals at [q][i].
-template <typename real>
-__device__ __forceinline__ real *quad_real(void *base, size_t n, int q, int i)
-{
-    return reinterpret_cast<real *>(base) + (((size_t)q * n + i) << 2);
-}
-
-
-// ------------------------------------------------------------------ a3-a4
-// The exact rows of the tile's atoms from their Verlet rows (r^2 < rc^2,
-// decided as the FP64 definition), kept in shared memory (slist, a column
-// per thread) and stored as the step's neighbour rows; then (kCompute) CN_i,
-// W_i, q_m(i) and FC_i.  One thread per atom; the rows are read four
-// entries (one 8-byte quad) at a time, the next quad loaded before the
-// current one is used.
-template <typename real, bool kStaged, bool kCompute, bool kVir>
-__device__ __forceinline__ void fwd_tile(const Sys &s, const TileTable &T, const Src<real, kStaged> &src,
-                                         unsigned short *slist, RunSum<real> &cn_sum)
-{
-    const size_t N = (size_t)s.n;
-    const int lane = threadIdx.x & 31;
-    const ushort4 none = make_ushort4(0, 0, 0, 0);
-    for (int a0 = threadIdx.x & ~31; a0 < T.n_own; a0 += kTileThreads) {
-        const int a = a0 + lane;
-        const bool ok = a < T.n_own;
-        const int i = T.atom0 + (ok ? a : 0);
-        const float4 pi = ok ? src.pos(a) : make_float4(0.f, 0.f, 0.f, 0.f);
-        const int vn = ok ? s.vnn[i] : 0;
-        const int qmax = __reduce_max_sync(0xffffffffu, (vn + 3) >> 2);
-        int cnt = 0;
-        ushort4 nxt = vn > 0 ? quad_at(s.vlist, N, 0, i) : none;
-        for (int q = 0; q < qmax; ++q) {
-            const ushort4 cur = nxt;
-            if (q + 1 < qmax) nxt = 4 * (q + 1) < vn ? quad_at(s.vlist, N, q + 1, i) : none;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                int jl = quad_get(cur, c);
-                const bool valid = 4 * q + c < vn && jl < T.total;  // rows hold staged atoms only
-                jl = valid ? jl : 0;
-                const float4 pj = valid ? src.pos(jl) : pi;
-                const Vec3<float> d = displacement_warp(s, pi, pj);  // every lane: a warp vote inside
-                if (valid && pair_in(s, pi, pj, d)) {
-                    if (cnt < s.max_nb) slist[cnt * kTileThreads + threadIdx.x] = (unsigned short)jl;
-                    ++cnt;
-                }
-            }
-        }
-        const int nn = min(cnt, s.max_nb);
-        if (ok) {
-            if (cnt > s.max_nb) set_err(s, kErrCapacity);
-            s.nn[i] = nn;
-            // the exact row, quad by quad (threads of a warp own consecutive
-            // atoms: each quad row is one contiguous store per warp)
-            for (int q = 0; 4 * q < nn; ++q) {
-                const unsigned short *col = slist + 4 * q * kTileThreads + threadIdx.x;
-                const int m = nn - 4 * q;  // entries of this quad in the row (the rest are 0)
-                quad_ref(s.elist, N, q, i) =
-                    make_ushort4(col[0], m > 1 ? col[kTileThreads] : 0, m > 2 ? col[2 * kTileThreads] : 0,
-                                 m > 3 ? col[3 * kTileThreads] : 0);
-            }
-        }
-        if (!kCompute) continue;
-        const int nmax = __reduce_max_sync(0xffffffffu, nn);
-        real Q[kNY];
-#pragma unroll
-        for (int m = 0; m < kNY; ++m) Q[m] = real(0);
-        real W = real(0), CN = real(0);
-        real f3[3] = {real(0), real(0), real(0)}, w3[3] = {real(0), real(0), real(0)};
-        for (int k0 = 0; k0 < nmax; k0 += 4) {
-            // a quad of entries, unrolled and predicated (an entry past the
-            // row is evaluated at a dummy displacement and not added)
-            real wq[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int k = k0 + c;
-                const bool valid = k < nn;
-                const int jl = valid ? (int)slist[k * kTileThreads + threadIdx.x] : 0;
-                const float4 pj = valid ? src.pos(jl) : pi;
-                Vec3<real> d = pair_disp<real>(s, pi, pj);
-                if (!valid) {
-                    d.x = real(s.r0);
-                    d.y = d.z = real(0);
-                }
-                real inv_r, w, dw;
-                pair_switch<real>(s, d, inv_r, w, dw);
-                w = valid ? w : real(0);
-                wq[c] = w;
-                W += w;
-                const bool cn = valid && (!s.cn_unlike || pj.w != pi.w);
-                CN += cn ? w : real(0);
-                const real f = cn ? dw * inv_r : real(0);
-                f3[0] = fma_r(f, d.x, f3[0]);
-                f3[1] = fma_r(f, d.y, f3[1]);
-                f3[2] = fma_r(f, d.z, f3[2]);
-                if (kVir) {
-                    w3[0] = fma_r(f * d.x, d.x, w3[0]);
-                    w3[1] = fma_r(f * d.y, d.y, w3[1]);
-                    w3[2] = fma_r(f * d.z, d.z, w3[2]);
-                }
-                if (s.ncv == 2) {
-                    real Y[kNY];
-                    ylm13<real>(d.x * inv_r, d.y * inv_r, d.z * inv_r, Y);
-#pragma unroll
-                    for (int m = 0; m < kNY; ++m) Q[m] = fma_r(w, Y[m], Q[m]);
-                }
-            }
-            // the quad's weights, for the passes that need w_ij without the
-            // geometry (entries past the row are 0)
-            if (s.ncv == 2 && k0 < nn) st4<real>(quad_real<real>(s.wl, N, k0 >> 2, i), wq[0], wq[1], wq[2], wq[3]);
-        }
-        if (!ok) continue;
-        real *rq = R<real>(s.rq) + (size_t)i * 16;
-        real q12 = real(0);
-        if (s.ncv == 2) {
-            const real inv_W = W > real(0) ? real(1) / W : real(0);
-            st4<real>(rq, Q[0] * inv_W, Q[1] * inv_W, Q[2] * inv_W, Q[3] * inv_W);
-            st4<real>(rq + 4, Q[4] * inv_W, Q[5] * inv_W, Q[6] * inv_W, Q[7] * inv_W);
-            st4<real>(rq + 8, Q[8] * inv_W, Q[9] * inv_W, Q[10] * inv_W, Q[11] * inv_W);
-            q12 = Q[12] * inv_W;
-        }
-        st4<real>(rq + 12, q12, W, CN, real(0));
-        st4<real>(R<real>(s.fc) + 4 * (size_t)i, f3[0], f3[1], f3[2], real(0));
-        if (kVir) st4<real>(R<real>(s.wc) + 4 * (size_t)i, w3[0], w3[1], w3[2], real(0));
-        cn_sum.add(CN);
-    }
-}
-
-// Where the Q6 and adjoint passes read an own atom's row quads and weights:
-// the tile's staged copy, or global memory.
-template <typename real, bool kStaged>
-struct RowSrc {
-    const OwnRows<real> &o;
-    const unsigned short *elist;
-    void *wl;
-    size_t n;
-    int atom0;
-    __device__ __forceinline__ ushort4 jq(int a, int q) const
-    {
-        return kStaged ? o.jq[o.qoff[a] + q] : quad_at(elist, n, q, atom0 + a);
-    }
-    __device__ __forceinline__ void w(int a, int q, real x[4]) const
-    {
-        ld4<real>(kStaged ? o.wq + 4 * (o.qoff[a] + q) : quad_real<real>(wl, n, q, atom0 + a), x);
-    }
-};
-
-// ------------------------------------------------------------------ a5
-// qbar_m(i), qbar6(i), the CV sums, record b (b_m(i) in 0..12, beta_i =
-// b(i).qbar(i) in 13, qbar6 in 14), and per entry e_ij = b_i.q_j (the half
-// of the cross term b_i.q_j + b_j.q_i this pass can form).  One thread per
-// atom: each neighbour's 13 q components from shared memory, the entry's
-// weight w_ij from the forward pass (no geometry here), rows a quad at a
-// time.
-template <typename real, bool kStaged>
-__device__ __forceinline__ void avg_tile(const Sys &s, const TileTable &T, const Src<real, kStaged> &src,
-                                         const RowSrc<real, kStaged> &rows, RunSum<real> &cn_sum,
-                                         RunSum<real> &q6_sum)
-{
-    const size_t N = (size_t)s.n;
-    for (int a = threadIdx.x; a < T.n_own; a += kTileThreads) {
-        const int i = T.atom0 + a;
-        const int nn = s.nn[i];
-        real A[kNY];
-#pragma unroll
-        for (int m = 0; m < kNY; ++m) A[m] = real(0);
-        for (int q = 0; 4 * q < nn; ++q) {
-            const ushort4 jq = rows.jq(a, q);
-            real wq[4];
-            rows.w(a, q, wq);
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                if (4 * q + e < nn) {
-                    real x[14];
-                    src.all(quad_get(jq, e), x);
-#pragma unroll
-                    for (int m = 0; m < kNY; ++m) A[m] = fma_r(wq[e], x[m], A[m]);
-                }
-            }
-        }
-        real qo[16];
-        const real *rq = R<real>(s.rq) + (size_t)i * 16;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) ld4<real>(rq + 4 * u, qo + 4 * u);
-        const real W = qo[13], CN = qo[14];
-        const real inv_D = real(1) / (real(1) + W);
-        real qb[kNY], sq = real(0);
-#pragma unroll
-        for (int m = 0; m < kNY; ++m) {
-            qb[m] = (qo[m] + A[m]) * inv_D;
-            sq += weighted_term<real>(m, qb[m]);
-        }
-        const real qb6 = sqrt(sq);
-        const real ci = qb6 > real(0) ? inv_D / (n_real<real>(s) * qb6) : real(0);
-        real b[kNY], beta = real(0);
-#pragma unroll
-        for (int m = 0; m < kNY; ++m) {
-            b[m] = ci * kweight<real>(m) * qb[m];
-            beta = fma_r(b[m], qb[m], beta);
-        }
-        // e_ij = b_i.q_j for every entry, a quad at a time
-        for (int q = 0; 4 * q < nn; ++q) {
-            const ushort4 jq = rows.jq(a, q);
-            real eo[4] = {real(0), real(0), real(0), real(0)};
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                if (4 * q + e < nn) {
-                    real x[14];
-                    src.all(quad_get(jq, e), x);
-                    real p = b[0] * x[0];
-#pragma unroll
-                    for (int m = 1; m < kNY; ++m) p = fma_r(b[m], x[m], p);
-                    eo[e] = p;
-                }
-            }
-            st4<real>(quad_real<real>(s.eq, N, q, i), eo[0], eo[1], eo[2], eo[3]);
-        }
-        real *rb = R<real>(s.rb) + (size_t)i * 16;
-        st4<real>(rb, b[0], b[1], b[2], b[3]);
-        st4<real>(rb + 4, b[4], b[5], b[6], b[7]);
-        st4<real>(rb + 8, b[8], b[9], b[10], b[11]);
-        st4<real>(rb + 12, b[12], beta, qb6, real(0));
-        cn_sum.add(CN);
-        q6_sum.add(qb6);
-    }
-}
-
-// ------------------------------------------------------------------ a7
-// g_m(k) = b_m(k) + sum_i w_ik b_m(i), h = g / W, record h (h_m in 0..12,
-// gamma_k = h(k).q(k) + beta_k in 13), and per entry the other half of the
-// cross term, d_ki = q_k.b_i.  One thread per atom as in the Q6 pass.
-template <typename real, bool kStaged>
-__device__ __forceinline__ void adj_tile(const Sys &s, const TileTable &T, const Src<real, kStaged> &src,
-                                         const RowSrc<real, kStaged> &rows)
-{
-    const size_t N = (size_t)s.n;
-    for (int a = threadIdx.x; a < T.n_own; a += kTileThreads) {
-        const int i = T.atom0 + a;
-        const int nn = s.nn[i];
-        real qi[16];
-        const real *rq = R<real>(s.rq) + (size_t)i * 16;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) ld4<real>(rq + 4 * u, qi + 4 * u);
-        real acc[kNY];
-#pragma unroll
-        for (int m = 0; m < kNY; ++m) acc[m] = real(0);
-        for (int q = 0; 4 * q < nn; ++q) {
-            const ushort4 jq = rows.jq(a, q);
-            real wq[4], dout[4] = {real(0), real(0), real(0), real(0)};
-            rows.w(a, q, wq);
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                if (4 * q + e < nn) {
-                    real x[14];
-                    src.all(quad_get(jq, e), x);
-                    real p = qi[0] * x[0];
-#pragma unroll
-                    for (int m = 0; m < kNY; ++m) {
-                        acc[m] = fma_r(wq[e], x[m], acc[m]);
-                        if (m > 0) p = fma_r(qi[m], x[m], p);
-                    }
-                    dout[e] = p;
-                }
-            }
-            st4<real>(quad_real<real>(s.dq, N, q, i), dout[0], dout[1], dout[2], dout[3]);
-        }
-        real bo[14];
-        src.all(a, bo);
-        const real W = qi[13];
-        const real inv_W = W > real(0) ? real(1) / W : real(0);
-        real h[kNY], alpha = real(0);
-#pragma unroll
-        for (int m = 0; m < kNY; ++m) {
-            h[m] = (bo[m] + acc[m]) * inv_W;
-            alpha = fma_r(h[m], qi[m], alpha);
-        }
-        real *rh = R<real>(s.rh) + (size_t)i * 16;
-        st4<real>(rh, h[0], h[1], h[2], h[3]);
-        st4<real>(rh + 4, h[4], h[5], h[6], h[7]);
-        st4<real>(rh + 8, h[8], h[9], h[10], h[11]);
-        st4<real>(rh + 12, h[12], alpha + bo[13], real(0), real(0));
-    }
-}
-
-// ------------------------------------------------------------------ a8
-// F_i = V1 (2/N) FC_i + V2 sum_j { [(h_i + h_j).Y - gam_i - gam_j + c_ij]
-// v_ij + w grad_d((h_i + h_j).Y) }, written in the caller's order.  One
-// thread per atom; the neighbour's h record (14 components) and position
-// come from shared memory, the row and its cross terms a quad at a time
-// (the next quad loaded ahead).  With kVir each thread also sums the bias
-// virial of its atom's entries (every pair appears in both rows: half of
-// it).
-template <typename real, bool kStaged, bool kVir>
-__device__ __forceinline__ void force_tile(const Sys &s, const TileTable &T, const Src<real, kStaged> &src,
-                                           real cn_fac, real V2, RunSum<real> vir[3])
-{
-    const size_t N = (size_t)s.n;
-    const int lane = threadIdx.x & 31;
-    const ushort4 none = make_ushort4(0, 0, 0, 0);
-    for (int a0 = threadIdx.x & ~31; a0 < T.n_own; a0 += kTileThreads) {
-        const int a = a0 + lane;
-        const bool ok = a < T.n_own;
-        const int i = T.atom0 + (ok ? a : 0);
-        const float4 pi = ok ? src.pos(a) : make_float4(0.f, 0.f, 0.f, 0.f);
-        real hi[14];
-        src.all(ok ? a : 0, hi);
-        const int nn = ok ? s.nn[i] : 0;
-        const int qmax = __reduce_max_sync(0xffffffffu, (nn + 3) >> 2);
-        real F[3] = {real(0), real(0), real(0)}, Wv[3] = {real(0), real(0), real(0)};
-        ushort4 nxt = nn > 0 ? quad_at(s.elist, N, 0, i) : none;
-        for (int q = 0; q < qmax; ++q) {
-            const ushort4 cur = nxt;
-            if (q + 1 < qmax) nxt = 4 * (q + 1) < nn ? quad_at(s.elist, N, q + 1, i) : none;
-            real cq[4] = {real(0), real(0), real(0), real(0)};
-            if (4 * q < nn) {  // the cross terms c = b_i.q_j + b_j.q_i of the quad
-                real dq[4];
-                ld4<real>(quad_real<real>(s.eq, N, q, i), cq);
-                ld4<real>(quad_real<real>(s.dq, N, q, i), dq);
-#pragma unroll
-                for (int c = 0; c < 4; ++c) cq[c] += dq[c];
-            }
-            // the quad's four entries, unrolled and predicated (an entry past
-            // the row is evaluated at a dummy displacement and not added)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const bool valid = 4 * q + c < nn;
-                const int jl = valid ? quad_get(cur, c) : 0;
-                const float4 pj = valid ? src.pos(jl) : pi;
-                Vec3<real> d = pair_disp<real>(s, pi, pj);
-                if (!valid) {
-                    d.x = real(s.r0);
-                    d.y = d.z = real(0);
-                }
-                real inv_r, w, dw;
-                pair_switch_fast<real>(s, d, inv_r, w, dw);
-                real hj[14];
-                src.all(jl, hj);
-                const real ux = d.x * inv_r, uy = d.y * inv_r, uz = d.z * inv_r;
-                real hs[kNY], cvec[kNY];
-#pragma unroll
-                for (int m = 0; m < kNY; ++m) {
-                    hs[m] = hi[m] + hj[m];
-                    cvec[m] = w * hs[m];
-                }
-                real Y[kNY], gY[3];
-                ylm13_grad<real>(ux, uy, uz, inv_r, cvec, Y, gY);
-                real t = cq[c] - (hi[13] + hj[13]);
-#pragma unroll
-                for (int m = 0; m < kNY; ++m) t = fma_r(hs[m], Y[m], t);
-                const real radial = valid ? V2 * t * dw : real(0);
-                const real V2v = valid ? V2 : real(0);
-                const real G[3] = {fma_r(radial, ux, V2v * gY[0]), fma_r(radial, uy, V2v * gY[1]),
-                                   fma_r(radial, uz, V2v * gY[2])};
-                F[0] += G[0];
-                F[1] += G[1];
-                F[2] += G[2];
-                if (kVir) {
-                    Wv[0] = fma_r(G[0], d.x, Wv[0]);
-                    Wv[1] = fma_r(G[1], d.y, Wv[1]);
-                    Wv[2] = fma_r(G[2], d.z, Wv[2]);
-                }
-            }
-        }
-        if (!ok) continue;
-        real fc[4];
-        ld4<real>(R<real>(s.fc) + 4 * (size_t)i, fc);
-        float *o = s.F_out + 3 * (size_t)s.perm[i];
-        real Ft[3];
-#pragma unroll
-        for (int z = 0; z < 3; ++z) Ft[z] = fma_r(cn_fac, fc[z], F[z]);
-        if (s.accumulate) {
-            o[0] += (float)Ft[0];
-            o[1] += (float)Ft[1];
-            o[2] += (float)Ft[2];
-        } else {
-            o[0] = (float)Ft[0];
-            o[1] = (float)Ft[1];
-            o[2] = (float)Ft[2];
-        }
-        if (kVir) {
-            real wc[4];
-            ld4<real>(R<real>(s.wc) + 4 * (size_t)i, wc);
-#pragma unroll
-            for (int z = 0; z < 3; ++z) vir[z].add(real(0.5) * fma_r(cn_fac, wc[z], Wv[z]));
-        }
-    }
-}
-
-// The chain-rule factors of the two CVs, once per block: an FP64 chain is
-// long and its pipe narrow on this part, so no thread repeats it.
-template <typename real>
-__device__ __forceinline__ void force_factors(const Sys &s, real &cn_fac, real &V2)
-{
+    // the chain-rule factors of the two CVs, once per block: an FP64 chain is
+    // long and its pipe narrow on this part, so no thread repeats it
     __shared__ real fac[2];
     if (threadIdx.x == 0) {
         fac[0] = (real)(s.scal[kDV0] * s.fscale * 2.0 / s.n);
         fac[1] = s.ncv == 2 ? (real)(s.scal[kDV1] * s.fscale) : real(0);
     }
     __syncthreads();
-    cn_fac = fac[0];
-    V2 = fac[1];
-}
-
-// ------------------------------------------------------------------ blocks
-// Each block walks tiles b, b + nb, ...; per tile: the staging table, the
-// staged atoms (when they fit), the pass, a barrier before the next tile.
-
-// Shared-memory layout of a staged pass: with positions, [cap] float4 then
-// the records; without, the records alone.
-template <typename real>
-__device__ __forceinline__ void stage_pointers(const Sys &s, bool with_pos, float4 *&spos, real *&srec, real *&spair)
-{
-    spos = with_pos ? reinterpret_cast<float4 *>(tile_dyn) : nullptr;
-    srec = reinterpret_cast<real *>(tile_dyn + (with_pos ? (size_t)s.stage_cap * 16 : 0));
-    spair = srec + (size_t)s.stage_cap * kRecQ;
-}
-
-template <typename real, bool kCompute, bool kVir>
-__device__ __forceinline__ void fwd_block(const Sys &s, Blk k)
-{
-    __shared__ __align__(16) TileTable T;
-    float4 *spos = reinterpret_cast<float4 *>(tile_dyn);
-    unsigned short *slist = reinterpret_cast<unsigned short *>(tile_dyn + (size_t)s.stage_cap * 16);
-    RunSum<real> cn;
-    for (int t = k.b; t < s.tiles; t += k.nb) {
-        tile_load(s, t, T);
-        if (T.total <= s.stage_cap) {
-            stage_tile<real>(T, s.pos_s, nullptr, spos, nullptr, nullptr);
-            const Src<real, true> src{T, spos, nullptr, nullptr, s.pos_s, nullptr};
-            fwd_tile<real, true, kCompute, kVir>(s, T, src, slist, cn);
-        } else {
-            const Src<real, false> src{T, nullptr, nullptr, nullptr, s.pos_s, nullptr};
-            fwd_tile<real, false, kCompute, kVir>(s, T, src, slist, cn);
-        }
-        __syncthreads();
-    }
-    // without a Q6 pass this pass holds the CV sum (its grid: one block per tile)
-    if (kCompute && s.ncv == 1) last_block_cv(s, k, cn.value(), 0.0);
-}
-
-// The Q6 and adjoint passes: records and the own rows staged (both must
-// fit), else both read from global memory.
-template <typename real, bool kAvg>
-__device__ __forceinline__ void records_block(const Sys &s, Blk k)
-{
-    __shared__ __align__(16) TileTable T;
-    float4 *spos;
-    real *srec, *spair;
-    stage_pointers<real>(s, false, spos, srec, spair);
-    const OwnRows<real> o = own_rows_at<real>(reinterpret_cast<unsigned char *>(spair + (size_t)s.stage_cap * 2));
-    const real *rec = R<real>(kAvg ? s.rq : s.rb);
-    const size_t N = (size_t)s.n;
-    RunSum<real> cn, q6;
-    for (int t = k.b; t < s.tiles; t += k.nb) {
-        tile_load(s, t, T);
-        if (T.total <= s.stage_cap && stage_own_rows<real>(s, T, o)) {
-            stage_tile<real>(T, nullptr, rec, nullptr, srec, spair);  // waits for the rows' copies too
-            const Src<real, true> src{T, nullptr, srec, spair, s.pos_s, rec};
-            const RowSrc<real, true> rows{o, s.elist, s.wl, N, T.atom0};
-            if (kAvg) avg_tile<real, true>(s, T, src, rows, cn, q6);
-            else adj_tile<real, true>(s, T, src, rows);
-        } else {
-            const Src<real, false> src{T, nullptr, nullptr, nullptr, s.pos_s, rec};
-            const RowSrc<real, false> rows{o, s.elist, s.wl, N, T.atom0};
-            if (kAvg) avg_tile<real, false>(s, T, src, rows, cn, q6);
-            else adj_tile<real, false>(s, T, src, rows);
-        }
-        __syncthreads();
-    }
-    if (kAvg) last_block_cv(s, k, cn.value(), q6.value());
-}
-
-template <typename real, bool kVir>
-__device__ __forceinline__ void force_block(const Sys &s, Blk k)
-{
-    __shared__ __align__(16) TileTable T;
-    float4 *spos;
-    real *srec, *spair;
-    stage_pointers<real>(s, true, spos, srec, spair);
-    real cn_fac, V2;
-    force_factors<real>(s, cn_fac, V2);
-    const real *rh = R<real>(s.rh);
-    RunSum<real> vir[3];
-    for (int t = k.b; t < s.tiles; t += k.nb) {
-        tile_load(s, t, T);
-        if (T.total <= s.stage_cap) {
-            stage_tile<real>(T, s.pos_s, rh, spos, srec, spair);
-            const Src<real, true> src{T, spos, srec, spair, s.pos_s, rh};
-            force_tile<real, true, kVir>(s, T, src, cn_fac, V2, vir);
-        } else {
-            const Src<real, false> src{T, nullptr, nullptr, nullptr, s.pos_s, rh};
-            force_tile<real, false, kVir>(s, T, src, cn_fac, V2, vir);
-        }
-        __syncthreads();
-    }
-    if (kVir) virial_finish<real>(s, k, vir[0], vir[1], vir[2]);
-}
-
-// n_cv == 1: F_i = V1 (2/N) FC_i, one thread per atom (sorted order).
-template <typename real, bool kVir>
-__device__ __forceinline__ void force_cn(const Sys &s, Blk k)
-{
-    real cn_fac, V2;
-    force_factors<real>(s, cn_fac, V2);
-    RunSum<real> vir[3];
-    for (int i = k.b * kTileThreads + threadIdx.x; i < s.n; i += k.nb * kTileThreads) {
-        real fc[4];
-        ld4<real>(R<real>(s.fc) + 4 * (size_t)i, fc);
-        float *o = s.F_out + 3 * (size_t)s.perm[i];
-        if (s.accumulate) {
-            o[0] += (float)(cn_fac * fc[0]);
-            o[1] += (float)(cn_fac * fc[1]);
-            o[2] += (float)(cn_fac * fc[2]);
-        } else {
-            o[0] = (float)(cn_fac * fc[0]);
-            o[1] = (float)(cn_fac * fc[1]);
-            o[2] = (float)(cn_fac * fc[2]);
-        }
-        if (kVir) {
-            real wc[4];
-            ld4<real>(R<real>(s.wc) + 4 * (size_t)i, wc);
+    const real cn_fac = fac[0], V2 = fac[1];
+    // each warp takes its own chunk of 32 atoms (a block of kBlockAtoms/32
+    // warps is one work item, one per 128 atoms of the grid): no barrier
+    constexpr int kWarps = kBlockAtoms / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int items = (s.n + kPairChunk * kWarps - 1) / (kPairChunk * kWarps);
+    RunSum<real> vx, vy, vz;
+    for (int it = 0, g; (g = work_item(k, it)) < items; ++it) {
+        const int i0 = (g * kWarps + warp) * kPairChunk;
+        if (i0 >= s.n) continue;  // warp-uniform
+        // inclusive prefix of the half-row lengths, one lane per atom
+        int off = i0 + lane < s.n ? s.nh[i0 + lane] : 0;
 #pragma unroll
-            for (int z = 0; z < 3; ++z) vir[z].add(real(0.5) * cn_fac * wc[z]);
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, off, o);
+            if (lane >= o) off += y;
+        }
+        const int T = __shfl_sync(0xffffffffu, off, 31);
+        for (int p0 = 0; p0 < T; p0 += 32) {
+            const int p = p0 + lane;
+            // the atom of entry p: the first a whose inclusive prefix exceeds p
+            int lo = 0, hi = 31;
+#pragma unroll
+            for (int step = 0; step < 5; ++step) {
+                const int mid = (lo + hi) >> 1;
+                if (__shfl_sync(0xffffffffu, off, mid) > p) hi = mid;
+                else lo = mid + 1;
+            }
+            const int prev = __shfl_sync(0xffffffffu, off, lo > 0 ? lo - 1 : 0);  // every lane shuffles
+            const int start = lo > 0 ? prev : 0;
+            if (p < T) pair_force<real, kVir>(s, i0 + lo, p - start, cn_fac, V2, vx, vy, vz);
         }
     }
-    if (kVir) virial_finish<real>(s, k, vir[0], vir[1], vir[2]);
+    if (kVir) virial_finish<real>(s, k, vx, vy, vz);
 }
 
-// ------------------------------------------------------------------ kernels
-// Single-system launches: one block per tile (the passes holding a sum keep
-// that grid; the others may be capped by a batch tile setting and walk
-// their tiles grid-stride).  Batched launches: a block finds its system and
-// its block index within that system's grid.
-#define METAD_TILE_KERNELS(NAME, BODY, MINB)                                                              \
-    template <typename real, bool kA, bool kB>                                                           \
-    __global__ void __launch_bounds__(kTileThreads, MINB) k_##NAME(Sys s) { BODY<real, kA, kB>(s, own_blk()); } \
-    template <typename real, bool kA, bool kB>                                                           \
-    __global__ void __launch_bounds__(kTileThreads, MINB) kb_##NAME(BatchView v)                          \
-    {                                                                                                    \
-        Blk k;                                                                                           \
-        const Sys &s = v.sys[batch_system(v, k)];                                                        \
-        BODY<real, kA, kB>(s, k);                                                                        \
+template <typename real, bool kVir = false>
+__global__ void __launch_bounds__(kBlockAtoms) k_force_pairs(Sys s) { force_pairs<real, kVir>(s, own_blk()); }
+
+template <typename real, bool kVir = false>
+__global__ void __launch_bounds__(kBlockAtoms) kb_force_pairs(BatchView v)
+{
+    Blk k;
+    const Sys &s = v.sys[batch_system(v, k)];
+    force_pairs<real, kVir>(s, k);
+}
+
+template <typename real>
+__device__ __forceinline__ void load_pair_force(const real *slot, real &fx, real &fy, real &fz);
+template <>
+__device__ __forceinline__ void load_pair_force<float>(const float *slot, float &fx, float &fy, float &fz)
+{
+    const float4 t = __ldcs(reinterpret_cast<const float4 *>(slot));
+    fx = t.x;
+    fy = t.y;
+    fz = t.z;
+}
+template <>
+__device__ __forceinline__ void load_pair_force<double>(const double *slot, double &fx, double &fy, double &fz)
+{
+    const double2 a = __ldcs(reinterpret_cast<const double2 *>(slot));
+    const double2 b = __ldcs(reinterpret_cast<const double2 *>(slot) + 1);
+    fx = a.x;
+    fy = a.y;
+    fz = b.x;
+}
+
+// a8, pass 2: F_i = sum_{j > i} G_ij - sum_{j < i} G_ji: the slots of i's
+// row hold exactly those terms (pass 1 wrote both ends of every pair), summed
+// in row order per lane and a fixed shuffle tree across lanes: deterministic,
+// no atomics, and contiguous reads.
+template <typename real>
+__device__ __forceinline__ void force_gather_group(const Sys &s, const AtomLane a, float *F, int accumulate)
+{
+    real fx = real(0), fy = real(0), fz = real(0);
+    if (a.ok) {
+        const int nn = s.nn[a.i];
+        const real *pf = R<real>(s.pairF) + (size_t)a.i * s.max_nb * 4;
+        for (int k = a.l; k < nn; k += kG) {
+            real gx, gy, gz;
+            load_pair_force<real>(pf + 4 * (size_t)k, gx, gy, gz);
+            fx += gx;
+            fy += gy;
+            fz += gz;
+        }
     }
+    fx = group_sum<real>(fx);
+    fy = group_sum<real>(fy);
+    fz = group_sum<real>(fz);
+    if (a.ok && a.l == 0) {
+        float *o = F + 3 * (size_t)s.perm[a.i];
+        if (accumulate) {
+            o[0] += (float)fx;
+            o[1] += (float)fy;
+            o[2] += (float)fz;
+        } else {
+            o[0] = (float)fx;
+            o[1] = (float)fy;
+            o[2] = (float)fz;
+        }
+    }
+}
 
-template <typename real, bool kCompute, bool kVir>
-__device__ __forceinline__ void fwd_body(const Sys &s, Blk k) { fwd_block<real, kCompute, kVir>(s, k); }
-template <typename real, bool kUnusedA, bool kUnusedB>
-__device__ __forceinline__ void avg_body(const Sys &s, Blk k) { records_block<real, true>(s, k); }
-template <typename real, bool kUnusedA, bool kUnusedB>
-__device__ __forceinline__ void adj_body(const Sys &s, Blk k) { records_block<real, false>(s, k); }
-template <typename real, bool kVir, bool kUnused>
-__device__ __forceinline__ void force_body(const Sys &s, Blk k) { force_block<real, kVir>(s, k); }
-template <typename real, bool kVir, bool kUnused>
-__device__ __forceinline__ void force_cn_body(const Sys &s, Blk k) { force_cn<real, kVir>(s, k); }
+template <typename real>
+__device__ __forceinline__ void force_gather(const Sys &s, Blk k)
+{
+    const int groups = group_grid(s.n);
+    for (int it = 0, g; (g = work_item(k, it)) < groups; ++it)
+        force_gather_group<real>(s, atom_lane_at(s, g), s.F_out, s.accumulate);
+}
 
-METAD_TILE_KERNELS(tile_fwd, fwd_body, 2)
-METAD_TILE_KERNELS(tile_avg, avg_body, 2)
-METAD_TILE_KERNELS(tile_adj, adj_body, 2)
-METAD_TILE_KERNELS(tile_force, force_body, 2)
-METAD_TILE_KERNELS(force_cn, force_cn_body, 1)
-#undef METAD_TILE_KERNELS
+template <typename real>
+__global__ void __launch_bounds__(kBlockAtoms) k_force_gather(Sys s) { force_gather<real>(s, own_blk()); }
+
+template <typename real>
+__global__ void __launch_bounds__(kBlockAtoms) kb_force_gather(BatchView v)
+{
+    Blk k;
+    const Sys &s = v.sys[batch_system(v, k)];
+    force_gather<real>(s, k);
+}
 
 template <typename real>
 __global__ void k_per_atom_out(Sys s, double *out)
@@ -1096,94 +1035,130 @@ __global__ void k_per_atom_out(Sys s, double *out)
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.n) return;
     const int u = s.perm[i];
-    out[u] = (double)R<real>(s.rq)[(size_t)i * 16 + 14];
-    if (s.ncv == 2) out[(size_t)s.n + u] = (double)R<real>(s.rb)[(size_t)i * 16 + 14];
+    out[u] = (double)R<real>(s.cn)[i];
+    if (s.ncv == 2) out[(size_t)s.n + u] = (double)R<real>(s.qb6)[i];
 }
+
 
 }  // namespace
 
-// ------------------------------------------------------------------ host side
-namespace {
-
-// The kernel of a pass: precision, flag (forward pass: with the CV math),
-// virial, single-system or batched.
-template <typename real>
-const void *pass_kernel(int pass, bool flag, bool vir, bool batched)
+void launch_cv_fwd(const Sys &s, int fp64, int fused_filter, cudaStream_t st)
 {
-#define METAD_PICK(K, A, B) (batched ? (const void *)kb_##K<real, A, B> : (const void *)k_##K<real, A, B>)
-    switch (pass) {
-    case kPassFwd:
-        if (!flag) return METAD_PICK(tile_fwd, false, false);
-        return vir ? METAD_PICK(tile_fwd, true, true) : METAD_PICK(tile_fwd, true, false);
-    case kPassAvg: return METAD_PICK(tile_avg, false, false);
-    case kPassAdj: return METAD_PICK(tile_adj, false, false);
-    case kPassForce: return vir ? METAD_PICK(tile_force, true, false) : METAD_PICK(tile_force, false, false);
-    case kPassForceCn: return vir ? METAD_PICK(force_cn, true, false) : METAD_PICK(force_cn, false, false);
-    }
-#undef METAD_PICK
-    return nullptr;
-}
-
-const void *pick(int pass, int fp64, bool flag, bool vir, bool batched)
-{
-    return fp64 ? pass_kernel<double>(pass, flag, vir, batched) : pass_kernel<float>(pass, flag, vir, batched);
-}
-
-}  // namespace
-
-int tile_smem(const Sys &s, int pass)
-{
-    const int rs = s.fp64 ? 8 : 4;
-    switch (pass) {
-    case kPassFwd: return s.stage_cap * 16 + s.max_nb * kTileThreads * 2;
-    case kPassForceCn: return 0;
-    case kPassForce: return s.stage_cap * (16 + (kRecQ + 2) * rs);
-    default: return s.stage_cap * (kRecQ + 2) * rs + own_rows_bytes(rs);  // records and own rows
+    const int nb = group_grid(s.n);
+    if (fp64) {
+        if (fused_filter)
+            k_cv_fwd<double, true><<<nb, kBlockAtoms, 0, st>>>(s);
+        else
+            k_cv_fwd<double, false><<<nb, kBlockAtoms, 0, st>>>(s);
+    } else {
+        if (fused_filter)
+            k_cv_fwd<float, true><<<nb, kBlockAtoms, 0, st>>>(s);
+        else
+            k_cv_fwd<float, false><<<nb, kBlockAtoms, 0, st>>>(s);
     }
 }
 
-int pass_blocks(const Sys &s, int pass)
+void launch_cv_avg(const Sys &s, int fp64, cudaStream_t st)
 {
-    if (pass == kPassForceCn) {
-        const int g = (s.n + kTileThreads - 1) / kTileThreads;
-        return g < 1 ? 1 : g;
+    if (fp64)
+        k_cv_avg<double><<<grid_blocks(s, GK_CV, 0), kBlockAtoms, 0, st>>>(s);
+    else
+        k_cv_avg<float><<<grid_blocks(s, GK_CV, 0), kBlockAtoms, 0, st>>>(s);
+}
+
+void launch_cv_sum(const Sys &s, int fp64, cudaStream_t st)
+{
+    if (fp64)
+        k_cv_sum<double><<<grid_blocks(s, GK_SUM, 0), kSumThreads, 0, st>>>(s);
+    else
+        k_cv_sum<float><<<grid_blocks(s, GK_SUM, 0), kSumThreads, 0, st>>>(s);
+}
+
+void launch_adjoint(const Sys &s, int fp64, cudaStream_t st)
+{
+    if (fp64)
+        k_adjoint<double><<<grid_blocks(s, GK_ATOM32, 0), kBlockAtoms, 0, st>>>(s);
+    else
+        k_adjoint<float><<<grid_blocks(s, GK_ATOM32, 0), kBlockAtoms, 0, st>>>(s);
+}
+
+void launch_force_pairs(const Sys &s, int fp64, double scale, cudaStream_t st)
+{
+    Sys t = s;
+    t.fscale = scale;
+    const int nb = grid_blocks(s, GK_ATOM128, 0);
+    if (fp64) {
+        if (s.virial) k_force_pairs<double, true><<<nb, kBlockAtoms, 0, st>>>(t);
+        else k_force_pairs<double><<<nb, kBlockAtoms, 0, st>>>(t);
+    } else {
+        if (s.virial) k_force_pairs<float, true><<<nb, kBlockAtoms, 0, st>>>(t);
+        else k_force_pairs<float><<<nb, kBlockAtoms, 0, st>>>(t);
     }
-    return s.tiles;
 }
 
-void launch_tile_pass(const Sys &s, int pass, int flag, cudaStream_t st)
+void launch_force_gather(const Sys &s, int fp64, float *F, int accumulate, cudaStream_t st)
 {
-    const void *k = pick(pass, s.fp64, flag != 0, s.virial != 0, false);
-    void *args[] = {const_cast<Sys *>(&s)};
-    cudaLaunchKernel(k, dim3((unsigned)pass_blocks(s, pass)), dim3(kTileThreads), args, (size_t)tile_smem(s, pass),
-                     st);
+    Sys t = s;
+    t.F_out = F;
+    t.accumulate = accumulate;
+    if (fp64)
+        k_force_gather<double><<<group_grid(s.n), kBlockAtoms, 0, st>>>(t);
+    else
+        k_force_gather<float><<<group_grid(s.n), kBlockAtoms, 0, st>>>(t);
 }
 
-void launch_batch_pass(const BatchView &v, int total, int pass, int fp64, int flag, int vir, int smem,
-                       cudaStream_t st)
+void launch_batch_cv(const BatchView &groups, int group_total, const BatchView &cv, int cv_total,
+                     const BatchView &sums, int sum_total, int fp64, int ncv, cudaStream_t st)
 {
-    if (total <= 0) return;
-    const void *k = pick(pass, fp64, flag != 0, vir != 0, true);
-    void *args[] = {const_cast<BatchView *>(&v)};
-    cudaLaunchKernel(k, dim3((unsigned)total), dim3(kTileThreads), args, (size_t)smem, st);
+    if (group_total <= 0) return;
+    if (fp64) {
+        kb_cv_fwd<double><<<group_total, kBlockAtoms, 0, st>>>(groups);
+        if (ncv == 2)
+            kb_cv_avg<double><<<cv_total, kBlockAtoms, 0, st>>>(cv);
+        else
+            kb_cv_sum<double><<<sum_total, kSumThreads, 0, st>>>(sums);
+    } else {
+        kb_cv_fwd<float><<<group_total, kBlockAtoms, 0, st>>>(groups);
+        if (ncv == 2)
+            kb_cv_avg<float><<<cv_total, kBlockAtoms, 0, st>>>(cv);
+        else
+            kb_cv_sum<float><<<sum_total, kSumThreads, 0, st>>>(sums);
+    }
 }
 
-// Dynamic shared memory limits of the tile passes (their staging capacity
-// needs more than the default 48 KB).
+void launch_batch_force(const BatchView &groups, int group_total, const BatchView &adj, int adj_total,
+                        const BatchView &pairs, int pair_total, int fp64, int ncv, int virial, cudaStream_t st,
+                        int part)
+{
+    if (group_total <= 0) return;
+    const bool adjoint = part != 2 && ncv == 2, forces = part != 1;
+    if (fp64) {
+        if (adjoint) kb_adjoint<double><<<adj_total, kBlockAtoms, 0, st>>>(adj);
+        if (!forces) return;
+        if (virial) kb_force_pairs<double, true><<<pair_total, kBlockAtoms, 0, st>>>(pairs);
+        else kb_force_pairs<double><<<pair_total, kBlockAtoms, 0, st>>>(pairs);
+        kb_force_gather<double><<<group_total, kBlockAtoms, 0, st>>>(groups);
+    } else {
+        if (adjoint) kb_adjoint<float><<<adj_total, kBlockAtoms, 0, st>>>(adj);
+        if (!forces) return;
+        if (virial) kb_force_pairs<float, true><<<pair_total, kBlockAtoms, 0, st>>>(pairs);
+        else kb_force_pairs<float><<<pair_total, kBlockAtoms, 0, st>>>(pairs);
+        kb_force_gather<float><<<group_total, kBlockAtoms, 0, st>>>(groups);
+    }
+}
+
+// The gather kernels without shared memory prefer the SM's unified storage
+// as L1.  (Kernels with even a small static shared array are left to the
+// driver: a minimal shared carve-out caps how many of their blocks fit.)
 void configure_kernels()
 {
-    for (int fp64 = 0; fp64 < 2; ++fp64)
-        for (int pass = 0; pass < kNumPasses; ++pass)
-            for (int flag = 0; flag < 2; ++flag)
-                for (int vir = 0; vir < 2; ++vir)
-                    for (int batched = 0; batched < 2; ++batched) {
-                        const void *k = pick(pass, fp64, flag != 0, vir != 0, batched != 0);
-                        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxTileSmem);
-                        // all of the SM's unified storage as shared memory, so
-                        // two blocks of a staged pass fit on an SM
-                        cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                             cudaSharedmemCarveoutMaxShared);
-                    }
+    const int l1 = cudaSharedmemCarveoutMaxL1;
+    cudaFuncSetAttribute(k_adjoint<float>, cudaFuncAttributePreferredSharedMemoryCarveout, l1);
+    cudaFuncSetAttribute(k_force_pairs<float>, cudaFuncAttributePreferredSharedMemoryCarveout, l1);
+    cudaFuncSetAttribute(k_force_gather<float>, cudaFuncAttributePreferredSharedMemoryCarveout, l1);
+    cudaFuncSetAttribute(kb_adjoint<float>, cudaFuncAttributePreferredSharedMemoryCarveout, l1);
+    cudaFuncSetAttribute(kb_force_pairs<float>, cudaFuncAttributePreferredSharedMemoryCarveout, l1);
+    cudaFuncSetAttribute(kb_force_gather<float>, cudaFuncAttributePreferredSharedMemoryCarveout, l1);
     cudaGetLastError();
 }
 
@@ -1245,6 +1220,4 @@ void set_ylm_constants(cudaStream_t st)
     cudaMemcpyToSymbolAsync(c_ylm, &h, sizeof(h), 0, cudaMemcpyHostToDevice, st);
 }
 
-
 }  // namespace metad
-

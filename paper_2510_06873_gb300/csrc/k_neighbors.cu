@@ -1,19 +1,18 @@
-// Steps a1-a3: ingest, tile-ranked cell order, Verlet rows, and the export
-// of the exact neighbour rows.
+// Steps a1-a3: ingest, Morton-ranked cell order, Verlet list and the exact
+// neighbour list.
 //
 // Each step:
 //   k_gather_check  positions in cell order (wrapped), and a flag when any
 //                   atom moved more than skin/2 since the last rebuild
 //   rebuild chain   (early exit unless flagged) counting sort of the atoms
-//                   into cells of edge >= rc + skin, ranked tile by tile,
-//                   stable by caller index, and the Verlet rows
-//                   r < rc + skin, one block per tile of cells
-// The exact rows {j : r_ij^2 < rc^2} are filtered from the Verlet rows by
-// the forward pass (k_cv.cu).  They are the FP64 definition bit for bit:
-// while no atom has moved more than skin/2, every pair now inside rc was
-// inside rc + skin at the rebuild, and the float32 estimate only decides
-// outside a guard band.
-#include "tiles.cuh"
+//                   into Morton-ranked cells of edge >= rc + skin, stable by
+//                   caller index, and the Verlet list r < rc + skin
+//   filter          exact rows {j : r_ij^2 < rc^2} from the Verlet rows
+//                   (fused into the CV kernel, or k_filter on its own)
+// The exact rows are the FP64 definition bit for bit: while no atom has moved
+// more than skin/2, every pair now inside rc was inside rc + skin at the
+// rebuild, and the float32 estimate only decides outside a guard band.
+#include "metad_impl.cuh"
 
 namespace metad {
 
@@ -221,6 +220,7 @@ __device__ __forceinline__ void sort_gather_cell(const Sys &s, int c)
         float4 p = load_wrapped(s, s.perm[t], bad);
         s.pos_s[t] = p;
         s.pos_ref[t] = p;
+        s.scell[t] = c;
     }
 }
 
@@ -230,9 +230,35 @@ __device__ __forceinline__ void cell_sort_gather(const Sys &s, Blk k)
     for (int c = k.b * blockDim.x + threadIdx.x; c < s.ncell; c += k.nb * blockDim.x) sort_gather_cell(s, c);
 }
 
+__device__ __forceinline__ int wrap_cell(int c, int nc)
+{
+    c += (c < 0) ? nc : 0;
+    c -= (c >= nc) ? nc : 0;
+    return c;
+}
+
+// Stencil offsets along one axis: -1, 0, 1 with three or more cells (each
+// distinct cell once with fewer).
+__device__ __forceinline__ int axis_span(int nc) { return nc >= 3 ? 3 : nc; }
+__device__ __forceinline__ int axis_off(int nc, int idx) { return nc >= 3 ? idx - 1 : idx; }
+
+constexpr int kStencil = 27;
+constexpr int kVerletBatch = 4;  // candidate rounds whose loads are issued together
+
+// Verlet rows {j : r_ij^2 < (rc + skin)^2 (1 + 1e-4)} over the 27 surrounding
+// cells (each distinct cell once): entries with j > i first, then j < i, in
+// stencil-cell order, atoms in cell order.  A group of kG lanes per atom.
+// Atoms are sorted by cell rank, so a cell ranked below the atom's own holds
+// only j < i and one ranked above only j > i: each part walks only its
+// cells (the own cell in both).  The group stages the part's cell starts
+// and the prefix of their counts in shared memory (the lanes look the cells
+// up in parallel); the candidates are then one flat range that the lanes
+// walk kG at a time, each lane finding its cell by advancing along the
+// prefix, so every position load is independent of the others and
 // End of a rebuild, run once by the last Verlet block to finish: the rows'
-// box becomes the reference and the flag is cleared for the next step (kept
-// set when the skin is zero, so every step rebuilds).
+// box becomes the reference, the rows are marked new, and the flag is
+// cleared for the next step (kept set when the skin is zero, so every step
+// rebuilds).
 __device__ __forceinline__ void finish_rebuild(const Sys &s, Blk k)
 {
     __shared__ bool am_last;
@@ -243,91 +269,138 @@ __device__ __forceinline__ void finish_rebuild(const Sys &s, Blk k)
     s.ticket[4] = 0u;
     *s.rebuilds += 1ull;
     for (int a = 0; a < 3; ++a) s.Lref[a] = s.Lhi[a];
+    if (s.mirror) *s.rows_fresh = 1;  // the next filter finds the mirror positions
     *s.flag = s.always_rebuild ? 1 : 0;
 }
 
-// The staged-list entries along one axis that the stencil of list entry e
-// touches: its cell coordinate -1, 0, +1 (periodic), each distinct cell
-// once (fewer than three cells on an axis repeat coordinates).
-__device__ __forceinline__ void stencil_axis(const TileTable &T, int axis, int e, int nc, int out[3], int &m)
-{
-    m = 0;
-    const int c = T.c[axis][e];
-    for (int d = -1; d <= 1; ++d) {
-        const int cc = (c + d + nc) % nc;
-        int j = 0;
-        while (j < T.n[axis] - 1 && T.c[axis][j] != cc) ++j;  // the list holds every neighbour cell
-        bool dup = false;
-        for (int q = 0; q < m; ++q) dup = dup || out[q] == j;
-        if (!dup) out[m++] = j;
-    }
-}
-
-// Verlet rows {j : r_ij^2 < (rc + skin)^2 (1 + 1e-4)} of the tile's atoms at
-// the reference positions, over the 27 surrounding cells (each distinct
-// cell once): entries in stencil order (offsets z, y, x), atoms in cell
-// order, stored as tile-local indices.  One thread per atom.
-template <bool kStaged>
-__device__ __forceinline__ void verlet_tile(const Sys &s, const TileTable &T, const float4 *spos)
-{
-    const size_t N = (size_t)s.n;
-    for (int a = threadIdx.x; a < T.n_own; a += kTileThreads) {
-        const int i = T.atom0 + a;
-        const float4 pi = kStaged ? spos[a] : s.pos_ref[i];
-        int lo = 0, hi = T.nown_cells - 1;  // own cell of a
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (T.lstart[mid] <= a) lo = mid;
-            else hi = mid - 1;
-        }
-        const int ix = lo % T.ext[0], iy = (lo / T.ext[0]) % T.ext[1], iz = lo / (T.ext[0] * T.ext[1]);
-        int sx[3], sy[3], sz[3], nx, ny, nz;
-        stencil_axis(T, 0, ix, s.nc[0], sx, nx);
-        stencil_axis(T, 1, iy, s.nc[1], sy, ny);
-        stencil_axis(T, 2, iz, s.nc[2], sz, nz);
-        int cnt = 0;
-        for (int z = 0; z < nz; ++z)
-            for (int y = 0; y < ny; ++y)
-                for (int x = 0; x < nx; ++x) {
-                    const int c = T.map[(sz[z] * T.n[1] + sy[y]) * T.n[0] + sx[x]];
-                    const int e = T.lstart[c + 1];
-                    for (int b = T.lstart[c]; b < e; ++b) {
-                        const float4 pj = kStaged ? spos[b] : s.pos_ref[tile_global(T, b)];
-                        const Vec3<float> d = displacement<float>(s, pi, pj);
-                        if (b != a && fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z)) < s.rv2) {
-                            if (cnt < s.max_vnb) entry_ref(s.vlist, N, cnt, i) = (unsigned short)b;
-                            ++cnt;
-                        }
-                    }
-                }
-        if (cnt > s.max_vnb) set_err(s, kErrCapacity);
-        s.vnn[i] = min(cnt, s.max_vnb);
-    }
-}
-
-// Verlet rows of the tiles b, b + nb, ... (reference positions staged in
-// shared memory when they fit), then the end of the rebuild.
+// kVerletBatch rounds are loaded at once.  Ballot compaction keeps the
+// order.  Grid-stride over atom groups so an idle launch (no rebuild)
+// retires at once.
 __device__ __forceinline__ void verlet(const Sys &s, Blk k)
 {
     if (!*s.flag) return;
-    __shared__ __align__(16) TileTable T;
-    float4 *spos = reinterpret_cast<float4 *>(tile_dyn);
-    for (int t = k.b; t < s.tiles; t += k.nb) {
-        tile_build(s, t, T);
-        tile_store(s, t, T);  // the passes load it until the next rebuild
-        if (T.total > 65535) {  // local indices are 16-bit: empty rows, and an error
-            if (threadIdx.x == 0) set_err(s, kErrCapacity);
-            for (int a = threadIdx.x; a < T.n_own; a += kTileThreads) s.vnn[T.atom0 + a] = 0;
-        } else if (T.total <= s.stage_cap) {
-            stage_tile<float>(T, s.pos_ref, nullptr, spos, nullptr, nullptr);
-            verlet_tile<true>(s, T, spos);
-        } else {
-            verlet_tile<false>(s, T, spos);
+    __shared__ int sh_base[kAtomsPerBlock][kStencil];  // start - prefix: j = p + base
+    __shared__ int sh_pre[kAtomsPerBlock][kStencil + 1];
+    const int sx = axis_span(s.nc[0]), sy = axis_span(s.nc[1]), sz = axis_span(s.nc[2]);
+    const int nq = sx * sy * sz;
+    const int g = threadIdx.x / kG;
+    int *base = sh_base[g], *pre = sh_pre[g];
+    // lane l owns the stencil cells q = 4l .. 4l + 3 (in order), so the
+    // prefix of their counts is a local sum plus a scan over the lanes
+    constexpr int kPerLane = (kStencil + kG - 1) / kG;
+    static_assert(kPerLane * kG >= kStencil, "stencil cells per lane");
+    int qoff[kPerLane];
+#pragma unroll
+    for (int r = 0; r < kPerLane; ++r) {
+        const int q = (threadIdx.x & (kG - 1)) * kPerLane + r;
+        const int e = q % sx, b = (q / sx) % sy, c3 = q / (sx * sy);  // once per launch
+        qoff[r] = q < nq ? (axis_off(s.nc[0], e) + 1) | ((axis_off(s.nc[1], b) + 1) << 2) |
+                               ((axis_off(s.nc[2], c3) + 1) << 4)
+                         : -1;
+    }
+    const int groups = group_grid(s.n);
+    for (int it = 0, blk; (blk = work_item(k, it)) < groups; ++it) {
+        const AtomLane a = atom_lane_at(s, blk);
+        const int i = a.ok ? a.i : 0;
+        const float4 pi = s.pos_s[i];
+        const int own = s.scell[i];
+        const int xyz = s.xyz_of_rank[own];
+        const int cx = xyz & 1023, cy = (xyz >> 10) & 1023, cz = xyz >> 20;
+        int cell_r[kPerLane], start_r[kPerLane], count_r[kPerLane];
+#pragma unroll
+        for (int r = 0; r < kPerLane; ++r) {
+            cell_r[r] = -1;
+            start_r[r] = count_r[r] = 0;
+            if (qoff[r] >= 0) {
+                const int o = qoff[r];
+                const int c = s.rank_of_xyz[(wrap_cell(cz + ((o >> 4) & 3) - 1, s.nc[2]) * s.nc[1] +
+                                             wrap_cell(cy + ((o >> 2) & 3) - 1, s.nc[1])) * s.nc[0] +
+                                            wrap_cell(cx + (o & 3) - 1, s.nc[0])];
+                cell_r[r] = c;
+                start_r[r] = s.cell_start[c];
+                count_r[r] = s.cell_start[c + 1] - start_r[r];
+            }
         }
-        __syncthreads();
+        int *vrow = s.vnbr + (size_t)i * s.max_vnb;
+        int cnt = 0, nup = 0;
+#pragma unroll 1
+        for (int part = 0; part < 2; ++part) {
+            // the part's cells: ranks >= own (j > i), then <= own (j < i)
+            int loc[kPerLane], tot = 0;
+#pragma unroll
+            for (int r = 0; r < kPerLane; ++r) {
+                const bool mine = cell_r[r] >= 0 && (part == 0 ? cell_r[r] >= own : cell_r[r] <= own);
+                loc[r] = tot;
+                tot += mine ? count_r[r] : 0;
+            }
+            int incl = tot;  // inclusive scan of the lane totals within the group
+#pragma unroll
+            for (int o = 1; o < kG; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o, kG);
+                if (a.l >= o) incl += y;
+            }
+            const int excl = incl - tot;
+            __syncwarp();  // the previous part's table is no longer read
+#pragma unroll
+            for (int r = 0; r < kPerLane; ++r) {
+                const int q = a.l * kPerLane + r;
+                if (q < nq) {
+                    pre[q] = excl + loc[r];
+                    base[q] = start_r[r] - (excl + loc[r]);
+                }
+            }
+            if (a.l == kG - 1) pre[nq] = incl;
+            __syncwarp();
+            const int T = a.ok ? pre[nq] : 0;
+            const int tmax = __reduce_max_sync(0xffffffffu, T);
+            int q = 0;
+            for (int base0 = 0; base0 < tmax; base0 += kG * kVerletBatch) {
+                int jb[kVerletBatch];
+                float4 pb[kVerletBatch];
+#pragma unroll
+                for (int u = 0; u < kVerletBatch; ++u) {
+                    const int p = base0 + u * kG + a.l;
+                    jb[u] = -1;
+                    if (p < T) {
+                        while (p >= pre[q + 1]) ++q;
+                        jb[u] = p + base[q];
+                        pb[u] = s.pos_s[jb[u]];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kVerletBatch; ++u) {
+                    if (base0 + u * kG >= tmax) break;  // warp-uniform
+                    const int j = jb[u];
+                    bool in = false;
+                    if (j >= 0 && (part == 0 ? j > i : j < i)) {
+                        Vec3<float> d = displacement<float>(s, pi, pb[u]);
+                        in = fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z)) < s.rv2;
+                    }
+                    const unsigned gm = group_mask_bits(__ballot_sync(0xffffffffu, in));
+                    const int at = cnt + __popc(gm & ((1u << a.l) - 1u));
+                    if (in && at < s.max_vnb) vrow[at] = j;
+                    cnt += __popc(gm);
+                }
+            }
+            if (part == 0) nup = cnt;
+        }
+        if (a.ok && a.l == 0) {
+            if (cnt > s.max_vnb) set_err(s, kErrCapacity);
+            s.vnn[i] = min(cnt, s.max_vnb);
+            s.vnh[i] = min(nup, s.max_vnb);
+        }
     }
     finish_rebuild(s, k);
 }
+
+// Exact rows from the Verlet rows, when the CV kernel does not fuse it.
+template <typename real>
+__global__ void __launch_bounds__(kBlockAtoms) k_filter(Sys s)
+{
+    const int groups = group_grid(s.n);
+    for (int blk = blockIdx.x; blk < groups; blk += gridDim.x) filter_row<real>(s, atom_lane_at(s, blk));
+}
+
 
 // Single-system kernels of the rebuild chain.
 __global__ void k_bin_count(Sys s)
@@ -355,7 +428,7 @@ __global__ void k_cell_sort_gather(Sys s)
     chain_enter();
     cell_sort_gather(s, own_blk());
 }
-__global__ void __launch_bounds__(kTileThreads) k_verlet(Sys s)
+__global__ void __launch_bounds__(kBlockAtoms) k_verlet(Sys s)
 {
     chain_enter();
     verlet(s, own_blk());
@@ -404,7 +477,7 @@ __global__ void kb_cell_sort_gather(BatchView v)
     const Sys &s = v.sys[batch_system(v, k)];
     cell_sort_gather(s, k);
 }
-__global__ void __launch_bounds__(kTileThreads) kb_verlet(BatchView v)
+__global__ void __launch_bounds__(kBlockAtoms) kb_verlet(BatchView v)
 {
     chain_enter();
     Blk k;
@@ -412,28 +485,20 @@ __global__ void __launch_bounds__(kTileThreads) kb_verlet(BatchView v)
     verlet(s, k);
 }
 
-// Pairs (i < j) in caller indices, for export: one block per tile, one
-// thread per owned atom, entries with caller(i) < caller(j) appended through
-// one counter.
-__global__ void __launch_bounds__(kTileThreads) k_export_pairs(Sys s, long long *pairs, int *count)
+// Pairs (i < j) in caller indices, for export: one thread per sorted atom,
+// entries with caller(i) < caller(j) appended through one counter.
+__global__ void k_export_pairs(Sys s, long long *pairs, int *count)
 {
-    __shared__ __align__(16) TileTable T;
-    const size_t N = (size_t)s.n;
-    for (int t = blockIdx.x; t < s.tiles; t += gridDim.x) {
-        tile_load(s, t, T);
-        for (int a = threadIdx.x; a < T.n_own; a += kTileThreads) {
-            const int i = T.atom0 + a;
-            const int ui = s.perm[i];
-            for (int k = 0; k < s.nn[i]; ++k) {
-                const int uj = s.perm[tile_global(T, (int)entry_ref(s.elist, N, k, i))];
-                if (ui < uj) {
-                    const int slot = atomicAdd(count, 1);
-                    pairs[2 * (size_t)slot] = ui;
-                    pairs[2 * (size_t)slot + 1] = uj;
-                }
-            }
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s.n) return;
+    int ui = s.perm[i];
+    for (int k = 0; k < s.nn[i]; ++k) {
+        int uj = s.perm[s.nbr[(size_t)i * s.max_nb + k]];
+        if (ui < uj) {
+            int slot = atomicAdd(count, 1);
+            pairs[2 * (size_t)slot] = ui;
+            pairs[2 * (size_t)slot + 1] = uj;
         }
-        __syncthreads();
     }
 }
 
@@ -479,10 +544,22 @@ int grid_blocks(const Sys &s, int kind, int persist_cap)
     case GK_ATOM256_CAP: return capped((s.n + 255) / 256);
     case GK_SCAN_TILES: return (s.ncell + kScanTile - 1) / kScanTile;
     case GK_CELL128_CAP: return capped((s.ncell + 127) / 128);
+    case GK_GROUPS_CAP: return persist_grid(s.n);  // Verlet rows: up to 16 blocks per SM
     case GK_ONE: return 1;
-    case GK_TILES: return persist_cap > 0 && persist_cap < s.tiles ? persist_cap : s.tiles;
-    case GK_TILES_SUM: return s.tiles;
-    case GK_TILES_CAP: return capped(s.tiles);
+    case GK_GROUPS: {
+        const int g = group_grid(s.n);
+        return persist_cap > 0 && persist_cap < g ? persist_cap : g;
+    }
+    case GK_CV: return persist_grid(s.n);  // not tiled: its grid fixes the CV sums' order
+    case GK_ATOM32: {
+        const int g = (s.n + 31) / 32;
+        return persist_cap > 0 && persist_cap < g ? persist_cap : g;
+    }
+    case GK_ATOM128: {
+        const int g = (s.n + 127) / 128;
+        return persist_cap > 0 && persist_cap < g ? persist_cap : g;
+    }
+    case GK_SUM: return sum_blocks(s.n);
     case GK_HILLS: return bias_blocks(s.K);
     case GK_DEPOSIT: return s.deposit ? bias_blocks(s.K) : 0;
     }
@@ -497,12 +574,11 @@ void launch_gather_check(const Sys &s, cudaStream_t st)
 // A kernel of the rebuild chain, launched so it may be scheduled while the
 // previous kernel of the stream still runs (it waits for it on the device).
 template <typename Arg>
-void chained(void (*kern)(Arg), int grid, int block, cudaStream_t st, const Arg &arg, size_t smem = 0)
+void chained(void (*kern)(Arg), int grid, int block, cudaStream_t st, const Arg &arg)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3((unsigned)block);
-    cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -528,7 +604,7 @@ void launch_rebuild(const Sys &s, cudaStream_t st)
     chained(k_scan_down, grid_blocks(s, GK_SCAN_TILES, 0), kScanThreads, st, s);
     chained(k_bin_scatter, grid_blocks(s, GK_ATOM256_CAP, 0), 256, st, s);
     chained(k_cell_sort_gather, grid_blocks(s, GK_CELL128_CAP, 0), 128, st, s);
-    chained(k_verlet, capped(s.tiles), kTileThreads, st, s, (size_t)s.stage_cap * 16);
+    chained(k_verlet, grid_blocks(s, GK_GROUPS_CAP, 0), kBlockAtoms, st, s);
 }
 
 void launch_batch_gather(const BatchView &v, int total, cudaStream_t st)
@@ -536,14 +612,22 @@ void launch_batch_gather(const BatchView &v, int total, cudaStream_t st)
     if (total > 0) kb_gather_check<<<total, 256, 0, st>>>(v);
 }
 
-void launch_batch_rebuild(const BatchView *rows, const int *totals, int verlet_smem, cudaStream_t st)
+void launch_batch_rebuild(const BatchView *rows, const int *totals, cudaStream_t st)
 {
     chained(kb_bin_count, totals[GK_ATOM256_CAP], 256, st, rows[GK_ATOM256_CAP]);
     chained(kb_scan_reduce, totals[GK_SCAN_TILES], kScanThreads, st, rows[GK_SCAN_TILES]);
     chained(kb_scan_down, totals[GK_SCAN_TILES], kScanThreads, st, rows[GK_SCAN_TILES]);
     chained(kb_bin_scatter, totals[GK_ATOM256_CAP], 256, st, rows[GK_ATOM256_CAP]);
     chained(kb_cell_sort_gather, totals[GK_CELL128_CAP], 128, st, rows[GK_CELL128_CAP]);
-    chained(kb_verlet, totals[GK_TILES_CAP], kTileThreads, st, rows[GK_TILES_CAP], (size_t)verlet_smem);
+    chained(kb_verlet, totals[GK_GROUPS_CAP], kBlockAtoms, st, rows[GK_GROUPS_CAP]);
+}
+
+void launch_filter(const Sys &s, int fp64, cudaStream_t st)
+{
+    if (fp64)
+        k_filter<double><<<group_grid(s.n), kBlockAtoms, 0, st>>>(s);
+    else
+        k_filter<float><<<group_grid(s.n), kBlockAtoms, 0, st>>>(s);
 }
 
 void launch_nn_stats(const Sys &s, unsigned long long *sum, int *mx, cudaStream_t st)
@@ -556,7 +640,7 @@ void launch_nn_stats(const Sys &s, unsigned long long *sum, int *mx, cudaStream_
 void launch_export_pairs(const Sys &s, long long *pairs, int *count, cudaStream_t st)
 {
     cudaMemsetAsync(count, 0, sizeof(int), st);
-    k_export_pairs<<<s.tiles > 0 ? s.tiles : 1, kTileThreads, 0, st>>>(s, pairs, count);
+    k_export_pairs<<<(s.n + 255) / 256, 256, 0, st>>>(s, pairs, count);
 }
 
 }  // namespace metad

@@ -68,31 +68,39 @@ struct Sys {
     float a_hi, a_lo;            // 1/(1 - s_raw(rc)) (1 when not stretched)
     float k_hi, k_lo;            // s_raw(rc)/(1 - s_raw(rc)) (0 when not stretched)
     double a_d, k_d, inv_r0_d;
-    // per-atom state, sorted order (cells ranked tile by tile) unless noted
+    // per-atom state, sorted (Morton) order unless noted
     const float4 *pos_in;  // caller order
     float4 *pos_s;
     int *perm;             // sorted -> caller
+    int *scell;            // cell of each sorted atom
     int *ucell, *uslot;    // caller order: cell and slot within it
     int *cell_count;       // [ncell]
     int *cell_start;       // [ncell + 1]
     int *scan_part;        // block partial sums of the cell scan
-    const int *rank_of_xyz;  // cell (x, y, z) -> rank
-    // tiles of up to 3 x 3 x 3 cells, one thread block each (tiles.cuh)
-    int tiles;             // tiles of the current cell grid
-    const int *tile_xyz;   // [tiles] tile coordinates x | y << 10 | z << 20, Morton order
-    void *tile_tab;        // [tiles] staging tables, written by each rebuild
-    int stage_cap;         // staged atoms a tile keeps in shared memory
-    int fp64;              // records in FP64 (precision 1)
-    // neighbour rows in quad-major order ([k / 4][n][4]: four entries of an
-    // atom side by side, quads of consecutive atoms side by side); entries
-    // are tile-local atom indices
-    unsigned short *elist; // [max_nb / 4][n][4]: r < rc exactly, in Verlet-row order
+    const int *rank_of_xyz;  // cell (x, y, z) -> Morton rank
+    const int *xyz_of_rank;  // Morton rank -> packed x | y << 10 | z << 20
+    int *nbr;              // [n][max_nb] sorted indices, row per atom: r < rc exactly;
+                           // entries j > i first (nh of them), then j < i
     int *nn;               // [n]
-    // Verlet rows (cutoff rc + skin at the reference positions)
+    int *nh;               // [n] entries with j > i
+    void *wl;              // JW<real> [n][max_nb]: neighbour and switch weight of each entry
+    void *pairF;           // real [n][max_nb][4]: G_ij in i's entry of j, -G_ji in the others
+    void *geo;             // real [n][max_nb][4]: r_j - r_i (minimum image) and the CN mask
+                           // of each exact entry, written by the exact filter
+    // Verlet list (cutoff rc + skin, built at the reference positions)
     float4 *pos_ref;       // sorted positions at the last rebuild
-    unsigned short *vlist; // [max_vnb / 4][n][4]
+    int *vnbr;             // [n][max_vnb]
     int *vnn;              // [n]
+    int *vnh;              // [n] Verlet entries with j > i (stored first)
     int max_vnb;
+    // mirror slots: where the pair force of i's entry j > i goes in j's row,
+    // without searching j's row in the force pass
+    int mirror;                // 1: in use (n < 2^23, rows of at most 255 entries)
+    unsigned char *vmirror;    // [n][max_vnb]: for j = vnbr[i][k] > i, i's position in j's Verlet row
+    unsigned short *vround;    // [n][vround_stride]: per filter round r (Verlet entries 8r .. 8r + 7),
+                               // the exact entries before it | the round's exact bits << 8
+    int vround_stride;
+    int *rows_fresh;           // 1 from a rebuild until the CV pass after the next filter
     int *flag;             // 1: rebuild the cell order and Verlet list this step
     float disp_thr2;       // (skin / 2)^2 with margin: rebuild above it
     float skin_eff;        // skin with margin
@@ -100,18 +108,8 @@ struct Sys {
     float rv2;             // (rc + skin)^2 with margin: Verlet cutoff
     int always_rebuild;    // skin == 0
     unsigned long long *rebuilds;  // number of rebuilds done
-    // per-atom records [n][16] in the pair precision:
-    //   rq: q_m (0..12), W (13), CN (14)
-    //   rb: b_m (0..12), beta (13), qbar6 (14)
-    //   rh: h_m (0..12), gamma (13)
-    // 4-vectors [n][4]: fc = FC (the CN force sum, which needs no dV/ds) and
-    // wc its virial sum (with the virial only); and per exact entry, in the
-    // rows' quad-major order, the switch weight w_ij (wl) and the two halves
-    // of the cross term c_ij = b_i.q_j + b_j.q_i: e_ij = b_i.q_j (eq) and
-    // d_ij = q_i.b_j (dq)
-    void *rq, *rb, *rh;
-    void *fc, *wc;
-    void *wl, *eq, *dq;
+    void *cn, *W, *qb6;    // real-typed per-atom scalars
+    void *q, *b, *h;       // real-typed per-atom records [n][16]: q_m; b_m, beta; h_m, gamma
     double *part;          // per-block FP64 partial sums, slots of part_stride
     int part_stride;
     unsigned *ticket;      // completion counters of the last-block reductions
@@ -213,10 +211,13 @@ enum GridKind : int {
     GK_ATOM256_CAP,    // rebuild: binning and scatter
     GK_SCAN_TILES,     // rebuild: cell scan
     GK_CELL128_CAP,    // rebuild: cell sort
+    GK_GROUPS_CAP,     // rebuild: Verlet rows
     GK_ONE,            // one block per system
-    GK_TILES,          // one block per tile; a batch tile setting caps it
-    GK_TILES_CAP,      // rebuild: Verlet rows (tiles, grid capped)
-    GK_TILES_SUM,      // one block per tile (the pass holding the CV sums: never capped)
+    GK_GROUPS,         // one block per 16 atoms (lane-group kernels); a batch tile caps it
+    GK_CV,             // the Q6 pass with the CV sums: persistent, by N only
+    GK_ATOM32,         // one block per 32 atoms (four-lane adjoint); a batch tile caps it
+    GK_ATOM128,        // one block per 128 atoms (pair-parallel force); a batch tile caps it
+    GK_SUM,            // the CV sums: blocks by N only
     GK_HILLS,          // hill kernel, evaluation
     GK_DEPOSIT,        // hill kernel, deposit (systems that deposit)
     kGridKinds
@@ -224,40 +225,32 @@ enum GridKind : int {
 
 // Block count of one system for a grid kind (host side; shared by the
 // single-system launches and the batch tables).  persist_cap > 0 caps the
-// tile grids that carry no sum (a batch tile setting), 0 keeps the default.
+// lane-group grids (a batch tile setting), 0 keeps the default.
 int grid_blocks(const Sys &s, int kind, int persist_cap);
-
-// The per-atom passes of a step on spatial tiles (k_cv.cu).
-enum Pass : int {
-    kPassFwd = 0,   // exact rows (+ CV forward with flag): a3-a4
-    kPassAvg,       // Q6 average and the CV sums: a5
-    kPassAdj,       // adjoint: a7
-    kPassForce,     // forces: a8
-    kPassForceCn,   // forces without a Q6 CV
-    kNumPasses
-};
-constexpr int kMaxTileSmem = 224 * 1024;  // dynamic shared memory limit of a pass
-// Staged atoms per tile kept in shared memory (a tile with its one-cell
-// shell holds about 1,000 atoms at the workloads' densities): in FP32 two
-// blocks of every pass fit on an SM.
-constexpr int kStageCapF32 = 1216;
-constexpr int kStageCapF64 = 1216;
-int tile_smem(const Sys &s, int pass);   // dynamic shared memory of a pass
-int pass_blocks(const Sys &s, int pass); // single-system grid of a pass
-void launch_tile_pass(const Sys &s, int pass, int flag, cudaStream_t st);
-void launch_batch_pass(const BatchView &v, int total, int pass, int fp64, int flag, int vir, int smem,
-                       cudaStream_t st);
 
 // Batched stage launches (one launch each over every system of the view).
 void launch_batch_gather(const BatchView &v, int total, cudaStream_t st);
-void launch_batch_rebuild(const BatchView *rows, const int *totals, int verlet_smem, cudaStream_t st);
+void launch_batch_rebuild(const BatchView *rows, const int *totals, cudaStream_t st);
+void launch_batch_cv(const BatchView &groups, int group_total, const BatchView &cv, int cv_total,
+                     const BatchView &sums, int sum_total, int fp64, int ncv, cudaStream_t st);
+void launch_cv_sum(const Sys &s, int fp64, cudaStream_t st);
 void launch_batch_bias(const BatchView &v, int total, int deposit, cudaStream_t st);
+// part 0: adjoint, pair forces and gather; 1: the adjoint only; 2: the rest
+void launch_batch_force(const BatchView &groups, int group_total, const BatchView &adj, int adj_total,
+                        const BatchView &pairs, int pair_total, int fp64, int ncv, int virial, cudaStream_t st,
+                        int part = 0);
 void launch_batch_collect(const BatchView &v, double *out, cudaStream_t st);
 
 // Launch entry points (stream-ordered, no host synchronisation).
 void launch_gather_check(const Sys &s, cudaStream_t st);
 void launch_rebuild(const Sys &s, cudaStream_t st);  // kernels early-exit unless *flag
+void launch_filter(const Sys &s, int fp64, cudaStream_t st);
+void launch_cv_fwd(const Sys &s, int fp64, int fused_filter, cudaStream_t st);
+void launch_cv_avg(const Sys &s, int fp64, cudaStream_t st);
 void launch_bias(const Sys &s, int K, const double *s_dev, double *out_dev, int deposit, cudaStream_t st);
+void launch_adjoint(const Sys &s, int fp64, cudaStream_t st);
+void launch_force_pairs(const Sys &s, int fp64, double scale, cudaStream_t st);  // + virial if s.virial
+void launch_force_gather(const Sys &s, int fp64, float *F, int accumulate, cudaStream_t st);
 void configure_kernels();
 void launch_grid_fold(const Sys &s, int K, cudaStream_t st);
 void launch_nn_stats(const Sys &s, unsigned long long *sum, int *mx, cudaStream_t st);
@@ -508,6 +501,66 @@ __device__ __forceinline__ void grid_value(const Sys &s, double x0, double x1, d
 }
 
 
+// ------------------------------------------------------------ lane groups
+// Per-atom kernels give one atom a group of kG lanes; lane l handles the
+// atom's neighbours l, l + kG, ... so all its neighbour loads are in flight
+// together.
+constexpr int kG = 8;
+constexpr int kAtomsPerBlock = kBlockAtoms / kG;
+
+// Grid of every lane-group kernel; the FP64 partial-sum slots are sized from
+// it, so launches and allocations can never disagree.
+__host__ __device__ inline int group_grid(int n) { return (n + kAtomsPerBlock - 1) / kAtomsPerBlock; }
+
+// Without a Q6 pass the CN sum runs in its own kernel: kSumThreads threads
+// per block, one block per kSumAtoms atoms (at most kMaxBiasBlocks blocks).
+constexpr int kSumThreads = 256;
+constexpr int kSumAtoms = 2048;
+__host__ __device__ inline int sum_blocks(int n)
+{
+    const int b = (n + kSumAtoms - 1) / kSumAtoms;
+    return b < 1 ? 1 : (b > kMaxBiasBlocks ? kMaxBiasBlocks : b);
+}
+
+// Persistent grids (the CV kernels, and the capped rebuild kernels) have at
+// most kPersistBlocks blocks, walking their work grid-stride.
+constexpr int kPersistBlocks = 152 * 16;
+
+// The it-th work item (atom group or chunk) of block b of nb: items b,
+// b + nb, b + 2 nb, ...  The items of one sweep form one compact window of
+// the Morton order, so the records they gather stay in L2.  (Mapping the
+// blocks that share an SM to consecutive items, for L1 reuse, measured
+// slower: the gather kernels lost more to L2 misses than they won in L1.)
+__device__ __forceinline__ int work_item(Blk k, int it) { return k.b + it * k.nb; }
+
+__host__ __device__ inline int persist_grid(int n)
+{
+    const int g = group_grid(n);
+    return g < kPersistBlocks ? g : kPersistBlocks;
+}
+
+struct AtomLane {
+    int i;    // atom (sorted index), may be >= n for idle groups
+    int l;    // lane within the group
+    bool ok;  // i < n
+};
+
+__device__ __forceinline__ AtomLane atom_lane_at(const Sys &s, int blk)
+{
+    AtomLane a;
+    a.i = blk * kAtomsPerBlock + (threadIdx.x / kG);
+    a.l = threadIdx.x & (kG - 1);
+    a.ok = a.i < s.n;
+    return a;
+}
+
+
+__device__ __forceinline__ unsigned group_mask_bits(unsigned ballot)
+{
+    const int base = (threadIdx.x & 31) & ~(kG - 1);
+    return (ballot >> base) & ((1u << kG) - 1u);
+}
+
 // Exact FP64 pair test: r^2 = (dx*dx + dy*dy) + dz*dz < rc^2 on the
 // minimum-image displacement, no contraction.  Kept out of line and given
 // plain values (no reference to the kernel's descriptor): it runs only for
@@ -549,6 +602,190 @@ __device__ __forceinline__ bool pair_in(const Sys &s, float4 pi, float4 pj, cons
     if (r2 < s.rc2_lo) return true;
     if (r2 > s.rc2_hi) return false;
     return pair_exact(s, pi, pj);
+}
+
+// The geometry of an exact entry, cached by the filter so the CV and force
+// passes read one contiguous record per entry instead of gathering the
+// neighbour's position again: r_j - r_i, and in the fourth slot a tag
+// (carried through float registers unchanged): the bits of j, the CN mask in
+// bit 31, and with mirror slots, for an entry j > i, i's position in j's
+// Verlet row in bits 23..30.  The force pass reads it for the last time
+// (kLast: an evict-first load, so the stream does not push the gathered
+// per-atom records out of L2).
+constexpr unsigned kCnBit = 0x80000000u;
+constexpr int kMirrorShift = 23;
+constexpr unsigned kMirrorJ = (1u << kMirrorShift) - 1u;
+
+__device__ __forceinline__ unsigned make_tag(const Sys &s, int j, float4 pi, float4 pj, unsigned vm)
+{
+    return (unsigned)j | (vm << kMirrorShift) | ((!s.cn_unlike || pj.w != pi.w) ? kCnBit : 0u);
+}
+
+template <typename real>
+__device__ __forceinline__ void store_geo(const Sys &s, size_t slot, const Vec3<float> &df, float4 pi, float4 pj,
+                                          int j, unsigned vm);
+template <>
+__device__ __forceinline__ void store_geo<float>(const Sys &s, size_t slot, const Vec3<float> &df, float4 pi,
+                                                 float4 pj, int j, unsigned vm)
+{
+    const unsigned tag = make_tag(s, j, pi, pj, vm);
+    reinterpret_cast<float4 *>(s.geo)[slot] = make_float4(df.x, df.y, df.z, __uint_as_float(tag));
+}
+template <>
+__device__ __forceinline__ void store_geo<double>(const Sys &s, size_t slot, const Vec3<float> &, float4 pi,
+                                                  float4 pj, int j, unsigned vm)
+{
+    const Vec3<double> d = displacement<double>(s, pi, pj);
+    const unsigned tag = make_tag(s, j, pi, pj, vm);
+    double2 *g = reinterpret_cast<double2 *>(s.geo) + 2 * slot;
+    g[0] = make_double2(d.x, d.y);
+    g[1] = make_double2(d.z, __longlong_as_double((long long)tag));
+}
+
+// j, the CN mask and the mirror position (0 without mirror slots) of a tag.
+__device__ __forceinline__ void untag(const Sys &s, unsigned tag, int &j, bool &cn, unsigned &vm)
+{
+    j = (int)(tag & (s.mirror ? kMirrorJ : ~kCnBit));
+    cn = (tag & kCnBit) != 0u;
+    vm = s.mirror ? (tag & ~kCnBit) >> kMirrorShift : 0u;
+}
+
+template <typename real, bool kLast = false>
+__device__ __forceinline__ void load_geo(const Sys &s, size_t slot, Vec3<real> &d, bool &cn, int &j, unsigned &vm);
+template <>
+__device__ __forceinline__ void load_geo<float, false>(const Sys &s, size_t slot, Vec3<float> &d, bool &cn, int &j,
+                                                       unsigned &vm)
+{
+    const float4 g = reinterpret_cast<const float4 *>(s.geo)[slot];
+    d.x = g.x;
+    d.y = g.y;
+    d.z = g.z;
+    untag(s, __float_as_uint(g.w), j, cn, vm);
+}
+template <>
+__device__ __forceinline__ void load_geo<float, true>(const Sys &s, size_t slot, Vec3<float> &d, bool &cn, int &j,
+                                                      unsigned &vm)
+{
+    const float4 g = __ldcs(reinterpret_cast<const float4 *>(s.geo) + slot);
+    d.x = g.x;
+    d.y = g.y;
+    d.z = g.z;
+    untag(s, __float_as_uint(g.w), j, cn, vm);
+}
+template <>
+__device__ __forceinline__ void load_geo<double, true>(const Sys &s, size_t slot, Vec3<double> &d, bool &cn, int &j,
+                                                       unsigned &vm)
+{
+    const double2 *g = reinterpret_cast<const double2 *>(s.geo) + 2 * slot;
+    const double2 a = __ldcs(g), b = __ldcs(g + 1);
+    d.x = a.x;
+    d.y = a.y;
+    d.z = b.x;
+    untag(s, (unsigned)__double_as_longlong(b.y), j, cn, vm);
+}
+template <>
+__device__ __forceinline__ void load_geo<double, false>(const Sys &s, size_t slot, Vec3<double> &d, bool &cn, int &j,
+                                                        unsigned &vm)
+{
+    const double2 *g = reinterpret_cast<const double2 *>(s.geo) + 2 * slot;
+    const double2 a = g[0], b = g[1];
+    d.x = a.x;
+    d.y = a.y;
+    d.z = b.x;
+    untag(s, (unsigned)__double_as_longlong(b.y), j, cn, vm);
+}
+
+// i's position in the j < i part of j's Verlet row (rows are symmetric: the
+// Verlet predicate is), four entries per load.  Run by the filter of the
+// first step on new rows only; the later steps read the stored result.
+__device__ __forceinline__ unsigned mirror_position(const Sys &s, int j, int i)
+{
+    const int *rj = s.vnbr + (size_t)j * s.max_vnb;
+    const int lo = s.vnh[j], hi = s.vnn[j];
+    for (int b = lo & ~3; b < hi; b += 4) {
+        const int4 v = *reinterpret_cast<const int4 *>(rj + b);
+        if (v.x == i && b >= lo) return (unsigned)b;
+        if (v.y == i && b + 1 >= lo && b + 1 < hi) return (unsigned)(b + 1);
+        if (v.z == i && b + 2 >= lo && b + 2 < hi) return (unsigned)(b + 2);
+        if (v.w == i && b + 3 >= lo && b + 3 < hi) return (unsigned)(b + 3);
+    }
+    set_err(s, kErrInternal);  // rows not symmetric: never expected
+    return 0u;
+}
+
+// One exact entry for the gather passes: the neighbour and the switch
+// weight side by side, read with one load.
+template <typename real>
+struct alignas(2 * sizeof(real)) JW {
+    int j;
+    real w;
+};
+
+template <typename real>
+__device__ __forceinline__ int filter_row(const Sys &s, const AtomLane &a)
+{
+    const int vn = a.ok ? s.vnn[a.i] : 0;
+    const int vh = a.ok ? s.vnh[a.i] : 0;
+    const float4 pi = a.ok ? s.pos_s[a.i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int *vrow = s.vnbr + (size_t)(a.ok ? a.i : 0) * s.max_vnb;
+    int *row = s.nbr + (size_t)(a.ok ? a.i : 0) * s.max_nb;
+    // mirror slots: each round records the exact entries before it and its
+    // exact bits, and each entry j > i carries i's Verlet position in j's
+    // row (searched once on new rows, stored for the steps after)
+    unsigned mw = 0u;
+    if (s.mirror) {
+        // new rows: find each j > i entry's mirror position once
+        if (*s.rows_fresh) {
+            for (int k = a.l; k < vh; k += kG)
+                s.vmirror[(size_t)a.i * s.max_vnb + k] = (unsigned char)mirror_position(s, vrow[k], a.i);
+            __syncwarp();
+        }
+        // the positions of the first four rounds in one sector: lane l holds
+        // bytes 4l .. 4l + 3 of the atom's row (rows are padded for it)
+        if (a.ok) mw = reinterpret_cast<const unsigned *>(s.vmirror + (size_t)a.i * s.max_vnb)[a.l];
+    }
+    int cnt = 0, nh = 0;
+    // one pass: the Verlet row already has its j > i part first, so accepted
+    // entries come out in the same order; nh counts those from that part
+    const int vmax = __reduce_max_sync(0xffffffffu, vn);
+    for (int base = 0; base < vmax; base += kG) {
+        const int k = base + a.l;
+        const bool valid = k < vn;
+        const int j = valid ? vrow[k] : 0;
+        // the mirror position of entry k: byte k & 3 of word k / 4 = 2 r + l / 4
+        // of the preloaded sector for the first four rounds r
+        unsigned vm = 0u;
+        if (s.mirror) {
+            unsigned w = 0u;
+            if (base < 4 * kG)  // warp-uniform
+                w = __shfl_sync(0xffffffffu, mw, ((threadIdx.x & 31) & ~(kG - 1)) + 2 * (base / kG) + (a.l >> 2));
+            if (valid && k < vh)
+                vm = base < 4 * kG ? (w >> (8 * (a.l & 3))) & 0xffu : (unsigned)s.vmirror[(size_t)a.i * s.max_vnb + k];
+        }
+        const float4 pj = valid ? s.pos_s[j] : pi;
+        const Vec3<float> d = displacement_warp(s, pi, pj);  // every lane: a warp vote inside
+        const bool in = valid && pair_in(s, pi, pj, d);
+        const unsigned ball = __ballot_sync(0xffffffffu, in);
+        const unsigned gm = group_mask_bits(ball);
+        const int below = min(max(vh - base, 0), kG);  // lanes of this round in the j > i part
+        const int at = cnt + __popc(gm & ((1u << a.l) - 1u));
+        // only rounds that reach the j < i part are ever looked up
+        if (s.mirror && a.l == 0 && base < vn && base + kG > vh)
+            s.vround[(size_t)a.i * s.vround_stride + base / kG] = (unsigned short)(min(cnt, 255) | (gm << 8));
+        if (in && at < s.max_nb) {
+            row[at] = j;
+            store_geo<real>(s, (size_t)a.i * s.max_nb + at, d, pi, pj, j, vm);
+        }
+        cnt += __popc(gm);
+        nh += __popc(gm & ((1u << below) - 1u));
+    }
+    if (a.ok && a.l == 0) {
+        if (cnt > s.max_nb) set_err(s, kErrCapacity);
+        s.nn[a.i] = min(cnt, s.max_nb);
+        s.nh[a.i] = min(nh, s.max_nb);
+    }
+    __syncwarp();
+    return min(cnt, s.max_nb);
 }
 
 }  // namespace metad

