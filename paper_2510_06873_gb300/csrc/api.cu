@@ -405,7 +405,7 @@ std::vector<double> pack_centres(const metad_ctx *c, const double *centers, int 
 
 struct Buffers {
     int *rank_xyz = nullptr, *xyz_rank = nullptr;
-    char *rb = nullptr, *wlb = nullptr, *pfb = nullptr, *geob = nullptr;
+    char *rb = nullptr, *wlb = nullptr, *pfb = nullptr, *geob = nullptr, *crossb = nullptr;
 };
 
 // Every device buffer of a context in one list: alloc(&ptr, count) allocates
@@ -440,6 +440,7 @@ metad_status state_buffers(metad_ctx *c, Buffers &b, Alloc &&alloc)
         (s = alloc(&y.nbr, (size_t)y.max_nb * n)) || (s = alloc(&y.nn, n)) || (s = alloc(&y.nh, n)) ||
         (s = alloc(&y.vnh, n)) || (s = alloc(&b.wlb, 2 * rs * (size_t)y.max_nb * n)) ||
         (s = alloc(&b.pfb, rs * 4 * (size_t)y.max_nb * n)) || (s = alloc(&b.geob, rs * 4 * (size_t)y.max_nb * n)) ||
+        (s = alloc(&b.crossb, c->p.n_cv == 2 ? rs * (size_t)y.max_nb * n : 1)) ||
         (s = alloc(&y.pos_ref, n)) ||
         (s = alloc(&y.vnbr, (size_t)y.max_vnb * n)) || (s = alloc(&y.vnn, n)) || (s = alloc(&y.flag, 1)) ||
         // the filter reads each row's first 32 bytes: rows shorter than that
@@ -636,6 +637,7 @@ metad_status metad_create(const metad_params *p, metad_ctx **out)
     y.qb6 = rb + rs * (3 * nq + 2 * (size_t)n);
     y.wl = wlb;
     y.pairF = pfb;
+    y.cross = bf.crossb;
     y.geo = bf.geob;
     y.rank_of_xyz = rank_xyz;
     y.xyz_of_rank = xyz_rank;

@@ -645,6 +645,21 @@ __device__ __forceinline__ real group4_sum(real v)
     return v;
 }
 
+// Reduce-scatter of four values over the four lanes of this thread's group:
+// lane l returns the group sum of v[l].  The shuffle masks name the group
+// alone, so groups of one warp may run different trip counts.
+template <typename real>
+__device__ __forceinline__ real group4_reduce_scatter(const real v[4], int l)
+{
+    const unsigned mask = 0xfu << (threadIdx.x & 28);
+    const bool hi2 = (l & 2) != 0, hi1 = (l & 1) != 0;
+    // lanes 2, 3 keep values 2, 3 and send 0, 1; lanes 0, 1 the reverse
+    const real a0 = (hi2 ? v[2] : v[0]) + __shfl_xor_sync(mask, hi2 ? v[0] : v[2], 2);
+    const real a1 = (hi2 ? v[3] : v[1]) + __shfl_xor_sync(mask, hi2 ? v[1] : v[3], 2);
+    // odd lanes keep the second of their pair, even lanes the first
+    return (hi1 ? a1 : a0) + __shfl_xor_sync(mask, hi1 ? a0 : a1, 1);
+}
+
 template <typename real>
 __device__ __forceinline__ void adjoint_group(const Sys &s, int g)
 {
@@ -653,18 +668,37 @@ __device__ __forceinline__ void adjoint_group(const Sys &s, int g)
     const bool ok = i < s.n;
     const real *bb = R<real>(s.b);
     real acc[4] = {real(0), real(0), real(0), real(0)};
+    real o[4] = {real(0), real(0), real(0), real(0)}, q[4] = {real(0), real(0), real(0), real(0)};
     if (ok) {
+        load4<real>(bb, i, l, o);
+        load4<real>(R<real>(s.q), i, l, q);
         const int nn = s.nn[i];
         const JW<real> *jwrow = reinterpret_cast<const JW<real> *>(s.wl) + (size_t)i * s.max_nb;
-#pragma unroll 4
-        for (int k = 0; k < nn; ++k) {
-            const JW<real> e = jwrow[k];
-            const int j = e.j;
-            const real w = e.w;
-            real x[4];
-            load4<real>(bb, j, l, x);
+        // with each gathered b_j also the half b_j.q_i of the pair's cross
+        // term b_i.q_j + b_j.q_i in ds2/dw (a8), stored per entry: the force
+        // pass adds the halves of entry ij and its mirror ji.  Entries go
+        // four at a time; a reduce-scatter over the group leaves entry
+        // k0 + l's sum in lane l, so the group stores 16 contiguous bytes.
+        real *crow = R<real>(s.cross) + (size_t)i * s.max_nb;
+        for (int k0 = 0; k0 < nn; k0 += 4) {
+            real p[4];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) acc[c] += w * x[c];
+            for (int u = 0; u < 4; ++u) {
+                p[u] = real(0);
+                if (k0 + u < nn) {
+                    const JW<real> e = jwrow[k0 + u];
+                    const real w = e.w;
+                    real x[4];
+                    load4<real>(bb, e.j, l, x);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        acc[c] += w * x[c];
+                        if (4 * l + c < kNY) p[u] += x[c] * q[c];
+                    }
+                }
+            }
+            const real t = group4_reduce_scatter<real>(p, l);
+            if (k0 + l < nn) crow[k0 + l] = t;
         }
     }
     real h[4] = {real(0), real(0), real(0), real(0)};
@@ -672,9 +706,6 @@ __device__ __forceinline__ void adjoint_group(const Sys &s, int g)
     if (ok) {
         const real W = R<real>(s.W)[i];
         const real inv_W = W > real(0) ? real(1) / W : real(0);
-        real o[4], q[4];
-        load4<real>(bb, i, l, o);
-        load4<real>(R<real>(s.q), i, l, q);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const int m = 4 * l + c;
@@ -755,29 +786,35 @@ __device__ __forceinline__ void pair_force(const Sys &s, int i, int k, real cn_f
     cached_geometry<real, true>(s, (size_t)i * s.max_nb + k, d, inv_r, w, dw, cn, j, vm);
     // the slot of i in j's exact row: with mirror slots, the exact entries
     // of j's Verlet row before i's position vm there (one 2 B load);
-    // otherwise a search of the j < i part of j's row
-    int kk = -1, nhj = 0, nnj = 0;
+    // otherwise a search of the j < i part [nh_j, nn_j) of j's row, four
+    // entries per load
+    int kk = -1;
     if (s.mirror) {
         const unsigned e = s.vround[(size_t)j * s.vround_stride + (vm >> 3)];
         kk = (int)(e & 0xffu) + __popc((e >> 8) & ((1u << (vm & 7u)) - 1u));
     } else {
-        nhj = s.nh[j];
-        nnj = s.nn[j];
+        const int nhj = s.nh[j], nnj = s.nn[j];
+        const int *rj = nbr_row(s, j);
+        for (int b = nhj & ~3; b < nnj && kk < 0; b += 4) {
+            const int4 v = *reinterpret_cast<const int4 *>(rj + b);
+            if (v.x == i && b >= nhj) kk = b;
+            else if (v.y == i && b + 1 >= nhj && b + 1 < nnj) kk = b + 1;
+            else if (v.z == i && b + 2 >= nhj && b + 2 < nnj) kk = b + 2;
+            else if (v.w == i && b + 3 >= nhj && b + 3 < nnj) kk = b + 3;
+        }
+    }
+    if (kk < 0 || kk >= s.max_nb) {
+        set_err(s, kErrInternal);  // rows not symmetric: never expected
+        return;
     }
     const real ux = d.x * inv_r, uy = d.y * inv_r, uz = d.z * inv_r;
     real radial = cn ? cn_fac * dw : real(0);
     real fx = real(0), fy = real(0), fz = real(0);
     if (s.ncv == 2) {
-        const real *hh = R<real>(s.h), *qq = R<real>(s.q), *qbb = R<real>(s.b);
-        // cross term b_i.q_j + b_j.q_i first, so the q and b records die early
-        real qi[kRec], qj[kRec], bi[kRec], bj[kRec];
-        load_rec<real>(qq, i, qi);
-        load_rec<real>(qq, j, qj);
-        load_rec<real>(qbb, i, bi);
-        load_rec<real>(qbb, j, bj);
-        real t = real(0);
-#pragma unroll
-        for (int m = 0; m < kNY; ++m) t += bi[m] * qj[m] + bj[m] * qi[m];
+        const real *hh = R<real>(s.h), *cc = R<real>(s.cross);
+        // cross term b_i.q_j + b_j.q_i: the halves the adjoint pass stored
+        // in entry ij (b_j.q_i) and in its mirror ji (b_i.q_j)
+        real t = cc[(size_t)i * s.max_nb + k] + cc[(size_t)j * s.max_nb + kk];
         real hi[kRec], hj[kRec];
         load_rec<real>(hh, i, hi);
         load_rec<real>(hh, j, hj);
@@ -807,20 +844,6 @@ __device__ __forceinline__ void pair_force(const Sys &s, int i, int k, real cn_f
     }
     real *pf = R<real>(s.pairF);
     store_pair_force<real>(pf + ((size_t)i * s.max_nb + k) * 4, fx, fy, fz);
-    // without mirror slots: position of i in the j < i part [nh_j, nn_j) of
-    // j's row, four entries per load
-    const int *rj = nbr_row(s, j);
-    for (int b = nhj & ~3; b < nnj && kk < 0; b += 4) {
-        const int4 v = *reinterpret_cast<const int4 *>(rj + b);
-        if (v.x == i && b >= nhj) kk = b;
-        else if (v.y == i && b + 1 >= nhj && b + 1 < nnj) kk = b + 1;
-        else if (v.z == i && b + 2 >= nhj && b + 2 < nnj) kk = b + 2;
-        else if (v.w == i && b + 3 >= nhj && b + 3 < nnj) kk = b + 3;
-    }
-    if (kk < 0 || kk >= s.max_nb) {
-        set_err(s, kErrInternal);  // rows not symmetric: never expected
-        return;
-    }
     store_pair_force<real>(pf + ((size_t)j * s.max_nb + kk) * 4, -fx, -fy, -fz);
 }
 

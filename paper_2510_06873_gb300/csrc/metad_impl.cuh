@@ -85,6 +85,7 @@ struct Sys {
     int *nh;               // [n] entries with j > i
     void *wl;              // JW<real> [n][max_nb]: neighbour and switch weight of each entry
     void *pairF;           // real [n][max_nb][4]: G_ij in i's entry of j, -G_ji in the others
+    void *cross;           // real [n][max_nb]: b_j.q_i of each exact entry (two CVs)
     void *geo;             // real [n][max_nb][4]: r_j - r_i (minimum image) and the CN mask
                            // of each exact entry, written by the exact filter
     // Verlet list (cutoff rc + skin, built at the reference positions)
