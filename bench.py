@@ -73,6 +73,9 @@ def parse():
     ap.add_argument("--hills", type=int, default=None, help="live hills (default: the workload's 20,000)")
     ap.add_argument("--hills-folded", type=int, default=None, help="hills folded into the grid (default 20,000)")
     ap.add_argument("--max-neighbors", type=int, default=64, help="per-atom neighbour-row capacity")
+    ap.add_argument("--drift-step", type=float, default=0.01,
+                    help="random-walk step (A per coordinate and frame) of the timed drifting trajectory")
+    ap.add_argument("--no-skin0", action="store_true", help="skip the rebuild-every-step (skin 0) measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-system batched comparison")
     ap.add_argument("--no-served", action="store_true", help="skip the served (continuous batching) trace")
     ap.add_argument("--no-small", action="store_true", help="skip the torsion / nearest-distance walker forms")
@@ -194,6 +197,33 @@ def max_over_ranks(x: float, device) -> float:
 def job_throughput(world_size: int, units_per_rank: int, steps: int, seconds: float) -> float:
     """Whole-job atom-steps/s: every replica's units over the slowest time."""
     return world_size * units_per_rank * steps / seconds
+
+
+def device_drift_frames(system, count, step_sigma, sigma, dev, seed):
+    """Frames 0 .. count-1 of synth.drift_trajectory's drifting trajectory
+    (per-atom random walk of step_sigma per coordinate and frame plus thermal
+    N(0, sigma^2), wrapped into the box in FP64 and rounded to float32),
+    generated on the device from torch's seeded generator so that a
+    1M-atom trajectory of a few hundred frames takes milliseconds, not the
+    minutes of the host generator: the same distribution, other draws.
+    Returns float32 [count, N, 4]."""
+    import torch
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    base = torch.from_numpy(system.base).to(dev)
+    b64 = base[:, :3].double()
+    L = torch.tensor(np.asarray(system.box, dtype=np.float64), device=dev)
+    out = torch.empty((count, system.n, 4), dtype=torch.float32, device=dev)
+    walk = torch.zeros_like(b64)
+    for f in range(count):
+        if f > 0:
+            walk += step_sigma * torch.randn(walk.shape, generator=g, device=dev, dtype=torch.float64)
+        x = b64 + walk + sigma * torch.randn(walk.shape, generator=g, device=dev, dtype=torch.float64)
+        w = x - L * torch.floor(x / L)
+        w32 = w.float()
+        out[f, :, :3] = torch.where(w32.double() >= L, torch.zeros_like(w32), w32)
+        out[f, :, 3] = base[:, 3]
+    return out
 
 
 def kbdt(mp):
@@ -381,28 +411,60 @@ def run_metad(args):
     pairs = entries / 2
     # kernels of this library launched before the timed region (for ncu -s)
     print(f"setup_launches={probe_launches + ctx.launch_count}", file=sys.stderr, flush=True)
-    # ---- timed region: CUDA events on the context stream, profile per stage
-    clocks = ClockSampler(local)
-    launches0 = ctx.launch_count
-    ctx.profile_begin(16 * args.steps + 64)
-    clocks.start()
-    time.sleep(0.3)
-    if ws > 1:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        one_step()
-    ev1.record(stream)
-    torch.cuda.synchronize(dev)
-    ms = ev0.elapsed_time(ev1)
-    if ws > 1:
-        dist.barrier()
-    clk = clocks.stop()
-    stages = ctx.profile_end()
-    launches = ctx.launch_count - launches0
-    ms = max_over_ranks(ms, dev)
+
+    def timed_region(c, step_fn, steps):
+        """CUDA events on the context stream around `steps` steps, per-stage
+        profile, clocks sampled during the region, launches and rebuilds."""
+        clocks = ClockSampler(local)
+        launches0, rebuilds0 = c.launch_count, c.rebuild_count
+        c.profile_begin(16 * steps + 64)
+        clocks.start()
+        time.sleep(0.3)
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(steps):
+            step_fn()
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        t_ms = ev0.elapsed_time(ev1)
+        if ws > 1:
+            dist.barrier()
+        clk_ = clocks.stop()
+        st = c.profile_end()
+        return max_over_ranks(t_ms, dev), st, c.launch_count - launches0, clk_, c.rebuild_count - rebuilds0
+
+    def stage_table(st, total_ms):
+        return {k: {"ms_per_launch": v[0] / v[1], "launches": v[1], "share": v[0] / max(total_ms, 1e-9)}
+                for k, v in st.items() if v[1] > 0}
+
+    # ---- static frames: independent thermal perturbations of one base
+    # (their spread stays inside half the skin: no rebuild in the region)
+    ms_s, stages_s, launches_s, clk_s, reb_s = timed_region(ctx, one_step, args.steps)
+    static_line = {"ms_per_step": ms_s / args.steps, "value": job_throughput(ws, n, args.steps, ms_s / 1e3),
+                   "rebuilds": reb_s, "gpu_launches": launches_s, "clocks": clk_s,
+                   "stages": stage_table(stages_s, ms_s),
+                   "frames": f"{nfr} resident frames base + N(0, 0.05^2), cycled"}
+    # ---- drifting trajectory (the headline): a per-atom random walk of
+    # args.drift_step A per coordinate and frame on top of the thermal noise,
+    # so the Verlet rows are rebuilt inside the region at an MD-like rate
+    # (the rebuild cost amortised into ms_per_step)
+    drift_count = max(3, args.warmup) + args.steps
+    drift = device_drift_frames(system, drift_count, args.drift_step, 0.05, dev, seed=20251006 + rank)
+    drift_no = 0
+
+    def drift_step():
+        nonlocal drift_no, frame_no
+        ctx.step(drift[drift_no], F, deposit=((frame_no + 1) % every == 0))
+        drift_no += 1
+        frame_no += 1
+
+    for _ in range(max(3, args.warmup)):
+        drift_step()
+    ms, stages, launches, clk, reb_d = timed_region(ctx, drift_step, args.steps)
+    drift = None  # release the trajectory's device memory
     value = job_throughput(ws, n, args.steps, ms / 1e3)
     # ---- dominant kernel roofline from the live per-stage events, against
     # the FP32 peak measured on this GPU (multiply-add chains, CUDA events)
@@ -452,8 +514,35 @@ def run_metad(args):
     graph_ms = max_over_ranks(g0.elapsed_time(g1), dev) / args.steps
     graph_line = {"ms_per_step": graph_ms, "value": job_throughput(ws, n, 1, graph_ms / 1e3), "steps": args.steps,
                   "note": "metad_step replayed from captured CUDA graphs, no per-stage events"}
-    stage_line = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1], "share": v[0] / max(ms, 1e-9)}
-                  for k, v in stages.items() if v[1] > 0}
+    stage_line = stage_table(stages, ms)
+    # ---- skin 0: the rows are rebuilt at every step (Verlet rows = exact
+    # rows), the same hills and grid; the full-rebuild cost is its
+    # "neighbors" stage
+    skin0 = None
+    if not args.no_skin0:
+        p0 = metad.params_for(n, system.box, n_cv=2, sigma=mp.sigma, grid=(cfgp["grid_n"], lo, hi),
+                              hill_capacity=cfgp["hills"] + 1024, stream=stream.cuda_stream,
+                              max_neighbors=args.max_neighbors, skin=0.0)
+        ctx0 = metad.Metad(p0)
+        ctx0.deposit_hills(cen[:K1], want_heights=False)
+        ctx0.fold_hills()
+        ctx0.deposit_hills(cen[K1:], want_heights=False)
+        k0 = [0]
+
+        def step0():
+            ctx0.step(frames[k0[0] % nfr], F)
+            k0[0] += 1
+
+        for _ in range(3):
+            step0()
+        steps0 = min(args.steps, 50)
+        ms0, st0, launches0, clk0, reb0 = timed_region(ctx0, step0, steps0)
+        ctx0.close()
+        nb0 = st0.get("neighbors", (0.0, 0))
+        skin0 = {"ms_per_step": ms0 / steps0, "value": job_throughput(ws, n, steps0, ms0 / 1e3), "steps": steps0,
+                 "rebuilds": reb0, "gpu_launches": launches0, "clocks": clk0, "stages": stage_table(st0, ms0),
+                 "ms_full_rebuild": nb0[0] / nb0[1] if nb0[1] else None,
+                 "note": "skin 0: cell binning, counting sort and rows rebuilt at every step"}
     # ---- end to end through the host-buffer entry point (pinned memory)
     e2e = None
     if args.e2e_steps > 0:
@@ -495,9 +584,13 @@ def run_metad(args):
                 "config": {"workload": WORKLOAD, "n_atoms": n, "unordered_pairs": int(pairs),
                            "max_neighbors_per_atom": max_nn, "live_hills_end": ctx.hill_count,
                            "precision": "FP32 pair arithmetic, FP64 CV reductions, hills and grid",
-                           "frames_resident": nfr, "parallelism": f"replica x{ws}" if ws > 1 else "single GPU",
-                           "l2": f"inputs larger than L2: {nfr} resident frames of {16 * n / 1e6:.0f} MB cycled "
-                                 f"({16 * n * nfr / 1e6:.0f} MB > 129 MB)"},
+                           "frames": f"drifting trajectory: per-atom random walk N(0, {args.drift_step}^2) A per "
+                                     f"coordinate and frame + thermal N(0, 0.05^2), {drift_count} frames resident, "
+                                     f"skin {args.skin} A (rebuilds amortised)",
+                           "frames_resident": drift_count, "skin": args.skin,
+                           "parallelism": f"replica x{ws}" if ws > 1 else "single GPU",
+                           "l2": f"inputs larger than L2: each step reads a new {16 * n / 1e6:.0f} MB frame "
+                                 f"({16 * n * drift_count / 1e6:.0f} MB resident > 129 MB)"},
                 "roofline": roof, "kernel_rooflines": per_kernel,
                 "step_roofline": {
                     "algorithmic_bytes": step_bytes, "bytes_per_atom": STEP_BYTES_PER_ATOM,
@@ -509,7 +602,8 @@ def run_metad(args):
                     "note": "algorithmic bytes = 160 B per atom-step (positions in, forces out, the "
                             "persisted neighbour list); measured DRAM bytes = the profiled per-kernel ncu "
                             "counters summed over the step's kernels (null unless every kernel has one)"},
-                "stages": stage_line, "graph_replay": graph_line, "gpu_launches": launches, "clocks": clk, "e2e": e2e,
+                "rebuilds": reb_d, "stages": stage_line, "static_frames": static_line, "skin0": skin0,
+                "graph_replay": graph_line, "gpu_launches": launches, "clocks": clk, "e2e": e2e,
                 "cpu_baseline": cpu, "errors_vs_oracle": errors,
                 **forms}
         print(json.dumps(line), flush=True)

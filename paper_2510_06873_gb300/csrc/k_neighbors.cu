@@ -242,19 +242,85 @@ __device__ __forceinline__ int wrap_cell(int c, int nc)
 __device__ __forceinline__ int axis_span(int nc) { return nc >= 3 ? 3 : nc; }
 __device__ __forceinline__ int axis_off(int nc, int idx) { return nc >= 3 ? idx - 1 : idx; }
 
-constexpr int kStencil = 27;
-constexpr int kVerletBatch = 4;  // candidate rounds whose loads are issued together
+// Verlet row of atom i: {j : r_ij^2 < (rc + skin)^2 (1 + 1e-4)} over the
+// 27 surrounding cells (each distinct cell once), entries with j > i first,
+// then j < i, each part in stencil-cell order (x fastest), atoms in cell
+// order.  One thread per atom, one pass over the cells: atoms are sorted by
+// cell rank, so j > i is the part test, and the j > i entries fill the row
+// from the front while the j < i ones fill it from the back; the back part is
+// then reversed in place and moved down behind the front part.
+// kImages (three or more cells along every axis): each stencil cell is a
+// distinct cell at one periodic image, so the displacement is
+// (r_j - r_i) + shift with the cell's image shift (0 or +-L per axis), and no
+// minimum-image test per candidate.  Both roundings are sign-symmetric, so
+// the pair's two directions give exactly opposite vectors and the rows stay
+// symmetric.  Otherwise the minimum image per candidate.  The 1e-4 margin on
+// the cutoff covers the rounding of either form (ulp(L) across the faces).
+template <bool kImages>
+__device__ __forceinline__ void verlet_row(const Sys &s, int i)
+{
+    const float4 pi = s.pos_s[i];
+    const int own = s.scell[i];
+    const int xyz = s.xyz_of_rank[own];
+    const int cx = xyz & 1023, cy = (xyz >> 10) & 1023, cz = xyz >> 20;
+    const int sx = axis_span(s.nc[0]), sy = axis_span(s.nc[1]), sz = axis_span(s.nc[2]);
+    const int cap = s.max_vnb;
+    int *vrow = s.vnbr + (size_t)i * cap;
+    int up = 0, dn = 0;  // entries kept with j > i (front), j < i (back)
+    bool over = false;   // more entries than the row holds
+    for (int oz = 0; oz < sz; ++oz) {
+        const int z = cz + axis_off(s.nc[2], oz);
+        const float hz = z < 0 ? -s.Lhi[2] : (z >= s.nc[2] ? s.Lhi[2] : 0.0f);
+        const int zr = wrap_cell(z, s.nc[2]) * s.nc[1];
+        for (int oy = 0; oy < sy; ++oy) {
+            const int y = cy + axis_off(s.nc[1], oy);
+            const float hy = y < 0 ? -s.Lhi[1] : (y >= s.nc[1] ? s.Lhi[1] : 0.0f);
+            const int yr = (zr + wrap_cell(y, s.nc[1])) * s.nc[0];
+            for (int ox = 0; ox < sx; ++ox) {
+                const int x = cx + axis_off(s.nc[0], ox);
+                const float hx = x < 0 ? -s.Lhi[0] : (x >= s.nc[0] ? s.Lhi[0] : 0.0f);
+                const int c = s.rank_of_xyz[yr + wrap_cell(x, s.nc[0])];
+                const int a = s.cell_start[c], e = s.cell_start[c + 1];
+#pragma unroll 4
+                for (int j = a; j < e; ++j) {
+                    const float4 pj = s.pos_s[j];
+                    Vec3<float> d;
+                    if (kImages) {
+                        d.x = (pj.x - pi.x) + hx;
+                        d.y = (pj.y - pi.y) + hy;
+                        d.z = (pj.z - pi.z) + hz;
+                    } else {
+                        d = displacement<float>(s, pi, pj);
+                    }
+                    if (j != i && fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z)) < s.rv2) {
+                        const bool fw = j > i;
+                        if (up + dn < cap) {
+                            vrow[fw ? up : cap - 1 - dn] = j;
+                            up += fw ? 1 : 0;
+                            dn += fw ? 0 : 1;
+                        } else {
+                            over = true;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    // the back part [cap - dn, cap) holds its first-found entry last: reverse
+    // it in place, then move it down behind the front part (a copy to lower
+    // addresses in increasing order never overwrites an unread entry)
+    for (int t = 0; t < dn / 2; ++t) {
+        const int u = vrow[cap - 1 - t], v = vrow[cap - dn + t];
+        vrow[cap - 1 - t] = v;
+        vrow[cap - dn + t] = u;
+    }
+    if (up + dn < cap)
+        for (int t = 0; t < dn; ++t) vrow[up + t] = vrow[cap - dn + t];
+    if (over) set_err(s, kErrCapacity);
+    s.vnn[i] = up + dn;
+    s.vnh[i] = up;
+}
 
-// Verlet rows {j : r_ij^2 < (rc + skin)^2 (1 + 1e-4)} over the 27 surrounding
-// cells (each distinct cell once): entries with j > i first, then j < i, in
-// stencil-cell order, atoms in cell order.  A group of kG lanes per atom.
-// Atoms are sorted by cell rank, so a cell ranked below the atom's own holds
-// only j < i and one ranked above only j > i: each part walks only its
-// cells (the own cell in both).  The group stages the part's cell starts
-// and the prefix of their counts in shared memory (the lanes look the cells
-// up in parallel); the candidates are then one flat range that the lanes
-// walk kG at a time, each lane finding its cell by advancing along the
-// prefix, so every position load is independent of the others and
 // End of a rebuild, run once by the last Verlet block to finish: the rows'
 // box becomes the reference, the rows are marked new, and the flag is
 // cleared for the next step (kept set when the skin is zero, so every step
@@ -273,121 +339,18 @@ __device__ __forceinline__ void finish_rebuild(const Sys &s, Blk k)
     *s.flag = s.always_rebuild ? 1 : 0;
 }
 
-// kVerletBatch rounds are loaded at once.  Ballot compaction keeps the
-// order.  Grid-stride over atom groups so an idle launch (no rebuild)
+// Grid-stride over tiles of blockDim atoms, so an idle launch (no rebuild)
 // retires at once.
 __device__ __forceinline__ void verlet(const Sys &s, Blk k)
 {
     if (!*s.flag) return;
-    __shared__ int sh_base[kAtomsPerBlock][kStencil];  // start - prefix: j = p + base
-    __shared__ int sh_pre[kAtomsPerBlock][kStencil + 1];
-    const int sx = axis_span(s.nc[0]), sy = axis_span(s.nc[1]), sz = axis_span(s.nc[2]);
-    const int nq = sx * sy * sz;
-    const int g = threadIdx.x / kG;
-    int *base = sh_base[g], *pre = sh_pre[g];
-    // lane l owns the stencil cells q = 4l .. 4l + 3 (in order), so the
-    // prefix of their counts is a local sum plus a scan over the lanes
-    constexpr int kPerLane = (kStencil + kG - 1) / kG;
-    static_assert(kPerLane * kG >= kStencil, "stencil cells per lane");
-    int qoff[kPerLane];
-#pragma unroll
-    for (int r = 0; r < kPerLane; ++r) {
-        const int q = (threadIdx.x & (kG - 1)) * kPerLane + r;
-        const int e = q % sx, b = (q / sx) % sy, c3 = q / (sx * sy);  // once per launch
-        qoff[r] = q < nq ? (axis_off(s.nc[0], e) + 1) | ((axis_off(s.nc[1], b) + 1) << 2) |
-                               ((axis_off(s.nc[2], c3) + 1) << 4)
-                         : -1;
-    }
-    const int groups = group_grid(s.n);
-    for (int it = 0, blk; (blk = work_item(k, it)) < groups; ++it) {
-        const AtomLane a = atom_lane_at(s, blk);
-        const int i = a.ok ? a.i : 0;
-        const float4 pi = s.pos_s[i];
-        const int own = s.scell[i];
-        const int xyz = s.xyz_of_rank[own];
-        const int cx = xyz & 1023, cy = (xyz >> 10) & 1023, cz = xyz >> 20;
-        int cell_r[kPerLane], start_r[kPerLane], count_r[kPerLane];
-#pragma unroll
-        for (int r = 0; r < kPerLane; ++r) {
-            cell_r[r] = -1;
-            start_r[r] = count_r[r] = 0;
-            if (qoff[r] >= 0) {
-                const int o = qoff[r];
-                const int c = s.rank_of_xyz[(wrap_cell(cz + ((o >> 4) & 3) - 1, s.nc[2]) * s.nc[1] +
-                                             wrap_cell(cy + ((o >> 2) & 3) - 1, s.nc[1])) * s.nc[0] +
-                                            wrap_cell(cx + (o & 3) - 1, s.nc[0])];
-                cell_r[r] = c;
-                start_r[r] = s.cell_start[c];
-                count_r[r] = s.cell_start[c + 1] - start_r[r];
-            }
-        }
-        int *vrow = s.vnbr + (size_t)i * s.max_vnb;
-        int cnt = 0, nup = 0;
-#pragma unroll 1
-        for (int part = 0; part < 2; ++part) {
-            // the part's cells: ranks >= own (j > i), then <= own (j < i)
-            int loc[kPerLane], tot = 0;
-#pragma unroll
-            for (int r = 0; r < kPerLane; ++r) {
-                const bool mine = cell_r[r] >= 0 && (part == 0 ? cell_r[r] >= own : cell_r[r] <= own);
-                loc[r] = tot;
-                tot += mine ? count_r[r] : 0;
-            }
-            int incl = tot;  // inclusive scan of the lane totals within the group
-#pragma unroll
-            for (int o = 1; o < kG; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, incl, o, kG);
-                if (a.l >= o) incl += y;
-            }
-            const int excl = incl - tot;
-            __syncwarp();  // the previous part's table is no longer read
-#pragma unroll
-            for (int r = 0; r < kPerLane; ++r) {
-                const int q = a.l * kPerLane + r;
-                if (q < nq) {
-                    pre[q] = excl + loc[r];
-                    base[q] = start_r[r] - (excl + loc[r]);
-                }
-            }
-            if (a.l == kG - 1) pre[nq] = incl;
-            __syncwarp();
-            const int T = a.ok ? pre[nq] : 0;
-            const int tmax = __reduce_max_sync(0xffffffffu, T);
-            int q = 0;
-            for (int base0 = 0; base0 < tmax; base0 += kG * kVerletBatch) {
-                int jb[kVerletBatch];
-                float4 pb[kVerletBatch];
-#pragma unroll
-                for (int u = 0; u < kVerletBatch; ++u) {
-                    const int p = base0 + u * kG + a.l;
-                    jb[u] = -1;
-                    if (p < T) {
-                        while (p >= pre[q + 1]) ++q;
-                        jb[u] = p + base[q];
-                        pb[u] = s.pos_s[jb[u]];
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < kVerletBatch; ++u) {
-                    if (base0 + u * kG >= tmax) break;  // warp-uniform
-                    const int j = jb[u];
-                    bool in = false;
-                    if (j >= 0 && (part == 0 ? j > i : j < i)) {
-                        Vec3<float> d = displacement<float>(s, pi, pb[u]);
-                        in = fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z)) < s.rv2;
-                    }
-                    const unsigned gm = group_mask_bits(__ballot_sync(0xffffffffu, in));
-                    const int at = cnt + __popc(gm & ((1u << a.l) - 1u));
-                    if (in && at < s.max_vnb) vrow[at] = j;
-                    cnt += __popc(gm);
-                }
-            }
-            if (part == 0) nup = cnt;
-        }
-        if (a.ok && a.l == 0) {
-            if (cnt > s.max_vnb) set_err(s, kErrCapacity);
-            s.vnn[i] = min(cnt, s.max_vnb);
-            s.vnh[i] = min(nup, s.max_vnb);
+    const bool images = s.nc[0] >= 3 && s.nc[1] >= 3 && s.nc[2] >= 3;
+    const int tiles = (s.n + (int)blockDim.x - 1) / (int)blockDim.x;
+    for (int it = 0, blk; (blk = work_item(k, it)) < tiles; ++it) {
+        const int i = blk * (int)blockDim.x + (int)threadIdx.x;
+        if (i < s.n) {
+            if (images) verlet_row<true>(s, i);
+            else verlet_row<false>(s, i);
         }
     }
     finish_rebuild(s, k);

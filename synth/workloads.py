@@ -233,6 +233,25 @@ def perturbed_frame(system: System, frame: int, sigma: float = 0.05) -> np.ndarr
     return out
 
 
+def drift_trajectory(system: System, count: int, step_sigma: float = 0.01, sigma: float = 0.05):
+    """Frames 0 .. count-1 of a drifting trajectory, in order: frame f =
+    wrap(base + W_f + eps_f), where W_f = sum_{t=1..f} xi_t is a per-atom
+    random walk (xi_t ~ N(0, step_sigma^2) iid per coordinate and frame,
+    W_0 = 0) and eps_f the thermal noise of perturbed_frame (so frame 0 is
+    perturbed_frame(system, 0)).  Atoms leave their neighbour shells at a
+    molecular-dynamics-like rate, so a Verlet list is rebuilt every few tens
+    of frames.  Yields float32 [N, 4] arrays."""
+    walk = np.zeros((system.n, 3))
+    for f in range(count):
+        if f > 0:
+            walk += rng(system.cfg, system.sys, 7, f).normal(0.0, step_sigma, size=(system.n, 3))
+        eps = rng(system.cfg, system.sys, 1, f).normal(0.0, sigma, size=(system.n, 3))
+        out = np.empty_like(system.base)
+        out[:, :3] = wrap_to_box(system.base[:, :3].astype(np.float64) + walk + eps, system.box)
+        out[:, 3] = system.base[:, 3]
+        yield out
+
+
 def hill_centres(cfg: int, sys: int, centre, sigma, count: int, half_width_sigmas: float = 10.0) -> np.ndarray:
     """Hill centres uniform in prod_d [centre_d - 10 sigma_d, centre_d + 10 sigma_d]."""
     centre = np.atleast_1d(np.asarray(centre, dtype=np.float64))

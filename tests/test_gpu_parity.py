@@ -134,6 +134,37 @@ def test_verlet_reuse_and_rebuild_stay_exact(dev, skin):
         assert ctx.rebuild_count == expect_rebuilds[k], (k, ctx.rebuild_count)
 
 
+def test_drifting_trajectory_rebuilds_and_stays_exact(dev):
+    """Whole steps along a drifting trajectory (random walk of 0.05 A per
+    coordinate and frame on the thermal noise): the rows are rebuilt inside
+    the run, and at sampled frames, rebuild or reuse, the neighbour set is
+    the definition's bit for bit and the CVs, bias and forces match the
+    oracle's."""
+    system = synth.wurtzite_system(20000, cfg=95)
+    mp = synth.MethodParams(n_cv=2, sigma=(0.05, 0.02))
+    c, _ = setup_hills(system, mp, 300, cfg=95)
+    ctx = make_ctx(dev, system, mp)
+    ctx.deposit_hills(c)
+    w = oracle.deposit_sequence(c, mp.sigma, mp.w0, kbdt(mp))
+    p = oracle.params_from(mp, system.box)
+    F = torch.zeros((system.n, 3), dtype=torch.float32, device=dev)
+    checked = []
+    for f, frame in enumerate(synth.drift_trajectory(system, 36, step_sigma=0.05)):
+        ctx.step(torch.from_numpy(frame).to(dev), F)
+        if f % 7 == 6:
+            assert np.array_equal(ctx.export_neighbors(), oracle.pairs_cells(frame, system.box, RC)), f
+            s, V, dV = ctx.read_results()
+            ref = oracle.step(frame, p, c, w, mp.sigma)
+            check_cv(s, ref["s"])
+            check_bias(V, dV, ref["V"], ref["dV"], mp)
+            check_forces(F.cpu().numpy().astype(np.float64), ref["F"])
+            checked.append(ctx.rebuild_count)
+    # the largest displacement since the last rebuild passes skin/2 = 0.5 A
+    # every few frames at this step: several rebuilds, rows reused between
+    assert 3 <= ctx.rebuild_count < 36, ctx.rebuild_count
+    assert len(set(checked)) > 1
+
+
 # ------------------------------------------------------------------ config 1 (FP64)
 def test_config1_fp64_frames(dev):
     system = synth.config1_system()
