@@ -242,83 +242,194 @@ __device__ __forceinline__ int wrap_cell(int c, int nc)
 __device__ __forceinline__ int axis_span(int nc) { return nc >= 3 ? 3 : nc; }
 __device__ __forceinline__ int axis_off(int nc, int idx) { return nc >= 3 ? idx - 1 : idx; }
 
-// Verlet row of atom i: {j : r_ij^2 < (rc + skin)^2 (1 + 1e-4)} over the
-// 27 surrounding cells (each distinct cell once), entries with j > i first,
-// then j < i, each part in stencil-cell order (x fastest), atoms in cell
-// order.  One thread per atom, one pass over the cells: atoms are sorted by
-// cell rank, so j > i is the part test, and the j > i entries fill the row
-// from the front while the j < i ones fill it from the back; the back part is
-// then reversed in place and moved down behind the front part.
-// kImages (three or more cells along every axis): each stencil cell is a
-// distinct cell at one periodic image, so the displacement is
-// (r_j - r_i) + shift with the cell's image shift (0 or +-L per axis), and no
-// minimum-image test per candidate.  Both roundings are sign-symmetric, so
-// the pair's two directions give exactly opposite vectors and the rows stay
-// symmetric.  Otherwise the minimum image per candidate.  The 1e-4 margin on
-// the cutoff covers the rounding of either form (ulp(L) across the faces).
-template <bool kImages>
-__device__ __forceinline__ void verlet_row(const Sys &s, int i)
+// Verlet rows {j : r_ij^2 < (rc + skin)^2 (1 + 1e-4)} over the 27 cells
+// around each atom's own (each distinct cell once): entries with j > i
+// first, then j < i, each part in stencil-cell order (x fastest), atoms in
+// cell order.  Atoms are sorted by cell rank, so a cell ranked above the
+// atom's own holds only j > i and one ranked below only j < i.
+//
+// One warp per cell A at a time.  The candidates of A's atoms are the same
+// list: the part-0 cells (rank >= A's) then the part-1 cells (rank <= A's),
+// each in stencil order, A itself in both.  The warp stages that list in
+// shared memory with coalesced loads (position, index, stencil cell), then
+// sweeps its 32 lanes over it for each atom of A in turn, compacting the
+// accepted entries with a ballot: the row comes out in its final order, with
+// no per-lane cell search and no divergence between lanes.  A list longer
+// than the buffer is staged and swept in chunks, per atom.
+//
+// Displacements: with three or more cells along every axis each stencil cell
+// is a distinct cell at one periodic image, and d = (r_j - r_i) + shift with
+// the cell's image shift (0 or +-L per axis): no minimum-image test per
+// candidate, and since both roundings are sign-symmetric the two directions
+// of a pair give exactly opposite vectors, so the rows stay symmetric.  With
+// fewer cells along an axis, the minimum image per candidate.  The 1e-4
+// margin on the cutoff covers the rounding of either form.
+constexpr int kStencil = 27;
+constexpr int kVerletWarps = kBlockAtoms / 32;
+constexpr int kCandBuf = 256;  // staged candidates per warp
+
+struct VerletWarpSmem {
+    float4 pos[kCandBuf];      // candidate position, index bits in w
+    unsigned char q[kCandBuf]; // candidate's stencil cell
+    float4 shift[kStencil];    // image shift of each stencil cell
+    int start[kStencil];       // first atom of each stencil cell
+    int off[2][kStencil];      // offset of the cell's segment in part 0 / 1 (-1: not in it)
+    int cnt[kStencil];         // atoms in the cell
+};
+
+// Copy the candidates [k0, k0 + len) of the list into the buffer: lane q
+// copies its stencil cell's segments (in part 0, in part 1), so the warp's
+// loads are all independent of one another.
+__device__ __forceinline__ void verlet_stage(const Sys &s, VerletWarpSmem &w, int nq, int k0, int len, int lane)
 {
-    const float4 pi = s.pos_s[i];
-    const int own = s.scell[i];
-    const int xyz = s.xyz_of_rank[own];
-    const int cx = xyz & 1023, cy = (xyz >> 10) & 1023, cz = xyz >> 20;
-    const int sx = axis_span(s.nc[0]), sy = axis_span(s.nc[1]), sz = axis_span(s.nc[2]);
-    const int cap = s.max_vnb;
-    int *vrow = s.vnbr + (size_t)i * cap;
-    int up = 0, dn = 0;  // entries kept with j > i (front), j < i (back)
-    bool over = false;   // more entries than the row holds
-    for (int oz = 0; oz < sz; ++oz) {
-        const int z = cz + axis_off(s.nc[2], oz);
-        const float hz = z < 0 ? -s.Lhi[2] : (z >= s.nc[2] ? s.Lhi[2] : 0.0f);
-        const int zr = wrap_cell(z, s.nc[2]) * s.nc[1];
-        for (int oy = 0; oy < sy; ++oy) {
-            const int y = cy + axis_off(s.nc[1], oy);
-            const float hy = y < 0 ? -s.Lhi[1] : (y >= s.nc[1] ? s.Lhi[1] : 0.0f);
-            const int yr = (zr + wrap_cell(y, s.nc[1])) * s.nc[0];
-            for (int ox = 0; ox < sx; ++ox) {
-                const int x = cx + axis_off(s.nc[0], ox);
-                const float hx = x < 0 ? -s.Lhi[0] : (x >= s.nc[0] ? s.Lhi[0] : 0.0f);
-                const int c = s.rank_of_xyz[yr + wrap_cell(x, s.nc[0])];
-                const int a = s.cell_start[c], e = s.cell_start[c + 1];
+    if (lane < nq) {
+        const int st = w.start[lane], n = w.cnt[lane];
+#pragma unroll
+        for (int part = 0; part < 2; ++part) {
+            const int o = w.off[part][lane];
+            if (o < 0) continue;
+            const int lo = max(o, k0), hi = min(o + n, k0 + len);
 #pragma unroll 4
-                for (int j = a; j < e; ++j) {
-                    const float4 pj = s.pos_s[j];
-                    Vec3<float> d;
-                    if (kImages) {
-                        d.x = (pj.x - pi.x) + hx;
-                        d.y = (pj.y - pi.y) + hy;
-                        d.z = (pj.z - pi.z) + hz;
-                    } else {
-                        d = displacement<float>(s, pi, pj);
-                    }
-                    if (j != i && fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z)) < s.rv2) {
-                        const bool fw = j > i;
-                        if (up + dn < cap) {
-                            vrow[fw ? up : cap - 1 - dn] = j;
-                            up += fw ? 1 : 0;
-                            dn += fw ? 0 : 1;
-                        } else {
-                            over = true;
-                        }
-                    }
-                }
+            for (int t = lo; t < hi; ++t) {
+                const int j = st + (t - o);
+                float4 pj = s.pos_s[j];
+                pj.w = __int_as_float(j);
+                w.pos[t - k0] = pj;
+                w.q[t - k0] = (unsigned char)lane;
             }
         }
     }
-    // the back part [cap - dn, cap) holds its first-found entry last: reverse
-    // it in place, then move it down behind the front part (a copy to lower
-    // addresses in increasing order never overwrites an unread entry)
-    for (int t = 0; t < dn / 2; ++t) {
-        const int u = vrow[cap - 1 - t], v = vrow[cap - dn + t];
-        vrow[cap - 1 - t] = v;
-        vrow[cap - dn + t] = u;
+    __syncwarp();
+}
+
+// Sweep atom i over the staged candidates [t0, t1) of the buffer, all in one
+// part (kUp: part 0, j > i; else part 1, j < i), appending to its row.
+// kShift: some stencil cell of this one is a periodic image (a cell on the
+// box faces); interior cells need no shift.
+template <bool kImages, bool kShift, bool kUp>
+__device__ __forceinline__ bool verlet_test(const Sys &s, const VerletWarpSmem &w, int i, float4 pi, int t, int t1,
+                                            int &j)
+{
+    // branch-free: the buffer position is clamped in bounds and the test
+    // masked by t < t1
+    const int tc = min(t, kCandBuf - 1);
+    const float4 cp = w.pos[tc];
+    j = __float_as_int(cp.w);
+    Vec3<float> d;
+    if (!kImages) {
+        d = displacement<float>(s, pi, cp);
+    } else if (kShift) {
+        // past the staged length w.q is stale: keep the index in the table
+        const float4 h = w.shift[min((int)w.q[tc], kStencil - 1)];
+        d.x = (cp.x - pi.x) + h.x;
+        d.y = (cp.y - pi.y) + h.y;
+        d.z = (cp.z - pi.z) + h.z;
+    } else {
+        d.x = cp.x - pi.x;
+        d.y = cp.y - pi.y;
+        d.z = cp.z - pi.z;
     }
-    if (up + dn < cap)
-        for (int t = 0; t < dn; ++t) vrow[up + t] = vrow[cap - dn + t];
-    if (over) set_err(s, kErrCapacity);
-    s.vnn[i] = up + dn;
-    s.vnh[i] = up;
+    return t < t1 && (kUp ? j > i : j < i) && fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z)) < s.rv2;
+}
+
+// Sweep atom i over the staged candidates [t0, t1) of the buffer, all in one
+// part (kUp: part 0, j > i; else part 1, j < i), appending to its row, two
+// rounds of 32 per iteration.  kShift: some stencil cell of this one is a
+// periodic image (a cell on the box faces); interior cells need no shift.
+template <bool kImages, bool kShift, bool kUp>
+__device__ __forceinline__ void verlet_sweep(const Sys &s, const VerletWarpSmem &w, int i, float4 pi, int t0, int t1,
+                                             int lane, int *vrow, int &total)
+{
+    const unsigned lt = (1u << lane) - 1u;
+    for (int r = t0; r < t1; r += 64) {
+        int ja, jb;
+        const bool ina = verlet_test<kImages, kShift, kUp>(s, w, i, pi, r + lane, t1, ja);
+        const bool inb = verlet_test<kImages, kShift, kUp>(s, w, i, pi, r + 32 + lane, t1, jb);
+        const unsigned ba = __ballot_sync(0xffffffffu, ina), bb = __ballot_sync(0xffffffffu, inb);
+        const int ata = total + __popc(ba & lt);
+        const int atb = total + __popc(ba) + __popc(bb & lt);
+        if (ina && ata < s.max_vnb) vrow[ata] = ja;
+        if (inb && atb < s.max_vnb) vrow[atb] = jb;
+        total += __popc(ba) + __popc(bb);
+    }
+}
+
+template <bool kImages, bool kShift>
+__device__ __forceinline__ void verlet_sweeps(const Sys &s, const VerletWarpSmem &w, int i, float4 pi, int k0, int len,
+                                              int T0, int lane, int *vrow, int &total, int &up)
+{
+    const int split = min(max(T0 - k0, 0), len);  // buffer positions below it are part 0
+    verlet_sweep<kImages, kShift, true>(s, w, i, pi, 0, split, lane, vrow, total);
+    if (k0 < T0) up = total;
+    verlet_sweep<kImages, kShift, false>(s, w, i, pi, split, len, lane, vrow, total);
+}
+
+template <bool kImages>
+__device__ __forceinline__ void verlet_cell(const Sys &s, VerletWarpSmem &w, int c, int lane)
+{
+    const int a0 = s.cell_start[c], na = s.cell_start[c + 1] - a0;
+    if (na == 0) return;
+    const int xyz = s.xyz_of_rank[c];
+    const int cx = xyz & 1023, cy = (xyz >> 10) & 1023, cz = xyz >> 20;
+    const int sx = axis_span(s.nc[0]), sy = axis_span(s.nc[1]), sz = axis_span(s.nc[2]);
+    const int nq = sx * sy * sz;
+    // the stencil: lane q < nq looks up cell q (x fastest) and its segments
+    int n0 = 0, n1 = 0;
+    if (lane < nq) {
+        const int ex = lane % sx, ey = (lane / sx) % sy, ez = lane / (sx * sy);
+        const int x = cx + axis_off(s.nc[0], ex), y = cy + axis_off(s.nc[1], ey), z = cz + axis_off(s.nc[2], ez);
+        const int cq = s.rank_of_xyz[(wrap_cell(z, s.nc[2]) * s.nc[1] + wrap_cell(y, s.nc[1])) * s.nc[0] +
+                                     wrap_cell(x, s.nc[0])];
+        const int st = s.cell_start[cq];
+        const int n = s.cell_start[cq + 1] - st;
+        w.start[lane] = st;
+        w.cnt[lane] = n;
+        w.shift[lane] = make_float4(x < 0 ? -s.Lhi[0] : (x >= s.nc[0] ? s.Lhi[0] : 0.0f),
+                                    y < 0 ? -s.Lhi[1] : (y >= s.nc[1] ? s.Lhi[1] : 0.0f),
+                                    z < 0 ? -s.Lhi[2] : (z >= s.nc[2] ? s.Lhi[2] : 0.0f), 0.0f);
+        n0 = cq >= c ? n : 0;
+        n1 = cq <= c ? n : 0;
+    }
+    // exclusive scans of the segment lengths over the stencil (lanes)
+    int i0 = n0, i1 = n1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y0 = __shfl_up_sync(0xffffffffu, i0, o), y1 = __shfl_up_sync(0xffffffffu, i1, o);
+        if (lane >= o) {
+            i0 += y0;
+            i1 += y1;
+        }
+    }
+    const int T0 = __shfl_sync(0xffffffffu, i0, 31), T1 = __shfl_sync(0xffffffffu, i1, 31);
+    if (lane < nq) {
+        w.off[0][lane] = n0 > 0 ? i0 - n0 : -1;
+        w.off[1][lane] = n1 > 0 ? T0 + i1 - n1 : -1;
+    }
+    __syncwarp();
+    const int T = T0 + T1;
+    const bool one_chunk = T <= kCandBuf;
+    // a cell on the box faces has stencil cells at a periodic image
+    const bool shifted = cx == 0 || cy == 0 || cz == 0 || cx == s.nc[0] - 1 || cy == s.nc[1] - 1 || cz == s.nc[2] - 1;
+    if (one_chunk) verlet_stage(s, w, nq, 0, T, lane);
+    for (int ia = 0; ia < na; ++ia) {
+        const int i = a0 + ia;
+        const float4 pi = s.pos_s[i];
+        int *vrow = s.vnbr + (size_t)i * s.max_vnb;
+        int total = 0, up = 0;
+        for (int k0 = 0; k0 < T; k0 += kCandBuf) {
+            const int len = min(kCandBuf, T - k0);
+            if (!one_chunk) verlet_stage(s, w, nq, k0, len, lane);
+            if (shifted) verlet_sweeps<kImages, true>(s, w, i, pi, k0, len, T0, lane, vrow, total, up);
+            else verlet_sweeps<kImages, false>(s, w, i, pi, k0, len, T0, lane, vrow, total, up);
+            if (!one_chunk) __syncwarp();  // the chunk is read before the next is staged
+        }
+        if (lane == 0) {
+            if (total > s.max_vnb) set_err(s, kErrCapacity);
+            s.vnn[i] = min(total, s.max_vnb);
+            s.vnh[i] = min(up, s.max_vnb);
+        }
+    }
+    __syncwarp();  // the tables are read before the next cell overwrites them
 }
 
 // End of a rebuild, run once by the last Verlet block to finish: the rows'
@@ -339,19 +450,18 @@ __device__ __forceinline__ void finish_rebuild(const Sys &s, Blk k)
     *s.flag = s.always_rebuild ? 1 : 0;
 }
 
-// Grid-stride over tiles of blockDim atoms, so an idle launch (no rebuild)
+// Grid-stride over cells, one warp per cell, so an idle launch (no rebuild)
 // retires at once.
 __device__ __forceinline__ void verlet(const Sys &s, Blk k)
 {
     if (!*s.flag) return;
+    __shared__ VerletWarpSmem sh[kVerletWarps];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const bool images = s.nc[0] >= 3 && s.nc[1] >= 3 && s.nc[2] >= 3;
-    const int tiles = (s.n + (int)blockDim.x - 1) / (int)blockDim.x;
-    for (int it = 0, blk; (blk = work_item(k, it)) < tiles; ++it) {
-        const int i = blk * (int)blockDim.x + (int)threadIdx.x;
-        if (i < s.n) {
-            if (images) verlet_row<true>(s, i);
-            else verlet_row<false>(s, i);
-        }
+    const int warps = k.nb * kVerletWarps;
+    for (int c = k.b * kVerletWarps + wid; c < s.ncell; c += warps) {
+        if (images) verlet_cell<true>(s, sh[wid], c, lane);
+        else verlet_cell<false>(s, sh[wid], c, lane);
     }
     finish_rebuild(s, k);
 }
