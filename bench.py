@@ -18,6 +18,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -76,6 +77,7 @@ def parse():
     ap.add_argument("--drift-step", type=float, default=0.01,
                     help="random-walk step (A per coordinate and frame) of the timed drifting trajectory")
     ap.add_argument("--no-skin0", action="store_true", help="skip the rebuild-every-step (skin 0) measurement")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the served offered-rate sweep")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-system batched comparison")
     ap.add_argument("--no-served", action="store_true", help="skip the served (continuous batching) trace")
     ap.add_argument("--no-small", action="store_true", help="skip the torsion / nearest-distance walker forms")
@@ -843,11 +845,11 @@ def run_served(args, dev, stream, metad):
                                                   rate_hz=cfgp["rate_hz"])
     systems = [synth.wurtzite_system(int(n_w[w]), cfg=5, sys=w) for w in range(len(n_w))]
 
-    def make_walkers():
+    def make_walkers(runs=1):
         out = []
         for w, sysm in enumerate(systems):
             p = metad.params_for(sysm.n, sysm.box, n_cv=2, sigma=mp.sigma, stream=stream.cuda_stream,
-                                 hill_capacity=cfgp["hills"] + cfgp["requests"] // cfgp["deposit_every"] + 64)
+                                 hill_capacity=cfgp["hills"] + runs * cfgp["requests"] // cfgp["deposit_every"] + 64)
             out.append(serve.Walker(params=p, centres=hill_sets[w][0], heights=hill_sets[w][1], frames=frames[w]))
         return out
 
@@ -870,12 +872,58 @@ def run_served(args, dev, stream, metad):
         wk.ctx.close()
     agree = all(np.array_equal(a.cv, b.cv) and a.V == b.V for a, b in zip(served.requests, plain.requests))
     s, q = served.summary(), plain.summary()
+    sweep = None
+    if not args.no_sweep:
+        sweep = served_sweep(args, stream, serve, cfgp, n_w, make_walkers)
     return {"walkers": len(n_w), "atoms_resident": int(sum(sysm.n for sysm in systems)),
             "requests": len(arrivals), "rate_hz": cfgp["rate_hz"], "budget_bytes": cfgp["budget_bytes"],
             "served": s, "plain": q, "p99_ratio_plain_over_served": q["p99_ms"] / s["p99_ms"],
             "throughput_ratio": s["atom_steps_per_s"] / q["atom_steps_per_s"],
-            "results_identical_to_plain": bool(agree), "kernels": served.launches,
+            "results_identical_to_plain": bool(agree), "kernels": served.launches, "sweep": sweep,
             "h2d": "positions from page-locked host memory per request; forces and CVs back per request"}
+
+
+SWEEP_RATES = (5000.0, 10000.0, 20000.0, float("inf"))
+SWEEP_SEEDS = (1, 2, 3)
+
+
+def served_sweep(args, stream, serve, cfgp, n_w, make_walkers):
+    """Offered rate against capacity: the served loop and sequential plain
+    evaluation on the same walkers, each rate with three request streams
+    (synth.served_arrivals seeds 1-3; an infinite rate is a burst of all
+    requests at t = 0, i.e. saturation).  Throughput is requests completed
+    over the span from the first arrival to the last completion; p50 / p99
+    are per-request latencies.  One server and one plain walker set serve
+    every stream in turn (their hills grow by the deposits on the way)."""
+    runs = len(SWEEP_RATES) * len(SWEEP_SEEDS)
+    srv = serve.Server(make_walkers(runs), stream, budget_bytes=cfgp["budget_bytes"],
+                       deposit_every=cfgp["deposit_every"])
+    srv.preload()
+    plain_walkers = make_walkers(runs)
+    points = []
+    for rate in SWEEP_RATES:
+        per = {"served": [], "plain": []}
+        for seed in SWEEP_SEEDS:
+            arr, wof = synth.served_arrivals(5, len(n_w), cfgp["requests"], rate, seed)
+            per["served"].append(srv.run(arr, wof).summary())
+            per["plain"].append(serve.run_plain(plain_walkers, stream, arr, wof,
+                                                deposit_every=cfgp["deposit_every"]).summary())
+        pt = {"offered_req_s": None if math.isinf(rate) else rate, "saturation": math.isinf(rate)}
+        for mode in ("served", "plain"):
+            rows = per[mode]
+            pt[mode] = {key: {"mean": float(np.mean([r[key] for r in rows])), "min": float(min(r[key] for r in rows)),
+                              "max": float(max(r[key] for r in rows))}
+                        for key in ("throughput_req_s", "atom_steps_per_s", "p50_ms", "p99_ms")}
+            pt[mode]["mean_batch"] = float(np.mean([r["mean_batch"] for r in rows]))
+        pt["throughput_ratio"] = pt["served"]["throughput_req_s"]["mean"] / pt["plain"]["throughput_req_s"]["mean"]
+        points.append(pt)
+    srv.close()
+    for wk in plain_walkers:
+        if wk.ctx is not None:
+            wk.ctx.close()
+    return {"requests_per_run": cfgp["requests"], "seeds": list(SWEEP_SEEDS), "points": points,
+            "capacity_req_s": {"served": points[-1]["served"]["throughput_req_s"]["mean"],
+                               "plain": points[-1]["plain"]["throughput_req_s"]["mean"]}}
 
 
 def main():

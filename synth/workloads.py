@@ -339,6 +339,20 @@ def served_trace(cfg: int = 5, n_walkers: int = 32, n_requests: int = 2000, rate
     return n, arrivals, walker
 
 
+def served_arrivals(cfg: int, n_walkers: int, n_requests: int, rate_hz: float, seed: int):
+    """Another request stream for the walkers of served_trace: Poisson
+    arrivals at rate_hz (all at t = 0 when rate_hz is infinite: a saturating
+    burst) and uniform walkers, from seed `seed` (>= 1; the walker sizes are
+    served_trace's)."""
+    g = rng(cfg, seed, 8)
+    if math.isinf(rate_hz):
+        arrivals = np.zeros(n_requests)
+    else:
+        arrivals = np.cumsum(g.exponential(1.0 / rate_hz, n_requests))
+    walker = g.integers(0, n_walkers, n_requests)
+    return arrivals, walker
+
+
 def npt_frame(system: System, frame: int, strain_sigma: float = 1e-3, sigma: float = 0.05, period: int = 0):
     """A frame of a triaxial NPT run: each box length scaled by 1 + e_a,
     positions scaled with it (fixed fractional coordinates) plus N(0, sigma^2)

@@ -52,3 +52,16 @@ def test_device_generator_draws_from_the_same_distribution(small):
         assert dev_std == pytest.approx(want, rel=0.05) and host_std == pytest.approx(want, rel=0.05)
     assert np.array_equal(out[3, :, 3], small.base[:, 3])
     assert np.all(out[:, :, :3] >= 0) and np.all(out[:, :, :3] < box.astype(np.float32))
+
+
+def test_served_arrivals_streams():
+    arr, wof = synth.served_arrivals(5, 32, 4000, 10000.0, seed=1)
+    assert np.all(np.diff(arr) >= 0) and np.mean(np.diff(arr)) == pytest.approx(1e-4, rel=0.05)
+    assert wof.min() >= 0 and wof.max() < 32 and len(np.unique(wof)) == 32
+    arr2, wof2 = synth.served_arrivals(5, 32, 4000, 10000.0, seed=2)
+    assert not np.array_equal(arr, arr2) and not np.array_equal(wof, wof2)
+    burst, _ = synth.served_arrivals(5, 32, 100, float("inf"), seed=3)
+    assert np.all(burst == 0.0)
+    # the walkers (sizes) are the served trace's whatever the stream
+    n, _, _ = synth.served_trace(5, n_walkers=32, n_requests=10)
+    assert n.shape == (32,)
