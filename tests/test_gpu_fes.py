@@ -47,10 +47,12 @@ def test_sum_of_hills_fes_matches_oracle(dev, n_cv):
     c = ctr + g.uniform(-8, 8, size=(700, n_cv)) * sig
     ctx = _ctx(dev, n_cv)
     w = ctx.deposit_hills(c)
+    w_ref = oracle.deposit_sequence(c, mp.sigma, mp.w0, kbdt(mp))
+    assert np.allclose(w, w_ref, rtol=1e-12, atol=0)
     lo, hi = ctr - 10 * sig, ctr + 10 * sig
     n = (37, 23)[:n_cv]
     F = ctx.fes_grid(lo, hi, n).ravel()
-    ref = oracle.fes_points(centres_of(lo, hi, n), c, w, mp.sigma, mp.biasfactor)
+    ref = oracle.fes_points(centres_of(lo, hi, n), c, w_ref, mp.sigma, mp.biasfactor)
     assert np.abs(F - ref).max() <= 1e-10 * np.abs(ref).max()
     assert F.min() == 0.0
 
@@ -66,11 +68,15 @@ def test_fes_includes_the_bias_grid(dev):
     w1 = ctx.deposit_hills(c[:600])
     ctx.fold_hills()
     w2 = ctx.deposit_hills(c[600:])
+    # the oracle's own heights: deposit, fold, deposit on top of the grid
+    w1_ref = oracle.deposit_sequence(c[:600], mp.sigma, mp.w0, kbdt(mp))
     G = oracle.HillGrid((60, 60), lo_g, hi_g)
-    G.fold(c[:600], w1, mp.sigma)
+    G.fold(c[:600], w1_ref, mp.sigma)
+    w2_ref = oracle.deposit_sequence(c[600:], mp.sigma, mp.w0, kbdt(mp), grid=G)
+    assert np.allclose(w1, w1_ref, rtol=1e-12, atol=0) and np.allclose(w2, w2_ref, rtol=1e-11, atol=0)
     lo, hi, n = ctr - 9 * sig, ctr + 9 * sig, (31, 29)
     F = ctx.fes_grid(lo, hi, n).ravel()
-    ref = oracle.fes_points(centres_of(lo, hi, n), c[600:], w2, mp.sigma, mp.biasfactor, grid=G)
+    ref = oracle.fes_points(centres_of(lo, hi, n), c[600:], w2_ref, mp.sigma, mp.biasfactor, grid=G)
     assert np.abs(F - ref).max() <= 1e-10 * np.abs(ref).max()
 
 

@@ -126,8 +126,16 @@ def test_lattice_deposits(dev, system):
     cg, wg = ctx.get_hills()
     assert cg.shape == (105, 4)
     assert np.array_equal(cg[:100], c) and np.array_equal(wg[:100], w)
-    w_ref = oracle.deposit_sequence(cg, sig, 1.0, kbdt(), heights_prefix=w)
-    assert np.abs(wg - w_ref).max() <= TOL
+    # the oracle's own chain: each hill at the oracle's CVs of that frame
+    live_c, live_w = c.copy(), w.copy()
+    for f in range(5):
+        fr, box = synth.npt_frame(system, 10 + f, strain_sigma=2e-3)
+        s_ref = oracle.step_box(fr, oracle.make_params(box, n_cv=1), live_c, live_w, sig, lattice=True)["s"]
+        h = oracle.deposit_sequence(np.vstack([live_c, s_ref[None, :]]), sig, 1.0, kbdt(), heights_prefix=live_w)[-1]
+        live_c = np.vstack([live_c, s_ref[None, :]])
+        live_w = np.append(live_w, h)
+    assert np.all(np.abs(cg[100:] - live_c[100:]) <= TOL * np.abs(live_c[100:]))
+    assert np.abs(wg - live_w).max() <= TOL
     ctx.close()
 
 

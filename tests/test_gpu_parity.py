@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 import synth
-from parity_util import check_bias, check_cv, check_forces, force_errors, kbdt, setup_hills
+from parity_util import TOL, check_bias, check_cv, check_forces, force_errors, kbdt, setup_hills
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -259,23 +259,20 @@ def test_config3_grid_deposit_and_frames(dev):
         frame = synth.perturbed_frame(system, f)
         got = gpu_step(ctx, dev, frame)
         ref = oracle.step(frame, p, live_c, live_w, mp.sigma, grid=G)
-        # error budget: CV rounding (through dV/ds) versus pair arithmetic (the
-        # oracle's forces at the GPU's dV/ds)
-        F_at_gpu_dv, _ = oracle.forces(frame, p, got["dV"])
         print(f"frame {f}: ds/s {(got['s'] - ref['s']) / ref['s']}, V {got['V']} vs {ref['V']}, "
-              f"dV {got['dV']} vs {ref['dV']}, F err {force_errors(got['F'], ref['F'])}, "
-              f"F err at GPU dV {force_errors(got['F'], F_at_gpu_dv)}")
-        check_forces(got["F"], F_at_gpu_dv)
+              f"dV {got['dV']} vs {ref['dV']}, F err {force_errors(got['F'], ref['F'])}")
         check_cv(got["s"], ref["s"])
         check_bias(got["V"], got["dV"], ref["V"], ref["dV"], mp)
         check_forces(got["F"], ref["F"])
         if (f + 1) % cfgp["deposit_every"] == 0:
+            # each side deposits at its own CVs; the heights differ through
+            # the centres' CV difference only (well inside 1e-5)
             h = ctx.deposit_hill()
-            href = oracle.deposit_sequence(np.vstack([live_c, got["s"][None, :]]), mp.sigma, mp.w0, kbdt(mp),
+            href = oracle.deposit_sequence(np.vstack([live_c, ref["s"][None, :]]), mp.sigma, mp.w0, kbdt(mp),
                                            grid=G, heights_prefix=live_w)[-1]
-            assert h == pytest.approx(href, rel=1e-11)
-            live_c = np.vstack([live_c, got["s"][None, :]])
-            live_w = np.append(live_w, h)
+            assert h == pytest.approx(href, rel=1e-5)
+            live_c = np.vstack([live_c, ref["s"][None, :]])
+            live_w = np.append(live_w, href)
     assert ctx.hill_count == K2 + 1
 
 
@@ -287,15 +284,17 @@ def test_ragged_and_tiny_systems(dev, n, fp64):
 
     Two atoms in FP32: the CVs are single rounded terms (one switch value,
     one averaged Q6 of a lone bond, exactly 1 in exact arithmetic), so their
-    relative error is one float32 rounding, ~1e-7, with nothing to average it
-    out.  The CVs meet 1e-5; dV/ds does not always: it moves by
-    (d2V/ds2) ds, and 200 hills of width 0.02 within a few sigma give
-    d2V/ds2 ~ V / sigma^2 ~ 1e4-1e5, so ds ~ 1e-7 shifts dV/ds by up to ~1e-3
-    against the floor 1e-5 w0 / sigma = 5e-4.  That is the CV's own float32
-    rounding, amplified by the bias curvature, not an error of the bias or
-    force arithmetic; the test checks each part against the oracle at the
-    CUDA path's own CVs (the bias FP64 at 1e-10, the forces at the CUDA
-    path's dV/ds at 1e-5) and prints the end-to-end dV/ds error."""
+    relative error is a few float32 roundings, ~1e-7, with nothing to average
+    it out.  The CVs meet 1e-5; dV/ds need not: it moves by (d2V/ds2) ds,
+    and 200 hills of width 0.02 within a few sigma give d2V/ds2 ~ V /
+    sigma^2 ~ 1e4-1e5, so ds ~ 1e-7 shifts dV/ds by up to ~1e-3 against the
+    floor 1e-5 w0 / sigma = 5e-4.  That is the CV's own float32 rounding
+    amplified by the bias curvature, not an error of the bias or force
+    arithmetic.  The test bounds it from the oracle alone: the CVs' rounding
+    is at most 8 float32 ulps, the oracle's bias gradient and curvature
+    (central differences of its bias at its own CVs) carry that to V and
+    dV/ds, and the oracle's CV gradients (its forces for unit dV/ds) carry
+    the dV/ds bound to the forces, each on top of the 1e-5 tolerance."""
     box = np.array([9.0, 9.5, 10.0]) * max(1.0, (n / 60.0) ** (1 / 3))
     if n <= 2:
         box = np.array([12.0, 12.0, 12.0])
@@ -312,7 +311,8 @@ def test_ragged_and_tiny_systems(dev, n, fp64):
     s0, _, _ = oracle.cv(pos, p)
     c = synth.hill_centres(96, n, s0, mp.sigma, 200)
     ctx = make_ctx(dev, s, mp, fp64=fp64)
-    w = ctx.deposit_hills(c)
+    ctx.deposit_hills(c)
+    w = oracle.deposit_sequence(c, mp.sigma, mp.w0, kbdt(mp))
     ref = oracle.step(pos, p, c, w, mp.sigma)
     got = gpu_step(ctx, dev, pos)
     if n == 1:
@@ -320,10 +320,22 @@ def test_ragged_and_tiny_systems(dev, n, fp64):
         return
     if n == 2 and not fp64:
         check_cv(got["s"], ref["s"])
-        V_at, dV_at = oracle.bias(got["s"], c, w, mp.sigma)
-        check_bias(got["V"], got["dV"], V_at, dV_at, mp, tol=1e-10)
-        F_at, _ = oracle.forces(pos, p, got["dV"])
-        check_forces(got["F"], F_at)
+        sig = np.asarray(mp.sigma)
+        ds = 8.0 * np.finfo(np.float32).eps * np.abs(ref["s"])  # the CVs' float32 rounding bound
+        # the oracle's bias curvature by central differences at its own CVs
+        H = np.zeros((2, 2))
+        for d in range(2):
+            e = np.zeros(2)
+            e[d] = 1e-4 * sig[d]
+            H[:, d] = (oracle.bias(ref["s"] + e, c, w, mp.sigma)[1] - oracle.bias(ref["s"] - e, c, w, mp.sigma)[1]) / (2 * e[d])
+        tol_V = TOL * max(abs(ref["V"]), mp.w0) + np.abs(ref["dV"]) @ ds
+        tol_dV = TOL * np.maximum(np.abs(ref["dV"]), mp.w0 / sig) + np.abs(H) @ ds
+        assert abs(got["V"] - ref["V"]) <= tol_V, (got["V"], ref["V"], tol_V)
+        assert np.all(np.abs(got["dV"] - ref["dV"]) <= tol_dV), (got["dV"], ref["dV"], tol_dV)
+        # forces: the oracle's CV gradients (its forces for unit dV/ds) carry the dV/ds bound
+        J = [np.abs(oracle.forces(pos, p, np.eye(2)[d])[0]) for d in range(2)]
+        tol_F = tol_dV[0] * J[0] + tol_dV[1] * J[1] + TOL * np.abs(ref["F"]).max()
+        assert np.all(np.abs(got["F"] - ref["F"]) <= tol_F)
         rel = [abs(got["dV"][d] - ref["dV"][d]) / max(abs(ref["dV"][d]), mp.w0 / mp.sigma[d]) for d in range(2)]
         print(f"N=2 FP32: ds/s {(got['s'] - ref['s']) / ref['s']}, dV/ds error over the floor {rel}")
         return
@@ -344,7 +356,8 @@ def test_isolated_atoms_have_zero_cv_and_force(dev):
     ctx = make_ctx(dev, _Sys(pos, box), mp)
     s0, _, _ = oracle.cv(pos, p)
     c = np.array([s0 + np.array([0.01, 0.01]), s0 - np.array([0.02, 0.005])])
-    w = ctx.deposit_hills(c)
+    ctx.deposit_hills(c)
+    w = oracle.deposit_sequence(c, mp.sigma, mp.w0, kbdt(mp))
     got = gpu_step(ctx, dev, pos, per_atom=True)
     ref = oracle.step(pos, p, c, w, mp.sigma)
     check_cv(got["s"], ref["s"])
@@ -370,7 +383,8 @@ def test_switch_and_mask_variants(dev, variant):
     s0, _, _ = oracle.cv(system.base, p)
     c = synth.hill_centres(91, 0, s0, mp.sigma, 300)
     ctx = make_ctx(dev, system, mp, cn_unlike=unlike, sw=sw)
-    w = ctx.deposit_hills(c)
+    ctx.deposit_hills(c)
+    w = oracle.deposit_sequence(c, mp.sigma, mp.w0, kbdt(mp))
     got = gpu_step(ctx, dev, frame)
     ref = oracle.step(frame, p, c, w, mp.sigma)
     check_cv(got["s"], ref["s"])
@@ -468,7 +482,9 @@ def test_mirror_slots_equal_the_row_search(dev, fp64, skin):
     c = synth.hill_centres(93, 0, s0, mp.sigma, 200)
     ctxs = [make_ctx(dev, system, mp, fp64=fp64, skin=skin),
             make_ctx(dev, system, mp, fp64=fp64, max_nb=128, skin=skin)]
-    w = [ctx.deposit_hills(c) for ctx in ctxs][0]
+    for ctx in ctxs:
+        ctx.deposit_hills(c, want_heights=False)
+    w = oracle.deposit_sequence(c, mp.sigma, mp.w0, kbdt(mp))
     # small moves reuse the rows; sigma 0.4 moves atoms past skin / 2
     for f, sig in enumerate((0.05, 0.05, 0.4, 0.05, 0.4, 0.4, 0.05)):
         frame = synth.perturbed_frame(system, f, sigma=sig)
