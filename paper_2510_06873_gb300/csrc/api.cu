@@ -443,9 +443,6 @@ metad_status state_buffers(metad_ctx *c, Buffers &b, Alloc &&alloc)
         (s = alloc(&b.crossb, c->p.n_cv == 2 ? rs * (size_t)y.max_nb * n : 1)) ||
         (s = alloc(&y.pos_ref, n)) ||
         (s = alloc(&y.vnbr, (size_t)y.max_vnb * n)) || (s = alloc(&y.vnn, n)) || (s = alloc(&y.flag, 1)) ||
-        // the filter reads each row's first 32 bytes: rows shorter than that
-        // read into the next row, the last one into this padding
-        (s = alloc(&y.vmirror, y.mirror ? (size_t)y.max_vnb * n + 32 : 1)) ||
         (s = alloc(&y.vround, y.mirror ? (size_t)y.vround_stride * n : 1)) || (s = alloc(&y.rows_fresh, 1)) ||
         (s = alloc(&y.rebuilds, 1)) || (s = alloc(&y.Lref, 4)) || (s = alloc(&b.rb, rs * (nq * 3 + (size_t)n * 4 + 64))) ||
         (s = alloc(&y.part, (size_t)y.part_stride * 4)) || (s = alloc(&y.ticket, 8)) ||
@@ -1083,7 +1080,7 @@ metad_status metad_export_neighbors(metad_ctx *c, int64_t *pairs_host, int64_t c
     }
     {
         StageScope t(c, ST_OTHER, 1);
-        metad::launch_export_pairs(c->sys, c->pairs, c->pair_count, c->stream);
+        metad::launch_export_pairs(c->sys, c->fp64, c->pairs, c->pair_count, c->stream);
     }
     if ((s = launched(c, "export"))) return s;
     int cnt = 0;

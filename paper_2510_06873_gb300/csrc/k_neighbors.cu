@@ -559,14 +559,22 @@ __global__ void __launch_bounds__(kBlockAtoms) kb_verlet(BatchView v)
 }
 
 // Pairs (i < j) in caller indices, for export: one thread per sorted atom,
-// entries with caller(i) < caller(j) appended through one counter.
+// entries with caller(i) < caller(j) appended through one counter.  Each
+// exact entry's j is read from its geometry tag (the exact rows of indices
+// are kept only without mirror slots).
+template <typename real>
 __global__ void k_export_pairs(Sys s, long long *pairs, int *count)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.n) return;
     int ui = s.perm[i];
     for (int k = 0; k < s.nn[i]; ++k) {
-        int uj = s.perm[s.nbr[(size_t)i * s.max_nb + k]];
+        Vec3<real> d;
+        bool cn;
+        int j;
+        unsigned vm;
+        load_geo<real>(s, (size_t)i * s.max_nb + k, d, cn, j, vm);
+        int uj = s.perm[j];
         if (ui < uj) {
             int slot = atomicAdd(count, 1);
             pairs[2 * (size_t)slot] = ui;
@@ -710,10 +718,13 @@ void launch_nn_stats(const Sys &s, unsigned long long *sum, int *mx, cudaStream_
     k_nn_stats<<<(s.n + 255) / 256, 256, 0, st>>>(s, sum, mx);
 }
 
-void launch_export_pairs(const Sys &s, long long *pairs, int *count, cudaStream_t st)
+void launch_export_pairs(const Sys &s, int fp64, long long *pairs, int *count, cudaStream_t st)
 {
     cudaMemsetAsync(count, 0, sizeof(int), st);
-    k_export_pairs<<<(s.n + 255) / 256, 256, 0, st>>>(s, pairs, count);
+    if (fp64)
+        k_export_pairs<double><<<(s.n + 255) / 256, 256, 0, st>>>(s, pairs, count);
+    else
+        k_export_pairs<float><<<(s.n + 255) / 256, 256, 0, st>>>(s, pairs, count);
 }
 
 }  // namespace metad

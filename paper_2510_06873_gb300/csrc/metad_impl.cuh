@@ -90,14 +90,14 @@ struct Sys {
                            // of each exact entry, written by the exact filter
     // Verlet list (cutoff rc + skin, built at the reference positions)
     float4 *pos_ref;       // sorted positions at the last rebuild
-    int *vnbr;             // [n][max_vnb]
+    int *vnbr;             // [n][max_vnb]; with mirror slots an entry j > i carries, above bit 23,
+                           // i's position in j's Verlet row (set once per rebuild by the filter)
     int *vnn;              // [n]
     int *vnh;              // [n] Verlet entries with j > i (stored first)
     int max_vnb;
     // mirror slots: where the pair force of i's entry j > i goes in j's row,
     // without searching j's row in the force pass
     int mirror;                // 1: in use (n < 2^23, rows of at most 255 entries)
-    unsigned char *vmirror;    // [n][max_vnb]: for j = vnbr[i][k] > i, i's position in j's Verlet row
     unsigned short *vround;    // [n][vround_stride]: per filter round r (Verlet entries 8r .. 8r + 7),
                                // the exact entries before it | the round's exact bits << 8
     int vround_stride;
@@ -255,7 +255,7 @@ void launch_force_gather(const Sys &s, int fp64, float *F, int accumulate, cudaS
 void configure_kernels();
 void launch_grid_fold(const Sys &s, int K, cudaStream_t st);
 void launch_nn_stats(const Sys &s, unsigned long long *sum, int *mx, cudaStream_t st);
-void launch_export_pairs(const Sys &s, long long *pairs, int *count, cudaStream_t st);
+void launch_export_pairs(const Sys &s, int fp64, long long *pairs, int *count, cudaStream_t st);
 void launch_per_atom_out(const Sys &s, int fp64, double *out, cudaStream_t st);
 void set_ylm_constants(cudaStream_t st);
 // Torsion and nearest-distance families: the CV pass (one block per system)
@@ -605,6 +605,20 @@ __device__ __forceinline__ bool pair_in(const Sys &s, float4 pi, float4 pj, cons
     return pair_exact(s, pi, pj);
 }
 
+// pair_in for code where the whole warp is converged: the FP64 decision runs
+// only when some lane of the warp has a candidate inside the guard band (a
+// vote), as a warp-uniform branch.  The same decisions as pair_in.
+__device__ __forceinline__ bool pair_in_warp(const Sys &s, bool valid, float4 pi, float4 pj, const Vec3<float> &d)
+{
+    const float r2 = fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z));
+    bool in = valid && r2 < s.rc2_lo;
+    const bool band = valid && r2 >= s.rc2_lo && r2 <= s.rc2_hi;
+    if (__any_sync(0xffffffffu, band)) {
+        if (band) in = pair_exact(s, pi, pj);
+    }
+    return in;
+}
+
 // The geometry of an exact entry, cached by the filter so the CV and force
 // passes read one contiguous record per entry instead of gathering the
 // neighbour's position again: r_j - r_i, and in the fourth slot a tag
@@ -698,7 +712,8 @@ __device__ __forceinline__ void load_geo<double, false>(const Sys &s, size_t slo
 
 // i's position in the j < i part of j's Verlet row (rows are symmetric: the
 // Verlet predicate is), four entries per load.  Run by the filter of the
-// first step on new rows only; the later steps read the stored result.
+// first step on new rows only; the later steps read the stored result.  The
+// part searched holds plain indices (only entries j > i carry a position).
 __device__ __forceinline__ unsigned mirror_position(const Sys &s, int j, int i)
 {
     const int *rj = s.vnbr + (size_t)j * s.max_vnb;
@@ -728,57 +743,58 @@ __device__ __forceinline__ int filter_row(const Sys &s, const AtomLane &a)
     const int vn = a.ok ? s.vnn[a.i] : 0;
     const int vh = a.ok ? s.vnh[a.i] : 0;
     const float4 pi = a.ok ? s.pos_s[a.i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const int *vrow = s.vnbr + (size_t)(a.ok ? a.i : 0) * s.max_vnb;
+    int *vrow = s.vnbr + (size_t)(a.ok ? a.i : 0) * s.max_vnb;
     int *row = s.nbr + (size_t)(a.ok ? a.i : 0) * s.max_nb;
-    // mirror slots: each round records the exact entries before it and its
-    // exact bits, and each entry j > i carries i's Verlet position in j's
-    // row (searched once on new rows, stored for the steps after)
-    unsigned mw = 0u;
-    if (s.mirror) {
-        // new rows: find each j > i entry's mirror position once
-        if (*s.rows_fresh) {
-            for (int k = a.l; k < vh; k += kG)
-                s.vmirror[(size_t)a.i * s.max_vnb + k] = (unsigned char)mirror_position(s, vrow[k], a.i);
-            __syncwarp();
+    unsigned short *vround = s.vround + (s.mirror ? (size_t)(a.ok ? a.i : 0) * s.vround_stride : 0);
+    // mirror slots: each Verlet entry j > i carries i's position in j's
+    // Verlet row in its high bits (searched once on new rows, kept there for
+    // the steps after, read with the entry), and each round records the exact
+    // entries before it and its exact bits
+    if (s.mirror && *s.rows_fresh) {
+        for (int k = a.l; k < vh; k += kG) {
+            const int j = vrow[k] & (int)kMirrorJ;
+            vrow[k] = j | (int)(mirror_position(s, j, a.i) << kMirrorShift);
         }
-        // the positions of the first four rounds in one sector: lane l holds
-        // bytes 4l .. 4l + 3 of the atom's row (rows are padded for it)
-        if (a.ok) mw = reinterpret_cast<const unsigned *>(s.vmirror + (size_t)a.i * s.max_vnb)[a.l];
+        __syncwarp();
     }
+    const unsigned lt = (1u << a.l) - 1u;
+    const unsigned jmask = s.mirror ? kMirrorJ : 0xffffffffu;
     int cnt = 0, nh = 0;
+    unsigned short rec = 0;  // lane r keeps round r's record (rounds below kG)
     // one pass: the Verlet row already has its j > i part first, so accepted
     // entries come out in the same order; nh counts those from that part
     const int vmax = __reduce_max_sync(0xffffffffu, vn);
     for (int base = 0; base < vmax; base += kG) {
         const int k = base + a.l;
         const bool valid = k < vn;
-        const int j = valid ? vrow[k] : 0;
-        // the mirror position of entry k: byte k & 3 of word k / 4 = 2 r + l / 4
-        // of the preloaded sector for the first four rounds r
-        unsigned vm = 0u;
-        if (s.mirror) {
-            unsigned w = 0u;
-            if (base < 4 * kG)  // warp-uniform
-                w = __shfl_sync(0xffffffffu, mw, ((threadIdx.x & 31) & ~(kG - 1)) + 2 * (base / kG) + (a.l >> 2));
-            if (valid && k < vh)
-                vm = base < 4 * kG ? (w >> (8 * (a.l & 3))) & 0xffu : (unsigned)s.vmirror[(size_t)a.i * s.max_vnb + k];
-        }
+        const unsigned raw = valid ? (unsigned)vrow[k] : 0u;
+        const int j = (int)(raw & jmask);
+        const unsigned vm = (s.mirror && k < vh) ? raw >> kMirrorShift : 0u;
         const float4 pj = valid ? s.pos_s[j] : pi;
         const Vec3<float> d = displacement_warp(s, pi, pj);  // every lane: a warp vote inside
-        const bool in = valid && pair_in(s, pi, pj, d);
-        const unsigned ball = __ballot_sync(0xffffffffu, in);
-        const unsigned gm = group_mask_bits(ball);
+        const bool in = pair_in_warp(s, valid, pi, pj, d);
+        const unsigned gm = group_mask_bits(__ballot_sync(0xffffffffu, in));
         const int below = min(max(vh - base, 0), kG);  // lanes of this round in the j > i part
-        const int at = cnt + __popc(gm & ((1u << a.l) - 1u));
-        // only rounds that reach the j < i part are ever looked up
-        if (s.mirror && a.l == 0 && base < vn && base + kG > vh)
-            s.vround[(size_t)a.i * s.vround_stride + base / kG] = (unsigned short)(min(cnt, 255) | (gm << 8));
+        const int at = cnt + __popc(gm & lt);
+        if (s.mirror) {  // only rounds that reach the j < i part are ever looked up
+            const unsigned short r = (unsigned short)(min(cnt, 255) | (gm << 8));
+            const int round = base / kG;
+            if (round < kG) {
+                if (a.l == round) rec = r;
+            } else if (a.l == 0 && base < vn && base + kG > vh) {
+                vround[round] = r;
+            }
+        }
         if (in && at < s.max_nb) {
-            row[at] = j;
+            if (!s.mirror) row[at] = j;  // with mirror slots the exact entries' j live in their tags
             store_geo<real>(s, (size_t)a.i * s.max_nb + at, d, pi, pj, j, vm);
         }
         cnt += __popc(gm);
         nh += __popc(gm & ((1u << below) - 1u));
+    }
+    if (s.mirror && a.ok) {
+        const int base = a.l * kG;
+        if (base < vn && base + kG > vh) vround[a.l] = rec;
     }
     if (a.ok && a.l == 0) {
         if (cnt > s.max_nb) set_err(s, kErrCapacity);
