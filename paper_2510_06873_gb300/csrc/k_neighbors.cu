@@ -272,31 +272,26 @@ struct VerletWarpSmem {
     float4 pos[kCandBuf];      // candidate position, index bits in w
     unsigned char q[kCandBuf]; // candidate's stencil cell
     float4 shift[kStencil];    // image shift of each stencil cell
-    int start[kStencil];       // first atom of each stencil cell
-    int off[2][kStencil];      // offset of the cell's segment in part 0 / 1 (-1: not in it)
-    int cnt[kStencil];         // atoms in the cell
 };
 
 // Copy the candidates [k0, k0 + len) of the list into the buffer: lane q
-// copies its stencil cell's segments (in part 0, in part 1), so the warp's
-// loads are all independent of one another.
-__device__ __forceinline__ void verlet_stage(const Sys &s, VerletWarpSmem &w, int nq, int k0, int len, int lane)
+// copies its stencil cell's segments (in part 0 at o0, in part 1 at o1; -1
+// when not in it), so the warp's loads are all independent of one another.
+__device__ __forceinline__ void verlet_stage(const Sys &s, VerletWarpSmem &w, int st, int n, int o0, int o1, int k0,
+                                             int len, int lane)
 {
-    if (lane < nq) {
-        const int st = w.start[lane], n = w.cnt[lane];
 #pragma unroll
-        for (int part = 0; part < 2; ++part) {
-            const int o = w.off[part][lane];
-            if (o < 0) continue;
-            const int lo = max(o, k0), hi = min(o + n, k0 + len);
+    for (int part = 0; part < 2; ++part) {
+        const int o = part == 0 ? o0 : o1;
+        if (o < 0) continue;
+        const int lo = max(o, k0), hi = min(o + n, k0 + len);
 #pragma unroll 4
-            for (int t = lo; t < hi; ++t) {
-                const int j = st + (t - o);
-                float4 pj = s.pos_s[j];
-                pj.w = __int_as_float(j);
-                w.pos[t - k0] = pj;
-                w.q[t - k0] = (unsigned char)lane;
-            }
+        for (int t = lo; t < hi; ++t) {
+            const int j = st + (t - o);
+            float4 pj = s.pos_s[j];
+            pj.w = __int_as_float(j);
+            w.pos[t - k0] = pj;
+            w.q[t - k0] = (unsigned char)lane;
         }
     }
     __syncwarp();
@@ -371,22 +366,25 @@ __device__ __forceinline__ void verlet_cell(const Sys &s, VerletWarpSmem &w, int
     if (na == 0) return;
     const int xyz = s.xyz_of_rank[c];
     const int cx = xyz & 1023, cy = (xyz >> 10) & 1023, cz = xyz >> 20;
-    const int sx = axis_span(s.nc[0]), sy = axis_span(s.nc[1]), sz = axis_span(s.nc[2]);
+    // with images every axis spans three cells: constant divisions below
+    const int sx = kImages ? 3 : axis_span(s.nc[0]), sy = kImages ? 3 : axis_span(s.nc[1]),
+              sz = kImages ? 3 : axis_span(s.nc[2]);
     const int nq = sx * sy * sz;
+    // a cell on the box faces has stencil cells at a periodic image
+    const bool shifted = cx == 0 || cy == 0 || cz == 0 || cx == s.nc[0] - 1 || cy == s.nc[1] - 1 || cz == s.nc[2] - 1;
     // the stencil: lane q < nq looks up cell q (x fastest) and its segments
-    int n0 = 0, n1 = 0;
+    int n0 = 0, n1 = 0, st = 0, n = 0;  // lane q's cell: first atom, atoms, its part-0 / part-1 lengths
     if (lane < nq) {
         const int ex = lane % sx, ey = (lane / sx) % sy, ez = lane / (sx * sy);
         const int x = cx + axis_off(s.nc[0], ex), y = cy + axis_off(s.nc[1], ey), z = cz + axis_off(s.nc[2], ez);
         const int cq = s.rank_of_xyz[(wrap_cell(z, s.nc[2]) * s.nc[1] + wrap_cell(y, s.nc[1])) * s.nc[0] +
                                      wrap_cell(x, s.nc[0])];
-        const int st = s.cell_start[cq];
-        const int n = s.cell_start[cq + 1] - st;
-        w.start[lane] = st;
-        w.cnt[lane] = n;
-        w.shift[lane] = make_float4(x < 0 ? -s.Lhi[0] : (x >= s.nc[0] ? s.Lhi[0] : 0.0f),
-                                    y < 0 ? -s.Lhi[1] : (y >= s.nc[1] ? s.Lhi[1] : 0.0f),
-                                    z < 0 ? -s.Lhi[2] : (z >= s.nc[2] ? s.Lhi[2] : 0.0f), 0.0f);
+        st = s.cell_start[cq];
+        n = s.cell_start[cq + 1] - st;
+        if (kImages && shifted)  // only a cell on the box faces reads the shifts
+            w.shift[lane] = make_float4(x < 0 ? -s.Lhi[0] : (x >= s.nc[0] ? s.Lhi[0] : 0.0f),
+                                        y < 0 ? -s.Lhi[1] : (y >= s.nc[1] ? s.Lhi[1] : 0.0f),
+                                        z < 0 ? -s.Lhi[2] : (z >= s.nc[2] ? s.Lhi[2] : 0.0f), 0.0f);
         n0 = cq >= c ? n : 0;
         n1 = cq <= c ? n : 0;
     }
@@ -401,16 +399,12 @@ __device__ __forceinline__ void verlet_cell(const Sys &s, VerletWarpSmem &w, int
         }
     }
     const int T0 = __shfl_sync(0xffffffffu, i0, 31), T1 = __shfl_sync(0xffffffffu, i1, 31);
-    if (lane < nq) {
-        w.off[0][lane] = n0 > 0 ? i0 - n0 : -1;
-        w.off[1][lane] = n1 > 0 ? T0 + i1 - n1 : -1;
-    }
-    __syncwarp();
+    // lane q's segments in the list (-1: not in that part); lanes past the
+    // stencil have none
+    const int o0 = n0 > 0 ? i0 - n0 : -1, o1 = n1 > 0 ? T0 + i1 - n1 : -1;
     const int T = T0 + T1;
     const bool one_chunk = T <= kCandBuf;
-    // a cell on the box faces has stencil cells at a periodic image
-    const bool shifted = cx == 0 || cy == 0 || cz == 0 || cx == s.nc[0] - 1 || cy == s.nc[1] - 1 || cz == s.nc[2] - 1;
-    if (one_chunk) verlet_stage(s, w, nq, 0, T, lane);
+    if (one_chunk) verlet_stage(s, w, st, n, o0, o1, 0, T, lane);
     for (int ia = 0; ia < na; ++ia) {
         const int i = a0 + ia;
         const float4 pi = s.pos_s[i];
@@ -418,7 +412,7 @@ __device__ __forceinline__ void verlet_cell(const Sys &s, VerletWarpSmem &w, int
         int total = 0, up = 0;
         for (int k0 = 0; k0 < T; k0 += kCandBuf) {
             const int len = min(kCandBuf, T - k0);
-            if (!one_chunk) verlet_stage(s, w, nq, k0, len, lane);
+            if (!one_chunk) verlet_stage(s, w, st, n, o0, o1, k0, len, lane);
             if (shifted) verlet_sweeps<kImages, true>(s, w, i, pi, k0, len, T0, lane, vrow, total, up);
             else verlet_sweeps<kImages, false>(s, w, i, pi, k0, len, T0, lane, vrow, total, up);
             if (!one_chunk) __syncwarp();  // the chunk is read before the next is staged
