@@ -51,12 +51,21 @@ struct metad_ctx {
     std::vector<int> prof_stage;
     int64_t launches = 0;
     int64_t device_bytes = 0;  // requested by cudaMalloc for this context
-    // metad_step as captured CUDA graphs, each valid for the buffers, flags
-    // and hill count it was captured with; a few are kept (least recently
-    // used replaced) so that a caller cycling through several position
-    // buffers replays instead of recapturing
+    // metad_step as captured CUDA graphs, each valid for the flags and hill
+    // count it was captured with; a few are kept (least recently used
+    // replaced).  When every kernel node takes only the descriptor, a graph
+    // serves any position and force buffers: their pointers are patched into
+    // the nodes' descriptors before a replay (otherwise the buffers are part
+    // of the key).
+    struct StepNode {
+        cudaGraphNode_t node;
+        metad::Sys sys;  // the node's argument as last set
+    };
     struct StepGraph {
         cudaGraphExec_t exec = nullptr;
+        cudaGraph_t graph = nullptr;  // kept while its nodes can be patched
+        std::vector<StepNode> nodes;
+        bool patchable = false;
         const float *pos = nullptr;
         float *forces = nullptr;
         int accumulate = -1;
@@ -71,6 +80,62 @@ struct metad_ctx {
 };
 
 namespace {
+
+// Release a captured step (its executable graph and, if kept, the graph).
+void drop_graph(metad_ctx::StepGraph &g)
+{
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+    g.exec = nullptr;
+    g.graph = nullptr;
+    g.nodes.clear();
+    g.patchable = false;
+}
+
+// The captured kernel nodes that take only the descriptor; false when some
+// kernel node takes other arguments (its buffers cannot be patched).
+bool collect_step_nodes(cudaGraph_t graph, std::vector<metad_ctx::StepNode> &out)
+{
+    size_t count = 0;
+    if (cudaGraphGetNodes(graph, nullptr, &count) != cudaSuccess) return false;
+    std::vector<cudaGraphNode_t> nodes(count);
+    if (count && cudaGraphGetNodes(graph, nodes.data(), &count) != cudaSuccess) return false;
+    out.clear();
+    for (cudaGraphNode_t n : nodes) {
+        cudaGraphNodeType type;
+        if (cudaGraphNodeGetType(n, &type) != cudaSuccess) return false;
+        if (type != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeParams kp = {};
+        if (cudaGraphKernelNodeGetParams(n, &kp) != cudaSuccess || !kp.kernelParams) return false;
+        if (!(metad::sys_kernel_neighbors(kp.func) || metad::sys_kernel_cv(kp.func) ||
+              metad::sys_kernel_bias(kp.func) || metad::sys_kernel_gcv(kp.func)))
+            return false;
+        out.push_back({n, *static_cast<const metad::Sys *>(kp.kernelParams[0])});
+    }
+    return true;
+}
+
+// Point a patchable captured step at new position and force buffers: every
+// descriptor that held the old ones gets the new ones.
+cudaError_t patch_step_buffers(metad_ctx::StepGraph &g, const float *pos, float *forces)
+{
+    for (auto &sn : g.nodes) {
+        metad::Sys t = sn.sys;
+        if (t.pos_in == reinterpret_cast<const float4 *>(g.pos)) t.pos_in = reinterpret_cast<const float4 *>(pos);
+        if (t.F_out == g.forces) t.F_out = forces;
+        cudaKernelNodeParams kp = {};
+        cudaError_t e = cudaGraphKernelNodeGetParams(sn.node, &kp);
+        if (e != cudaSuccess) return e;
+        void *args[1] = {&t};
+        kp.kernelParams = args;
+        kp.extra = nullptr;
+        if ((e = cudaGraphExecKernelNodeSetParams(g.exec, sn.node, &kp)) != cudaSuccess) return e;
+        sn.sys = t;
+    }
+    g.pos = pos;
+    g.forces = forces;
+    return cudaSuccess;
+}
 
 metad_status fail(metad_ctx *c, metad_status s, const std::string &msg)
 {
@@ -550,8 +615,7 @@ metad_status metad_destroy(metad_ctx *c)
     for (void *ptr : c->allocs) cudaFree(ptr);
     if (c->host_pinned) cudaFreeHost(c->host_pinned);
     if (c->err_pinned) cudaFreeHost(c->err_pinned);
-    for (auto &g : c->graphs)
-        if (g.exec) cudaGraphExecDestroy(g.exec);
+    for (auto &g : c->graphs) drop_graph(g);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->side) cudaStreamDestroy(c->side);
@@ -860,11 +924,7 @@ metad_status metad_set_cv_atoms(metad_ctx *c, const int32_t *atoms_host, int32_t
         return s;
     c->atoms_set = true;
     c->have_cv = c->have_bias = false;
-    for (auto &g : c->graphs)  // captured steps hold the old descriptor
-        if (g.exec) {
-            cudaGraphExecDestroy(g.exec);
-            g.exec = nullptr;
-        }
+    for (auto &g : c->graphs) drop_graph(g);  // captured steps hold the old descriptor
     return METAD_OK;
 }
 
@@ -907,11 +967,7 @@ metad_status metad_set_box(metad_ctx *c, const double *box_host)
         c->have_nbr = false;
     }
     c->have_cv = c->have_bias = false;
-    for (auto &g : c->graphs)  // captured steps hold the old box
-        if (g.exec) {
-            cudaGraphExecDestroy(g.exec);
-            g.exec = nullptr;
-        }
+    for (auto &g : c->graphs) drop_graph(g);  // captured steps hold the old box
     return METAD_OK;
 }
 
@@ -1195,19 +1251,25 @@ metad_status step_graph(metad_ctx *c, const float *pos_dev, float *forces_dev, i
     if (deposit && c->K >= c->p.hill_capacity) return fail(c, METAD_ERR_CAPACITY, "hill list full");
     const int acc = accumulate ? 1 : 0, dep = deposit ? 1 : 0;
     metad_ctx::StepGraph *hit = nullptr, *lru = &c->graphs[0];
+    bool exact = false;  // a graph captured with these very buffers
     for (auto &x : c->graphs) {
-        if (x.exec && x.pos == pos_dev && x.forces == forces_dev && x.accumulate == acc && x.deposit == dep &&
-            x.K == c->K)
-            hit = &x;
+        if (x.exec && x.accumulate == acc && x.deposit == dep && x.K == c->K) {
+            if (x.pos == pos_dev && x.forces == forces_dev) {
+                hit = &x;
+                exact = true;
+            } else if (x.patchable && !exact && !hit) {
+                hit = &x;  // any buffers, patched in below
+            }
+        }
         if (!x.exec || (lru->exec && x.last_use < lru->last_use)) lru = &x;
     }
     metad_ctx::StepGraph &g = hit ? *hit : *lru;
     g.last_use = ++c->graph_clock;
+    if (hit && !exact) {
+        if ((s = cuda_check(c, patch_step_buffers(g, pos_dev, forces_dev), "graph buffers"))) return s;
+    }
     if (!hit) {
-        if (g.exec) {
-            cudaGraphExecDestroy(g.exec);
-            g.exec = nullptr;
-        }
+        drop_graph(g);
         const int K0 = c->K;
         const int64_t l0 = c->launches;
         if ((s = cuda_check(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "capture")))
@@ -1222,7 +1284,13 @@ metad_status step_graph(metad_ctx *c, const float *pos_dev, float *forces_dev, i
         }
         if ((s = cuda_check(c, e, "end capture"))) return s;
         e = cudaGraphInstantiate(&g.exec, graph, 0);
-        cudaGraphDestroy(graph);
+        if (e == cudaSuccess && collect_step_nodes(graph, g.nodes)) {
+            g.graph = graph;  // kept: its nodes take new buffers in place
+            g.patchable = true;
+        } else {
+            g.nodes.clear();
+            cudaGraphDestroy(graph);
+        }
         if ((s = cuda_check(c, e, "graph instantiate"))) return s;
         g.pos = pos_dev;
         g.forces = forces_dev;

@@ -113,4 +113,17 @@ void launch_grid_fold(const Sys &s, int K, cudaStream_t st)
     k_grid_fold<<<(nodes + 127) / 128, 128, 0, st>>>(s, K);
 }
 
+
+// The kernels of this file whose only argument is the system descriptor
+// (a captured step's nodes of these can take new I/O buffers in place).
+bool sys_kernel_bias(const void *func)
+{
+    static const void *const kernels[] = {
+        (const void *)k_bias,
+    };
+    for (const void *k : kernels)
+        if (k == func) return true;
+    return false;
+}
+
 }  // namespace metad

@@ -1249,4 +1249,32 @@ void set_ylm_constants(cudaStream_t st)
     cudaMemcpyToSymbolAsync(c_ylm, &h, sizeof(h), 0, cudaMemcpyHostToDevice, st);
 }
 
+
+// The kernels of this file whose only argument is the system descriptor
+// (a captured step's nodes of these can take new I/O buffers in place).
+bool sys_kernel_cv(const void *func)
+{
+    static const void *const kernels[] = {
+        (const void *)k_cv_fwd<float, true>,
+        (const void *)k_cv_fwd<float, false>,
+        (const void *)k_cv_fwd<double, true>,
+        (const void *)k_cv_fwd<double, false>,
+        (const void *)k_cv_avg<float>,
+        (const void *)k_cv_avg<double>,
+        (const void *)k_cv_sum<float>,
+        (const void *)k_cv_sum<double>,
+        (const void *)k_adjoint<float>,
+        (const void *)k_adjoint<double>,
+        (const void *)k_force_pairs<float, false>,
+        (const void *)k_force_pairs<float, true>,
+        (const void *)k_force_pairs<double, false>,
+        (const void *)k_force_pairs<double, true>,
+        (const void *)k_force_gather<float>,
+        (const void *)k_force_gather<double>,
+    };
+    for (const void *k : kernels)
+        if (k == func) return true;
+    return false;
+}
+
 }  // namespace metad

@@ -440,4 +440,21 @@ void launch_batch_gcv_step(const BatchView &hills, int hill_total, int fp64, cud
         kb_gcv_step<float><<<hill_total, kGcvThreads, 0, st>>>(hills);
 }
 
+
+// The kernels of this file whose only argument is the system descriptor
+// (a captured step's nodes of these can take new I/O buffers in place).
+bool sys_kernel_gcv(const void *func)
+{
+    static const void *const kernels[] = {
+        (const void *)k_gcv_forward<float>,
+        (const void *)k_gcv_forward<double>,
+        (const void *)k_gcv_forces,
+        (const void *)k_gcv_step<float>,
+        (const void *)k_gcv_step<double>,
+    };
+    for (const void *k : kernels)
+        if (k == func) return true;
+    return false;
+}
+
 }  // namespace metad

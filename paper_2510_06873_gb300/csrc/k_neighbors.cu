@@ -721,4 +721,25 @@ void launch_export_pairs(const Sys &s, int fp64, long long *pairs, int *count, c
         k_export_pairs<float><<<(s.n + 255) / 256, 256, 0, st>>>(s, pairs, count);
 }
 
+
+// The kernels of this file whose only argument is the system descriptor
+// (a captured step's nodes of these can take new I/O buffers in place).
+bool sys_kernel_neighbors(const void *func)
+{
+    static const void *const kernels[] = {
+        (const void *)k_gather_check,
+        (const void *)k_bin_count,
+        (const void *)k_scan_reduce,
+        (const void *)k_scan_down,
+        (const void *)k_bin_scatter,
+        (const void *)k_cell_sort_gather,
+        (const void *)k_verlet,
+        (const void *)k_filter<float>,
+        (const void *)k_filter<double>,
+    };
+    for (const void *k : kernels)
+        if (k == func) return true;
+    return false;
+}
+
 }  // namespace metad

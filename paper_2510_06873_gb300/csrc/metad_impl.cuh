@@ -255,6 +255,12 @@ void launch_force_gather(const Sys &s, int fp64, float *F, int accumulate, cudaS
 void configure_kernels();
 void launch_grid_fold(const Sys &s, int K, cudaStream_t st);
 void launch_nn_stats(const Sys &s, unsigned long long *sum, int *mx, cudaStream_t st);
+// Kernels whose only argument is the descriptor, per file (step graphs patch
+// their I/O buffers in place).
+bool sys_kernel_neighbors(const void *func);
+bool sys_kernel_cv(const void *func);
+bool sys_kernel_bias(const void *func);
+bool sys_kernel_gcv(const void *func);
 void launch_export_pairs(const Sys &s, int fp64, long long *pairs, int *count, cudaStream_t st);
 void launch_per_atom_out(const Sys &s, int fp64, double *out, cudaStream_t st);
 void set_ylm_constants(cudaStream_t st);

@@ -545,6 +545,36 @@ def test_graph_replay_matches_direct_steps(dev):
     assert graph.launch_count - launches0[1] == direct.launch_count - launches0[0]
 
 
+def test_graph_replay_with_new_buffers_every_step(dev):
+    """A captured step serves new position and force buffers (patched into
+    its nodes) with the direct launches' bits: a drifting trajectory, every
+    frame in a buffer of its own, three force buffers in turn, a deposit
+    and rebuilds on the way."""
+    system = synth.wurtzite_system(5000, cfg=94)
+    mp = synth.MethodParams(n_cv=2)
+    p = oracle.params_from(mp, system.box)
+    s0, _, _ = oracle.cv(system.base, p)
+    c = synth.hill_centres(94, 0, s0, mp.sigma, 300)
+    direct = make_ctx(dev, system, mp)
+    graph = make_ctx(dev, system, mp)
+    graph.set_step_graph(True)
+    direct.deposit_hills(c, want_heights=False)
+    graph.deposit_hills(c, want_heights=False)
+    frames = [torch.from_numpy(f).to(dev) for f in synth.drift_trajectory(system, 14, step_sigma=0.1)]
+    FA = [torch.zeros((system.n, 3), dtype=torch.float32, device=dev) for _ in range(3)]
+    FB = [torch.zeros_like(FA[0]) for _ in range(3)]
+    for step, pos in enumerate(frames):
+        dep = step == 5
+        direct.step(pos, FA[step % 3], deposit=dep)
+        graph.step(pos, FB[step % 3], deposit=dep)
+        cvA, VA, _ = direct.read_results()
+        cvB, VB, _ = graph.read_results()
+        assert np.array_equal(cvA, cvB) and VA == VB, step
+        assert torch.equal(FA[step % 3], FB[step % 3]), step
+    assert graph.rebuild_count == direct.rebuild_count > 2
+    assert graph.hill_count == direct.hill_count == 301
+
+
 def test_call_order_and_capacity_errors(dev):
     metad = _metad()
     system = synth.wurtzite_system(3000, cfg=93)
