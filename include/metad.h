@@ -360,6 +360,17 @@ metad_status metad_bias_eval_noalloc(const double *s_dev, int32_t n_cv, const do
  * Errors: METAD_ERR_INVALID (NULL, iters or repeats < 1), METAD_ERR_CUDA. */
 metad_status metad_probe_fp32_peak(int32_t device, int32_t iters, int32_t repeats, double *tflops_host);
 
+/* Accuracy probe of the kernels' FP32 reciprocal square root and reciprocal
+ * (the SFU estimate refined by one Newton-Raphson step with an exactly formed
+ * residual) beside CUDA's correctly rounded intrinsics, for a test.  (No
+ * counterpart in the paper.)  out_dev[i] = f(v_dev[i]) for i < n, with f by
+ * `which`: 0 the kernels' 1/sqrt, 1 __frsqrt_rn, 2 the kernels' 1/v,
+ * 3 __frcp_rn.  Device arrays of n floats, owned by the caller; launched on
+ * `stream` (NULL: the default stream), asynchronous.
+ * Errors: METAD_ERR_INVALID (NULL array, n < 0, which outside 0..3),
+ * METAD_ERR_CUDA (launch failure). */
+metad_status metad_probe_recip(const float *v_dev, float *out_dev, int64_t n, int32_t which, void *stream);
+
 /* Copy the last CVs, bias and bias gradient to the host (any may be NULL).
  * Synchronises and reports any pending device error. */
 metad_status metad_read_results(metad_ctx *ctx, double *cv_host, double *V_host, double *dVds_host);

@@ -9,6 +9,7 @@
 #include <stdint.h>
 
 #include "metad.h"
+#include "metad_impl.cuh"
 
 namespace {
 
@@ -77,4 +78,34 @@ extern "C" metad_status metad_probe_fp32_peak(int32_t device, int32_t iters, int
     if (s) cudaStreamDestroy(s);
     cudaSetDevice(prev);
     return st;
+}
+
+// Accuracy probe of the kernels' FP32 reciprocal square root and reciprocal
+// against CUDA's correctly rounded intrinsics, on the caller's inputs.
+namespace {
+
+__global__ void k_recip_probe(const float *v, float *out, int64_t n, int which)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float x = v[i];
+    float y;
+    switch (which) {
+    case 0: y = metad::rsqrt_newton(x); break;
+    case 1: y = __frsqrt_rn(x); break;
+    case 2: y = metad::recip_newton(x); break;
+    default: y = __frcp_rn(x); break;
+    }
+    out[i] = y;
+}
+
+}  // namespace
+
+extern "C" metad_status metad_probe_recip(const float *v_dev, float *out_dev, int64_t n, int32_t which, void *stream)
+{
+    if (!v_dev || !out_dev || n < 0 || which < 0 || which > 3) return METAD_ERR_INVALID;
+    if (n == 0) return METAD_OK;
+    const int threads = 256;
+    k_recip_probe<<<(unsigned)((n + threads - 1) / threads), threads, 0, (cudaStream_t)stream>>>(v_dev, out_dev, n, which);
+    return cudaGetLastError() == cudaSuccess ? METAD_OK : METAD_ERR_CUDA;
 }

@@ -346,21 +346,44 @@ __device__ __forceinline__ Vec3<double> displacement<double>(const Sys &s, float
     return d;
 }
 
-// 1/sqrt(v) and 1/v with IEEE rounding.  (The SFU estimate refined by one
-// Newton step is cheaper, but its rounding is not centred: over many pairs it
-// shifted the averaged Q6 by about -2e-7 relative, which the bias gradient
-// amplifies past the 1e-5 tolerance.)
+// 1/sqrt(v) and 1/v in FP32, branch-free: the SFU estimate y refined by one
+// Newton-Raphson step whose residual is formed without losing the product's
+// rounding error (Markstein's scheme; the exact error of v*y recovered by an
+// FMA, as in Dekker's two-product).  The step's result is y (1 + r/2) (resp.
+// y (1 + r)) rounded once, within a few units of 2^-44 of the exact value:
+// correctly rounded except next to a rounding tie, and with no rounding
+// bias.  (An estimate refined with a rounded residual rounds with a bias:
+// over many pairs it shifted the averaged Q6 by about -2e-7 relative, which
+// the bias gradient amplifies past the 1e-5 tolerance.)  Positive normal
+// arguments only (squared pair distances, switch denominators >= 1).
+__device__ __forceinline__ float rsqrt_newton(float v)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(v));
+    const float p = v * y;
+    const float pe = fmaf(v, y, -p);                  // v y = p + pe exactly
+    const float r = fmaf(-pe, y, fmaf(-p, y, 1.0f));  // 1 - v y^2
+    return fmaf(0.5f * y, r, y);
+}
+__device__ __forceinline__ float recip_newton(float v)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(v));
+    const float r = fmaf(-v, y, 1.0f);  // 1 - v y, one rounding of a quantity of order 2^-22
+    return fmaf(y, r, y);
+}
+
 template <typename real>
 __device__ __forceinline__ real rsqrt_r(real v);
 template <>
-__device__ __forceinline__ float rsqrt_r<float>(float v) { return __frcp_rn(__fsqrt_rn(v)); }
+__device__ __forceinline__ float rsqrt_r<float>(float v) { return rsqrt_newton(v); }
 template <>
 __device__ __forceinline__ double rsqrt_r<double>(double v) { return 1.0 / sqrt(v); }
 
 template <typename real>
 __device__ __forceinline__ real recip_r(real v);
 template <>
-__device__ __forceinline__ float recip_r<float>(float v) { return __frcp_rn(v); }
+__device__ __forceinline__ float recip_r<float>(float v) { return recip_newton(v); }
 template <>
 __device__ __forceinline__ double recip_r<double>(double v) { return 1.0 / v; }
 

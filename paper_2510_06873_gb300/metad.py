@@ -80,6 +80,8 @@ _SIGS = {
     "metad_rebuild_count": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
     "metad_bias_eval_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.c_int32, _P, _P, ctypes.c_int32,
                                                _P]),
+    "metad_probe_recip": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                         ctypes.c_void_p]),
     "metad_probe_fp32_peak": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                              ctypes.POINTER(ctypes.c_double)]),
     "metad_estimate_bytes": (ctypes.c_int, [ctypes.POINTER(metad_params), ctypes.POINTER(ctypes.c_int64)]),
@@ -337,6 +339,20 @@ def metad_bias_eval_noalloc(s, centers, heights, sigma, out, device=None, stream
         raise MetadError(METAD_ERR_INVALID, where, "s needs n_cv entries and out at least 3")
     _check(None, lib().metad_bias_eval_noalloc(_dptr(s), n_cv, _dptr(centers), _dptr(heights), K, _hptr(sg),
                                                _dptr(out), int(device), stream), where)
+
+
+def metad_probe_recip(v, out, which, stream=None):
+    """out = f(v) on the device for a test of the kernels' FP32 reciprocals:
+    which 0 / 2 the kernels' 1/sqrt / 1/v, 1 / 3 CUDA's correctly rounded ones.
+    v, out: contiguous float32 CUDA tensors of the same size."""
+    import torch
+    for t in (v, out):
+        if not (isinstance(t, torch.Tensor) and t.dtype == torch.float32 and t.is_contiguous() and t.is_cuda):
+            raise MetadError(METAD_ERR_INVALID, "metad_probe_recip", "float32 contiguous CUDA tensors")
+    if v.numel() != out.numel():
+        raise MetadError(METAD_ERR_INVALID, "metad_probe_recip", "sizes differ")
+    _check(None, lib().metad_probe_recip(ctypes.c_void_p(v.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                         int(v.numel()), int(which), stream), "metad_probe_recip")
 
 
 def metad_probe_fp32_peak(device=0, iters=16384, repeats=20):

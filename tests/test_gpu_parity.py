@@ -647,3 +647,32 @@ def test_cv_trajectory_matches_oracle_and_single_frames(dev):
         check_cv(cvs[t], ref)
         one.build_neighbors(frames[t])
         assert np.array_equal(one.cv_forward(), cvs[t])
+
+
+def test_fp32_reciprocals_against_correctly_rounded(dev):
+    """The kernels' FP32 1/sqrt and 1/v (SFU estimate, one Newton-Raphson
+    step with an exactly formed residual) against CUDA's correctly rounded
+    intrinsics over the arguments the kernels see (squared pair distances,
+    switch denominators): at most one ulp apart, almost always equal, and no
+    rounding bias (the signed mean difference far below an ulp)."""
+    metad = _metad()
+    g = torch.Generator(device=dev)
+    g.manual_seed(11)
+    for which, lo, hi in ((0, 0.25, 20.25), (2, 1.0, 12.0)):
+        v = lo + (hi - lo) * torch.rand(4_000_000, generator=g, device=dev, dtype=torch.float32)
+        mine, ref = torch.empty_like(v), torch.empty_like(v)
+        metad.metad_probe_recip(v, mine, which, torch.cuda.current_stream(dev).cuda_stream)
+        metad.metad_probe_recip(v, ref, which + 1, torch.cuda.current_stream(dev).cuda_stream)
+        torch.cuda.synchronize(dev)
+        ulps = (mine.view(torch.int32).long() - ref.view(torch.int32).long()).cpu().numpy()
+        assert np.abs(ulps).max() <= 1, which
+        assert np.mean(ulps != 0) < 1e-3, (which, np.mean(ulps != 0))
+        assert abs(np.mean(ulps)) < 1e-4, (which, np.mean(ulps))
+    # and the absolute error of the refined 1/sqrt against FP64
+    v = 0.25 + 20.0 * torch.rand(1_000_000, generator=g, device=dev, dtype=torch.float32)
+    mine = torch.empty_like(v)
+    metad.metad_probe_recip(v, mine, 0, torch.cuda.current_stream(dev).cuda_stream)
+    torch.cuda.synchronize(dev)
+    exact = 1.0 / np.sqrt(v.double().cpu().numpy())
+    rel = (mine.double().cpu().numpy() - exact) / exact
+    assert np.abs(rel).max() <= 2.0 ** -23 and abs(rel.mean()) < 1e-9
