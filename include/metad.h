@@ -84,10 +84,12 @@ typedef struct {
                                rounded up to a multiple of 4) */
     int32_t device;         /* CUDA device ordinal */
     int32_t step_graph;     /* 1: metad_step replays a captured CUDA graph of
-                               its kernels, one per combination of buffers,
-                               flags and hill count (up to 16 kept, least
-                               recently used replaced; not while profiling).
-                               0 (default): direct launches */
+                               its kernels, one per combination of flags and
+                               hill count (up to 16 kept, least recently used
+                               replaced; not while profiling); new position
+                               and force buffers are patched into a captured
+                               graph, not recaptured.  0 (default): direct
+                               launches */
     void *stream;           /* cudaStream_t, or NULL */
     double skin;            /* Verlet skin in Angstrom (1.0): the cell order and
                                the rc + skin candidate list are rebuilt only
