@@ -140,6 +140,33 @@ __device__ __forceinline__ void ylm13_grad(real x, real y, real z, real inv_r, c
     g[2] = (gz - ug * z) * inv_r;
 }
 
+// sum_k h_k Y_k(u) and g = (I - u u^T) grad(sum_k h_k Y_k) / r in one loop,
+// without materialising the harmonics (fewer live registers in the pair pass).
+template <typename real>
+__device__ __forceinline__ real ylm13_dot_grad(real x, real y, real z, real inv_r, const real h[kNY], real g[3])
+{
+    real P[7], D[7], C[7], S[7];
+    legendre_parts<real>(z, P);
+    legendre_dparts<real>(z, D);
+    cs_powers<real>(x, y, C, S);
+    real t = h[0] * P[0];
+    real gx = real(0), gy = real(0), gz = h[0] * D[0];
+#pragma unroll
+    for (int m = 1; m <= 6; ++m) {
+        const real hc = h[2 * m - 1], hs = h[2 * m];
+        t += hc * (P[m] * C[m]) + hs * (P[m] * S[m]);
+        const real pm = P[m] * real(m);
+        gx += pm * (hc * C[m - 1] + hs * S[m - 1]);
+        gy += pm * (hs * C[m - 1] - hc * S[m - 1]);
+        gz += D[m] * (hc * C[m] + hs * S[m]);
+    }
+    const real ug = x * gx + y * gy + z * gz;
+    g[0] = (gx - ug * x) * inv_r;
+    g[1] = (gy - ug * y) * inv_r;
+    g[2] = (gz - ug * z) * inv_r;
+    return t;
+}
+
 // sum_k K_k a_k^2 with K as a float pair (FP32) or exact (FP64).
 template <typename real>
 __device__ __forceinline__ real weighted_sq(const real a[kNY]);
@@ -825,20 +852,18 @@ __device__ __forceinline__ void pair_force(const Sys &s, int i, int k, real cn_f
         load_rec<real>(hh, i, hi);
         load_rec<real>(hh, j, hj);
         t -= hi[13] + hj[13];
-        real hs[kNY], cvec[kNY];
+        real hs[kNY];
 #pragma unroll
-        for (int m = 0; m < kNY; ++m) {
-            hs[m] = hi[m] + hj[m];
-            cvec[m] = w * hs[m];
-        }
-        real Y[kNY], gY[3];
-        ylm13_grad<real>(ux, uy, uz, inv_r, cvec, Y, gY);
-#pragma unroll
-        for (int m = 0; m < kNY; ++m) t += hs[m] * Y[m];
+        for (int m = 0; m < kNY; ++m) hs[m] = hi[m] + hj[m];
+        // (h_i + h_j).Y and its transverse gradient; the w Y term's gradient
+        // is w times it
+        real gY[3];
+        t += ylm13_dot_grad<real>(ux, uy, uz, inv_r, hs, gY);
         radial += V2 * t * dw;
-        fx = V2 * gY[0];
-        fy = V2 * gY[1];
-        fz = V2 * gY[2];
+        const real vw = V2 * w;
+        fx = vw * gY[0];
+        fy = vw * gY[1];
+        fz = vw * gY[2];
     }
     fx += radial * ux;
     fy += radial * uy;
