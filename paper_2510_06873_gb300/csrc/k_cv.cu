@@ -1202,16 +1202,16 @@ void launch_batch_force(const BatchView &groups, int group_total, const BatchVie
 }
 
 // The gather kernels without shared memory prefer the SM's unified storage
-// as L1.  (Kernels with even a small static shared array are left to the
-// driver: a minimal shared carve-out caps how many of their blocks fit.)
+// as L1.  (Kernels with even a small static shared array, the pair pass's
+// two chain-rule factors among them, are left to the driver: a minimal
+// shared carve-out caps how many of their blocks fit, 7 where the pair
+// pass's registers allow 9.)
 void configure_kernels()
 {
     const int l1 = cudaSharedmemCarveoutMaxL1;
     cudaFuncSetAttribute(k_adjoint<float>, cudaFuncAttributePreferredSharedMemoryCarveout, l1);
-    cudaFuncSetAttribute(k_force_pairs<float>, cudaFuncAttributePreferredSharedMemoryCarveout, l1);
     cudaFuncSetAttribute(k_force_gather<float>, cudaFuncAttributePreferredSharedMemoryCarveout, l1);
     cudaFuncSetAttribute(kb_adjoint<float>, cudaFuncAttributePreferredSharedMemoryCarveout, l1);
-    cudaFuncSetAttribute(kb_force_pairs<float>, cudaFuncAttributePreferredSharedMemoryCarveout, l1);
     cudaFuncSetAttribute(kb_force_gather<float>, cudaFuncAttributePreferredSharedMemoryCarveout, l1);
     cudaGetLastError();
 }
