@@ -790,7 +790,7 @@ __device__ __forceinline__ void adjoint(const Sys &s, Blk k)
 // registers, no spill; measured 163 against 183 us at 1M atoms with the
 // default 47 registers and 10 blocks), unconstrained in FP64.
 template <typename real>
-constexpr int kAdjointBlocks = sizeof(real) == 4 ? 12 : 1;
+constexpr int kAdjointBlocks = sizeof(real) == 4 ? 12 : 0;
 
 template <typename real>
 __global__ void __launch_bounds__(kBlockAtoms, kAdjointBlocks<real>) k_adjoint(Sys s) { adjoint<real>(s, own_blk()); }
