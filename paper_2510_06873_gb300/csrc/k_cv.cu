@@ -90,26 +90,34 @@ __device__ __forceinline__ void legendre_dparts(real z, real D[7])
 template <typename real>
 __device__ __forceinline__ void cs_powers(real x, real y, real C[7], real S[7])
 {
+    // (x + iy)^m; the first power written out (x 1 - y 0 is not folded to x
+    // under IEEE rules: y 0 is not 0 for every y)
     C[0] = real(1);
     S[0] = real(0);
+    C[1] = x;
+    S[1] = y;
 #pragma unroll
-    for (int m = 1; m <= 6; ++m) {
+    for (int m = 2; m <= 6; ++m) {
         C[m] = x * C[m - 1] - y * S[m - 1];
         S[m] = x * S[m - 1] + y * C[m - 1];
     }
 }
 
+// v_k += w Y_k(u) for the 13 harmonics, w applied to the seven Legendre
+// parts (seven products before the thirteen accumulations, where forming
+// the harmonics first takes twelve).
 template <typename real>
-__device__ __forceinline__ void ylm13(real x, real y, real z, real Y[kNY])
+__device__ __forceinline__ void ylm13_acc(real x, real y, real z, real w, real v[kNY])
 {
     real P[7], C[7], S[7];
     legendre_parts<real>(z, P);
     cs_powers<real>(x, y, C, S);
-    Y[0] = P[0];
+    v[0] += w * P[0];
 #pragma unroll
     for (int m = 1; m <= 6; ++m) {
-        Y[2 * m - 1] = P[m] * C[m];
-        Y[2 * m] = P[m] * S[m];
+        const real wp = w * P[m];
+        v[2 * m - 1] += wp * C[m];
+        v[2 * m] += wp * S[m];
     }
 }
 
@@ -383,12 +391,7 @@ __device__ __forceinline__ double cv_fwd_group(const Sys &s, const AtomLane a)
             jwrow[k] = JW<real>{j, w};
             if (cn) v[14] += w;
             v[13] += w;
-            if (s.ncv == 2) {
-                real Y[kNY];
-                ylm13<real>(d.x * inv_r, d.y * inv_r, d.z * inv_r, Y);
-#pragma unroll
-                for (int m = 0; m < kNY; ++m) v[m] += w * Y[m];
-            }
+            if (s.ncv == 2) ylm13_acc<real>(d.x * inv_r, d.y * inv_r, d.z * inv_r, w, v);
         }
     }
     reduce_scatter16<real>(v, a.l);
