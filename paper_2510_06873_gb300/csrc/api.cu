@@ -524,6 +524,16 @@ metad_status state_buffers(metad_ctx *c, Buffers &b, Alloc &&alloc)
 
 extern "C" {
 
+// The row capacity a context uses: 0 asks for 64; rows hold a multiple of
+// four entries, so rows of 8 B (j, w) entries start on 32 B and every even
+// entry begins a 16 B pair that lies inside its row (the Q6 and adjoint
+// passes read entries two per load; the pair search reads four).
+static int32_t row_capacity(int32_t max_neighbors)
+{
+    const int32_t m = max_neighbors == 0 ? 64 : max_neighbors;
+    return (m + 3) / 4 * 4;
+}
+
 metad_status metad_estimate_bytes(const metad_params *p, int64_t *bytes)
 {
     if (!bytes) return METAD_ERR_INVALID;
@@ -533,8 +543,7 @@ metad_status metad_estimate_bytes(const metad_params *p, int64_t *bytes)
     if (v != METAD_OK) return v;
     metad_ctx c;
     c.p = *p;
-    if (c.p.max_neighbors == 0) c.p.max_neighbors = 64;
-    c.p.max_neighbors = (c.p.max_neighbors + 3) / 4 * 4;
+    c.p.max_neighbors = row_capacity(c.p.max_neighbors);
     c.fp64 = c.p.precision == 1;
     if ((v = setup_system(&c))) return v;
     Buffers bf;
@@ -635,9 +644,7 @@ metad_status metad_create(const metad_params *p, metad_ctx **out)
     metad_ctx *c = new (std::nothrow) metad_ctx();
     if (!c) return METAD_ERR_OOM;
     c->p = *p;
-    if (c->p.max_neighbors == 0) c->p.max_neighbors = 64;
-    // rows are read four entries at a time: keep their length a multiple of 4
-    c->p.max_neighbors = (c->p.max_neighbors + 3) / 4 * 4;
+    c->p.max_neighbors = row_capacity(c->p.max_neighbors);
     c->fp64 = c->p.precision == 1;
     metad_status s = cuda_check(c, cudaSetDevice(c->p.device), "cudaSetDevice");
     if (s != METAD_OK) { metad_destroy(c); return s; }

@@ -104,6 +104,20 @@ def test_estimate_bytes_needs_no_gpu_and_grows_with_size(metad):
     assert e.value.status == metad.METAD_ERR_INVALID
 
 
+def test_row_capacity_is_a_multiple_of_four(metad):
+    """Rows hold a multiple of four (j, w) entries (0 asks for 64), so an even
+    entry always begins a 16 B pair inside its row: the Q6 and adjoint passes
+    read row entries two per load.  The creation path and the estimate share
+    the rounding; the estimate shows it without a GPU."""
+    def est(m):
+        p = metad.params_for(20_000, [62.0, 62.0, 62.0])
+        p.max_neighbors = m
+        return metad.metad_estimate_bytes(p)
+
+    assert est(5) == est(6) == est(7) == est(8) < est(9) == est(12)
+    assert est(0) == est(64) == est(61)
+
+
 def test_batch_entry_points_reject_null_without_a_gpu(metad):
     import ctypes
     L = metad.lib()
